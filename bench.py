@@ -1,0 +1,419 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the analyzer hot path; prints one JSON line on rank 0.
+
+Workload: 3840x2160 8-bit 4:2:0 synthetic video (seeded: 30% flat block-aligned area,
+sinusoid texture of period 2-8 px, global pan), block size 32 with the low-pass option --
+the all-optimisations mode of the paper's speed test (Section 3).  One step is one
+vca_push_frames call over a batch of frames already resident in HBM (all seven features
+of every frame, the h state update and the feature read-back).  The batch (64 frames,
+796 MB) is larger than L2, so no step reads its inputs from cache.
+
+`e2e` is the same metric through the same public call with pinned HOST frames: the
+host-to-device copies and the device-to-host feature copy are inside the timed region.
+
+Multi-GPU: the path shards by video (each channel keeps its own h state), so N ranks run
+N independent analyzers on N batches (weak scaling, no collective on the data path);
+the timing is the max over ranks.
+
+--impl reference times the CPU oracle (the plain FP64 statement of the method) on the
+host cores, on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "2160p 8-bit frames/sec (7 features), % of HBM roofline; p99 per-frame latency"
+PAPER_FPS = 292.68  # paper, Section 3: VCA v2.0 with all optimisations on 8 CPU threads, UHD 8-bit
+W, H = 3840, 2160
+FRAME_BYTES = W * H + 2 * (W // 2) * (H // 2)  # 12,441,600 B per 8-bit 4:2:0 frame
+KERNEL_SOURCES = ("paper_2304_12384_gb300/csrc/vca_tc.cu", "paper_2304_12384_gb300/csrc/vca_plain.cu")
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="vca", choices=["vca", "reference"])
+    p.add_argument("--frames", type=int, default=64, help="frames per step (one push)")
+    p.add_argument("--distinct", type=int, default=16, help="distinct synthetic frames tiled into the batch")
+    p.add_argument("--kernel", default="auto", choices=["auto", "plain", "tc"])
+    p.add_argument("--block-size", type=int, default=32)
+    p.add_argument("--full", action="store_true", help="all coefficients instead of the low-pass subset")
+    p.add_argument("--no-extras", action="store_true", help="skip variants, latency, e2e and cpu baseline")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# CPU legs (oracle)
+# ---------------------------------------------------------------------------
+
+def oracle_fps(frames, cfg, budget_s):
+    """Frames/s of the oracle on the host cores over a bounded sample; returns (fps, n)."""
+    from oracle import frame_block_values, frame_features
+
+    prev = None
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        y, u, v = frames[n % len(frames)]
+        vals = frame_block_values(y, u, v, cfg)
+        frame_features(vals, prev, cfg)
+        prev = vals["H_Y"]
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or n >= 200:
+            return n / el, n
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import Config
+    from synth import frames_list, uhd_spec
+
+    lp = not args.full
+    cfg = Config(W, H, 8, args.block_size, lp)
+    frames = frames_list(uhd_spec(3), 0, 2)
+    per_step = max(1.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_fps(frames, cfg, 0.0)
+    times = []
+    total_frames = 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        _, n = oracle_fps(frames, cfg, per_step)
+        times.append(time.perf_counter() - t0)
+        total_frames += n
+    value = total_frames / sum(times)
+    sample = (f"{total_frames} frames of 3840x2160 8-bit (2 distinct synthetic frames), w={args.block_size}, "
+              f"low_pass={lp}, oracle frame_block_values + frame_features, one process")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": value / PAPER_FPS, "dtype": "int64",
+        "data": "synthetic", "config": workload_config(args),
+        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU legs
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, power, reasons = [], None, [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for n, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def workload_config(args):
+    lp = not args.full
+    return {"workload": f"3840x2160 8-bit 4:2:0 synthetic, block {args.block_size}, "
+                        f"{'low-pass quarter' if lp else 'all coefficients'}, {args.frames} frames per push",
+            "width": W, "height": H, "bit_depth": 8, "block_size": args.block_size, "low_pass": lp,
+            "frames_per_step": args.frames,
+            "l2": f"inputs larger than L2 ({args.frames * FRAME_BYTES / 1e6:.0f} MB per step, 129 MB L2)"}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel_name, block_size, low_pass):
+    """DRAM bytes per frame of the analysis kernel from the committed ncu summary, if it was
+    captured from the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic_summary.txt")
+    if not os.path.exists(path):
+        return None
+    want = kernel_source_hash()
+    key = f"{kernel_name} w{block_size} lp{int(low_pass)}"
+    with open(path) as f:
+        for line in f:
+            if line.startswith(key + " "):
+                parts = dict(p.split("=", 1) for p in line.split()[3:] if "=" in p)
+                if parts.get("source_hash") == want:
+                    return float(parts["dram_bytes_per_frame"])
+    return None
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def make_device_frames(args, device, bit_depth=8):
+    import numpy as np
+    import torch
+
+    from synth import frames_list, pack_planes, uhd_spec
+
+    frames = frames_list(uhd_spec(3, bit_depth=bit_depth), 0, args.distinct)
+    pk = pack_planes(frames)
+    tens = []
+    for k in ("y", "u", "v"):
+        a = pk[k]
+        if a.dtype == np.uint16:
+            a = a.view(np.int16)
+        src = torch.from_numpy(np.ascontiguousarray(a))
+        dst = torch.empty((args.frames,) + tuple(src.shape[1:]), dtype=src.dtype, device=device)
+        for i in range(args.frames):
+            dst[i].copy_(src[i % args.distinct])
+        tens.append(dst)
+    return frames, tens
+
+
+def time_pushes(an, y, u, v, steps, warmup, stream, barrier):
+    import torch
+
+    from paper_2304_12384_gb300 import vca
+
+    for _ in range(warmup):
+        an.push(y, u, v)
+    an.sync()
+    barrier()
+    torch.cuda.synchronize()
+    vca.vca_set_kernel_timing(an.handle, 1)
+    ms0, n0 = vca.vca_read_kernel_timing(an.handle)
+    l0 = an.launches
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(steps):
+        an.push(y, u, v)
+    end.record(stream)
+    end.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    ms = start.elapsed_time(end)
+    ms1, n1 = vca.vca_read_kernel_timing(an.handle)
+    vca.vca_set_kernel_timing(an.handle, 0)
+    launches = an.launches - l0
+    kernel_ms = (ms1 - ms0) / max(1, n1 - n0)
+    return ms, kernel_ms, launches
+
+
+def run_vca(args):
+    import torch
+
+    from paper_2304_12384_gb300 import build as vbuild
+    from paper_2304_12384_gb300 import vca
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+
+        def barrier():
+            dist.barrier()
+
+        def max_over_ranks(x):
+            t = torch.tensor([x], dtype=torch.float64, device=device)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return float(t.item())
+    else:
+        def barrier():
+            pass
+
+        def max_over_ranks(x):
+            return x
+
+    vbuild.build()
+    kern = {"auto": vca.VCA_KERNEL_AUTO, "plain": vca.VCA_KERNEL_PLAIN, "tc": vca.VCA_KERNEL_TC}[args.kernel]
+    lp = not args.full
+    stream = torch.cuda.current_stream(device)
+    frames, (y, u, v) = make_device_frames(args, device)
+    torch.cuda.synchronize()
+
+    an = vca.Analyzer(W, H, 8, args.block_size, lp, kernel=kern, max_batch=args.frames, stream=stream.cuda_stream)
+    kernel_name = {1: "plain", 2: "tc"}[an.kernel]
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms, kernel_ms, launches = time_pushes(an, y, u, v, args.steps, args.warmup, stream, barrier)
+    clocks = sampler.stop()
+    ms_max = max_over_ranks(ms)
+    frames_total = args.steps * args.frames * world
+    value = frames_total / (ms_max / 1000.0)
+    ms_per_step = ms_max / args.steps
+
+    peak, peak_kind = load_peaks()
+    kernel_frames_per_launch = args.frames
+    achieved = kernel_frames_per_launch * FRAME_BYTES / (kernel_ms / 1000.0) / 1e9
+    traffic_pf = measured_traffic(kernel_name, args.block_size, lp)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic_pf * kernel_frames_per_launch if traffic_pf else None,
+                "peak_kind": peak_kind, "kernel": f"vca analysis ({kernel_name})",
+                "algorithmic_bytes_per_launch": kernel_frames_per_launch * FRAME_BYTES,
+                "kernel_ms_per_launch": kernel_ms}
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras = run_extras(args, an, y, u, v, frames, stream, kern, lp, device)
+    an.close()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": value / PAPER_FPS, "dtype": "int32", "data": "synthetic",
+            "config": workload_config(args), "kernel": kernel_name, "roofline": roofline,
+            "gpu_launches": launches, "clocks": clocks,
+            "hbm_roofline_fps": peak * 1e9 / FRAME_BYTES,
+        }
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_extras(args, an, y, u, v, frames, stream, kern, lp, device):
+    import numpy as np
+    import torch
+
+    from oracle import Config
+    from paper_2304_12384_gb300 import vca
+
+    out = {}
+    # Per-frame latency: one device-resident frame per push, features read back (blocking).
+    lat = []
+    for i in range(20 + 200):
+        t0 = time.perf_counter()
+        an.push(y[i % args.frames], u[i % args.frames], v[i % args.frames])
+        last = vca.vca_read_frame_features(an.handle, an.frames_pushed - 1, 1)
+        t1 = time.perf_counter()
+        if i >= 20:
+            lat.append((t1 - t0) * 1000.0)
+    assert last.frame >= 0
+    out["latency_ms"] = {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                         "frames": len(lat), "mode": "one 2160p frame per push, blocking feature read"}
+
+    # End to end: pinned host frames through the same call, copies inside the timed region.
+    hy = y.cpu().pin_memory()
+    hu = u.cpu().pin_memory()
+    hv = v.cpu().pin_memory()
+    for _ in range(2):
+        an.push(hy, hu, hv)
+    an.sync()
+    steps = max(3, min(args.steps, 10))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        an.push(hy, hu, hv)
+        vca.vca_read_frame_features(an.handle, an.frames_pushed - 1, 1)
+    an.sync()
+    el = time.perf_counter() - t0
+    out["e2e"] = {"value": steps * args.frames / el, "unit": "frames/s",
+                  "h2d_bytes_per_step": args.frames * FRAME_BYTES, "d2h_bytes_per_step": args.frames * 8 * 8}
+    del hy, hu, hv
+
+    # Other block-size / low-pass variants and the plain CUDA-core form, same frames.
+    variants = {}
+    for (bs, vlp, vk) in ((32, True, vca.VCA_KERNEL_PLAIN), (32, False, kern), (16, True, kern), (16, False, kern),
+                          (32, False, vca.VCA_KERNEL_PLAIN)):
+        try:
+            a2 = vca.Analyzer(W, H, 8, bs, vlp, kernel=vk, max_batch=args.frames, stream=stream.cuda_stream)
+        except vca.VcaError as e:
+            variants[f"w{bs}_{'lp' if vlp else 'full'}_{vk}"] = f"unsupported: {e}"
+            continue
+        name = f"w{bs}_{'lowpass' if vlp else 'full'}_{ {1: 'plain', 2: 'tc'}[a2.kernel] }"
+        ms, kms, _ = time_pushes(a2, y, u, v, max(3, args.steps // 3), 2, stream, lambda: None)
+        n = max(3, args.steps // 3) * args.frames
+        variants[name] = {"fps": n / (ms / 1000.0), "kernel_ms_per_launch": kms,
+                          "hbm_frac_of_measured": args.frames * FRAME_BYTES / (kms / 1000.0) / 1e9 / load_peaks()[0]}
+        a2.close()
+    out["variants"] = variants
+
+    # CPU oracle on the host cores, bounded sample of the same workload.
+    cfg = Config(W, H, 8, args.block_size, lp)
+    fps, n = oracle_fps(frames[:2], cfg, args.cpu_seconds)
+    out["cpu_baseline"] = {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                           "sample": f"{n} frames of the same 3840x2160 workload through the FP64/int64 oracle "
+                                     f"(numpy, one process, single-threaded integer matmul)"}
+    return out
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_vca(args)
+
+
+if __name__ == "__main__":
+    main()

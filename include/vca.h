@@ -1,0 +1,178 @@
+/*
+ * vca.h -- C ABI of the GB300 Video Complexity Analyzer (VCA) hot path.
+ *
+ * The analyzer computes, for every frame of a planar YUV 4:2:0 video, the seven
+ * blockwise DCT-energy features named in Section 2 of "Green Video Complexity
+ * Analysis for Efficient Encoding in Adaptive Video Streaming" (GMSys '23):
+ * the luma texture energy E_Y, its temporal gradient h, the luminescence L_Y,
+ * the chroma texture energies E_U, E_V and the chrominances L_U, L_V.  Section 2
+ * item (3) adds the low-pass option (only the low-frequency quarter of each
+ * block's coefficients is computed).
+ *
+ * Definitions used (the paper names the features; these are the readings the
+ * library implements, identically to the test oracle):
+ *   blocks      luma w x w, chroma (w/2) x (w/2) on the same grid, C blocks per
+ *               plane, raster order; partial edge blocks repeat the last
+ *               row/column (VCA_PAD_REPLICATE) or are dropped (VCA_PAD_SKIP);
+ *   transform   integer DCT, M_N[k][n] = round_half_away(64 sqrt(N) alpha_k
+ *               cos(pi(2n+1)k/2N)); rows first, T = (X M^T + 2^(s1-1)) >> s1,
+ *               then columns, Z = (M T + 2^(s2-1)) >> s2, s1 = log2 N + B - 9,
+ *               s2 = log2 N + 6 (B = bit depth); results are bit-exact integers;
+ *   block       H = sum_{(u,v) != (0,0)} w_N(u,v) |Z(u,v)| with
+ *               w_N(u,v) = exp(|((u+1)(v+1)/N^2)^2 - 1|), in FP32;
+ *               L = sqrt(Z(0,0)), in FP32;
+ *   frame       E_P = sum_k H_{P,k} / (C N_P^2), L_P = sum_k L_{P,k} / C,
+ *               h_t = sum_k |H_{Y,k,t} - H_{Y,k,t-1}| / (C w^2), h_0 = 0,
+ *               summed in FP64 in a fixed order (deterministic);
+ *   sequence    arithmetic mean over frames (h over frames t >= 1).
+ *
+ * Conventions for every call:
+ *   - every call returns a vca_status; no exception or abort crosses the ABI;
+ *     vca_last_error() gives a one-line message for the calling thread;
+ *   - the caller owns frame buffers; the library owns its device state, which
+ *     vca_close() frees;
+ *   - device frame buffers must stay valid and unchanged until the pushed
+ *     frames' features have been read (or vca_sync() returned); host frame
+ *     buffers are consumed before vca_push_frame(s) returns;
+ *   - plane base pointers and pitches must be multiples of 16 bytes;
+ *     samples are uint8 (bit_depth 8) or little-endian 16-bit words holding
+ *     values in [0, 1023] (bit_depth 10); values outside [0, 2^B - 1] are
+ *     undefined behaviour;
+ *   - an analyzer is bound to one CUDA stream and is not thread-safe; distinct
+ *     analyzers may be used from distinct threads.
+ */
+#ifndef VCA_H
+#define VCA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum vca_status {
+  VCA_OK = 0,
+  VCA_E_ARG = -1,          /* invalid argument (NULL, size, alignment, range) */
+  VCA_E_UNSUPPORTED = -2,  /* valid but unsupported configuration */
+  VCA_E_NOMEM = -3,        /* device or pinned host allocation failed */
+  VCA_E_CUDA = -4,         /* a CUDA runtime / driver call failed */
+  VCA_E_AGAIN = -5,        /* result not ready (non-blocking read) */
+  VCA_E_TIMEOUT = -6,      /* a bounded device wait gave up */
+  VCA_E_STATE = -7         /* call not valid in the analyzer's current state */
+} vca_status;
+
+enum { VCA_PAD_REPLICATE = 0, VCA_PAD_SKIP = 1 };
+enum { VCA_KERNEL_AUTO = 0, VCA_KERNEL_PLAIN = 1, VCA_KERNEL_TC = 2 };
+
+/* Analyzer configuration (Section 2: one analyzer per video). */
+typedef struct vca_config {
+  int32_t width;       /* luma width in samples, even, >= 2 */
+  int32_t height;      /* luma height in samples, even, >= 2 */
+  int32_t bit_depth;   /* 8 or 10 */
+  int32_t block_size;  /* luma block size w: 16 or 32; chroma blocks are w/2 */
+  int32_t low_pass;    /* 0 = all coefficients, 1 = only u, v < N/2 (Section 2 item (3)) */
+  int32_t pad_mode;    /* VCA_PAD_REPLICATE (default) or VCA_PAD_SKIP */
+  int32_t kernel;      /* VCA_KERNEL_AUTO, VCA_KERNEL_PLAIN (CUDA cores) or VCA_KERNEL_TC (tensor cores) */
+  int32_t max_batch;   /* most frames one vca_push_frames call may carry; 0 selects 64 */
+} vca_config;
+
+/* The seven features of one frame (Section 2), frame = 0-based index since vca_open. */
+typedef struct vca_frame_features {
+  int64_t frame;
+  double E_Y, h, L_Y, E_U, E_V, L_U, L_V;
+} vca_frame_features;
+
+/* Means over all frames read so far; h averages frames t >= 1. */
+typedef struct vca_sequence_features {
+  int64_t frames;
+  double E_Y, h, L_Y, E_U, E_V, L_U, L_V;
+} vca_sequence_features;
+
+typedef struct vca_analyzer vca_analyzer;
+
+/* Number of blocks C per plane for a configuration (Section 2: blockwise features).
+ * Returns VCA_E_ARG for an invalid configuration. */
+vca_status vca_block_count(const vca_config* cfg, int64_t* blocks_x, int64_t* blocks_y);
+
+/* Open an analyzer for one video (Section 2).  cuda_stream is a cudaStream_t
+ * (NULL = the legacy default stream) on which all of the analyzer's device work
+ * is ordered.  The current CUDA device at this call is the analyzer's device.
+ * On success *out owns device buffers sized for cfg->max_batch frames. */
+vca_status vca_open(const vca_config* cfg, void* cuda_stream, vca_analyzer** out);
+
+/* Analyse one frame (Section 2: seven features per frame).  y, u, v point at the
+ * first sample of each plane; pitch_y / pitch_uv are row strides in bytes.
+ * on_device = 1: the planes are device memory, read asynchronously on the
+ * analyzer's stream.  on_device = 0: host memory, copied to the device before
+ * the call returns (pinned memory makes that copy faster). */
+vca_status vca_push_frame(vca_analyzer* a, const void* y, const void* u, const void* v,
+                          int64_t pitch_y, int64_t pitch_uv, int32_t on_device);
+
+/* Analyse n_frames consecutive frames in one launch.  Frame i's planes start at
+ * y + i*frame_stride_y, u + i*frame_stride_uv, v + i*frame_stride_uv (bytes).
+ * Strides must be multiples of 16 bytes; 1 <= n_frames <= max_batch. */
+vca_status vca_push_frames(vca_analyzer* a, const void* y, const void* u, const void* v,
+                           int64_t pitch_y, int64_t pitch_uv,
+                           int64_t frame_stride_y, int64_t frame_stride_uv,
+                           int32_t n_frames, int32_t on_device);
+
+/* Features of frame `frame` (0-based).  blocking = 0 returns VCA_E_AGAIN while the
+ * frame is still being computed; blocking = 1 waits.  VCA_E_ARG for a frame not
+ * pushed yet. */
+vca_status vca_read_frame_features(vca_analyzer* a, int64_t frame, int32_t blocking, vca_frame_features* out);
+
+/* Per-sequence features over every frame pushed so far (waits for them). */
+vca_status vca_read_sequence_features(vca_analyzer* a, vca_sequence_features* out);
+
+/* Per-block values (FP32, raster order, C entries each; any pointer may be NULL)
+ * of frame `index` within the most recent vca_push_frame(s) call.  Waits for it. */
+vca_status vca_read_block_values(vca_analyzer* a, int32_t index, float* H_Y, float* L_Y,
+                                 float* H_U, float* L_U, float* H_V, float* L_V);
+
+/* Quantised coefficients Z of one frame, computed by the analyzer's kernel with
+ * the coefficient dump enabled (bit-exact integers; parity checks).  zy, zu, zv
+ * are device buffers of C*Nk*Nk int16 each (Nk = N, or N/2 with low_pass; N = w
+ * for Y, w/2 for U, V), block-major, then row u, then column v.  Planes are on
+ * the device.  Does not change the analyzer's frame count or h state. */
+vca_status vca_dump_coefficients(vca_analyzer* a, const void* y, const void* u, const void* v,
+                                 int64_t pitch_y, int64_t pitch_uv,
+                                 int16_t* zy, int16_t* zu, int16_t* zv);
+
+/* Wait for all of the analyzer's device work. */
+vca_status vca_sync(vca_analyzer* a);
+
+/* Cross-frame state (the previous frame's luma block energies that h needs, and
+ * the frame counter) as bytes, so a channel can resume with a correct h.
+ * Call with buf = NULL to get the size in *len. */
+vca_status vca_export_state(vca_analyzer* a, void* buf, size_t* len);
+vca_status vca_import_state(vca_analyzer* a, const void* buf, size_t len);
+
+/* Frames pushed since vca_open (or since the frame count an imported state carried). */
+vca_status vca_frames_pushed(vca_analyzer* a, int64_t* frames);
+
+/* Number of kernel launches this analyzer has issued (for launch accounting). */
+vca_status vca_launch_count(vca_analyzer* a, int64_t* launches);
+
+/* Kernel timing: with enable = 1, every later push brackets its analysis kernel(s) with
+ * CUDA events on the analyzer's stream; vca_read_kernel_timing returns the summed
+ * device time (ms) and the number of timed pushes among the pushes read so far
+ * (it waits for all pushed frames). */
+vca_status vca_set_kernel_timing(vca_analyzer* a, int32_t enable);
+vca_status vca_read_kernel_timing(vca_analyzer* a, double* total_ms, int64_t* timed_pushes);
+
+/* Kernel the analyzer runs: VCA_KERNEL_PLAIN or VCA_KERNEL_TC. */
+vca_status vca_kernel_in_use(vca_analyzer* a, int32_t* kernel);
+
+/* Free the analyzer (waits for its device work). NULL is accepted. */
+vca_status vca_close(vca_analyzer* a);
+
+/* Static description of a status code, and the calling thread's last error message. */
+const char* vca_status_str(vca_status s);
+const char* vca_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VCA_H */

@@ -1,0 +1,321 @@
+"""ctypes binding of libvca.so (include/vca.h), argument marshalling only.
+
+Every function keeps the C name and forwards to the library; all analysis runs in the
+library's CUDA kernels.  If the library has not been built, loading fails loudly: there
+is no Python or CPU fallback.  ``Analyzer`` is a small convenience wrapper that passes
+torch tensors' device pointers and the current torch stream.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+from .build import LIB_PATH
+
+VCA_OK = 0
+VCA_E_ARG = -1
+VCA_E_UNSUPPORTED = -2
+VCA_E_NOMEM = -3
+VCA_E_CUDA = -4
+VCA_E_AGAIN = -5
+VCA_E_TIMEOUT = -6
+VCA_E_STATE = -7
+
+VCA_PAD_REPLICATE = 0
+VCA_PAD_SKIP = 1
+VCA_KERNEL_AUTO = 0
+VCA_KERNEL_PLAIN = 1
+VCA_KERNEL_TC = 2
+
+FEATURES = ("E_Y", "h", "L_Y", "E_U", "E_V", "L_U", "L_V")
+
+
+class VcaConfig(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("bit_depth", ctypes.c_int32),
+                ("block_size", ctypes.c_int32), ("low_pass", ctypes.c_int32), ("pad_mode", ctypes.c_int32),
+                ("kernel", ctypes.c_int32), ("max_batch", ctypes.c_int32)]
+
+
+class VcaFrameFeatures(ctypes.Structure):
+    _fields_ = [("frame", ctypes.c_int64)] + [(k, ctypes.c_double) for k in FEATURES]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k in FEATURES}
+
+
+class VcaSequenceFeatures(ctypes.Structure):
+    _fields_ = [("frames", ctypes.c_int64)] + [(k, ctypes.c_double) for k in FEATURES]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k in FEATURES}
+        d["frames"] = self.frames
+        return d
+
+
+class VcaError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+
+_PROTOS = {
+    "vca_block_count": (ctypes.POINTER(VcaConfig), ctypes.POINTER(_I64), ctypes.POINTER(_I64)),
+    "vca_open": (ctypes.POINTER(VcaConfig), _P, ctypes.POINTER(_P)),
+    "vca_push_frame": (_P, _P, _P, _P, _I64, _I64, _I32),
+    "vca_push_frames": (_P, _P, _P, _P, _I64, _I64, _I64, _I64, _I32, _I32),
+    "vca_read_frame_features": (_P, _I64, _I32, ctypes.POINTER(VcaFrameFeatures)),
+    "vca_read_sequence_features": (_P, ctypes.POINTER(VcaSequenceFeatures)),
+    "vca_read_block_values": (_P, _I32, _P, _P, _P, _P, _P, _P),
+    "vca_dump_coefficients": (_P, _P, _P, _P, _I64, _I64, _P, _P, _P),
+    "vca_sync": (_P,),
+    "vca_export_state": (_P, _P, ctypes.POINTER(ctypes.c_size_t)),
+    "vca_import_state": (_P, _P, ctypes.c_size_t),
+    "vca_frames_pushed": (_P, ctypes.POINTER(_I64)),
+    "vca_launch_count": (_P, ctypes.POINTER(_I64)),
+    "vca_kernel_in_use": (_P, ctypes.POINTER(_I32)),
+    "vca_set_kernel_timing": (_P, _I32),
+    "vca_read_kernel_timing": (_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)),
+    "vca_close": (_P,),
+}
+
+
+def lib():
+    """The loaded library; raises if it was not built (no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libvca.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _PROTOS.items():
+            fn = getattr(L, name)
+            fn.argtypes = list(args)
+            fn.restype = ctypes.c_int
+        L.vca_status_str.argtypes = [ctypes.c_int]
+        L.vca_status_str.restype = ctypes.c_char_p
+        L.vca_last_error.argtypes = []
+        L.vca_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_PROTOS) + ["vca_status_str", "vca_last_error"]
+
+
+def _check(status: int) -> int:
+    if status != VCA_OK:
+        L = lib()
+        raise VcaError(status, (L.vca_last_error() or b"").decode() or L.vca_status_str(status).decode())
+    return status
+
+
+def vca_status_str(status: int) -> str:
+    return lib().vca_status_str(status).decode()
+
+
+def vca_last_error() -> str:
+    return lib().vca_last_error().decode()
+
+
+def vca_block_count(cfg: VcaConfig) -> tuple[int, int]:
+    bx, by = _I64(), _I64()
+    _check(lib().vca_block_count(ctypes.byref(cfg), ctypes.byref(bx), ctypes.byref(by)))
+    return bx.value, by.value
+
+
+def vca_open(cfg: VcaConfig, stream: int = 0) -> int:
+    h = _P()
+    _check(lib().vca_open(ctypes.byref(cfg), _P(stream), ctypes.byref(h)))
+    return h.value
+
+
+def vca_push_frame(a, y, u, v, pitch_y, pitch_uv, on_device=1):
+    return _check(lib().vca_push_frame(a, y, u, v, pitch_y, pitch_uv, on_device))
+
+
+def vca_push_frames(a, y, u, v, pitch_y, pitch_uv, frame_stride_y, frame_stride_uv, n_frames, on_device=1):
+    return _check(lib().vca_push_frames(a, y, u, v, pitch_y, pitch_uv, frame_stride_y, frame_stride_uv,
+                                        n_frames, on_device))
+
+
+def vca_read_frame_features(a, frame: int, blocking: int = 1) -> VcaFrameFeatures:
+    out = VcaFrameFeatures()
+    _check(lib().vca_read_frame_features(a, frame, blocking, ctypes.byref(out)))
+    return out
+
+
+def vca_read_sequence_features(a) -> VcaSequenceFeatures:
+    out = VcaSequenceFeatures()
+    _check(lib().vca_read_sequence_features(a, ctypes.byref(out)))
+    return out
+
+
+def vca_read_block_values(a, index: int, H_Y=None, L_Y=None, H_U=None, L_U=None, H_V=None, L_V=None):
+    return _check(lib().vca_read_block_values(a, index, H_Y, L_Y, H_U, L_U, H_V, L_V))
+
+
+def vca_dump_coefficients(a, y, u, v, pitch_y, pitch_uv, zy, zu, zv):
+    return _check(lib().vca_dump_coefficients(a, y, u, v, pitch_y, pitch_uv, zy, zu, zv))
+
+
+def vca_sync(a):
+    return _check(lib().vca_sync(a))
+
+
+def vca_export_state(a) -> bytes:
+    n = ctypes.c_size_t(0)
+    _check(lib().vca_export_state(a, None, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib().vca_export_state(a, buf, ctypes.byref(n)))
+    return buf.raw[: n.value]
+
+
+def vca_import_state(a, state: bytes):
+    buf = ctypes.create_string_buffer(state, len(state))
+    return _check(lib().vca_import_state(a, buf, len(state)))
+
+
+def vca_frames_pushed(a) -> int:
+    n = _I64()
+    _check(lib().vca_frames_pushed(a, ctypes.byref(n)))
+    return n.value
+
+
+def vca_launch_count(a) -> int:
+    n = _I64()
+    _check(lib().vca_launch_count(a, ctypes.byref(n)))
+    return n.value
+
+
+def vca_kernel_in_use(a) -> int:
+    k = _I32()
+    _check(lib().vca_kernel_in_use(a, ctypes.byref(k)))
+    return k.value
+
+
+def vca_set_kernel_timing(a, enable: int):
+    return _check(lib().vca_set_kernel_timing(a, int(enable)))
+
+
+def vca_read_kernel_timing(a) -> tuple[float, int]:
+    ms, n = ctypes.c_double(), _I64()
+    _check(lib().vca_read_kernel_timing(a, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def vca_close(a):
+    return _check(lib().vca_close(a))
+
+
+class Analyzer:
+    """One analyzer (one video) on the current CUDA device and torch stream.
+
+    Frames are torch tensors: device tensors are read in place; CPU tensors are copied by
+    the library.  Planes are indexed (frame, row, column-in-samples) and may have a row
+    pitch larger than the width.
+    """
+
+    def __init__(self, width, height, bit_depth=8, block_size=32, low_pass=False, pad_mode=VCA_PAD_REPLICATE,
+                 kernel=VCA_KERNEL_AUTO, max_batch=64, stream=None):
+        import torch
+
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.cfg = VcaConfig(width, height, bit_depth, block_size, int(bool(low_pass)), pad_mode, kernel, max_batch)
+        self.handle = vca_open(self.cfg, stream)
+        self.blocks_x, self.blocks_y = vca_block_count(self.cfg)
+        self.C = self.blocks_x * self.blocks_y
+
+    def close(self):
+        if self.handle:
+            vca_close(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _plane_args(t):
+        es = t.element_size()
+        pitch = t.stride(-2) * es
+        fstride = t.stride(0) * es if t.dim() == 3 else 0
+        return t.data_ptr(), pitch, fstride
+
+    def push(self, y, u, v):
+        """Push frames given as (F, H, pitch) / (F, H/2, pitch) tensors or one (H, pitch) frame each."""
+        on_device = 1 if y.is_cuda else 0
+        n = y.shape[0] if y.dim() == 3 else 1
+        py, pitch_y, fy = self._plane_args(y)
+        pu, pitch_uv, fu = self._plane_args(u)
+        pv, pitch_v, fv = self._plane_args(v)
+        if pitch_v != pitch_uv or fv != fu:
+            raise ValueError("U and V planes must share pitch and frame stride")
+        vca_push_frames(self.handle, py, pu, pv, pitch_y, pitch_uv, fy, fu, n, on_device)
+        return n
+
+    def frame_features(self, frame, blocking=True) -> dict:
+        return vca_read_frame_features(self.handle, frame, int(blocking)).as_dict()
+
+    def sequence_features(self) -> dict:
+        return vca_read_sequence_features(self.handle).as_dict()
+
+    def block_values(self, index=0) -> dict:
+        import numpy as np
+
+        out = {k: np.zeros(self.C, dtype=np.float32) for k in ("H_Y", "L_Y", "H_U", "L_U", "H_V", "L_V")}
+        vca_read_block_values(self.handle, index, *(out[k].ctypes.data for k in ("H_Y", "L_Y", "H_U", "L_U", "H_V",
+                                                                                  "L_V")))
+        return out
+
+    def dump_coefficients(self, y, u, v):
+        """Quantised coefficients of one device frame: dict plane -> int16 tensor (C, Nk, Nk)."""
+        import torch
+
+        w = self.cfg.block_size
+        nk_y = w // 2 if self.cfg.low_pass else w
+        nk_c = nk_y // 2
+        zy = torch.empty((self.C, nk_y, nk_y), dtype=torch.int16, device=y.device)
+        zu = torch.empty((self.C, nk_c, nk_c), dtype=torch.int16, device=y.device)
+        zv = torch.empty_like(zu)
+        py, pitch_y, _ = self._plane_args(y)
+        pu, pitch_uv, _ = self._plane_args(u)
+        pv, _, _ = self._plane_args(v)
+        vca_dump_coefficients(self.handle, py, pu, pv, pitch_y, pitch_uv, zy.data_ptr(), zu.data_ptr(), zv.data_ptr())
+        vca_sync(self.handle)
+        return {"Y": zy, "U": zu, "V": zv}
+
+    def sync(self):
+        vca_sync(self.handle)
+
+    def export_state(self) -> bytes:
+        return vca_export_state(self.handle)
+
+    def import_state(self, state: bytes):
+        vca_import_state(self.handle, state)
+
+    @property
+    def frames_pushed(self) -> int:
+        return vca_frames_pushed(self.handle)
+
+    @property
+    def launches(self) -> int:
+        return vca_launch_count(self.handle)
+
+    @property
+    def kernel(self) -> int:
+        return vca_kernel_in_use(self.handle)

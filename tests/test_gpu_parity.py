@@ -1,0 +1,228 @@
+"""GPU parity of the analyzer's CUDA path against the CPU oracle, through the C ABI.
+
+Coefficients are compared bit-exactly (debug dump of the same kernel), per-block H/L and
+per-frame features within the tolerances derived in vca_testutil.  Inputs are the seeded
+synthetic workloads: the tiny 640x352 sequence, ragged small frames that leave partial
+blocks on both edges, 1080p low-pass with its partial bottom block row, and sampled frames
+of 2160p in the benchmark's launch configuration.
+"""
+
+import numpy as np
+import pytest
+
+from synth import SequenceSpec, frames_list, hd_spec, tiny_spec, uhd_spec
+from vca_testutil import (assert_block_values_close, assert_features_close, frame_block_values, oracle_coefficients,
+                          oracle_config, oracle_sequence, to_device, to_host_pinned)
+
+pytestmark = pytest.mark.gpu
+
+KERNELS = {"plain": 1, "tc": 2}
+
+
+@pytest.fixture(scope="session")
+def vca():
+    import torch
+
+    from paper_2304_12384_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2304_12384_gb300 import vca as v
+    return v
+
+
+def open_analyzer(vca, kernel, **kw):
+    try:
+        return vca.Analyzer(kernel=KERNELS[kernel], **kw)
+    except vca.VcaError as e:
+        if e.status == vca.VCA_E_UNSUPPORTED and kernel == "tc":
+            pytest.skip("the tensor-core kernel does not cover this configuration")
+        raise
+
+
+def run_and_compare(vca, kernel, frames, *, width, height, bit_depth=8, block_size=32, low_pass=False, pad_mode=0,
+                    batch=None, dump_frames=(0,), block_frames=None):
+    import torch
+
+    an = open_analyzer(vca, kernel, width=width, height=height, bit_depth=bit_depth, block_size=block_size,
+                       low_pass=low_pass, pad_mode=pad_mode, max_batch=max(len(frames), 1))
+    try:
+        y, u, v = to_device(frames)
+        assert an.kernel == KERNELS[kernel]
+        an.push(y, u, v)
+        cfg = oracle_config(an)
+        per, seqf = oracle_sequence(frames, cfg)
+        for t, exp in enumerate(per):
+            assert_features_close(an.frame_features(t), exp, where=f"frame {t}")
+        assert_features_close(an.sequence_features(), seqf, where="sequence")
+        for t in (block_frames if block_frames is not None else range(len(frames))):
+            assert_block_values_close(an.block_values(t), frame_block_values(*frames[t], cfg), where=f"frame {t}")
+        for t in dump_frames:
+            z = an.dump_coefficients(y[t], u[t], v[t])
+            exp = oracle_coefficients(frames[t], cfg)
+            for p in ("Y", "U", "V"):
+                got = z[p].cpu().numpy().astype(np.int64)
+                assert got.shape == exp[p].shape
+                mism = np.argwhere(got != exp[p])
+                assert mism.size == 0, f"{p} coefficients differ at {mism[:5].tolist()} (frame {t})"
+        torch.cuda.synchronize()
+        return an
+    finally:
+        an.close()
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+def test_tiny_sequence(vca, kernel):
+    frames = frames_list(tiny_spec(1))
+    run_and_compare(vca, kernel, frames, width=640, height=352, dump_frames=(0, 8, 15))
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+@pytest.mark.parametrize("block_size", [32, 16])
+@pytest.mark.parametrize("low_pass", [False, True])
+@pytest.mark.parametrize("bit_depth", [8, 10])
+@pytest.mark.parametrize("pad_mode", [0, 1])
+def test_ragged_frames(vca, kernel, block_size, low_pass, bit_depth, pad_mode):
+    # 200 x 120 leaves partial blocks at the right and bottom edges of every plane.
+    spec = SequenceSpec(200, 120, 3, seed=11 + block_size + bit_depth, bit_depth=bit_depth, sigma=6.0,
+                        periods=(2.0, 16.0))
+    frames = frames_list(spec)
+    run_and_compare(vca, kernel, frames, width=200, height=120, bit_depth=bit_depth, block_size=block_size,
+                    low_pass=low_pass, pad_mode=pad_mode, dump_frames=(0, 2))
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+def test_hd_low_pass_around_scene_cut(vca, kernel):
+    frames = frames_list(hd_spec(2), 38, 43)  # a scene cut at frame 40
+    run_and_compare(vca, kernel, frames, width=1920, height=1080, low_pass=True, dump_frames=(0, 2),
+                    block_frames=(0, 2, 4))
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+@pytest.mark.parametrize("block_size,low_pass", [(32, True), (32, False), (16, True), (16, False)])
+def test_uhd_sampled(vca, kernel, block_size, low_pass):
+    # 2160p in the benchmark's launch configuration (one push of several frames); the oracle
+    # checks every frame's features, and block values / coefficients on sampled frames.
+    frames = frames_list(uhd_spec(3), 0, 4)
+    run_and_compare(vca, kernel, frames, width=3840, height=2160, block_size=block_size, low_pass=low_pass,
+                    dump_frames=(3,), block_frames=(0, 3))
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+@pytest.mark.parametrize("bit_depth", [8, 10])
+def test_extreme_blocks_are_exact(vca, kernel, bit_depth):
+    # All-max, all-zero, checkerboards and sign-matched stripes: the largest intermediates of
+    # both transform stages.
+    W, H = 256, 128
+    mx = (1 << bit_depth) - 1
+    dt = np.uint16 if bit_depth > 8 else np.uint8
+    yy, xx = np.indices((H, W))
+    pats = [np.full((H, W), mx), np.zeros((H, W)), ((yy + xx) % 2) * mx, (xx % 2) * mx, (yy % 2) * mx,
+            ((xx // 4) % 2) * mx, ((yy // 8) % 2) * mx, (((xx % 32) < 16) ^ ((yy % 32) < 16)) * mx]
+    frames = []
+    for i, p in enumerate(pats):
+        cy, cx = np.indices((H // 2, W // 2))
+        q = pats[(i + 3) % len(pats)]
+        frames.append((p.astype(dt), q[:H // 2, :W // 2].astype(dt), (mx - q[:H // 2, :W // 2]).astype(dt)))
+    for bs in (32, 16):
+        for lp in (False, True):
+            run_and_compare(vca, kernel, frames, width=W, height=H, bit_depth=bit_depth, block_size=bs,
+                            low_pass=lp, dump_frames=range(len(frames)))
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+def test_frame_by_frame_equals_batch_and_is_deterministic(vca, kernel):
+    import torch
+
+    frames = frames_list(tiny_spec(5))[:10]
+    y, u, v = to_device(frames)
+    a = open_analyzer(vca, kernel, width=640, height=352, max_batch=10)
+    b = open_analyzer(vca, kernel, width=640, height=352, max_batch=10)
+    c = open_analyzer(vca, kernel, width=640, height=352, max_batch=10)
+    try:
+        a.push(y, u, v)
+        for t in range(10):
+            b.push(y[t], u[t], v[t])
+        c.push(y[:3], u[:3], v[:3])
+        c.push(y[3:], u[3:], v[3:])
+        torch.cuda.synchronize()
+        for t in range(10):
+            fa, fb, fc = a.frame_features(t), b.frame_features(t), c.frame_features(t)
+            assert fa == fb == fc, t
+    finally:
+        a.close()
+        b.close()
+        c.close()
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+def test_host_frames_equal_device_frames(vca, kernel):
+    frames = frames_list(tiny_spec(6))[:6]
+    y, u, v = to_device(frames)
+    hy, hu, hv = to_host_pinned(frames)
+    a = open_analyzer(vca, kernel, width=640, height=352, max_batch=6)
+    b = open_analyzer(vca, kernel, width=640, height=352, max_batch=6)
+    try:
+        a.push(y, u, v)
+        b.push(hy, hu, hv)
+        for t in range(6):
+            assert a.frame_features(t) == b.frame_features(t)
+        # pageable (non-pinned) host memory and a single-frame push
+        b.push(hy[0].clone(), hu[0].clone(), hv[0].clone())
+        assert b.frame_features(6)["h"] > 0
+    finally:
+        a.close()
+        b.close()
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+def test_state_export_import_resumes_h(vca, kernel):
+    frames = frames_list(tiny_spec(7))[:8]
+    y, u, v = to_device(frames)
+    a = open_analyzer(vca, kernel, width=640, height=352, max_batch=8)
+    b = open_analyzer(vca, kernel, width=640, height=352, max_batch=8)
+    c = open_analyzer(vca, kernel, width=640, height=352, max_batch=8)
+    try:
+        a.push(y, u, v)
+        b.push(y[:4], u[:4], v[:4])
+        state = b.export_state()
+        c.import_state(state)
+        c.push(y[4:], u[4:], v[4:])
+        for t in range(4, 8):
+            assert c.frame_features(t) == a.frame_features(t)
+        assert c.sequence_features() == a.sequence_features()
+        with pytest.raises(vca.VcaError):
+            c.frame_features(3)
+    finally:
+        a.close()
+        b.close()
+        c.close()
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+def test_argument_errors_on_device(vca, kernel):
+    import torch
+
+    an = open_analyzer(vca, kernel, width=640, height=352, max_batch=2)
+    try:
+        frames = frames_list(tiny_spec(8))[:3]
+        y, u, v = to_device(frames)
+        with pytest.raises(vca.VcaError) as e:
+            an.push(y, u, v)  # 3 frames > max_batch
+        assert e.value.status == vca.VCA_E_ARG
+        raw = torch.zeros(640 * 352 + 64, dtype=torch.uint8, device="cuda")
+        with pytest.raises(vca.VcaError) as e:
+            vca.vca_push_frame(an.handle, raw.data_ptr() + 1, u.data_ptr(), v.data_ptr(), 640, 320, 1)
+        assert e.value.status == vca.VCA_E_ARG
+        with pytest.raises(vca.VcaError) as e:
+            vca.vca_push_frame(an.handle, raw.data_ptr(), u.data_ptr(), v.data_ptr(), 600, 320, 1)
+        assert e.value.status == vca.VCA_E_ARG
+        with pytest.raises(vca.VcaError) as e:
+            an.frame_features(0)  # nothing pushed
+        assert e.value.status == vca.VCA_E_ARG
+        an.push(y[:1], u[:1], v[:1])
+        f = vca.VcaFrameFeatures()
+        st = vca.lib().vca_read_frame_features(an.handle, 0, 0, vca.ctypes.byref(f))
+        assert st in (vca.VCA_OK, vca.VCA_E_AGAIN)
+        assert an.frame_features(0)["h"] == 0.0
+    finally:
+        an.close()

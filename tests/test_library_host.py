@@ -1,0 +1,89 @@
+"""Host-side checks of the C-ABI library that need no GPU: it builds, loads, exports every
+function include/vca.h declares, and rejects bad configurations before touching CUDA."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2304_12384_gb300 import build as vbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libvca():
+    vbuild.build()
+    from paper_2304_12384_gb300 import vca
+    return vca
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"^\s*(?:const\s+)?\w+\*?\s+\*?(vca_\w+)\s*\(", text, flags=re.M))
+    return sorted(names)
+
+
+def test_header_declares_the_api():
+    names = declared_functions()
+    for required in ("vca_open", "vca_push_frame", "vca_push_frames", "vca_read_frame_features",
+                     "vca_read_sequence_features", "vca_export_state", "vca_import_state", "vca_close",
+                     "vca_status_str"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libvca):
+    L = libvca.lib()
+    for name in declared_functions():
+        assert hasattr(L, name), name
+    assert set(declared_functions()) <= set(libvca.exported_symbols()) | {"vca_status_str", "vca_last_error"}
+
+
+def test_status_strings(libvca):
+    assert libvca.vca_status_str(0) == "ok"
+    assert libvca.vca_status_str(-1) == "invalid argument"
+
+
+@pytest.mark.parametrize("cfg,status", [
+    ((3841, 2160, 8, 32, 0, 0, 0, 64), -1),   # odd width
+    ((0, 2160, 8, 32, 0, 0, 0, 64), -1),      # empty
+    ((3840, 2160, 12, 32, 0, 0, 0, 64), -1),  # bit depth
+    ((3840, 2160, 8, 24, 0, 0, 0, 64), -1),   # block size
+    ((3840, 2160, 8, 8, 0, 0, 0, 64), -2),    # 4x4 chroma blocks unsupported
+    ((3840, 2160, 8, 32, 2, 0, 0, 64), -1),   # low_pass flag
+    ((3840, 2160, 8, 32, 0, 5, 0, 64), -1),   # pad mode
+    ((3840, 2160, 8, 32, 0, 0, 7, 64), -1),   # kernel selector
+    ((3840, 2160, 8, 32, 0, 0, 0, 99999), -1),
+    ((30, 30, 8, 32, 0, 1, 0, 64), -1),       # skip mode leaves no block
+])
+def test_config_validation(libvca, cfg, status):
+    c = libvca.VcaConfig(*cfg)
+    bx, by = ctypes.c_int64(), ctypes.c_int64()
+    assert libvca.lib().vca_block_count(ctypes.byref(c), ctypes.byref(bx), ctypes.byref(by)) == status
+    assert libvca.vca_last_error()
+    h = ctypes.c_void_p()
+    assert libvca.lib().vca_open(ctypes.byref(c), None, ctypes.byref(h)) == status
+    assert h.value is None
+
+
+@pytest.mark.parametrize("w,h,bs,mode,expect", [
+    (3840, 2160, 32, 0, (120, 68)), (3840, 2160, 16, 0, (240, 135)), (1920, 1080, 32, 0, (60, 34)),
+    (1920, 1080, 32, 1, (60, 33)), (640, 352, 32, 0, (20, 11)), (2, 2, 32, 0, (1, 1)),
+])
+def test_block_grid_matches_oracle(libvca, w, h, bs, mode, expect):
+    from oracle import Config, block_grid
+    c = libvca.VcaConfig(w, h, 8, bs, 0, mode, 0, 64)
+    assert libvca.vca_block_count(c) == expect
+    assert block_grid(Config(w, h, block_size=bs, pad_mode="skip" if mode else "replicate")) == expect
+
+
+def test_null_arguments_are_rejected(libvca):
+    L = libvca.lib()
+    assert L.vca_open(None, None, None) == -1
+    assert L.vca_push_frames(None, None, None, None, 0, 0, 0, 0, 1, 1) == -1
+    assert L.vca_read_frame_features(None, 0, 1, None) == -1
+    assert L.vca_close(None) == 0

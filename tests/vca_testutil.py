@@ -1,0 +1,105 @@
+"""Helpers shared by the GPU parity tests: device upload of synthetic frames, oracle
+evaluation of the same frames, and the feature tolerance.
+
+Tolerance (per feature, FP32 block arithmetic against the FP64 oracle):
+  E_*, L_*: |got - exp| <= 1e-6 * |exp|;
+  h:        |got - exp| <= 1e-6 * max(h, E_Y), because h is a difference of FP32 block
+            energies and cancels (|H_t - H_{t-1}| << H);
+  per-block H: relative 3e-6 -- 32 FMAs along u and a 5-level tree over v, each rounding
+            by at most 2^-24 of a sum of non-negative terms, plus the FP32 weight rounding,
+            bound the relative error by 38 * 2^-24 = 2.3e-6;
+  per-block L: relative 2^-23 (one correctly rounded FP32 square root of an exact integer);
+  coefficients: bit-exact.
+"""
+
+import numpy as np
+
+from oracle import (Config, analyze_sequence, block_grid, frame_block_values, int_dct2, plane_blocks,
+                    sequence_features)
+from synth import pack_planes
+
+FEATURES = ("E_Y", "h", "L_Y", "E_U", "E_V", "L_U", "L_V")
+FEATURE_RTOL = 1e-6
+BLOCK_H_RTOL = 3e-6
+BLOCK_L_RTOL = 2.0 ** -23
+
+
+def to_device(frames, pitch_align=64):
+    """(y, u, v) torch CUDA tensors shaped (F, rows, pitch_in_samples) from numpy planes."""
+    import torch
+
+    pk = pack_planes(frames, pitch_align)
+    out = []
+    for k in ("y", "u", "v"):
+        a = pk[k]
+        if a.dtype == np.uint16:
+            a = a.view(np.int16)
+        out.append(torch.from_numpy(np.ascontiguousarray(a)).cuda())
+    return tuple(out)
+
+
+def to_host_pinned(frames, pitch_align=64):
+    import torch
+
+    pk = pack_planes(frames, pitch_align)
+    out = []
+    for k in ("y", "u", "v"):
+        a = pk[k]
+        if a.dtype == np.uint16:
+            a = a.view(np.int16)
+        out.append(torch.from_numpy(np.ascontiguousarray(a)).pin_memory())
+    return tuple(out)
+
+
+def oracle_config(an) -> Config:
+    c = an.cfg
+    return Config(c.width, c.height, c.bit_depth, c.block_size, bool(c.low_pass),
+                  "skip" if c.pad_mode == 1 else "replicate")
+
+
+def oracle_coefficients(frame, cfg: Config):
+    nbx, nby = block_grid(cfg)
+    y, u, v = frame
+    w = cfg.block_size
+    return {
+        "Y": int_dct2(plane_blocks(y, w, nbx, nby), cfg.bit_depth, cfg.low_pass),
+        "U": int_dct2(plane_blocks(u, w // 2, nbx, nby), cfg.bit_depth, cfg.low_pass),
+        "V": int_dct2(plane_blocks(v, w // 2, nbx, nby), cfg.bit_depth, cfg.low_pass),
+    }
+
+
+def feature_errors(got: dict, exp: dict) -> dict:
+    err = {}
+    for k in FEATURES:
+        if k == "h":
+            denom = max(abs(exp["h"]), abs(exp["E_Y"]), 1e-300)
+        else:
+            denom = max(abs(exp[k]), 1e-300)
+        err[k] = abs(got[k] - exp[k]) / denom
+    return err
+
+
+def assert_features_close(got: dict, exp: dict, rtol=FEATURE_RTOL, where=""):
+    err = feature_errors(got, exp)
+    bad = {k: (got[k], exp[k], e) for k, e in err.items() if e > rtol}
+    assert not bad, f"{where}: features off (got, expected, rel err): {bad}"
+
+
+def assert_block_values_close(got: dict, exp: dict, where=""):
+    for p in ("Y", "U", "V"):
+        gH, eH = got["H_" + p].astype(np.float64), exp["H_" + p]
+        tolH = BLOCK_H_RTOL * np.abs(eH) + 1e-30
+        bad = np.nonzero(np.abs(gH - eH) > tolH)[0]
+        assert bad.size == 0, f"{where}: H_{p} off at blocks {bad[:5]}: {gH[bad[:5]]} vs {eH[bad[:5]]}"
+        gL, eL = got["L_" + p].astype(np.float64), exp["L_" + p]
+        bad = np.nonzero(np.abs(gL - eL) > BLOCK_L_RTOL * np.abs(eL) + 1e-30)[0]
+        assert bad.size == 0, f"{where}: L_{p} off at blocks {bad[:5]}: {gL[bad[:5]]} vs {eL[bad[:5]]}"
+
+
+def oracle_sequence(frames, cfg: Config, prev_HY=None):
+    per = analyze_sequence(frames, cfg, prev_HY)
+    return per, sequence_features(per)
+
+
+__all__ = ["FEATURES", "to_device", "to_host_pinned", "oracle_config", "oracle_coefficients", "feature_errors",
+           "assert_features_close", "assert_block_values_close", "oracle_sequence", "frame_block_values"]
