@@ -83,10 +83,12 @@ struct vca_analyzer {
   float* d_prevH[2] = {nullptr, nullptr};
   int cur_prev = 0;
   double* d_feats = nullptr;     // max_batch * FEAT_STRIDE
+  int* d_err = nullptr;          // kernel wait-timeout flag of the current push
   uint8_t* d_staging = nullptr;  // host frames are copied here
   size_t staging_bytes = 0;
 
   double* h_ring = nullptr;      // pinned, kRing slots of max_batch * FEAT_STRIDE
+  int* h_err = nullptr;          // pinned, one timeout flag per ring slot
   cudaEvent_t ring_ev[kRing] = {};
   cudaEvent_t t0_ev[kRing] = {};   // analysis-kernel timing, per ring slot
   cudaEvent_t t1_ev[kRing] = {};
@@ -167,6 +169,8 @@ void destroy(vca_analyzer* a) {
   cudaFree(a->d_prevH[0]);
   cudaFree(a->d_prevH[1]);
   cudaFree(a->d_feats);
+  cudaFree(a->d_err);
+  if (a->h_err) cudaFreeHost(a->h_err);
   cudaFree(a->d_staging);
   if (a->h_ring) cudaFreeHost(a->h_ring);
   for (auto& e : a->ring_ev)
@@ -194,6 +198,11 @@ vca_status harvest_front(vca_analyzer* a, bool blocking) {
     VCA_CUDA(cudaEventElapsedTime(&ms, a->t0_ev[p.slot], a->t1_ev[p.slot]), "reading kernel timing");
     a->kernel_ms += ms;
     a->timed_pushes += 1;
+  }
+  if (a->h_err[p.slot] != 0) {
+    a->pending.pop_front();
+    return fail(VCA_E_TIMEOUT, "analysis kernel gave up on a bounded wait (code %d); frames %lld..%lld are lost",
+                a->h_err[p.slot], (long long)p.first, (long long)(p.first + p.n - 1));
   }
   const double* base = a->h_ring + (size_t)p.slot * a->max_batch * vca::FEAT_STRIDE;
   for (int i = 0; i < p.n; ++i) {
@@ -272,7 +281,7 @@ vca_status stage_host_frames(vca_analyzer* a, FramePlanes* fp, int n) {
 
 cudaError_t run_analysis(vca_analyzer* a, const FramePlanes& fp, int n, float* blockvals, int16_t* const zdump[3]) {
   if (a->kernel == VCA_KERNEL_TC)
-    return vca::launch_tc(a->g, fp, n, a->tables, blockvals, zdump, a->stream, &a->launches);
+    return vca::launch_tc(a->g, fp, n, a->tables, blockvals, zdump, a->d_err, a->stream, &a->launches);
   return vca::launch_plain(a->g, fp, n, a->tables, blockvals, zdump, a->stream, &a->launches);
 }
 
@@ -350,6 +359,10 @@ vca_status vca_open(const vca_config* cfg, void* cuda_stream, vca_analyzer** out
     OPEN_CUDA(cudaMemset(a->d_prevH[i], 0, (size_t)g.C * sizeof(float)), "clearing h state");
   }
   OPEN_CUDA(cudaMalloc(&a->d_feats, (size_t)a->max_batch * vca::FEAT_STRIDE * sizeof(double)), "allocating features");
+  OPEN_CUDA(cudaMalloc(&a->d_err, sizeof(int)), "allocating the error flag");
+  OPEN_CUDA(cudaMemset(a->d_err, 0, sizeof(int)), "clearing the error flag");
+  OPEN_CUDA(cudaMallocHost(&a->h_err, kRing * sizeof(int)), "allocating pinned error flags");
+  memset(a->h_err, 0, kRing * sizeof(int));
   OPEN_CUDA(cudaMallocHost(&a->h_ring, (size_t)kRing * a->max_batch * vca::FEAT_STRIDE * sizeof(double)),
             "allocating pinned feature ring");
   for (auto& ev : a->ring_ev) OPEN_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "creating events");
@@ -371,6 +384,8 @@ vca_status vca_push_frames(vca_analyzer* a, const void* y, const void* u, const 
   if (s != VCA_OK) return s;
   if (n_frames > 1 && ((frame_stride_y & 15) || (frame_stride_uv & 15) || frame_stride_y <= 0 || frame_stride_uv <= 0))
     return fail(VCA_E_ARG, "frame strides must be positive multiples of 16 bytes");
+  if (n_frames > 1 && (frame_stride_y < pitch_y * a->g.H || frame_stride_uv < pitch_uv * a->g.ch))
+    return fail(VCA_E_ARG, "frame strides must not be smaller than one plane (frames may not overlap)");
   if (on_device != 0 && on_device != 1) return fail(VCA_E_ARG, "on_device must be 0 or 1");
 
   FramePlanes fp{static_cast<const uint8_t*>(y), static_cast<const uint8_t*>(u), static_cast<const uint8_t*>(v),
@@ -386,6 +401,7 @@ vca_status vca_push_frames(vca_analyzer* a, const void* y, const void* u, const 
   }
   const int slot = a->next_slot;
   const bool timed = a->timing;
+  VCA_CUDA(cudaMemsetAsync(a->d_err, 0, sizeof(int), a->stream), "clearing the error flag");
   if (timed) VCA_CUDA(cudaEventRecord(a->t0_ev[slot], a->stream), "recording timing event");
   cudaError_t e = run_analysis(a, fp, n_frames, a->d_blockvals, nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "launching the analysis kernel");
@@ -396,6 +412,8 @@ vca_status vca_push_frames(vca_analyzer* a, const void* y, const void* u, const 
   VCA_CUDA(cudaMemcpyAsync(a->h_ring + (size_t)slot * a->max_batch * vca::FEAT_STRIDE, a->d_feats,
                            (size_t)n_frames * vca::FEAT_STRIDE * sizeof(double), cudaMemcpyDeviceToHost, a->stream),
            "copying features to the host");
+  VCA_CUDA(cudaMemcpyAsync(a->h_err + slot, a->d_err, sizeof(int), cudaMemcpyDeviceToHost, a->stream),
+           "copying the error flag");
   VCA_CUDA(cudaEventRecord(a->ring_ev[slot], a->stream), "recording feature event");
   a->pending.push_back({a->frames_pushed, n_frames, slot, a->has_prev != 0, timed});
   a->next_slot = (slot + 1) % kRing;

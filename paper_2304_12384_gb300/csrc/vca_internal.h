@@ -57,9 +57,10 @@ cudaError_t launch_plain(const Geometry& g, const FramePlanes& fp, int nframes, 
                          float* blockvals, int16_t* const zdump[3], cudaStream_t s, int64_t* launches);
 
 // Tensor-core analysis (same outputs).  Returns cudaErrorNotSupported if the geometry is
-// outside what the tensor-core kernel handles.
+// outside what the tensor-core kernel handles.  *err (device) receives a nonzero code if a
+// bounded wait inside the kernel gave up.
 cudaError_t launch_tc(const Geometry& g, const FramePlanes& fp, int nframes, const DeviceTables& t,
-                      float* blockvals, int16_t* const zdump[3], cudaStream_t s, int64_t* launches);
+                      float* blockvals, int16_t* const zdump[3], int* err, cudaStream_t s, int64_t* launches);
 bool tc_supported(const Geometry& g);
 
 // Deterministic FP64 frame reduction: features of n frames and the h state update.
