@@ -27,12 +27,24 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
+// True once the phase with the given parity has completed (may block briefly in hardware).
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t done;
   asm volatile(
       "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
       : "=r"(done)
       : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Same, but lets the thread sleep until the phase completes or about 20 us pass.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, 0, p; }"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(20000)
       : "memory");
   return done != 0;
 }
@@ -121,6 +133,27 @@ __device__ __forceinline__ void tmem_st<32>(uint32_t t, const uint32_t (&v)[32])
       "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
       "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
       "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31]));
+}
+
+// Stores `first` into the first column and `rest` into the other N-1 columns of this warp's 32 lanes
+// (the same register is repeated in the operand list, so no copies are made).
+template <int N>
+__device__ __forceinline__ void tmem_fill(uint32_t t, uint32_t first, uint32_t rest);
+template <>
+__device__ __forceinline__ void tmem_fill<8>(uint32_t t, uint32_t a, uint32_t b) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%2,%2,%2,%2,%2,%2};" ::"r"(t), "r"(a), "r"(b));
+}
+template <>
+__device__ __forceinline__ void tmem_fill<16>(uint32_t t, uint32_t a, uint32_t b) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2};" ::"r"(t),
+               "r"(a), "r"(b));
+}
+template <>
+__device__ __forceinline__ void tmem_fill<32>(uint32_t t, uint32_t a, uint32_t b) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,"
+      "%2,%2,%2,%2,%2,%2,%2,%2};" ::"r"(t),
+      "r"(a), "r"(b));
 }
 
 // ---- UMMA descriptors and issue ---------------------------------------------

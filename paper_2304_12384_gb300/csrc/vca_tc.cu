@@ -1,11 +1,19 @@
 // Tensor-core form of the analyzer's per-block work (Section 2 of the paper: integer DCT of
 // every Y, U, V block, texture energy H and brightness L; Section 2 item (3): low-pass).
 //
-// Persistent kernel, one CTA per SM, warp-specialised:
-//   warp 0   TMA producer: one 128x128 luma + two 64x64 chroma tiles per work item into a
-//            4-stage ring (128-byte / 64-byte swizzled);
-//   warp 1   TMEM owner and MMA issuer (tcgen05.mma kind::f16, FP32 accumulate);
-//   warps 2-5 workers, one per TMEM lane quarter.
+// Persistent kernel, one CTA of 24 warps per SM, specialised by warpgroup:
+//   warpgroup 0   warp 0: TMA producer (one 128x128 luma + two 64x64 chroma tiles per work item
+//                 into a 5-stage ring, 128-byte / 64-byte swizzled); warp 1: TMEM owner and
+//                 stage-1 MMA issuer; warp 2: stage-2 MMA issuer (tcgen05.mma kind::f16, FP32
+//                 accumulate), so neither stage waits on the other's epilogue;
+//   warpgroup 1   convert: raw samples -> stage-1 A operand in TMEM;
+//   warpgroups 2, 3  epilogue 1 (luma jobs, chroma jobs): stage-1 accumulators -> stage-2 A
+//                 operand in shared memory;
+//   warpgroups 4, 5  epilogue 2 (luma jobs, chroma jobs): stage-2 accumulators -> block
+//                 energies and brightness.
+// Each warpgroup has one warp per TMEM lane quarter.  Jobs flow through 8 TMEM slots (64 columns
+// each) and 3 shared-memory operand slots; every slot has a full and a free mbarrier, so the
+// three roles run concurrently on different jobs.
 //
 // A "job" is 128 stage-2 rows: 8 (low-pass) or 4 luma 32x32 blocks, or 16 / 8 chroma 16x16
 // blocks.  Per job, through 4 TMEM slots and 2 shared-memory slots:
@@ -39,24 +47,37 @@ namespace {
 
 using namespace ptx;
 
-constexpr int kStages = 4;
+constexpr int kStages = 5;    // raw tile ring
+constexpr int kSlots = 8;     // TMEM job slots
+constexpr int kSlotCols = 64; // TMEM columns per job slot
+constexpr int kA2Slots = 4;   // shared-memory stage-2 operand slots: 0-1 luma jobs, 2-3 chroma jobs
 constexpr int kRawY = 128 * 128;
 constexpr int kRawC = 64 * 64;
 constexpr int kStageBytes = kRawY + 2 * kRawC;
 constexpr int kA2Bytes = 8192;  // one operand (hi or lo) of one job: 128 rows x 32 K x fp16
 constexpr int OFF_RAW = 0;
 constexpr int OFF_A2 = kStages * kStageBytes;
-constexpr int OFF_BL = OFF_A2 + 2 * 2 * kA2Bytes;
+constexpr int OFF_BL = OFF_A2 + kA2Slots * 2 * kA2Bytes;
 constexpr int OFF_BC = OFF_BL + 2048;
 constexpr int OFF_BAR = OFF_BC + 512;
-constexpr int OFF_MISC = OFF_BAR + 32 * 8;
+constexpr int OFF_MISC = OFF_BAR + 64 * 8;
 constexpr int kSmemBytes = OFF_MISC + 64 + 1024;  // + slack to align the base to 1024
 
 // barrier indices
-constexpr int B_RAW_FULL = 0, B_RAW_EMPTY = 4, B_A1 = 8, B_D1 = 12, B_A2 = 16, B_D2 = 18, B_DRAIN = 22;
+__host__ __device__ constexpr int b_raw_full(int s) { return s; }
+__host__ __device__ constexpr int b_raw_empty(int s) { return kStages + s; }
+__host__ __device__ constexpr int b_slot_free(int s) { return 2 * kStages + s; }
+__host__ __device__ constexpr int b_a1(int s) { return 2 * kStages + kSlots + s; }
+__host__ __device__ constexpr int b_d1(int s) { return 2 * kStages + 2 * kSlots + s; }
+__host__ __device__ constexpr int b_d2(int s) { return 2 * kStages + 3 * kSlots + s; }
+__host__ __device__ constexpr int b_a2_full(int s) { return 2 * kStages + 4 * kSlots + s; }
+__host__ __device__ constexpr int b_a2_free(int s) { return 2 * kStages + 4 * kSlots + kA2Slots + s; }
+__host__ __device__ constexpr int b_drain(int i) { return 2 * kStages + 4 * kSlots + 2 * kA2Slots + i; }
+static_assert(b_drain(1) < 64, "barrier area");
 
-constexpr int kThreads = 192;
+constexpr int kThreads = 768;
 constexpr uint32_t kTmemCols = 512;
+static_assert(kSlots * kSlotCols <= 512, "TMEM budget");
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 // FP32 magic constants (see the file comment).
@@ -113,22 +134,29 @@ struct Ctl {
 };
 
 // Bounded wait: false on timeout (flag raised) or when another role aborted.
-__device__ bool wait_bar(const Ctl& c, int idx, uint32_t parity, int code, bool ignore_abort = false) {
-  uint64_t t0 = 0;
-  for (uint32_t i = 0;; ++i) {
-    if (mbar_try_wait(&c.bars[idx], parity)) return true;
-    if ((i & 63) == 63) {
-      if (!ignore_abort && *c.abort) return false;
-      const uint64_t t = now_ns();
-      if (t0 == 0) {
-        t0 = t;
-      } else if (t - t0 > kWaitNs) {
-        *c.abort = 1;
-        atomicOr(c.err, code);
-        return false;
-      }
+__device__ __noinline__ bool wait_bar_slow(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                          int code, bool ignore_abort, bool sleep) {
+  const uint64_t t0 = now_ns();
+  for (;;) {
+#pragma unroll 1
+    for (int i = 0; i < 32; ++i)
+      if (sleep ? mbar_try_wait_sleep(bar, parity) : mbar_try_wait(bar, parity)) return true;
+    if (!ignore_abort && *abort_flag) return false;
+    if (now_ns() - t0 > kWaitNs) {
+      *abort_flag = 1;
+      atomicOr(err, code);
+      return false;
     }
   }
+}
+
+// Bounded wait on barrier idx.  Roles on the critical path spin; the producer (sleep = true) lets
+// its thread sleep in hardware between polls.
+__device__ __forceinline__ bool wait_bar(const Ctl& c, int idx, uint32_t parity, int code, bool ignore_abort = false,
+                                         bool sleep = false) {
+  uint64_t* bar = c.bars + idx;
+  if (mbar_try_wait(bar, parity)) return true;
+  return wait_bar_slow(bar, parity, c.abort, c.err, code, ignore_abort, sleep);
 }
 
 // Stage-1 operand conversion for one stage-1 group: this thread's row of 2 * A1COLS samples.
@@ -169,55 +197,66 @@ __device__ __forceinline__ void load_row_fp16(const uint8_t* raw, int y, int x, 
 
 template <int N>
 __device__ __forceinline__ void fill_cols(uint32_t taddr, float first, float rest) {
-  uint32_t v[N];
-  v[0] = __float_as_uint(first);
-#pragma unroll
-  for (int i = 1; i < N; ++i) v[i] = __float_as_uint(rest);
-  tmem_st<N>(taddr, v);
+  tmem_fill<N>(taddr, __float_as_uint(first), __float_as_uint(rest));
 }
 
-struct JobRef {
+// Job bookkeeping carried through the worker pipeline in registers.
+struct JobCtx {
   int plane;  // 0 Y, 1 U, 2 V
   int jp;     // job index within the plane's tile
-  int item;   // work item (frame, tile)
-  int slot;   // TMEM slot
+  int f;      // frame
+  int tx, ty; // tile position (units of 4 blocks)
+  int slot;   // TMEM slot within the group
+  int job;    // group-local job index
 };
 
 template <bool LP>
-__device__ __forceinline__ JobRef job_ref(int it, int cta, int grid) {
-  constexpr int JPT = Jobs<LP>::PER_TILE;
+__device__ __forceinline__ void plane_of(int j, int& plane, int& jp) {
   constexpr int JL = PC<32, LP>::JOBS;
   constexpr int JC = PC<16, LP>::JOBS;
-  JobRef r;
-  const int t = it / JPT;
-  const int j = it - t * JPT;
-  r.item = cta + t * grid;
   if (j < JL) {
-    r.plane = 0;
-    r.jp = j;
+    plane = 0;
+    jp = j;
   } else if (j < JL + JC) {
-    r.plane = 1;
-    r.jp = j - JL;
+    plane = 1;
+    jp = j - JL;
   } else {
-    r.plane = 2;
-    r.jp = j - JL - JC;
+    plane = 2;
+    jp = j - JL - JC;
   }
-  r.slot = it & 3;
-  return r;
+}
+
+// Stage-2 operand slot of job j and its use count: each plane type cycles through its own two
+// slots, so every slot's full / free barriers see one in-order stream of jobs (a barrier is never
+// waited on more than one phase ahead of its current phase).
+template <bool LP>
+__device__ __forceinline__ void a2_slot_of(int j, int& slot, int& use) {
+  constexpr int JPT = Jobs<LP>::PER_TILE;
+  constexpr int JL = PC<32, LP>::JOBS;
+  const int t = j / JPT, r = j - t * JPT;
+  if (r < JL) {
+    const int idx = t * JL + r;
+    slot = idx & 1;
+    use = idx >> 1;
+  } else {
+    const int idx = t * (JPT - JL) + (r - JL);
+    slot = 2 + (idx & 1);
+    use = idx >> 1;
+  }
 }
 
 // ---- worker phases ----------------------------------------------------------
+// TMEM slot layout (64 columns): A1 (stage-1 A operand, fp16 pairs) at [0, G*Nb/2), D1 (stage-1
+// accumulators) at [32, 32 + G*N1).  Once stage 1 has been read back, the stage-2 accumulators
+// reuse the slot: D2_hi at [0, N1), D2_lo at [N1, 2*N1).
 
 template <int Nb, bool LP>
-__device__ void convert_job(const TcParams& p, const uint8_t* raw_plane, int jp, int tile_x, int tile_y, int plane_w,
-                            int plane_h, uint32_t tslot, int q, int lane, float c0, float c, float hi0, float lo) {
+__device__ __forceinline__ void convert_job(const uint8_t* raw_plane, int jp, int h_rem, int w_rem, uint32_t taddr,
+                                            int q, int lane, const uint32_t (&d1init)[PC<Nb, LP>::N1]) {
   using P = PC<Nb, LP>;
-  const uint32_t lanebase = (uint32_t)(32 * q) << 16;
   const int l = 32 * q + lane;
   const int bg = l / Nb;
   const int r = l % Nb;
-  const int h_rem = plane_h - tile_y * 4 * Nb;
-  const int w_rem = plane_w - tile_x * 4 * Nb;
 #pragma unroll
   for (int g = 0; g < P::G; ++g) {
     const int idx = jp * P::BPG2 + g * P::BPG1 + bg;
@@ -226,85 +265,185 @@ __device__ void convert_job(const TcParams& p, const uint8_t* raw_plane, int jp,
     const int x = (idx & 3) * Nb;
     uint32_t a[Nb / 2];
     load_row_fp16<Nb>(raw_plane, y, x, w_rem, a);
-    tmem_st<Nb / 2>(tslot + lanebase + g * P::A1COLS, a);
-    fill_cols<P::N1>(tslot + lanebase + 32 + g * P::N1, c0, c);
+    tmem_st<Nb / 2>(taddr + g * P::A1COLS, a);
+    tmem_st<P::N1>(taddr + 32 + g * P::N1, d1init);
   }
-  fill_cols<P::N1>(tslot + lanebase + 64, hi0, kK1);
-  fill_cols<P::N1>(tslot + lanebase + 96, lo, lo);
 }
 
 template <int Nb, bool LP>
-__device__ void epilogue1(uint32_t tslot, uint32_t a2hi, uint32_t a2lo, int q, int lane, float s1inv) {
+__device__ __forceinline__ void epilogue1(uint32_t taddr, uint32_t a2hi, uint32_t a2lo, int q, int lane, float s1inv,
+                                          float hi0, float lo) {
   using P = PC<Nb, LP>;
   constexpr int NK = P::NK;
-  const uint32_t lanebase = (uint32_t)(32 * q) << 16;
   const int l = 32 * q + lane;
   const int bg = l / Nb;
   const int r = l % Nb;
+  uint32_t acc[P::G][NK];
+#pragma unroll
+  for (int g = 0; g < P::G; ++g) tmem_ld<NK>(taddr + 32 + g * P::N1, acc[g]);
+  tmem_wait_ld();
+  // The slot now belongs to stage 2: pre-set its accumulators (see the file comment).
+  fill_cols<P::N1>(taddr, hi0, kK1);
+  fill_cols<P::N1>(taddr + P::N1, lo, lo);
+  const uint32_t rowoff = (uint32_t)((r >> 3) * 2048 + (r & 7) * 128);
 #pragma unroll
   for (int g = 0; g < P::G; ++g) {
-    uint32_t acc[NK];
-    tmem_ld<NK>(tslot + lanebase + 32 + g * P::N1, acc);
-    tmem_wait_ld();
-    uint32_t hi[NK / 2], lo[NK / 2];
+    uint32_t hi[NK / 2], lw[NK / 2];
 #pragma unroll
     for (int k = 0; k < NK; k += 2) {
-      const uint32_t za = __float_as_uint(__fmaf_rd(__uint_as_float(acc[k]), s1inv, kT1));
-      const uint32_t zb = __float_as_uint(__fmaf_rd(__uint_as_float(acc[k + 1]), s1inv, kT1));
-      lo[k / 2] = prmt(za, zb, 0x6420);
+      const uint32_t za = __float_as_uint(__fmaf_rd(__uint_as_float(acc[g][k]), s1inv, kT1));
+      const uint32_t zb = __float_as_uint(__fmaf_rd(__uint_as_float(acc[g][k + 1]), s1inv, kT1));
+      lw[k / 2] = prmt(za, zb, 0x6420);
       hi[k / 2] = prmt(za, zb, 0x6521);
     }
     const int m0 = (g * P::BPG1 + bg) * NK;
-    const uint32_t rowoff = (uint32_t)((r >> 3) * 2048 + (r & 7) * 128);
 #pragma unroll
     for (int c = 0; c < NK / 8; ++c) {
       const int m = m0 + 8 * c;
       const uint32_t off = rowoff + (uint32_t)((m >> 6) * 1024) + (uint32_t)(((((m & 63) >> 3) ^ (r & 7))) << 4);
       sts128(a2hi + off, hi[4 * c], hi[4 * c + 1], hi[4 * c + 2], hi[4 * c + 3]);
-      sts128(a2lo + off, lo[4 * c], lo[4 * c + 1], lo[4 * c + 2], lo[4 * c + 3]);
+      sts128(a2lo + off, lw[4 * c], lw[4 * c + 1], lw[4 * c + 2], lw[4 * c + 3]);
     }
   }
 }
 
 template <int Nb, bool LP, bool DUMP>
-__device__ void epilogue2(const TcParams& p, uint32_t tslot, int plane, int jp, int f, int tile_x, int tile_y, int q,
-                          int lane, const float (&wts)[PC<Nb, LP>::NK], float einv, float c2) {
+__device__ __forceinline__ void epilogue2(const TcParams& p, uint32_t taddr, const JobCtx& jc, int q, int lane,
+                                          const float (&wts)[PC<Nb, LP>::NK], float einv, float c2,
+                                          uint64_t* slot_free) {
   using P = PC<Nb, LP>;
   constexpr int NK = P::NK;
-  const uint32_t lanebase = (uint32_t)(32 * q) << 16;
-  uint32_t hi[NK], lo[NK];
-  tmem_ld<NK>(tslot + lanebase + 64, hi);
-  tmem_ld<NK>(tslot + lanebase + 96, lo);
-  tmem_wait_ld();
+  constexpr int HALF = NK > 16 ? 16 : NK;  // columns loaded at a time (bounds register use)
   const int m = 32 * q + lane;
   const int b2 = m / NK;
   const int v = m % NK;
-  const int idx = jp * P::BPG2 + b2;
-  const int bx = tile_x * 4 + (idx & 3);
-  const int by = tile_y * 4 + (idx >> 2);
+  const int idx = jc.jp * P::BPG2 + b2;
+  const int bx = jc.tx * 4 + (idx & 3);
+  const int by = jc.ty * 4 + (idx >> 2);
   const bool valid = bx < p.nbx && by < p.nby;
   const int64_t k = (int64_t)by * p.nbx + bx;
   int16_t* zd = nullptr;
-  if (DUMP) zd = (valid && f == 0) ? p.zdump[plane] + k * NK * NK : nullptr;
+  if (DUMP) zd = (valid && jc.f == 0) ? p.zdump[jc.plane] + k * NK * NK : nullptr;
   float H = 0.0f, z00 = 0.0f;
 #pragma unroll
-  for (int u = 0; u < NK; ++u) {
-    const float w = __fmaf_rd(__uint_as_float(lo[u]), 0.00390625f, __uint_as_float(hi[u]));
-    const float z = __fmaf_rd(w, einv, c2) - kK1;
-    if (u == 0) z00 = z;
-    if (DUMP && zd) zd[u * NK + v] = (int16_t)z;
-    H = fmaf(fabsf(z), wts[u], H);
+  for (int h0 = 0; h0 < NK; h0 += HALF) {
+    uint32_t hi[HALF], lo[HALF];
+    tmem_ld<HALF>(taddr + h0, hi);
+    tmem_ld<HALF>(taddr + P::N1 + h0, lo);
+    tmem_wait_ld();
+    if (h0 + HALF == NK) {  // every accumulator of the slot is in registers: hand the slot back
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(slot_free);
+    }
+#pragma unroll
+    for (int uu = 0; uu < HALF; ++uu) {
+      const int u = h0 + uu;
+      const float w = __fmaf_rd(__uint_as_float(lo[uu]), 0.00390625f, __uint_as_float(hi[uu]));
+      const float z = __fmaf_rd(w, einv, c2) - kK1;
+      if (u == 0) z00 = z;
+      if (DUMP && zd) zd[u * NK + v] = (int16_t)z;
+      H = fmaf(fabsf(z), wts[u], H);
+    }
   }
 #pragma unroll
   for (int o = NK / 2; o > 0; o >>= 1) H += __shfl_xor_sync(0xffffffffu, H, o);
   if (valid && v == 0) {
-    float* out = p.blockvals + (int64_t)f * p.out_fstride;
-    out[(2 * plane) * p.C + k] = H;
-    out[(2 * plane + 1) * p.C + k] = __fsqrt_rn(z00);
+    float* out = p.blockvals + (int64_t)jc.f * p.out_fstride + (2 * jc.plane) * p.C + k;
+    out[0] = H;
+    out[p.C] = __fsqrt_rn(z00);
   }
 }
 
 // ---- the kernel --------------------------------------------------------------
+
+// Tile bookkeeping of a role's current tile (recomputed at the first job of each tile).
+struct TileInfo {
+  int f, tx, ty, stage, t;
+};
+
+__device__ __forceinline__ TileInfo tile_info(const TcParams& p, int t, int cta, int grid, int tiles_per_frame) {
+  TileInfo ti;
+  const int item = cta + t * grid;
+  ti.t = t;
+  ti.f = item / tiles_per_frame;
+  const int r = item - ti.f * tiles_per_frame;
+  ti.tx = r % p.tiles_x;
+  ti.ty = r / p.tiles_x;
+  ti.stage = t % kStages;
+  return ti;
+}
+
+// ---- role loops of the two epilogues (one instantiation per plane type) ------------------
+
+template <bool LP>
+__device__ __forceinline__ bool is_plane_job(int j, bool luma) {
+  int plane, jp;
+  plane_of<LP>(j, plane, jp);
+  return (plane == 0) == luma;
+}
+
+// Epilogue 1 of every job of one plane type: T = floor(T'/2^s1) into the stage-2 operand (hi and
+// lo bytes as fp16, MN-major), and the stage-2 accumulators pre-set: hi starts at
+// K1 - 1156 * 64 * N for u = 0 (the 1024 + byte encoding of both halves) and K1 otherwise, lo at
+// 2^(s2-1) (luma N = 32: s1 = 4, s2 = 11; chroma N = 16: s1 = 3, s2 = 10).
+template <int Nb, bool LP>
+__device__ void epi1_loop(const Ctl& ctl, uint32_t sbase, uint32_t tq, int n_jobs, int q, int lane) {
+  constexpr int JPT = Jobs<LP>::PER_TILE;
+  const float s1inv = Nb == 32 ? 0.0625f : 0.125f;
+  const float hi0 = Nb == 32 ? kK1 - 2367488.0f : kK1 - 1183744.0f;
+  const float lo = Nb == 32 ? 1024.0f : 512.0f;
+  for (int jj = 0; jj < n_jobs; ++jj) {
+    if (!is_plane_job<LP>(jj % JPT, Nb == 32)) continue;
+    const int slot = jj % kSlots;
+    int a2, use;
+    a2_slot_of<LP>(jj, a2, use);
+    if (!wait_bar(ctl, b_d1(slot), (jj / kSlots) & 1, 4)) break;
+    if (use >= 1 && !wait_bar(ctl, b_a2_free(a2), (use - 1) & 1, 4)) break;
+    tc_fence_after();
+    const uint32_t ahi = sbase + OFF_A2 + a2 * 2 * kA2Bytes, alo = ahi + kA2Bytes;
+    epilogue1<Nb, LP>(tq + slot * kSlotCols, ahi, alo, q, lane, s1inv, hi0, lo);
+    tmem_wait_st();
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&ctl.bars[b_a2_full(a2)]);
+  }
+}
+
+// Epilogue 2 of every job of one plane type: Z, the block energy H and brightness L.
+template <int Nb, bool LP, bool DUMP>
+__device__ void epi2_loop(const TcParams& p, const Ctl& ctl, uint32_t tq, int n_jobs, int cta, int grid,
+                          int tiles_per_frame, int q, int lane) {
+  using P = PC<Nb, LP>;
+  constexpr int JPT = Jobs<LP>::PER_TILE;
+  const float* Wt = Nb == 32 ? p.W_y : p.W_c;
+  float w[P::NK];
+#pragma unroll
+  for (int u = 0; u < P::NK; ++u) w[u] = Wt[u * Nb + (lane % P::NK)];
+  const float einv = Nb == 32 ? 0.125f : 0.25f;
+  const float c2 = Nb == 32 ? kK1 - kK1 / 8.0f : kK1 - kK1 / 4.0f;
+  TileInfo ti{};
+  int last_tile = -1;
+  for (int jj = 0; jj < n_jobs; ++jj) {
+    const int j = jj % JPT;
+    if (!is_plane_job<LP>(j, Nb == 32)) continue;
+    const int t = jj / JPT;
+    if (t != last_tile) {
+      ti = tile_info(p, t, cta, grid, tiles_per_frame);
+      last_tile = t;
+    }
+    const int slot = jj % kSlots;
+    if (!wait_bar(ctl, b_d2(slot), (jj / kSlots) & 1, 4)) break;
+    tc_fence_after();
+    JobCtx jc;
+    plane_of<LP>(j, jc.plane, jc.jp);
+    jc.f = ti.f;
+    jc.tx = ti.tx;
+    jc.ty = ti.ty;
+    epilogue2<Nb, LP, DUMP>(p, tq + slot * kSlotCols, jc, q, lane, w, einv, c2, &ctl.bars[b_slot_free(slot)]);
+  }
+}
 
 template <bool LP, bool DUMP>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -321,6 +460,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const int lane = tid & 31;
+  const int role = warp >> 2;  // warpgroup
+  const int q = warp & 3;      // TMEM lane quarter of this warp
   const int cta = blockIdx.x;
   const int grid = gridDim.x;
   const int n_items = cta < p.total_items ? (p.total_items - cta + grid - 1) / grid : 0;
@@ -342,16 +483,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   if (tid == 0) {
     for (int i = 0; i < kStages; ++i) {
-      mbar_init(&bars[B_RAW_FULL + i], 1);
-      mbar_init(&bars[B_RAW_EMPTY + i], 4);
+      mbar_init(&bars[b_raw_full(i)], 1);
+      mbar_init(&bars[b_raw_empty(i)], 4);
     }
-    for (int i = 0; i < 4; ++i) {
-      mbar_init(&bars[B_A1 + i], 4);
-      mbar_init(&bars[B_D1 + i], 1);
-      mbar_init(&bars[B_D2 + i], 1);
+    for (int i = 0; i < kSlots; ++i) {
+      mbar_init(&bars[b_slot_free(i)], 4);
+      mbar_init(&bars[b_a1(i)], 4);
+      mbar_init(&bars[b_d1(i)], 1);
+      mbar_init(&bars[b_d2(i)], 1);
     }
-    for (int i = 0; i < 2; ++i) mbar_init(&bars[B_A2 + i], 4);
-    mbar_init(&bars[B_DRAIN], 1);
+    for (int i = 0; i < kA2Slots; ++i) {
+      mbar_init(&bars[b_a2_full(i)], 4);
+      mbar_init(&bars[b_a2_free(i)], 1);
+    }
+    mbar_init(&bars[b_drain(0)], 1);
+    mbar_init(&bars[b_drain(1)], 1);
     *abort_flag = 0;
     fence_mbar_init();
   }
@@ -370,168 +516,146 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const uint32_t sbase = smem_u32(sm);
+  const uint32_t lanebase = (uint32_t)(32 * q) << 16;
 
-  if (warp == 0) {
-    // ---------------- TMA producer ----------------
-    if (lane == 0) {
+  if (role == 0) {
+    if (warp == 0 && lane == 0) {
+      // ---------------- TMA producer: tiles in order into the ring ----------------
       int issued = 0;
       for (int t = 0; t < n_items; ++t) {
         const int stage = t % kStages;
-        if (t >= kStages && !wait_bar(ctl, B_RAW_EMPTY + stage, ((t / kStages) - 1) & 1, 1)) break;
-        const int item = cta + t * grid;
-        const int f = item / tiles_per_frame;
-        const int ti = item - f * tiles_per_frame;
-        const int tx = ti % p.tiles_x, ty = ti / p.tiles_x;
+        if (t >= kStages && !wait_bar(ctl, b_raw_empty(stage), ((t / kStages) - 1) & 1, 1, false, true)) break;
+        const TileInfo ti = tile_info(p, t, cta, grid, tiles_per_frame);
         uint8_t* dst = sm + OFF_RAW + stage * kStageBytes;
-        mbar_arrive_expect_tx(&bars[B_RAW_FULL + stage], kStageBytes);
-        tma_load_3d(dst, &mapY, tx * 128, ty * 128, f, &bars[B_RAW_FULL + stage]);
-        tma_load_3d(dst + kRawY, &mapU, tx * 64, ty * 64, f, &bars[B_RAW_FULL + stage]);
-        tma_load_3d(dst + kRawY + kRawC, &mapV, tx * 64, ty * 64, f, &bars[B_RAW_FULL + stage]);
+        mbar_arrive_expect_tx(&bars[b_raw_full(stage)], kStageBytes);
+        tma_load_3d(dst, &mapY, ti.tx * 128, ti.ty * 128, ti.f, &bars[b_raw_full(stage)]);
+        tma_load_3d(dst + kRawY, &mapU, ti.tx * 64, ti.ty * 64, ti.f, &bars[b_raw_full(stage)]);
+        tma_load_3d(dst + kRawY + kRawC, &mapV, ti.tx * 64, ti.ty * 64, ti.f, &bars[b_raw_full(stage)]);
         ++issued;
       }
       if (*abort_flag) {
         // Let every copy this CTA issued land before the CTA's shared memory goes away.
         for (int t = (issued > kStages ? issued - kStages : 0); t < issued; ++t)
-          wait_bar(ctl, B_RAW_FULL + (t % kStages), (t / kStages) & 1, 1, true);
+          wait_bar(ctl, b_raw_full(t % kStages), (t / kStages) & 1, 1, true);
       }
-    }
-  } else if (warp == 1) {
-    // ---------------- MMA issuer ----------------
-    if (lane == 0) {
+    } else if (warp == 1 && lane == 0) {
+      // ---------------- stage-1 MMA issuer: D1 = A1 (TMEM) x M^T ----------------
       const uint32_t bl = sbase + OFF_BL, bc = sbase + OFF_BC;
       constexpr uint32_t idL = idesc_f16(128, L::N1, 0, 0), idC = idesc_f16(128, Cc::N1, 0, 0);
-      constexpr uint32_t id2L = idesc_f16(128, L::N1, 1, 0), id2C = idesc_f16(128, Cc::N1, 1, 0);
-      auto stage2 = [&](int pj) -> bool {
-        const JobRef jr = job_ref<LP>(pj, cta, grid);
-        const int a2 = pj & 1;
-        if (!wait_bar(ctl, B_A2 + a2, (pj >> 1) & 1, 2)) return false;
+      bool ok = true;
+      for (int j = 0; j < n_jobs; ++j) {
+        int plane, jp;
+        plane_of<LP>(j % JPT, plane, jp);
+        const int slot = j % kSlots;
+        if (!wait_bar(ctl, b_a1(slot), (j / kSlots) & 1, 2)) {
+          ok = false;
+          break;
+        }
         tc_fence_after();
-        const uint32_t d = tmem + jr.slot * 128;
+        const uint32_t d = tmem + slot * kSlotCols;
+        if (plane == 0) {
+          // K-step outer: consecutive MMAs write different accumulators, so none waits on the last.
+#pragma unroll
+          for (int ks = 0; ks < L::KS; ++ks)
+#pragma unroll
+            for (int gg = 0; gg < L::G; ++gg)
+              mma_ts(d + 32 + gg * L::N1, d + gg * L::A1COLS + ks * 8, smem_desc(bl + ks * 256, 128, 512, 0), idL, 1);
+        } else {
+#pragma unroll
+          for (int gg = 0; gg < Cc::G; ++gg)
+            mma_ts(d + 32 + gg * Cc::N1, d + gg * Cc::A1COLS, smem_desc(bc, 128, 256, 0), idC, 1);
+        }
+        mma_commit(&bars[b_d1(slot)]);
+      }
+      if (!ok) {
+        mma_commit(&bars[b_drain(0)]);
+        wait_bar(ctl, b_drain(0), 0, 2, true);
+      }
+    } else if (warp == 2 && lane == 0) {
+      // ---------------- stage-2 MMA issuer: D2 = A2 (smem, MN-major) x M^T, hi and lo ----------------
+      const uint32_t bl = sbase + OFF_BL, bc = sbase + OFF_BC;
+      constexpr uint32_t id2L = idesc_f16(128, L::N1, 1, 0), id2C = idesc_f16(128, Cc::N1, 1, 0);
+      bool ok = true;
+      for (int j = 0; j < n_jobs; ++j) {
+        int plane, jp;
+        plane_of<LP>(j % JPT, plane, jp);
+        int a2, use;
+        a2_slot_of<LP>(j, a2, use);
+        if (!wait_bar(ctl, b_a2_full(a2), use & 1, 2)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (j % kSlots) * kSlotCols;
         const uint32_t ahi = sbase + OFF_A2 + a2 * 2 * kA2Bytes, alo = ahi + kA2Bytes;
-        if (jr.plane == 0) {
+        if (plane == 0) {
 #pragma unroll
           for (int ks = 0; ks < L::KS; ++ks) {
             const uint64_t b = smem_desc(bl + ks * 256, 128, 512, 0);
-            mma_ss(d + 64, smem_desc(ahi + ks * 4096, 1024, 2048, 2), b, id2L, 1);
-            mma_ss(d + 96, smem_desc(alo + ks * 4096, 1024, 2048, 2), b, id2L, 1);
+            mma_ss(d, smem_desc(ahi + ks * 4096, 1024, 2048, 2), b, id2L, 1);
+            mma_ss(d + L::N1, smem_desc(alo + ks * 4096, 1024, 2048, 2), b, id2L, 1);
           }
         } else {
           const uint64_t b = smem_desc(bc, 128, 256, 0);
-          mma_ss(d + 64, smem_desc(ahi, 1024, 2048, 2), b, id2C, 1);
-          mma_ss(d + 96, smem_desc(alo, 1024, 2048, 2), b, id2C, 1);
+          mma_ss(d, smem_desc(ahi, 1024, 2048, 2), b, id2C, 1);
+          mma_ss(d + Cc::N1, smem_desc(alo, 1024, 2048, 2), b, id2C, 1);
         }
-        mma_commit(&bars[B_D2 + jr.slot]);
-        return true;
-      };
-      bool ok = true;
-      for (int it = 0; it < n_jobs && ok; ++it) {
-        const JobRef jr = job_ref<LP>(it, cta, grid);
-        if (!wait_bar(ctl, B_A1 + jr.slot, (it >> 2) & 1, 2)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t d = tmem + jr.slot * 128;
-        if (jr.plane == 0) {
-#pragma unroll
-          for (int g = 0; g < L::G; ++g)
-#pragma unroll
-            for (int ks = 0; ks < L::KS; ++ks)
-              mma_ts(d + 32 + g * L::N1, d + g * L::A1COLS + ks * 8, smem_desc(bl + ks * 256, 128, 512, 0), idL, 1);
-        } else {
-#pragma unroll
-          for (int g = 0; g < Cc::G; ++g)
-            mma_ts(d + 32 + g * Cc::N1, d + g * Cc::A1COLS, smem_desc(bc, 128, 256, 0), idC, 1);
-        }
-        mma_commit(&bars[B_D1 + jr.slot]);
-        if (it >= 1) ok = stage2(it - 1);
+        mma_commit(&bars[b_d2(j % kSlots)]);
+        mma_commit(&bars[b_a2_free(a2)]);
       }
-      if (ok && n_jobs > 0) ok = stage2(n_jobs - 1);
       if (!ok) {
-        mma_commit(&bars[B_DRAIN]);
-        wait_bar(ctl, B_DRAIN, 0, 2, true);
+        mma_commit(&bars[b_drain(1)]);
+        wait_bar(ctl, b_drain(1), 0, 2, true);
       }
     }
+  } else if (role == 1) {
+    // ---------------- convert: raw samples -> TMEM A operand, accumulator offsets ----------------
+    // Luma (N = 32, 8-bit): s1 = 4; chroma (N = 16): s1 = 3.  D1 starts at 2^(s1-1), minus the
+    // 1024 * 64 * N bias that the 1024 + x sample encoding adds to the DC row.
+    uint32_t initL[L::N1], initC[Cc::N1];
+#pragma unroll
+    for (int i = 0; i < L::N1; ++i) initL[i] = __float_as_uint(i == 0 ? 8.0f - 2097152.0f : 8.0f);
+#pragma unroll
+    for (int i = 0; i < Cc::N1; ++i) initC[i] = __float_as_uint(i == 0 ? 4.0f - 1048576.0f : 4.0f);
+    TileInfo ti{};
+    int h_remL = 0, w_remL = 0, h_remC = 0, w_remC = 0;
+    for (int jj = 0; jj < n_jobs; ++jj) {
+      const int j = jj % JPT;
+      if (j == 0) {
+        ti = tile_info(p, jj / JPT, cta, grid, tiles_per_frame);
+        h_remL = p.H - ti.ty * 128;
+        w_remL = p.W - ti.tx * 128;
+        h_remC = p.ch - ti.ty * 64;
+        w_remC = p.cw - ti.tx * 64;
+        if (!wait_bar(ctl, b_raw_full(ti.stage), (ti.t / kStages) & 1, 4)) break;
+      }
+      const int slot = jj % kSlots;
+      if (jj >= kSlots && !wait_bar(ctl, b_slot_free(slot), ((jj / kSlots) - 1) & 1, 4)) break;
+      tc_fence_after();
+      int plane, jp;
+      plane_of<LP>(j, plane, jp);
+      const uint8_t* raw = sm + OFF_RAW + ti.stage * kStageBytes;
+      const uint32_t ta = tmem + lanebase + slot * kSlotCols;
+      if (plane == 0)
+        convert_job<32, LP>(raw, jp, h_remL, w_remL, ta, q, lane, initL);
+      else
+        convert_job<16, LP>(raw + kRawY + (plane - 1) * kRawC, jp, h_remC, w_remC, ta, q, lane, initC);
+      tmem_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&bars[b_a1(slot)]);
+        if (j == JPT - 1) mbar_arrive(&bars[b_raw_empty(ti.stage)]);
+      }
+    }
+  } else if (role == 2) {
+    epi1_loop<32, LP>(ctl, sbase, tmem + lanebase, n_jobs, q, lane);
+  } else if (role == 3) {
+    epi1_loop<16, LP>(ctl, sbase, tmem + lanebase, n_jobs, q, lane);
+  } else if (role == 4) {
+    epi2_loop<32, LP, DUMP>(p, ctl, tmem + lanebase, n_jobs, cta, grid, tiles_per_frame, q, lane);
   } else {
-    // ---------------- workers ----------------
-    const int q = warp & 3;  // TMEM lane quarter this warp may access
-    float wL[L::NK], wC[Cc::NK];
-#pragma unroll
-    for (int u = 0; u < L::NK; ++u) wL[u] = p.W_y[u * 32 + (lane % L::NK)];
-#pragma unroll
-    for (int u = 0; u < Cc::NK; ++u) wC[u] = p.W_c[u * 16 + (lane % Cc::NK)];
-    // Luma (N = 32, 8-bit): s1 = 4, s2 = 11; chroma (N = 16): s1 = 3, s2 = 10.
-    const float c0L = 8.0f - 2097152.0f, cL = 8.0f, c0C = 4.0f - 1048576.0f, cC = 4.0f;
-    const float hi0L = kK1 - 2367488.0f, hi0C = kK1 - 1183744.0f;
-    const float loL = 1024.0f, loC = 512.0f;
-    const float c2L = kK1 - kK1 / 8.0f, c2C = kK1 - kK1 / 4.0f;
-    bool ok = true;
-    for (int it = 0; it < n_jobs + 2 && ok; ++it) {
-      if (it < n_jobs) {
-        const JobRef jr = job_ref<LP>(it, cta, grid);
-        const int t = it / JPT;
-        const int j = it - t * JPT;
-        const int stage = t % kStages;
-        if (j == 0 && !wait_bar(ctl, B_RAW_FULL + stage, (t / kStages) & 1, 4)) {
-          ok = false;
-          break;
-        }
-        const int f = jr.item / tiles_per_frame;
-        const int ti = jr.item - f * tiles_per_frame;
-        const int tx = ti % p.tiles_x, ty = ti / p.tiles_x;
-        const uint8_t* raw = sm + OFF_RAW + stage * kStageBytes;
-        const uint32_t ts = tmem + jr.slot * 128;
-        if (jr.plane == 0)
-          convert_job<32, LP>(p, raw, jr.jp, tx, ty, p.W, p.H, ts, q, lane, c0L, cL, hi0L, loL);
-        else
-          convert_job<16, LP>(p, raw + kRawY + (jr.plane - 1) * kRawC, jr.jp, tx, ty, p.cw, p.ch, ts, q, lane, c0C,
-                              cC, hi0C, loC);
-        tmem_wait_st();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(&bars[B_A1 + jr.slot]);
-          if (j == JPT - 1) mbar_arrive(&bars[B_RAW_EMPTY + stage]);
-        }
-      }
-      if (it >= 1 && it - 1 < n_jobs) {
-        const int pj = it - 1;
-        const JobRef jr = job_ref<LP>(pj, cta, grid);
-        if (!wait_bar(ctl, B_D1 + jr.slot, (pj >> 2) & 1, 4)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t ahi = sbase + OFF_A2 + (pj & 1) * 2 * kA2Bytes, alo = ahi + kA2Bytes;
-        const uint32_t ts = tmem + jr.slot * 128;
-        if (jr.plane == 0)
-          epilogue1<32, LP>(ts, ahi, alo, q, lane, 0.0625f);
-        else
-          epilogue1<16, LP>(ts, ahi, alo, q, lane, 0.125f);
-        fence_proxy_async_smem();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&bars[B_A2 + (pj & 1)]);
-      }
-      if (it >= 2) {
-        const int pj = it - 2;
-        const JobRef jr = job_ref<LP>(pj, cta, grid);
-        if (!wait_bar(ctl, B_D2 + jr.slot, (pj >> 2) & 1, 4)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const int f = jr.item / tiles_per_frame;
-        const int ti = jr.item - f * tiles_per_frame;
-        const int tx = ti % p.tiles_x, ty = ti / p.tiles_x;
-        const uint32_t ts = tmem + jr.slot * 128;
-        if (jr.plane == 0)
-          epilogue2<32, LP, DUMP>(p, ts, 0, jr.jp, f, tx, ty, q, lane, wL, 0.125f, c2L);
-        else
-          epilogue2<16, LP, DUMP>(p, ts, jr.plane, jr.jp, f, tx, ty, q, lane, wC, 0.25f, c2C);
-        tc_fence_before();
-      }
-    }
+    epi2_loop<16, LP, DUMP>(p, ctl, tmem + lanebase, n_jobs, cta, grid, tiles_per_frame, q, lane);
   }
 
   tc_fence_before();
