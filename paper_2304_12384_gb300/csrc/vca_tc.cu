@@ -1,12 +1,12 @@
 // Tensor-core form of the analyzer's per-block work (Section 2 of the paper: integer DCT of
 // every Y, U, V block, texture energy H and brightness L; Section 2 item (3): low-pass).
 //
-// Persistent kernel, one CTA of 24 warps per SM, specialised by warpgroup:
+// Persistent kernel, one CTA of 28 warps per SM, specialised by warpgroup:
 //   warpgroup 0   warp 0: TMA producer (one 128x128 luma + two 64x64 chroma tiles per work item
 //                 into a 5-stage ring, 128-byte / 64-byte swizzled); warp 1: TMEM owner and
 //                 stage-1 MMA issuer; warp 2: stage-2 MMA issuer (tcgen05.mma kind::f16, FP32
 //                 accumulate), so neither stage waits on the other's epilogue;
-//   warpgroup 1   convert: raw samples -> stage-1 A operand in TMEM;
+//   warpgroups 1, 6  convert (luma jobs, chroma jobs): raw samples -> stage-1 A operand in TMEM;
 //   warpgroups 2, 3  epilogue 1 (luma jobs, chroma jobs): stage-1 accumulators -> stage-2 A
 //                 operand in shared memory;
 //   warpgroups 4, 5  epilogue 2 (luma jobs, chroma jobs): stage-2 accumulators -> block
@@ -18,12 +18,14 @@
 // A "job" is 128 stage-2 rows: 8 (low-pass) or 4 luma 32x32 blocks, or 16 / 8 chroma 16x16
 // blocks.  Per job, through 4 TMEM slots and 2 shared-memory slots:
 //   convert   raw u8 row -> fp16 (1024 + x, one PRMT per two samples) written to TMEM as the
-//             A operand; accumulators pre-set with the rounding offsets and magic constants;
-//   stage 1   T' = X M^T + c  (A from TMEM, M from shared memory), exact integers in FP32;
-//   epilogue1 T = floor(T'/2^s1) by one round-down FMA whose magic constant leaves
+//             A operand;
+//   stage 1   D1 = X M^T (A from TMEM, M from shared memory), exact integers in FP32;
+//   epilogue1 T' = D1 + c (rounding offset, minus the encoding bias on the DC row), then
+//             T = floor(T'/2^s1) by one round-down FMA whose magic constant leaves
 //             U = T + 32768 in the low 16 bits and 0x64 in byte 2, so two PRMTs give the
 //             fp16 pairs (1024 + U_lo8, 1024 + U_hi8); stored MN-major (128-byte swizzle)
-//             as the stage-2 A operand -- the row/column transpose is the layout;
+//             as the stage-2 A operand -- the row/column transpose is the layout -- and the
+//             stage-2 accumulators pre-set to the magic constants of epilogue 2;
 //   stage 2   S_hi, S_lo = M T_hi, M T_lo (A MN-major from shared memory);
 //   epilogue2 Z = floor((256 S_hi + S_lo + 2^(s2-1)) / 2^s2) by two round-down FMAs, then
 //             H_v = sum_u w(u,v) |Z| in increasing u and an xor tree over v.
@@ -48,36 +50,56 @@ namespace {
 using namespace ptx;
 
 constexpr int kStages = 5;    // raw tile ring
-constexpr int kSlots = 8;     // TMEM job slots
-constexpr int kSlotCols = 64; // TMEM columns per job slot
-constexpr int kA2Slots = 4;   // shared-memory stage-2 operand slots: 0-1 luma jobs, 2-3 chroma jobs
 constexpr int kRawY = 128 * 128;
 constexpr int kRawC = 64 * 64;
 constexpr int kStageBytes = kRawY + 2 * kRawC;
-constexpr int kA2Bytes = 8192;  // one operand (hi or lo) of one job: 128 rows x 32 K x fp16
+constexpr int kA2L = 8192;  // one stage-2 operand (hi or lo) of one luma job: 128 rows x 32 K x fp16
+constexpr int kA2C = 4096;  // of one chroma job: 128 rows x 16 K x fp16
 constexpr int OFF_RAW = 0;
-constexpr int OFF_A2 = kStages * kStageBytes;
-constexpr int OFF_BL = OFF_A2 + kA2Slots * 2 * kA2Bytes;
+constexpr int OFF_A2 = kStages * kStageBytes;   // luma: 2 slots x (hi, lo)
+constexpr int OFF_A2C = OFF_A2 + 2 * 2 * kA2L;  // chroma: 2 slots x (hi, lo)
+constexpr int OFF_BL = OFF_A2C + 2 * 2 * kA2C;
 constexpr int OFF_BC = OFF_BL + 2048;
 constexpr int OFF_BAR = OFF_BC + 512;
-constexpr int OFF_MISC = OFF_BAR + 64 * 8;
+constexpr int kBars = 80;
+constexpr int OFF_MISC = OFF_BAR + kBars * 8;
 constexpr int kSmemBytes = OFF_MISC + 64 + 1024;  // + slack to align the base to 1024
+constexpr int kA2Slots = 4;                       // 0-1 luma jobs, 2-3 chroma jobs
+
+// TMEM layout.  Low-pass: 12 accumulator slots of 32 columns (D1, then D2 in the same columns) and
+// a separate ring of 4 stage-1 operand buffers of 32 columns, freed as soon as stage 1 completes,
+// so 12 jobs can be in flight.  Full: 8 slots of 64 columns holding A1 at [0, 32), D1 at [32, 64)
+// and then D2 at [0, 64).
+#ifndef VCA_TC_SEP_A1
+#define VCA_TC_SEP_A1 0
+#endif
+template <bool LP>
+struct Lay {
+  static constexpr bool SEP = LP && VCA_TC_SEP_A1;  // stage-1 operands in their own ring
+  static constexpr int kD = SEP ? 12 : 8;           // accumulator slots
+  static constexpr int DCols = SEP ? 32 : 64;
+  static constexpr int kA1 = SEP ? 4 : kD;          // stage-1 operand buffers
+  static constexpr int A1Base = SEP ? 384 : 0;      // first column of the operand ring
+  static constexpr int A1Stride = SEP ? 32 : 64;
+  static constexpr int D1Off = SEP ? 0 : 32;        // D1 within an accumulator slot
+  static_assert(kD * DCols + (SEP ? kA1 * A1Stride : 0) <= 512, "TMEM budget");
+};
 
 // barrier indices
 __host__ __device__ constexpr int b_raw_full(int s) { return s; }
 __host__ __device__ constexpr int b_raw_empty(int s) { return kStages + s; }
-__host__ __device__ constexpr int b_slot_free(int s) { return 2 * kStages + s; }
-__host__ __device__ constexpr int b_a1(int s) { return 2 * kStages + kSlots + s; }
-__host__ __device__ constexpr int b_d1(int s) { return 2 * kStages + 2 * kSlots + s; }
-__host__ __device__ constexpr int b_d2(int s) { return 2 * kStages + 3 * kSlots + s; }
-__host__ __device__ constexpr int b_a2_full(int s) { return 2 * kStages + 4 * kSlots + s; }
-__host__ __device__ constexpr int b_a2_free(int s) { return 2 * kStages + 4 * kSlots + kA2Slots + s; }
-__host__ __device__ constexpr int b_drain(int i) { return 2 * kStages + 4 * kSlots + 2 * kA2Slots + i; }
-static_assert(b_drain(1) < 64, "barrier area");
+__host__ __device__ constexpr int b_slot_free(int s) { return 2 * kStages + s; }     // up to 12
+__host__ __device__ constexpr int b_d1(int s) { return 2 * kStages + 12 + s; }
+__host__ __device__ constexpr int b_d2(int s) { return 2 * kStages + 24 + s; }
+__host__ __device__ constexpr int b_a1_full(int s) { return 2 * kStages + 36 + s; }  // up to 8
+__host__ __device__ constexpr int b_a1_free(int s) { return 2 * kStages + 44 + s; }  // up to 4
+__host__ __device__ constexpr int b_a2_full(int s) { return 2 * kStages + 48 + s; }
+__host__ __device__ constexpr int b_a2_free(int s) { return 2 * kStages + 52 + s; }
+__host__ __device__ constexpr int b_drain(int i) { return 2 * kStages + 56 + i; }
+static_assert(b_drain(1) < kBars, "barrier area");
 
-constexpr int kThreads = 768;
+constexpr int kThreads = 896;
 constexpr uint32_t kTmemCols = 512;
-static_assert(kSlots * kSlotCols <= 512, "TMEM budget");
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 // FP32 magic constants (see the file comment).
@@ -200,14 +222,12 @@ __device__ __forceinline__ void fill_cols(uint32_t taddr, float first, float res
   tmem_fill<N>(taddr, __float_as_uint(first), __float_as_uint(rest));
 }
 
-// Job bookkeeping carried through the worker pipeline in registers.
+// Block coordinates of one job for the epilogue that writes its results.
 struct JobCtx {
   int plane;  // 0 Y, 1 U, 2 V
   int jp;     // job index within the plane's tile
   int f;      // frame
   int tx, ty; // tile position (units of 4 blocks)
-  int slot;   // TMEM slot within the group
-  int job;    // group-local job index
 };
 
 template <bool LP>
@@ -245,14 +265,16 @@ __device__ __forceinline__ void a2_slot_of(int j, int& slot, int& use) {
   }
 }
 
+// Shared-memory address of the stage-2 operand (hi; lo follows at +kA2L / +kA2C).
+__device__ __forceinline__ uint32_t a2_addr(uint32_t sbase, int a2) {
+  return a2 < 2 ? sbase + OFF_A2 + a2 * 2 * kA2L : sbase + OFF_A2C + (a2 - 2) * 2 * kA2C;
+}
+
 // ---- worker phases ----------------------------------------------------------
-// TMEM slot layout (64 columns): A1 (stage-1 A operand, fp16 pairs) at [0, G*Nb/2), D1 (stage-1
-// accumulators) at [32, 32 + G*N1).  Once stage 1 has been read back, the stage-2 accumulators
-// reuse the slot: D2_hi at [0, N1), D2_lo at [N1, 2*N1).
 
 template <int Nb, bool LP>
-__device__ __forceinline__ void convert_job(const uint8_t* raw_plane, int jp, int h_rem, int w_rem, uint32_t taddr,
-                                            int q, int lane, const uint32_t (&d1init)[PC<Nb, LP>::N1]) {
+__device__ __forceinline__ void convert_job(const uint8_t* raw_plane, int jp, int h_rem, int w_rem, uint32_t ta1,
+                                            int q, int lane) {
   using P = PC<Nb, LP>;
   const int l = 32 * q + lane;
   const int bg = l / Nb;
@@ -265,14 +287,15 @@ __device__ __forceinline__ void convert_job(const uint8_t* raw_plane, int jp, in
     const int x = (idx & 3) * Nb;
     uint32_t a[Nb / 2];
     load_row_fp16<Nb>(raw_plane, y, x, w_rem, a);
-    tmem_st<Nb / 2>(taddr + g * P::A1COLS, a);
-    tmem_st<P::N1>(taddr + 32 + g * P::N1, d1init);
+    tmem_st<Nb / 2>(ta1 + g * P::A1COLS, a);
   }
 }
 
+// Reads D1 (stage-1 accumulators at td1 + g*N1), writes the stage-2 operand to shared memory, and
+// pre-sets the stage-2 accumulators at td2 (hi) and td2 + N1 (lo), which may overlap D1.
 template <int Nb, bool LP>
-__device__ __forceinline__ void epilogue1(uint32_t taddr, uint32_t a2hi, uint32_t a2lo, int q, int lane, float s1inv,
-                                          float hi0, float lo) {
+__device__ __forceinline__ void epilogue1(uint32_t td1, uint32_t td2, uint32_t a2hi, uint32_t a2lo, int q, int lane,
+                                          float s1inv, float c0, float c, float hi0, float lo) {
   using P = PC<Nb, LP>;
   constexpr int NK = P::NK;
   const int l = 32 * q + lane;
@@ -280,35 +303,37 @@ __device__ __forceinline__ void epilogue1(uint32_t taddr, uint32_t a2hi, uint32_
   const int r = l % Nb;
   uint32_t acc[P::G][NK];
 #pragma unroll
-  for (int g = 0; g < P::G; ++g) tmem_ld<NK>(taddr + 32 + g * P::N1, acc[g]);
+  for (int g = 0; g < P::G; ++g) tmem_ld<NK>(td1 + g * P::N1, acc[g]);
   tmem_wait_ld();
-  // The slot now belongs to stage 2: pre-set its accumulators (see the file comment).
-  fill_cols<P::N1>(taddr, hi0, kK1);
-  fill_cols<P::N1>(taddr + P::N1, lo, lo);
+  fill_cols<P::N1>(td2, hi0, kK1);
+  fill_cols<P::N1>(td2 + P::N1, lo, lo);
   const uint32_t rowoff = (uint32_t)((r >> 3) * 2048 + (r & 7) * 128);
 #pragma unroll
   for (int g = 0; g < P::G; ++g) {
     uint32_t hi[NK / 2], lw[NK / 2];
 #pragma unroll
     for (int k = 0; k < NK; k += 2) {
-      const uint32_t za = __float_as_uint(__fmaf_rd(__uint_as_float(acc[g][k]), s1inv, kT1));
-      const uint32_t zb = __float_as_uint(__fmaf_rd(__uint_as_float(acc[g][k + 1]), s1inv, kT1));
+      // T' = D1 + c_k (rounding offset 2^(s1-1), minus the sample-encoding bias on the DC row): exact.
+      const float ta = __uint_as_float(acc[g][k]) + (k == 0 ? c0 : c);
+      const float tb = __uint_as_float(acc[g][k + 1]) + c;
+      const uint32_t za = __float_as_uint(__fmaf_rd(ta, s1inv, kT1));
+      const uint32_t zb = __float_as_uint(__fmaf_rd(tb, s1inv, kT1));
       lw[k / 2] = prmt(za, zb, 0x6420);
       hi[k / 2] = prmt(za, zb, 0x6521);
     }
     const int m0 = (g * P::BPG1 + bg) * NK;
 #pragma unroll
-    for (int c = 0; c < NK / 8; ++c) {
-      const int m = m0 + 8 * c;
+    for (int cc = 0; cc < NK / 8; ++cc) {
+      const int m = m0 + 8 * cc;
       const uint32_t off = rowoff + (uint32_t)((m >> 6) * 1024) + (uint32_t)(((((m & 63) >> 3) ^ (r & 7))) << 4);
-      sts128(a2hi + off, hi[4 * c], hi[4 * c + 1], hi[4 * c + 2], hi[4 * c + 3]);
-      sts128(a2lo + off, lw[4 * c], lw[4 * c + 1], lw[4 * c + 2], lw[4 * c + 3]);
+      sts128(a2hi + off, hi[4 * cc], hi[4 * cc + 1], hi[4 * cc + 2], hi[4 * cc + 3]);
+      sts128(a2lo + off, lw[4 * cc], lw[4 * cc + 1], lw[4 * cc + 2], lw[4 * cc + 3]);
     }
   }
 }
 
 template <int Nb, bool LP, bool DUMP>
-__device__ __forceinline__ void epilogue2(const TcParams& p, uint32_t taddr, const JobCtx& jc, int q, int lane,
+__device__ __forceinline__ void epilogue2(const TcParams& p, uint32_t td2, const JobCtx& jc, int q, int lane,
                                           const float (&wts)[PC<Nb, LP>::NK], float einv, float c2,
                                           uint64_t* slot_free) {
   using P = PC<Nb, LP>;
@@ -328,8 +353,8 @@ __device__ __forceinline__ void epilogue2(const TcParams& p, uint32_t taddr, con
 #pragma unroll
   for (int h0 = 0; h0 < NK; h0 += HALF) {
     uint32_t hi[HALF], lo[HALF];
-    tmem_ld<HALF>(taddr + h0, hi);
-    tmem_ld<HALF>(taddr + P::N1 + h0, lo);
+    tmem_ld<HALF>(td2 + h0, hi);
+    tmem_ld<HALF>(td2 + P::N1 + h0, lo);
     tmem_wait_ld();
     if (h0 + HALF == NK) {  // every accumulator of the slot is in registers: hand the slot back
       tc_fence_before();
@@ -355,9 +380,7 @@ __device__ __forceinline__ void epilogue2(const TcParams& p, uint32_t taddr, con
   }
 }
 
-// ---- the kernel --------------------------------------------------------------
-
-// Tile bookkeeping of a role's current tile (recomputed at the first job of each tile).
+// Tile bookkeeping of a role's current tile.
 struct TileInfo {
   int f, tx, ty, stage, t;
 };
@@ -374,35 +397,79 @@ __device__ __forceinline__ TileInfo tile_info(const TcParams& p, int t, int cta,
   return ti;
 }
 
-// ---- role loops of the two epilogues (one instantiation per plane type) ------------------
+// ---- role loops (one instantiation per plane type) -------------------------------
 
-template <bool LP>
-__device__ __forceinline__ bool is_plane_job(int j, bool luma) {
-  int plane, jp;
-  plane_of<LP>(j, plane, jp);
-  return (plane == 0) == luma;
+// Convert: raw samples of the tile -> stage-1 A operand in TMEM, for every job of one plane type.
+template <int Nb, bool LP>
+__device__ void convert_loop(const TcParams& p, const Ctl& ctl, uint8_t* sm, uint32_t tq, int n_jobs, int cta,
+                             int grid, int tiles_per_frame, int q, int lane) {
+  using Y = Lay<LP>;
+  constexpr int JPT = Jobs<LP>::PER_TILE;
+  constexpr int T = 4 * Nb;  // tile edge of this plane in samples
+  const int pw = Nb == 32 ? p.W : p.cw, ph = Nb == 32 ? p.H : p.ch;
+  const int last_of_plane = Nb == 32 ? PC<32, LP>::JOBS - 1 : JPT - 1;
+  TileInfo ti{};
+  int h_rem = 0, w_rem = 0, last_tile = -1;
+  for (int jj = 0; jj < n_jobs; ++jj) {
+    const int j = jj % JPT;
+    int plane, jp;
+    plane_of<LP>(j, plane, jp);
+    if ((plane == 0) != (Nb == 32)) continue;
+    const int t = jj / JPT;
+    if (t != last_tile) {
+      ti = tile_info(p, t, cta, grid, tiles_per_frame);
+      h_rem = ph - ti.ty * T;
+      w_rem = pw - ti.tx * T;
+      last_tile = t;
+      if (!wait_bar(ctl, b_raw_full(ti.stage), (t / kStages) & 1, 4)) break;
+    }
+    const int buf = jj % Y::kA1;
+    if (Y::SEP) {
+      if (jj >= Y::kA1 && !wait_bar(ctl, b_a1_free(buf), ((jj / Y::kA1) - 1) & 1, 4)) break;
+    } else {
+      if (jj >= Y::kD && !wait_bar(ctl, b_slot_free(buf), ((jj / Y::kD) - 1) & 1, 4)) break;
+    }
+    tc_fence_after();
+    const uint8_t* raw = sm + OFF_RAW + ti.stage * kStageBytes + (plane == 0 ? 0 : kRawY + (plane - 1) * kRawC);
+    convert_job<Nb, LP>(raw, jp, h_rem, w_rem, tq + Y::A1Base + buf * Y::A1Stride, q, lane);
+    tmem_wait_st();
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) {
+      mbar_arrive(&ctl.bars[b_a1_full(buf)]);
+      if (j == last_of_plane) mbar_arrive(&ctl.bars[b_raw_empty(ti.stage)]);
+    }
+  }
 }
 
-// Epilogue 1 of every job of one plane type: T = floor(T'/2^s1) into the stage-2 operand (hi and
-// lo bytes as fp16, MN-major), and the stage-2 accumulators pre-set: hi starts at
-// K1 - 1156 * 64 * N for u = 0 (the 1024 + byte encoding of both halves) and K1 otherwise, lo at
-// 2^(s2-1) (luma N = 32: s1 = 4, s2 = 11; chroma N = 16: s1 = 3, s2 = 10).
+// Epilogue 1: T = floor(T'/2^s1) into the stage-2 operand (hi and lo bytes as fp16, MN-major), and
+// the stage-2 accumulators pre-set: hi starts at K1 - 1156 * 64 * N for u = 0 (the 1024 + byte
+// encoding of both halves) and K1 otherwise, lo at 2^(s2-1) (luma N = 32: s1 = 4, s2 = 11; chroma
+// N = 16: s1 = 3, s2 = 10).
 template <int Nb, bool LP>
 __device__ void epi1_loop(const Ctl& ctl, uint32_t sbase, uint32_t tq, int n_jobs, int q, int lane) {
+  using Y = Lay<LP>;
   constexpr int JPT = Jobs<LP>::PER_TILE;
   const float s1inv = Nb == 32 ? 0.0625f : 0.125f;
+  // D1 + c_k: 2^(s1-1), minus the 1024 * 64 * N bias of the 1024 + x sample encoding on the DC row.
+  const float c0 = Nb == 32 ? 8.0f - 2097152.0f : 4.0f - 1048576.0f;
+  const float c = Nb == 32 ? 8.0f : 4.0f;
   const float hi0 = Nb == 32 ? kK1 - 2367488.0f : kK1 - 1183744.0f;
   const float lo = Nb == 32 ? 1024.0f : 512.0f;
+  const uint32_t lo_off = Nb == 32 ? kA2L : kA2C;
   for (int jj = 0; jj < n_jobs; ++jj) {
-    if (!is_plane_job<LP>(jj % JPT, Nb == 32)) continue;
-    const int slot = jj % kSlots;
+    int plane, jp;
+    plane_of<LP>(jj % JPT, plane, jp);
+    if ((plane == 0) != (Nb == 32)) continue;
+    const int slot = jj % Y::kD;
     int a2, use;
     a2_slot_of<LP>(jj, a2, use);
-    if (!wait_bar(ctl, b_d1(slot), (jj / kSlots) & 1, 4)) break;
-    if (use >= 1 && !wait_bar(ctl, b_a2_free(a2), (use - 1) & 1, 4)) break;
+    if (!wait_bar(ctl, b_d1(slot), (jj / Y::kD) & 1, 4, false, true)) break;
+    if (use >= 1 && !wait_bar(ctl, b_a2_free(a2), (use - 1) & 1, 4, false, true)) break;
     tc_fence_after();
-    const uint32_t ahi = sbase + OFF_A2 + a2 * 2 * kA2Bytes, alo = ahi + kA2Bytes;
-    epilogue1<Nb, LP>(tq + slot * kSlotCols, ahi, alo, q, lane, s1inv, hi0, lo);
+    const uint32_t ahi = a2_addr(sbase, a2);
+    const uint32_t td = tq + slot * Y::DCols;
+    epilogue1<Nb, LP>(td + Y::D1Off, td, ahi, ahi + lo_off, q, lane, s1inv, c0, c, hi0, lo);
     tmem_wait_st();
     fence_proxy_async_smem();
     tc_fence_before();
@@ -411,11 +478,12 @@ __device__ void epi1_loop(const Ctl& ctl, uint32_t sbase, uint32_t tq, int n_job
   }
 }
 
-// Epilogue 2 of every job of one plane type: Z, the block energy H and brightness L.
+// Epilogue 2: Z, the block energy H and brightness L, for every job of one plane type.
 template <int Nb, bool LP, bool DUMP>
 __device__ void epi2_loop(const TcParams& p, const Ctl& ctl, uint32_t tq, int n_jobs, int cta, int grid,
                           int tiles_per_frame, int q, int lane) {
   using P = PC<Nb, LP>;
+  using Y = Lay<LP>;
   constexpr int JPT = Jobs<LP>::PER_TILE;
   const float* Wt = Nb == 32 ? p.W_y : p.W_c;
   float w[P::NK];
@@ -427,21 +495,21 @@ __device__ void epi2_loop(const TcParams& p, const Ctl& ctl, uint32_t tq, int n_
   int last_tile = -1;
   for (int jj = 0; jj < n_jobs; ++jj) {
     const int j = jj % JPT;
-    if (!is_plane_job<LP>(j, Nb == 32)) continue;
+    JobCtx jc;
+    plane_of<LP>(j, jc.plane, jc.jp);
+    if ((jc.plane == 0) != (Nb == 32)) continue;
     const int t = jj / JPT;
     if (t != last_tile) {
       ti = tile_info(p, t, cta, grid, tiles_per_frame);
       last_tile = t;
     }
-    const int slot = jj % kSlots;
-    if (!wait_bar(ctl, b_d2(slot), (jj / kSlots) & 1, 4)) break;
+    const int slot = jj % Y::kD;
+    if (!wait_bar(ctl, b_d2(slot), (jj / Y::kD) & 1, 4, false, true)) break;
     tc_fence_after();
-    JobCtx jc;
-    plane_of<LP>(j, jc.plane, jc.jp);
     jc.f = ti.f;
     jc.tx = ti.tx;
     jc.ty = ti.ty;
-    epilogue2<Nb, LP, DUMP>(p, tq + slot * kSlotCols, jc, q, lane, w, einv, c2, &ctl.bars[b_slot_free(slot)]);
+    epilogue2<Nb, LP, DUMP>(p, tq + slot * Y::DCols, jc, q, lane, w, einv, c2, &ctl.bars[b_slot_free(slot)]);
   }
 }
 
@@ -451,7 +519,9 @@ __global__ void __launch_bounds__(kThreads, 1)
               const __grid_constant__ CUtensorMap mapV, const TcParams p) {
   using L = PC<32, LP>;
   using Cc = PC<16, LP>;
+  using Y = Lay<LP>;
   constexpr int JPT = Jobs<LP>::PER_TILE;
+  static_assert(Y::kD % JPT == 0 && Y::kA1 % JPT == 0, "a TMEM slot must always hold the same plane type");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(sm + OFF_BAR);
@@ -482,22 +552,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     *(__half*)(sm + OFF_BC + (n >> 3) * 256 + (kk >> 3) * 128 + (n & 7) * 16 + (kk & 7) * 2) = h;
   }
   if (tid == 0) {
-    for (int i = 0; i < kStages; ++i) {
-      mbar_init(&bars[b_raw_full(i)], 1);
-      mbar_init(&bars[b_raw_empty(i)], 4);
-    }
-    for (int i = 0; i < kSlots; ++i) {
-      mbar_init(&bars[b_slot_free(i)], 4);
-      mbar_init(&bars[b_a1(i)], 4);
-      mbar_init(&bars[b_d1(i)], 1);
-      mbar_init(&bars[b_d2(i)], 1);
-    }
-    for (int i = 0; i < kA2Slots; ++i) {
-      mbar_init(&bars[b_a2_full(i)], 4);
-      mbar_init(&bars[b_a2_free(i)], 1);
-    }
-    mbar_init(&bars[b_drain(0)], 1);
-    mbar_init(&bars[b_drain(1)], 1);
+    for (int i = 0; i < kBars; ++i) mbar_init(&bars[i], 1);
+    for (int i = 0; i < kStages; ++i) mbar_init(&bars[b_raw_empty(i)], 8);  // both convert warpgroups
+    for (int i = 0; i < Y::kD; ++i) mbar_init(&bars[b_slot_free(i)], 4);
+    for (int i = 0; i < Y::kA1; ++i) mbar_init(&bars[b_a1_full(i)], 4);
+    for (int i = 0; i < kA2Slots; ++i) mbar_init(&bars[b_a2_full(i)], 4);
     *abort_flag = 0;
     fence_mbar_init();
   }
@@ -546,26 +605,33 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int j = 0; j < n_jobs; ++j) {
         int plane, jp;
         plane_of<LP>(j % JPT, plane, jp);
-        const int slot = j % kSlots;
-        if (!wait_bar(ctl, b_a1(slot), (j / kSlots) & 1, 2)) {
+        const int buf = j % Y::kA1;
+        const int slot = j % Y::kD;
+        if (!wait_bar(ctl, b_a1_full(buf), (j / Y::kA1) & 1, 2)) {
+          ok = false;
+          break;
+        }
+        if (Y::SEP && j >= Y::kD && !wait_bar(ctl, b_slot_free(slot), ((j / Y::kD) - 1) & 1, 2)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        const uint32_t d = tmem + slot * kSlotCols;
+        const uint32_t d = tmem + slot * Y::DCols + Y::D1Off;
+        const uint32_t a = tmem + Y::A1Base + buf * Y::A1Stride;
         if (plane == 0) {
-          // K-step outer: consecutive MMAs write different accumulators, so none waits on the last.
+          // K-step outer: consecutive MMAs write different accumulators.
 #pragma unroll
           for (int ks = 0; ks < L::KS; ++ks)
 #pragma unroll
             for (int gg = 0; gg < L::G; ++gg)
-              mma_ts(d + 32 + gg * L::N1, d + gg * L::A1COLS + ks * 8, smem_desc(bl + ks * 256, 128, 512, 0), idL, 1);
+              mma_ts(d + gg * L::N1, a + gg * L::A1COLS + ks * 8, smem_desc(bl + ks * 256, 128, 512, 0), idL, ks > 0);
         } else {
 #pragma unroll
           for (int gg = 0; gg < Cc::G; ++gg)
-            mma_ts(d + 32 + gg * Cc::N1, d + gg * Cc::A1COLS, smem_desc(bc, 128, 256, 0), idC, 1);
+            mma_ts(d + gg * Cc::N1, a + gg * Cc::A1COLS, smem_desc(bc, 128, 256, 0), idC, 0);
         }
         mma_commit(&bars[b_d1(slot)]);
+        if (Y::SEP) mma_commit(&bars[b_a1_free(buf)]);
       }
       if (!ok) {
         mma_commit(&bars[b_drain(0)]);
@@ -586,21 +652,21 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t d = tmem + (j % kSlots) * kSlotCols;
-        const uint32_t ahi = sbase + OFF_A2 + a2 * 2 * kA2Bytes, alo = ahi + kA2Bytes;
+        const uint32_t d = tmem + (j % Y::kD) * Y::DCols;
+        const uint32_t ahi = a2_addr(sbase, a2);
         if (plane == 0) {
 #pragma unroll
           for (int ks = 0; ks < L::KS; ++ks) {
             const uint64_t b = smem_desc(bl + ks * 256, 128, 512, 0);
             mma_ss(d, smem_desc(ahi + ks * 4096, 1024, 2048, 2), b, id2L, 1);
-            mma_ss(d + L::N1, smem_desc(alo + ks * 4096, 1024, 2048, 2), b, id2L, 1);
+            mma_ss(d + L::N1, smem_desc(ahi + kA2L + ks * 4096, 1024, 2048, 2), b, id2L, 1);
           }
         } else {
           const uint64_t b = smem_desc(bc, 128, 256, 0);
           mma_ss(d, smem_desc(ahi, 1024, 2048, 2), b, id2C, 1);
-          mma_ss(d + Cc::N1, smem_desc(alo, 1024, 2048, 2), b, id2C, 1);
+          mma_ss(d + Cc::N1, smem_desc(ahi + kA2C, 1024, 2048, 2), b, id2C, 1);
         }
-        mma_commit(&bars[b_d2(j % kSlots)]);
+        mma_commit(&bars[b_d2(j % Y::kD)]);
         mma_commit(&bars[b_a2_free(a2)]);
       }
       if (!ok) {
@@ -609,45 +675,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else if (role == 1) {
-    // ---------------- convert: raw samples -> TMEM A operand, accumulator offsets ----------------
-    // Luma (N = 32, 8-bit): s1 = 4; chroma (N = 16): s1 = 3.  D1 starts at 2^(s1-1), minus the
-    // 1024 * 64 * N bias that the 1024 + x sample encoding adds to the DC row.
-    uint32_t initL[L::N1], initC[Cc::N1];
-#pragma unroll
-    for (int i = 0; i < L::N1; ++i) initL[i] = __float_as_uint(i == 0 ? 8.0f - 2097152.0f : 8.0f);
-#pragma unroll
-    for (int i = 0; i < Cc::N1; ++i) initC[i] = __float_as_uint(i == 0 ? 4.0f - 1048576.0f : 4.0f);
-    TileInfo ti{};
-    int h_remL = 0, w_remL = 0, h_remC = 0, w_remC = 0;
-    for (int jj = 0; jj < n_jobs; ++jj) {
-      const int j = jj % JPT;
-      if (j == 0) {
-        ti = tile_info(p, jj / JPT, cta, grid, tiles_per_frame);
-        h_remL = p.H - ti.ty * 128;
-        w_remL = p.W - ti.tx * 128;
-        h_remC = p.ch - ti.ty * 64;
-        w_remC = p.cw - ti.tx * 64;
-        if (!wait_bar(ctl, b_raw_full(ti.stage), (ti.t / kStages) & 1, 4)) break;
-      }
-      const int slot = jj % kSlots;
-      if (jj >= kSlots && !wait_bar(ctl, b_slot_free(slot), ((jj / kSlots) - 1) & 1, 4)) break;
-      tc_fence_after();
-      int plane, jp;
-      plane_of<LP>(j, plane, jp);
-      const uint8_t* raw = sm + OFF_RAW + ti.stage * kStageBytes;
-      const uint32_t ta = tmem + lanebase + slot * kSlotCols;
-      if (plane == 0)
-        convert_job<32, LP>(raw, jp, h_remL, w_remL, ta, q, lane, initL);
-      else
-        convert_job<16, LP>(raw + kRawY + (plane - 1) * kRawC, jp, h_remC, w_remC, ta, q, lane, initC);
-      tmem_wait_st();
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(&bars[b_a1(slot)]);
-        if (j == JPT - 1) mbar_arrive(&bars[b_raw_empty(ti.stage)]);
-      }
-    }
+    convert_loop<32, LP>(p, ctl, sm, tmem + lanebase, n_jobs, cta, grid, tiles_per_frame, q, lane);
+  } else if (role == 6) {
+    convert_loop<16, LP>(p, ctl, sm, tmem + lanebase, n_jobs, cta, grid, tiles_per_frame, q, lane);
   } else if (role == 2) {
     epi1_loop<32, LP>(ctl, sbase, tmem + lanebase, n_jobs, q, lane);
   } else if (role == 3) {
