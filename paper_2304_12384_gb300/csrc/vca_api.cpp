@@ -84,6 +84,8 @@ struct vca_analyzer {
   int cur_prev = 0;
   double* d_feats = nullptr;     // max_batch * FEAT_STRIDE
   int* d_err = nullptr;          // kernel wait-timeout flag of the current push
+  double* d_red_partials = nullptr;       // frame-reduction scratch
+  unsigned int* d_red_counters = nullptr; // one arrival counter per frame, kept at zero between launches
   uint8_t* d_staging = nullptr;  // host frames are copied here
   size_t staging_bytes = 0;
 
@@ -170,6 +172,8 @@ void destroy(vca_analyzer* a) {
   cudaFree(a->d_prevH[1]);
   cudaFree(a->d_feats);
   cudaFree(a->d_err);
+  cudaFree(a->d_red_partials);
+  cudaFree(a->d_red_counters);
   if (a->h_err) cudaFreeHost(a->h_err);
   cudaFree(a->d_staging);
   if (a->h_ring) cudaFreeHost(a->h_ring);
@@ -359,6 +363,9 @@ vca_status vca_open(const vca_config* cfg, void* cuda_stream, vca_analyzer** out
     OPEN_CUDA(cudaMemset(a->d_prevH[i], 0, (size_t)g.C * sizeof(float)), "clearing h state");
   }
   OPEN_CUDA(cudaMalloc(&a->d_feats, (size_t)a->max_batch * vca::FEAT_STRIDE * sizeof(double)), "allocating features");
+  OPEN_CUDA(cudaMalloc(&a->d_red_partials, vca::reduce_partials_bytes(a->max_batch)), "allocating reduction scratch");
+  OPEN_CUDA(cudaMalloc(&a->d_red_counters, (size_t)a->max_batch * sizeof(unsigned int)), "allocating counters");
+  OPEN_CUDA(cudaMemset(a->d_red_counters, 0, (size_t)a->max_batch * sizeof(unsigned int)), "clearing counters");
   OPEN_CUDA(cudaMalloc(&a->d_err, sizeof(int)), "allocating the error flag");
   OPEN_CUDA(cudaMemset(a->d_err, 0, sizeof(int)), "clearing the error flag");
   OPEN_CUDA(cudaMallocHost(&a->h_err, kRing * sizeof(int)), "allocating pinned error flags");
@@ -407,7 +414,8 @@ vca_status vca_push_frames(vca_analyzer* a, const void* y, const void* u, const 
   if (e != cudaSuccess) return cuda_fail(e, "launching the analysis kernel");
   if (timed) VCA_CUDA(cudaEventRecord(a->t1_ev[slot], a->stream), "recording timing event");
   e = vca::launch_reduce(a->g, n_frames, a->d_blockvals, a->d_prevH[a->cur_prev], a->has_prev,
-                         a->d_prevH[a->cur_prev ^ 1], a->d_feats, a->stream, &a->launches);
+                         a->d_prevH[a->cur_prev ^ 1], a->d_feats, a->d_red_partials, a->d_red_counters, a->stream,
+                         &a->launches);
   if (e != cudaSuccess) return cuda_fail(e, "launching the frame reduction");
   VCA_CUDA(cudaMemcpyAsync(a->h_ring + (size_t)slot * a->max_batch * vca::FEAT_STRIDE, a->d_feats,
                            (size_t)n_frames * vca::FEAT_STRIDE * sizeof(double), cudaMemcpyDeviceToHost, a->stream),

@@ -63,8 +63,12 @@ cudaError_t launch_tc(const Geometry& g, const FramePlanes& fp, int nframes, con
                       float* blockvals, int16_t* const zdump[3], int* err, cudaStream_t s, int64_t* launches);
 bool tc_supported(const Geometry& g);
 
-// Deterministic FP64 frame reduction: features of n frames and the h state update.
+// Deterministic FP64 frame reduction: features of n frames and the h state update.  `partials`
+// holds reduce_partials_bytes(max frames) of scratch; `counters` (one per frame) must be zero on
+// entry and is zero again on exit.
+size_t reduce_partials_bytes(int max_frames);
 cudaError_t launch_reduce(const Geometry& g, int nframes, const float* blockvals, const float* prevH_in,
-                          int has_prev, float* prevH_out, double* feats, cudaStream_t s, int64_t* launches);
+                          int has_prev, float* prevH_out, double* feats, double* partials, unsigned int* counters,
+                          cudaStream_t s, int64_t* launches);
 
 }  // namespace vca
