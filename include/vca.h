@@ -167,6 +167,34 @@ vca_status vca_kernel_in_use(vca_analyzer* a, int32_t* kernel);
 /* Free the analyzer (waits for its device work). NULL is accepted. */
 vca_status vca_close(vca_analyzer* a);
 
+/* Frame features from per-block values already on the device, without allocating any device
+ * memory.  The paper has no counterpart: this is a runtime convenience for callers that must not
+ * call the CUDA allocator on their hot path (a serving loop that has budgeted all device memory
+ * up front to decide admission; a host thread with other streams in flight, for which an
+ * allocation may block and a free waits for the whole device).
+ *
+ * Computes, like the analyzer (Section 2 of the paper), per frame f: E_P = sum_k H_{P,k} /
+ * (C N_P^2), L_P = sum_k L_{P,k} / C, h = sum_k |H_{Y,k,f} - H_{Y,k,f-1}| / (C w^2).
+ *   block_values  device, [n_frames][6][C] FP32, rows H_Y, L_Y, H_U, L_U, H_V, L_V (C =
+ *                 blocks_per_plane, raster block order); read only.
+ *   block_size    luma block size w: 32 or 16 (chroma blocks are w/2).
+ *   n_frames      1 .. 256: the frames the fixed scratch holds; more gives VCA_E_ARG.
+ *   prev_H_Y      device, C FP32 luma energies of the frame before frame 0, or NULL for h = 0
+ *                 on frame 0.
+ *   last_H_Y      device, C FP32, receives H_Y of frame n_frames - 1 (the next call's
+ *                 prev_H_Y); must not be prev_H_Y.
+ *   features      device, n_frames x 8 doubles: E_Y, h, L_Y, E_U, E_V, L_U, L_V, 0.
+ *   cuda_stream   the stream the work is queued on (NULL: legacy default stream); the call
+ *                 returns without waiting.
+ * The caller owns every buffer.  The scratch is one fixed array per device: calls that may
+ * overlap on the device (unordered streams, several host threads) race on it; order them.
+ * The first call on a device looks the array up and may load the module, so make it before
+ * any stream capture.  VCA_E_ARG for NULL outputs, a bad block size or a size outside the
+ * limits; VCA_E_CUDA if the lookup or the launch fails. */
+vca_status vca_reduce_frames_noalloc(const float* block_values, int64_t blocks_per_plane, int32_t block_size,
+                                     int32_t n_frames, const float* prev_H_Y, float* last_H_Y,
+                                     double* features, void* cuda_stream);
+
 /* Static description of a status code, and the calling thread's last error message. */
 const char* vca_status_str(vca_status s);
 const char* vca_last_error(void);

@@ -36,6 +36,13 @@ vca_status fail(vca_status s, const char* fmt, ...) {
   return s;
 }
 
+}  // namespace
+
+// Lets entry points defined in other translation units report a message through vca_last_error.
+void vca::record_error(const char* msg) { g_last_error = msg; }
+
+namespace {
+
 vca_status cuda_fail(cudaError_t e, const char* what) {
   cudaGetLastError();  // clear a sticky-free error so later calls are not blamed for it
   return fail(e == cudaErrorMemoryAllocation ? VCA_E_NOMEM : VCA_E_CUDA, "%s: %s (%d)", what,

@@ -71,4 +71,7 @@ cudaError_t launch_reduce(const Geometry& g, int nframes, const float* blockvals
                           int has_prev, float* prevH_out, double* feats, double* partials, unsigned int* counters,
                           cudaStream_t s, int64_t* launches);
 
+// Sets the calling thread's vca_last_error message.
+void record_error(const char* msg);
+
 }  // namespace vca

@@ -9,6 +9,10 @@
 //   h_t = sum_k |H_{Y,k,t} - H_{Y,k,t-1}| / (C w^2), and h = 0 without a previous frame.
 // The CTAs of the last frame also copy its luma energies as the next call's previous-frame state
 // (into a buffer distinct from the one read here).
+#include <cstdio>
+#include <mutex>
+
+#include "vca.h"
 #include "vca_internal.h"
 
 namespace vca {
@@ -118,3 +122,103 @@ cudaError_t launch_reduce(const Geometry& g, int nframes, const float* blockvals
 }
 
 }  // namespace vca
+
+// ---- Allocation-free entry point ------------------------------------------------------
+//
+// vca_reduce_frames_noalloc runs the same reduction kernel on block values the caller already
+// holds on the device, with its scratch (the per-slice partial sums and the per-frame arrival
+// counters) in a fixed array of this module instead of memory from the CUDA allocator.  It exists
+// for callers that must not allocate device memory on their hot path: a serving loop that has
+// budgeted every byte of HBM up front to decide how many channels it admits, and a host thread
+// that keeps other streams' work in flight, for which cudaMalloc may block and cudaFree waits for
+// the whole device.
+//
+// The scratch is one array per device, so calls that can run on the device at the same time
+// (different streams without ordering between them, or several host threads) race on it and give
+// wrong features; the caller keeps such calls ordered (one stream, or events).  The arrival
+// counters must be zero when a launch starts: the loader zero-fills the array when the module is
+// loaded, and every launch leaves the counters of the frames it touched at zero again.  The first
+// call on each device looks up the array's device address (cudaGetSymbolAddress, which may also
+// load the module), so make that first call before capturing a stream into a CUDA graph.
+
+namespace vca {
+namespace {
+
+constexpr int kNoAllocMaxFrames = 256;
+constexpr size_t kNoAllocPartialBytes = (size_t)kNoAllocMaxFrames * kSlices * kSums * sizeof(double);
+constexpr size_t kNoAllocBytes = kNoAllocPartialBytes + (size_t)kNoAllocMaxFrames * sizeof(unsigned int);
+static_assert(kNoAllocPartialBytes % 256 == 0, "counters start on a 256-byte boundary");
+
+// 114,688 B of partial sums (256 frames x 8 slices x 7 doubles), then 256 counters.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+vca_status noalloc_fail(vca_status st, const char* msg) {
+  record_error(msg);
+  return st;
+}
+
+}  // namespace
+}  // namespace vca
+
+extern "C" vca_status vca_reduce_frames_noalloc(const float* block_values, int64_t blocks_per_plane,
+                                                int32_t block_size, int32_t n_frames, const float* prev_H_Y,
+                                                float* last_H_Y, double* features, void* cuda_stream) {
+  using namespace vca;
+  char msg[256];
+  if (!block_values || !last_H_Y || !features)
+    return noalloc_fail(VCA_E_ARG, "vca_reduce_frames_noalloc: block_values, last_H_Y and features must be non-NULL");
+  if (block_size != 16 && block_size != 32)
+    return noalloc_fail(VCA_E_ARG, "vca_reduce_frames_noalloc: block_size must be 16 or 32");
+  if (blocks_per_plane < 1 || blocks_per_plane > (int64_t)1 << 30)
+    return noalloc_fail(VCA_E_ARG, "vca_reduce_frames_noalloc: blocks_per_plane must be in [1, 2^30]");
+  if (n_frames < 1 || n_frames > kNoAllocMaxFrames) {
+    snprintf(msg, sizeof msg,
+             "vca_reduce_frames_noalloc: n_frames = %d is outside [1, %d], the frames its fixed scratch holds",
+             (int)n_frames, kNoAllocMaxFrames);
+    return noalloc_fail(VCA_E_ARG, msg);
+  }
+  if (prev_H_Y == last_H_Y)
+    return noalloc_fail(VCA_E_ARG, "vca_reduce_frames_noalloc: prev_H_Y and last_H_Y must be different buffers");
+
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return noalloc_fail(VCA_E_CUDA, "vca_reduce_frames_noalloc: no usable current device");
+  }
+  void* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      e = cudaGetSymbolAddress(&g_noalloc_ptr[dev], g_noalloc_scratch);
+      if (e != cudaSuccess) {
+        g_noalloc_ptr[dev] = nullptr;
+        cudaGetLastError();
+        snprintf(msg, sizeof msg, "vca_reduce_frames_noalloc: cudaGetSymbolAddress failed: %s (%d)",
+                 cudaGetErrorString(e), (int)e);
+        return noalloc_fail(VCA_E_CUDA, msg);
+      }
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+
+  Geometry g{};
+  g.C = blocks_per_plane;
+  g.w = block_size;
+  g.nc = block_size / 2;
+  int64_t launches = 0;
+  e = launch_reduce(g, n_frames, block_values, prev_H_Y, prev_H_Y != nullptr, last_H_Y, features,
+                    static_cast<double*>(scratch),
+                    reinterpret_cast<unsigned int*>(static_cast<unsigned char*>(scratch) + kNoAllocPartialBytes),
+                    static_cast<cudaStream_t>(cuda_stream), &launches);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    snprintf(msg, sizeof msg, "vca_reduce_frames_noalloc: launch failed: %s (%d)", cudaGetErrorString(e), (int)e);
+    return noalloc_fail(VCA_E_CUDA, msg);
+  }
+  return VCA_OK;
+}

@@ -82,6 +82,7 @@ _PROTOS = {
     "vca_set_kernel_timing": (_P, _I32),
     "vca_read_kernel_timing": (_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)),
     "vca_close": (_P,),
+    "vca_reduce_frames_noalloc": (_P, _I64, _I32, _I32, _P, _P, _P, _P),
 }
 
 
@@ -127,6 +128,13 @@ def vca_block_count(cfg: VcaConfig) -> tuple[int, int]:
     bx, by = _I64(), _I64()
     _check(lib().vca_block_count(ctypes.byref(cfg), ctypes.byref(bx), ctypes.byref(by)))
     return bx.value, by.value
+
+
+def vca_reduce_frames_noalloc(block_values: int, blocks_per_plane: int, block_size: int, n_frames: int,
+                              prev_H_Y: int | None, last_H_Y: int, features: int, stream: int = 0) -> int:
+    """Frame features from device block values with no device allocation (device pointers)."""
+    return _check(lib().vca_reduce_frames_noalloc(_P(block_values), blocks_per_plane, block_size, n_frames,
+                                                  _P(prev_H_Y or 0), _P(last_H_Y), _P(features), _P(stream)))
 
 
 def vca_open(cfg: VcaConfig, stream: int = 0) -> int:
