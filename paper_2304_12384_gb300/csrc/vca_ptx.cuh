@@ -216,5 +216,17 @@ __device__ __forceinline__ uint8_t lds_u8(uint32_t saddr) {
   return (uint8_t)r;
 }
 
+// Named barrier over `count` threads that also ORs a predicate across them: every participant
+// gets true if any passed true.  Orders shared-memory accesses like bar.sync.
+__device__ __forceinline__ bool bar_or(uint32_t id, uint32_t count, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{ .reg .pred p, q; setp.ne.u32 p, %1, 0; barrier.cta.red.or.pred q, %2, %3, p; selp.u32 %0, 1, 0, q; }"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(id), "r"(count)
+      : "memory");
+  return r != 0;
+}
+
 }  // namespace ptx
 }  // namespace vca

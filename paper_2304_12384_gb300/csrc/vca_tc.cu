@@ -12,16 +12,16 @@
 //   warpgroups 4, 5  epilogue 2 (luma jobs, chroma jobs): stage-2 accumulators -> block
 //                 energies and brightness.
 // Each warpgroup has one warp per TMEM lane quarter.  Jobs flow through 8 TMEM slots (64 columns
-// each) and 3 shared-memory operand slots; every slot has a full and a free mbarrier, so the
-// three roles run concurrently on different jobs.
+// each) and, per plane type, 2 shared-memory operand slots; every slot has a full and a free
+// mbarrier, so the roles run concurrently on different jobs.
 //
 // A "job" is 128 stage-2 rows: 8 (low-pass) or 4 luma 32x32 blocks, or 16 / 8 chroma 16x16
-// blocks.  Per job, through 4 TMEM slots and 2 shared-memory slots:
+// blocks.  Per job:
 //   convert   raw u8 row -> fp16 (1024 + x, one PRMT per two samples) written to TMEM as the
-//             A operand;
-//   stage 1   D1 = X M^T (A from TMEM, M from shared memory), exact integers in FP32;
-//   epilogue1 T' = D1 + c (rounding offset, minus the encoding bias on the DC row), then
-//             T = floor(T'/2^s1) by one round-down FMA whose magic constant leaves
+//             A operand; the stage-1 accumulators pre-set to c_k (the rounding offset 2^(s1-1),
+//             minus the 1024 * 64 * N encoding bias on the DC row);
+//   stage 1   D1 = c + X M^T (A from TMEM, M from shared memory), exact integers in FP32;
+//   epilogue1 T = floor(D1/2^s1) by one round-down FMA whose magic constant leaves
 //             U = T + 32768 in the low 16 bits and 0x64 in byte 2, so two PRMTs give the
 //             fp16 pairs (1024 + U_lo8, 1024 + U_hi8); stored MN-major (128-byte swizzle)
 //             as the stage-2 A operand -- the row/column transpose is the layout -- and the
@@ -66,36 +66,24 @@ constexpr int OFF_MISC = OFF_BAR + kBars * 8;
 constexpr int kSmemBytes = OFF_MISC + 64 + 1024;  // + slack to align the base to 1024
 constexpr int kA2Slots = 4;                       // 0-1 luma jobs, 2-3 chroma jobs
 
-// TMEM layout.  Low-pass: 12 accumulator slots of 32 columns (D1, then D2 in the same columns) and
-// a separate ring of 4 stage-1 operand buffers of 32 columns, freed as soon as stage 1 completes,
-// so 12 jobs can be in flight.  Full: 8 slots of 64 columns holding A1 at [0, 32), D1 at [32, 64)
-// and then D2 at [0, 64).
-#ifndef VCA_TC_SEP_A1
-#define VCA_TC_SEP_A1 0
-#endif
-template <bool LP>
-struct Lay {
-  static constexpr bool SEP = LP && VCA_TC_SEP_A1;  // stage-1 operands in their own ring
-  static constexpr int kD = SEP ? 12 : 8;           // accumulator slots
-  static constexpr int DCols = SEP ? 32 : 64;
-  static constexpr int kA1 = SEP ? 4 : kD;          // stage-1 operand buffers
-  static constexpr int A1Base = SEP ? 384 : 0;      // first column of the operand ring
-  static constexpr int A1Stride = SEP ? 32 : 64;
-  static constexpr int D1Off = SEP ? 0 : 32;        // D1 within an accumulator slot
-  static_assert(kD * DCols + (SEP ? kA1 * A1Stride : 0) <= 512, "TMEM budget");
-};
+// TMEM layout: 8 job slots of 64 columns, each holding the stage-1 operand A1 at [0, 32), the
+// stage-1 accumulators D1 at [32, 64), and then the stage-2 accumulators D2 over [0, 32)
+// (low-pass) or [0, 64) (all coefficients) once stage 1 has consumed A1 and epilogue 1 has read
+// D1 into registers.
+constexpr int kSlots = 8;
+constexpr int kSlotCols = 64;
+constexpr int kD1Off = 32;
 
 // barrier indices
 __host__ __device__ constexpr int b_raw_full(int s) { return s; }
 __host__ __device__ constexpr int b_raw_empty(int s) { return kStages + s; }
-__host__ __device__ constexpr int b_slot_free(int s) { return 2 * kStages + s; }     // up to 12
-__host__ __device__ constexpr int b_d1(int s) { return 2 * kStages + 12 + s; }
-__host__ __device__ constexpr int b_d2(int s) { return 2 * kStages + 24 + s; }
-__host__ __device__ constexpr int b_a1_full(int s) { return 2 * kStages + 36 + s; }  // up to 8
-__host__ __device__ constexpr int b_a1_free(int s) { return 2 * kStages + 44 + s; }  // up to 4
-__host__ __device__ constexpr int b_a2_full(int s) { return 2 * kStages + 48 + s; }
-__host__ __device__ constexpr int b_a2_free(int s) { return 2 * kStages + 52 + s; }
-__host__ __device__ constexpr int b_drain(int i) { return 2 * kStages + 56 + i; }
+__host__ __device__ constexpr int b_slot_free(int s) { return 2 * kStages + s; }
+__host__ __device__ constexpr int b_d1(int s) { return 2 * kStages + kSlots + s; }
+__host__ __device__ constexpr int b_d2(int s) { return 2 * kStages + 2 * kSlots + s; }
+__host__ __device__ constexpr int b_a1_full(int s) { return 2 * kStages + 3 * kSlots + s; }
+__host__ __device__ constexpr int b_a2_full(int s) { return 2 * kStages + 4 * kSlots + s; }
+__host__ __device__ constexpr int b_a2_free(int s) { return 2 * kStages + 4 * kSlots + kA2Slots + s; }
+__host__ __device__ constexpr int b_drain(int i) { return 2 * kStages + 4 * kSlots + 2 * kA2Slots + i; }
 static_assert(b_drain(1) < kBars, "barrier area");
 
 constexpr int kThreads = 896;
@@ -111,6 +99,7 @@ struct TcParams {
   int W, H, cw, ch;
   int nbx, nby;
   int tiles_x, tiles_y;
+  float inv_tiles_x, inv_tiles_per_frame;  // 1 / tiles_x and 1 / (tiles_x * tiles_y) for tile indexing
   int nframes;
   int total_items;
   int64_t C;
@@ -132,7 +121,6 @@ struct PC {
   static constexpr int BPG2 = 128 / NK;           // blocks per job (128 stage-2 rows)
   static constexpr int G = BPG2 / BPG1;           // stage-1 groups per job
   static constexpr int JOBS = 16 / BPG2;          // jobs of this plane per tile
-  static constexpr int KS = Nb / 16;              // K = 16 steps
   static constexpr int A1COLS = Nb / 2;           // TMEM columns of one group's A operand
 };
 
@@ -181,28 +169,25 @@ __device__ __forceinline__ bool wait_bar(const Ctl& c, int idx, uint32_t parity,
   return wait_bar_slow(bar, parity, c.abort, c.err, code, ignore_abort, sleep);
 }
 
-// Stage-1 operand conversion for one stage-1 group: this thread's row of 2 * A1COLS samples.
+// Stage-1 operand conversion: 16 samples of this thread's row starting at column x (of the raw
+// tile, edge columns repeated past w_rem) -> 8 words of fp16 pairs (1024 + sample) at TMEM taddr.
 template <int Nb>
-__device__ __forceinline__ void load_row_fp16(const uint8_t* raw, int y, int x, int w_rem, uint32_t (&out)[Nb / 2]) {
+__device__ __forceinline__ void convert_16(uint32_t base, int y, int x, int w_rem, uint32_t taddr) {
   constexpr int kRow = Nb == 32 ? 128 : 64;  // raw tile row pitch in bytes
-  uint32_t words[Nb / 4];
-  const uint32_t base = smem_u32(raw);
-  if (x + Nb <= w_rem) {
-#pragma unroll
-    for (int c = 0; c < Nb / 16; ++c) {
-      const int chunk = (x >> 4) + c;
-      const int sw = Nb == 32 ? (chunk ^ (y & 7)) : (chunk ^ ((y >> 1) & 3));
-      const uint4 q = lds128(base + y * kRow + (sw << 4));
-      words[4 * c + 0] = q.x;
-      words[4 * c + 1] = q.y;
-      words[4 * c + 2] = q.z;
-      words[4 * c + 3] = q.w;
-    }
+  uint32_t words[4];
+  if (x + 16 <= w_rem) {
+    const int chunk = x >> 4;
+    const int sw = Nb == 32 ? (chunk ^ (y & 7)) : (chunk ^ ((y >> 1) & 3));
+    const uint4 q = lds128(base + y * kRow + (sw << 4));
+    words[0] = q.x;
+    words[1] = q.y;
+    words[2] = q.z;
+    words[3] = q.w;
   } else {
 #pragma unroll
-    for (int i = 0; i < Nb / 4; ++i) words[i] = 0;
+    for (int i = 0; i < 4; ++i) words[i] = 0;
 #pragma unroll
-    for (int c = 0; c < Nb; ++c) {
+    for (int c = 0; c < 16; ++c) {
       const int xx = min(x + c, w_rem - 1);
       const int chunk = xx >> 4;
       const int sw = Nb == 32 ? (chunk ^ (y & 7)) : (chunk ^ ((y >> 1) & 3));
@@ -210,11 +195,13 @@ __device__ __forceinline__ void load_row_fp16(const uint8_t* raw, int y, int x, 
       words[c >> 2] |= b << (8 * (c & 3));
     }
   }
+  uint32_t out[8];
 #pragma unroll
-  for (int i = 0; i < Nb / 4; ++i) {
+  for (int i = 0; i < 4; ++i) {
     out[2 * i] = prmt(words[i], kSel6464, 0x5140);
     out[2 * i + 1] = prmt(words[i], kSel6464, 0x5342);
   }
+  tmem_st<8>(taddr, out);
 }
 
 template <int N>
@@ -272,10 +259,14 @@ __device__ __forceinline__ uint32_t a2_addr(uint32_t sbase, int a2) {
 
 // ---- worker phases ----------------------------------------------------------
 
+// Writes the job's stage-1 A operand at ta1 and pre-sets its stage-1 accumulators at td1 to c0
+// (DC column) and c (the others), so that stage 1 leaves T' = c_k + sum in D1.
 template <int Nb, bool LP>
 __device__ __forceinline__ void convert_job(const uint8_t* raw_plane, int jp, int h_rem, int w_rem, uint32_t ta1,
-                                            int q, int lane) {
+                                            uint32_t td1, float c0, float c, int q, int lane) {
   using P = PC<Nb, LP>;
+#pragma unroll
+  for (int g = 0; g < P::G; ++g) fill_cols<P::N1>(td1 + g * P::N1, c0, c);
   const int l = 32 * q + lane;
   const int bg = l / Nb;
   const int r = l % Nb;
@@ -285,9 +276,8 @@ __device__ __forceinline__ void convert_job(const uint8_t* raw_plane, int jp, in
     int y = (idx >> 2) * Nb + r;
     if (y >= h_rem) y = h_rem - 1;
     const int x = (idx & 3) * Nb;
-    uint32_t a[Nb / 2];
-    load_row_fp16<Nb>(raw_plane, y, x, w_rem, a);
-    tmem_st<Nb / 2>(ta1 + g * P::A1COLS, a);
+#pragma unroll
+    for (int c = 0; c < Nb / 16; ++c) convert_16<Nb>(smem_u32(raw_plane), y, x + 16 * c, w_rem, ta1 + g * P::A1COLS + 8 * c);
   }
 }
 
@@ -295,7 +285,7 @@ __device__ __forceinline__ void convert_job(const uint8_t* raw_plane, int jp, in
 // pre-sets the stage-2 accumulators at td2 (hi) and td2 + N1 (lo), which may overlap D1.
 template <int Nb, bool LP>
 __device__ __forceinline__ void epilogue1(uint32_t td1, uint32_t td2, uint32_t a2hi, uint32_t a2lo, int q, int lane,
-                                          float s1inv, float c0, float c, float hi0, float lo) {
+                                          float s1inv, float hi0, float lo) {
   using P = PC<Nb, LP>;
   constexpr int NK = P::NK;
   const int l = 32 * q + lane;
@@ -313,11 +303,9 @@ __device__ __forceinline__ void epilogue1(uint32_t td1, uint32_t td2, uint32_t a
     uint32_t hi[NK / 2], lw[NK / 2];
 #pragma unroll
     for (int k = 0; k < NK; k += 2) {
-      // T' = D1 + c_k (rounding offset 2^(s1-1), minus the sample-encoding bias on the DC row): exact.
-      const float ta = __uint_as_float(acc[g][k]) + (k == 0 ? c0 : c);
-      const float tb = __uint_as_float(acc[g][k + 1]) + c;
-      const uint32_t za = __float_as_uint(__fmaf_rd(ta, s1inv, kT1));
-      const uint32_t zb = __float_as_uint(__fmaf_rd(tb, s1inv, kT1));
+      // D1 already holds T' = c_k + sum (the accumulators were pre-set), an exact integer.
+      const uint32_t za = __float_as_uint(__fmaf_rd(__uint_as_float(acc[g][k]), s1inv, kT1));
+      const uint32_t zb = __float_as_uint(__fmaf_rd(__uint_as_float(acc[g][k + 1]), s1inv, kT1));
       lw[k / 2] = prmt(za, zb, 0x6420);
       hi[k / 2] = prmt(za, zb, 0x6521);
     }
@@ -385,59 +373,82 @@ struct TileInfo {
   int f, tx, ty, stage, t;
 };
 
+// a / b for 0 <= a < 2^24, b >= 1, from a float estimate that is off by at most one.
+__device__ __forceinline__ int div_small(int a, int b, float binv) {
+  int qt = __float2int_rz((float)a * binv);
+  const int r = a - qt * b;
+  qt += (r >= b) - (r < 0);
+  return qt;
+}
+
 __device__ __forceinline__ TileInfo tile_info(const TcParams& p, int t, int cta, int grid, int tiles_per_frame) {
   TileInfo ti;
   const int item = cta + t * grid;
   ti.t = t;
-  ti.f = item / tiles_per_frame;
+  ti.f = div_small(item, tiles_per_frame, p.inv_tiles_per_frame);
   const int r = item - ti.f * tiles_per_frame;
-  ti.tx = r % p.tiles_x;
-  ti.ty = r / p.tiles_x;
+  ti.ty = div_small(r, p.tiles_x, p.inv_tiles_x);
+  ti.tx = r - ti.ty * p.tiles_x;
   ti.stage = t % kStages;
   return ti;
 }
 
 // ---- role loops (one instantiation per plane type) -------------------------------
+//
+// Jobs are numbered jj = t * JPT + r (tile t of this CTA, r < JPT): luma jobs first, then U,
+// then V.  Job jj lives in TMEM slot jj % kSlots; each role visits only its plane type's jobs.
 
-// Convert: raw samples of the tile -> stage-1 A operand in TMEM, for every job of one plane type.
 template <int Nb, bool LP>
-__device__ void convert_loop(const TcParams& p, const Ctl& ctl, uint8_t* sm, uint32_t tq, int n_jobs, int cta,
+__device__ __forceinline__ void plane_jobs(int& r0, int& r1) {
+  constexpr int JL = PC<32, LP>::JOBS;
+  r0 = Nb == 32 ? 0 : JL;
+  r1 = Nb == 32 ? JL : Jobs<LP>::PER_TILE;
+}
+
+// Convert: raw samples of the tile -> stage-1 A operand in TMEM (and the D1 presets).
+template <int Nb, bool LP>
+__device__ void convert_loop(const TcParams& p, const Ctl& ctl, uint8_t* sm, uint32_t tq, int n_items, int cta,
                              int grid, int tiles_per_frame, int q, int lane) {
-  using Y = Lay<LP>;
   constexpr int JPT = Jobs<LP>::PER_TILE;
   constexpr int T = 4 * Nb;  // tile edge of this plane in samples
   const int pw = Nb == 32 ? p.W : p.cw, ph = Nb == 32 ? p.H : p.ch;
-  const int last_of_plane = Nb == 32 ? PC<32, LP>::JOBS - 1 : JPT - 1;
+  const float c0 = Nb == 32 ? 8.0f - 2097152.0f : 4.0f - 1048576.0f;  // 2^(s1-1) - 1024 * 64 * N
+  const float c = Nb == 32 ? 8.0f : 4.0f;                             // 2^(s1-1)
+  int r0, r1;
+  plane_jobs<Nb, LP>(r0, r1);
+  const int per_tile = r1 - r0;
   TileInfo ti{};
-  int h_rem = 0, w_rem = 0, last_tile = -1;
-  for (int jj = 0; jj < n_jobs; ++jj) {
-    const int j = jj % JPT;
-    int plane, jp;
-    plane_of<LP>(j, plane, jp);
-    if ((plane == 0) != (Nb == 32)) continue;
-    const int t = jj / JPT;
-    if (t != last_tile) {
+  int h_rem = 0, w_rem = 0;
+  const int n = n_items * per_tile;
+  for (int k = 0, t = 0, r = r0; k < n; ++k) {
+    if (r == r0) {
       ti = tile_info(p, t, cta, grid, tiles_per_frame);
       h_rem = ph - ti.ty * T;
       w_rem = pw - ti.tx * T;
-      last_tile = t;
-      if (!wait_bar(ctl, b_raw_full(ti.stage), (t / kStages) & 1, 4)) break;
+      if (!wait_bar(ctl, b_raw_full(ti.stage), (t / kStages) & 1, 4)) return;
     }
-    const int buf = jj % Y::kA1;
-    if (Y::SEP) {
-      if (jj >= Y::kA1 && !wait_bar(ctl, b_a1_free(buf), ((jj / Y::kA1) - 1) & 1, 4)) break;
-    } else {
-      if (jj >= Y::kD && !wait_bar(ctl, b_slot_free(buf), ((jj / Y::kD) - 1) & 1, 4)) break;
-    }
+    const int jj = t * JPT + r;
+    int plane, jp;
+    plane_of<LP>(r, plane, jp);
+    const int slot = jj % kSlots;
+    if (jj >= kSlots && !wait_bar(ctl, b_slot_free(slot), ((jj / kSlots) - 1) & 1, 4)) return;
     tc_fence_after();
     const uint8_t* raw = sm + OFF_RAW + ti.stage * kStageBytes + (plane == 0 ? 0 : kRawY + (plane - 1) * kRawC);
-    convert_job<Nb, LP>(raw, jp, h_rem, w_rem, tq + Y::A1Base + buf * Y::A1Stride, q, lane);
+    const uint32_t ta = tq + slot * kSlotCols;
+    convert_job<Nb, LP>(raw, jp, h_rem, w_rem, ta, ta + kD1Off, c0, c, q, lane);
     tmem_wait_st();
     tc_fence_before();
     __syncwarp();
+    const bool last = r == r1 - 1;
     if (lane == 0) {
-      mbar_arrive(&ctl.bars[b_a1_full(buf)]);
-      if (j == last_of_plane) mbar_arrive(&ctl.bars[b_raw_empty(ti.stage)]);
+      mbar_arrive(&ctl.bars[b_a1_full(slot)]);
+      if (last) mbar_arrive(&ctl.bars[b_raw_empty(ti.stage)]);
+    }
+    if (last) {
+      r = r0;
+      ++t;
+    } else {
+      ++r;
     }
   }
 }
@@ -445,45 +456,47 @@ __device__ void convert_loop(const TcParams& p, const Ctl& ctl, uint8_t* sm, uin
 // Epilogue 1: T = floor(T'/2^s1) into the stage-2 operand (hi and lo bytes as fp16, MN-major), and
 // the stage-2 accumulators pre-set: hi starts at K1 - 1156 * 64 * N for u = 0 (the 1024 + byte
 // encoding of both halves) and K1 otherwise, lo at 2^(s2-1) (luma N = 32: s1 = 4, s2 = 11; chroma
-// N = 16: s1 = 3, s2 = 10).
+// N = 16: s1 = 3, s2 = 10).  Each plane type cycles through its own two stage-2 operand slots, so
+// every slot's full / free barriers see one in-order stream of jobs.
 template <int Nb, bool LP>
-__device__ void epi1_loop(const Ctl& ctl, uint32_t sbase, uint32_t tq, int n_jobs, int q, int lane) {
-  using Y = Lay<LP>;
+__device__ void epi1_loop(const Ctl& ctl, uint32_t sbase, uint32_t tq, int n_items, int q, int lane) {
   constexpr int JPT = Jobs<LP>::PER_TILE;
   const float s1inv = Nb == 32 ? 0.0625f : 0.125f;
-  // D1 + c_k: 2^(s1-1), minus the 1024 * 64 * N bias of the 1024 + x sample encoding on the DC row.
-  const float c0 = Nb == 32 ? 8.0f - 2097152.0f : 4.0f - 1048576.0f;
-  const float c = Nb == 32 ? 8.0f : 4.0f;
   const float hi0 = Nb == 32 ? kK1 - 2367488.0f : kK1 - 1183744.0f;
   const float lo = Nb == 32 ? 1024.0f : 512.0f;
   const uint32_t lo_off = Nb == 32 ? kA2L : kA2C;
-  for (int jj = 0; jj < n_jobs; ++jj) {
-    int plane, jp;
-    plane_of<LP>(jj % JPT, plane, jp);
-    if ((plane == 0) != (Nb == 32)) continue;
-    const int slot = jj % Y::kD;
-    int a2, use;
-    a2_slot_of<LP>(jj, a2, use);
-    if (!wait_bar(ctl, b_d1(slot), (jj / Y::kD) & 1, 4, false, true)) break;
-    if (use >= 1 && !wait_bar(ctl, b_a2_free(a2), (use - 1) & 1, 4, false, true)) break;
+  const uint32_t a2base = Nb == 32 ? sbase + OFF_A2 : sbase + OFF_A2C;
+  const int a2first = Nb == 32 ? 0 : 2;
+  int r0, r1;
+  plane_jobs<Nb, LP>(r0, r1);
+  const int n = n_items * (r1 - r0);
+  for (int use = 0, t = 0, r = r0; use < n; ++use) {  // use: jobs of this plane type so far
+    const int jj = t * JPT + r;
+    const int slot = jj % kSlots;
+    const int a2 = use & 1;
+    if (!wait_bar(ctl, b_d1(slot), (jj / kSlots) & 1, 4, false, true)) return;
+    if (use >= 2 && !wait_bar(ctl, b_a2_free(a2first + a2), ((use >> 1) - 1) & 1, 4, false, true)) return;
     tc_fence_after();
-    const uint32_t ahi = a2_addr(sbase, a2);
-    const uint32_t td = tq + slot * Y::DCols;
-    epilogue1<Nb, LP>(td + Y::D1Off, td, ahi, ahi + lo_off, q, lane, s1inv, c0, c, hi0, lo);
+    const uint32_t ahi = a2base + a2 * 2 * lo_off;
+    const uint32_t td = tq + slot * kSlotCols;
+    epilogue1<Nb, LP>(td + kD1Off, td, ahi, ahi + lo_off, q, lane, s1inv, hi0, lo);
     tmem_wait_st();
     fence_proxy_async_smem();
     tc_fence_before();
     __syncwarp();
-    if (lane == 0) mbar_arrive(&ctl.bars[b_a2_full(a2)]);
+    if (lane == 0) mbar_arrive(&ctl.bars[b_a2_full(a2first + a2)]);
+    if (++r == r1) {
+      r = r0;
+      ++t;
+    }
   }
 }
 
 // Epilogue 2: Z, the block energy H and brightness L, for every job of one plane type.
 template <int Nb, bool LP, bool DUMP>
-__device__ void epi2_loop(const TcParams& p, const Ctl& ctl, uint32_t tq, int n_jobs, int cta, int grid,
+__device__ void epi2_loop(const TcParams& p, const Ctl& ctl, uint32_t tq, int n_items, int cta, int grid,
                           int tiles_per_frame, int q, int lane) {
   using P = PC<Nb, LP>;
-  using Y = Lay<LP>;
   constexpr int JPT = Jobs<LP>::PER_TILE;
   const float* Wt = Nb == 32 ? p.W_y : p.W_c;
   float w[P::NK];
@@ -491,25 +504,27 @@ __device__ void epi2_loop(const TcParams& p, const Ctl& ctl, uint32_t tq, int n_
   for (int u = 0; u < P::NK; ++u) w[u] = Wt[u * Nb + (lane % P::NK)];
   const float einv = Nb == 32 ? 0.125f : 0.25f;
   const float c2 = Nb == 32 ? kK1 - kK1 / 8.0f : kK1 - kK1 / 4.0f;
-  TileInfo ti{};
-  int last_tile = -1;
-  for (int jj = 0; jj < n_jobs; ++jj) {
-    const int j = jj % JPT;
-    JobCtx jc;
-    plane_of<LP>(j, jc.plane, jc.jp);
-    if ((jc.plane == 0) != (Nb == 32)) continue;
-    const int t = jj / JPT;
-    if (t != last_tile) {
-      ti = tile_info(p, t, cta, grid, tiles_per_frame);
-      last_tile = t;
+  int r0, r1;
+  plane_jobs<Nb, LP>(r0, r1);
+  const int n = n_items * (r1 - r0);
+  JobCtx jc{};
+  for (int k = 0, t = 0, r = r0; k < n; ++k) {
+    if (r == r0) {
+      const TileInfo ti = tile_info(p, t, cta, grid, tiles_per_frame);
+      jc.f = ti.f;
+      jc.tx = ti.tx;
+      jc.ty = ti.ty;
     }
-    const int slot = jj % Y::kD;
-    if (!wait_bar(ctl, b_d2(slot), (jj / Y::kD) & 1, 4, false, true)) break;
+    const int jj = t * JPT + r;
+    const int slot = jj % kSlots;
+    plane_of<LP>(r, jc.plane, jc.jp);
+    if (!wait_bar(ctl, b_d2(slot), (jj / kSlots) & 1, 4, false, true)) return;
     tc_fence_after();
-    jc.f = ti.f;
-    jc.tx = ti.tx;
-    jc.ty = ti.ty;
-    epilogue2<Nb, LP, DUMP>(p, tq + slot * Y::DCols, jc, q, lane, w, einv, c2, &ctl.bars[b_slot_free(slot)]);
+    epilogue2<Nb, LP, DUMP>(p, tq + slot * kSlotCols, jc, q, lane, w, einv, c2, &ctl.bars[b_slot_free(slot)]);
+    if (++r == r1) {
+      r = r0;
+      ++t;
+    }
   }
 }
 
@@ -519,9 +534,8 @@ __global__ void __launch_bounds__(kThreads, 1)
               const __grid_constant__ CUtensorMap mapV, const TcParams p) {
   using L = PC<32, LP>;
   using Cc = PC<16, LP>;
-  using Y = Lay<LP>;
   constexpr int JPT = Jobs<LP>::PER_TILE;
-  static_assert(Y::kD % JPT == 0 && Y::kA1 % JPT == 0, "a TMEM slot must always hold the same plane type");
+  static_assert(kSlots % JPT == 0, "a TMEM slot must always hold the same plane type");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(sm + OFF_BAR);
@@ -554,8 +568,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (tid == 0) {
     for (int i = 0; i < kBars; ++i) mbar_init(&bars[i], 1);
     for (int i = 0; i < kStages; ++i) mbar_init(&bars[b_raw_empty(i)], 8);  // both convert warpgroups
-    for (int i = 0; i < Y::kD; ++i) mbar_init(&bars[b_slot_free(i)], 4);
-    for (int i = 0; i < Y::kA1; ++i) mbar_init(&bars[b_a1_full(i)], 4);
+    for (int i = 0; i < kSlots; ++i) mbar_init(&bars[b_slot_free(i)], 4);
+    for (int i = 0; i < kSlots; ++i) mbar_init(&bars[b_a1_full(i)], 4);
     for (int i = 0; i < kA2Slots; ++i) mbar_init(&bars[b_a2_full(i)], 4);
     *abort_flag = 0;
     fence_mbar_init();
@@ -598,40 +612,34 @@ __global__ void __launch_bounds__(kThreads, 1)
           wait_bar(ctl, b_raw_full(t % kStages), (t / kStages) & 1, 1, true);
       }
     } else if (warp == 1 && lane == 0) {
-      // ---------------- stage-1 MMA issuer: D1 = A1 (TMEM) x M^T ----------------
+      // ---------------- stage-1 MMA issuer: D1 += A1 (TMEM) x M^T (D1 pre-set by convert) ----------------
       const uint32_t bl = sbase + OFF_BL, bc = sbase + OFF_BC;
       constexpr uint32_t idL = idesc_f16(128, L::N1, 0, 0), idC = idesc_f16(128, Cc::N1, 0, 0);
       bool ok = true;
       for (int j = 0; j < n_jobs; ++j) {
         int plane, jp;
         plane_of<LP>(j % JPT, plane, jp);
-        const int buf = j % Y::kA1;
-        const int slot = j % Y::kD;
-        if (!wait_bar(ctl, b_a1_full(buf), (j / Y::kA1) & 1, 2)) {
-          ok = false;
-          break;
-        }
-        if (Y::SEP && j >= Y::kD && !wait_bar(ctl, b_slot_free(slot), ((j / Y::kD) - 1) & 1, 2)) {
+        const int slot = j % kSlots;
+        if (!wait_bar(ctl, b_a1_full(slot), (j / kSlots) & 1, 2)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        const uint32_t d = tmem + slot * Y::DCols + Y::D1Off;
-        const uint32_t a = tmem + Y::A1Base + buf * Y::A1Stride;
+        const uint32_t a = tmem + slot * kSlotCols;
+        const uint32_t d = a + kD1Off;
         if (plane == 0) {
           // K-step outer: consecutive MMAs write different accumulators.
 #pragma unroll
-          for (int ks = 0; ks < L::KS; ++ks)
+          for (int ks = 0; ks < 2; ++ks)
 #pragma unroll
             for (int gg = 0; gg < L::G; ++gg)
-              mma_ts(d + gg * L::N1, a + gg * L::A1COLS + ks * 8, smem_desc(bl + ks * 256, 128, 512, 0), idL, ks > 0);
+              mma_ts(d + gg * L::N1, a + gg * L::A1COLS + ks * 8, smem_desc(bl + ks * 256, 128, 512, 0), idL, 1);
         } else {
 #pragma unroll
           for (int gg = 0; gg < Cc::G; ++gg)
-            mma_ts(d + gg * Cc::N1, a + gg * Cc::A1COLS, smem_desc(bc, 128, 256, 0), idC, 0);
+            mma_ts(d + gg * Cc::N1, a + gg * Cc::A1COLS, smem_desc(bc, 128, 256, 0), idC, 1);
         }
         mma_commit(&bars[b_d1(slot)]);
-        if (Y::SEP) mma_commit(&bars[b_a1_free(buf)]);
       }
       if (!ok) {
         mma_commit(&bars[b_drain(0)]);
@@ -652,11 +660,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t d = tmem + (j % Y::kD) * Y::DCols;
+        const uint32_t d = tmem + (j % kSlots) * kSlotCols;
         const uint32_t ahi = a2_addr(sbase, a2);
         if (plane == 0) {
 #pragma unroll
-          for (int ks = 0; ks < L::KS; ++ks) {
+          for (int ks = 0; ks < 2; ++ks) {
             const uint64_t b = smem_desc(bl + ks * 256, 128, 512, 0);
             mma_ss(d, smem_desc(ahi + ks * 4096, 1024, 2048, 2), b, id2L, 1);
             mma_ss(d + L::N1, smem_desc(ahi + kA2L + ks * 4096, 1024, 2048, 2), b, id2L, 1);
@@ -666,7 +674,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           mma_ss(d, smem_desc(ahi, 1024, 2048, 2), b, id2C, 1);
           mma_ss(d + Cc::N1, smem_desc(ahi + kA2C, 1024, 2048, 2), b, id2C, 1);
         }
-        mma_commit(&bars[b_d2(j % Y::kD)]);
+        mma_commit(&bars[b_d2(j % kSlots)]);
         mma_commit(&bars[b_a2_free(a2)]);
       }
       if (!ok) {
@@ -675,17 +683,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else if (role == 1) {
-    convert_loop<32, LP>(p, ctl, sm, tmem + lanebase, n_jobs, cta, grid, tiles_per_frame, q, lane);
+    convert_loop<32, LP>(p, ctl, sm, tmem + lanebase, n_items, cta, grid, tiles_per_frame, q, lane);
   } else if (role == 6) {
-    convert_loop<16, LP>(p, ctl, sm, tmem + lanebase, n_jobs, cta, grid, tiles_per_frame, q, lane);
+    convert_loop<16, LP>(p, ctl, sm, tmem + lanebase, n_items, cta, grid, tiles_per_frame, q, lane);
   } else if (role == 2) {
-    epi1_loop<32, LP>(ctl, sbase, tmem + lanebase, n_jobs, q, lane);
+    epi1_loop<32, LP>(ctl, sbase, tmem + lanebase, n_items, q, lane);
   } else if (role == 3) {
-    epi1_loop<16, LP>(ctl, sbase, tmem + lanebase, n_jobs, q, lane);
+    epi1_loop<16, LP>(ctl, sbase, tmem + lanebase, n_items, q, lane);
   } else if (role == 4) {
-    epi2_loop<32, LP, DUMP>(p, ctl, tmem + lanebase, n_jobs, cta, grid, tiles_per_frame, q, lane);
+    epi2_loop<32, LP, DUMP>(p, ctl, tmem + lanebase, n_items, cta, grid, tiles_per_frame, q, lane);
   } else {
-    epi2_loop<16, LP, DUMP>(p, ctl, tmem + lanebase, n_jobs, cta, grid, tiles_per_frame, q, lane);
+    epi2_loop<16, LP, DUMP>(p, ctl, tmem + lanebase, n_items, cta, grid, tiles_per_frame, q, lane);
   }
 
   tc_fence_before();
@@ -774,6 +782,8 @@ cudaError_t launch_tc(const Geometry& g, const FramePlanes& fp, int nframes, con
   p.nby = g.nby;
   p.tiles_x = (g.nbx + 3) / 4;
   p.tiles_y = (g.nby + 3) / 4;
+  p.inv_tiles_x = 1.0f / (float)p.tiles_x;
+  p.inv_tiles_per_frame = 1.0f / (float)(p.tiles_x * p.tiles_y);
   p.nframes = nframes;
   p.total_items = p.tiles_x * p.tiles_y * nframes;
   p.C = g.C;
