@@ -398,6 +398,8 @@ def run_extras(args, an, y, u, v, frames, stream, kern, lp, device):
         a2.close()
     out["variants"] = variants
 
+    out["ladder"] = run_ladder(args, stream)
+
     # CPU oracle on the host cores, bounded sample of the same workload.
     cfg = Config(W, H, 8, args.block_size, lp)
     fps, n = oracle_fps(frames[:2], cfg, args.cpu_seconds)
@@ -405,6 +407,73 @@ def run_extras(args, an, y, u, v, frames, stream, kern, lp, device):
                            "sample": f"{n} frames of the same 3840x2160 workload through the FP64/int64 oracle "
                                      f"(numpy, one process, single-threaded integer matmul)"}
     return out
+
+
+def run_ladder(args, stream, distinct=2, ticks=20):
+    """24-channel ladder tick (4 channels at each of 640x360 .. 3840x2160, half 10-bit, block 32,
+    low-pass): the batched path (one graph per tick: two kernels for all channels) against one
+    push per channel per tick through the single-analyzer path."""
+    import numpy as np
+    import torch
+
+    from paper_2304_12384_gb300 import vca
+    from synth import frames_list, ladder_specs, pack_planes
+
+    specs = ladder_specs(4, n_frames=distinct)
+    dev = []
+    tick_bytes = 0
+    for sp in specs:
+        pk = pack_planes(frames_list(sp, 0, distinct))
+        planes = []
+        for k in ("y", "u", "v"):
+            a = pk[k]
+            if a.dtype == np.uint16:
+                a = a.view(np.int16)
+            planes.append(torch.from_numpy(np.ascontiguousarray(a)).cuda())
+        dev.append(planes)
+        tick_bytes += sp.width * sp.height * 3 // 2 * (2 if sp.bit_depth > 8 else 1)
+    torch.cuda.synchronize()
+    ans = [vca.Analyzer(sp.width, sp.height, sp.bit_depth, 32, True, max_batch=1, stream=stream.cuda_stream)
+           for sp in specs]
+
+    def refs(t):
+        return [(y[t % distinct], u[t % distinct], v[t % distinct]) for (y, u, v) in dev]
+
+    batch = vca.Batch(ans)
+    for t in range(3):
+        batch.tick(refs(t))
+    batch.sync()
+    t0 = time.perf_counter()
+    for t in range(ticks):
+        batch.tick(refs(t))
+    batch.sync()
+    el_b = time.perf_counter() - t0
+    launches = batch.launches()
+    batch.close()
+
+    for t in range(3):
+        for a, r in zip(ans, refs(t)):
+            a.push(*r)
+    for a in ans:
+        a.sync()
+    t0 = time.perf_counter()
+    for t in range(ticks):
+        for a, r in zip(ans, refs(t)):
+            a.push(*r)
+    for a in ans:
+        vca.vca_read_frame_features(a.handle, a.frames_pushed - 1, 1)
+    el_s = time.perf_counter() - t0
+    for a in ans:
+        a.close()
+    peak = load_peaks()[0]
+    tb = ticks / el_b
+    return {"channels": len(specs), "tick_bytes": tick_bytes, "ticks": ticks,
+            "batched_ticks_per_s": tb, "batched_gbs": tb * tick_bytes / 1e9,
+            "batched_hbm_frac_of_measured": tb * tick_bytes / 1e9 / peak,
+            "batched_launches_per_tick": launches / (ticks + 3),
+            "per_channel_push_ticks_per_s": ticks / el_s,
+            "hbm_roofline_ticks_per_s": peak * 1e9 / tick_bytes,
+            "timing": "host wall clock around queued ticks, synchronized at both ends; frames device-resident"}
 
 
 def main():

@@ -167,6 +167,49 @@ vca_status vca_kernel_in_use(vca_analyzer* a, int32_t* kernel);
 /* Free the analyzer (waits for its device work). NULL is accepted. */
 vca_status vca_close(vca_analyzer* a);
 
+/* ---- Batched multi-stream ticks --------------------------------------------------------
+ *
+ * A batch ticks many analyzers (channels) together: each tick analyses one frame per analyzer
+ * with one launch of the batched CUDA-core block kernel (Section 2 of the paper: integer DCT,
+ * texture energy and brightness of every block of every channel) and one launch of the batched
+ * frame reduction, replayed from a CUDA graph.  The analyzers may differ in frame size and bit
+ * depth; they must share device, block size and low_pass.  Features arrive in each analyzer as
+ * if its frames had been pushed one at a time: read them with vca_read_frame_features /
+ * vca_read_sequence_features, and the h state carries across ticks and across the batch's
+ * destruction.  While in a batch an analyzer accepts no vca_push_frame(s),
+ * vca_dump_coefficients or vca_import_state (VCA_E_STATE) and cannot be closed. */
+typedef struct vca_batch vca_batch;
+
+/* One channel's frame of a tick: device planes (16-byte aligned, pitches multiples of 16 bytes),
+ * or y = NULL to skip the channel this tick. */
+typedef struct {
+  const void* y;
+  const void* u;
+  const void* v;
+  int64_t pitch_y;
+  int64_t pitch_uv;
+} vca_frame_ref;
+
+/* Groups n analyzers (1 .. 65535, distinct, none already in a batch).  Waits for the analyzers'
+ * earlier work, builds the CTA map and captures two tick graphs on a stream of its own.
+ * VCA_E_ARG for mismatched devices, block sizes or low_pass. */
+vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch** out);
+
+/* One tick: frames[i] (n entries, in the order of vca_batch_create) for analyzer i.  Returns
+ * after queuing the tick (at most two ticks are in flight; the third waits for the first).
+ * The frame buffers must stay valid until the tick's features are read or vca_batch_sync
+ * returns.  A bad frame reference gives VCA_E_ARG and queues nothing. */
+vca_status vca_batch_tick(vca_batch* b, const vca_frame_ref* frames);
+
+/* Waits for every queued tick and delivers its features to the analyzers. */
+vca_status vca_batch_sync(vca_batch* b);
+
+/* Kernel launches issued by the batch's ticks (two per tick). */
+vca_status vca_batch_launch_count(vca_batch* b, int64_t* launches);
+
+/* Waits for the batch's ticks and dissolves it; the analyzers stay open.  NULL is accepted. */
+vca_status vca_batch_destroy(vca_batch* b);
+
 /* Frame features from per-block values already on the device, without allocating any device
  * memory.  The paper has no counterpart: this is a runtime convenience for callers that must not
  * call the CUDA allocator on their hot path (a serving loop that has budgeted all device memory

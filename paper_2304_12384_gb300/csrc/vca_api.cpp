@@ -77,6 +77,7 @@ struct StateHeader {
 }  // namespace
 
 struct vca_analyzer {
+  vca_batch* batch = nullptr;  // the batch this analyzer belongs to, if any
   vca_config cfg{};
   Geometry g{};
   int kernel = VCA_KERNEL_PLAIN;
@@ -124,6 +125,45 @@ struct vca_analyzer {
   double seq_sum[7] = {0, 0, 0, 0, 0, 0, 0};
   int64_t seq_n = 0;
   int64_t seq_nh = 0;
+};
+
+// A batch of analyzers ticked together: one frame each per tick, analysed by one launch of the
+// batched plain kernel and one launch of the batched reduction, replayed from a CUDA graph.  The
+// per-tick arguments live in pinned host memory that a copy node of the graph uploads, so the
+// graph never changes; two graphs alternate so that a tick's arguments can be written while the
+// previous tick runs.
+struct vca_batch {
+  std::vector<vca_analyzer*> m;
+  int n = 0;
+  int device = 0;
+  int w = 32;
+  bool low_pass = false;
+  cudaStream_t stream = nullptr;
+  vca::BatchCta* d_map = nullptr;
+  int n_cta = 0;
+  size_t ma_bytes = 0, desc_bytes = 0;
+  uint8_t* d_desc = nullptr;       // BatchMemberArgs[n] | ReduceArgs[n]
+  uint8_t* h_desc[2] = {nullptr, nullptr};
+  double* d_feats = nullptr;       // n x FEAT_STRIDE
+  double* h_feats[2] = {nullptr, nullptr};
+  double* d_partials = nullptr;
+  unsigned int* d_counters = nullptr;
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  struct Member {
+    int index;
+    int64_t frame;
+    bool has_prev;
+  };
+  struct Tick {
+    int k;
+    std::vector<Member> members;
+  };
+  std::deque<Tick> pending;
+  int next_k = 0;
+  int64_t ticks = 0;
+  int64_t launches = 0;
 };
 
 namespace {
@@ -296,6 +336,138 @@ cudaError_t run_analysis(vca_analyzer* a, const FramePlanes& fp, int n, float* b
   return vca::launch_plain(a->g, fp, n, a->tables, blockvals, zdump, a->stream, &a->launches);
 }
 
+
+// ---- batches ----------------------------------------------------------------------------
+
+// Delivers the features of the oldest tick in flight to its analyzers.
+vca_status batch_harvest_front(vca_batch* b, bool blocking) {
+  const vca_batch::Tick t = b->pending.front();
+  if (blocking) {
+    VCA_CUDA(cudaEventSynchronize(b->ev[t.k]), "waiting for a batch tick");
+  } else {
+    cudaError_t q = cudaEventQuery(b->ev[t.k]);
+    if (q == cudaErrorNotReady) return fail(VCA_E_AGAIN, "frame features not ready yet");
+    if (q != cudaSuccess) return cuda_fail(q, "querying a batch tick");
+  }
+  for (const auto& mm : t.members) {
+    vca_analyzer* a = b->m[mm.index];
+    const double* f = b->h_feats[t.k] + (size_t)mm.index * vca::FEAT_STRIDE;
+    vca_frame_features ff;
+    ff.frame = mm.frame;
+    ff.E_Y = f[0];
+    ff.h = f[1];
+    ff.L_Y = f[2];
+    ff.E_U = f[3];
+    ff.E_V = f[4];
+    ff.L_U = f[5];
+    ff.L_V = f[6];
+    a->done.push_back(ff);
+    const double v[7] = {ff.E_Y, ff.h, ff.L_Y, ff.E_U, ff.E_V, ff.L_U, ff.L_V};
+    for (int j = 0; j < 7; ++j) a->seq_sum[j] += v[j];
+    a->seq_n += 1;
+    if (mm.has_prev) a->seq_nh += 1;
+  }
+  b->pending.pop_front();
+  return VCA_OK;
+}
+
+vca_status batch_harvest_all(vca_batch* b) {
+  while (!b->pending.empty()) {
+    vca_status s = batch_harvest_front(b, true);
+    if (s != VCA_OK) return s;
+  }
+  return VCA_OK;
+}
+
+// Brings an analyzer's results up to date: its own pushes, then its batch's ticks.
+vca_status catch_up_all(vca_analyzer* a) {
+  vca_status s = harvest_all(a);
+  if (s == VCA_OK && a->batch) s = batch_harvest_all(a->batch);
+  return s;
+}
+
+void destroy_batch(vca_batch* b) {
+  if (!b) return;
+  int prev_dev = -1;
+  cudaGetDevice(&prev_dev);
+  cudaSetDevice(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (vca_analyzer* a : b->m)
+    if (a && a->batch == b) a->batch = nullptr;
+  for (int k = 0; k < 2; ++k) {
+    if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]);
+    if (b->graph[k]) cudaGraphDestroy(b->graph[k]);
+    if (b->ev[k]) cudaEventDestroy(b->ev[k]);
+    if (b->h_desc[k]) cudaFreeHost(b->h_desc[k]);
+    if (b->h_feats[k]) cudaFreeHost(b->h_feats[k]);
+  }
+  cudaFree(b->d_map);
+  cudaFree(b->d_desc);
+  cudaFree(b->d_feats);
+  cudaFree(b->d_partials);
+  cudaFree(b->d_counters);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  if (prev_dev >= 0) cudaSetDevice(prev_dev);
+  delete b;
+}
+
+// Captures tick graph k: upload the arguments, analyse, reduce, read the features back.
+cudaError_t build_tick_graph(vca_batch* b, int k) {
+  cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t e1 = cudaMemcpyAsync(b->d_desc, b->h_desc[k], b->desc_bytes, cudaMemcpyHostToDevice, b->stream);
+  if (e1 == cudaSuccess)
+    e1 = vca::launch_batch_plain(b->d_map, b->n_cta, reinterpret_cast<const vca::BatchMemberArgs*>(b->d_desc), b->w,
+                                 b->low_pass, b->stream);
+  if (e1 == cudaSuccess)
+    e1 = vca::launch_reduce_batch(reinterpret_cast<const vca::ReduceArgs*>(b->d_desc + b->ma_bytes), b->n, b->stream);
+  if (e1 == cudaSuccess)
+    e1 = cudaMemcpyAsync(b->h_feats[k], b->d_feats, (size_t)b->n * vca::FEAT_STRIDE * sizeof(double),
+                         cudaMemcpyDeviceToHost, b->stream);
+  e = cudaStreamEndCapture(b->stream, &b->graph[k]);
+  if (e1 != cudaSuccess) return e1;
+  if (e != cudaSuccess) return e;
+  return cudaGraphInstantiate(&b->exec[k], b->graph[k], 0);
+}
+
+// Plain-routine arguments of one frame of analyzer a: kind 0 luma, 1 both chroma planes.
+vca::PlainArgs member_plain_args(const vca_analyzer* a, int kind, const vca_frame_ref& f) {
+  const Geometry& g = a->g;
+  vca::PlainArgs pa{};
+  pa.nbx = g.nbx;
+  pa.C = g.C;
+  pa.out_fstride = 0;
+  pa.fstride = 0;
+  float* bv = a->d_blockvals;
+  if (kind == 0) {
+    pa.base[0] = static_cast<const uint8_t*>(f.y);
+    pa.pitch = f.pitch_y;
+    pa.width = g.W;
+    pa.height = g.H;
+    pa.s1 = g.s1y;
+    pa.s2 = g.s2y;
+    pa.M = a->tables.M_y;
+    pa.W = a->tables.W_y;
+    pa.outH[0] = bv + vca::ROW_H_Y * g.C;
+    pa.outL[0] = bv + vca::ROW_L_Y * g.C;
+  } else {
+    pa.base[0] = static_cast<const uint8_t*>(f.u);
+    pa.base[1] = static_cast<const uint8_t*>(f.v);
+    pa.pitch = f.pitch_uv;
+    pa.width = g.cw;
+    pa.height = g.ch;
+    pa.s1 = g.s1c;
+    pa.s2 = g.s2c;
+    pa.M = a->tables.M_c;
+    pa.W = a->tables.W_c;
+    pa.outH[0] = bv + vca::ROW_H_U * g.C;
+    pa.outL[0] = bv + vca::ROW_L_U * g.C;
+    pa.outH[1] = bv + vca::ROW_H_V * g.C;
+    pa.outL[1] = bv + vca::ROW_L_V * g.C;
+  }
+  return pa;
+}
+
 }  // namespace
 
 extern "C" {
@@ -392,6 +564,7 @@ vca_status vca_push_frames(vca_analyzer* a, const void* y, const void* u, const 
                            int64_t pitch_uv, int64_t frame_stride_y, int64_t frame_stride_uv, int32_t n_frames,
                            int32_t on_device) {
   if (!a) return fail(VCA_E_ARG, "analyzer is NULL");
+  if (a->batch) return fail(VCA_E_STATE, "the analyzer belongs to a batch; push through vca_batch_tick");
   if (n_frames < 1 || n_frames > a->max_batch)
     return fail(VCA_E_ARG, "n_frames must be in [1, %d] (got %d)", a->max_batch, n_frames);
   vca_status s = check_planes(a, y, u, v, pitch_y, pitch_uv);
@@ -450,7 +623,9 @@ vca_status vca_read_frame_features(vca_analyzer* a, int64_t frame, int32_t block
   if (frame < a->done_base || frame >= a->frames_pushed)
     return fail(VCA_E_ARG, "frame %lld is not available (pushed %lld)", (long long)frame, (long long)a->frames_pushed);
   while (frame >= a->done_base + (int64_t)a->done.size()) {
-    vca_status s = harvest_front(a, blocking != 0);
+    vca_status s = !a->pending.empty() ? harvest_front(a, blocking != 0)
+                   : a->batch && !a->batch->pending.empty() ? batch_harvest_front(a->batch, blocking != 0)
+                   : fail(VCA_E_STATE, "frame %lld has no pending work", (long long)frame);
     if (s != VCA_OK) return s;
   }
   *out = a->done[(size_t)(frame - a->done_base)];
@@ -459,7 +634,7 @@ vca_status vca_read_frame_features(vca_analyzer* a, int64_t frame, int32_t block
 
 vca_status vca_read_sequence_features(vca_analyzer* a, vca_sequence_features* out) {
   if (!a || !out) return fail(VCA_E_ARG, "NULL argument");
-  vca_status s = harvest_all(a);
+  vca_status s = catch_up_all(a);
   if (s != VCA_OK) return s;
   out->frames = a->seq_n;
   const double n = a->seq_n > 0 ? (double)a->seq_n : 1.0;
@@ -478,7 +653,7 @@ vca_status vca_read_block_values(vca_analyzer* a, int32_t index, float* H_Y, flo
   if (!a) return fail(VCA_E_ARG, "analyzer is NULL");
   if (a->last_n == 0 || index < 0 || index >= a->last_n)
     return fail(VCA_E_ARG, "index %d outside the last push (%d frames)", index, a->last_n);
-  VCA_CUDA(cudaStreamSynchronize(a->stream), "waiting for block values");
+  VCA_CUDA(cudaStreamSynchronize(a->batch ? a->batch->stream : a->stream), "waiting for block values");
   float* const dst[6] = {H_Y, L_Y, H_U, L_U, H_V, L_V};
   const float* src = a->d_blockvals + (size_t)index * vca::N_ROWS * a->g.C;
   for (int r = 0; r < 6; ++r) {
@@ -492,6 +667,7 @@ vca_status vca_read_block_values(vca_analyzer* a, int32_t index, float* H_Y, flo
 vca_status vca_dump_coefficients(vca_analyzer* a, const void* y, const void* u, const void* v, int64_t pitch_y,
                                  int64_t pitch_uv, int16_t* zy, int16_t* zu, int16_t* zv) {
   if (!a) return fail(VCA_E_ARG, "analyzer is NULL");
+  if (a->batch) return fail(VCA_E_STATE, "the analyzer belongs to a batch");
   vca_status s = check_planes(a, y, u, v, pitch_y, pitch_uv);
   if (s != VCA_OK) return s;
   if (!zy || !zu || !zv) return fail(VCA_E_ARG, "coefficient buffer is NULL");
@@ -507,6 +683,7 @@ vca_status vca_dump_coefficients(vca_analyzer* a, const void* y, const void* u, 
 vca_status vca_sync(vca_analyzer* a) {
   if (!a) return fail(VCA_E_ARG, "analyzer is NULL");
   VCA_CUDA(cudaStreamSynchronize(a->stream), "synchronising the analyzer stream");
+  if (a->batch) VCA_CUDA(cudaStreamSynchronize(a->batch->stream), "synchronising the batch stream");
   return VCA_OK;
 }
 
@@ -518,7 +695,7 @@ vca_status vca_export_state(vca_analyzer* a, void* buf, size_t* len) {
     return VCA_OK;
   }
   if (*len < need) return fail(VCA_E_ARG, "state buffer too small (%zu < %zu)", *len, need);
-  vca_status s = harvest_all(a);
+  vca_status s = catch_up_all(a);
   if (s != VCA_OK) return s;
   VCA_CUDA(cudaStreamSynchronize(a->stream), "waiting before state export");
   StateHeader h{};
@@ -545,6 +722,7 @@ vca_status vca_import_state(vca_analyzer* a, const void* buf, size_t len) {
   if (memcmp(h.magic, kStateMagic, 8) != 0) return fail(VCA_E_ARG, "not an analyzer state buffer");
   if (h.C != a->g.C || h.block_size != a->g.w) return fail(VCA_E_ARG, "state belongs to another block grid");
   if (len < sizeof h + (size_t)h.C * sizeof(float) || h.frames < 0) return fail(VCA_E_ARG, "truncated state buffer");
+  if (a->batch) return fail(VCA_E_STATE, "the analyzer belongs to a batch");
   vca_status s = harvest_all(a);
   if (s != VCA_OK) return s;
   VCA_CUDA(cudaStreamSynchronize(a->stream), "waiting before state import");
@@ -595,8 +773,166 @@ vca_status vca_kernel_in_use(vca_analyzer* a, int32_t* kernel) {
 }
 
 vca_status vca_close(vca_analyzer* a) {
+  if (a && a->batch) return fail(VCA_E_STATE, "the analyzer belongs to a batch; destroy the batch first");
   destroy(a);
   return VCA_OK;
+}
+
+vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch** out) {
+  if (!out) return fail(VCA_E_ARG, "out is NULL");
+  *out = nullptr;
+  if (!members || n < 1 || n > 65535) return fail(VCA_E_ARG, "need 1 to 65535 analyzers (got %d)", n);
+  for (int i = 0; i < n; ++i) {
+    vca_analyzer* a = members[i];
+    if (!a) return fail(VCA_E_ARG, "analyzer %d is NULL", i);
+    if (a->batch) return fail(VCA_E_STATE, "analyzer %d already belongs to a batch", i);
+    for (int j = 0; j < i; ++j)
+      if (members[j] == a) return fail(VCA_E_ARG, "analyzer %d appears twice", i);
+    if (a->device != members[0]->device) return fail(VCA_E_ARG, "analyzers of a batch must share one device");
+    if (a->g.w != members[0]->g.w || a->g.low_pass != members[0]->g.low_pass)
+      return fail(VCA_E_ARG, "analyzers of a batch must share block size and low_pass");
+  }
+  vca_batch* b = new (std::nothrow) vca_batch();
+  if (!b) return fail(VCA_E_NOMEM, "host allocation failed");
+  b->m.assign(members, members + n);
+  b->n = n;
+  b->device = members[0]->device;
+  b->w = members[0]->g.w;
+  b->low_pass = members[0]->g.low_pass;
+  int prev_dev = -1;
+  cudaGetDevice(&prev_dev);
+
+#define BATCH_CUDA(call, what)             \
+  do {                                     \
+    cudaError_t e2 = (call);               \
+    if (e2 != cudaSuccess) {               \
+      vca_status st = cuda_fail(e2, what); \
+      destroy_batch(b);                    \
+      if (prev_dev >= 0) cudaSetDevice(prev_dev); \
+      return st;                           \
+    }                                      \
+  } while (0)
+
+  BATCH_CUDA(cudaSetDevice(b->device), "selecting the batch device");
+  for (int i = 0; i < n; ++i) {
+    vca_status st = harvest_all(members[i]);
+    if (st != VCA_OK) {
+      destroy_batch(b);
+      return st;
+    }
+    BATCH_CUDA(cudaStreamSynchronize(members[i]->stream), "waiting for an analyzer's earlier work");
+  }
+  std::vector<vca::BatchCta> map;
+  for (int i = 0; i < n; ++i) {
+    const Geometry& g = members[i]->g;
+    const int64_t cl = (g.C + vca::plain_blocks_per_cta(g.w) - 1) / vca::plain_blocks_per_cta(g.w);
+    const int64_t cc = (g.C + vca::plain_blocks_per_cta(g.nc) - 1) / vca::plain_blocks_per_cta(g.nc);
+    for (int64_t c = 0; c < cl; ++c) map.push_back({(uint16_t)i, 0, 0, (uint32_t)c});
+    for (int pl = 0; pl < 2; ++pl)
+      for (int64_t c = 0; c < cc; ++c) map.push_back({(uint16_t)i, 1, (uint8_t)pl, (uint32_t)c});
+  }
+  if (map.size() > (size_t)INT32_MAX) {
+    destroy_batch(b);
+    return fail(VCA_E_ARG, "batch too large");
+  }
+  b->n_cta = (int)map.size();
+  b->ma_bytes = round_up((size_t)n * sizeof(vca::BatchMemberArgs), 256);
+  b->desc_bytes = b->ma_bytes + (size_t)n * sizeof(vca::ReduceArgs);
+  BATCH_CUDA(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking), "creating the batch stream");
+  BATCH_CUDA(cudaMalloc(&b->d_map, map.size() * sizeof(vca::BatchCta)), "allocating the CTA map");
+  BATCH_CUDA(cudaMemcpy(b->d_map, map.data(), map.size() * sizeof(vca::BatchCta), cudaMemcpyHostToDevice),
+             "uploading the CTA map");
+  BATCH_CUDA(cudaMalloc(&b->d_desc, b->desc_bytes), "allocating tick arguments");
+  BATCH_CUDA(cudaMalloc(&b->d_feats, (size_t)n * vca::FEAT_STRIDE * sizeof(double)), "allocating features");
+  BATCH_CUDA(cudaMalloc(&b->d_partials, vca::reduce_partials_bytes(n)), "allocating reduction scratch");
+  BATCH_CUDA(cudaMalloc(&b->d_counters, (size_t)n * sizeof(unsigned int)), "allocating counters");
+  BATCH_CUDA(cudaMemset(b->d_counters, 0, (size_t)n * sizeof(unsigned int)), "clearing counters");
+  for (int k = 0; k < 2; ++k) {
+    BATCH_CUDA(cudaMallocHost(&b->h_desc[k], b->desc_bytes), "allocating pinned tick arguments");
+    memset(b->h_desc[k], 0, b->desc_bytes);
+    BATCH_CUDA(cudaMallocHost(&b->h_feats[k], (size_t)n * vca::FEAT_STRIDE * sizeof(double)),
+               "allocating pinned features");
+    BATCH_CUDA(cudaEventCreateWithFlags(&b->ev[k], cudaEventDisableTiming), "creating batch events");
+    BATCH_CUDA(build_tick_graph(b, k), "capturing the tick graph");
+  }
+#undef BATCH_CUDA
+  for (int i = 0; i < n; ++i) members[i]->batch = b;
+  if (prev_dev >= 0) cudaSetDevice(prev_dev);
+  *out = b;
+  return VCA_OK;
+}
+
+vca_status vca_batch_tick(vca_batch* b, const vca_frame_ref* frames) {
+  if (!b || !frames) return fail(VCA_E_ARG, "NULL argument");
+  const int k = b->next_k;
+  // The pinned arguments of graph k are rewritten only after its previous tick has run.
+  while (!b->pending.empty() && (b->pending.size() >= 2 || b->pending.front().k == k)) {
+    vca_status s = batch_harvest_front(b, true);
+    if (s != VCA_OK) return s;
+  }
+  for (int i = 0; i < b->n; ++i) {
+    if (!frames[i].y) continue;
+    vca_status s = check_planes(b->m[i], frames[i].y, frames[i].u, frames[i].v, frames[i].pitch_y, frames[i].pitch_uv);
+    if (s != VCA_OK) return fail(s, "frame of analyzer %d: %s", i, vca_last_error());
+  }
+  auto* ma = reinterpret_cast<vca::BatchMemberArgs*>(b->h_desc[k]);
+  auto* ra = reinterpret_cast<vca::ReduceArgs*>(b->h_desc[k] + b->ma_bytes);
+  vca_batch::Tick tick;
+  tick.k = k;
+  for (int i = 0; i < b->n; ++i) {
+    vca_analyzer* a = b->m[i];
+    if (!frames[i].y) {
+      ma[i].active = 0;
+      ra[i].nframes = 0;
+      continue;
+    }
+    ma[i].pa[0] = member_plain_args(a, 0, frames[i]);
+    ma[i].pa[1] = member_plain_args(a, 1, frames[i]);
+    ma[i].bps = a->g.bps;
+    ma[i].active = 1;
+    ra[i] = vca::reduce_args(a->g, 1, a->d_blockvals, a->d_prevH[a->cur_prev], a->has_prev,
+                             a->d_prevH[a->cur_prev ^ 1], b->d_feats + (size_t)i * vca::FEAT_STRIDE,
+                             b->d_partials + (size_t)i * vca::reduce_partials_bytes(1) / sizeof(double),
+                             b->d_counters + i);
+    tick.members.push_back({i, a->frames_pushed, a->has_prev != 0});
+  }
+  int prev_dev = -1;
+  cudaGetDevice(&prev_dev);
+  if (prev_dev != b->device) VCA_CUDA(cudaSetDevice(b->device), "selecting the batch device");
+  cudaError_t e = cudaGraphLaunch(b->exec[k], b->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(b->ev[k], b->stream);
+  if (prev_dev >= 0 && prev_dev != b->device) cudaSetDevice(prev_dev);
+  if (e != cudaSuccess) return cuda_fail(e, "launching a batch tick");
+  for (const auto& mm : tick.members) {
+    vca_analyzer* a = b->m[mm.index];
+    a->cur_prev ^= 1;
+    a->has_prev = 1;
+    a->frames_pushed += 1;
+    a->last_n = 1;
+  }
+  b->pending.push_back(std::move(tick));
+  b->next_k ^= 1;
+  b->ticks += 1;
+  b->launches += 2;
+  return VCA_OK;
+}
+
+vca_status vca_batch_sync(vca_batch* b) {
+  if (!b) return fail(VCA_E_ARG, "batch is NULL");
+  return batch_harvest_all(b);
+}
+
+vca_status vca_batch_launch_count(vca_batch* b, int64_t* launches) {
+  if (!b || !launches) return fail(VCA_E_ARG, "NULL argument");
+  *launches = b->launches;
+  return VCA_OK;
+}
+
+vca_status vca_batch_destroy(vca_batch* b) {
+  if (!b) return VCA_OK;
+  vca_status s = batch_harvest_all(b);
+  destroy_batch(b);
+  return s;
 }
 
 const char* vca_status_str(vca_status s) {

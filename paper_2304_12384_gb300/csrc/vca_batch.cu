@@ -1,0 +1,62 @@
+// Batched multi-stream analysis: one frame of every analyzer of a batch in one launch of the plain
+// block routine (Section 2 of the paper, per block: integer DCT, texture energy H, brightness L).
+//
+// The analyzers may differ in frame size and bit depth but share block size and the low-pass
+// option.  Each CTA reads its (analyzer, plane kind, plane, block chunk) from a map built once
+// when the batch is created, and the analyzer's arguments for this tick from a table the host
+// refreshes every tick; an analyzer skipped this tick has active = 0 and its CTAs return at once.
+#include "vca_plain.cuh"
+
+namespace vca {
+namespace {
+
+template <int Nl, bool LP>
+__global__ void __launch_bounds__(kWarps * 32)
+    batch_plain_kernel(const BatchCta* __restrict__ map, const BatchMemberArgs* __restrict__ args) {
+  constexpr int Nc = Nl / 2;
+  __shared__ union {
+    PlainSmem<Nl, LP> luma;
+    PlainSmem<Nc, LP> chroma;
+  } sh;
+  const BatchCta w = map[blockIdx.x];
+  const BatchMemberArgs& ma = args[w.member];
+  if (!ma.active) return;
+  const PlainArgs a = ma.pa[w.kind];
+  if (w.kind == 0) {
+    if (ma.bps == 1)
+      plain_blocks<Nl, LP, uint8_t>(a, w.plane, 0, w.chunk, sh.luma);
+    else
+      plain_blocks<Nl, LP, uint16_t>(a, w.plane, 0, w.chunk, sh.luma);
+  } else {
+    if (ma.bps == 1)
+      plain_blocks<Nc, LP, uint8_t>(a, w.plane, 0, w.chunk, sh.chroma);
+    else
+      plain_blocks<Nc, LP, uint16_t>(a, w.plane, 0, w.chunk, sh.chroma);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_batch_plain(const BatchCta* d_map, int n_cta, const BatchMemberArgs* d_args, int w, bool low_pass,
+                               cudaStream_t s) {
+  if (n_cta <= 0) return cudaSuccess;
+  static_assert(plain_blocks_per_cta(32) == kWarps * 1 && plain_blocks_per_cta(16) == kWarps * 2,
+                "blocks per CTA of the plain routine");
+  const dim3 grid((unsigned)n_cta), block(kWarps * 32);
+  if (w == 32) {
+    if (low_pass)
+      batch_plain_kernel<32, true><<<grid, block, 0, s>>>(d_map, d_args);
+    else
+      batch_plain_kernel<32, false><<<grid, block, 0, s>>>(d_map, d_args);
+  } else if (w == 16) {
+    if (low_pass)
+      batch_plain_kernel<16, true><<<grid, block, 0, s>>>(d_map, d_args);
+    else
+      batch_plain_kernel<16, false><<<grid, block, 0, s>>>(d_map, d_args);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace vca

@@ -43,6 +43,37 @@ struct DeviceTables {
   const float* W_c;    // (w/2) x (w/2)
 };
 
+// Arguments of one launch of the plain block routine (one plane kind of a batch of frames).
+struct PlainArgs {
+  const uint8_t* base[2];  // plane of frame 0, per plane in this launch
+  int64_t pitch;           // bytes between rows
+  int64_t fstride;         // bytes between frames
+  int width, height;       // plane size in samples
+  int nbx;
+  int64_t C;
+  int s1, s2;
+  const int8_t* M;         // N x N
+  const float* W;          // N x N, W[0] = 0
+  float* outH[2];
+  float* outL[2];
+  int64_t out_fstride;     // floats between frames of block values
+  int16_t* zdump[2];       // optional coefficient dump (frame 0 only)
+};
+
+// Arguments of the frame reduction of one analyzer's batch of frames.
+struct ReduceArgs {
+  const float* blockvals;
+  const float* prevH_in;
+  float* prevH_out;
+  double* feats;
+  double* partials;        // [frame][kSlices][kSums]
+  unsigned int* counters;  // [frame], zero on entry, left at zero on exit
+  int64_t C;
+  int nframes;
+  int has_prev;
+  double normY, normC;  // C w^2 and C (w/2)^2
+};
+
 // Integer DCT matrix M_N[k][n] = round_half_away(64 sqrt(N) alpha_k cos(pi (2n+1) k / 2N)).
 void make_dct_matrix(int N, int8_t* out);
 // Energy weights w_N(u,v) = exp(|((u+1)(v+1)/N^2)^2 - 1|) rounded to FP32, with (0,0) set to 0.
@@ -70,6 +101,37 @@ size_t reduce_partials_bytes(int max_frames);
 cudaError_t launch_reduce(const Geometry& g, int nframes, const float* blockvals, const float* prevH_in,
                           int has_prev, float* prevH_out, double* feats, double* partials, unsigned int* counters,
                           cudaStream_t s, int64_t* launches);
+
+// Reduction arguments of one analyzer (reduce_partials_bytes(nframes) of `partials`; `counters`
+// zero on entry).
+ReduceArgs reduce_args(const Geometry& g, int nframes, const float* blockvals, const float* prevH_in, int has_prev,
+                       float* prevH_out, double* feats, double* partials, unsigned int* counters);
+// Frame reduction of one frame per analyzer of a batch, in one launch: d_args (device) holds n
+// ReduceArgs with nframes 1 (or 0 for an analyzer skipped this tick).
+cudaError_t launch_reduce_batch(const ReduceArgs* d_args, int n, cudaStream_t s);
+
+// One CTA of the batched plain kernel: analyzer `member`, plane kind (0 luma, 1 chroma), plane
+// within the kind (chroma: 0 U, 1 V) and block chunk (BPC blocks).
+struct BatchCta {
+  uint16_t member;
+  uint8_t kind;
+  uint8_t plane;
+  uint32_t chunk;
+};
+// Per-analyzer arguments of one batched tick: the plain routine's arguments for luma and chroma,
+// the sample size, and whether the analyzer takes part in this tick.
+struct BatchMemberArgs {
+  PlainArgs pa[2];
+  int32_t bps;
+  int32_t active;
+  int32_t pad[2];
+};
+// Blocks per CTA of the plain routine for block size N.
+constexpr int plain_blocks_per_cta(int N) { return 4 * (32 / N); }
+// The batched plain analysis of one frame per analyzer: n_cta CTAs described by d_map (device),
+// arguments d_args (device, one per analyzer).  All analyzers share block size w and low_pass.
+cudaError_t launch_batch_plain(const BatchCta* d_map, int n_cta, const BatchMemberArgs* d_args, int w, bool low_pass,
+                               cudaStream_t s);
 
 // Sets the calling thread's vca_last_error message.
 void record_error(const char* msg);

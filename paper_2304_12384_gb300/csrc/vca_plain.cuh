@@ -1,0 +1,138 @@
+// The plain CUDA-core block routine (Section 2 of the paper: blockwise integer DCT, texture energy
+// H and brightness L of every Y, U and V block), shared by the single-analyzer kernel and the
+// batched multi-stream kernel.
+//
+// One warp owns 32/N blocks.  Stage 1: lane (j, r) keeps row r of block j in registers
+// and produces T[r][k] = (sum_c x[r][c] M[k][c] + 2^(s1-1)) >> s1; stage 2: lane (j, v)
+// keeps column v of T in registers and produces Z[u][v] = (sum_r M[u][r] T[r][v] +
+// 2^(s2-1)) >> s2, accumulating H_v = sum_u w(u,v) |Z[u][v]| in increasing u with FMA.
+// The block energy is then the xor-butterfly sum of H_v over the NK lanes of the block
+// (offsets NK/2 .. 1), the same order the tensor-core form uses, so both forms give
+// bit-identical H.
+#pragma once
+
+#include <cstdint>
+
+#include "vca_internal.h"
+
+namespace vca {
+
+constexpr int kWarps = 4;
+
+// Loads N samples of one block row, repeating the last sample of the plane past its edge.
+template <int N, typename Pix>
+__device__ __forceinline__ void load_row(const Pix* row, int x0, int width, int (&x)[N]) {
+  constexpr int kBytes = N * (int)sizeof(Pix);
+  if (x0 + N <= width && (kBytes % 16) == 0) {
+    uint32_t words[kBytes / 4];
+#pragma unroll
+    for (int i = 0; i < kBytes / 16; ++i) {
+      const uint4 q = __ldg(reinterpret_cast<const uint4*>(row + x0) + i);
+      words[4 * i + 0] = q.x;
+      words[4 * i + 1] = q.y;
+      words[4 * i + 2] = q.z;
+      words[4 * i + 3] = q.w;
+    }
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+      if (sizeof(Pix) == 1) {
+        x[c] = (words[c / 4] >> (8 * (c % 4))) & 0xff;
+      } else {
+        x[c] = (words[c / 2] >> (16 * (c % 2))) & 0xffff;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < N; ++c) x[c] = row[min(x0 + c, width - 1)];
+  }
+}
+
+// Shared memory of one CTA of the block routine.
+template <int N, bool LP>
+struct PlainSmem {
+  static constexpr int NK = LP ? N / 2 : N;
+  static constexpr int BPW = 32 / N;
+  __align__(16) int M[N][N];
+  float W[NK][NK];
+  int T[kWarps][BPW][N][NK + 1];
+};
+
+// Blocks chunk * BPC .. chunk * BPC + BPC - 1 of plane `plane` of frame f (one CTA of 4 warps; the
+// warp owns 32/N blocks).  Stage 1: lane (j, r) keeps row r of block j in registers and produces
+// T[r][k]; stage 2: lane (j, v) keeps column v of T and produces Z[u][v], accumulating H_v.
+template <int N, bool LP, typename Pix>
+__device__ __forceinline__ void plain_blocks(const PlainArgs& p, int plane, int f, int64_t chunk,
+                                             PlainSmem<N, LP>& sh) {
+  constexpr int NK = LP ? N / 2 : N;
+  constexpr int BPW = 32 / N;
+  constexpr int BPC = kWarps * BPW;
+  auto& sM = sh.M;
+  auto& sW = sh.W;
+  auto& sT = sh.T;
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int lane = tid & 31;
+  for (int i = tid; i < N * N; i += kWarps * 32) sM[i / N][i % N] = p.M[i];
+  for (int i = tid; i < NK * NK; i += kWarps * 32) sW[i / NK][i % NK] = p.W[(i / NK) * N + (i % NK)];
+  __syncthreads();
+
+  const int j = lane / N;
+  const int r = lane % N;
+  const int64_t k = chunk * BPC + warp * BPW + j;
+  const bool valid = k < p.C;
+  const int bx = valid ? (int)(k % p.nbx) : 0;
+  const int by = valid ? (int)(k / p.nbx) : 0;
+  const uint8_t* base = p.base[plane] + (int64_t)f * p.fstride;
+  const int off1 = 1 << (p.s1 - 1);
+  const int off2 = 1 << (p.s2 - 1);
+
+  if (valid) {
+    int x[N];
+    const int yy = min(by * N + r, p.height - 1);
+    load_row<N, Pix>(reinterpret_cast<const Pix*>(base + (int64_t)yy * p.pitch), bx * N, p.width, x);
+#pragma unroll 2
+    for (int kk = 0; kk < NK; ++kk) {
+      int acc = 0;
+#pragma unroll
+      for (int c = 0; c < N; c += 4) {
+        const int4 m = *reinterpret_cast<const int4*>(&sM[kk][c]);
+        acc += m.x * x[c] + m.y * x[c + 1] + m.z * x[c + 2] + m.w * x[c + 3];
+      }
+      sT[warp][j][r][kk] = (acc + off1) >> p.s1;
+    }
+  }
+  __syncwarp();
+
+  float H = 0.0f;
+  int z00 = 0;
+  const int v = r;
+  if (valid && v < NK) {
+    int t[N];
+#pragma unroll
+    for (int rr = 0; rr < N; ++rr) t[rr] = sT[warp][j][rr][v];
+    int16_t* zd = p.zdump[plane] && f == 0 ? p.zdump[plane] + k * NK * NK : nullptr;
+#pragma unroll 2
+    for (int u = 0; u < NK; ++u) {
+      int acc = 0;
+#pragma unroll
+      for (int c = 0; c < N; c += 4) {
+        const int4 m = *reinterpret_cast<const int4*>(&sM[u][c]);
+        acc += m.x * t[c] + m.y * t[c + 1] + m.z * t[c + 2] + m.w * t[c + 3];
+      }
+      const int z = (acc + off2) >> p.s2;
+      if (u == 0) z00 = z;
+      if (zd) zd[u * NK + v] = (int16_t)z;
+      H = fmaf(fabsf((float)z), sW[u][v], H);
+    }
+  }
+#pragma unroll
+  for (int o = NK / 2; o > 0; o >>= 1) H += __shfl_xor_sync(0xffffffffu, H, o);
+  if (valid && v == 0) {
+    p.outH[plane][f * p.out_fstride + k] = H;
+    p.outL[plane][f * p.out_fstride + k] = __fsqrt_rn((float)z00);
+  }
+}
+
+
+}  // namespace vca

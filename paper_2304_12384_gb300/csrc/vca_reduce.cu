@@ -22,24 +22,10 @@ constexpr int kThreads = 256;
 constexpr int kSlices = 8;
 constexpr int kSums = 7;  // H_Y, L_Y, H_U, L_U, H_V, L_V, |dH_Y|
 
-struct ReduceArgs {
-  const float* blockvals;
-  const float* prevH_in;
-  float* prevH_out;
-  double* feats;
-  double* partials;        // [frame][kSlices][kSums]
-  unsigned int* counters;  // [frame], zero on entry, left at zero on exit
-  int64_t C;
-  int nframes;
-  int has_prev;
-  double normY, normC;  // C w^2 and C (w/2)^2
-};
-
-__global__ void __launch_bounds__(kThreads) reduce_kernel(const ReduceArgs a) {
+// Slice `slice` of frame f (one CTA of kThreads threads).
+__device__ __forceinline__ void reduce_slice(const ReduceArgs& a, int f, int slice) {
   __shared__ double part[kSums][kThreads];
   __shared__ bool last;
-  const int f = blockIdx.x / kSlices;
-  const int slice = blockIdx.x % kSlices;
   const int tid = threadIdx.x;
   const int64_t C = a.C;
   const int64_t k0 = C * slice / kSlices, k1 = C * (slice + 1) / kSlices;
@@ -95,6 +81,17 @@ __global__ void __launch_bounds__(kThreads) reduce_kernel(const ReduceArgs a) {
   }
 }
 
+__global__ void __launch_bounds__(kThreads) reduce_kernel(const ReduceArgs a) {
+  reduce_slice(a, blockIdx.x / kSlices, blockIdx.x % kSlices);
+}
+
+// One frame per analyzer of a batch: args[m] describes analyzer m (nframes 0: skipped this tick).
+__global__ void __launch_bounds__(kThreads) reduce_batch_kernel(const ReduceArgs* __restrict__ args) {
+  const ReduceArgs a = args[blockIdx.x / kSlices];
+  if (a.nframes == 0) return;
+  reduce_slice(a, 0, blockIdx.x % kSlices);
+}
+
 }  // namespace
 
 size_t reduce_partials_bytes(int max_frames) { return (size_t)max_frames * kSlices * kSums * sizeof(double); }
@@ -119,6 +116,29 @@ cudaError_t launch_reduce(const Geometry& g, int nframes, const float* blockvals
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) ++*launches;
   return e;
+}
+
+ReduceArgs reduce_args(const Geometry& g, int nframes, const float* blockvals, const float* prevH_in, int has_prev,
+                       float* prevH_out, double* feats, double* partials, unsigned int* counters) {
+  ReduceArgs a{};
+  a.blockvals = blockvals;
+  a.prevH_in = prevH_in;
+  a.prevH_out = prevH_out;
+  a.feats = feats;
+  a.partials = partials;
+  a.counters = counters;
+  a.C = g.C;
+  a.nframes = nframes;
+  a.has_prev = has_prev;
+  a.normY = (double)g.C * g.w * g.w;
+  a.normC = (double)g.C * g.nc * g.nc;
+  return a;
+}
+
+cudaError_t launch_reduce_batch(const ReduceArgs* d_args, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  reduce_batch_kernel<<<n * kSlices, kThreads, 0, s>>>(d_args);
+  return cudaGetLastError();
 }
 
 }  // namespace vca

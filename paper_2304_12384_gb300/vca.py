@@ -53,6 +53,11 @@ class VcaSequenceFeatures(ctypes.Structure):
         return d
 
 
+class VcaFrameRef(ctypes.Structure):
+    _fields_ = [("y", ctypes.c_void_p), ("u", ctypes.c_void_p), ("v", ctypes.c_void_p),
+                ("pitch_y", ctypes.c_int64), ("pitch_uv", ctypes.c_int64)]
+
+
 class VcaError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{message} (status {status})")
@@ -83,6 +88,11 @@ _PROTOS = {
     "vca_read_kernel_timing": (_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)),
     "vca_close": (_P,),
     "vca_reduce_frames_noalloc": (_P, _I64, _I32, _I32, _P, _P, _P, _P),
+    "vca_batch_create": (ctypes.POINTER(_P), _I32, ctypes.POINTER(_P)),
+    "vca_batch_tick": (_P, ctypes.POINTER(VcaFrameRef)),
+    "vca_batch_sync": (_P,),
+    "vca_batch_launch_count": (_P, ctypes.POINTER(_I64)),
+    "vca_batch_destroy": (_P,),
 }
 
 
@@ -135,6 +145,32 @@ def vca_reduce_frames_noalloc(block_values: int, blocks_per_plane: int, block_si
     """Frame features from device block values with no device allocation (device pointers)."""
     return _check(lib().vca_reduce_frames_noalloc(_P(block_values), blocks_per_plane, block_size, n_frames,
                                                   _P(prev_H_Y or 0), _P(last_H_Y), _P(features), _P(stream)))
+
+
+def vca_batch_create(handles) -> int:
+    arr = (_P * len(handles))(*handles)
+    h = _P()
+    _check(lib().vca_batch_create(arr, len(handles), ctypes.byref(h)))
+    return h.value
+
+
+def vca_batch_tick(batch: int, refs) -> None:
+    arr = (VcaFrameRef * len(refs))(*refs)
+    _check(lib().vca_batch_tick(_P(batch), arr))
+
+
+def vca_batch_sync(batch: int) -> None:
+    _check(lib().vca_batch_sync(_P(batch)))
+
+
+def vca_batch_launch_count(batch: int) -> int:
+    n = _I64()
+    _check(lib().vca_batch_launch_count(_P(batch), ctypes.byref(n)))
+    return n.value
+
+
+def vca_batch_destroy(batch: int) -> None:
+    _check(lib().vca_batch_destroy(_P(batch)))
 
 
 def vca_open(cfg: VcaConfig, stream: int = 0) -> int:
@@ -327,3 +363,48 @@ class Analyzer:
     @property
     def kernel(self) -> int:
         return vca_kernel_in_use(self.handle)
+
+
+class Batch:
+    """Analyzers ticked together: one frame per analyzer per tick in one batched launch."""
+
+    def __init__(self, analyzers):
+        self.analyzers = list(analyzers)
+        self.handle = vca_batch_create([a.handle for a in self.analyzers])
+
+    def tick(self, frames):
+        """frames: one (y, u, v) device-tensor triple per analyzer (one frame each), or None to skip."""
+        refs = []
+        for f in frames:
+            if f is None:
+                refs.append(VcaFrameRef(None, None, None, 0, 0))
+                continue
+            y, u, v = f
+            es = y.element_size()
+            if u.stride(-2) != v.stride(-2):
+                raise ValueError("U and V planes must share a pitch")
+            refs.append(VcaFrameRef(y.data_ptr(), u.data_ptr(), v.data_ptr(), y.stride(-2) * es, u.stride(-2) * es))
+        vca_batch_tick(self.handle, refs)
+
+    def sync(self):
+        vca_batch_sync(self.handle)
+
+    def launches(self) -> int:
+        return vca_batch_launch_count(self.handle)
+
+    def close(self):
+        if self.handle:
+            vca_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,127 @@
+"""Batched multi-stream ticks (one launch of the block kernel and one of the reduction for one
+frame of every channel, replayed from a CUDA graph) against single analyzers and the oracle.
+
+Channels of one batch differ in frame size (ragged block grids included) and bit depth; some
+ticks skip a channel.  Each channel's features must equal, bit for bit, those of its own
+analyzer fed the same frames one at a time through the plain kernel (same arithmetic), and
+match the oracle within the feature tolerance; the h state must carry across ticks, skipped
+ticks and the batch's destruction.
+"""
+
+import pytest
+
+from synth import SequenceSpec, frames_list
+from vca_testutil import assert_features_close, oracle_config, oracle_sequence, to_device
+
+pytestmark = pytest.mark.gpu
+
+CHANNELS = [  # (width, height, bit depth)
+    (640, 352, 8),
+    (320, 180, 10),
+    (656, 368, 8),
+    (200, 120, 10),
+]
+TICKS = 6
+SKIP = {(3, 2), (1, 0)}  # (tick, channel) pairs left out
+
+
+@pytest.fixture(scope="module")
+def vca():
+    import torch
+
+    from paper_2304_12384_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2304_12384_gb300 import vca as v
+    return v
+
+
+def _channel_frames(i, w, h, bd):
+    spec = SequenceSpec(w, h, TICKS + 2, 700 + i, bit_depth=bd, sigma=4.0, cuts=(4,), motion=4)
+    return frames_list(spec)
+
+
+@pytest.mark.parametrize("low_pass", [True, False])
+def test_batch_matches_single_analyzers_and_oracle(vca, low_pass):
+    import torch
+
+    frames = [_channel_frames(i, *c) for i, c in enumerate(CHANNELS)]
+    dev = [to_device(f) for f in frames]
+    members = [vca.Analyzer(w, h, bd, 32, low_pass, kernel=vca.VCA_KERNEL_PLAIN, max_batch=4)
+               for (w, h, bd) in CHANNELS]
+    singles = [vca.Analyzer(w, h, bd, 32, low_pass, kernel=vca.VCA_KERNEL_PLAIN, max_batch=4)
+               for (w, h, bd) in CHANNELS]
+    fed = [[] for _ in CHANNELS]
+    try:
+        batch = vca.Batch(members)
+        for t in range(TICKS):
+            refs = []
+            for i in range(len(CHANNELS)):
+                if (t, i) in SKIP:
+                    refs.append(None)
+                    continue
+                y, u, v = dev[i]
+                refs.append((y[t], u[t], v[t]))
+                singles[i].push(y[t], u[t], v[t])
+                fed[i].append(t)
+            batch.tick(refs)
+        batch.sync()
+        assert batch.launches() == 2 * TICKS
+        for i, (w, h, bd) in enumerate(CHANNELS):
+            got = [members[i].frame_features(k) for k in range(len(fed[i]))]
+            exp = [singles[i].frame_features(k) for k in range(len(fed[i]))]
+            assert got == exp, f"channel {i}"
+            cfg = oracle_config(members[i])
+            per, seqf = oracle_sequence([frames[i][t] for t in fed[i]], cfg)
+            for k, e in enumerate(per):
+                assert_features_close(got[k], e, where=f"channel {i} frame {k}")
+            assert_features_close(members[i].sequence_features(), seqf, where=f"channel {i} sequence")
+        batch.close()
+        # The h state continues after the batch is gone.
+        for i in range(len(CHANNELS)):
+            y, u, v = dev[i]
+            members[i].push(y[TICKS], u[TICKS], v[TICKS])
+            singles[i].push(y[TICKS], u[TICKS], v[TICKS])
+            k = len(fed[i])
+            assert members[i].frame_features(k) == singles[i].frame_features(k)
+        torch.cuda.synchronize()
+    finally:
+        for a in members + singles:
+            try:
+                a.close()
+            except vca.VcaError:
+                pass
+
+
+def test_batch_state_rules(vca):
+    a = vca.Analyzer(640, 352, 8, 32, True, kernel=vca.VCA_KERNEL_PLAIN, max_batch=2)
+    b = vca.Analyzer(320, 180, 10, 32, True, kernel=vca.VCA_KERNEL_PLAIN, max_batch=2)
+    c = vca.Analyzer(320, 180, 8, 16, True, kernel=vca.VCA_KERNEL_PLAIN, max_batch=2)
+    d = vca.Analyzer(320, 180, 8, 32, False, kernel=vca.VCA_KERNEL_PLAIN, max_batch=2)
+    try:
+        for bad in ([a, c], [a, d], [a, a]):
+            with pytest.raises(vca.VcaError) as ei:
+                vca.Batch(bad)
+            assert ei.value.status == vca.VCA_E_ARG
+        batch = vca.Batch([a, b])
+        frames = to_device(frames_list(SequenceSpec(640, 352, 1, 9), 0, 1))
+        with pytest.raises(vca.VcaError) as ei:
+            a.push(frames[0][0], frames[1][0], frames[2][0])
+        assert ei.value.status == vca.VCA_E_STATE
+        with pytest.raises(vca.VcaError) as ei:
+            vca.vca_close(a.handle)
+        assert ei.value.status == vca.VCA_E_STATE
+        with pytest.raises(vca.VcaError) as ei:
+            vca.Batch([a])
+        assert ei.value.status == vca.VCA_E_STATE
+        # A misaligned plane pointer is rejected before anything is queued.
+        y, u, v = frames
+        with pytest.raises(vca.VcaError) as ei:
+            batch.tick([(y[0][:, 1:], u[0], v[0]), None])
+        assert ei.value.status == vca.VCA_E_ARG
+        batch.tick([(y[0], u[0], v[0]), None])
+        batch.close()
+        assert a.frame_features(0)["h"] == 0.0
+    finally:
+        for x in (a, b, c, d):
+            x.close()
