@@ -399,6 +399,7 @@ def run_extras(args, an, y, u, v, frames, stream, kern, lp, device):
     out["variants"] = variants
 
     out["ladder"] = run_ladder(args, stream)
+    out["serving"] = run_serving(args)
 
     # CPU oracle on the host cores, bounded sample of the same workload.
     cfg = Config(W, H, 8, args.block_size, lp)
@@ -474,6 +475,114 @@ def run_ladder(args, stream, distinct=2, ticks=20):
             "per_channel_push_ticks_per_s": ticks / el_s,
             "hbm_roofline_ticks_per_s": peak * 1e9 / tick_bytes,
             "timing": "host wall clock around queued ticks, synchronized at both ends; frames device-resident"}
+
+
+def run_serving(args, n_channels=64, distinct=4, capacity_s=3.0, poisson_s=6.0, seed=5):
+    """Serving loop: 64 live channels (frame size uniform over the six ladder resolutions, 8/10-bit
+    mix, 2-second segments at 30 or 60 fps = 60 or 120 frames), segments copied from device
+    buffers into the server's rings (standing in for a decoder) and analysed by continuous
+    batching.  First the capacity (segments/s with every channel submitting back to back), then
+    Poisson arrivals per channel at 0.8 x capacity in total; latency = features ready - arrival."""
+    import numpy as np
+    import torch
+
+    from paper_2304_12384_gb300 import vca
+    from synth import LADDER_RESOLUTIONS, SequenceSpec, frames_list, pack_planes
+
+    rng = np.random.default_rng(seed)
+    chans = []
+    for i in range(n_channels):
+        w, h = LADDER_RESOLUTIONS[int(rng.integers(len(LADDER_RESOLUTIONS)))]
+        chans.append((w, h, int(rng.choice([8, 10])), int(rng.choice([60, 120]))))
+    # One 120-frame source segment per (size, depth) class, shared by that class's channels.
+    src = {}
+    for (w, h, bd, _) in chans:
+        if (w, h, bd) in src:
+            continue
+        pk = pack_planes(frames_list(SequenceSpec(w, h, distinct, 9000 + w + bd, bit_depth=bd), 0, distinct))
+        planes = []
+        for k in ("y", "u", "v"):
+            a = pk[k]
+            if a.dtype == np.uint16:
+                a = a.view(np.int16)
+            t = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+            planes.append(t[torch.arange(120, device="cuda") % distinct].contiguous())
+        src[(w, h, bd)] = planes
+    torch.cuda.synchronize()
+    srv = vca.Server()
+    ids = [srv.add_channel(w, h, bd, 32, True, max_segment_frames=seg) for (w, h, bd, seg) in chans]
+    stats0 = srv.stats()
+
+    def submit(i, tag):
+        w, h, bd, seg = chans[i]
+        y, u, v = src[(w, h, bd)]
+        return srv.submit_frames(ids[i], y[:seg], u[:seg], v[:seg], tag=tag)
+
+    # Capacity: keep every channel's two slots busy.
+    done = []
+    t_end = time.monotonic() + capacity_s
+    tag = 0
+    t0 = time.monotonic()
+    while time.monotonic() < t_end:
+        sent = 0
+        for i in range(n_channels):
+            if submit(i, tag) == vca.VCA_OK:
+                tag += 1
+                sent += 1
+        done += srv.poll(1024)
+        if not sent:
+            time.sleep(0.0002)
+    while len(done) < tag:
+        done += srv.poll(1024)
+        time.sleep(0.0005)
+    el = time.monotonic() - t0
+    capacity = len(done) / el
+    frames_cap = sum(d["n_frames"] for d in done) / el
+
+    # Poisson arrivals at 0.8 x capacity, each channel an independent stream of rate/n_channels.
+    rate = 0.8 * capacity / n_channels
+    arrivals = []
+    for i in range(n_channels):
+        t = rng.exponential(1.0 / rate)
+        while t < poisson_s:
+            arrivals.append((t, i))
+            t += rng.exponential(1.0 / rate)
+    arrivals.sort()
+    backlog = [[] for _ in range(n_channels)]
+    arrival_ns = {}
+    lat = []
+    base = time.monotonic_ns()
+    k = 0
+    tag0 = 1 << 32
+    n_arr = len(arrivals)
+    while len(lat) < n_arr:
+        now = time.monotonic_ns()
+        while k < n_arr and base + int(arrivals[k][0] * 1e9) <= now:
+            t_arr, i = arrivals[k]
+            backlog[i].append((tag0 + k, base + int(t_arr * 1e9)))
+            k += 1
+        for i in range(n_channels):
+            while backlog[i]:
+                tg, ta = backlog[i][0]
+                if submit(i, tg) != vca.VCA_OK:
+                    break
+                arrival_ns[tg] = ta
+                backlog[i].pop(0)
+        for d in srv.poll(1024):
+            if d["tag"] in arrival_ns:
+                lat.append((d["ready_ns"] - arrival_ns.pop(d["tag"])) / 1e6)
+        time.sleep(0.0002)
+    st = srv.stats()
+    srv.close()
+    lat = np.array(lat)
+    return {"channels": n_channels, "segments_capacity_per_s": capacity, "frames_capacity_per_s": frames_cap,
+            "poisson_rate_segments_per_s": 0.8 * capacity, "segments": int(lat.size),
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max()), "mean": float(lat.mean())},
+            "device_budget_bytes": st["budget_bytes"], "device_used_bytes": st["used_bytes"],
+            "launches": st["launches"] - stats0["launches"], "ticks": st["ticks"],
+            "mix": "frame size uniform over 640x360..3840x2160, 8/10-bit, 60/120-frame segments; "
+                   "segments copied device-to-device into the server's rings inside the measured latency"}
 
 
 def main():

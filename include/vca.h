@@ -210,6 +210,70 @@ vca_status vca_batch_launch_count(vca_batch* b, int64_t* launches);
 /* Waits for the batch's ticks and dissolves it; the analyzers stay open.  NULL is accepted. */
 vca_status vca_batch_destroy(vca_batch* b);
 
+/* ---- Serving runtime ----------------------------------------------------------------------
+ *
+ * A server holds live channels (one analyzer each, h state kept on the device between segments)
+ * and runs a scheduler thread of its own.  A channel's producer (a decoder writing into device
+ * memory, say) fills one of the channel's two segment slots -- device buffers owned by the
+ * server -- and submits it; the scheduler ticks continuously, each tick analysing the next
+ * frame of every channel that has a submitted segment (one batched tick, vca_batch_tick), so
+ * channels join and leave ticks as segments arrive and finish.  A finished segment appears in
+ * vca_server_poll with its submit and feature-ready times (steady clock, ns).
+ * Admission is by device memory: a channel costs its analyzer's state plus its two segment slots
+ * (2 x max_segment_frames frames); vca_server_add_channel gives VCA_E_NOMEM when the budget
+ * cannot hold it.  All channels of a server share block size and low_pass (the batch rule). */
+typedef struct vca_server vca_server;
+
+typedef struct {
+  int32_t channel;
+  int32_t status;      /* VCA_OK, or the error that ended the segment */
+  uint64_t tag;        /* the caller's tag from vca_server_submit */
+  int64_t first_frame; /* the channel's frame index of the segment's first frame */
+  int32_t n_frames;
+  int32_t pad;
+  int64_t submit_ns;   /* steady clock at vca_server_submit */
+  int64_t ready_ns;    /* steady clock when the last frame's features reached the host */
+} vca_segment_done;
+
+typedef struct {
+  int64_t ticks, frames, launches;
+  int64_t budget_bytes, used_bytes;
+  int32_t channels;
+  int32_t pad;
+} vca_server_stats_t;
+
+/* device_budget_bytes = 0: 90 % of the device memory free now.  Starts the scheduler thread
+ * on the current device. */
+vca_status vca_server_create(size_t device_budget_bytes, vca_server** out);
+/* Admits a channel (cfg as for vca_open; max_batch is ignored) whose segments hold up to
+ * max_segment_frames frames; *id receives its number. */
+vca_status vca_server_add_channel(vca_server* s, const vca_config* cfg, int32_t max_segment_frames, int32_t* id);
+/* Device address of frame 0 of segment slot `slot` (0 or 1) of channel id (pitches in *frame0)
+ * and the byte strides between its frames: the slot holds the Y planes of all its frames one
+ * after another, then the U planes, then the V planes. */
+vca_status vca_server_segment_buffer(vca_server* s, int32_t id, int32_t slot, vca_frame_ref* frame0,
+                                     int64_t* frame_stride_y, int64_t* frame_stride_uv);
+/* Queues the n_frames frames of slot `slot` of channel id.  ready_event (a cudaEvent_t, or
+ * NULL): the frames are analysed only after it completes.  VCA_E_AGAIN while that slot is still
+ * queued or being analysed. */
+vca_status vca_server_submit(vca_server* s, int32_t id, int32_t slot, int32_t n_frames, uint64_t tag,
+                             void* ready_event);
+/* Copies n_frames frames (frame i: Y at frame0.y + i * frame_stride_y bytes, U and V at
+ * frame0.u / frame0.v + i * frame_stride_uv; device or host memory) into a free segment slot of
+ * channel id on the
+ * server's copy stream, after ready_event (or NULL), and queues them.  The source may be reused
+ * once the segment is finished.  VCA_E_AGAIN when both slots are in use.  One thread at a time
+ * may submit to a channel. */
+vca_status vca_server_submit_frames(vca_server* s, int32_t id, const vca_frame_ref* frame0, int64_t frame_stride_y,
+                                    int64_t frame_stride_uv, int32_t n_frames, uint64_t tag, void* ready_event);
+/* Up to max finished segments, oldest first; *n receives the count (0 if none). */
+vca_status vca_server_poll(vca_server* s, vca_segment_done* out, int32_t max, int32_t* n);
+/* Features of frame `frame` of channel id (waits for them). */
+vca_status vca_server_read_features(vca_server* s, int32_t id, int64_t frame, vca_frame_features* out);
+vca_status vca_server_stats(vca_server* s, vca_server_stats_t* st);
+/* Finishes every submitted segment, stops the scheduler and frees the channels. */
+vca_status vca_server_destroy(vca_server* s);
+
 /* Frame features from per-block values already on the device, without allocating any device
  * memory.  The paper has no counterpart: this is a runtime convenience for callers that must not
  * call the CUDA allocator on their hot path (a serving loop that has budgeted all device memory

@@ -58,6 +58,18 @@ class VcaFrameRef(ctypes.Structure):
                 ("pitch_y", ctypes.c_int64), ("pitch_uv", ctypes.c_int64)]
 
 
+class VcaSegmentDone(ctypes.Structure):
+    _fields_ = [("channel", ctypes.c_int32), ("status", ctypes.c_int32), ("tag", ctypes.c_uint64),
+                ("first_frame", ctypes.c_int64), ("n_frames", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("submit_ns", ctypes.c_int64), ("ready_ns", ctypes.c_int64)]
+
+
+class VcaServerStats(ctypes.Structure):
+    _fields_ = [("ticks", ctypes.c_int64), ("frames", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("budget_bytes", ctypes.c_int64), ("used_bytes", ctypes.c_int64), ("channels", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
+
+
 class VcaError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{message} (status {status})")
@@ -93,6 +105,16 @@ _PROTOS = {
     "vca_batch_sync": (_P,),
     "vca_batch_launch_count": (_P, ctypes.POINTER(_I64)),
     "vca_batch_destroy": (_P,),
+    "vca_server_create": (ctypes.c_size_t, ctypes.POINTER(_P)),
+    "vca_server_add_channel": (_P, ctypes.POINTER(VcaConfig), _I32, ctypes.POINTER(_I32)),
+    "vca_server_segment_buffer": (_P, _I32, _I32, ctypes.POINTER(VcaFrameRef), ctypes.POINTER(_I64),
+                                  ctypes.POINTER(_I64)),
+    "vca_server_submit": (_P, _I32, _I32, _I32, ctypes.c_uint64, _P),
+    "vca_server_submit_frames": (_P, _I32, ctypes.POINTER(VcaFrameRef), _I64, _I64, _I32, ctypes.c_uint64, _P),
+    "vca_server_poll": (_P, ctypes.POINTER(VcaSegmentDone), _I32, ctypes.POINTER(_I32)),
+    "vca_server_read_features": (_P, _I32, _I64, ctypes.POINTER(VcaFrameFeatures)),
+    "vca_server_stats": (_P, ctypes.POINTER(VcaServerStats)),
+    "vca_server_destroy": (_P,),
 }
 
 
@@ -395,6 +417,71 @@ class Batch:
     def close(self):
         if self.handle:
             vca_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Serving runtime: live channels, segment submission, continuous batching on a native
+    scheduler thread, admission by a device-memory budget."""
+
+    def __init__(self, device_budget_bytes=0):
+        h = _P()
+        _check(lib().vca_server_create(device_budget_bytes, ctypes.byref(h)))
+        self.handle = h.value
+
+    def add_channel(self, width, height, bit_depth=8, block_size=32, low_pass=True, max_segment_frames=120,
+                    pad_mode=VCA_PAD_REPLICATE) -> int:
+        cfg = VcaConfig(width, height, bit_depth, block_size, int(bool(low_pass)), pad_mode, VCA_KERNEL_AUTO, 1)
+        cid = _I32()
+        _check(lib().vca_server_add_channel(_P(self.handle), ctypes.byref(cfg), max_segment_frames, ctypes.byref(cid)))
+        return cid.value
+
+    def submit_frames(self, channel, y, u, v, tag=0) -> int:
+        """Copies (F, H, pitch) / (F, H/2, pitch) frames into a free slot and queues them (tag: the
+        caller's number for the segment).
+        Returns VCA_OK, or VCA_E_AGAIN when both slots of the channel are busy."""
+        es = y.element_size()
+        if u.stride(0) != v.stride(0) or u.stride(-2) != v.stride(-2):
+            raise ValueError("U and V planes must share pitch and frame stride")
+        ref = VcaFrameRef(y.data_ptr(), u.data_ptr(), v.data_ptr(), y.stride(-2) * es, u.stride(-2) * es)
+        st = lib().vca_server_submit_frames(_P(self.handle), channel, ctypes.byref(ref), y.stride(0) * es,
+                                            u.stride(0) * es, y.shape[0], tag, None)
+        if st == VCA_E_AGAIN:
+            return st
+        return _check(st)
+
+    def poll(self, max_items=256):
+        arr = (VcaSegmentDone * max_items)()
+        n = _I32()
+        _check(lib().vca_server_poll(_P(self.handle), arr, max_items, ctypes.byref(n)))
+        return [{"channel": d.channel, "status": d.status, "tag": d.tag, "first_frame": d.first_frame,
+                 "n_frames": d.n_frames, "submit_ns": d.submit_ns, "ready_ns": d.ready_ns} for d in arr[:n.value]]
+
+    def frame_features(self, channel, frame) -> dict:
+        out = VcaFrameFeatures()
+        _check(lib().vca_server_read_features(_P(self.handle), channel, frame, ctypes.byref(out)))
+        return out.as_dict()
+
+    def stats(self) -> dict:
+        st = VcaServerStats()
+        _check(lib().vca_server_stats(_P(self.handle), ctypes.byref(st)))
+        return {k: getattr(st, k) for k in ("ticks", "frames", "launches", "budget_bytes", "used_bytes", "channels")}
+
+    def close(self):
+        if self.handle:
+            _check(lib().vca_server_destroy(_P(self.handle)))
             self.handle = None
 
     def __enter__(self):
