@@ -254,6 +254,7 @@ def time_pushes(an, y, u, v, steps, warmup, stream, barrier):
     start.record(stream)
     for _ in range(steps):
         an.push(y, u, v)
+    vca.vca_stream_join(an.handle)  # the last push's reduction and read-back run on a second stream
     end.record(stream)
     end.synchronize()
     torch.cuda.synchronize()

@@ -142,6 +142,12 @@ vca_status vca_dump_coefficients(vca_analyzer* a, const void* y, const void* u, 
 /* Wait for all of the analyzer's device work. */
 vca_status vca_sync(vca_analyzer* a);
 
+/* The frame reduction and the feature read-back of a push run on a second stream of the
+ * analyzer, overlapping the next push's analysis.  This makes the analyzer's own stream wait
+ * (on the device, without blocking the host) for all of that work, so later work on that stream
+ * -- or an event recorded there -- comes after every queued push is complete. */
+vca_status vca_stream_join(vca_analyzer* a);
+
 /* Cross-frame state (the previous frame's luma block energies that h needs, and
  * the frame counter) as bytes, so a channel can resume with a correct h.
  * Call with buf = NULL to get the size in *len. */
@@ -283,7 +289,9 @@ vca_status vca_server_destroy(vca_server* s);
  * Computes, like the analyzer (Section 2 of the paper), per frame f: E_P = sum_k H_{P,k} /
  * (C N_P^2), L_P = sum_k L_{P,k} / C, h = sum_k |H_{Y,k,f} - H_{Y,k,f-1}| / (C w^2).
  *   block_values  device, [n_frames][6][C] FP32, rows H_Y, L_Y, H_U, L_U, H_V, L_V (C =
- *                 blocks_per_plane, raster block order); read only.
+ *                 blocks_per_plane, raster block order); read only.  Values must lie in
+ *                 [0, 2^30); each is summed exactly when it is a multiple of 2^-23 (every value
+ *                 the analyzer writes is: 0 or at least 1), else rounded to the nearest one.
  *   block_size    luma block size w: 32 or 16 (chroma blocks are w/2).
  *   n_frames      1 .. 256: the frames the fixed scratch holds; more gives VCA_E_ARG.
  *   prev_H_Y      device, C FP32 luma energies of the frame before frame 0, or NULL for h = 0

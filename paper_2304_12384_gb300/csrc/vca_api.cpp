@@ -87,11 +87,17 @@ struct vca_analyzer {
 
   void* d_tables = nullptr;
   DeviceTables tables{};
-  float* d_blockvals = nullptr;  // (max_batch + 1) frames of [6][C]; the last slot serves coefficient dumps
+  float* d_blockvals = nullptr;  // 2 x max_batch + 1 frames of [6][C]: two push buffers, then a dump slot
+  float* last_bv = nullptr;      // block values of the most recent push
+  int bv_slot = 0;               // push buffer of the next push
+  cudaStream_t side = nullptr;   // reduction and feature read-back, overlapping the next analysis
+  cudaEvent_t an_done[2] = {nullptr, nullptr};   // analysis of the push in buffer b finished
+  cudaEvent_t red_done[2] = {nullptr, nullptr};  // reduction that read buffer b finished
+  bool red_recorded[2] = {false, false};
   float* d_prevH[2] = {nullptr, nullptr};
   int cur_prev = 0;
   double* d_feats = nullptr;     // max_batch * FEAT_STRIDE
-  int* d_err = nullptr;          // kernel wait-timeout flag of the current push
+  int* d_err = nullptr;          // kernel wait-timeout flags: one per push buffer, one for dumps
   double* d_red_partials = nullptr;       // frame-reduction scratch
   unsigned int* d_red_counters = nullptr; // one arrival counter per frame, kept at zero between launches
   uint8_t* d_staging = nullptr;  // host frames are copied here
@@ -213,6 +219,7 @@ void destroy(vca_analyzer* a) {
   cudaGetDevice(&prev_dev);
   cudaSetDevice(a->device);
   cudaStreamSynchronize(a->stream);
+  if (a->side) cudaStreamSynchronize(a->side);
   cudaFree(a->d_tables);
   cudaFree(a->d_blockvals);
   cudaFree(a->d_prevH[0]);
@@ -231,6 +238,11 @@ void destroy(vca_analyzer* a) {
   for (auto& e : a->t1_ev)
     if (e) cudaEventDestroy(e);
   if (a->copy_ev) cudaEventDestroy(a->copy_ev);
+  for (int b = 0; b < 2; ++b) {
+    if (a->an_done[b]) cudaEventDestroy(a->an_done[b]);
+    if (a->red_done[b]) cudaEventDestroy(a->red_done[b]);
+  }
+  if (a->side) cudaStreamDestroy(a->side);
   if (prev_dev >= 0) cudaSetDevice(prev_dev);
   delete a;
 }
@@ -330,9 +342,10 @@ vca_status stage_host_frames(vca_analyzer* a, FramePlanes* fp, int n) {
   return VCA_OK;
 }
 
-cudaError_t run_analysis(vca_analyzer* a, const FramePlanes& fp, int n, float* blockvals, int16_t* const zdump[3]) {
+cudaError_t run_analysis(vca_analyzer* a, const FramePlanes& fp, int n, float* blockvals, int16_t* const zdump[3],
+                         int* err) {
   if (a->kernel == VCA_KERNEL_TC)
-    return vca::launch_tc(a->g, fp, n, a->tables, blockvals, zdump, a->d_err, a->stream, &a->launches);
+    return vca::launch_tc(a->g, fp, n, a->tables, blockvals, zdump, err, a->stream, &a->launches);
   return vca::launch_plain(a->g, fp, n, a->tables, blockvals, zdump, a->stream, &a->launches);
 }
 
@@ -534,7 +547,7 @@ vca_status vca_open(const vca_config* cfg, void* cuda_stream, vca_analyzer** out
   a->tables.W_y = reinterpret_cast<const float*>(tb + oWy);
   a->tables.W_c = reinterpret_cast<const float*>(tb + oWc);
 
-  const size_t bv = (size_t)(a->max_batch + 1) * vca::N_ROWS * g.C * sizeof(float);
+  const size_t bv = (size_t)(2 * a->max_batch + 1) * vca::N_ROWS * g.C * sizeof(float);
   OPEN_CUDA(cudaMalloc(&a->d_blockvals, bv), "allocating block values");
   OPEN_CUDA(cudaMemset(a->d_blockvals, 0, bv), "clearing block values");
   for (int i = 0; i < 2; ++i) {
@@ -545,8 +558,14 @@ vca_status vca_open(const vca_config* cfg, void* cuda_stream, vca_analyzer** out
   OPEN_CUDA(cudaMalloc(&a->d_red_partials, vca::reduce_partials_bytes(a->max_batch)), "allocating reduction scratch");
   OPEN_CUDA(cudaMalloc(&a->d_red_counters, (size_t)a->max_batch * sizeof(unsigned int)), "allocating counters");
   OPEN_CUDA(cudaMemset(a->d_red_counters, 0, (size_t)a->max_batch * sizeof(unsigned int)), "clearing counters");
-  OPEN_CUDA(cudaMalloc(&a->d_err, sizeof(int)), "allocating the error flag");
-  OPEN_CUDA(cudaMemset(a->d_err, 0, sizeof(int)), "clearing the error flag");
+  a->last_bv = a->d_blockvals;
+  OPEN_CUDA(cudaMalloc(&a->d_err, 3 * sizeof(int)), "allocating the error flags");
+  OPEN_CUDA(cudaMemset(a->d_err, 0, 3 * sizeof(int)), "clearing the error flags");
+  OPEN_CUDA(cudaStreamCreateWithFlags(&a->side, cudaStreamNonBlocking), "creating the reduction stream");
+  for (int b = 0; b < 2; ++b) {
+    OPEN_CUDA(cudaEventCreateWithFlags(&a->an_done[b], cudaEventDisableTiming), "creating events");
+    OPEN_CUDA(cudaEventCreateWithFlags(&a->red_done[b], cudaEventDisableTiming), "creating events");
+  }
   OPEN_CUDA(cudaMallocHost(&a->h_err, kRing * sizeof(int)), "allocating pinned error flags");
   memset(a->h_err, 0, kRing * sizeof(int));
   OPEN_CUDA(cudaMallocHost(&a->h_ring, (size_t)kRing * a->max_batch * vca::FEAT_STRIDE * sizeof(double)),
@@ -588,21 +607,33 @@ vca_status vca_push_frames(vca_analyzer* a, const void* y, const void* u, const 
   }
   const int slot = a->next_slot;
   const bool timed = a->timing;
-  VCA_CUDA(cudaMemsetAsync(a->d_err, 0, sizeof(int), a->stream), "clearing the error flag");
+  // Analysis on the analyzer's stream into push buffer bs; the reduction and the read-back on the
+  // side stream, so they overlap the next push's analysis (which uses the other buffer).
+  const int bs = a->bv_slot;
+  float* bv = a->d_blockvals + (size_t)bs * a->max_batch * vca::N_ROWS * a->g.C;
+  int* derr = a->d_err + bs;
+  if (a->red_recorded[bs])
+    VCA_CUDA(cudaStreamWaitEvent(a->stream, a->red_done[bs], 0), "ordering after the previous reduction");
+  VCA_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), a->stream), "clearing the error flag");
   if (timed) VCA_CUDA(cudaEventRecord(a->t0_ev[slot], a->stream), "recording timing event");
-  cudaError_t e = run_analysis(a, fp, n_frames, a->d_blockvals, nullptr);
+  cudaError_t e = run_analysis(a, fp, n_frames, bv, nullptr, derr);
   if (e != cudaSuccess) return cuda_fail(e, "launching the analysis kernel");
   if (timed) VCA_CUDA(cudaEventRecord(a->t1_ev[slot], a->stream), "recording timing event");
-  e = vca::launch_reduce(a->g, n_frames, a->d_blockvals, a->d_prevH[a->cur_prev], a->has_prev,
-                         a->d_prevH[a->cur_prev ^ 1], a->d_feats, a->d_red_partials, a->d_red_counters, a->stream,
-                         &a->launches);
+  VCA_CUDA(cudaEventRecord(a->an_done[bs], a->stream), "recording analysis event");
+  VCA_CUDA(cudaStreamWaitEvent(a->side, a->an_done[bs], 0), "ordering the reduction");
+  e = vca::launch_reduce(a->g, n_frames, bv, a->d_prevH[a->cur_prev], a->has_prev, a->d_prevH[a->cur_prev ^ 1],
+                         a->d_feats, a->d_red_partials, a->d_red_counters, a->side, &a->launches);
   if (e != cudaSuccess) return cuda_fail(e, "launching the frame reduction");
   VCA_CUDA(cudaMemcpyAsync(a->h_ring + (size_t)slot * a->max_batch * vca::FEAT_STRIDE, a->d_feats,
-                           (size_t)n_frames * vca::FEAT_STRIDE * sizeof(double), cudaMemcpyDeviceToHost, a->stream),
+                           (size_t)n_frames * vca::FEAT_STRIDE * sizeof(double), cudaMemcpyDeviceToHost, a->side),
            "copying features to the host");
-  VCA_CUDA(cudaMemcpyAsync(a->h_err + slot, a->d_err, sizeof(int), cudaMemcpyDeviceToHost, a->stream),
+  VCA_CUDA(cudaMemcpyAsync(a->h_err + slot, derr, sizeof(int), cudaMemcpyDeviceToHost, a->side),
            "copying the error flag");
-  VCA_CUDA(cudaEventRecord(a->ring_ev[slot], a->stream), "recording feature event");
+  VCA_CUDA(cudaEventRecord(a->ring_ev[slot], a->side), "recording feature event");
+  VCA_CUDA(cudaEventRecord(a->red_done[bs], a->side), "recording reduction event");
+  a->red_recorded[bs] = true;
+  a->bv_slot = bs ^ 1;
+  a->last_bv = bv;
   a->pending.push_back({a->frames_pushed, n_frames, slot, a->has_prev != 0, timed});
   a->next_slot = (slot + 1) % kRing;
   a->cur_prev ^= 1;
@@ -654,8 +685,9 @@ vca_status vca_read_block_values(vca_analyzer* a, int32_t index, float* H_Y, flo
   if (a->last_n == 0 || index < 0 || index >= a->last_n)
     return fail(VCA_E_ARG, "index %d outside the last push (%d frames)", index, a->last_n);
   VCA_CUDA(cudaStreamSynchronize(a->batch ? a->batch->stream : a->stream), "waiting for block values");
+  VCA_CUDA(cudaStreamSynchronize(a->side), "waiting for block values");
   float* const dst[6] = {H_Y, L_Y, H_U, L_U, H_V, L_V};
-  const float* src = a->d_blockvals + (size_t)index * vca::N_ROWS * a->g.C;
+  const float* src = a->last_bv + (size_t)index * vca::N_ROWS * a->g.C;
   for (int r = 0; r < 6; ++r) {
     if (!dst[r]) continue;
     VCA_CUDA(cudaMemcpy(dst[r], src + (size_t)r * a->g.C, (size_t)a->g.C * sizeof(float), cudaMemcpyDeviceToHost),
@@ -674,15 +706,23 @@ vca_status vca_dump_coefficients(vca_analyzer* a, const void* y, const void* u, 
   FramePlanes fp{static_cast<const uint8_t*>(y), static_cast<const uint8_t*>(u), static_cast<const uint8_t*>(v),
                  pitch_y, pitch_uv, 0, 0};
   int16_t* const z[3] = {zy, zu, zv};
-  float* scratch = a->d_blockvals + (size_t)a->max_batch * vca::N_ROWS * a->g.C;
-  cudaError_t e = run_analysis(a, fp, 1, scratch, z);
+  float* scratch = a->d_blockvals + (size_t)2 * a->max_batch * vca::N_ROWS * a->g.C;
+  cudaError_t e = run_analysis(a, fp, 1, scratch, z, a->d_err + 2);
   if (e != cudaSuccess) return cuda_fail(e, "launching the coefficient dump");
+  return VCA_OK;
+}
+
+vca_status vca_stream_join(vca_analyzer* a) {
+  if (!a) return fail(VCA_E_ARG, "analyzer is NULL");
+  for (int b = 0; b < 2; ++b)
+    if (a->red_recorded[b]) VCA_CUDA(cudaStreamWaitEvent(a->stream, a->red_done[b], 0), "joining the reduction stream");
   return VCA_OK;
 }
 
 vca_status vca_sync(vca_analyzer* a) {
   if (!a) return fail(VCA_E_ARG, "analyzer is NULL");
   VCA_CUDA(cudaStreamSynchronize(a->stream), "synchronising the analyzer stream");
+  VCA_CUDA(cudaStreamSynchronize(a->side), "synchronising the reduction stream");
   if (a->batch) VCA_CUDA(cudaStreamSynchronize(a->batch->stream), "synchronising the batch stream");
   return VCA_OK;
 }
@@ -698,6 +738,7 @@ vca_status vca_export_state(vca_analyzer* a, void* buf, size_t* len) {
   vca_status s = catch_up_all(a);
   if (s != VCA_OK) return s;
   VCA_CUDA(cudaStreamSynchronize(a->stream), "waiting before state export");
+  VCA_CUDA(cudaStreamSynchronize(a->side), "waiting before state export");
   StateHeader h{};
   memcpy(h.magic, kStateMagic, 8);
   h.C = a->g.C;
@@ -726,6 +767,7 @@ vca_status vca_import_state(vca_analyzer* a, const void* buf, size_t len) {
   vca_status s = harvest_all(a);
   if (s != VCA_OK) return s;
   VCA_CUDA(cudaStreamSynchronize(a->stream), "waiting before state import");
+  VCA_CUDA(cudaStreamSynchronize(a->side), "waiting before state import");
   VCA_CUDA(cudaMemcpy(a->d_prevH[a->cur_prev], static_cast<const uint8_t*>(buf) + sizeof h,
                       (size_t)h.C * sizeof(float), cudaMemcpyHostToDevice), "restoring h state");
   a->has_prev = h.has_prev != 0;
@@ -821,6 +863,7 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
       return st;
     }
     BATCH_CUDA(cudaStreamSynchronize(members[i]->stream), "waiting for an analyzer's earlier work");
+    BATCH_CUDA(cudaStreamSynchronize(members[i]->side), "waiting for an analyzer's earlier work");
   }
   std::vector<vca::BatchCta> map;
   for (int i = 0; i < n; ++i) {
@@ -909,6 +952,7 @@ vca_status vca_batch_tick(vca_batch* b, const vca_frame_ref* frames) {
     a->has_prev = 1;
     a->frames_pushed += 1;
     a->last_n = 1;
+    a->last_bv = a->d_blockvals;
   }
   b->pending.push_back(std::move(tick));
   b->next_k ^= 1;

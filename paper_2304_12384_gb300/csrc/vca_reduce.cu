@@ -1,10 +1,10 @@
 // Frame reduction of the analyzer (Section 2 of the paper: the seven per-frame features).
 //
 // Each frame is summed by kSlices CTAs.  CTA s takes the blocks [s*C/kSlices, (s+1)*C/kSlices):
-// thread i sums blocks i, i + 256, ... of the slice in FP64, then a fixed shared-memory tree gives
-// the slice's seven partial sums.  The last CTA of the frame to finish (a per-frame arrival
-// counter) adds the kSlices partials in slice order and writes the features, so the result does
-// not depend on scheduling:
+// thread i sums blocks i, i + 256, ... of the slice exactly in fixed point, then a fixed FP64
+// shared-memory tree gives the slice's seven partial sums.  The last CTA of the frame to finish
+// (a per-frame arrival counter) adds the kSlices partials in slice order and writes the
+// features, so the result does not depend on scheduling:
 //   E_P = sum_k H_{P,k} / (C N_P^2), L_P = sum_k L_{P,k} / C,
 //   h_t = sum_k |H_{Y,k,t} - H_{Y,k,t-1}| / (C w^2), and h = 0 without a previous frame.
 // The CTAs of the last frame also copy its luma energies as the next call's previous-frame state
@@ -33,12 +33,27 @@ __device__ __forceinline__ void reduce_slice(const ReduceArgs& a, int f, int sli
   const float* prev = f > 0 ? a.blockvals + (int64_t)(f - 1) * N_ROWS * C + ROW_H_Y * C : a.prevH_in;
   const bool has_prev = f > 0 || a.has_prev;
 
-  double s[kSums] = {0, 0, 0, 0, 0, 0, 0};
+  // Per-thread sums in fixed point, v * 2^23 as an unsigned integer.  Every block value the
+  // analyzer writes is 0 or at least 1 (H sums weights >= 1 times integers |Z| < 2^16; L is the
+  // square root of an integer), so it is a multiple of 2^-23 below 2^30 and converts exactly;
+  // the sums, and |H_t - H_{t-1}|, are then exact integer arithmetic (a thread adds at most
+  // 2^20 / (8 * 256) = 512 values below 2^53).  The per-thread sums enter the FP64 tree below.
+  unsigned long long q[kSums] = {0, 0, 0, 0, 0, 0, 0};
   for (int64_t k = k0 + tid; k < k1; k += kThreads) {
+    unsigned long long v[N_ROWS];
 #pragma unroll
-    for (int r = 0; r < N_ROWS; ++r) s[r] += (double)bv[r * C + k];
-    if (has_prev) s[6] += fabs((double)bv[ROW_H_Y * C + k] - (double)prev[k]);
+    for (int r = 0; r < N_ROWS; ++r) {
+      v[r] = __float2ull_rn(bv[r * C + k] * 8388608.0f);
+      q[r] += v[r];
+    }
+    if (has_prev) {
+      const unsigned long long p = __float2ull_rn(prev[k] * 8388608.0f);
+      q[6] += v[ROW_H_Y] > p ? v[ROW_H_Y] - p : p - v[ROW_H_Y];
+    }
   }
+  double s[kSums];
+#pragma unroll
+  for (int r = 0; r < kSums; ++r) s[r] = (double)q[r] * 1.1920928955078125e-07;  // 2^-23
   if (f == a.nframes - 1) {
     for (int64_t k = k0 + tid; k < k1; k += kThreads) a.prevH_out[k] = bv[ROW_H_Y * C + k];
   }

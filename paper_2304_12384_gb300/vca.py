@@ -91,6 +91,7 @@ _PROTOS = {
     "vca_read_block_values": (_P, _I32, _P, _P, _P, _P, _P, _P),
     "vca_dump_coefficients": (_P, _P, _P, _P, _I64, _I64, _P, _P, _P),
     "vca_sync": (_P,),
+    "vca_stream_join": (_P,),
     "vca_export_state": (_P, _P, ctypes.POINTER(ctypes.c_size_t)),
     "vca_import_state": (_P, _P, ctypes.c_size_t),
     "vca_frames_pushed": (_P, ctypes.POINTER(_I64)),
@@ -232,6 +233,10 @@ def vca_dump_coefficients(a, y, u, v, pitch_y, pitch_uv, zy, zu, zv):
 
 def vca_sync(a):
     return _check(lib().vca_sync(a))
+
+
+def vca_stream_join(a):
+    return _check(lib().vca_stream_join(a))
 
 
 def vca_export_state(a) -> bytes:
