@@ -29,6 +29,11 @@ is used:
   each stage adding 2^(s-1) before an arithmetic right shift;
 * low-pass: only coefficients with u, v < N/2 are computed (stage 1 keeps the
   first N/2 row outputs, stage 2 the first N/2 column outputs);
+* low-pass, downsample reading: every plane is first downsampled by two in each
+  direction (the rounded mean of each 2x2 group, (a + b + c + d + 2) >> 2, edges
+  repeated for odd sizes); the downsampled frame is then analysed with half-size
+  blocks (luma w/2, chroma w/4) on the same block grid, all coefficients, and the
+  normalisations use the half-size blocks;
 * block texture energy H = sum over computed (u,v) != (0,0) of
   w_N(u,v) |Z(u,v)| with w_N(u,v) = exp(|((u+1)(v+1)/N^2)^2 - 1|), N the full
   block size also under low-pass;
@@ -236,6 +241,12 @@ class Config:
     block_size: int = 32
     low_pass: bool = False
     pad_mode: str = "replicate"  # or "skip"
+    downsample: bool = False     # the downsample reading of the low-pass option (excludes low_pass)
+
+    def transform_sizes(self) -> tuple[int, int]:
+        """(luma, chroma) block size of the transform: w, w/2, or w/2, w/4 when downsampling."""
+        w = self.block_size
+        return (w // 2, w // 4) if self.downsample else (w, w // 2)
 
 
 def block_grid(cfg: Config) -> tuple[int, int]:
@@ -272,12 +283,26 @@ def plane_block_values(plane, n: int, nbx: int, nby: int, bit_depth: int, low_pa
     return block_texture_energy(Z, n), block_brightness(Z), Z
 
 
+def downsample_plane(plane: np.ndarray) -> np.ndarray:
+    """Halve a plane in each direction: each output sample is the rounded mean of a 2x2 group,
+    (a + b + c + d + 2) >> 2; a plane of odd height or width repeats its last row or column."""
+    p = np.asarray(plane).astype(np.int64)
+    h, w = p.shape
+    ys = np.minimum(np.arange(2 * ((h + 1) // 2)), h - 1)
+    xs = np.minimum(np.arange(2 * ((w + 1) // 2)), w - 1)
+    q = p[ys][:, xs]
+    s = q[0::2, 0::2] + q[0::2, 1::2] + q[1::2, 0::2] + q[1::2, 1::2]
+    return (s + 2) >> 2
+
+
 def frame_block_values(y, u, v, cfg: Config) -> dict:
     """Per-block H and L of the Y, U and V planes of one frame."""
     nbx, nby = block_grid(cfg)
-    w = cfg.block_size
+    ny, nc = cfg.transform_sizes()
+    if cfg.downsample:
+        y, u, v = downsample_plane(y), downsample_plane(u), downsample_plane(v)
     out = {}
-    for name, plane, n in (("Y", y, w), ("U", u, w // 2), ("V", v, w // 2)):
+    for name, plane, n in (("Y", y, ny), ("U", u, nc), ("V", v, nc)):
         H, L, _ = plane_block_values(plane, n, nbx, nby, cfg.bit_depth, cfg.low_pass)
         out["H_" + name] = H
         out["L_" + name] = L
@@ -296,8 +321,7 @@ def frame_features(values: dict, prev_HY, cfg: Config) -> dict:
     """
     nbx, nby = block_grid(cfg)
     C = nbx * nby
-    w = cfg.block_size
-    c = w // 2
+    w, c = cfg.transform_sizes()
     f = {
         "E_Y": float(np.sum(values["H_Y"])) / (C * w * w),
         "L_Y": float(np.sum(values["L_Y"])) / C,

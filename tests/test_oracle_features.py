@@ -10,7 +10,8 @@ import math
 import numpy as np
 import pytest
 
-from oracle import (Config, analyze_sequence, block_brightness, block_grid, block_texture_energy, energy_weights,
+from oracle import (Config, analyze_sequence, block_brightness, block_grid, block_texture_energy, downsample_plane,
+                    energy_weights,
                     frame_block_values, frame_features, int_dct2, int_dct_matrix, plane_blocks,
                     sequence_features, transform_shifts)
 
@@ -179,3 +180,61 @@ def test_low_pass_features_use_quarter_coefficients():
     blocks = plane_blocks(y, 32, 2, 2)
     Z = int_dct2(blocks, 8)[:, :16, :16]
     np.testing.assert_allclose(lp["H_Y"], block_texture_energy(Z, 32), rtol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# Downsample reading of the low-pass option (Section 2 item 3: "spatially
+# downsampled by a factor of two"): 2x2 rounded mean, then half-size blocks.
+# ---------------------------------------------------------------------------
+
+def test_downsample_rounding_by_hand():
+    # (a + b + c + d + 2) >> 2: 11 -> 3, 2 -> 1 (a half rounds up), 1 -> 0, 1020 -> 255.
+    assert downsample_plane(np.array([[1, 2], [3, 5]])).tolist() == [[3]]
+    assert downsample_plane(np.array([[0, 0], [0, 2]])).tolist() == [[1]]
+    assert downsample_plane(np.array([[0, 0], [0, 1]])).tolist() == [[0]]
+    assert downsample_plane(np.full((2, 2), 255)).tolist() == [[255]]
+
+
+def test_downsample_odd_sizes_repeat_the_edge():
+    # 3 x 3 -> 2 x 2; the last row and column pair with themselves.
+    p = np.array([[0, 4, 8], [4, 8, 12], [8, 12, 16]])
+    assert downsample_plane(p).tolist() == [[4, 10], [10, 16]]
+
+
+def test_downsample_inverts_pixel_doubling():
+    rng = np.random.default_rng(7)
+    base = rng.integers(0, 1024, size=(9, 13))
+    doubled = np.repeat(np.repeat(base, 2, axis=0), 2, axis=1)
+    assert np.array_equal(downsample_plane(doubled), base)
+
+
+@pytest.mark.parametrize("bit_depth", [8, 10])
+def test_downsample_reading_equals_half_size_analysis_of_the_base_frame(bit_depth):
+    # A frame made by pixel doubling a base frame, analysed with the downsample reading and
+    # w = 32, is the base frame analysed with w = 16 on the same block grid (both pinned paths).
+    rng = np.random.default_rng(11 + bit_depth)
+    hi = (1 << bit_depth) - 1
+    W, H = 96, 80  # base 48 x 40: luma grid 3 x 3 with a partial row
+    base = [(rng.integers(0, hi + 1, size=(H // 2, W // 2)), rng.integers(0, hi + 1, size=(H // 4, W // 4)),
+             rng.integers(0, hi + 1, size=(H // 4, W // 4))) for _ in range(3)]
+    up = [tuple(np.repeat(np.repeat(p, 2, axis=0), 2, axis=1) for p in f) for f in base]
+    got = analyze_sequence(up, Config(W, H, bit_depth, 32, downsample=True))
+    exp = analyze_sequence(base, Config(W // 2, H // 2, bit_depth, 16))
+    assert got == exp
+
+
+def test_downsample_reading_normalises_with_half_size_blocks():
+    # One textured block: E_Y = H / (C (w/2)^2) with H of the 16 x 16 transform of the
+    # downsampled block.
+    W = H = 64
+    y = np.full((H, W), 100)
+    y[:32, :32] = np.tile(np.array([100, 100, 140, 140]), (32, 8))  # alternates column by column after halving
+    u = np.full((H // 2, W // 2), 128)
+    cfg = Config(W, H, 8, 32, downsample=True)
+    f = analyze_sequence([(y, u, u)], cfg)[0]
+    d = downsample_plane(y)
+    Z = int_dct2(plane_blocks(d, 16, 2, 2), 8)
+    Hb = block_texture_energy(Z, 16)
+    assert Hb[0] > 0 and Hb[1:].tolist() == [0.0, 0.0, 0.0]
+    assert f["E_Y"] == pytest.approx(Hb[0] / (4 * 16 * 16), rel=1e-15)
+    assert f["E_U"] == 0.0
