@@ -384,14 +384,15 @@ def run_extras(args, an, y, u, v, frames, stream, kern, lp, device):
 
     # Other block-size / low-pass variants and the plain CUDA-core form, same frames.
     variants = {}
+    lp_name = {False: "full", True: "lowpass", "downsample": "downsample"}
     for (bs, vlp, vk) in ((32, True, vca.VCA_KERNEL_PLAIN), (32, False, kern), (16, True, kern), (16, False, kern),
-                          (32, False, vca.VCA_KERNEL_PLAIN)):
+                          (32, False, vca.VCA_KERNEL_PLAIN), (32, "downsample", vca.VCA_KERNEL_AUTO)):
         try:
             a2 = vca.Analyzer(W, H, 8, bs, vlp, kernel=vk, max_batch=args.frames, stream=stream.cuda_stream)
         except vca.VcaError as e:
-            variants[f"w{bs}_{'lp' if vlp else 'full'}_{vk}"] = f"unsupported: {e}"
+            variants[f"w{bs}_{lp_name[vlp]}_{vk}"] = f"unsupported: {e}"
             continue
-        name = f"w{bs}_{'lowpass' if vlp else 'full'}_{ {1: 'plain', 2: 'tc'}[a2.kernel] }"
+        name = f"w{bs}_{lp_name[vlp]}_{ {1: 'plain', 2: 'tc'}[a2.kernel] }"
         ms, kms, _ = time_pushes(a2, y, u, v, max(3, args.steps // 3), 2, stream, lambda: None)
         n = max(3, args.steps // 3) * args.frames
         variants[name] = {"fps": n / (ms / 1000.0), "kernel_ms_per_launch": kms,

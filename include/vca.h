@@ -6,8 +6,12 @@
  * Analysis for Efficient Encoding in Adaptive Video Streaming" (GMSys '23):
  * the luma texture energy E_Y, its temporal gradient h, the luminescence L_Y,
  * the chroma texture energies E_U, E_V and the chrominances L_U, L_V.  Section 2
- * item (3) adds the low-pass option (only the low-frequency quarter of each
- * block's coefficients is computed).
+ * item (3) adds the low-pass option, which the library offers in two readings:
+ * only the low-frequency quarter of each block's coefficients is computed
+ * (VCA_LOWPASS_QUARTER), or every plane is first halved in each direction (rounded
+ * 2x2 mean, (a + b + c + d + 2) >> 2, odd edges repeated) and analysed with half-size
+ * blocks on the same block grid (VCA_LOWPASS_DOWNSAMPLE; the normalisations use the
+ * half-size blocks).
  *
  * Definitions used (the paper names the features; these are the readings the
  * library implements, identically to the test oracle):
@@ -63,6 +67,7 @@ typedef enum vca_status {
 } vca_status;
 
 enum { VCA_PAD_REPLICATE = 0, VCA_PAD_SKIP = 1 };
+enum { VCA_LOWPASS_OFF = 0, VCA_LOWPASS_QUARTER = 1, VCA_LOWPASS_DOWNSAMPLE = 2 };
 enum { VCA_KERNEL_AUTO = 0, VCA_KERNEL_PLAIN = 1, VCA_KERNEL_TC = 2 };
 
 /* Analyzer configuration (Section 2: one analyzer per video). */
@@ -71,7 +76,9 @@ typedef struct vca_config {
   int32_t height;      /* luma height in samples, even, >= 2 */
   int32_t bit_depth;   /* 8 or 10 */
   int32_t block_size;  /* luma block size w: 16 or 32; chroma blocks are w/2 */
-  int32_t low_pass;    /* 0 = all coefficients, 1 = only u, v < N/2 (Section 2 item (3)) */
+  int32_t low_pass;    /* VCA_LOWPASS_OFF: all coefficients; VCA_LOWPASS_QUARTER: only u, v < N/2;
+                          VCA_LOWPASS_DOWNSAMPLE: halved planes, w/2 and w/4 blocks (block_size 32
+                          only; not in batches) -- Section 2 item (3) */
   int32_t pad_mode;    /* VCA_PAD_REPLICATE (default) or VCA_PAD_SKIP */
   int32_t kernel;      /* VCA_KERNEL_AUTO, VCA_KERNEL_PLAIN (CUDA cores) or VCA_KERNEL_TC (tensor cores) */
   int32_t max_batch;   /* most frames one vca_push_frames call may carry; 0 selects 64 */
@@ -132,9 +139,10 @@ vca_status vca_read_block_values(vca_analyzer* a, int32_t index, float* H_Y, flo
 
 /* Quantised coefficients Z of one frame, computed by the analyzer's kernel with
  * the coefficient dump enabled (bit-exact integers; parity checks).  zy, zu, zv
- * are device buffers of C*Nk*Nk int16 each (Nk = N, or N/2 with low_pass; N = w
- * for Y, w/2 for U, V), block-major, then row u, then column v.  Planes are on
- * the device.  Does not change the analyzer's frame count or h state. */
+ * are device buffers of C*Nk*Nk int16 each (Nk = N, or N/2 with VCA_LOWPASS_QUARTER;
+ * N = w for Y, w/2 for U, V, halved again with VCA_LOWPASS_DOWNSAMPLE), block-major,
+ * then row u, then column v.  Planes are on the device.  Does not change the
+ * analyzer's frame count or h state. */
 vca_status vca_dump_coefficients(vca_analyzer* a, const void* y, const void* u, const void* v,
                                  int64_t pitch_y, int64_t pitch_uv,
                                  int16_t* zy, int16_t* zu, int16_t* zv);

@@ -79,7 +79,12 @@ struct StateHeader {
 struct vca_analyzer {
   vca_batch* batch = nullptr;  // the batch this analyzer belongs to, if any
   vca_config cfg{};
-  Geometry g{};
+  Geometry g{};    // geometry the analysis runs on (the halved planes under the downsample reading)
+  Geometry gin{};  // geometry of the pushed frames
+  uint8_t* d_down = nullptr;     // halved planes of up to max_batch frames (downsample reading)
+  size_t down_fbytes = 0;        // bytes per frame in d_down: Y | U | V
+  int64_t down_pitch_y = 0, down_pitch_uv = 0;
+  size_t down_off_u = 0, down_off_v = 0;
   int kernel = VCA_KERNEL_PLAIN;
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -174,7 +179,7 @@ struct vca_batch {
 
 namespace {
 
-vca_status check_config(const vca_config* c, Geometry* g) {
+vca_status check_config(const vca_config* c, Geometry* g, Geometry* gin = nullptr) {
   if (!c) return fail(VCA_E_ARG, "config is NULL");
   if (c->width < 2 || c->height < 2 || (c->width & 1) || (c->height & 1) || c->width > 16384 ||
       c->height > 16384)
@@ -184,7 +189,10 @@ vca_status check_config(const vca_config* c, Geometry* g) {
     if (c->block_size == 8) return fail(VCA_E_UNSUPPORTED, "block_size 8 (4x4 chroma) is not supported");
     return fail(VCA_E_ARG, "block_size must be 16 or 32");
   }
-  if (c->low_pass != 0 && c->low_pass != 1) return fail(VCA_E_ARG, "low_pass must be 0 or 1");
+  if (c->low_pass < VCA_LOWPASS_OFF || c->low_pass > VCA_LOWPASS_DOWNSAMPLE)
+    return fail(VCA_E_ARG, "low_pass must be 0, 1 or 2");
+  if (c->low_pass == VCA_LOWPASS_DOWNSAMPLE && c->block_size != 32)
+    return fail(VCA_E_UNSUPPORTED, "the downsample reading needs block_size 32 (16 x 16 / 8 x 8 blocks after halving)");
   if (c->pad_mode != VCA_PAD_REPLICATE && c->pad_mode != VCA_PAD_SKIP) return fail(VCA_E_ARG, "bad pad_mode");
   if (c->kernel < VCA_KERNEL_AUTO || c->kernel > VCA_KERNEL_TC) return fail(VCA_E_ARG, "bad kernel selector");
   if (c->max_batch < 0 || c->max_batch > kMaxBatch) return fail(VCA_E_ARG, "max_batch must be in [0, %d]", kMaxBatch);
@@ -206,9 +214,21 @@ vca_status check_config(const vca_config* c, Geometry* g) {
   }
   q.C = (int64_t)q.nbx * q.nby;
   if (q.C <= 0) return fail(VCA_E_ARG, "frame smaller than one block with pad_mode skip");
-  q.low_pass = c->low_pass != 0;
+  q.low_pass = c->low_pass == VCA_LOWPASS_QUARTER;
   vca::transform_shifts(q.w, q.B, &q.s1y, &q.s2y);
   vca::transform_shifts(q.nc, q.B, &q.s1c, &q.s2c);
+  if (gin) *gin = q;
+  if (c->low_pass == VCA_LOWPASS_DOWNSAMPLE) {
+    // Halved planes, half-size blocks, same block grid (ceil(ceil(W/2) / (w/2)) = ceil(W/w)).
+    q.W = (q.W + 1) / 2;
+    q.H = (q.H + 1) / 2;
+    q.cw = (q.cw + 1) / 2;
+    q.ch = (q.ch + 1) / 2;
+    q.w /= 2;
+    q.nc /= 2;
+    vca::transform_shifts(q.w, q.B, &q.s1y, &q.s2y);
+    vca::transform_shifts(q.nc, q.B, &q.s1c, &q.s2c);
+  }
   if (g) *g = q;
   return VCA_OK;
 }
@@ -230,6 +250,7 @@ void destroy(vca_analyzer* a) {
   cudaFree(a->d_red_counters);
   if (a->h_err) cudaFreeHost(a->h_err);
   cudaFree(a->d_staging);
+  cudaFree(a->d_down);
   if (a->h_ring) cudaFreeHost(a->h_ring);
   for (auto& e : a->ring_ev)
     if (e) cudaEventDestroy(e);
@@ -299,7 +320,7 @@ vca_status harvest_all(vca_analyzer* a) {
 
 vca_status check_planes(const vca_analyzer* a, const void* y, const void* u, const void* v, int64_t pitch_y,
                         int64_t pitch_uv) {
-  const Geometry& g = a->g;
+  const Geometry& g = a->gin;
   if (!y || !u || !v) return fail(VCA_E_ARG, "plane pointer is NULL");
   if (!aligned16(y) || !aligned16(u) || !aligned16(v)) return fail(VCA_E_ARG, "plane pointers must be 16-byte aligned");
   if (pitch_y < (int64_t)g.W * g.bps || pitch_uv < (int64_t)g.cw * g.bps)
@@ -311,7 +332,7 @@ vca_status check_planes(const vca_analyzer* a, const void* y, const void* u, con
 
 // Copies n host frames into the staging buffer (allocating it on first use) and points fp at it.
 vca_status stage_host_frames(vca_analyzer* a, FramePlanes* fp, int n) {
-  const Geometry& g = a->g;
+  const Geometry& g = a->gin;
   const size_t py = round_up((size_t)g.W * g.bps, 64), pc = round_up((size_t)g.cw * g.bps, 64);
   const size_t ybytes = round_up(py * g.H, 256), cbytes = round_up(pc * g.ch, 256);
   const size_t fbytes = ybytes + 2 * cbytes;
@@ -342,8 +363,32 @@ vca_status stage_host_frames(vca_analyzer* a, FramePlanes* fp, int n) {
   return VCA_OK;
 }
 
-cudaError_t run_analysis(vca_analyzer* a, const FramePlanes& fp, int n, float* blockvals, int16_t* const zdump[3],
+cudaError_t run_analysis(vca_analyzer* a, const FramePlanes& fp_in, int n, float* blockvals, int16_t* const zdump[3],
                          int* err) {
+  FramePlanes fp = fp_in;
+  if (a->cfg.low_pass == VCA_LOWPASS_DOWNSAMPLE) {
+    vca::DownArgs d{};
+    const uint8_t* src[3] = {fp_in.y, fp_in.u, fp_in.v};
+    const size_t off[3] = {0, a->down_off_u, a->down_off_v};
+    for (int p = 0; p < 3; ++p) {
+      vca::DownPlane& P = d.p[p];
+      P.src = src[p];
+      P.src_pitch = p == 0 ? fp_in.pitch_y : fp_in.pitch_uv;
+      P.src_fstride = p == 0 ? fp_in.fstride_y : fp_in.fstride_uv;
+      P.dst = a->d_down + off[p];
+      P.dst_pitch = p == 0 ? a->down_pitch_y : a->down_pitch_uv;
+      P.dst_fstride = (int64_t)a->down_fbytes;
+      P.w = p == 0 ? a->gin.W : a->gin.cw;
+      P.h = p == 0 ? a->gin.H : a->gin.ch;
+      P.wd = p == 0 ? a->g.W : a->g.cw;
+      P.hd = p == 0 ? a->g.H : a->g.ch;
+    }
+    cudaError_t e = vca::launch_downsample(d, n, a->g.bps, a->stream);
+    if (e != cudaSuccess) return e;
+    ++a->launches;
+    fp = FramePlanes{a->d_down, a->d_down + a->down_off_u, a->d_down + a->down_off_v, a->down_pitch_y,
+                     a->down_pitch_uv, (int64_t)a->down_fbytes, (int64_t)a->down_fbytes};
+  }
   if (a->kernel == VCA_KERNEL_TC)
     return vca::launch_tc(a->g, fp, n, a->tables, blockvals, zdump, err, a->stream, &a->launches);
   return vca::launch_plain(a->g, fp, n, a->tables, blockvals, zdump, a->stream, &a->launches);
@@ -497,8 +542,8 @@ vca_status vca_block_count(const vca_config* cfg, int64_t* blocks_x, int64_t* bl
 vca_status vca_open(const vca_config* cfg, void* cuda_stream, vca_analyzer** out) {
   if (!out) return fail(VCA_E_ARG, "out is NULL");
   *out = nullptr;
-  Geometry g{};
-  vca_status s = check_config(cfg, &g);
+  Geometry g{}, gin{};
+  vca_status s = check_config(cfg, &g, &gin);
   if (s != VCA_OK) return s;
   int kernel = cfg->kernel;
   if (kernel == VCA_KERNEL_AUTO) kernel = vca::tc_supported(g) ? VCA_KERNEL_TC : VCA_KERNEL_PLAIN;
@@ -509,6 +554,7 @@ vca_status vca_open(const vca_config* cfg, void* cuda_stream, vca_analyzer** out
   if (!a) return fail(VCA_E_NOMEM, "host allocation failed");
   a->cfg = *cfg;
   a->g = g;
+  a->gin = gin;
   a->kernel = kernel;
   a->stream = (cudaStream_t)cuda_stream;
   a->max_batch = cfg->max_batch > 0 ? cfg->max_batch : kDefaultBatch;
@@ -559,6 +605,14 @@ vca_status vca_open(const vca_config* cfg, void* cuda_stream, vca_analyzer** out
   OPEN_CUDA(cudaMalloc(&a->d_red_counters, (size_t)a->max_batch * sizeof(unsigned int)), "allocating counters");
   OPEN_CUDA(cudaMemset(a->d_red_counters, 0, (size_t)a->max_batch * sizeof(unsigned int)), "clearing counters");
   a->last_bv = a->d_blockvals;
+  if (cfg->low_pass == VCA_LOWPASS_DOWNSAMPLE) {
+    a->down_pitch_y = (int64_t)round_up((size_t)g.W * g.bps, 256);
+    a->down_pitch_uv = (int64_t)round_up((size_t)g.cw * g.bps, 256);
+    a->down_off_u = round_up((size_t)a->down_pitch_y * g.H, 256);
+    a->down_off_v = a->down_off_u + round_up((size_t)a->down_pitch_uv * g.ch, 256);
+    a->down_fbytes = a->down_off_v + round_up((size_t)a->down_pitch_uv * g.ch, 256);
+    OPEN_CUDA(cudaMalloc(&a->d_down, a->down_fbytes * a->max_batch), "allocating the downsampled frames");
+  }
   OPEN_CUDA(cudaMalloc(&a->d_err, 3 * sizeof(int)), "allocating the error flags");
   OPEN_CUDA(cudaMemset(a->d_err, 0, 3 * sizeof(int)), "clearing the error flags");
   OPEN_CUDA(cudaStreamCreateWithFlags(&a->side, cudaStreamNonBlocking), "creating the reduction stream");
@@ -590,7 +644,7 @@ vca_status vca_push_frames(vca_analyzer* a, const void* y, const void* u, const 
   if (s != VCA_OK) return s;
   if (n_frames > 1 && ((frame_stride_y & 15) || (frame_stride_uv & 15) || frame_stride_y <= 0 || frame_stride_uv <= 0))
     return fail(VCA_E_ARG, "frame strides must be positive multiples of 16 bytes");
-  if (n_frames > 1 && (frame_stride_y < pitch_y * a->g.H || frame_stride_uv < pitch_uv * a->g.ch))
+  if (n_frames > 1 && (frame_stride_y < pitch_y * a->gin.H || frame_stride_uv < pitch_uv * a->gin.ch))
     return fail(VCA_E_ARG, "frame strides must not be smaller than one plane (frames may not overlap)");
   if (on_device != 0 && on_device != 1) return fail(VCA_E_ARG, "on_device must be 0 or 1");
 
@@ -744,7 +798,7 @@ vca_status vca_export_state(vca_analyzer* a, void* buf, size_t* len) {
   h.C = a->g.C;
   h.frames = a->frames_pushed;
   h.has_prev = a->has_prev;
-  h.block_size = a->g.w;
+  h.block_size = a->cfg.block_size;
   for (int j = 0; j < 7; ++j) h.seq_sum[j] = a->seq_sum[j];
   h.seq_n = a->seq_n;
   h.seq_nh = a->seq_nh;
@@ -761,7 +815,7 @@ vca_status vca_import_state(vca_analyzer* a, const void* buf, size_t len) {
   StateHeader h;
   memcpy(&h, buf, sizeof h);
   if (memcmp(h.magic, kStateMagic, 8) != 0) return fail(VCA_E_ARG, "not an analyzer state buffer");
-  if (h.C != a->g.C || h.block_size != a->g.w) return fail(VCA_E_ARG, "state belongs to another block grid");
+  if (h.C != a->g.C || h.block_size != a->cfg.block_size) return fail(VCA_E_ARG, "state belongs to another block grid");
   if (len < sizeof h + (size_t)h.C * sizeof(float) || h.frames < 0) return fail(VCA_E_ARG, "truncated state buffer");
   if (a->batch) return fail(VCA_E_STATE, "the analyzer belongs to a batch");
   vca_status s = harvest_all(a);
@@ -833,6 +887,8 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
     if (a->device != members[0]->device) return fail(VCA_E_ARG, "analyzers of a batch must share one device");
     if (a->g.w != members[0]->g.w || a->g.low_pass != members[0]->g.low_pass)
       return fail(VCA_E_ARG, "analyzers of a batch must share block size and low_pass");
+    if (a->cfg.low_pass == VCA_LOWPASS_DOWNSAMPLE)
+      return fail(VCA_E_UNSUPPORTED, "the downsample reading is not available in batches");
   }
   vca_batch* b = new (std::nothrow) vca_batch();
   if (!b) return fail(VCA_E_NOMEM, "host allocation failed");

@@ -133,6 +133,21 @@ constexpr int plain_blocks_per_cta(int N) { return 4 * (32 / N); }
 cudaError_t launch_batch_plain(const BatchCta* d_map, int n_cta, const BatchMemberArgs* d_args, int w, bool low_pass,
                                cudaStream_t s);
 
+// One plane of the 2x2 downsample: n frames of w x h samples at src (pitch, frame stride in
+// bytes) -> wd x hd = ceil(w/2) x ceil(h/2) samples at dst.
+struct DownPlane {
+  const uint8_t* src;
+  int64_t src_pitch, src_fstride;
+  uint8_t* dst;
+  int64_t dst_pitch, dst_fstride;
+  int w, h, wd, hd;
+};
+struct DownArgs {
+  DownPlane p[3];  // Y, U, V
+};
+// Halves the three planes of n frames (the downsample reading of the low-pass option).
+cudaError_t launch_downsample(const DownArgs& a, int nframes, int bps, cudaStream_t s);
+
 // Sets the calling thread's vca_last_error message.
 void record_error(const char* msg);
 

@@ -24,6 +24,9 @@ VCA_E_STATE = -7
 
 VCA_PAD_REPLICATE = 0
 VCA_PAD_SKIP = 1
+VCA_LOWPASS_OFF = 0
+VCA_LOWPASS_QUARTER = 1
+VCA_LOWPASS_DOWNSAMPLE = 2
 VCA_KERNEL_AUTO = 0
 VCA_KERNEL_PLAIN = 1
 VCA_KERNEL_TC = 2
@@ -298,7 +301,8 @@ class Analyzer:
 
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
-        self.cfg = VcaConfig(width, height, bit_depth, block_size, int(bool(low_pass)), pad_mode, kernel, max_batch)
+        lp = VCA_LOWPASS_DOWNSAMPLE if low_pass in ("downsample", VCA_LOWPASS_DOWNSAMPLE) else int(bool(low_pass))
+        self.cfg = VcaConfig(width, height, bit_depth, block_size, lp, pad_mode, kernel, max_batch)
         self.handle = vca_open(self.cfg, stream)
         self.blocks_x, self.blocks_y = vca_block_count(self.cfg)
         self.C = self.blocks_x * self.blocks_y
@@ -358,7 +362,7 @@ class Analyzer:
         import torch
 
         w = self.cfg.block_size
-        nk_y = w // 2 if self.cfg.low_pass else w
+        nk_y = w // 2 if self.cfg.low_pass else w  # quarter: N/2 coefficients; downsample: w/2 blocks
         nk_c = nk_y // 2
         zy = torch.empty((self.C, nk_y, nk_y), dtype=torch.int16, device=y.device)
         zu = torch.empty((self.C, nk_c, nk_c), dtype=torch.int16, device=y.device)

@@ -226,3 +226,32 @@ def test_argument_errors_on_device(vca, kernel):
         assert an.frame_features(0)["h"] == 0.0
     finally:
         an.close()
+
+
+# Downsample reading of the low-pass option: halved planes (rounded 2x2 mean, odd edges
+# repeated) analysed with 16 x 16 / 8 x 8 blocks on the 32-block grid.
+@pytest.mark.parametrize("bit_depth", [8, 10])
+@pytest.mark.parametrize("size", [(640, 352), (200, 120), (202, 118)])
+def test_downsample_reading(vca, bit_depth, size):
+    w, h = size
+    frames = frames_list(SequenceSpec(w, h, 5, 41, bit_depth=bit_depth, sigma=4.0, cuts=(3,)))
+    run_and_compare(vca, "plain", frames, width=w, height=h, bit_depth=bit_depth, low_pass="downsample",
+                    dump_frames=(0, 3))
+
+
+def test_downsample_reading_hd(vca):
+    frames = frames_list(hd_spec(2, 3))
+    run_and_compare(vca, "plain", frames, width=1920, height=1080, low_pass="downsample", dump_frames=(2,),
+                    block_frames=(0,))
+
+
+def test_downsample_reading_rules(vca):
+    an = vca.Analyzer(640, 352, 8, 32, "downsample")
+    assert an.kernel == vca.VCA_KERNEL_PLAIN
+    an.close()
+    for kw in ({"block_size": 16}, {"kernel": vca.VCA_KERNEL_TC}):
+        args = dict(block_size=32, kernel=vca.VCA_KERNEL_AUTO)
+        args.update(kw)
+        with pytest.raises(vca.VcaError) as ei:
+            vca.Analyzer(640, 352, 8, args["block_size"], "downsample", kernel=args["kernel"])
+        assert ei.value.status == vca.VCA_E_UNSUPPORTED

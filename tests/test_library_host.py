@@ -54,7 +54,8 @@ def test_status_strings(libvca):
     ((3840, 2160, 12, 32, 0, 0, 0, 64), -1),  # bit depth
     ((3840, 2160, 8, 24, 0, 0, 0, 64), -1),   # block size
     ((3840, 2160, 8, 8, 0, 0, 0, 64), -2),    # 4x4 chroma blocks unsupported
-    ((3840, 2160, 8, 32, 2, 0, 0, 64), -1),   # low_pass flag
+    ((3840, 2160, 8, 32, 3, 0, 0, 64), -1),   # low_pass flag
+    ((3840, 2160, 8, 16, 2, 0, 0, 64), -2),   # downsample reading needs block 32
     ((3840, 2160, 8, 32, 0, 5, 0, 64), -1),   # pad mode
     ((3840, 2160, 8, 32, 0, 0, 7, 64), -1),   # kernel selector
     ((3840, 2160, 8, 32, 0, 0, 0, 99999), -1),

@@ -14,8 +14,8 @@ Tolerance (per feature, FP32 block arithmetic against the FP64 oracle):
 
 import numpy as np
 
-from oracle import (Config, analyze_sequence, block_grid, frame_block_values, int_dct2, plane_blocks,
-                    sequence_features)
+from oracle import (Config, analyze_sequence, block_grid, downsample_plane, frame_block_values, int_dct2,
+                    plane_blocks, sequence_features)
 from synth import pack_planes
 
 FEATURES = ("E_Y", "h", "L_Y", "E_U", "E_V", "L_U", "L_V")
@@ -53,18 +53,20 @@ def to_host_pinned(frames, pitch_align=64):
 
 def oracle_config(an) -> Config:
     c = an.cfg
-    return Config(c.width, c.height, c.bit_depth, c.block_size, bool(c.low_pass),
-                  "skip" if c.pad_mode == 1 else "replicate")
+    return Config(c.width, c.height, c.bit_depth, c.block_size, c.low_pass == 1,
+                  "skip" if c.pad_mode == 1 else "replicate", downsample=c.low_pass == 2)
 
 
 def oracle_coefficients(frame, cfg: Config):
     nbx, nby = block_grid(cfg)
     y, u, v = frame
-    w = cfg.block_size
+    if cfg.downsample:
+        y, u, v = downsample_plane(y), downsample_plane(u), downsample_plane(v)
+    ny, nc = cfg.transform_sizes()
     return {
-        "Y": int_dct2(plane_blocks(y, w, nbx, nby), cfg.bit_depth, cfg.low_pass),
-        "U": int_dct2(plane_blocks(u, w // 2, nbx, nby), cfg.bit_depth, cfg.low_pass),
-        "V": int_dct2(plane_blocks(v, w // 2, nbx, nby), cfg.bit_depth, cfg.low_pass),
+        "Y": int_dct2(plane_blocks(y, ny, nbx, nby), cfg.bit_depth, cfg.low_pass),
+        "U": int_dct2(plane_blocks(u, nc, nbx, nby), cfg.bit_depth, cfg.low_pass),
+        "V": int_dct2(plane_blocks(v, nc, nbx, nby), cfg.bit_depth, cfg.low_pass),
     }
 
 
