@@ -19,10 +19,12 @@ The formulas themselves sit in the VCA reference that the paper cites and does
 not reproduce.  Every definition below is therefore a *reading*, stated where it
 is used:
 
-* input: planar Y, U, V (4:2:0), integer samples of bit depth B in {8, 10};
-* block grid: luma w x w blocks, chroma (w/2) x (w/2) blocks on the same
-  (co-located) grid; partial blocks at the right/bottom edge are completed by
-  repeating the last row/column ("replicate"), or dropped ("skip");
+* input: planar Y, U, V, integer samples of bit depth B in {8, 10, 12}; chroma
+  4:2:0 (planes of half width and height) or 4:4:4 (full-size planes);
+* block grid: luma w x w blocks, chroma blocks covering the same picture area
+  ((w/2) x (w/2) samples in 4:2:0, w x w in 4:4:4) on the same (co-located)
+  grid; partial blocks at the right/bottom edge are completed by repeating the
+  last row/column ("replicate"), or dropped ("skip");
 * integer DCT matrix M_N[k][n] = round_half_away(64 sqrt(N) alpha_k
   cos(pi (2n+1) k / 2N)) and the two-stage forward transform of HEVC encoders:
   rows first with shift s1 = log2 N + B - 9, then columns with s2 = log2 N + 6,
@@ -242,11 +244,14 @@ class Config:
     low_pass: bool = False
     pad_mode: str = "replicate"  # or "skip"
     downsample: bool = False     # the downsample reading of the low-pass option (excludes low_pass)
+    chroma_format: str = "420"   # or "444"
 
     def transform_sizes(self) -> tuple[int, int]:
-        """(luma, chroma) block size of the transform: w, w/2, or w/2, w/4 when downsampling."""
+        """(luma, chroma) block size of the transform: w and w/2 (4:2:0) or w (4:4:4), each
+        halved when downsampling."""
         w = self.block_size
-        return (w // 2, w // 4) if self.downsample else (w, w // 2)
+        c = w if self.chroma_format == "444" else w // 2
+        return (w // 2, c // 2) if self.downsample else (w, c)
 
 
 def block_grid(cfg: Config) -> tuple[int, int]:
@@ -260,7 +265,9 @@ def block_grid(cfg: Config) -> tuple[int, int]:
 
 
 def chroma_shape(cfg: Config) -> tuple[int, int]:
-    """(height, width) of a 4:2:0 chroma plane."""
+    """(height, width) of a chroma plane: half size in 4:2:0, full size in 4:4:4."""
+    if cfg.chroma_format == "444":
+        return cfg.height, cfg.width
     return (cfg.height + 1) // 2, (cfg.width + 1) // 2
 
 

@@ -15,7 +15,10 @@ Content model (one "scene" = one parameter draw; a scene cut draws a new one):
   random walk (dx, dy uniform in [-m, m]) or a constant global pan;
 * optional flat regions: block-aligned rectangles fixed on screen, filled with
   a constant and no noise (whole analyzer blocks in all three planes are flat);
-* 10-bit: the 8-bit model scaled by 4 (noise sigma too), clipped to [64, 940].
+* 10-bit / 12-bit: the 8-bit model scaled by 4 / 16 (noise sigma too), clipped to
+  [64, 940] / [256, 3760];
+* chroma format 4:2:0 (default: chroma planes of half width and height) or 4:4:4
+  (full-size chroma planes, rendered at full resolution).
 
 Everything is a pure function of the seed; the same call gives the same frames on
 the same machine.  This module holds none of the analyzer's arithmetic.
@@ -70,6 +73,7 @@ class SequenceSpec:
     n_patches: tuple = (3, 6)
     flat_fraction: float = 0.0           # share of the area made of flat, noise-free blocks
     flat_align: int = 32                 # luma alignment of the flat rectangles
+    chroma_format: str = "420"           # "420" or "444"
     extra: dict = field(default_factory=dict)
 
 
@@ -153,8 +157,9 @@ def generate(spec: SequenceSpec, start: int = 0, stop: int | None = None):
     """
     stop = spec.n_frames if stop is None else min(stop, spec.n_frames)
     W, H = spec.width, spec.height
-    cw, ch = (W + 1) // 2, (H + 1) // 2
-    scale = 4 if spec.bit_depth == 10 else 1
+    full_chroma = spec.chroma_format == "444"
+    cw, ch = (W, H) if full_chroma else ((W + 1) // 2, (H + 1) // 2)
+    scale = 1 << (spec.bit_depth - 8)
     dtype = np.uint16 if spec.bit_depth > 8 else np.uint8
     cuts = set(spec.cuts)
     if spec.cut_every:
@@ -196,7 +201,7 @@ def generate(spec: SequenceSpec, start: int = 0, stop: int | None = None):
         nrng = np.random.Generator(np.random.PCG64(noise_seed))
         planes = []
         for i, (scene, w, h) in enumerate(((scenes[0], W, H), (scenes[1], cw, ch), (scenes[2], cw, ch))):
-            div = 1 if i == 0 else 2
+            div = 1 if i == 0 or full_chroma else 2
             img = _render(scene, w, h, ox / div, oy / div)
             img += (sigma * nrng.standard_normal((h, w), dtype=np.float32))
             for (x0, y0, x1, y1, level) in rects:

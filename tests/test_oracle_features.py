@@ -10,7 +10,8 @@ import math
 import numpy as np
 import pytest
 
-from oracle import (Config, analyze_sequence, block_brightness, block_grid, block_texture_energy, downsample_plane,
+from oracle import (Config, analyze_sequence, block_brightness, block_grid, block_texture_energy, chroma_shape,
+                    downsample_plane,
                     energy_weights,
                     frame_block_values, frame_features, int_dct2, int_dct_matrix, plane_blocks,
                     sequence_features, transform_shifts)
@@ -29,10 +30,10 @@ def test_weights_closed_form():
     assert energy_weights(4)[3, 1] == pytest.approx(math.exp(0.75), rel=1e-15)
 
 
-@pytest.mark.parametrize("N", [8, 16, 32])
+@pytest.mark.parametrize("N", [4, 8, 16, 32])
 @pytest.mark.parametrize("low_pass", [False, True])
 def test_flat_block_has_zero_energy_and_closed_form_brightness(N, low_pass):
-    for B in (8, 10):
+    for B in (8, 10, 12):
         for v in (0, 16, 200):
             Z = int_dct2(np.full((1, N, N), v), B, low_pass)
             assert block_texture_energy(Z, N)[0] == 0.0
@@ -238,3 +239,36 @@ def test_downsample_reading_normalises_with_half_size_blocks():
     assert Hb[0] > 0 and Hb[1:].tolist() == [0.0, 0.0, 0.0]
     assert f["E_Y"] == pytest.approx(Hb[0] / (4 * 16 * 16), rel=1e-15)
     assert f["E_U"] == 0.0
+
+
+# ---------------------------------------------------------------------------
+# Variants of the input: 4:4:4 chroma, 8 x 8 blocks (4 x 4 chroma), 12-bit samples
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("bit_depth", [8, 12])
+def test_444_chroma_runs_the_luma_path(bit_depth):
+    # In 4:4:4 a chroma block is w x w like a luma block: equal planes give equal features.
+    rng = np.random.default_rng(3 + bit_depth)
+    W, H = 72, 40
+    frames = [tuple([rng.integers(0, 1 << bit_depth, size=(H, W))] * 3) for _ in range(2)]
+    per = analyze_sequence(frames, Config(W, H, bit_depth, 16, chroma_format="444"))
+    for f in per:
+        assert f["E_U"] == f["E_Y"] and f["E_V"] == f["E_Y"]
+        assert f["L_U"] == f["L_Y"] and f["L_V"] == f["L_Y"]
+    assert chroma_shape(Config(W, H, chroma_format="444")) == (H, W)
+    assert chroma_shape(Config(W + 2, H + 2)) == (H // 2 + 1, W // 2 + 1)
+
+
+@pytest.mark.parametrize("bit_depth", [8, 10, 12])
+def test_block_8_flat_frame_closed_forms(bit_depth):
+    # 8 x 8 luma and 4 x 4 chroma blocks on a 3 x 2 grid with partial blocks: flat planes give
+    # E = 0 and L = sqrt(v 2^(15 - B)) for both block sizes.
+    W, H = 20, 12
+    v, c = 37, 150
+    y = np.full((H, W), v)
+    u = np.full((H // 2, W // 2), c)
+    f = analyze_sequence([(y, u, u)], Config(W, H, bit_depth, 8))[0]
+    assert block_grid(Config(W, H, bit_depth, 8)) == (3, 2)
+    assert f["E_Y"] == 0.0 and f["E_U"] == 0.0 and f["E_V"] == 0.0
+    assert f["L_Y"] == pytest.approx(math.sqrt(v * 2 ** (15 - bit_depth)), rel=1e-15)  # mean of 6 equal values
+    assert f["L_U"] == pytest.approx(math.sqrt(c * 2 ** (15 - bit_depth)), rel=1e-15)

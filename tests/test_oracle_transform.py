@@ -127,7 +127,7 @@ def test_int_dct_worked_examples():
 
 
 @pytest.mark.parametrize("N", [4, 8, 16, 32])
-@pytest.mark.parametrize("B", [8, 10])
+@pytest.mark.parametrize("B", [8, 10, 12])
 def test_matrix_form_equals_butterfly_form(N, B):
     rng = np.random.default_rng(N * 31 + B)
     x = rng.integers(0, 1 << B, size=(40, N, N))
@@ -139,8 +139,8 @@ def test_matrix_form_equals_butterfly_form(N, B):
     np.testing.assert_array_equal(int_dct2(x, B), int_dct2_butterfly(x, B))
 
 
-@pytest.mark.parametrize("N", [8, 16, 32])
-@pytest.mark.parametrize("B", [8, 10])
+@pytest.mark.parametrize("N", [4, 8, 16, 32])
+@pytest.mark.parametrize("B", [8, 10, 12])
 def test_flat_block_closed_form(N, B):
     for v in (0, 1, 17, (1 << B) - 1):
         x = np.full((N, N), v, dtype=np.int64)
@@ -174,8 +174,8 @@ def test_orientation_rows_first(N):
     assert np.all(Z[:, 1:] == 0)
 
 
-@pytest.mark.parametrize("N", [8, 16, 32])
-@pytest.mark.parametrize("B", [8, 10])
+@pytest.mark.parametrize("N", [4, 8, 16, 32])
+@pytest.mark.parametrize("B", [8, 10, 12])
 def test_integer_transform_tracks_real_dct(N, B):
     # Z ~ 4096 / (N 2^(B-3)) * orthonormal DCT-II: the matrix is 64 sqrt(N) A rounded, and the
     # two shifts divide by 2^(2 log2 N + B - 3).
