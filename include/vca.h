@@ -15,9 +15,10 @@
  *
  * Definitions used (the paper names the features; these are the readings the
  * library implements, identically to the test oracle):
- *   blocks      luma w x w, chroma (w/2) x (w/2) on the same grid, C blocks per
- *               plane, raster order; partial edge blocks repeat the last
- *               row/column (VCA_PAD_REPLICATE) or are dropped (VCA_PAD_SKIP);
+ *   blocks      luma w x w, chroma (w/2) x (w/2) (4:2:0) or w x w (4:4:4) on the
+ *               same grid, C blocks per plane, raster order; partial edge blocks
+ *               repeat the last row/column (VCA_PAD_REPLICATE) or are dropped
+ *               (VCA_PAD_SKIP);
  *   transform   integer DCT, M_N[k][n] = round_half_away(64 sqrt(N) alpha_k
  *               cos(pi(2n+1)k/2N)); rows first, T = (X M^T + 2^(s1-1)) >> s1,
  *               then columns, Z = (M T + 2^(s2-1)) >> s2, s1 = log2 N + B - 9,
@@ -40,8 +41,8 @@
  *     buffers are consumed before vca_push_frame(s) returns;
  *   - plane base pointers and pitches must be multiples of 16 bytes;
  *     samples are uint8 (bit_depth 8) or little-endian 16-bit words holding
- *     values in [0, 1023] (bit_depth 10); values outside [0, 2^B - 1] are
- *     undefined behaviour;
+ *     values in [0, 2^B - 1] (bit_depth 10, 12); other values are undefined
+ *     behaviour;
  *   - an analyzer is bound to one CUDA stream and is not thread-safe; distinct
  *     analyzers may be used from distinct threads.
  */
@@ -68,20 +69,24 @@ typedef enum vca_status {
 
 enum { VCA_PAD_REPLICATE = 0, VCA_PAD_SKIP = 1 };
 enum { VCA_LOWPASS_OFF = 0, VCA_LOWPASS_QUARTER = 1, VCA_LOWPASS_DOWNSAMPLE = 2 };
+enum { VCA_CHROMA_420 = 0, VCA_CHROMA_444 = 1, VCA_CHROMA_422 = 2 };
 enum { VCA_KERNEL_AUTO = 0, VCA_KERNEL_PLAIN = 1, VCA_KERNEL_TC = 2 };
 
 /* Analyzer configuration (Section 2: one analyzer per video). */
 typedef struct vca_config {
   int32_t width;       /* luma width in samples, even, >= 2 */
   int32_t height;      /* luma height in samples, even, >= 2 */
-  int32_t bit_depth;   /* 8 or 10 */
-  int32_t block_size;  /* luma block size w: 16 or 32; chroma blocks are w/2 */
+  int32_t bit_depth;   /* 8, 10 or 12 */
+  int32_t block_size;  /* luma block size w: 8, 16 or 32; chroma blocks cover the same area */
   int32_t low_pass;    /* VCA_LOWPASS_OFF: all coefficients; VCA_LOWPASS_QUARTER: only u, v < N/2;
                           VCA_LOWPASS_DOWNSAMPLE: halved planes, w/2 and w/4 blocks (block_size 32
                           only; not in batches) -- Section 2 item (3) */
   int32_t pad_mode;    /* VCA_PAD_REPLICATE (default) or VCA_PAD_SKIP */
   int32_t kernel;      /* VCA_KERNEL_AUTO, VCA_KERNEL_PLAIN (CUDA cores) or VCA_KERNEL_TC (tensor cores) */
   int32_t max_batch;   /* most frames one vca_push_frames call may carry; 0 selects 64 */
+  int32_t chroma_format; /* VCA_CHROMA_420 (default: half-size chroma planes, w/2 blocks) or
+                            VCA_CHROMA_444 (full-size chroma planes, w blocks); VCA_CHROMA_422
+                            (non-square chroma blocks) gives VCA_E_UNSUPPORTED */
 } vca_config;
 
 /* The seven features of one frame (Section 2), frame = 0-based index since vca_open. */

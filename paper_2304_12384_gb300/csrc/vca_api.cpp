@@ -148,6 +148,7 @@ struct vca_batch {
   int n = 0;
   int device = 0;
   int w = 32;
+  int nc = 16;
   bool low_pass = false;
   cudaStream_t stream = nullptr;
   vca::BatchCta* d_map = nullptr;
@@ -184,27 +185,32 @@ vca_status check_config(const vca_config* c, Geometry* g, Geometry* gin = nullpt
   if (c->width < 2 || c->height < 2 || (c->width & 1) || (c->height & 1) || c->width > 16384 ||
       c->height > 16384)
     return fail(VCA_E_ARG, "width/height must be even and in [2, 16384] (got %d x %d)", c->width, c->height);
-  if (c->bit_depth != 8 && c->bit_depth != 10) return fail(VCA_E_ARG, "bit_depth must be 8 or 10");
-  if (c->block_size != 16 && c->block_size != 32) {
-    if (c->block_size == 8) return fail(VCA_E_UNSUPPORTED, "block_size 8 (4x4 chroma) is not supported");
-    return fail(VCA_E_ARG, "block_size must be 16 or 32");
-  }
+  if (c->bit_depth != 8 && c->bit_depth != 10 && c->bit_depth != 12)
+    return fail(VCA_E_ARG, "bit_depth must be 8, 10 or 12");
+  if (c->block_size != 8 && c->block_size != 16 && c->block_size != 32)
+    return fail(VCA_E_ARG, "block_size must be 8, 16 or 32");
+  if (c->chroma_format == VCA_CHROMA_422)
+    return fail(VCA_E_UNSUPPORTED, "4:2:2 would need non-square chroma blocks; not supported");
+  if (c->chroma_format != VCA_CHROMA_420 && c->chroma_format != VCA_CHROMA_444)
+    return fail(VCA_E_ARG, "chroma_format must be VCA_CHROMA_420 or VCA_CHROMA_444");
   if (c->low_pass < VCA_LOWPASS_OFF || c->low_pass > VCA_LOWPASS_DOWNSAMPLE)
     return fail(VCA_E_ARG, "low_pass must be 0, 1 or 2");
-  if (c->low_pass == VCA_LOWPASS_DOWNSAMPLE && c->block_size != 32)
-    return fail(VCA_E_UNSUPPORTED, "the downsample reading needs block_size 32 (16 x 16 / 8 x 8 blocks after halving)");
+  if (c->low_pass == VCA_LOWPASS_DOWNSAMPLE && (c->block_size != 32 || c->chroma_format != VCA_CHROMA_420))
+    return fail(VCA_E_UNSUPPORTED,
+                "the downsample reading needs block_size 32 and 4:2:0 (16 x 16 / 8 x 8 blocks after halving)");
   if (c->pad_mode != VCA_PAD_REPLICATE && c->pad_mode != VCA_PAD_SKIP) return fail(VCA_E_ARG, "bad pad_mode");
   if (c->kernel < VCA_KERNEL_AUTO || c->kernel > VCA_KERNEL_TC) return fail(VCA_E_ARG, "bad kernel selector");
   if (c->max_batch < 0 || c->max_batch > kMaxBatch) return fail(VCA_E_ARG, "max_batch must be in [0, %d]", kMaxBatch);
   Geometry q{};
   q.W = c->width;
   q.H = c->height;
-  q.cw = c->width / 2;
-  q.ch = c->height / 2;
+  const bool full_chroma = c->chroma_format == VCA_CHROMA_444;
+  q.cw = full_chroma ? c->width : c->width / 2;
+  q.ch = full_chroma ? c->height : c->height / 2;
   q.B = c->bit_depth;
   q.bps = c->bit_depth > 8 ? 2 : 1;
   q.w = c->block_size;
-  q.nc = c->block_size / 2;
+  q.nc = full_chroma ? c->block_size : c->block_size / 2;
   if (c->pad_mode == VCA_PAD_REPLICATE) {
     q.nbx = (q.W + q.w - 1) / q.w;
     q.nby = (q.H + q.w - 1) / q.w;
@@ -476,7 +482,7 @@ cudaError_t build_tick_graph(vca_batch* b, int k) {
   cudaError_t e1 = cudaMemcpyAsync(b->d_desc, b->h_desc[k], b->desc_bytes, cudaMemcpyHostToDevice, b->stream);
   if (e1 == cudaSuccess)
     e1 = vca::launch_batch_plain(b->d_map, b->n_cta, reinterpret_cast<const vca::BatchMemberArgs*>(b->d_desc), b->w,
-                                 b->low_pass, b->stream);
+                                 b->nc, b->low_pass, b->stream);
   if (e1 == cudaSuccess)
     e1 = vca::launch_reduce_batch(reinterpret_cast<const vca::ReduceArgs*>(b->d_desc + b->ma_bytes), b->n, b->stream);
   if (e1 == cudaSuccess)
@@ -885,8 +891,8 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
     for (int j = 0; j < i; ++j)
       if (members[j] == a) return fail(VCA_E_ARG, "analyzer %d appears twice", i);
     if (a->device != members[0]->device) return fail(VCA_E_ARG, "analyzers of a batch must share one device");
-    if (a->g.w != members[0]->g.w || a->g.low_pass != members[0]->g.low_pass)
-      return fail(VCA_E_ARG, "analyzers of a batch must share block size and low_pass");
+    if (a->g.w != members[0]->g.w || a->g.nc != members[0]->g.nc || a->g.low_pass != members[0]->g.low_pass)
+      return fail(VCA_E_ARG, "analyzers of a batch must share block size, chroma format and low_pass");
     if (a->cfg.low_pass == VCA_LOWPASS_DOWNSAMPLE)
       return fail(VCA_E_UNSUPPORTED, "the downsample reading is not available in batches");
   }
@@ -896,6 +902,7 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
   b->n = n;
   b->device = members[0]->device;
   b->w = members[0]->g.w;
+  b->nc = members[0]->g.nc;
   b->low_pass = members[0]->g.low_pass;
   int prev_dev = -1;
   cudaGetDevice(&prev_dev);

@@ -1,19 +1,19 @@
 // Batched multi-stream analysis: one frame of every analyzer of a batch in one launch of the plain
 // block routine (Section 2 of the paper, per block: integer DCT, texture energy H, brightness L).
 //
-// The analyzers may differ in frame size and bit depth but share block size and the low-pass
-// option.  Each CTA reads its (analyzer, plane kind, plane, block chunk) from a map built once
-// when the batch is created, and the analyzer's arguments for this tick from a table the host
-// refreshes every tick; an analyzer skipped this tick has active = 0 and its CTAs return at once.
+// The analyzers may differ in frame size and bit depth but share block sizes (chroma format) and
+// the low-pass option.  Each CTA reads its (analyzer, plane kind, plane, block chunk) from a map
+// built once when the batch is created, and the analyzer's arguments for this tick from a table
+// the host refreshes every tick; an analyzer skipped this tick has active = 0 and its CTAs return
+// at once.
 #include "vca_plain.cuh"
 
 namespace vca {
 namespace {
 
-template <int Nl, bool LP>
+template <int Nl, int Nc, bool LP>
 __global__ void __launch_bounds__(kWarps * 32)
     batch_plain_kernel(const BatchCta* __restrict__ map, const BatchMemberArgs* __restrict__ args) {
-  constexpr int Nc = Nl / 2;
   __shared__ union {
     PlainSmem<Nl, LP> luma;
     PlainSmem<Nc, LP> chroma;
@@ -35,28 +35,31 @@ __global__ void __launch_bounds__(kWarps * 32)
   }
 }
 
+template <int Nl, int Nc>
+cudaError_t launch_sizes(const BatchCta* d_map, int n_cta, const BatchMemberArgs* d_args, bool low_pass,
+                         cudaStream_t s) {
+  const dim3 grid((unsigned)n_cta), block(kWarps * 32);
+  if (low_pass)
+    batch_plain_kernel<Nl, Nc, true><<<grid, block, 0, s>>>(d_map, d_args);
+  else
+    batch_plain_kernel<Nl, Nc, false><<<grid, block, 0, s>>>(d_map, d_args);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
-cudaError_t launch_batch_plain(const BatchCta* d_map, int n_cta, const BatchMemberArgs* d_args, int w, bool low_pass,
-                               cudaStream_t s) {
+cudaError_t launch_batch_plain(const BatchCta* d_map, int n_cta, const BatchMemberArgs* d_args, int w, int nc,
+                               bool low_pass, cudaStream_t s) {
   if (n_cta <= 0) return cudaSuccess;
   static_assert(plain_blocks_per_cta(32) == kWarps * 1 && plain_blocks_per_cta(16) == kWarps * 2,
                 "blocks per CTA of the plain routine");
-  const dim3 grid((unsigned)n_cta), block(kWarps * 32);
-  if (w == 32) {
-    if (low_pass)
-      batch_plain_kernel<32, true><<<grid, block, 0, s>>>(d_map, d_args);
-    else
-      batch_plain_kernel<32, false><<<grid, block, 0, s>>>(d_map, d_args);
-  } else if (w == 16) {
-    if (low_pass)
-      batch_plain_kernel<16, true><<<grid, block, 0, s>>>(d_map, d_args);
-    else
-      batch_plain_kernel<16, false><<<grid, block, 0, s>>>(d_map, d_args);
-  } else {
-    return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+  if (w == 32 && nc == 16) return launch_sizes<32, 16>(d_map, n_cta, d_args, low_pass, s);
+  if (w == 16 && nc == 8) return launch_sizes<16, 8>(d_map, n_cta, d_args, low_pass, s);
+  if (w == 8 && nc == 4) return launch_sizes<8, 4>(d_map, n_cta, d_args, low_pass, s);
+  if (w == 32 && nc == 32) return launch_sizes<32, 32>(d_map, n_cta, d_args, low_pass, s);
+  if (w == 16 && nc == 16) return launch_sizes<16, 16>(d_map, n_cta, d_args, low_pass, s);
+  if (w == 8 && nc == 8) return launch_sizes<8, 8>(d_map, n_cta, d_args, low_pass, s);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace vca

@@ -129,9 +129,10 @@ struct BatchMemberArgs {
 // Blocks per CTA of the plain routine for block size N.
 constexpr int plain_blocks_per_cta(int N) { return 4 * (32 / N); }
 // The batched plain analysis of one frame per analyzer: n_cta CTAs described by d_map (device),
-// arguments d_args (device, one per analyzer).  All analyzers share block size w and low_pass.
-cudaError_t launch_batch_plain(const BatchCta* d_map, int n_cta, const BatchMemberArgs* d_args, int w, bool low_pass,
-                               cudaStream_t s);
+// arguments d_args (device, one per analyzer).  All analyzers share block sizes w (luma) and nc
+// (chroma) and low_pass.
+cudaError_t launch_batch_plain(const BatchCta* d_map, int n_cta, const BatchMemberArgs* d_args, int w, int nc,
+                               bool low_pass, cudaStream_t s);
 
 // One plane of the 2x2 downsample: n frames of w x h samples at src (pitch, frame stride in
 // bytes) -> wd x hd = ceil(w/2) x ceil(h/2) samples at dst.

@@ -34,6 +34,7 @@ cudaError_t launch_n(int N, const PlainArgs& a, int nplanes, int nframes, bool l
     case 32: return launch_planes<32>(a, nplanes, nframes, lp, bps, s);
     case 16: return launch_planes<16>(a, nplanes, nframes, lp, bps, s);
     case 8: return launch_planes<8>(a, nplanes, nframes, lp, bps, s);
+    case 4: return launch_planes<4>(a, nplanes, nframes, lp, bps, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -100,7 +100,7 @@ namespace {
 // Device bytes of an analyzer of this configuration (the allocations vca_open makes for
 // max_batch = 1), rounded up generously for allocator granularity.
 size_t analyzer_cost(const vca_config& c, int64_t C) {
-  const size_t w = c.block_size, nc = w / 2;
+  const size_t w = c.block_size, nc = c.chroma_format == VCA_CHROMA_444 ? w : w / 2;
   size_t b = round_up(w * w + nc * nc + 4 * (w * w + nc * nc), 4096);
   b += round_up(2 * 6 * (size_t)C * 4, 4096);   // block values, 1 + 1 frames
   b += 2 * round_up((size_t)C * 4, 4096);        // previous-frame luma energies
@@ -311,8 +311,10 @@ vca_status vca_server_add_channel(vca_server* s, const vca_config* cfg, int32_t 
   vca_config c = *cfg;
   c.max_batch = 1;
   const int bps = c.bit_depth > 8 ? 2 : 1;
-  const int64_t py = (int64_t)round_up((size_t)c.width * bps, 256), pc = (int64_t)round_up((size_t)c.width / 2 * bps, 256);
-  const size_t ystride = (size_t)py * c.height, cstride = (size_t)pc * (c.height / 2);
+  const bool full_chroma = c.chroma_format == VCA_CHROMA_444;
+  const int cw = full_chroma ? c.width : c.width / 2, chh = full_chroma ? c.height : c.height / 2;
+  const int64_t py = (int64_t)round_up((size_t)c.width * bps, 256), pc = (int64_t)round_up((size_t)cw * bps, 256);
+  const size_t ystride = (size_t)py * c.height, cstride = (size_t)pc * chh;
   const size_t off_u = round_up(ystride * max_segment_frames, 256);
   const size_t off_v = off_u + round_up(cstride * max_segment_frames, 256);
   const size_t slot_bytes = off_v + round_up(cstride * max_segment_frames, 256);
@@ -442,10 +444,11 @@ vca_status vca_server_submit_frames(vca_server* s, int32_t id, const vca_frame_r
   }
   const Channel& c = *cp;
   const int bps = c.cfg.bit_depth > 8 ? 2 : 1;
-  const size_t wy = (size_t)c.cfg.width * bps, wc = (size_t)c.cfg.width / 2 * bps;
+  const bool full_chroma = c.cfg.chroma_format == VCA_CHROMA_444;
+  const size_t wy = (size_t)c.cfg.width * bps, wc = (size_t)(full_chroma ? c.cfg.width : c.cfg.width / 2) * bps;
   if (frame0->pitch_y < (int64_t)wy || frame0->pitch_uv < (int64_t)wc) return sfail(VCA_E_ARG, "pitch smaller than a row");
   uint8_t* dst = c.ring + (size_t)slot * c.slot_bytes;
-  const int h = c.cfg.height, hc = c.cfg.height / 2;
+  const int h = c.cfg.height, hc = full_chroma ? c.cfg.height : c.cfg.height / 2;
   cudaError_t e = cudaSuccess;
   if (ready_event) e = cudaStreamWaitEvent(s->copy_stream, (cudaEvent_t)ready_event, 0);
   // Frames stacked without gaps (frame stride = pitch x rows) copy as one 2-D copy per plane.

@@ -760,7 +760,7 @@ int sm_count() {
 
 }  // namespace
 
-bool tc_supported(const Geometry& g) { return g.B == 8 && g.w == 32 && encode_fn() != nullptr; }
+bool tc_supported(const Geometry& g) { return g.B == 8 && g.w == 32 && g.nc == 16 && encode_fn() != nullptr; }
 
 cudaError_t launch_tc(const Geometry& g, const FramePlanes& fp, int nframes, const DeviceTables& t, float* blockvals,
                       int16_t* const zdump[3], int* err, cudaStream_t s, int64_t* launches) {

@@ -27,6 +27,9 @@ VCA_PAD_SKIP = 1
 VCA_LOWPASS_OFF = 0
 VCA_LOWPASS_QUARTER = 1
 VCA_LOWPASS_DOWNSAMPLE = 2
+VCA_CHROMA_420 = 0
+VCA_CHROMA_444 = 1
+VCA_CHROMA_422 = 2
 VCA_KERNEL_AUTO = 0
 VCA_KERNEL_PLAIN = 1
 VCA_KERNEL_TC = 2
@@ -37,7 +40,7 @@ FEATURES = ("E_Y", "h", "L_Y", "E_U", "E_V", "L_U", "L_V")
 class VcaConfig(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("bit_depth", ctypes.c_int32),
                 ("block_size", ctypes.c_int32), ("low_pass", ctypes.c_int32), ("pad_mode", ctypes.c_int32),
-                ("kernel", ctypes.c_int32), ("max_batch", ctypes.c_int32)]
+                ("kernel", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("chroma_format", ctypes.c_int32)]
 
 
 class VcaFrameFeatures(ctypes.Structure):
@@ -296,13 +299,13 @@ class Analyzer:
     """
 
     def __init__(self, width, height, bit_depth=8, block_size=32, low_pass=False, pad_mode=VCA_PAD_REPLICATE,
-                 kernel=VCA_KERNEL_AUTO, max_batch=64, stream=None):
+                 kernel=VCA_KERNEL_AUTO, max_batch=64, stream=None, chroma_format=VCA_CHROMA_420):
         import torch
 
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
         lp = VCA_LOWPASS_DOWNSAMPLE if low_pass in ("downsample", VCA_LOWPASS_DOWNSAMPLE) else int(bool(low_pass))
-        self.cfg = VcaConfig(width, height, bit_depth, block_size, lp, pad_mode, kernel, max_batch)
+        self.cfg = VcaConfig(width, height, bit_depth, block_size, lp, pad_mode, kernel, max_batch, chroma_format)
         self.handle = vca_open(self.cfg, stream)
         self.blocks_x, self.blocks_y = vca_block_count(self.cfg)
         self.C = self.blocks_x * self.blocks_y
@@ -363,7 +366,7 @@ class Analyzer:
 
         w = self.cfg.block_size
         nk_y = w // 2 if self.cfg.low_pass else w  # quarter: N/2 coefficients; downsample: w/2 blocks
-        nk_c = nk_y // 2
+        nk_c = nk_y if self.cfg.chroma_format == VCA_CHROMA_444 else nk_y // 2
         zy = torch.empty((self.C, nk_y, nk_y), dtype=torch.int16, device=y.device)
         zu = torch.empty((self.C, nk_c, nk_c), dtype=torch.int16, device=y.device)
         zv = torch.empty_like(zu)
@@ -451,8 +454,9 @@ class Server:
         self.handle = h.value
 
     def add_channel(self, width, height, bit_depth=8, block_size=32, low_pass=True, max_segment_frames=120,
-                    pad_mode=VCA_PAD_REPLICATE) -> int:
-        cfg = VcaConfig(width, height, bit_depth, block_size, int(bool(low_pass)), pad_mode, VCA_KERNEL_AUTO, 1)
+                    pad_mode=VCA_PAD_REPLICATE, chroma_format=VCA_CHROMA_420) -> int:
+        cfg = VcaConfig(width, height, bit_depth, block_size, int(bool(low_pass)), pad_mode, VCA_KERNEL_AUTO, 1,
+                        chroma_format)
         cid = _I32()
         _check(lib().vca_server_add_channel(_P(self.handle), ctypes.byref(cfg), max_segment_frames, ctypes.byref(cid)))
         return cid.value

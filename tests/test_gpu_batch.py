@@ -125,3 +125,27 @@ def test_batch_state_rules(vca):
     finally:
         for x in (a, b, c, d):
             x.close()
+
+
+def test_batch_444_and_block_8(vca):
+    # Batches of 4:4:4 channels and of 8 x 8-block channels match single analyzers bit for bit.
+    for kw in ({"chroma_format": vca.VCA_CHROMA_444, "block_size": 16}, {"chroma_format": 0, "block_size": 8}):
+        cf = "444" if kw["chroma_format"] == 1 else "420"
+        chans = [(200, 120, 8), (136, 72, 12)]
+        frames = [frames_list(SequenceSpec(w, h, 3, 60 + i, bit_depth=bd, sigma=4.0, chroma_format=cf))
+                  for i, (w, h, bd) in enumerate(chans)]
+        dev = [to_device(f) for f in frames]
+        members = [vca.Analyzer(w, h, bd, kw["block_size"], False, kernel=vca.VCA_KERNEL_PLAIN, max_batch=3,
+                                chroma_format=kw["chroma_format"]) for (w, h, bd) in chans]
+        singles = [vca.Analyzer(w, h, bd, kw["block_size"], False, kernel=vca.VCA_KERNEL_PLAIN, max_batch=3,
+                                chroma_format=kw["chroma_format"]) for (w, h, bd) in chans]
+        batch = vca.Batch(members)
+        for t in range(3):
+            batch.tick([(y[t], u[t], v[t]) for (y, u, v) in dev])
+            for s_, (y, u, v) in zip(singles, dev):
+                s_.push(y[t], u[t], v[t])
+        batch.close()
+        for m, s_ in zip(members, singles):
+            assert [m.frame_features(t) for t in range(3)] == [s_.frame_features(t) for t in range(3)]
+            m.close()
+            s_.close()

@@ -40,11 +40,12 @@ def open_analyzer(vca, kernel, **kw):
 
 
 def run_and_compare(vca, kernel, frames, *, width, height, bit_depth=8, block_size=32, low_pass=False, pad_mode=0,
-                    batch=None, dump_frames=(0,), block_frames=None):
+                    batch=None, dump_frames=(0,), block_frames=None, chroma_format=0):
     import torch
 
     an = open_analyzer(vca, kernel, width=width, height=height, bit_depth=bit_depth, block_size=block_size,
-                       low_pass=low_pass, pad_mode=pad_mode, max_batch=max(len(frames), 1))
+                       low_pass=low_pass, pad_mode=pad_mode, max_batch=max(len(frames), 1),
+                       chroma_format=chroma_format)
     try:
         y, u, v = to_device(frames)
         assert an.kernel == KERNELS[kernel]
@@ -255,3 +256,41 @@ def test_downsample_reading_rules(vca):
         with pytest.raises(vca.VcaError) as ei:
             vca.Analyzer(640, 352, 8, args["block_size"], "downsample", kernel=args["kernel"])
         assert ei.value.status == vca.VCA_E_UNSUPPORTED
+
+
+# Input variants: 8 x 8 blocks (4 x 4 chroma), 12-bit samples, 4:4:4 chroma (CUDA-core form).
+@pytest.mark.parametrize("bit_depth", [8, 10, 12])
+@pytest.mark.parametrize("low_pass", [False, True])
+def test_block_8(vca, bit_depth, low_pass):
+    frames = frames_list(SequenceSpec(200, 120, 4, 51, bit_depth=bit_depth, sigma=4.0, cuts=(2,)))
+    run_and_compare(vca, "plain", frames, width=200, height=120, bit_depth=bit_depth, block_size=8,
+                    low_pass=low_pass, dump_frames=(0, 2))
+
+
+@pytest.mark.parametrize("block_size", [32, 16])
+@pytest.mark.parametrize("low_pass", [False, True])
+def test_12_bit(vca, block_size, low_pass):
+    frames = frames_list(SequenceSpec(640, 352, 4, 52, bit_depth=12, sigma=4.0, cuts=(2,)))
+    run_and_compare(vca, "plain", frames, width=640, height=352, bit_depth=12, block_size=block_size,
+                    low_pass=low_pass, dump_frames=(1,))
+
+
+@pytest.mark.parametrize("block_size", [32, 16, 8])
+@pytest.mark.parametrize("bit_depth", [8, 12])
+def test_chroma_444(vca, block_size, bit_depth):
+    frames = frames_list(SequenceSpec(200, 120, 4, 53, bit_depth=bit_depth, sigma=4.0, cuts=(2,), chroma_format="444"))
+    run_and_compare(vca, "plain", frames, width=200, height=120, bit_depth=bit_depth, block_size=block_size,
+                    low_pass=block_size == 16, dump_frames=(0, 3), chroma_format=1)
+
+
+def test_variant_rules(vca):
+    # The tensor-core form covers 8-bit 4:2:0 with 32 x 32 blocks; the others run on CUDA cores.
+    for kw in ({"bit_depth": 12}, {"block_size": 8}, {"chroma_format": 1}):
+        args = dict(width=640, height=352, bit_depth=8, block_size=32)
+        args.update(kw)
+        an = vca.Analyzer(**args)
+        assert an.kernel == vca.VCA_KERNEL_PLAIN
+        an.close()
+    with pytest.raises(vca.VcaError) as ei:
+        vca.Analyzer(640, 352, 8, 32, chroma_format=vca.VCA_CHROMA_422)
+    assert ei.value.status == vca.VCA_E_UNSUPPORTED

@@ -51,9 +51,11 @@ def test_status_strings(libvca):
 @pytest.mark.parametrize("cfg,status", [
     ((3841, 2160, 8, 32, 0, 0, 0, 64), -1),   # odd width
     ((0, 2160, 8, 32, 0, 0, 0, 64), -1),      # empty
-    ((3840, 2160, 12, 32, 0, 0, 0, 64), -1),  # bit depth
+    ((3840, 2160, 9, 32, 0, 0, 0, 64), -1),   # bit depth
     ((3840, 2160, 8, 24, 0, 0, 0, 64), -1),   # block size
-    ((3840, 2160, 8, 8, 0, 0, 0, 64), -2),    # 4x4 chroma blocks unsupported
+    ((3840, 2160, 14, 32, 0, 0, 0, 64), -1),  # bit depth 14
+    ((3840, 2160, 8, 32, 0, 0, 0, 64, 2), -2),  # 4:2:2 unsupported
+    ((3840, 2160, 8, 32, 0, 0, 0, 64, 5), -1),  # chroma format
     ((3840, 2160, 8, 32, 3, 0, 0, 64), -1),   # low_pass flag
     ((3840, 2160, 8, 16, 2, 0, 0, 64), -2),   # downsample reading needs block 32
     ((3840, 2160, 8, 32, 0, 5, 0, 64), -1),   # pad mode

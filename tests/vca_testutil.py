@@ -54,7 +54,8 @@ def to_host_pinned(frames, pitch_align=64):
 def oracle_config(an) -> Config:
     c = an.cfg
     return Config(c.width, c.height, c.bit_depth, c.block_size, c.low_pass == 1,
-                  "skip" if c.pad_mode == 1 else "replicate", downsample=c.low_pass == 2)
+                  "skip" if c.pad_mode == 1 else "replicate", downsample=c.low_pass == 2,
+                  chroma_format="444" if c.chroma_format == 1 else "420")
 
 
 def oracle_coefficients(frame, cfg: Config):
