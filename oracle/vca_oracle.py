@@ -364,3 +364,49 @@ def sequence_features(per_frame: list[dict]) -> dict:
             vals = vals[1:]
         out[k] = float(sum(vals) / len(vals)) if vals else 0.0
     return out
+
+
+# ---------------------------------------------------------------------------
+# SI / TI (the spatial and temporal information the paper compares VCA with,
+# Section 2: SI = max over frames of std[Sobel(F)], TI = max over frames of
+# std[F_t - F_{t-1}])
+#
+# Readings: F is the luma plane in raw sample values; Sobel(F) is the gradient
+# magnitude sqrt(Gx^2 + Gy^2) of the 3x3 Sobel responses, evaluated on the interior
+# pixels (the one-pixel border has no full neighbourhood); std is the population
+# standard deviation over the pixels; the per-frame TI of the first frame is 0 and
+# the sequence TI is the maximum over frames t >= 1.
+# ---------------------------------------------------------------------------
+
+def sobel_responses(plane) -> tuple[np.ndarray, np.ndarray]:
+    """(Gx, Gy) on the interior pixels: Gx = right column - left column with weights 1, 2, 1
+    down the rows, Gy = bottom row - top row with weights 1, 2, 1 across the columns (int64)."""
+    F = np.asarray(plane).astype(np.int64)
+    gx = (F[:-2, 2:] + 2 * F[1:-1, 2:] + F[2:, 2:]) - (F[:-2, :-2] + 2 * F[1:-1, :-2] + F[2:, :-2])
+    gy = (F[2:, :-2] + 2 * F[2:, 1:-1] + F[2:, 2:]) - (F[:-2, :-2] + 2 * F[:-2, 1:-1] + F[:-2, 2:])
+    return gx, gy
+
+
+def frame_si(plane) -> float:
+    """std over the interior pixels of sqrt(Gx^2 + Gy^2) (FP64)."""
+    gx, gy = sobel_responses(plane)
+    return float(np.std(np.sqrt((gx * gx + gy * gy).astype(np.float64))))
+
+
+def frame_ti(plane, prev) -> float:
+    """std over all pixels of F_t - F_{t-1} (FP64); 0 without a previous frame."""
+    if prev is None:
+        return 0.0
+    d = np.asarray(plane).astype(np.int64) - np.asarray(prev).astype(np.int64)
+    return float(np.std(d.astype(np.float64)))
+
+
+def siti_sequence(lumas, prev=None) -> tuple[list, dict]:
+    """Per-frame (SI, TI) of a sequence of luma planes and the sequence maxima."""
+    per = []
+    for F in lumas:
+        per.append({"SI": frame_si(F), "TI": frame_ti(F, prev)})
+        prev = F
+    seq = {"SI": max(p["SI"] for p in per) if per else 0.0,
+           "TI": max((p["TI"] for p in per[1:]), default=0.0)}
+    return per, seq
