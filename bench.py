@@ -400,6 +400,21 @@ def run_extras(args, an, y, u, v, frames, stream, kern, lp, device):
         a2.close()
     out["variants"] = variants
 
+    # SI / TI of the same 2160p frames (the paper's comparison features; its CPU reference runs
+    # at 8.55 fps on an i7-11370H, Section 3 -- another machine, context only).
+    s = vca.Siti(W, H, 8, max_batch=args.frames, stream=stream.cuda_stream)
+    s.push(y)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps = 5
+    for _ in range(reps):
+        s.push(y)
+    el = time.perf_counter() - t0
+    out["siti"] = {"fps": reps * args.frames / el, "frames_per_push": args.frames, "launches_per_push": 2,
+                   "hbm_frac_of_measured": reps * args.frames * W * H / el / 1e9 / load_peaks()[0],
+                   "timing": "host wall clock per synchronous push (luma read once, 3x3 neighbourhood from cache)"}
+    s.close()
+
     out["ladder"] = run_ladder(args, stream)
     out["serving"] = run_serving(args)
 

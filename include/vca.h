@@ -293,6 +293,34 @@ vca_status vca_server_stats(vca_server* s, vca_server_stats_t* st);
 /* Finishes every submitted segment, stops the scheduler and frees the channels. */
 vca_status vca_server_destroy(vca_server* s);
 
+/* ---- SI / TI ---------------------------------------------------------------------------
+ *
+ * The spatial and temporal information features that the paper compares VCA with (Section 2:
+ * SI = max over frames of std[Sobel(F)], TI = max over frames of std[F_t - F_{t-1}]), on the luma
+ * plane in raw sample values.  Per frame: SI_t = population standard deviation over the
+ * interior pixels (the one-pixel border excluded) of sqrt(Gx^2 + Gy^2), Gx and Gy the 3x3 Sobel
+ * responses; TI_t = population standard deviation over all pixels of F_t - F_{t-1}, 0 for the
+ * first frame.  The sequence values are the maxima (TI over t >= 1).  Sums of Gx^2 + Gy^2 and of
+ * the differences are exact integers; the gradient magnitudes use an FP32 square root and are
+ * summed in 2^-16 fixed point; the deviations are formed in FP64. */
+typedef struct vca_siti vca_siti;
+typedef struct {
+  int64_t frame;
+  double SI, TI;
+} vca_siti_features;
+
+/* width, height in [3, 16384]; bit_depth 8, 10 or 12; up to max_batch frames per push. */
+vca_status vca_siti_open(int32_t width, int32_t height, int32_t bit_depth, int32_t max_batch, void* cuda_stream,
+                         vca_siti** out);
+/* n_frames luma planes (pitch and frame stride in bytes; device planes 16-byte aligned, or host
+ * planes with on_device = 0).  Returns when their features are on the host. */
+vca_status vca_siti_push(vca_siti* s, const void* y, int64_t pitch, int64_t frame_stride, int32_t n_frames,
+                         int32_t on_device);
+vca_status vca_siti_read(vca_siti* s, int64_t frame, vca_siti_features* out);
+vca_status vca_siti_sequence(vca_siti* s, double* si, double* ti, int64_t* frames);
+vca_status vca_siti_launch_count(vca_siti* s, int64_t* launches);
+vca_status vca_siti_close(vca_siti* s);
+
 /* Frame features from per-block values already on the device, without allocating any device
  * memory.  The paper has no counterpart: this is a runtime convenience for callers that must not
  * call the CUDA allocator on their hot path (a serving loop that has budgeted all device memory

@@ -76,6 +76,10 @@ class VcaServerStats(ctypes.Structure):
                 ("pad", ctypes.c_int32)]
 
 
+class VcaSitiFeatures(ctypes.Structure):
+    _fields_ = [("frame", ctypes.c_int64), ("SI", ctypes.c_double), ("TI", ctypes.c_double)]
+
+
 class VcaError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{message} (status {status})")
@@ -122,6 +126,12 @@ _PROTOS = {
     "vca_server_read_features": (_P, _I32, _I64, ctypes.POINTER(VcaFrameFeatures)),
     "vca_server_stats": (_P, ctypes.POINTER(VcaServerStats)),
     "vca_server_destroy": (_P,),
+    "vca_siti_open": (_I32, _I32, _I32, _I32, _P, ctypes.POINTER(_P)),
+    "vca_siti_push": (_P, _P, _I64, _I64, _I32, _I32),
+    "vca_siti_read": (_P, _I64, ctypes.POINTER(VcaSitiFeatures)),
+    "vca_siti_sequence": (_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)),
+    "vca_siti_launch_count": (_P, ctypes.POINTER(_I64)),
+    "vca_siti_close": (_P,),
 }
 
 
@@ -495,6 +505,61 @@ class Server:
     def close(self):
         if self.handle:
             _check(lib().vca_server_destroy(_P(self.handle)))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Siti:
+    """SI / TI of a luma sequence (the paper's comparison features) on the current CUDA stream."""
+
+    def __init__(self, width, height, bit_depth=8, max_batch=64, stream=None):
+        import torch
+
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        h = _P()
+        _check(lib().vca_siti_open(width, height, bit_depth, max_batch, _P(stream), ctypes.byref(h)))
+        self.handle = h.value
+        self.frames = 0
+
+    def push(self, y):
+        """(F, H, pitch) or (H, pitch) luma tensor, on the device or the host."""
+        es = y.element_size()
+        n = y.shape[0] if y.dim() == 3 else 1
+        fs = y.stride(0) * es if y.dim() == 3 else 0
+        _check(lib().vca_siti_push(_P(self.handle), _P(y.data_ptr()), y.stride(-2) * es, fs, n, 1 if y.is_cuda else 0))
+        self.frames += n
+        return n
+
+    def frame_features(self, frame) -> dict:
+        out = VcaSitiFeatures()
+        _check(lib().vca_siti_read(_P(self.handle), frame, ctypes.byref(out)))
+        return {"SI": out.SI, "TI": out.TI}
+
+    def sequence_features(self) -> dict:
+        si, ti, n = ctypes.c_double(), ctypes.c_double(), _I64()
+        _check(lib().vca_siti_sequence(_P(self.handle), ctypes.byref(si), ctypes.byref(ti), ctypes.byref(n)))
+        return {"SI": si.value, "TI": ti.value, "frames": n.value}
+
+    def launches(self) -> int:
+        n = _I64()
+        _check(lib().vca_siti_launch_count(_P(self.handle), ctypes.byref(n)))
+        return n.value
+
+    def close(self):
+        if self.handle:
+            _check(lib().vca_siti_close(_P(self.handle)))
             self.handle = None
 
     def __enter__(self):
