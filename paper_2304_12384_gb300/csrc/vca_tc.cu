@@ -291,21 +291,29 @@ __device__ __forceinline__ void epilogue1(uint32_t td1, uint32_t td2, uint32_t a
   const int l = 32 * q + lane;
   const int bg = l / Nb;
   const int r = l % Nb;
-  uint32_t acc[P::G][NK];
-#pragma unroll
-  for (int g = 0; g < P::G; ++g) tmem_ld<NK>(td1 + g * P::N1, acc[g]);
-  tmem_wait_ld();
-  fill_cols<P::N1>(td2, hi0, kK1);
-  fill_cols<P::N1>(td2 + P::N1, lo, lo);
+  // With several groups (low-pass) D2 lies beside D1, so the groups are read one at a time; a
+  // single group (all coefficients) is read before D2, which then overwrites its columns.
+  static_assert(P::G == 1 || LP, "several stage-1 groups only in low-pass mode");
+  if (P::G > 1) {
+    fill_cols<P::N1>(td2, hi0, kK1);
+    fill_cols<P::N1>(td2 + P::N1, lo, lo);
+  }
   const uint32_t rowoff = (uint32_t)((r >> 3) * 2048 + (r & 7) * 128);
 #pragma unroll
   for (int g = 0; g < P::G; ++g) {
+    uint32_t acc[NK];
+    tmem_ld<NK>(td1 + g * P::N1, acc);
+    tmem_wait_ld();
+    if (P::G == 1) {
+      fill_cols<P::N1>(td2, hi0, kK1);
+      fill_cols<P::N1>(td2 + P::N1, lo, lo);
+    }
     uint32_t hi[NK / 2], lw[NK / 2];
 #pragma unroll
     for (int k = 0; k < NK; k += 2) {
       // D1 already holds T' = c_k + sum (the accumulators were pre-set), an exact integer.
-      const uint32_t za = __float_as_uint(__fmaf_rd(__uint_as_float(acc[g][k]), s1inv, kT1));
-      const uint32_t zb = __float_as_uint(__fmaf_rd(__uint_as_float(acc[g][k + 1]), s1inv, kT1));
+      const uint32_t za = __float_as_uint(__fmaf_rd(__uint_as_float(acc[k]), s1inv, kT1));
+      const uint32_t zb = __float_as_uint(__fmaf_rd(__uint_as_float(acc[k + 1]), s1inv, kT1));
       lw[k / 2] = prmt(za, zb, 0x6420);
       hi[k / 2] = prmt(za, zb, 0x6521);
     }
