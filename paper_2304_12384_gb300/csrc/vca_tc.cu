@@ -291,41 +291,41 @@ __device__ __forceinline__ void epilogue1(uint32_t td1, uint32_t td2, uint32_t a
   const int l = 32 * q + lane;
   const int bg = l / Nb;
   const int r = l % Nb;
-  // With several groups (low-pass) D2 lies beside D1, so the groups are read one at a time; a
-  // single group (all coefficients) is read before D2, which then overwrites its columns.
-  static_assert(P::G == 1 || LP, "several stage-1 groups only in low-pass mode");
-  if (P::G > 1) {
-    fill_cols<P::N1>(td2, hi0, kK1);
-    fill_cols<P::N1>(td2 + P::N1, lo, lo);
-  }
+  // D1 is read 16 columns at a time (bounds register use).  The stage-2 hi presets at [0, N1)
+  // never overlap D1 (at column kD1Off = 32); the lo presets at [N1, 2 N1) do when N1 = 32 (all
+  // coefficients, luma), so they are written after every column of D1 has been read.
+  constexpr int CH = NK < 16 ? NK : 16;
+  constexpr bool kLoOverD1 = 2 * P::N1 > kD1Off;
+  fill_cols<P::N1>(td2, hi0, kK1);
+  if (!kLoOverD1) fill_cols<P::N1>(td2 + P::N1, lo, lo);
   const uint32_t rowoff = (uint32_t)((r >> 3) * 2048 + (r & 7) * 128);
 #pragma unroll
   for (int g = 0; g < P::G; ++g) {
-    uint32_t acc[NK];
-    tmem_ld<NK>(td1 + g * P::N1, acc);
-    tmem_wait_ld();
-    if (P::G == 1) {
-      fill_cols<P::N1>(td2, hi0, kK1);
-      fill_cols<P::N1>(td2 + P::N1, lo, lo);
-    }
-    uint32_t hi[NK / 2], lw[NK / 2];
 #pragma unroll
-    for (int k = 0; k < NK; k += 2) {
-      // D1 already holds T' = c_k + sum (the accumulators were pre-set), an exact integer.
-      const uint32_t za = __float_as_uint(__fmaf_rd(__uint_as_float(acc[k]), s1inv, kT1));
-      const uint32_t zb = __float_as_uint(__fmaf_rd(__uint_as_float(acc[k + 1]), s1inv, kT1));
-      lw[k / 2] = prmt(za, zb, 0x6420);
-      hi[k / 2] = prmt(za, zb, 0x6521);
-    }
-    const int m0 = (g * P::BPG1 + bg) * NK;
+    for (int h0 = 0; h0 < NK; h0 += CH) {
+      uint32_t acc[CH];
+      tmem_ld<CH>(td1 + g * P::N1 + h0, acc);
+      tmem_wait_ld();
+      uint32_t hi[CH / 2], lw[CH / 2];
 #pragma unroll
-    for (int cc = 0; cc < NK / 8; ++cc) {
-      const int m = m0 + 8 * cc;
-      const uint32_t off = rowoff + (uint32_t)((m >> 6) * 1024) + (uint32_t)(((((m & 63) >> 3) ^ (r & 7))) << 4);
-      sts128(a2hi + off, hi[4 * cc], hi[4 * cc + 1], hi[4 * cc + 2], hi[4 * cc + 3]);
-      sts128(a2lo + off, lw[4 * cc], lw[4 * cc + 1], lw[4 * cc + 2], lw[4 * cc + 3]);
+      for (int k = 0; k < CH; k += 2) {
+        // D1 already holds T' = c_k + sum (the accumulators were pre-set), an exact integer.
+        const uint32_t za = __float_as_uint(__fmaf_rd(__uint_as_float(acc[k]), s1inv, kT1));
+        const uint32_t zb = __float_as_uint(__fmaf_rd(__uint_as_float(acc[k + 1]), s1inv, kT1));
+        lw[k / 2] = prmt(za, zb, 0x6420);
+        hi[k / 2] = prmt(za, zb, 0x6521);
+      }
+      const int m0 = (g * P::BPG1 + bg) * NK + h0;
+#pragma unroll
+      for (int cc = 0; cc < CH / 8; ++cc) {
+        const int m = m0 + 8 * cc;
+        const uint32_t off = rowoff + (uint32_t)((m >> 6) * 1024) + (uint32_t)(((((m & 63) >> 3) ^ (r & 7))) << 4);
+        sts128(a2hi + off, hi[4 * cc], hi[4 * cc + 1], hi[4 * cc + 2], hi[4 * cc + 3]);
+        sts128(a2lo + off, lw[4 * cc], lw[4 * cc + 1], lw[4 * cc + 2], lw[4 * cc + 3]);
+      }
     }
   }
+  if (kLoOverD1) fill_cols<P::N1>(td2 + P::N1, lo, lo);
 }
 
 template <int Nb, bool LP, bool DUMP>
@@ -334,7 +334,7 @@ __device__ __forceinline__ void epilogue2(const TcParams& p, uint32_t td2, const
                                           uint64_t* slot_free) {
   using P = PC<Nb, LP>;
   constexpr int NK = P::NK;
-  constexpr int HALF = NK > 16 ? 16 : NK;  // columns loaded at a time (bounds register use)
+  constexpr int HALF = NK > 16 ? 8 : NK;  // columns loaded at a time (bounds register use)
   const int m = 32 * q + lane;
   const int b2 = m / NK;
   const int v = m % NK;
