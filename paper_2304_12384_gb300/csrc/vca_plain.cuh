@@ -6,6 +6,7 @@
 // and produces T[r][k] = (sum_c x[r][c] M[k][c] + 2^(s1-1)) >> s1; stage 2: lane (j, v)
 // keeps column v of T in registers and produces Z[u][v] = (sum_r M[u][r] T[r][v] +
 // 2^(s2-1)) >> s2, accumulating H_v = sum_u w(u,v) |Z[u][v]| in increasing u with FMA.
+// Both sums use the even/odd butterfly (Butterfly below), which equals the matrix form exactly.
 // The block energy is then the xor-butterfly sum of H_v over the NK lanes of the block
 // (offsets NK/2 .. 1), the same order the tensor-core form uses, so both forms give
 // bit-identical H.
@@ -46,6 +47,52 @@ __device__ __forceinline__ void load_row(const Pix* row, int x0, int width, int 
     for (int c = 0; c < N; ++c) x[c] = row[min(x0 + c, width - 1)];
   }
 }
+
+// y[k] = sum_n M_N[k][n] x[n] for k < NK (N a power of two), by even/odd decomposition: with
+// e[n] = x[n] + x[N-1-n] and o[n] = x[n] - x[N-1-n] (n < N/2), the even outputs are the
+// N/2-point transform of e (the even rows of M_N are M_{N/2} on the first N/2 columns) and the
+// odd outputs apply the odd rows of M_N, first N/2 columns, to o; M_1 = [64].  M points at the
+// full matrix in shared memory (LD ints per row); at recursion step S, row k of the current
+// matrix is row k * S of the full one.  Integer arithmetic, so the result equals the matrix form
+// exactly.
+template <int N, int NK, int S, int LD>
+struct Butterfly {
+  static __device__ __forceinline__ void run(const int (&x)[N], int (&y)[NK], const int* M) {
+    constexpr int H = N / 2;
+    constexpr int NKE = (NK + 1) / 2;
+    int e[H], o[H];
+#pragma unroll
+    for (int n = 0; n < H; ++n) {
+      e[n] = x[n] + x[N - 1 - n];
+      o[n] = x[n] - x[N - 1 - n];
+    }
+    int ye[NKE];
+    Butterfly<H, NKE, 2 * S, LD>::run(e, ye, M);
+#pragma unroll
+    for (int k = 0; 2 * k < NK; ++k) y[2 * k] = ye[k];
+#pragma unroll
+    for (int k = 1; k < NK; k += 2) {
+      const int* row = M + k * S * LD;
+      int acc = 0;
+      if (H >= 4) {
+#pragma unroll
+        for (int n = 0; n < H; n += 4) {
+          const int4 m = *reinterpret_cast<const int4*>(row + n);
+          acc += m.x * o[n] + m.y * o[n + 1] + m.z * o[n + 2] + m.w * o[n + 3];
+        }
+      } else {
+#pragma unroll
+        for (int n = 0; n < H; ++n) acc += row[n] * o[n];
+      }
+      y[k] = acc;
+    }
+  }
+};
+
+template <int NK, int S, int LD>
+struct Butterfly<1, NK, S, LD> {
+  static __device__ __forceinline__ void run(const int (&x)[1], int (&y)[NK], const int*) { y[0] = 64 * x[0]; }
+};
 
 // Shared memory of one CTA of the block routine.
 template <int N, bool LP>
@@ -91,16 +138,10 @@ __device__ __forceinline__ void plain_blocks(const PlainArgs& p, int plane, int 
     int x[N];
     const int yy = min(by * N + r, p.height - 1);
     load_row<N, Pix>(reinterpret_cast<const Pix*>(base + (int64_t)yy * p.pitch), bx * N, p.width, x);
-#pragma unroll 2
-    for (int kk = 0; kk < NK; ++kk) {
-      int acc = 0;
+    int y[NK];
+    Butterfly<N, NK, 1, N>::run(x, y, &sM[0][0]);
 #pragma unroll
-      for (int c = 0; c < N; c += 4) {
-        const int4 m = *reinterpret_cast<const int4*>(&sM[kk][c]);
-        acc += m.x * x[c] + m.y * x[c + 1] + m.z * x[c + 2] + m.w * x[c + 3];
-      }
-      sT[warp][j][r][kk] = (acc + off1) >> p.s1;
-    }
+    for (int kk = 0; kk < NK; ++kk) sT[warp][j][r][kk] = (y[kk] + off1) >> p.s1;
   }
   __syncwarp();
 
@@ -112,15 +153,11 @@ __device__ __forceinline__ void plain_blocks(const PlainArgs& p, int plane, int 
 #pragma unroll
     for (int rr = 0; rr < N; ++rr) t[rr] = sT[warp][j][rr][v];
     int16_t* zd = p.zdump[plane] && f == 0 ? p.zdump[plane] + k * NK * NK : nullptr;
-#pragma unroll 2
-    for (int u = 0; u < NK; ++u) {
-      int acc = 0;
+    int zr[NK];
+    Butterfly<N, NK, 1, N>::run(t, zr, &sM[0][0]);
 #pragma unroll
-      for (int c = 0; c < N; c += 4) {
-        const int4 m = *reinterpret_cast<const int4*>(&sM[u][c]);
-        acc += m.x * t[c] + m.y * t[c + 1] + m.z * t[c + 2] + m.w * t[c + 3];
-      }
-      const int z = (acc + off2) >> p.s2;
+    for (int u = 0; u < NK; ++u) {
+      const int z = (zr[u] + off2) >> p.s2;
       if (u == 0) z00 = z;
       if (zd) zd[u * NK + v] = (int16_t)z;
       H = fmaf(fabsf((float)z), sW[u][v], H);
