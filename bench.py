@@ -398,6 +398,17 @@ def run_extras(args, an, y, u, v, frames, stream, kern, lp, device):
         variants[name] = {"fps": n / (ms / 1000.0), "kernel_ms_per_launch": kms,
                           "hbm_frac_of_measured": args.frames * FRAME_BYTES / (kms / 1000.0) / 1e9 / load_peaks()[0]}
         a2.close()
+    # 10-bit 2160p (16-bit words): tensor-core and CUDA-core forms on the same frames.
+    _, (y10, u10, v10) = make_device_frames(args, device, bit_depth=10)
+    for vk in (vca.VCA_KERNEL_TC, vca.VCA_KERNEL_PLAIN):
+        a2 = vca.Analyzer(W, H, 10, 32, True, kernel=vk, max_batch=args.frames, stream=stream.cuda_stream)
+        name = f"w32_lowpass_10bit_{ {1: 'plain', 2: 'tc'}[a2.kernel] }"
+        ms, kms, _ = time_pushes(a2, y10, u10, v10, max(3, args.steps // 3), 2, stream, lambda: None)
+        n = max(3, args.steps // 3) * args.frames
+        variants[name] = {"fps": n / (ms / 1000.0), "kernel_ms_per_launch": kms,
+                          "hbm_frac_of_measured": args.frames * 2 * FRAME_BYTES / (kms / 1000.0) / 1e9 / load_peaks()[0]}
+        a2.close()
+    del y10, u10, v10
     out["variants"] = variants
 
     # SI / TI of the same 2160p frames (the paper's comparison features; its CPU reference runs

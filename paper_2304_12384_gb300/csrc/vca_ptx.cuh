@@ -210,6 +210,12 @@ __device__ __forceinline__ uint4 lds128(uint32_t saddr) {
   return r;
 }
 
+__device__ __forceinline__ uint16_t lds_u16(uint32_t saddr) {
+  uint16_t r;
+  asm volatile("ld.shared.u16 %0, [%1];" : "=h"(r) : "r"(saddr));
+  return r;
+}
+
 __device__ __forceinline__ uint8_t lds_u8(uint32_t saddr) {
   uint16_t r;
   asm volatile("ld.shared.u8 %0, [%1];" : "=h"(r) : "r"(saddr));

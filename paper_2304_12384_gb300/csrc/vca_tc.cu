@@ -49,22 +49,32 @@ namespace {
 
 using namespace ptx;
 
-constexpr int kStages = 5;    // raw tile ring
-constexpr int kRawY = 128 * 128;
-constexpr int kRawC = 64 * 64;
-constexpr int kStageBytes = kRawY + 2 * kRawC;
-constexpr int kA2L = 8192;  // one stage-2 operand (hi or lo) of one luma job: 128 rows x 32 K x fp16
-constexpr int kA2C = 4096;  // of one chroma job: 128 rows x 16 K x fp16
+constexpr int kMaxStages = 5;  // raw tile ring (barrier indices are laid out for the longest)
+constexpr int kA2L = 8192;      // one stage-2 operand (hi or lo) of one luma job: 128 rows x 32 K x fp16
+constexpr int kA2C = 4096;      // of one chroma job: 128 rows x 16 K x fp16
 constexpr int OFF_RAW = 0;
-constexpr int OFF_A2 = kStages * kStageBytes;   // luma: 2 slots x (hi, lo)
-constexpr int OFF_A2C = OFF_A2 + 2 * 2 * kA2L;  // chroma: 2 slots x (hi, lo)
-constexpr int OFF_BL = OFF_A2C + 2 * 2 * kA2C;
-constexpr int OFF_BC = OFF_BL + 2048;
-constexpr int OFF_BAR = OFF_BC + 512;
 constexpr int kBars = 80;
-constexpr int OFF_MISC = OFF_BAR + kBars * 8;
-constexpr int kSmemBytes = OFF_MISC + 64 + 1024;  // + slack to align the base to 1024
-constexpr int kA2Slots = 4;                       // 0-1 luma jobs, 2-3 chroma jobs
+constexpr int kA2Slots = 4;     // 0-1 luma jobs, 2-3 chroma jobs
+
+// Shared-memory layout for BPS bytes per sample.  8-bit: a 128x128 luma tile (128-byte rows,
+// 128-byte swizzle) and two 64x64 chroma tiles (64-byte rows and swizzle), 5 stages.  10-bit
+// (16-bit words): the luma tile as two 64-sample-wide boxes side by side (128-byte rows each,
+// 128-byte swizzle) and 64x64 chroma tiles with 128-byte rows and swizzle, 3 stages.
+template <int BPS>
+struct SmemLay {
+  static constexpr int kStages = BPS == 1 ? 5 : 3;
+  static constexpr int kRawY = 128 * 128 * BPS;
+  static constexpr int kRawC = 64 * 64 * BPS;
+  static constexpr int kStageBytes = kRawY + 2 * kRawC;
+  static constexpr int OFF_A2 = kStages * kStageBytes;   // luma: 2 slots x (hi, lo)
+  static constexpr int OFF_A2C = OFF_A2 + 2 * 2 * kA2L;  // chroma: 2 slots x (hi, lo)
+  static constexpr int OFF_BL = OFF_A2C + 2 * 2 * kA2C;
+  static constexpr int OFF_BC = OFF_BL + 2048;
+  static constexpr int OFF_BAR = OFF_BC + 512;
+  static constexpr int OFF_MISC = OFF_BAR + kBars * 8;
+  static constexpr int kSmemBytes = OFF_MISC + 64 + 1024;  // + slack to align the base to 1024
+  static_assert(kStages <= kMaxStages && OFF_A2 % 1024 == 0 && kSmemBytes <= 232448, "layout");
+};
 
 // TMEM layout: 8 job slots of 64 columns, each holding the stage-1 operand A1 at [0, 32), the
 // stage-1 accumulators D1 at [32, 64), and then the stage-2 accumulators D2 over [0, 32)
@@ -76,14 +86,14 @@ constexpr int kD1Off = 32;
 
 // barrier indices
 __host__ __device__ constexpr int b_raw_full(int s) { return s; }
-__host__ __device__ constexpr int b_raw_empty(int s) { return kStages + s; }
-__host__ __device__ constexpr int b_slot_free(int s) { return 2 * kStages + s; }
-__host__ __device__ constexpr int b_d1(int s) { return 2 * kStages + kSlots + s; }
-__host__ __device__ constexpr int b_d2(int s) { return 2 * kStages + 2 * kSlots + s; }
-__host__ __device__ constexpr int b_a1_full(int s) { return 2 * kStages + 3 * kSlots + s; }
-__host__ __device__ constexpr int b_a2_full(int s) { return 2 * kStages + 4 * kSlots + s; }
-__host__ __device__ constexpr int b_a2_free(int s) { return 2 * kStages + 4 * kSlots + kA2Slots + s; }
-__host__ __device__ constexpr int b_drain(int i) { return 2 * kStages + 4 * kSlots + 2 * kA2Slots + i; }
+__host__ __device__ constexpr int b_raw_empty(int s) { return kMaxStages + s; }
+__host__ __device__ constexpr int b_slot_free(int s) { return 2 * kMaxStages + s; }
+__host__ __device__ constexpr int b_d1(int s) { return 2 * kMaxStages + kSlots + s; }
+__host__ __device__ constexpr int b_d2(int s) { return 2 * kMaxStages + 2 * kSlots + s; }
+__host__ __device__ constexpr int b_a1_full(int s) { return 2 * kMaxStages + 3 * kSlots + s; }
+__host__ __device__ constexpr int b_a2_full(int s) { return 2 * kMaxStages + 4 * kSlots + s; }
+__host__ __device__ constexpr int b_a2_free(int s) { return 2 * kMaxStages + 4 * kSlots + kA2Slots + s; }
+__host__ __device__ constexpr int b_drain(int i) { return 2 * kMaxStages + 4 * kSlots + 2 * kA2Slots + i; }
 static_assert(b_drain(1) < kBars, "barrier area");
 
 constexpr int kThreads = 896;
@@ -100,6 +110,9 @@ struct TcParams {
   int nbx, nby;
   int tiles_x, tiles_y;
   float inv_tiles_x, inv_tiles_per_frame;  // 1 / tiles_x and 1 / (tiles_x * tiles_y) for tile indexing
+  // Stage-1 constants per plane type (0 luma, 1 chroma): accumulator presets c0 (DC column:
+  // 2^(s1-1) - 1024 * 64 * N) and c (2^(s1-1)), and 2^-s1 (s1 = log2 N + B - 9).
+  float s1_c0[2], s1_c[2], s1_inv[2];
   int nframes;
   int total_items;
   int64_t C;
@@ -169,37 +182,74 @@ __device__ __forceinline__ bool wait_bar(const Ctl& c, int idx, uint32_t parity,
   return wait_bar_slow(bar, parity, c.abort, c.err, code, ignore_abort, sleep);
 }
 
+// Byte offset of sample xx of row y of the raw tile of this plane type.
+template <int Nb, int BPS>
+__device__ __forceinline__ uint32_t raw_offset(int y, int xx) {
+  if (BPS == 1) {
+    const int chunk = xx >> 4;
+    const int sw = Nb == 32 ? (chunk ^ (y & 7)) : (chunk ^ ((y >> 1) & 3));
+    return (uint32_t)(y * (Nb == 32 ? 128 : 64) + (sw << 4) + (xx & 15));
+  }
+  // 16-bit samples: 64-sample boxes with 128-byte rows and 128-byte swizzle; luma has two.
+  const int box = Nb == 32 ? (xx >> 6) : 0;
+  const int cx = xx & 63;
+  const int chunk = cx >> 3;
+  return (uint32_t)(box * (Nb == 32 ? 128 : 64) * 128 + y * 128 + ((chunk ^ (y & 7)) << 4) + (cx & 7) * 2);
+}
+
 // Stage-1 operand conversion: 16 samples of this thread's row starting at column x (of the raw
 // tile, edge columns repeated past w_rem) -> 8 words of fp16 pairs (1024 + sample) at TMEM taddr.
-template <int Nb>
+// 8-bit samples become fp16 0x6400 | x by one PRMT per two samples; 10-bit samples (below 1024)
+// by one AND-OR per two.
+template <int Nb, int BPS>
 __device__ __forceinline__ void convert_16(uint32_t base, int y, int x, int w_rem, uint32_t taddr) {
-  constexpr int kRow = Nb == 32 ? 128 : 64;  // raw tile row pitch in bytes
-  uint32_t words[4];
-  if (x + 16 <= w_rem) {
-    const int chunk = x >> 4;
-    const int sw = Nb == 32 ? (chunk ^ (y & 7)) : (chunk ^ ((y >> 1) & 3));
-    const uint4 q = lds128(base + y * kRow + (sw << 4));
-    words[0] = q.x;
-    words[1] = q.y;
-    words[2] = q.z;
-    words[3] = q.w;
-  } else {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) words[i] = 0;
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      const int xx = min(x + c, w_rem - 1);
-      const int chunk = xx >> 4;
-      const int sw = Nb == 32 ? (chunk ^ (y & 7)) : (chunk ^ ((y >> 1) & 3));
-      const uint32_t b = lds_u8(base + y * kRow + (sw << 4) + (xx & 15));
-      words[c >> 2] |= b << (8 * (c & 3));
-    }
-  }
   uint32_t out[8];
+  if (BPS == 1) {
+    uint32_t words[4];
+    if (x + 16 <= w_rem) {
+      const uint4 q = lds128(base + raw_offset<Nb, 1>(y, x));
+      words[0] = q.x;
+      words[1] = q.y;
+      words[2] = q.z;
+      words[3] = q.w;
+    } else {
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    out[2 * i] = prmt(words[i], kSel6464, 0x5140);
-    out[2 * i + 1] = prmt(words[i], kSel6464, 0x5342);
+      for (int i = 0; i < 4; ++i) words[i] = 0;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const uint32_t b = lds_u8(base + raw_offset<Nb, 1>(y, min(x + c, w_rem - 1)));
+        words[c >> 2] |= b << (8 * (c & 3));
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      out[2 * i] = prmt(words[i], kSel6464, 0x5140);
+      out[2 * i + 1] = prmt(words[i], kSel6464, 0x5342);
+    }
+  } else {
+    uint32_t words[8];
+    if (x + 16 <= w_rem) {
+      const uint4 q0 = lds128(base + raw_offset<Nb, 2>(y, x));
+      const uint4 q1 = lds128(base + raw_offset<Nb, 2>(y, x + 8));
+      words[0] = q0.x;
+      words[1] = q0.y;
+      words[2] = q0.z;
+      words[3] = q0.w;
+      words[4] = q1.x;
+      words[5] = q1.y;
+      words[6] = q1.z;
+      words[7] = q1.w;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) words[i] = 0;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const uint32_t v = lds_u16(base + raw_offset<Nb, 2>(y, min(x + c, w_rem - 1)));
+        words[c >> 1] |= v << (16 * (c & 1));
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) out[i] = (words[i] & 0x03FF03FFu) | 0x64006400u;
   }
   tmem_st<8>(taddr, out);
 }
@@ -253,15 +303,17 @@ __device__ __forceinline__ void a2_slot_of(int j, int& slot, int& use) {
 }
 
 // Shared-memory address of the stage-2 operand (hi; lo follows at +kA2L / +kA2C).
+template <int BPS>
 __device__ __forceinline__ uint32_t a2_addr(uint32_t sbase, int a2) {
-  return a2 < 2 ? sbase + OFF_A2 + a2 * 2 * kA2L : sbase + OFF_A2C + (a2 - 2) * 2 * kA2C;
+  using SL = SmemLay<BPS>;
+  return a2 < 2 ? sbase + SL::OFF_A2 + a2 * 2 * kA2L : sbase + SL::OFF_A2C + (a2 - 2) * 2 * kA2C;
 }
 
 // ---- worker phases ----------------------------------------------------------
 
 // Writes the job's stage-1 A operand at ta1 and pre-sets its stage-1 accumulators at td1 to c0
 // (DC column) and c (the others), so that stage 1 leaves T' = c_k + sum in D1.
-template <int Nb, bool LP>
+template <int Nb, bool LP, int BPS>
 __device__ __forceinline__ void convert_job(const uint8_t* raw_plane, int jp, int h_rem, int w_rem, uint32_t ta1,
                                             uint32_t td1, float c0, float c, int q, int lane) {
   using P = PC<Nb, LP>;
@@ -277,7 +329,8 @@ __device__ __forceinline__ void convert_job(const uint8_t* raw_plane, int jp, in
     if (y >= h_rem) y = h_rem - 1;
     const int x = (idx & 3) * Nb;
 #pragma unroll
-    for (int c = 0; c < Nb / 16; ++c) convert_16<Nb>(smem_u32(raw_plane), y, x + 16 * c, w_rem, ta1 + g * P::A1COLS + 8 * c);
+    for (int c = 0; c < Nb / 16; ++c)
+      convert_16<Nb, BPS>(smem_u32(raw_plane), y, x + 16 * c, w_rem, ta1 + g * P::A1COLS + 8 * c);
   }
 }
 
@@ -389,7 +442,8 @@ __device__ __forceinline__ int div_small(int a, int b, float binv) {
   return qt;
 }
 
-__device__ __forceinline__ TileInfo tile_info(const TcParams& p, int t, int cta, int grid, int tiles_per_frame) {
+__device__ __forceinline__ TileInfo tile_info(const TcParams& p, int t, int cta, int grid, int tiles_per_frame,
+                                              int stages = kMaxStages) {
   TileInfo ti;
   const int item = cta + t * grid;
   ti.t = t;
@@ -397,7 +451,7 @@ __device__ __forceinline__ TileInfo tile_info(const TcParams& p, int t, int cta,
   const int r = item - ti.f * tiles_per_frame;
   ti.ty = div_small(r, p.tiles_x, p.inv_tiles_x);
   ti.tx = r - ti.ty * p.tiles_x;
-  ti.stage = t % kStages;
+  ti.stage = t % stages;
   return ti;
 }
 
@@ -414,14 +468,15 @@ __device__ __forceinline__ void plane_jobs(int& r0, int& r1) {
 }
 
 // Convert: raw samples of the tile -> stage-1 A operand in TMEM (and the D1 presets).
-template <int Nb, bool LP>
+template <int Nb, bool LP, int BPS>
 __device__ void convert_loop(const TcParams& p, const Ctl& ctl, uint8_t* sm, uint32_t tq, int n_items, int cta,
                              int grid, int tiles_per_frame, int q, int lane) {
+  using SL = SmemLay<BPS>;
   constexpr int JPT = Jobs<LP>::PER_TILE;
   constexpr int T = 4 * Nb;  // tile edge of this plane in samples
   const int pw = Nb == 32 ? p.W : p.cw, ph = Nb == 32 ? p.H : p.ch;
-  const float c0 = Nb == 32 ? 8.0f - 2097152.0f : 4.0f - 1048576.0f;  // 2^(s1-1) - 1024 * 64 * N
-  const float c = Nb == 32 ? 8.0f : 4.0f;                             // 2^(s1-1)
+  const float c0 = p.s1_c0[Nb == 32 ? 0 : 1];  // 2^(s1-1) - 1024 * 64 * N
+  const float c = p.s1_c[Nb == 32 ? 0 : 1];    // 2^(s1-1)
   int r0, r1;
   plane_jobs<Nb, LP>(r0, r1);
   const int per_tile = r1 - r0;
@@ -430,10 +485,10 @@ __device__ void convert_loop(const TcParams& p, const Ctl& ctl, uint8_t* sm, uin
   const int n = n_items * per_tile;
   for (int k = 0, t = 0, r = r0; k < n; ++k) {
     if (r == r0) {
-      ti = tile_info(p, t, cta, grid, tiles_per_frame);
+      ti = tile_info(p, t, cta, grid, tiles_per_frame, SL::kStages);
       h_rem = ph - ti.ty * T;
       w_rem = pw - ti.tx * T;
-      if (!wait_bar(ctl, b_raw_full(ti.stage), (t / kStages) & 1, 4)) return;
+      if (!wait_bar(ctl, b_raw_full(ti.stage), (t / SL::kStages) & 1, 4)) return;
     }
     const int jj = t * JPT + r;
     int plane, jp;
@@ -441,9 +496,10 @@ __device__ void convert_loop(const TcParams& p, const Ctl& ctl, uint8_t* sm, uin
     const int slot = jj % kSlots;
     if (jj >= kSlots && !wait_bar(ctl, b_slot_free(slot), ((jj / kSlots) - 1) & 1, 4)) return;
     tc_fence_after();
-    const uint8_t* raw = sm + OFF_RAW + ti.stage * kStageBytes + (plane == 0 ? 0 : kRawY + (plane - 1) * kRawC);
+    const uint8_t* raw =
+        sm + OFF_RAW + ti.stage * SL::kStageBytes + (plane == 0 ? 0 : SL::kRawY + (plane - 1) * SL::kRawC);
     const uint32_t ta = tq + slot * kSlotCols;
-    convert_job<Nb, LP>(raw, jp, h_rem, w_rem, ta, ta + kD1Off, c0, c, q, lane);
+    convert_job<Nb, LP, BPS>(raw, jp, h_rem, w_rem, ta, ta + kD1Off, c0, c, q, lane);
     tmem_wait_st();
     tc_fence_before();
     __syncwarp();
@@ -463,17 +519,19 @@ __device__ void convert_loop(const TcParams& p, const Ctl& ctl, uint8_t* sm, uin
 
 // Epilogue 1: T = floor(T'/2^s1) into the stage-2 operand (hi and lo bytes as fp16, MN-major), and
 // the stage-2 accumulators pre-set: hi starts at K1 - 1156 * 64 * N for u = 0 (the 1024 + byte
-// encoding of both halves) and K1 otherwise, lo at 2^(s2-1) (luma N = 32: s1 = 4, s2 = 11; chroma
-// N = 16: s1 = 3, s2 = 10).  Each plane type cycles through its own two stage-2 operand slots, so
+// encoding of both halves) and K1 otherwise, lo at 2^(s2-1) (luma N = 32: s2 = 11; chroma
+// N = 16: s2 = 10; s1 = log2 N + B - 9 comes with the parameters).  Each plane type cycles through its own two stage-2 operand slots, so
 // every slot's full / free barriers see one in-order stream of jobs.
-template <int Nb, bool LP>
-__device__ void epi1_loop(const Ctl& ctl, uint32_t sbase, uint32_t tq, int n_items, int q, int lane) {
+template <int Nb, bool LP, int BPS>
+__device__ void epi1_loop(const TcParams& p, const Ctl& ctl, uint32_t sbase, uint32_t tq, int n_items, int q,
+                          int lane) {
+  using SL = SmemLay<BPS>;
   constexpr int JPT = Jobs<LP>::PER_TILE;
-  const float s1inv = Nb == 32 ? 0.0625f : 0.125f;
+  const float s1inv = p.s1_inv[Nb == 32 ? 0 : 1];
   const float hi0 = Nb == 32 ? kK1 - 2367488.0f : kK1 - 1183744.0f;
   const float lo = Nb == 32 ? 1024.0f : 512.0f;
   const uint32_t lo_off = Nb == 32 ? kA2L : kA2C;
-  const uint32_t a2base = Nb == 32 ? sbase + OFF_A2 : sbase + OFF_A2C;
+  const uint32_t a2base = Nb == 32 ? sbase + SL::OFF_A2 : sbase + SL::OFF_A2C;
   const int a2first = Nb == 32 ? 0 : 2;
   int r0, r1;
   plane_jobs<Nb, LP>(r0, r1);
@@ -536,7 +594,7 @@ __device__ void epi2_loop(const TcParams& p, const Ctl& ctl, uint32_t tq, int n_
   }
 }
 
-template <bool LP, bool DUMP>
+template <bool LP, bool DUMP, int BPS>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_kernel(const __grid_constant__ CUtensorMap mapY, const __grid_constant__ CUtensorMap mapU,
               const __grid_constant__ CUtensorMap mapV, const TcParams p) {
@@ -546,9 +604,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   static_assert(kSlots % JPT == 0, "a TMEM slot must always hold the same plane type");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = (uint64_t*)(sm + OFF_BAR);
-  uint32_t* tmem_slot = (uint32_t*)(sm + OFF_MISC);
-  volatile int* abort_flag = (volatile int*)(sm + OFF_MISC + 4);
+  using SL = SmemLay<BPS>;
+  uint64_t* bars = (uint64_t*)(sm + SL::OFF_BAR);
+  uint32_t* tmem_slot = (uint32_t*)(sm + SL::OFF_MISC);
+  volatile int* abort_flag = (volatile int*)(sm + SL::OFF_MISC + 4);
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const int lane = tid & 31;
@@ -566,16 +625,16 @@ __global__ void __launch_bounds__(kThreads, 1)
   for (int i = tid; i < L::N1 * 32; i += kThreads) {
     const int n = i >> 5, kk = i & 31;
     const __half h = __float2half_rn((float)p.M_y[n * 32 + kk]);
-    *(__half*)(sm + OFF_BL + (n >> 3) * 512 + (kk >> 3) * 128 + (n & 7) * 16 + (kk & 7) * 2) = h;
+    *(__half*)(sm + SL::OFF_BL + (n >> 3) * 512 + (kk >> 3) * 128 + (n & 7) * 16 + (kk & 7) * 2) = h;
   }
   for (int i = tid; i < 16 * 16; i += kThreads) {
     const int n = i >> 4, kk = i & 15;
     const __half h = __float2half_rn((float)p.M_c[n * 16 + kk]);
-    *(__half*)(sm + OFF_BC + (n >> 3) * 256 + (kk >> 3) * 128 + (n & 7) * 16 + (kk & 7) * 2) = h;
+    *(__half*)(sm + SL::OFF_BC + (n >> 3) * 256 + (kk >> 3) * 128 + (n & 7) * 16 + (kk & 7) * 2) = h;
   }
   if (tid == 0) {
     for (int i = 0; i < kBars; ++i) mbar_init(&bars[i], 1);
-    for (int i = 0; i < kStages; ++i) mbar_init(&bars[b_raw_empty(i)], 8);  // both convert warpgroups
+    for (int i = 0; i < SL::kStages; ++i) mbar_init(&bars[b_raw_empty(i)], 8);  // both convert warpgroups
     for (int i = 0; i < kSlots; ++i) mbar_init(&bars[b_slot_free(i)], 4);
     for (int i = 0; i < kSlots; ++i) mbar_init(&bars[b_a1_full(i)], 4);
     for (int i = 0; i < kA2Slots; ++i) mbar_init(&bars[b_a2_full(i)], 4);
@@ -604,24 +663,27 @@ __global__ void __launch_bounds__(kThreads, 1)
       // ---------------- TMA producer: tiles in order into the ring ----------------
       int issued = 0;
       for (int t = 0; t < n_items; ++t) {
-        const int stage = t % kStages;
-        if (t >= kStages && !wait_bar(ctl, b_raw_empty(stage), ((t / kStages) - 1) & 1, 1, false, true)) break;
+        const int stage = t % SL::kStages;
+        if (t >= SL::kStages && !wait_bar(ctl, b_raw_empty(stage), ((t / SL::kStages) - 1) & 1, 1, false, true))
+          break;
         const TileInfo ti = tile_info(p, t, cta, grid, tiles_per_frame);
-        uint8_t* dst = sm + OFF_RAW + stage * kStageBytes;
-        mbar_arrive_expect_tx(&bars[b_raw_full(stage)], kStageBytes);
+        uint8_t* dst = sm + OFF_RAW + stage * SL::kStageBytes;
+        mbar_arrive_expect_tx(&bars[b_raw_full(stage)], SL::kStageBytes);
         tma_load_3d(dst, &mapY, ti.tx * 128, ti.ty * 128, ti.f, &bars[b_raw_full(stage)]);
-        tma_load_3d(dst + kRawY, &mapU, ti.tx * 64, ti.ty * 64, ti.f, &bars[b_raw_full(stage)]);
-        tma_load_3d(dst + kRawY + kRawC, &mapV, ti.tx * 64, ti.ty * 64, ti.f, &bars[b_raw_full(stage)]);
+        if (BPS == 2)  // 16-bit luma: the right half of the tile is a second 64-sample box
+          tma_load_3d(dst + SL::kRawY / 2, &mapY, ti.tx * 128 + 64, ti.ty * 128, ti.f, &bars[b_raw_full(stage)]);
+        tma_load_3d(dst + SL::kRawY, &mapU, ti.tx * 64, ti.ty * 64, ti.f, &bars[b_raw_full(stage)]);
+        tma_load_3d(dst + SL::kRawY + SL::kRawC, &mapV, ti.tx * 64, ti.ty * 64, ti.f, &bars[b_raw_full(stage)]);
         ++issued;
       }
       if (*abort_flag) {
         // Let every copy this CTA issued land before the CTA's shared memory goes away.
-        for (int t = (issued > kStages ? issued - kStages : 0); t < issued; ++t)
-          wait_bar(ctl, b_raw_full(t % kStages), (t / kStages) & 1, 1, true);
+        for (int t = (issued > SL::kStages ? issued - SL::kStages : 0); t < issued; ++t)
+          wait_bar(ctl, b_raw_full(t % SL::kStages), (t / SL::kStages) & 1, 1, true);
       }
     } else if (warp == 1 && lane == 0) {
       // ---------------- stage-1 MMA issuer: D1 += A1 (TMEM) x M^T (D1 pre-set by convert) ----------------
-      const uint32_t bl = sbase + OFF_BL, bc = sbase + OFF_BC;
+      const uint32_t bl = sbase + SL::OFF_BL, bc = sbase + SL::OFF_BC;
       constexpr uint32_t idL = idesc_f16(128, L::N1, 0, 0), idC = idesc_f16(128, Cc::N1, 0, 0);
       bool ok = true;
       for (int j = 0; j < n_jobs; ++j) {
@@ -655,7 +717,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     } else if (warp == 2 && lane == 0) {
       // ---------------- stage-2 MMA issuer: D2 = A2 (smem, MN-major) x M^T, hi and lo ----------------
-      const uint32_t bl = sbase + OFF_BL, bc = sbase + OFF_BC;
+      const uint32_t bl = sbase + SL::OFF_BL, bc = sbase + SL::OFF_BC;
       constexpr uint32_t id2L = idesc_f16(128, L::N1, 1, 0), id2C = idesc_f16(128, Cc::N1, 1, 0);
       bool ok = true;
       for (int j = 0; j < n_jobs; ++j) {
@@ -669,7 +731,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc_fence_after();
         const uint32_t d = tmem + (j % kSlots) * kSlotCols;
-        const uint32_t ahi = a2_addr(sbase, a2);
+        const uint32_t ahi = a2_addr<BPS>(sbase, a2);
         if (plane == 0) {
 #pragma unroll
           for (int ks = 0; ks < 2; ++ks) {
@@ -691,13 +753,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else if (role == 1) {
-    convert_loop<32, LP>(p, ctl, sm, tmem + lanebase, n_items, cta, grid, tiles_per_frame, q, lane);
+    convert_loop<32, LP, BPS>(p, ctl, sm, tmem + lanebase, n_items, cta, grid, tiles_per_frame, q, lane);
   } else if (role == 6) {
-    convert_loop<16, LP>(p, ctl, sm, tmem + lanebase, n_items, cta, grid, tiles_per_frame, q, lane);
+    convert_loop<16, LP, BPS>(p, ctl, sm, tmem + lanebase, n_items, cta, grid, tiles_per_frame, q, lane);
   } else if (role == 2) {
-    epi1_loop<32, LP>(ctl, sbase, tmem + lanebase, n_items, q, lane);
+    epi1_loop<32, LP, BPS>(p, ctl, sbase, tmem + lanebase, n_items, q, lane);
   } else if (role == 3) {
-    epi1_loop<16, LP>(ctl, sbase, tmem + lanebase, n_items, q, lane);
+    epi1_loop<16, LP, BPS>(p, ctl, sbase, tmem + lanebase, n_items, q, lane);
   } else if (role == 4) {
     epi2_loop<32, LP, DUMP>(p, ctl, tmem + lanebase, n_items, cta, grid, tiles_per_frame, q, lane);
   } else {
@@ -732,30 +794,32 @@ EncodeTiledFn encode_fn() {
 }
 
 cudaError_t make_map(CUtensorMap* m, const void* base, int w, int h, int64_t pitch, int64_t fstride, int nframes,
-                     int box, CUtensorMapSwizzle sw) {
+                     int box_w, int box_h, int bps, CUtensorMapSwizzle sw) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   if (nframes == 1 || fstride <= 0) fstride = ((pitch * h + 15) / 16) * 16;
   cuuint64_t dims[3] = {(cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)nframes};
   cuuint64_t strides[2] = {(cuuint64_t)pitch, (cuuint64_t)fstride};
-  cuuint32_t boxd[3] = {(cuuint32_t)box, (cuuint32_t)box, 1};
+  cuuint32_t boxd[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1};
   cuuint32_t es[3] = {1, 1, 1};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void*>(base), dims, strides, boxd, es,
+  const CUtensorMapDataType dt = bps == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+  CUresult r = enc(m, dt, 3, const_cast<void*>(base), dims, strides, boxd, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <bool LP, bool DUMP>
+template <bool LP, bool DUMP, int BPS>
 cudaError_t launch_inst(const CUtensorMap& my, const CUtensorMap& mu, const CUtensorMap& mv, const TcParams& p,
                         int grid, cudaStream_t s) {
+  constexpr int kSmem = SmemLay<BPS>::kSmemBytes;
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(tc_kernel<LP, DUMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    attr = cudaFuncSetAttribute(tc_kernel<LP, DUMP, BPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
   });
   if (attr != cudaSuccess) return attr;
-  tc_kernel<LP, DUMP><<<grid, kThreads, kSmemBytes, s>>>(my, mu, mv, p);
+  tc_kernel<LP, DUMP, BPS><<<grid, kThreads, kSmem, s>>>(my, mu, mv, p);
   return cudaGetLastError();
 }
 
@@ -768,18 +832,23 @@ int sm_count() {
 
 }  // namespace
 
-bool tc_supported(const Geometry& g) { return g.B == 8 && g.w == 32 && g.nc == 16 && encode_fn() != nullptr; }
+bool tc_supported(const Geometry& g) {
+  return (g.B == 8 || g.B == 10) && g.w == 32 && g.nc == 16 && encode_fn() != nullptr;
+}
 
 cudaError_t launch_tc(const Geometry& g, const FramePlanes& fp, int nframes, const DeviceTables& t, float* blockvals,
                       int16_t* const zdump[3], int* err, cudaStream_t s, int64_t* launches) {
   if (!tc_supported(g)) return cudaErrorNotSupported;
   if (nframes <= 0) return cudaSuccess;
+  // 8-bit: 128x128 luma boxes (128-byte swizzle), 64x64 chroma boxes (64-byte swizzle); 16-bit:
+  // 64x128 luma boxes (two per tile) and 64x64 chroma boxes, all 128-byte rows and swizzle.
+  const int bps = g.bps;
+  const CUtensorMapSwizzle swc = bps == 1 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
   CUtensorMap my, mu, mv;
-  cudaError_t e = make_map(&my, fp.y, g.W, g.H, fp.pitch_y, fp.fstride_y, nframes, 128, CU_TENSOR_MAP_SWIZZLE_128B);
-  if (e == cudaSuccess)
-    e = make_map(&mu, fp.u, g.cw, g.ch, fp.pitch_uv, fp.fstride_uv, nframes, 64, CU_TENSOR_MAP_SWIZZLE_64B);
-  if (e == cudaSuccess)
-    e = make_map(&mv, fp.v, g.cw, g.ch, fp.pitch_uv, fp.fstride_uv, nframes, 64, CU_TENSOR_MAP_SWIZZLE_64B);
+  cudaError_t e = make_map(&my, fp.y, g.W, g.H, fp.pitch_y, fp.fstride_y, nframes, bps == 1 ? 128 : 64, 128, bps,
+                           CU_TENSOR_MAP_SWIZZLE_128B);
+  if (e == cudaSuccess) e = make_map(&mu, fp.u, g.cw, g.ch, fp.pitch_uv, fp.fstride_uv, nframes, 64, 64, bps, swc);
+  if (e == cudaSuccess) e = make_map(&mv, fp.v, g.cw, g.ch, fp.pitch_uv, fp.fstride_uv, nframes, 64, 64, bps, swc);
   if (e != cudaSuccess) return e;
   TcParams p{};
   p.W = g.W;
@@ -803,12 +872,28 @@ cudaError_t launch_tc(const Geometry& g, const FramePlanes& fp, int nframes, con
   p.W_y = t.W_y;
   p.W_c = t.W_c;
   p.err = err;
+  for (int pt = 0; pt < 2; ++pt) {  // s1 = log2 N + B - 9; presets 2^(s1-1) (- 1024 * 64 * N on the DC column)
+    const int s1 = pt == 0 ? g.s1y : g.s1c;
+    const int N = pt == 0 ? g.w : g.nc;
+    p.s1_c[pt] = (float)(1 << (s1 - 1));
+    p.s1_c0[pt] = (float)(1 << (s1 - 1)) - 1024.0f * 64.0f * (float)N;
+    p.s1_inv[pt] = 1.0f / (float)(1 << s1);
+  }
   const int grid = p.total_items < sm_count() ? p.total_items : sm_count();
   const bool dump = zdump != nullptr;
-  if (g.low_pass)
-    e = dump ? launch_inst<true, true>(my, mu, mv, p, grid, s) : launch_inst<true, false>(my, mu, mv, p, grid, s);
-  else
-    e = dump ? launch_inst<false, true>(my, mu, mv, p, grid, s) : launch_inst<false, false>(my, mu, mv, p, grid, s);
+  if (bps == 1) {
+    if (g.low_pass)
+      e = dump ? launch_inst<true, true, 1>(my, mu, mv, p, grid, s) : launch_inst<true, false, 1>(my, mu, mv, p, grid, s);
+    else
+      e = dump ? launch_inst<false, true, 1>(my, mu, mv, p, grid, s)
+               : launch_inst<false, false, 1>(my, mu, mv, p, grid, s);
+  } else {
+    if (g.low_pass)
+      e = dump ? launch_inst<true, true, 2>(my, mu, mv, p, grid, s) : launch_inst<true, false, 2>(my, mu, mv, p, grid, s);
+    else
+      e = dump ? launch_inst<false, true, 2>(my, mu, mv, p, grid, s)
+               : launch_inst<false, false, 2>(my, mu, mv, p, grid, s);
+  }
   if (e == cudaSuccess) ++*launches;
   return e;
 }
