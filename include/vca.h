@@ -210,9 +210,15 @@ typedef struct {
 } vca_frame_ref;
 
 /* Groups n analyzers (1 .. 65535, distinct, none already in a batch).  Waits for the analyzers'
- * earlier work, builds the CTA map and captures two tick graphs on a stream of its own.
- * VCA_E_ARG for mismatched devices, block sizes or low_pass. */
+ * earlier work and captures two tick graphs on a stream of its own.  If every analyzer runs the
+ * tensor-core kernel and n <= 64, a tick analyses all of them in one launch of the persistent
+ * tensor-core kernel (8- and 10-bit members may be mixed; the tensor maps of the tick's frames
+ * are encoded on the host at each tick); otherwise in one launch of the batched CUDA-core kernel,
+ * whose CTA map is built here.  VCA_E_ARG for mismatched devices, block sizes or low_pass. */
 vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch** out);
+
+/* The kernel family a batch's ticks run: VCA_KERNEL_TC or VCA_KERNEL_PLAIN. */
+vca_status vca_batch_kernel(vca_batch* b, int32_t* kernel);
 
 /* One tick: frames[i] (n entries, in the order of vca_batch_create) for analyzer i.  Returns
  * after queuing the tick (at most two ticks are in flight; the third waits for the first).
@@ -220,7 +226,9 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
  * returns.  A bad frame reference gives VCA_E_ARG and queues nothing. */
 vca_status vca_batch_tick(vca_batch* b, const vca_frame_ref* frames);
 
-/* Waits for every queued tick and delivers its features to the analyzers. */
+/* Waits for every queued tick and delivers its features to the analyzers.  VCA_E_TIMEOUT if the
+ * tensor-core kernel gave up on a bounded wait during a tick: that tick's features are lost (the
+ * analyzers' frame counters and h state have moved on). */
 vca_status vca_batch_sync(vca_batch* b);
 
 /* Kernel launches issued by the batch's ticks (two per tick). */

@@ -139,10 +139,11 @@ struct vca_analyzer {
 };
 
 // A batch of analyzers ticked together: one frame each per tick, analysed by one launch of the
-// batched plain kernel and one launch of the batched reduction, replayed from a CUDA graph.  The
-// per-tick arguments live in pinned host memory that a copy node of the graph uploads, so the
-// graph never changes; two graphs alternate so that a tick's arguments can be written while the
-// previous tick runs.
+// batched tensor-core kernel (every member on the tensor-core kernel, at most
+// tc_batch_max_members()) or of the batched plain kernel, and one launch of the batched
+// reduction, replayed from a CUDA graph.  The per-tick arguments live in pinned host memory that
+// a copy node of the graph uploads, so the graph never changes; two graphs alternate so that a
+// tick's arguments can be written while the previous tick runs.
 struct vca_batch {
   std::vector<vca_analyzer*> m;
   int n = 0;
@@ -150,12 +151,17 @@ struct vca_batch {
   int w = 32;
   int nc = 16;
   bool low_pass = false;
+  bool tc = false;                 // analysis on the tensor-core kernel
+  int tc_bps = 1;                  // members' sample size (0: mixed)
   cudaStream_t stream = nullptr;
   vca::BatchCta* d_map = nullptr;
   int n_cta = 0;
   size_t ma_bytes = 0, desc_bytes = 0;
-  uint8_t* d_desc = nullptr;       // BatchMemberArgs[n] | ReduceArgs[n]
+  uint8_t* d_desc = nullptr;       // analysis arguments (tensor-core descriptor block or BatchMemberArgs[n]) | ReduceArgs[n]
   uint8_t* h_desc[2] = {nullptr, nullptr};
+  int* d_err = nullptr;            // the tensor-core kernel's wait-timeout flag
+  int* h_err = nullptr;            // pinned, one per graph
+  std::vector<vca::TcBatchFrame> tc_frames;
   double* d_feats = nullptr;       // n x FEAT_STRIDE
   double* h_feats[2] = {nullptr, nullptr};
   double* d_partials = nullptr;
@@ -413,6 +419,13 @@ vca_status batch_harvest_front(vca_batch* b, bool blocking) {
     if (q == cudaErrorNotReady) return fail(VCA_E_AGAIN, "frame features not ready yet");
     if (q != cudaSuccess) return cuda_fail(q, "querying a batch tick");
   }
+  if (b->h_err[t.k] != 0) {
+    const int code = b->h_err[t.k];
+    b->h_err[t.k] = 0;
+    b->pending.pop_front();
+    return fail(VCA_E_TIMEOUT, "batched analysis kernel gave up on a bounded wait (code %d); the tick's frames are lost",
+                code);
+  }
   for (const auto& mm : t.members) {
     vca_analyzer* a = b->m[mm.index];
     const double* f = b->h_feats[t.k] + (size_t)mm.index * vca::FEAT_STRIDE;
@@ -467,6 +480,8 @@ void destroy_batch(vca_batch* b) {
   }
   cudaFree(b->d_map);
   cudaFree(b->d_desc);
+  cudaFree(b->d_err);
+  if (b->h_err) cudaFreeHost(b->h_err);
   cudaFree(b->d_feats);
   cudaFree(b->d_partials);
   cudaFree(b->d_counters);
@@ -480,14 +495,21 @@ cudaError_t build_tick_graph(vca_batch* b, int k) {
   cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
   cudaError_t e1 = cudaMemcpyAsync(b->d_desc, b->h_desc[k], b->desc_bytes, cudaMemcpyHostToDevice, b->stream);
-  if (e1 == cudaSuccess)
+  if (e1 == cudaSuccess && b->tc) {
+    e1 = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
+    if (e1 == cudaSuccess)
+      e1 = vca::launch_tc_batch(b->d_desc, b->tc_bps, b->low_pass, b->m[0]->tables, b->d_err, b->stream);
+  } else if (e1 == cudaSuccess) {
     e1 = vca::launch_batch_plain(b->d_map, b->n_cta, reinterpret_cast<const vca::BatchMemberArgs*>(b->d_desc), b->w,
                                  b->nc, b->low_pass, b->stream);
+  }
   if (e1 == cudaSuccess)
     e1 = vca::launch_reduce_batch(reinterpret_cast<const vca::ReduceArgs*>(b->d_desc + b->ma_bytes), b->n, b->stream);
   if (e1 == cudaSuccess)
     e1 = cudaMemcpyAsync(b->h_feats[k], b->d_feats, (size_t)b->n * vca::FEAT_STRIDE * sizeof(double),
                          cudaMemcpyDeviceToHost, b->stream);
+  if (e1 == cudaSuccess && b->tc)
+    e1 = cudaMemcpyAsync(b->h_err + k, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
   e = cudaStreamEndCapture(b->stream, &b->graph[k]);
   if (e1 != cudaSuccess) return e1;
   if (e != cudaSuccess) return e;
@@ -904,6 +926,11 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
   b->w = members[0]->g.w;
   b->nc = members[0]->g.nc;
   b->low_pass = members[0]->g.low_pass;
+  b->tc = n <= vca::tc_batch_max_members();
+  for (int i = 0; i < n; ++i) b->tc = b->tc && members[i]->kernel == VCA_KERNEL_TC;
+  b->tc_bps = members[0]->g.bps;
+  for (int i = 0; i < n; ++i)
+    if (members[i]->g.bps != b->tc_bps) b->tc_bps = 0;
   int prev_dev = -1;
   cudaGetDevice(&prev_dev);
 
@@ -929,7 +956,7 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
     BATCH_CUDA(cudaStreamSynchronize(members[i]->side), "waiting for an analyzer's earlier work");
   }
   std::vector<vca::BatchCta> map;
-  for (int i = 0; i < n; ++i) {
+  for (int i = 0; i < n && !b->tc; ++i) {
     const Geometry& g = members[i]->g;
     const int64_t cl = (g.C + vca::plain_blocks_per_cta(g.w) - 1) / vca::plain_blocks_per_cta(g.w);
     const int64_t cc = (g.C + vca::plain_blocks_per_cta(g.nc) - 1) / vca::plain_blocks_per_cta(g.nc);
@@ -942,12 +969,21 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
     return fail(VCA_E_ARG, "batch too large");
   }
   b->n_cta = (int)map.size();
-  b->ma_bytes = round_up((size_t)n * sizeof(vca::BatchMemberArgs), 256);
+  b->ma_bytes = b->tc ? round_up(vca::tc_batch_desc_bytes(), 256)
+                      : round_up((size_t)n * sizeof(vca::BatchMemberArgs), 256);
   b->desc_bytes = b->ma_bytes + (size_t)n * sizeof(vca::ReduceArgs);
   BATCH_CUDA(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking), "creating the batch stream");
-  BATCH_CUDA(cudaMalloc(&b->d_map, map.size() * sizeof(vca::BatchCta)), "allocating the CTA map");
-  BATCH_CUDA(cudaMemcpy(b->d_map, map.data(), map.size() * sizeof(vca::BatchCta), cudaMemcpyHostToDevice),
-             "uploading the CTA map");
+  if (!b->tc) {
+    BATCH_CUDA(cudaMalloc(&b->d_map, map.size() * sizeof(vca::BatchCta)), "allocating the CTA map");
+    BATCH_CUDA(cudaMemcpy(b->d_map, map.data(), map.size() * sizeof(vca::BatchCta), cudaMemcpyHostToDevice),
+               "uploading the CTA map");
+  }
+  if (b->tc) BATCH_CUDA(vca::tc_batch_prepare(b->tc_bps, b->low_pass), "preparing the tensor-core kernel");
+  BATCH_CUDA(cudaMalloc(&b->d_err, sizeof(int)), "allocating the error flag");
+  BATCH_CUDA(cudaMemset(b->d_err, 0, sizeof(int)), "clearing the error flag");
+  BATCH_CUDA(cudaMallocHost(&b->h_err, 2 * sizeof(int)), "allocating pinned error flags");
+  b->h_err[0] = b->h_err[1] = 0;
+  b->tc_frames.reserve(n);
   BATCH_CUDA(cudaMalloc(&b->d_desc, b->desc_bytes), "allocating tick arguments");
   BATCH_CUDA(cudaMalloc(&b->d_feats, (size_t)n * vca::FEAT_STRIDE * sizeof(double)), "allocating features");
   BATCH_CUDA(cudaMalloc(&b->d_partials, vca::reduce_partials_bytes(n)), "allocating reduction scratch");
@@ -985,22 +1021,35 @@ vca_status vca_batch_tick(vca_batch* b, const vca_frame_ref* frames) {
   auto* ra = reinterpret_cast<vca::ReduceArgs*>(b->h_desc[k] + b->ma_bytes);
   vca_batch::Tick tick;
   tick.k = k;
+  b->tc_frames.clear();
   for (int i = 0; i < b->n; ++i) {
     vca_analyzer* a = b->m[i];
     if (!frames[i].y) {
-      ma[i].active = 0;
+      if (!b->tc) ma[i].active = 0;
       ra[i].nframes = 0;
       continue;
     }
-    ma[i].pa[0] = member_plain_args(a, 0, frames[i]);
-    ma[i].pa[1] = member_plain_args(a, 1, frames[i]);
-    ma[i].bps = a->g.bps;
-    ma[i].active = 1;
+    if (b->tc) {
+      const vca_frame_ref& f = frames[i];
+      b->tc_frames.push_back({&a->g,
+                              {static_cast<const uint8_t*>(f.y), static_cast<const uint8_t*>(f.u),
+                               static_cast<const uint8_t*>(f.v), f.pitch_y, f.pitch_uv, 0, 0},
+                              a->d_blockvals});
+    } else {
+      ma[i].pa[0] = member_plain_args(a, 0, frames[i]);
+      ma[i].pa[1] = member_plain_args(a, 1, frames[i]);
+      ma[i].bps = a->g.bps;
+      ma[i].active = 1;
+    }
     ra[i] = vca::reduce_args(a->g, 1, a->d_blockvals, a->d_prevH[a->cur_prev], a->has_prev,
                              a->d_prevH[a->cur_prev ^ 1], b->d_feats + (size_t)i * vca::FEAT_STRIDE,
                              b->d_partials + (size_t)i * vca::reduce_partials_bytes(1) / sizeof(double),
                              b->d_counters + i);
     tick.members.push_back({i, a->frames_pushed, a->has_prev != 0});
+  }
+  if (b->tc) {
+    const cudaError_t e = vca::tc_batch_fill(b->h_desc[k], b->tc_frames.data(), (int)b->tc_frames.size());
+    if (e != cudaSuccess) return cuda_fail(e, "encoding the tensor maps of a batch tick");
   }
   int prev_dev = -1;
   cudaGetDevice(&prev_dev);
@@ -1027,6 +1076,12 @@ vca_status vca_batch_tick(vca_batch* b, const vca_frame_ref* frames) {
 vca_status vca_batch_sync(vca_batch* b) {
   if (!b) return fail(VCA_E_ARG, "batch is NULL");
   return batch_harvest_all(b);
+}
+
+vca_status vca_batch_kernel(vca_batch* b, int32_t* kernel) {
+  if (!b || !kernel) return fail(VCA_E_ARG, "NULL argument");
+  *kernel = b->tc ? VCA_KERNEL_TC : VCA_KERNEL_PLAIN;
+  return VCA_OK;
 }
 
 vca_status vca_batch_launch_count(vca_batch* b, int64_t* launches) {

@@ -94,6 +94,27 @@ cudaError_t launch_tc(const Geometry& g, const FramePlanes& fp, int nframes, con
                       float* blockvals, int16_t* const zdump[3], int* err, cudaStream_t s, int64_t* launches);
 bool tc_supported(const Geometry& g);
 
+// Batched tensor-core analysis: one frame of each of up to tc_batch_max_members() analyzers in
+// one launch of the persistent kernel.  The launch reads a descriptor block (the member table and
+// each member's tensor maps, tc_batch_desc_bytes() bytes, 128-byte aligned) that the host writes
+// with tc_batch_fill and copies to the device unchanged before the launch.
+struct TcBatchFrame {
+  const Geometry* g;   // the member's analysis geometry (tc_supported)
+  FramePlanes fp;      // its frame (frame strides unused)
+  float* blockvals;    // its [6][C] block values
+};
+int tc_batch_max_members();
+size_t tc_batch_desc_bytes();
+// Fills the descriptor block at h (host memory) for n frames; cudaErrorInvalidValue if n is out
+// of range or a tensor map cannot be encoded.
+cudaError_t tc_batch_fill(void* h, const TcBatchFrame* frames, int n);
+// Sets up the kernel instance for this sample size and low_pass (outside any stream capture).
+cudaError_t tc_batch_prepare(int bps, bool low_pass);
+// Launches the analysis of the descriptor block at d_desc (device).  bps: the members' sample
+// size, or 0 if 8- and 10-bit members are mixed.
+cudaError_t launch_tc_batch(const void* d_desc, int bps, bool low_pass, const DeviceTables& t, int* err,
+                            cudaStream_t s);
+
 // Deterministic FP64 frame reduction: features of n frames and the h state update.  `partials`
 // holds reduce_partials_bytes(max frames) of scratch; `counters` (one per frame) must be zero on
 // entry and is zero again on exit.

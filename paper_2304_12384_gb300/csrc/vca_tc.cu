@@ -55,6 +55,35 @@ constexpr int kA2C = 4096;      // of one chroma job: 128 rows x 16 K x fp16
 constexpr int OFF_RAW = 0;
 constexpr int kBars = 80;
 constexpr int kA2Slots = 4;     // 0-1 luma jobs, 2-3 chroma jobs
+constexpr int kMaxMembers = 64;
+
+// One analyzer ("member") of a launch: its work items, geometry, outputs and stage-1 constants.
+// A single analyzer's launch has one member with all its frames; a batched tick has one member
+// per channel with one frame each.  Items are numbered member by member, frame-major tiles.
+struct TcMember {
+  int item_base;                   // first item of this member
+  int tiles_x, tiles_per_frame;
+  float inv_tiles_x, inv_tiles_per_frame;
+  int W, H, cw, ch, nbx, nby;
+  int bps;                         // bytes per sample: 1 for 8-bit, 2 for 10-bit samples
+  int64_t C, out_fstride;
+  float* blockvals;
+};
+
+// Stage-1 shift s1 = log2 N + B - 9 of a plane type; the bit depth follows from the sample size
+// (8-bit samples in bytes, 10-bit in 16-bit words).
+template <int Nb>
+__host__ __device__ constexpr int s1_of(int bps) {
+  return (Nb == 32 ? 5 : 4) + (bps == 1 ? 8 : 10) - 9;
+}
+constexpr int kMemBytes = kMaxMembers * (int)sizeof(TcMember);
+static_assert(sizeof(TcMember) % 8 == 0, "member table entries are copied as words");
+
+// The member table of a batched launch, in device memory.
+struct TcTable {
+  int n_members, total_items, pad[2];
+  TcMember mem[kMaxMembers];
+};
 
 // Shared-memory layout for BPS bytes per sample.  8-bit: a 128x128 luma tile (128-byte rows,
 // 128-byte swizzle) and two 64x64 chroma tiles (64-byte rows and swizzle), 5 stages.  10-bit
@@ -62,9 +91,10 @@ constexpr int kA2Slots = 4;     // 0-1 luma jobs, 2-3 chroma jobs
 // 128-byte swizzle) and 64x64 chroma tiles with 128-byte rows and swizzle, 3 stages.
 template <int BPS>
 struct SmemLay {
-  static constexpr int kStages = BPS == 1 ? 5 : 3;
-  static constexpr int kRawY = 128 * 128 * BPS;
-  static constexpr int kRawC = 64 * 64 * BPS;
+  static constexpr int kB = BPS == 1 ? 1 : 2;  // BPS 0 (8- and 10-bit members mixed) uses the 16-bit layout
+  static constexpr int kStages = kB == 1 ? 5 : 3;
+  static constexpr int kRawY = 128 * 128 * kB;
+  static constexpr int kRawC = 64 * 64 * kB;
   static constexpr int kStageBytes = kRawY + 2 * kRawC;
   static constexpr int OFF_A2 = kStages * kStageBytes;   // luma: 2 slots x (hi, lo)
   static constexpr int OFF_A2C = OFF_A2 + 2 * 2 * kA2L;  // chroma: 2 slots x (hi, lo)
@@ -73,7 +103,8 @@ struct SmemLay {
   static constexpr int OFF_BAR = OFF_BC + 512;
   static constexpr int OFF_MISC = OFF_BAR + kBars * 8;
   static constexpr int kSmemBytes = OFF_MISC + 64 + 1024;  // + slack to align the base to 1024
-  static_assert(kStages <= kMaxStages && OFF_A2 % 1024 == 0 && kSmemBytes <= 232448, "layout");
+  // (the member table is a static shared array of kMemBytes beside this dynamic area)
+  static_assert(kStages <= kMaxStages && OFF_A2 % 1024 == 0 && kSmemBytes + kMemBytes <= 232448, "layout");
 };
 
 // TMEM layout: 8 job slots of 64 columns, each holding the stage-1 operand A1 at [0, 32), the
@@ -106,24 +137,17 @@ constexpr float kK1 = 12582912.0f;  // 1.5 * 2^23
 constexpr uint32_t kSel6464 = 0x64646464u;
 
 struct TcParams {
-  int W, H, cw, ch;
-  int nbx, nby;
-  int tiles_x, tiles_y;
-  float inv_tiles_x, inv_tiles_per_frame;  // 1 / tiles_x and 1 / (tiles_x * tiles_y) for tile indexing
-  // Stage-1 constants per plane type (0 luma, 1 chroma): accumulator presets c0 (DC column:
-  // 2^(s1-1) - 1024 * 64 * N) and c (2^(s1-1)), and 2^-s1 (s1 = log2 N + B - 9).
-  float s1_c0[2], s1_c[2], s1_inv[2];
-  int nframes;
-  int total_items;
-  int64_t C;
-  int64_t out_fstride;
-  float* blockvals;
+  const TcTable* table;     // batched launch: members in device memory; null: mem0 below
+  const CUtensorMap* maps;  // batched launch: Y, U, V maps of each member
+  int total_items;          // single analyzer
+  TcMember mem0;            // single analyzer
   int16_t* zdump[3];
   const int8_t* M_y;
   const int8_t* M_c;
   const float* W_y;
   const float* W_c;
   int* err;
+  CUtensorMap map0[3];              // single analyzer: Y, U, V
 };
 
 template <int Nb, bool LP>
@@ -203,6 +227,7 @@ __device__ __forceinline__ uint32_t raw_offset(int y, int xx) {
 // by one AND-OR per two.
 template <int Nb, int BPS>
 __device__ __forceinline__ void convert_16(uint32_t base, int y, int x, int w_rem, uint32_t taddr) {
+  static_assert(BPS == 1 || BPS == 2, "one sample size");
   uint32_t out[8];
   if (BPS == 1) {
     uint32_t words[4];
@@ -315,7 +340,7 @@ __device__ __forceinline__ uint32_t a2_addr(uint32_t sbase, int a2) {
 // (DC column) and c (the others), so that stage 1 leaves T' = c_k + sum in D1.
 template <int Nb, bool LP, int BPS>
 __device__ __forceinline__ void convert_job(const uint8_t* raw_plane, int jp, int h_rem, int w_rem, uint32_t ta1,
-                                            uint32_t td1, float c0, float c, int q, int lane) {
+                                            uint32_t td1, float c0, float c, int bps, int q, int lane) {
   using P = PC<Nb, LP>;
 #pragma unroll
   for (int g = 0; g < P::G; ++g) fill_cols<P::N1>(td1 + g * P::N1, c0, c);
@@ -329,8 +354,12 @@ __device__ __forceinline__ void convert_job(const uint8_t* raw_plane, int jp, in
     if (y >= h_rem) y = h_rem - 1;
     const int x = (idx & 3) * Nb;
 #pragma unroll
-    for (int c = 0; c < Nb / 16; ++c)
-      convert_16<Nb, BPS>(smem_u32(raw_plane), y, x + 16 * c, w_rem, ta1 + g * P::A1COLS + 8 * c);
+    for (int c = 0; c < Nb / 16; ++c) {
+      if (BPS == 1 || (BPS == 0 && bps == 1))
+        convert_16<Nb, 1>(smem_u32(raw_plane), y, x + 16 * c, w_rem, ta1 + g * P::A1COLS + 8 * c);
+      else
+        convert_16<Nb, 2>(smem_u32(raw_plane), y, x + 16 * c, w_rem, ta1 + g * P::A1COLS + 8 * c);
+    }
   }
 }
 
@@ -382,7 +411,8 @@ __device__ __forceinline__ void epilogue1(uint32_t td1, uint32_t td2, uint32_t a
 }
 
 template <int Nb, bool LP, bool DUMP>
-__device__ __forceinline__ void epilogue2(const TcParams& p, uint32_t td2, const JobCtx& jc, int q, int lane,
+__device__ __forceinline__ void epilogue2(const TcParams& p, const TcMember& M, uint32_t td2, const JobCtx& jc,
+                                          int q, int lane,
                                           const float (&wts)[PC<Nb, LP>::NK], float einv, float c2,
                                           uint64_t* slot_free) {
   using P = PC<Nb, LP>;
@@ -394,8 +424,8 @@ __device__ __forceinline__ void epilogue2(const TcParams& p, uint32_t td2, const
   const int idx = jc.jp * P::BPG2 + b2;
   const int bx = jc.tx * 4 + (idx & 3);
   const int by = jc.ty * 4 + (idx >> 2);
-  const bool valid = bx < p.nbx && by < p.nby;
-  const int64_t k = (int64_t)by * p.nbx + bx;
+  const bool valid = bx < M.nbx && by < M.nby;
+  const int64_t k = (int64_t)by * M.nbx + bx;
   int16_t* zd = nullptr;
   if (DUMP) zd = (valid && jc.f == 0) ? p.zdump[jc.plane] + k * NK * NK : nullptr;
   float H = 0.0f, z00 = 0.0f;
@@ -423,15 +453,15 @@ __device__ __forceinline__ void epilogue2(const TcParams& p, uint32_t td2, const
 #pragma unroll
   for (int o = NK / 2; o > 0; o >>= 1) H += __shfl_xor_sync(0xffffffffu, H, o);
   if (valid && v == 0) {
-    float* out = p.blockvals + (int64_t)jc.f * p.out_fstride + (2 * jc.plane) * p.C + k;
+    float* out = M.blockvals + (int64_t)jc.f * M.out_fstride + (2 * jc.plane) * M.C + k;
     out[0] = H;
-    out[p.C] = __fsqrt_rn(z00);
+    out[M.C] = __fsqrt_rn(z00);
   }
 }
 
 // Tile bookkeeping of a role's current tile.
 struct TileInfo {
-  int f, tx, ty, stage, t;
+  int f, tx, ty, stage, t, m;  // frame, tile position, ring stage, CTA-local tile number, member
 };
 
 // a / b for 0 <= a < 2^24, b >= 1, from a float estimate that is off by at most one.
@@ -442,15 +472,52 @@ __device__ __forceinline__ int div_small(int a, int b, float binv) {
   return qt;
 }
 
-__device__ __forceinline__ TileInfo tile_info(const TcParams& p, int t, int cta, int grid, int tiles_per_frame,
-                                              int stages = kMaxStages) {
+// The members of a launch as the roles see them.  A single analyzer's launch reads its one member
+// from the kernel parameters (fields become constant-bank operands); a batched launch reads the
+// member table that the CTA copied into shared memory.
+struct OneMember {
+  const TcMember& m0;
+  __device__ __forceinline__ int member_of(int) const { return 0; }
+  __device__ __forceinline__ const TcMember& operator[](int) const { return m0; }
+};
+
+struct MemberTable {
+  const TcMember* mem;
+  int n;
+  mutable int cur;  // member of the last item asked for
+  // The member that work item `item` belongs to: the last one whose first item is <= item.  Each
+  // thread asks for its CTA's items in increasing order, so the search moves forward only.
+  __device__ __forceinline__ int member_of(int item) const {
+    while (cur + 1 < n && mem[cur + 1].item_base <= item) ++cur;
+    return cur;
+  }
+  __device__ __forceinline__ const TcMember& operator[](int i) const { return mem[i]; }
+};
+
+template <bool BATCH>
+struct MemberView;
+template <>
+struct MemberView<false> {
+  using T = OneMember;
+};
+template <>
+struct MemberView<true> {
+  using T = MemberTable;
+};
+
+template <class MS>
+__device__ __forceinline__ TileInfo tile_info(const MS& ms, int t, int item0, int step, int stages = kMaxStages) {
   TileInfo ti;
-  const int item = cta + t * grid;
+  const int item = item0 + t * step;
+  const int m = ms.member_of(item);
+  const TcMember& M = ms[m];
+  const int local = item - M.item_base;
+  ti.m = m;
   ti.t = t;
-  ti.f = div_small(item, tiles_per_frame, p.inv_tiles_per_frame);
-  const int r = item - ti.f * tiles_per_frame;
-  ti.ty = div_small(r, p.tiles_x, p.inv_tiles_x);
-  ti.tx = r - ti.ty * p.tiles_x;
+  ti.f = div_small(local, M.tiles_per_frame, M.inv_tiles_per_frame);
+  const int r = local - ti.f * M.tiles_per_frame;
+  ti.ty = div_small(r, M.tiles_x, M.inv_tiles_x);
+  ti.tx = r - ti.ty * M.tiles_x;
   ti.stage = t % stages;
   return ti;
 }
@@ -468,15 +535,14 @@ __device__ __forceinline__ void plane_jobs(int& r0, int& r1) {
 }
 
 // Convert: raw samples of the tile -> stage-1 A operand in TMEM (and the D1 presets).
-template <int Nb, bool LP, int BPS>
-__device__ void convert_loop(const TcParams& p, const Ctl& ctl, uint8_t* sm, uint32_t tq, int n_items, int cta,
-                             int grid, int tiles_per_frame, int q, int lane) {
+template <int Nb, bool LP, int BPS, class MS>
+__device__ void convert_loop(const MS& ms, const Ctl& ctl, uint8_t* sm, uint32_t tq, int n_items, int item0,
+                             int step, int q, int lane) {
   using SL = SmemLay<BPS>;
   constexpr int JPT = Jobs<LP>::PER_TILE;
   constexpr int T = 4 * Nb;  // tile edge of this plane in samples
-  const int pw = Nb == 32 ? p.W : p.cw, ph = Nb == 32 ? p.H : p.ch;
-  const float c0 = p.s1_c0[Nb == 32 ? 0 : 1];  // 2^(s1-1) - 1024 * 64 * N
-  const float c = p.s1_c[Nb == 32 ? 0 : 1];    // 2^(s1-1)
+  float c0 = 0.0f, c = 0.0f;  // stage-1 presets of the tile's member
+  int bps = 1;
   int r0, r1;
   plane_jobs<Nb, LP>(r0, r1);
   const int per_tile = r1 - r0;
@@ -485,9 +551,14 @@ __device__ void convert_loop(const TcParams& p, const Ctl& ctl, uint8_t* sm, uin
   const int n = n_items * per_tile;
   for (int k = 0, t = 0, r = r0; k < n; ++k) {
     if (r == r0) {
-      ti = tile_info(p, t, cta, grid, tiles_per_frame, SL::kStages);
-      h_rem = ph - ti.ty * T;
-      w_rem = pw - ti.tx * T;
+      ti = tile_info(ms, t, item0, step, SL::kStages);
+      const TcMember& M = ms[ti.m];
+      h_rem = (Nb == 32 ? M.H : M.ch) - ti.ty * T;
+      w_rem = (Nb == 32 ? M.W : M.cw) - ti.tx * T;
+      bps = BPS == 0 ? M.bps : BPS;
+      // Presets 2^(s1-1) and, on the DC column, 2^(s1-1) - 1024 * 64 * N (the 1024 + x encoding).
+      c = (float)(1 << (s1_of<Nb>(bps) - 1));
+      c0 = c - 1024.0f * 64.0f * (float)Nb;
       if (!wait_bar(ctl, b_raw_full(ti.stage), (t / SL::kStages) & 1, 4)) return;
     }
     const int jj = t * JPT + r;
@@ -496,10 +567,11 @@ __device__ void convert_loop(const TcParams& p, const Ctl& ctl, uint8_t* sm, uin
     const int slot = jj % kSlots;
     if (jj >= kSlots && !wait_bar(ctl, b_slot_free(slot), ((jj / kSlots) - 1) & 1, 4)) return;
     tc_fence_after();
+    // Plane offsets within the stage follow the member's sample size (the stage fits the largest).
     const uint8_t* raw =
-        sm + OFF_RAW + ti.stage * SL::kStageBytes + (plane == 0 ? 0 : SL::kRawY + (plane - 1) * SL::kRawC);
+        sm + OFF_RAW + ti.stage * SL::kStageBytes + (plane == 0 ? 0 : 128 * 128 * bps + (plane - 1) * 64 * 64 * bps);
     const uint32_t ta = tq + slot * kSlotCols;
-    convert_job<Nb, LP, BPS>(raw, jp, h_rem, w_rem, ta, ta + kD1Off, c0, c, q, lane);
+    convert_job<Nb, LP, BPS>(raw, jp, h_rem, w_rem, ta, ta + kD1Off, c0, c, bps, q, lane);
     tmem_wait_st();
     tc_fence_before();
     __syncwarp();
@@ -522,12 +594,12 @@ __device__ void convert_loop(const TcParams& p, const Ctl& ctl, uint8_t* sm, uin
 // encoding of both halves) and K1 otherwise, lo at 2^(s2-1) (luma N = 32: s2 = 11; chroma
 // N = 16: s2 = 10; s1 = log2 N + B - 9 comes with the parameters).  Each plane type cycles through its own two stage-2 operand slots, so
 // every slot's full / free barriers see one in-order stream of jobs.
-template <int Nb, bool LP, int BPS>
-__device__ void epi1_loop(const TcParams& p, const Ctl& ctl, uint32_t sbase, uint32_t tq, int n_items, int q,
-                          int lane) {
+template <int Nb, bool LP, int BPS, class MS>
+__device__ void epi1_loop(const MS& ms, const Ctl& ctl, uint32_t sbase, uint32_t tq, int n_items, int item0,
+                          int step, int q, int lane) {
   using SL = SmemLay<BPS>;
   constexpr int JPT = Jobs<LP>::PER_TILE;
-  const float s1inv = p.s1_inv[Nb == 32 ? 0 : 1];
+  float s1inv = 0.0f;
   const float hi0 = Nb == 32 ? kK1 - 2367488.0f : kK1 - 1183744.0f;
   const float lo = Nb == 32 ? 1024.0f : 512.0f;
   const uint32_t lo_off = Nb == 32 ? kA2L : kA2C;
@@ -537,6 +609,10 @@ __device__ void epi1_loop(const TcParams& p, const Ctl& ctl, uint32_t sbase, uin
   plane_jobs<Nb, LP>(r0, r1);
   const int n = n_items * (r1 - r0);
   for (int use = 0, t = 0, r = r0; use < n; ++use) {  // use: jobs of this plane type so far
+    if (r == r0) {  // 2^-s1 of the tile's member
+      const int bps = BPS == 0 ? ms[ms.member_of(item0 + t * step)].bps : BPS;
+      s1inv = __int_as_float((127 - s1_of<Nb>(bps)) << 23);
+    }
     const int jj = t * JPT + r;
     const int slot = jj % kSlots;
     const int a2 = use & 1;
@@ -559,9 +635,9 @@ __device__ void epi1_loop(const TcParams& p, const Ctl& ctl, uint32_t sbase, uin
 }
 
 // Epilogue 2: Z, the block energy H and brightness L, for every job of one plane type.
-template <int Nb, bool LP, bool DUMP>
-__device__ void epi2_loop(const TcParams& p, const Ctl& ctl, uint32_t tq, int n_items, int cta, int grid,
-                          int tiles_per_frame, int q, int lane) {
+template <int Nb, bool LP, bool DUMP, class MS>
+__device__ void epi2_loop(const TcParams& p, const MS& ms, const Ctl& ctl, uint32_t tq, int n_items, int item0,
+                          int step, int q, int lane) {
   using P = PC<Nb, LP>;
   constexpr int JPT = Jobs<LP>::PER_TILE;
   const float* Wt = Nb == 32 ? p.W_y : p.W_c;
@@ -574,19 +650,22 @@ __device__ void epi2_loop(const TcParams& p, const Ctl& ctl, uint32_t tq, int n_
   plane_jobs<Nb, LP>(r0, r1);
   const int n = n_items * (r1 - r0);
   JobCtx jc{};
+  int m = 0;
   for (int k = 0, t = 0, r = r0; k < n; ++k) {
     if (r == r0) {
-      const TileInfo ti = tile_info(p, t, cta, grid, tiles_per_frame);
+      const TileInfo ti = tile_info(ms, t, item0, step);
       jc.f = ti.f;
       jc.tx = ti.tx;
       jc.ty = ti.ty;
+      m = ti.m;
     }
     const int jj = t * JPT + r;
     const int slot = jj % kSlots;
     plane_of<LP>(r, jc.plane, jc.jp);
     if (!wait_bar(ctl, b_d2(slot), (jj / kSlots) & 1, 4, false, true)) return;
     tc_fence_after();
-    epilogue2<Nb, LP, DUMP>(p, tq + slot * kSlotCols, jc, q, lane, w, einv, c2, &ctl.bars[b_slot_free(slot)]);
+    epilogue2<Nb, LP, DUMP>(p, ms[m], tq + slot * kSlotCols, jc, q, lane, w, einv, c2,
+                            &ctl.bars[b_slot_free(slot)]);
     if (++r == r1) {
       r = r0;
       ++t;
@@ -594,10 +673,8 @@ __device__ void epi2_loop(const TcParams& p, const Ctl& ctl, uint32_t tq, int n_
   }
 }
 
-template <bool LP, bool DUMP, int BPS>
-__global__ void __launch_bounds__(kThreads, 1)
-    tc_kernel(const __grid_constant__ CUtensorMap mapY, const __grid_constant__ CUtensorMap mapU,
-              const __grid_constant__ CUtensorMap mapV, const TcParams p) {
+template <bool LP, bool DUMP, int BPS, bool BATCH>
+__global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__ TcParams p) {
   using L = PC<32, LP>;
   using Cc = PC<16, LP>;
   constexpr int JPT = Jobs<LP>::PER_TILE;
@@ -615,10 +692,39 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int q = warp & 3;      // TMEM lane quarter of this warp
   const int cta = blockIdx.x;
   const int grid = gridDim.x;
-  const int n_items = cta < p.total_items ? (p.total_items - cta + grid - 1) / grid : 0;
+  const int n_mem = BATCH ? p.table->n_members : 1;
+  const int total_items = BATCH ? p.table->total_items : p.total_items;
+  // This CTA's items: item0, item0 + step, ...  A single analyzer's CTAs take every grid-th item
+  // (neighbouring CTAs read neighbouring tiles); a batched launch gives each CTA one contiguous
+  // run, so that a CTA meets few members (and few tensor maps).
+  int item0, step, n_items;
+  if (BATCH) {
+    item0 = (int)((int64_t)cta * total_items / grid);
+    n_items = (int)((int64_t)(cta + 1) * total_items / grid) - item0;
+    step = 1;
+  } else {
+    item0 = cta;
+    n_items = cta < total_items ? (total_items - cta + grid - 1) / grid : 0;
+    step = grid;
+  }
   const int n_jobs = n_items * JPT;
-  const int tiles_per_frame = p.tiles_x * p.tiles_y;
   Ctl ctl{bars, abort_flag, p.err};
+
+  // A batched launch's member table, copied into shared memory as 8-byte words.
+  __shared__ alignas(16) TcMember s_mem[BATCH ? kMaxMembers : 1];
+  if (BATCH) {
+    const uint64_t* src = (const uint64_t*)p.table->mem;
+    uint64_t* dst = (uint64_t*)s_mem;
+    const int words = n_mem * (int)(sizeof(TcMember) / 8);
+    for (int i = tid; i < words; i += kThreads) dst[i] = src[i];
+  }
+  using MS = typename MemberView<BATCH>::T;
+  MS ms = [&] {
+    if constexpr (BATCH)
+      return MemberTable{s_mem, n_mem, 0};
+    else
+      return OneMember{p.mem0};
+  }();
 
   // Constant B operands (the integer DCT matrices as fp16), K-major without swizzle:
   // element (n, k) at (n/8)*SBO + (k/8)*128 + (n%8)*16 + (k%8)*2.
@@ -641,10 +747,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     *abort_flag = 0;
     fence_mbar_init();
   }
-  if (warp == 0 && lane == 0) {
-    prefetch_tensormap(&mapY);
-    prefetch_tensormap(&mapU);
-    prefetch_tensormap(&mapV);
+  if (warp == 0 && lane == 0 && !BATCH) {
+    prefetch_tensormap(&p.map0[0]);
+    prefetch_tensormap(&p.map0[1]);
+    prefetch_tensormap(&p.map0[2]);
   }
   if (warp == 1) {
     tmem_alloc(tmem_slot, kTmemCols);
@@ -661,19 +767,31 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (role == 0) {
     if (warp == 0 && lane == 0) {
       // ---------------- TMA producer: tiles in order into the ring ----------------
+      const CUtensorMap* maps = BATCH ? p.maps : p.map0;
       int issued = 0;
+      int fenced = -1;  // batched launch: the member whose maps were last fenced
       for (int t = 0; t < n_items; ++t) {
         const int stage = t % SL::kStages;
         if (t >= SL::kStages && !wait_bar(ctl, b_raw_empty(stage), ((t / SL::kStages) - 1) & 1, 1, false, true))
           break;
-        const TileInfo ti = tile_info(p, t, cta, grid, tiles_per_frame);
+        const TileInfo ti = tile_info(ms, t, item0, step, SL::kStages);
+        const CUtensorMap* mm = maps + 3 * ti.m;
+        if (BATCH && ti.m != fenced) {
+          for (int i = 0; i < 3; ++i) fence_tensormap_acquire(mm + i);
+          fenced = ti.m;
+        }
+        const int bps = BPS == 0 ? ms[ti.m].bps : BPS;
         uint8_t* dst = sm + OFF_RAW + stage * SL::kStageBytes;
-        mbar_arrive_expect_tx(&bars[b_raw_full(stage)], SL::kStageBytes);
-        tma_load_3d(dst, &mapY, ti.tx * 128, ti.ty * 128, ti.f, &bars[b_raw_full(stage)]);
-        if (BPS == 2)  // 16-bit luma: the right half of the tile is a second 64-sample box
-          tma_load_3d(dst + SL::kRawY / 2, &mapY, ti.tx * 128 + 64, ti.ty * 128, ti.f, &bars[b_raw_full(stage)]);
-        tma_load_3d(dst + SL::kRawY, &mapU, ti.tx * 64, ti.ty * 64, ti.f, &bars[b_raw_full(stage)]);
-        tma_load_3d(dst + SL::kRawY + SL::kRawC, &mapV, ti.tx * 64, ti.ty * 64, ti.f, &bars[b_raw_full(stage)]);
+        uint64_t* full = &bars[b_raw_full(stage)];
+        mbar_arrive_expect_tx(full, (uint32_t)(128 * 128 + 2 * 64 * 64) * bps);
+        if (bps == 1) {
+          tma_load_3d(dst, mm, ti.tx * 128, ti.ty * 128, ti.f, full);
+        } else {  // 16-bit luma: the tile is two 64-sample boxes side by side
+          tma_load_3d(dst, mm, ti.tx * 128, ti.ty * 128, ti.f, full);
+          tma_load_3d(dst + 128 * 64 * 2, mm, ti.tx * 128 + 64, ti.ty * 128, ti.f, full);
+        }
+        tma_load_3d(dst + 128 * 128 * bps, mm + 1, ti.tx * 64, ti.ty * 64, ti.f, full);
+        tma_load_3d(dst + (128 * 128 + 64 * 64) * bps, mm + 2, ti.tx * 64, ti.ty * 64, ti.f, full);
         ++issued;
       }
       if (*abort_flag) {
@@ -753,17 +871,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else if (role == 1) {
-    convert_loop<32, LP, BPS>(p, ctl, sm, tmem + lanebase, n_items, cta, grid, tiles_per_frame, q, lane);
+    convert_loop<32, LP, BPS>(ms, ctl, sm, tmem + lanebase, n_items, item0, step, q, lane);
   } else if (role == 6) {
-    convert_loop<16, LP, BPS>(p, ctl, sm, tmem + lanebase, n_items, cta, grid, tiles_per_frame, q, lane);
+    convert_loop<16, LP, BPS>(ms, ctl, sm, tmem + lanebase, n_items, item0, step, q, lane);
   } else if (role == 2) {
-    epi1_loop<32, LP, BPS>(p, ctl, sbase, tmem + lanebase, n_items, q, lane);
+    epi1_loop<32, LP, BPS>(ms, ctl, sbase, tmem + lanebase, n_items, item0, step, q, lane);
   } else if (role == 3) {
-    epi1_loop<16, LP, BPS>(p, ctl, sbase, tmem + lanebase, n_items, q, lane);
+    epi1_loop<16, LP, BPS>(ms, ctl, sbase, tmem + lanebase, n_items, item0, step, q, lane);
   } else if (role == 4) {
-    epi2_loop<32, LP, DUMP>(p, ctl, tmem + lanebase, n_items, cta, grid, tiles_per_frame, q, lane);
+    epi2_loop<32, LP, DUMP>(p, ms, ctl, tmem + lanebase, n_items, item0, step, q, lane);
   } else {
-    epi2_loop<16, LP, DUMP>(p, ctl, tmem + lanebase, n_items, cta, grid, tiles_per_frame, q, lane);
+    epi2_loop<16, LP, DUMP>(p, ms, ctl, tmem + lanebase, n_items, item0, step, q, lane);
   }
 
   tc_fence_before();
@@ -809,18 +927,68 @@ cudaError_t make_map(CUtensorMap* m, const void* base, int w, int h, int64_t pit
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <bool LP, bool DUMP, int BPS>
-cudaError_t launch_inst(const CUtensorMap& my, const CUtensorMap& mu, const CUtensorMap& mv, const TcParams& p,
-                        int grid, cudaStream_t s) {
-  constexpr int kSmem = SmemLay<BPS>::kSmemBytes;
+// Raises the instance's dynamic shared-memory limit (once per process).
+template <bool LP, bool DUMP, int BPS, bool BATCH>
+cudaError_t prepare_inst() {
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(tc_kernel<LP, DUMP, BPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    attr = cudaFuncSetAttribute(tc_kernel<LP, DUMP, BPS, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                SmemLay<BPS>::kSmemBytes);
   });
+  return attr;
+}
+
+// grid 0: only prepare the instance.
+template <bool LP, bool DUMP, int BPS, bool BATCH>
+cudaError_t launch_inst(const TcParams& p, int grid, cudaStream_t s) {
+  const cudaError_t attr = prepare_inst<LP, DUMP, BPS, BATCH>();
   if (attr != cudaSuccess) return attr;
-  tc_kernel<LP, DUMP, BPS><<<grid, kThreads, kSmem, s>>>(my, mu, mv, p);
+  if (grid <= 0) return cudaSuccess;
+  tc_kernel<LP, DUMP, BPS, BATCH><<<grid, kThreads, SmemLay<BPS>::kSmemBytes, s>>>(p);
   return cudaGetLastError();
+}
+
+// A single analyzer's launch (bps 1 or 2).
+cudaError_t launch_single(const TcParams& p, int grid, bool low_pass, bool dump, int bps, cudaStream_t s) {
+  if (bps == 1) {
+    if (low_pass)
+      return dump ? launch_inst<true, true, 1, false>(p, grid, s) : launch_inst<true, false, 1, false>(p, grid, s);
+    return dump ? launch_inst<false, true, 1, false>(p, grid, s) : launch_inst<false, false, 1, false>(p, grid, s);
+  }
+  if (low_pass)
+    return dump ? launch_inst<true, true, 2, false>(p, grid, s) : launch_inst<true, false, 2, false>(p, grid, s);
+  return dump ? launch_inst<false, true, 2, false>(p, grid, s) : launch_inst<false, false, 2, false>(p, grid, s);
+}
+
+// A batched launch: bps 1 or 2 for members of one sample size, 0 for a mix.
+cudaError_t launch_batched(const TcParams& p, int grid, bool low_pass, int bps, cudaStream_t s) {
+  if (bps == 1)
+    return low_pass ? launch_inst<true, false, 1, true>(p, grid, s) : launch_inst<false, false, 1, true>(p, grid, s);
+  if (bps == 2)
+    return low_pass ? launch_inst<true, false, 2, true>(p, grid, s) : launch_inst<false, false, 2, true>(p, grid, s);
+  return low_pass ? launch_inst<true, false, 0, true>(p, grid, s) : launch_inst<false, false, 0, true>(p, grid, s);
+}
+
+// One member's entry: geometry, outputs and stage-1 constants; returns its number of items.
+int fill_member(TcMember& m, const Geometry& g, int item_base, int nframes, float* blockvals) {
+  m = TcMember{};
+  m.item_base = item_base;
+  m.tiles_x = (g.nbx + 3) / 4;
+  m.tiles_per_frame = m.tiles_x * ((g.nby + 3) / 4);
+  m.inv_tiles_x = 1.0f / (float)m.tiles_x;
+  m.inv_tiles_per_frame = 1.0f / (float)m.tiles_per_frame;
+  m.W = g.W;
+  m.H = g.H;
+  m.cw = g.cw;
+  m.ch = g.ch;
+  m.nbx = g.nbx;
+  m.nby = g.nby;
+  m.bps = g.bps;
+  m.C = g.C;
+  m.out_fstride = (int64_t)N_ROWS * g.C;
+  m.blockvals = blockvals;
+  return m.tiles_per_frame * nframes;
 }
 
 int sm_count() {
@@ -833,7 +1001,57 @@ int sm_count() {
 }  // namespace
 
 bool tc_supported(const Geometry& g) {
-  return (g.B == 8 || g.B == 10) && g.w == 32 && g.nc == 16 && encode_fn() != nullptr;
+  return (g.B == 8 || g.B == 10) && g.w == 32 && g.nc == 16 && g.s1y == s1_of<32>(g.bps) &&
+         g.s1c == s1_of<16>(g.bps) && encode_fn() != nullptr;
+}
+
+// Descriptor block of a batched launch: the member table, then three tensor maps per member.
+constexpr size_t kTcMapsOff = (sizeof(TcTable) + 127) / 128 * 128;
+
+int tc_batch_max_members() { return kMaxMembers; }
+
+size_t tc_batch_desc_bytes() { return kTcMapsOff + (size_t)3 * kMaxMembers * sizeof(CUtensorMap); }
+
+cudaError_t tc_batch_fill(void* h, const TcBatchFrame* frames, int n) {
+  if (n < 0 || n > kMaxMembers) return cudaErrorInvalidValue;
+  TcTable* tab = static_cast<TcTable*>(h);
+  CUtensorMap* maps = reinterpret_cast<CUtensorMap*>(static_cast<uint8_t*>(h) + kTcMapsOff);
+  int items = 0;
+  for (int i = 0; i < n; ++i) {
+    const Geometry& g = *frames[i].g;
+    const FramePlanes& fp = frames[i].fp;
+    if (!tc_supported(g)) return cudaErrorInvalidValue;
+    items += fill_member(tab->mem[i], g, items, 1, frames[i].blockvals);
+    const CUtensorMapSwizzle swc = g.bps == 1 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
+    cudaError_t e = make_map(&maps[3 * i], fp.y, g.W, g.H, fp.pitch_y, 0, 1, g.bps == 1 ? 128 : 64, 128, g.bps,
+                             CU_TENSOR_MAP_SWIZZLE_128B);
+    if (e == cudaSuccess) e = make_map(&maps[3 * i + 1], fp.u, g.cw, g.ch, fp.pitch_uv, 0, 1, 64, 64, g.bps, swc);
+    if (e == cudaSuccess) e = make_map(&maps[3 * i + 2], fp.v, g.cw, g.ch, fp.pitch_uv, 0, 1, 64, 64, g.bps, swc);
+    if (e != cudaSuccess) return e;
+  }
+  tab->n_members = n;
+  tab->total_items = items;
+  return cudaSuccess;
+}
+
+cudaError_t tc_batch_prepare(int bps, bool low_pass) {
+  if (bps < 0 || bps > 2) return cudaErrorInvalidValue;
+  return launch_batched(TcParams{}, 0, low_pass, bps, nullptr);
+}
+
+cudaError_t launch_tc_batch(const void* d_desc, int bps, bool low_pass, const DeviceTables& t, int* err,
+                            cudaStream_t s) {
+  if (bps < 0 || bps > 2) return cudaErrorInvalidValue;
+  TcParams p{};
+  p.table = static_cast<const TcTable*>(d_desc);
+  p.maps = reinterpret_cast<const CUtensorMap*>(static_cast<const uint8_t*>(d_desc) + kTcMapsOff);
+  p.M_y = t.M_y;
+  p.M_c = t.M_c;
+  p.W_y = t.W_y;
+  p.W_c = t.W_c;
+  p.err = err;
+  // The number of items is known only on the device; CTAs beyond it find no work.
+  return launch_batched(p, sm_count(), low_pass, bps, s);
 }
 
 cudaError_t launch_tc(const Geometry& g, const FramePlanes& fp, int nframes, const DeviceTables& t, float* blockvals,
@@ -851,49 +1069,18 @@ cudaError_t launch_tc(const Geometry& g, const FramePlanes& fp, int nframes, con
   if (e == cudaSuccess) e = make_map(&mv, fp.v, g.cw, g.ch, fp.pitch_uv, fp.fstride_uv, nframes, 64, 64, bps, swc);
   if (e != cudaSuccess) return e;
   TcParams p{};
-  p.W = g.W;
-  p.H = g.H;
-  p.cw = g.cw;
-  p.ch = g.ch;
-  p.nbx = g.nbx;
-  p.nby = g.nby;
-  p.tiles_x = (g.nbx + 3) / 4;
-  p.tiles_y = (g.nby + 3) / 4;
-  p.inv_tiles_x = 1.0f / (float)p.tiles_x;
-  p.inv_tiles_per_frame = 1.0f / (float)(p.tiles_x * p.tiles_y);
-  p.nframes = nframes;
-  p.total_items = p.tiles_x * p.tiles_y * nframes;
-  p.C = g.C;
-  p.out_fstride = (int64_t)N_ROWS * g.C;
-  p.blockvals = blockvals;
+  p.total_items = fill_member(p.mem0, g, 0, nframes, blockvals);
+  p.map0[0] = my;
+  p.map0[1] = mu;
+  p.map0[2] = mv;
   for (int i = 0; i < 3; ++i) p.zdump[i] = zdump ? zdump[i] : nullptr;
   p.M_y = t.M_y;
   p.M_c = t.M_c;
   p.W_y = t.W_y;
   p.W_c = t.W_c;
   p.err = err;
-  for (int pt = 0; pt < 2; ++pt) {  // s1 = log2 N + B - 9; presets 2^(s1-1) (- 1024 * 64 * N on the DC column)
-    const int s1 = pt == 0 ? g.s1y : g.s1c;
-    const int N = pt == 0 ? g.w : g.nc;
-    p.s1_c[pt] = (float)(1 << (s1 - 1));
-    p.s1_c0[pt] = (float)(1 << (s1 - 1)) - 1024.0f * 64.0f * (float)N;
-    p.s1_inv[pt] = 1.0f / (float)(1 << s1);
-  }
   const int grid = p.total_items < sm_count() ? p.total_items : sm_count();
-  const bool dump = zdump != nullptr;
-  if (bps == 1) {
-    if (g.low_pass)
-      e = dump ? launch_inst<true, true, 1>(my, mu, mv, p, grid, s) : launch_inst<true, false, 1>(my, mu, mv, p, grid, s);
-    else
-      e = dump ? launch_inst<false, true, 1>(my, mu, mv, p, grid, s)
-               : launch_inst<false, false, 1>(my, mu, mv, p, grid, s);
-  } else {
-    if (g.low_pass)
-      e = dump ? launch_inst<true, true, 2>(my, mu, mv, p, grid, s) : launch_inst<true, false, 2>(my, mu, mv, p, grid, s);
-    else
-      e = dump ? launch_inst<false, true, 2>(my, mu, mv, p, grid, s)
-               : launch_inst<false, false, 2>(my, mu, mv, p, grid, s);
-  }
+  e = launch_single(p, grid, g.low_pass, zdump != nullptr, bps, s);
   if (e == cudaSuccess) ++*launches;
   return e;
 }

@@ -115,6 +115,7 @@ _PROTOS = {
     "vca_batch_tick": (_P, ctypes.POINTER(VcaFrameRef)),
     "vca_batch_sync": (_P,),
     "vca_batch_launch_count": (_P, ctypes.POINTER(_I64)),
+    "vca_batch_kernel": (_P, ctypes.POINTER(_I32)),
     "vca_batch_destroy": (_P,),
     "vca_server_create": (ctypes.c_size_t, ctypes.POINTER(_P)),
     "vca_server_add_channel": (_P, ctypes.POINTER(VcaConfig), _I32, ctypes.POINTER(_I32)),
@@ -206,6 +207,12 @@ def vca_batch_launch_count(batch: int) -> int:
     n = _I64()
     _check(lib().vca_batch_launch_count(_P(batch), ctypes.byref(n)))
     return n.value
+
+
+def vca_batch_kernel(batch: int) -> int:
+    k = _I32()
+    _check(lib().vca_batch_kernel(_P(batch), ctypes.byref(k)))
+    return k.value
 
 
 def vca_batch_destroy(batch: int) -> None:
@@ -435,6 +442,10 @@ class Batch:
 
     def launches(self) -> int:
         return vca_batch_launch_count(self.handle)
+
+    @property
+    def kernel(self) -> int:
+        return vca_batch_kernel(self.handle)
 
     def close(self):
         if self.handle:

@@ -41,22 +41,33 @@ def _channel_frames(i, w, h, bd):
     return frames_list(spec)
 
 
+CHANNELS_8 = [(640, 352, 8), (656, 368, 8), (200, 120, 8)]
+CHANNELS_10 = [(320, 180, 10), (200, 120, 10), (136, 72, 10)]
+CASES = [  # (kernel, channels): the tensor-core batch with one sample size (bytes or words) and mixed
+    ("plain", CHANNELS),
+    ("tc", CHANNELS),
+    ("tc", CHANNELS_8),
+    ("tc", CHANNELS_10),
+]
+
+
 @pytest.mark.parametrize("low_pass", [True, False])
-def test_batch_matches_single_analyzers_and_oracle(vca, low_pass):
+@pytest.mark.parametrize("kind,channels", CASES, ids=["plain", "tc-mixed", "tc-8bit", "tc-10bit"])
+def test_batch_matches_single_analyzers_and_oracle(vca, low_pass, kind, channels):
     import torch
 
-    frames = [_channel_frames(i, *c) for i, c in enumerate(CHANNELS)]
+    kernel = vca.VCA_KERNEL_TC if kind == "tc" else vca.VCA_KERNEL_PLAIN
+    frames = [_channel_frames(i, *c) for i, c in enumerate(channels)]
     dev = [to_device(f) for f in frames]
-    members = [vca.Analyzer(w, h, bd, 32, low_pass, kernel=vca.VCA_KERNEL_PLAIN, max_batch=4)
-               for (w, h, bd) in CHANNELS]
-    singles = [vca.Analyzer(w, h, bd, 32, low_pass, kernel=vca.VCA_KERNEL_PLAIN, max_batch=4)
-               for (w, h, bd) in CHANNELS]
-    fed = [[] for _ in CHANNELS]
+    members = [vca.Analyzer(w, h, bd, 32, low_pass, kernel=kernel, max_batch=4) for (w, h, bd) in channels]
+    singles = [vca.Analyzer(w, h, bd, 32, low_pass, kernel=kernel, max_batch=4) for (w, h, bd) in channels]
+    fed = [[] for _ in channels]
     try:
         batch = vca.Batch(members)
+        assert batch.kernel == kernel
         for t in range(TICKS):
             refs = []
-            for i in range(len(CHANNELS)):
+            for i in range(len(channels)):
                 if (t, i) in SKIP:
                     refs.append(None)
                     continue
@@ -67,7 +78,7 @@ def test_batch_matches_single_analyzers_and_oracle(vca, low_pass):
             batch.tick(refs)
         batch.sync()
         assert batch.launches() == 2 * TICKS
-        for i, (w, h, bd) in enumerate(CHANNELS):
+        for i, (w, h, bd) in enumerate(channels):
             got = [members[i].frame_features(k) for k in range(len(fed[i]))]
             exp = [singles[i].frame_features(k) for k in range(len(fed[i]))]
             assert got == exp, f"channel {i}"
@@ -78,7 +89,7 @@ def test_batch_matches_single_analyzers_and_oracle(vca, low_pass):
             assert_features_close(members[i].sequence_features(), seqf, where=f"channel {i} sequence")
         batch.close()
         # The h state continues after the batch is gone.
-        for i in range(len(CHANNELS)):
+        for i in range(len(channels)):
             y, u, v = dev[i]
             members[i].push(y[TICKS], u[TICKS], v[TICKS])
             singles[i].push(y[TICKS], u[TICKS], v[TICKS])
@@ -120,8 +131,18 @@ def test_batch_state_rules(vca):
             batch.tick([(y[0][:, 1:], u[0], v[0]), None])
         assert ei.value.status == vca.VCA_E_ARG
         batch.tick([(y[0], u[0], v[0]), None])
+        assert batch.kernel == vca.VCA_KERNEL_PLAIN
         batch.close()
         assert a.frame_features(0)["h"] == 0.0
+        # One member off the tensor-core kernel puts the whole batch on the CUDA-core kernel.
+        e = vca.Analyzer(640, 352, 8, 32, True, kernel=vca.VCA_KERNEL_TC, max_batch=2)
+        try:
+            with vca.Batch([e, b]) as mixed:
+                assert mixed.kernel == vca.VCA_KERNEL_PLAIN
+            with vca.Batch([e]) as alone:
+                assert alone.kernel == vca.VCA_KERNEL_TC
+        finally:
+            e.close()
     finally:
         for x in (a, b, c, d):
             x.close()

@@ -4,7 +4,7 @@ thread, and admission by device memory.
 Three channels of different frame sizes and bit depths submit segments of 4 frames; the
 scheduler analyses one frame of every channel with a segment in progress per tick.  Each
 channel's features must equal, bit for bit, those of a single analyzer fed the same frames (the
-same plain arithmetic), match the oracle, and the h state must carry from one segment to the next.
+same kernel's arithmetic), match the oracle, and the h state must carry from one segment to the next.
 """
 
 import time
@@ -76,7 +76,7 @@ def test_server_segments_match_single_analyzers(vca):
         assert stats["ticks"] <= stats["frames"]
         for i, (w, h, bd) in enumerate(CHANNELS):
             got = [srv.frame_features(ids[i], t) for t in range(SEG * NSEG)]
-            single = vca.Analyzer(w, h, bd, 32, True, kernel=vca.VCA_KERNEL_PLAIN, max_batch=SEG)
+            single = vca.Analyzer(w, h, bd, 32, True, max_batch=SEG)  # the channel's kernel
             y, u, v = dev[i]
             for k in range(NSEG):
                 sl = slice(k * SEG, (k + 1) * SEG)
