@@ -28,7 +28,9 @@
  *               L = sqrt(Z(0,0)), in FP32;
  *   frame       E_P = sum_k H_{P,k} / (C N_P^2), L_P = sum_k L_{P,k} / C,
  *               h_t = sum_k |H_{Y,k,t} - H_{Y,k,t-1}| / (C w^2), h_0 = 0,
- *               summed in FP64 in a fixed order (deterministic);
+ *               the block sums exact (128-bit fixed point in units of 2^-23),
+ *               each total rounded once to FP64, then divided (deterministic,
+ *               and independent of how frames are batched);
  *   sequence    arithmetic mean over frames (h over frames t >= 1).
  *
  * Conventions for every call:
@@ -211,10 +213,10 @@ typedef struct {
 
 /* Groups n analyzers (1 .. 65535, distinct, none already in a batch).  Waits for the analyzers'
  * earlier work and captures two tick graphs on a stream of its own.  If every analyzer runs the
- * tensor-core kernel and n <= 64, a tick analyses all of them in one launch of the persistent
- * tensor-core kernel (8- and 10-bit members may be mixed; the tensor maps of the tick's frames
- * are encoded on the host at each tick); otherwise in one launch of the batched CUDA-core kernel,
- * whose CTA map is built here.  VCA_E_ARG for mismatched devices, block sizes or low_pass. */
+ * tensor-core kernel and n <= 64, a tick analyses them with the persistent tensor-core kernel:
+ * one launch for the 8-bit members and one for the 10-bit members, the two on forked branches
+ * of the tick graph (the tensor maps of the tick's frames are encoded on the host at each tick);
+ * otherwise with one launch of the batched CUDA-core kernel, whose CTA map is built here.  VCA_E_ARG for mismatched devices, block sizes or low_pass. */
 vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch** out);
 
 /* The kernel family a batch's ticks run: VCA_KERNEL_TC or VCA_KERNEL_PLAIN. */
@@ -231,7 +233,8 @@ vca_status vca_batch_tick(vca_batch* b, const vca_frame_ref* frames);
  * analyzers' frame counters and h state have moved on). */
 vca_status vca_batch_sync(vca_batch* b);
 
-/* Kernel launches issued by the batch's ticks (two per tick). */
+/* Kernel launches issued by the batch's ticks: per tick, the analysis (two launches for a
+ * tensor-core batch with 8- and 10-bit members, else one) and the reduction. */
 vca_status vca_batch_launch_count(vca_batch* b, int64_t* launches);
 
 /* Waits for the batch's ticks and dissolves it; the analyzers stay open.  NULL is accepted. */

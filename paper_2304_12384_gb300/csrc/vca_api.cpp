@@ -103,7 +103,7 @@ struct vca_analyzer {
   int cur_prev = 0;
   double* d_feats = nullptr;     // max_batch * FEAT_STRIDE
   int* d_err = nullptr;          // kernel wait-timeout flags: one per push buffer, one for dumps
-  double* d_red_partials = nullptr;       // frame-reduction scratch
+  unsigned long long* d_red_partials = nullptr;  // frame-reduction scratch
   unsigned int* d_red_counters = nullptr; // one arrival counter per frame, kept at zero between launches
   uint8_t* d_staging = nullptr;  // host frames are copied here
   size_t staging_bytes = 0;
@@ -152,8 +152,14 @@ struct vca_batch {
   int nc = 16;
   bool low_pass = false;
   bool tc = false;                 // analysis on the tensor-core kernel
-  int tc_bps = 1;                  // members' sample size (0: mixed)
+  // Tensor-core members are launched in one group per sample size (8-bit samples in bytes,
+  // 10-bit in 16-bit words); two groups run as two launches on forked streams of the graph.
+  int tc_groups = 1;
+  int tc_gbps[2] = {1, 2};
+  size_t tc_desc_bytes = 0;        // one group's descriptor block
   cudaStream_t stream = nullptr;
+  cudaStream_t stream2 = nullptr;  // the second group's branch while capturing
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   vca::BatchCta* d_map = nullptr;
   int n_cta = 0;
   size_t ma_bytes = 0, desc_bytes = 0;
@@ -161,10 +167,11 @@ struct vca_batch {
   uint8_t* h_desc[2] = {nullptr, nullptr};
   int* d_err = nullptr;            // the tensor-core kernel's wait-timeout flag
   int* h_err = nullptr;            // pinned, one per graph
-  std::vector<vca::TcBatchFrame> tc_frames;
+  std::vector<vca::TcBatchFrame> tc_frames[2];
   double* d_feats = nullptr;       // n x FEAT_STRIDE
   double* h_feats[2] = {nullptr, nullptr};
-  double* d_partials = nullptr;
+  unsigned long long* d_partials = nullptr;
+  int red_slices = 1;              // slices per frame of the batched reduction
   unsigned int* d_counters = nullptr;
   cudaGraph_t graph[2] = {nullptr, nullptr};
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
@@ -486,6 +493,9 @@ void destroy_batch(vca_batch* b) {
   cudaFree(b->d_partials);
   cudaFree(b->d_counters);
   if (b->stream) cudaStreamDestroy(b->stream);
+  if (b->stream2) cudaStreamDestroy(b->stream2);
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+  if (b->join_ev) cudaEventDestroy(b->join_ev);
   if (prev_dev >= 0) cudaSetDevice(prev_dev);
   delete b;
 }
@@ -497,14 +507,24 @@ cudaError_t build_tick_graph(vca_batch* b, int k) {
   cudaError_t e1 = cudaMemcpyAsync(b->d_desc, b->h_desc[k], b->desc_bytes, cudaMemcpyHostToDevice, b->stream);
   if (e1 == cudaSuccess && b->tc) {
     e1 = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
+    if (e1 == cudaSuccess && b->tc_groups == 2) {  // fork: the second group on its own branch
+      e1 = cudaEventRecord(b->fork_ev, b->stream);
+      if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(b->stream2, b->fork_ev, 0);
+      if (e1 == cudaSuccess)
+        e1 = vca::launch_tc_batch(b->d_desc + b->tc_desc_bytes, b->tc_gbps[1], b->low_pass, b->m[0]->tables,
+                                  b->d_err, b->stream2);
+      if (e1 == cudaSuccess) e1 = cudaEventRecord(b->join_ev, b->stream2);
+    }
     if (e1 == cudaSuccess)
-      e1 = vca::launch_tc_batch(b->d_desc, b->tc_bps, b->low_pass, b->m[0]->tables, b->d_err, b->stream);
+      e1 = vca::launch_tc_batch(b->d_desc, b->tc_gbps[0], b->low_pass, b->m[0]->tables, b->d_err, b->stream);
+    if (e1 == cudaSuccess && b->tc_groups == 2) e1 = cudaStreamWaitEvent(b->stream, b->join_ev, 0);
   } else if (e1 == cudaSuccess) {
     e1 = vca::launch_batch_plain(b->d_map, b->n_cta, reinterpret_cast<const vca::BatchMemberArgs*>(b->d_desc), b->w,
                                  b->nc, b->low_pass, b->stream);
   }
   if (e1 == cudaSuccess)
-    e1 = vca::launch_reduce_batch(reinterpret_cast<const vca::ReduceArgs*>(b->d_desc + b->ma_bytes), b->n, b->stream);
+    e1 = vca::launch_reduce_batch(reinterpret_cast<const vca::ReduceArgs*>(b->d_desc + b->ma_bytes), b->n,
+                                  b->red_slices, b->stream);
   if (e1 == cudaSuccess)
     e1 = cudaMemcpyAsync(b->h_feats[k], b->d_feats, (size_t)b->n * vca::FEAT_STRIDE * sizeof(double),
                          cudaMemcpyDeviceToHost, b->stream);
@@ -928,9 +948,13 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
   b->low_pass = members[0]->g.low_pass;
   b->tc = n <= vca::tc_batch_max_members();
   for (int i = 0; i < n; ++i) b->tc = b->tc && members[i]->kernel == VCA_KERNEL_TC;
-  b->tc_bps = members[0]->g.bps;
-  for (int i = 0; i < n; ++i)
-    if (members[i]->g.bps != b->tc_bps) b->tc_bps = 0;
+  bool has_bps[3] = {false, false, false};
+  for (int i = 0; i < n; ++i) has_bps[members[i]->g.bps] = true;
+  b->tc_groups = has_bps[1] && has_bps[2] ? 2 : 1;
+  if (b->tc_groups == 1) b->tc_gbps[0] = members[0]->g.bps;
+  int64_t max_C = 0;
+  for (int i = 0; i < n; ++i) max_C = members[i]->g.C > max_C ? members[i]->g.C : max_C;
+  b->red_slices = vca::reduce_batch_slices(max_C);
   int prev_dev = -1;
   cudaGetDevice(&prev_dev);
 
@@ -969,8 +993,8 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
     return fail(VCA_E_ARG, "batch too large");
   }
   b->n_cta = (int)map.size();
-  b->ma_bytes = b->tc ? round_up(vca::tc_batch_desc_bytes(), 256)
-                      : round_up((size_t)n * sizeof(vca::BatchMemberArgs), 256);
+  b->tc_desc_bytes = round_up(vca::tc_batch_desc_bytes(), 256);
+  b->ma_bytes = b->tc ? b->tc_groups * b->tc_desc_bytes : round_up((size_t)n * sizeof(vca::BatchMemberArgs), 256);
   b->desc_bytes = b->ma_bytes + (size_t)n * sizeof(vca::ReduceArgs);
   BATCH_CUDA(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking), "creating the batch stream");
   if (!b->tc) {
@@ -978,12 +1002,19 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
     BATCH_CUDA(cudaMemcpy(b->d_map, map.data(), map.size() * sizeof(vca::BatchCta), cudaMemcpyHostToDevice),
                "uploading the CTA map");
   }
-  if (b->tc) BATCH_CUDA(vca::tc_batch_prepare(b->tc_bps, b->low_pass), "preparing the tensor-core kernel");
+  for (int gi = 0; b->tc && gi < b->tc_groups; ++gi)
+    BATCH_CUDA(vca::tc_batch_prepare(b->tc_gbps[gi], b->low_pass), "preparing the tensor-core kernel");
+  if (b->tc && b->tc_groups == 2) {
+    BATCH_CUDA(cudaStreamCreateWithFlags(&b->stream2, cudaStreamNonBlocking), "creating the batch's second stream");
+    BATCH_CUDA(cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming), "creating batch events");
+    BATCH_CUDA(cudaEventCreateWithFlags(&b->join_ev, cudaEventDisableTiming), "creating batch events");
+  }
   BATCH_CUDA(cudaMalloc(&b->d_err, sizeof(int)), "allocating the error flag");
   BATCH_CUDA(cudaMemset(b->d_err, 0, sizeof(int)), "clearing the error flag");
   BATCH_CUDA(cudaMallocHost(&b->h_err, 2 * sizeof(int)), "allocating pinned error flags");
   b->h_err[0] = b->h_err[1] = 0;
-  b->tc_frames.reserve(n);
+  b->tc_frames[0].reserve(n);
+  b->tc_frames[1].reserve(n);
   BATCH_CUDA(cudaMalloc(&b->d_desc, b->desc_bytes), "allocating tick arguments");
   BATCH_CUDA(cudaMalloc(&b->d_feats, (size_t)n * vca::FEAT_STRIDE * sizeof(double)), "allocating features");
   BATCH_CUDA(cudaMalloc(&b->d_partials, vca::reduce_partials_bytes(n)), "allocating reduction scratch");
@@ -1021,7 +1052,8 @@ vca_status vca_batch_tick(vca_batch* b, const vca_frame_ref* frames) {
   auto* ra = reinterpret_cast<vca::ReduceArgs*>(b->h_desc[k] + b->ma_bytes);
   vca_batch::Tick tick;
   tick.k = k;
-  b->tc_frames.clear();
+  b->tc_frames[0].clear();
+  b->tc_frames[1].clear();
   for (int i = 0; i < b->n; ++i) {
     vca_analyzer* a = b->m[i];
     if (!frames[i].y) {
@@ -1031,7 +1063,8 @@ vca_status vca_batch_tick(vca_batch* b, const vca_frame_ref* frames) {
     }
     if (b->tc) {
       const vca_frame_ref& f = frames[i];
-      b->tc_frames.push_back({&a->g,
+      const int gi = b->tc_groups == 2 && a->g.bps == b->tc_gbps[1] ? 1 : 0;
+      b->tc_frames[gi].push_back({&a->g,
                               {static_cast<const uint8_t*>(f.y), static_cast<const uint8_t*>(f.u),
                                static_cast<const uint8_t*>(f.v), f.pitch_y, f.pitch_uv, 0, 0},
                               a->d_blockvals});
@@ -1043,12 +1076,13 @@ vca_status vca_batch_tick(vca_batch* b, const vca_frame_ref* frames) {
     }
     ra[i] = vca::reduce_args(a->g, 1, a->d_blockvals, a->d_prevH[a->cur_prev], a->has_prev,
                              a->d_prevH[a->cur_prev ^ 1], b->d_feats + (size_t)i * vca::FEAT_STRIDE,
-                             b->d_partials + (size_t)i * vca::reduce_partials_bytes(1) / sizeof(double),
+                             b->d_partials + (size_t)i * vca::reduce_partials_bytes(1) / sizeof(unsigned long long),
                              b->d_counters + i);
     tick.members.push_back({i, a->frames_pushed, a->has_prev != 0});
   }
-  if (b->tc) {
-    const cudaError_t e = vca::tc_batch_fill(b->h_desc[k], b->tc_frames.data(), (int)b->tc_frames.size());
+  for (int gi = 0; b->tc && gi < b->tc_groups; ++gi) {
+    const cudaError_t e = vca::tc_batch_fill(b->h_desc[k] + gi * b->tc_desc_bytes, b->tc_frames[gi].data(),
+                                             (int)b->tc_frames[gi].size());
     if (e != cudaSuccess) return cuda_fail(e, "encoding the tensor maps of a batch tick");
   }
   int prev_dev = -1;
@@ -1069,7 +1103,7 @@ vca_status vca_batch_tick(vca_batch* b, const vca_frame_ref* frames) {
   b->pending.push_back(std::move(tick));
   b->next_k ^= 1;
   b->ticks += 1;
-  b->launches += 2;
+  b->launches += (b->tc ? b->tc_groups : 1) + 1;  // analysis (one per sample-size group), reduction
   return VCA_OK;
 }
 

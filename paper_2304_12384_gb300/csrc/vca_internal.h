@@ -66,7 +66,7 @@ struct ReduceArgs {
   const float* prevH_in;
   float* prevH_out;
   double* feats;
-  double* partials;        // [frame][kSlices][kSums]
+  unsigned long long* partials;  // [frame][slice][sum] 128-bit slice totals (reduce_partials_bytes)
   unsigned int* counters;  // [frame], zero on entry, left at zero on exit
   int64_t C;
   int nframes;
@@ -94,8 +94,8 @@ cudaError_t launch_tc(const Geometry& g, const FramePlanes& fp, int nframes, con
                       float* blockvals, int16_t* const zdump[3], int* err, cudaStream_t s, int64_t* launches);
 bool tc_supported(const Geometry& g);
 
-// Batched tensor-core analysis: one frame of each of up to tc_batch_max_members() analyzers in
-// one launch of the persistent kernel.  The launch reads a descriptor block (the member table and
+// Batched tensor-core analysis: one frame of each of up to tc_batch_max_members() analyzers of
+// one sample size in one launch of the persistent kernel.  The launch reads a descriptor block (the member table and
 // each member's tensor maps, tc_batch_desc_bytes() bytes, 128-byte aligned) that the host writes
 // with tc_batch_fill and copies to the device unchanged before the launch.
 struct TcBatchFrame {
@@ -106,30 +106,32 @@ struct TcBatchFrame {
 int tc_batch_max_members();
 size_t tc_batch_desc_bytes();
 // Fills the descriptor block at h (host memory) for n frames; cudaErrorInvalidValue if n is out
-// of range or a tensor map cannot be encoded.
+// of range, the frames' sample sizes differ or a tensor map cannot be encoded.
 cudaError_t tc_batch_fill(void* h, const TcBatchFrame* frames, int n);
 // Sets up the kernel instance for this sample size and low_pass (outside any stream capture).
 cudaError_t tc_batch_prepare(int bps, bool low_pass);
 // Launches the analysis of the descriptor block at d_desc (device).  bps: the members' sample
-// size, or 0 if 8- and 10-bit members are mixed.
+// size (1 or 2).
 cudaError_t launch_tc_batch(const void* d_desc, int bps, bool low_pass, const DeviceTables& t, int* err,
                             cudaStream_t s);
 
-// Deterministic FP64 frame reduction: features of n frames and the h state update.  `partials`
-// holds reduce_partials_bytes(max frames) of scratch; `counters` (one per frame) must be zero on
-// entry and is zero again on exit.
+// Exact frame reduction: features of n frames (the block sums exact in 128-bit fixed point, each
+// total rounded once to FP64) and the h state update.  `partials` holds reduce_partials_bytes(max
+// frames) of scratch; `counters` (one per frame) must be zero on entry and is zero again on exit.
 size_t reduce_partials_bytes(int max_frames);
 cudaError_t launch_reduce(const Geometry& g, int nframes, const float* blockvals, const float* prevH_in,
-                          int has_prev, float* prevH_out, double* feats, double* partials, unsigned int* counters,
-                          cudaStream_t s, int64_t* launches);
+                          int has_prev, float* prevH_out, double* feats, unsigned long long* partials,
+                          unsigned int* counters, cudaStream_t s, int64_t* launches);
 
 // Reduction arguments of one analyzer (reduce_partials_bytes(nframes) of `partials`; `counters`
 // zero on entry).
 ReduceArgs reduce_args(const Geometry& g, int nframes, const float* blockvals, const float* prevH_in, int has_prev,
-                       float* prevH_out, double* feats, double* partials, unsigned int* counters);
+                       float* prevH_out, double* feats, unsigned long long* partials, unsigned int* counters);
 // Frame reduction of one frame per analyzer of a batch, in one launch: d_args (device) holds n
 // ReduceArgs with nframes 1 (or 0 for an analyzer skipped this tick).
-cudaError_t launch_reduce_batch(const ReduceArgs* d_args, int n, cudaStream_t s);
+cudaError_t launch_reduce_batch(const ReduceArgs* d_args, int n, int slices, cudaStream_t s);
+// Slices per frame of a batched reduction whose largest member has max_C blocks per plane.
+int reduce_batch_slices(int64_t max_C);
 
 // One CTA of the batched plain kernel: analyzer `member`, plane kind (0 luma, 1 chroma), plane
 // within the kind (chroma: 0 U, 1 V) and block chunk (BPC blocks).

@@ -1,14 +1,21 @@
 // Frame reduction of the analyzer (Section 2 of the paper: the seven per-frame features).
 //
-// Each frame is summed by kSlices CTAs.  CTA s takes the blocks [s*C/kSlices, (s+1)*C/kSlices):
-// thread i sums blocks i, i + 256, ... of the slice exactly in fixed point, then a fixed FP64
-// shared-memory tree gives the slice's seven partial sums.  The last CTA of the frame to finish
-// (a per-frame arrival counter) adds the kSlices partials in slice order and writes the
-// features, so the result does not depend on scheduling:
 //   E_P = sum_k H_{P,k} / (C N_P^2), L_P = sum_k L_{P,k} / C,
 //   h_t = sum_k |H_{Y,k,t} - H_{Y,k,t-1}| / (C w^2), and h = 0 without a previous frame.
-// The CTAs of the last frame also copy its luma energies as the next call's previous-frame state
-// (into a buffer distinct from the one read here).
+//
+// The sums are exact.  Every block value the analyzer writes is 0 or a float in [1, 2^30) (H adds
+// weights >= 1 times integers |Z| < 2^16 over at most 32 x 32 coefficients; L is the square root
+// of an integer), so it is a multiple of 2^-23 and v * 2^23 is an integer below 2^53, taken from
+// the float's bits with integer instructions.  The per-frame sums of those integers, and of
+// |H_t - H_{t-1}| in the same units, are kept in 128 bits; only the final total is rounded to
+// FP64 (once, to nearest) and divided by its norm.  The features therefore do not depend on how
+// the blocks are split between threads and CTAs.
+//
+// Each frame is summed by S CTAs ("slices", S = ceil(C / 512) up to 32, chosen per launch): CTA s
+// takes the blocks [s*C/S, (s+1)*C/S), its threads and warps combine their sums by shuffles and
+// shared memory, and the last CTA of the frame to finish (a per-frame arrival counter) adds the S
+// slice totals and writes the features.  The CTAs of the last frame also copy its luma energies
+// as the next call's previous-frame state (into a buffer distinct from the one read here).
 #include <cstdio>
 #include <mutex>
 
@@ -19,122 +26,164 @@ namespace vca {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kSlices = 8;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxSlices = 32;
+constexpr int64_t kSliceBlocks = 512;
 constexpr int kSums = 7;  // H_Y, L_Y, H_U, L_U, H_V, L_V, |dH_Y|
 
-// Slice `slice` of frame f (one CTA of kThreads threads).
-__device__ __forceinline__ void reduce_slice(const ReduceArgs& a, int f, int slice) {
-  __shared__ double part[kSums][kThreads];
+// Slices of a frame of C blocks.
+int slices_for(int64_t C) {
+  const int64_t s = (C + kSliceBlocks - 1) / kSliceBlocks;
+  return (int)(s < 1 ? 1 : s > kMaxSlices ? kMaxSlices : s);
+}
+
+// v * 2^23 for a block value v that is 0 or a float in [1, 2^40): the significand shifted by the
+// unbiased exponent.  (The analyzer writes no value in (0, 1); such a value would be truncated.)
+__device__ __forceinline__ unsigned long long fixed23(float v) {
+  const uint32_t b = __float_as_uint(v);
+  if (b == 0u) return 0ull;
+  const int e = (int)(b >> 23) - 127;
+  const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
+  return e >= 0 ? m << e : m >> -e;
+}
+
+struct U128 {
+  unsigned long long lo, hi;
+};
+
+__device__ __forceinline__ void add_to(U128& a, unsigned long long v) {
+  asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, 0;" : "+l"(a.lo), "+l"(a.hi) : "l"(v));
+}
+
+__device__ __forceinline__ void add_to(U128& a, const U128& b) {
+  asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(a.lo), "+l"(a.hi) : "l"(b.lo), "l"(b.hi));
+}
+
+// The 128-bit integer as the nearest double (ties to even): its leading 64 bits, with a sticky
+// bit for anything below them, rounded once by the 64-bit conversion and scaled.
+__device__ __forceinline__ double to_double(const U128& a) {
+  if (a.hi == 0ull) return __ull2double_rn(a.lo);
+  const int lz = __clzll((long long)a.hi);
+  const unsigned long long top = lz ? (a.hi << lz) | (a.lo >> (64 - lz)) : a.hi;
+  const unsigned long long rest = lz ? a.lo << lz : a.lo;
+  const double scale = __hiloint2double((1023 + 64 - lz) << 20, 0);  // 2^(64 - lz)
+  return __ull2double_rn(top | (rest != 0ull ? 1ull : 0ull)) * scale;
+}
+
+// Slice `slice` of S of frame f (one CTA of kThreads threads).  partials: [frame][kMaxSlices][kSums]
+// 128-bit slice totals.
+__device__ __forceinline__ void reduce_slice(const ReduceArgs& a, int f, int slice, int S) {
+  __shared__ U128 wsum[kWarps][kSums];
   __shared__ bool last;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t C = a.C;
-  const int64_t k0 = C * slice / kSlices, k1 = C * (slice + 1) / kSlices;
+  const int64_t k0 = C * slice / S, k1 = C * (slice + 1) / S;
   const float* bv = a.blockvals + (int64_t)f * N_ROWS * C;
   const float* prev = f > 0 ? a.blockvals + (int64_t)(f - 1) * N_ROWS * C + ROW_H_Y * C : a.prevH_in;
   const bool has_prev = f > 0 || a.has_prev;
 
-  // Per-thread sums in fixed point, v * 2^23 as an unsigned integer.  Every block value the
-  // analyzer writes is 0 or at least 1 (H sums weights >= 1 times integers |Z| < 2^16; L is the
-  // square root of an integer), so it is a multiple of 2^-23 below 2^30 and converts exactly;
-  // the sums, and |H_t - H_{t-1}|, are then exact integer arithmetic (a thread adds at most
-  // 2^20 / (8 * 256) = 512 values below 2^53).  The per-thread sums enter the FP64 tree below.
-  unsigned long long q[kSums] = {0, 0, 0, 0, 0, 0, 0};
+  U128 q[kSums];
+#pragma unroll
+  for (int r = 0; r < kSums; ++r) q[r] = U128{0ull, 0ull};
   for (int64_t k = k0 + tid; k < k1; k += kThreads) {
     unsigned long long v[N_ROWS];
 #pragma unroll
     for (int r = 0; r < N_ROWS; ++r) {
-      v[r] = __float2ull_rn(bv[r * C + k] * 8388608.0f);
-      q[r] += v[r];
+      v[r] = fixed23(bv[r * C + k]);
+      add_to(q[r], v[r]);
     }
     if (has_prev) {
-      const unsigned long long p = __float2ull_rn(prev[k] * 8388608.0f);
-      q[6] += v[ROW_H_Y] > p ? v[ROW_H_Y] - p : p - v[ROW_H_Y];
+      const unsigned long long pv = fixed23(prev[k]);
+      add_to(q[6], v[ROW_H_Y] > pv ? v[ROW_H_Y] - pv : pv - v[ROW_H_Y]);
     }
   }
-  double s[kSums];
-#pragma unroll
-  for (int r = 0; r < kSums; ++r) s[r] = (double)q[r] * 1.1920928955078125e-07;  // 2^-23
   if (f == a.nframes - 1) {
     for (int64_t k = k0 + tid; k < k1; k += kThreads) a.prevH_out[k] = bv[ROW_H_Y * C + k];
   }
 #pragma unroll
-  for (int r = 0; r < kSums; ++r) part[r][tid] = s[r];
-  __syncthreads();
-  for (int half = kThreads / 2; half > 0; half >>= 1) {
-    if (tid < half) {
+  for (int r = 0; r < kSums; ++r) {
 #pragma unroll
-      for (int r = 0; r < kSums; ++r) part[r][tid] += part[r][tid + half];
+    for (int o = 16; o > 0; o >>= 1) {
+      U128 other;
+      other.lo = __shfl_xor_sync(0xffffffffu, q[r].lo, o);
+      other.hi = __shfl_xor_sync(0xffffffffu, q[r].hi, o);
+      add_to(q[r], other);
     }
-    __syncthreads();
-  }
-  if (tid == 0) {
-    double* mine = a.partials + ((int64_t)f * kSlices + slice) * kSums;
-#pragma unroll
-    for (int r = 0; r < kSums; ++r) mine[r] = part[r][0];
-    __threadfence();
-    last = atomicAdd(&a.counters[f], 1u) == kSlices - 1;
+    if (lane == 0) wsum[warp][r] = q[r];
   }
   __syncthreads();
-  if (last && tid == 0) {
-    __threadfence();
-    const volatile double* all = a.partials + (int64_t)f * kSlices * kSums;
-    double t[kSums] = {0, 0, 0, 0, 0, 0, 0};
-    for (int sl = 0; sl < kSlices; ++sl)
+  if (tid < kSums) {  // this slice's total of sum tid, published before the arrival below
+    U128 t = wsum[0][tid];
 #pragma unroll
-      for (int r = 0; r < kSums; ++r) t[r] += all[sl * kSums + r];
+    for (int w = 1; w < kWarps; ++w) add_to(t, wsum[w][tid]);
+    volatile unsigned long long* mine = a.partials + (((int64_t)f * kMaxSlices + slice) * kSums + tid) * 2;
+    mine[0] = t.lo;
+    mine[1] = t.hi;
+    __threadfence();
+  }
+  __syncthreads();
+  if (tid == 0) last = atomicAdd(&a.counters[f], 1u) == (unsigned)S - 1u;
+  __syncthreads();
+  if (!last) return;
+  // The last slice to arrive: every slice total, read in parallel, then added in slice order.
+  __shared__ U128 slice_tot[kMaxSlices][kSums];
+  __threadfence();
+  const volatile unsigned long long* all = a.partials + (int64_t)f * kMaxSlices * kSums * 2;
+  for (int i = tid; i < S * kSums; i += kThreads) slice_tot[i / kSums][i % kSums] = U128{all[2 * i], all[2 * i + 1]};
+  __syncthreads();
+  if (tid < kSums) {  // thread r: sum r -> its feature (E_Y, h, L_Y, E_U, E_V, L_U, L_V)
+    U128 t{0ull, 0ull};
+    for (int sl = 0; sl < S; ++sl) add_to(t, slice_tot[sl][tid]);
+    const double total = to_double(t) * 1.1920928955078125e-07;  // x 2^-23 (exact)
+    int slot;
+    double norm;
+    switch (tid) {
+      case ROW_H_Y: slot = 0; norm = a.normY; break;
+      case ROW_L_Y: slot = 2; norm = (double)C; break;
+      case ROW_H_U: slot = 3; norm = a.normC; break;
+      case ROW_L_U: slot = 5; norm = (double)C; break;
+      case ROW_H_V: slot = 4; norm = a.normC; break;
+      case ROW_L_V: slot = 6; norm = (double)C; break;
+      default: slot = 1; norm = a.normY; break;  // the |dH_Y| sum: h
+    }
     double* out = a.feats + (int64_t)f * FEAT_STRIDE;
-    const double Cd = (double)C;
-    out[0] = t[ROW_H_Y] / a.normY;  // E_Y
-    out[1] = t[6] / a.normY;        // h
-    out[2] = t[ROW_L_Y] / Cd;       // L_Y
-    out[3] = t[ROW_H_U] / a.normC;  // E_U
-    out[4] = t[ROW_H_V] / a.normC;  // E_V
-    out[5] = t[ROW_L_U] / Cd;       // L_U
-    out[6] = t[ROW_L_V] / Cd;       // L_V
-    out[7] = 0.0;
-    a.counters[f] = 0;  // ready for the next launch (stream order separates launches)
+    out[slot] = total / norm;
+    if (tid == 0) {
+      out[7] = 0.0;
+      a.counters[f] = 0;  // ready for the next launch (stream order separates launches)
+    }
   }
 }
 
-__global__ void __launch_bounds__(kThreads) reduce_kernel(const ReduceArgs a) {
-  reduce_slice(a, blockIdx.x / kSlices, blockIdx.x % kSlices);
+__global__ void __launch_bounds__(kThreads) reduce_kernel(const ReduceArgs a, int S) {
+  reduce_slice(a, blockIdx.x / S, blockIdx.x % S, S);
 }
 
 // One frame per analyzer of a batch: args[m] describes analyzer m (nframes 0: skipped this tick).
-__global__ void __launch_bounds__(kThreads) reduce_batch_kernel(const ReduceArgs* __restrict__ args) {
-  const ReduceArgs a = args[blockIdx.x / kSlices];
+__global__ void __launch_bounds__(kThreads) reduce_batch_kernel(const ReduceArgs* __restrict__ args, int S) {
+  const ReduceArgs a = args[blockIdx.x / S];
   if (a.nframes == 0) return;
-  reduce_slice(a, 0, blockIdx.x % kSlices);
+  reduce_slice(a, 0, blockIdx.x % S, S);
 }
 
 }  // namespace
 
-size_t reduce_partials_bytes(int max_frames) { return (size_t)max_frames * kSlices * kSums * sizeof(double); }
+size_t reduce_partials_bytes(int max_frames) { return (size_t)max_frames * kMaxSlices * kSums * 16; }
 
 cudaError_t launch_reduce(const Geometry& g, int nframes, const float* blockvals, const float* prevH_in,
-                          int has_prev, float* prevH_out, double* feats, double* partials, unsigned int* counters,
-                          cudaStream_t s, int64_t* launches) {
+                          int has_prev, float* prevH_out, double* feats, unsigned long long* partials,
+                          unsigned int* counters, cudaStream_t s, int64_t* launches) {
   if (nframes <= 0) return cudaSuccess;
-  ReduceArgs a{};
-  a.blockvals = blockvals;
-  a.prevH_in = prevH_in;
-  a.prevH_out = prevH_out;
-  a.feats = feats;
-  a.partials = partials;
-  a.counters = counters;
-  a.C = g.C;
-  a.nframes = nframes;
-  a.has_prev = has_prev;
-  a.normY = (double)g.C * g.w * g.w;
-  a.normC = (double)g.C * g.nc * g.nc;
-  reduce_kernel<<<nframes * kSlices, kThreads, 0, s>>>(a);
+  const ReduceArgs a = reduce_args(g, nframes, blockvals, prevH_in, has_prev, prevH_out, feats, partials, counters);
+  const int S = slices_for(g.C);
+  reduce_kernel<<<nframes * S, kThreads, 0, s>>>(a, S);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) ++*launches;
   return e;
 }
 
 ReduceArgs reduce_args(const Geometry& g, int nframes, const float* blockvals, const float* prevH_in, int has_prev,
-                       float* prevH_out, double* feats, double* partials, unsigned int* counters) {
+                       float* prevH_out, double* feats, unsigned long long* partials, unsigned int* counters) {
   ReduceArgs a{};
   a.blockvals = blockvals;
   a.prevH_in = prevH_in;
@@ -150,9 +199,12 @@ ReduceArgs reduce_args(const Geometry& g, int nframes, const float* blockvals, c
   return a;
 }
 
-cudaError_t launch_reduce_batch(const ReduceArgs* d_args, int n, cudaStream_t s) {
+int reduce_batch_slices(int64_t max_C) { return slices_for(max_C); }
+
+cudaError_t launch_reduce_batch(const ReduceArgs* d_args, int n, int slices, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  reduce_batch_kernel<<<n * kSlices, kThreads, 0, s>>>(d_args);
+  if (slices < 1 || slices > kMaxSlices) return cudaErrorInvalidValue;
+  reduce_batch_kernel<<<n * slices, kThreads, 0, s>>>(d_args, slices);
   return cudaGetLastError();
 }
 
@@ -180,11 +232,11 @@ namespace vca {
 namespace {
 
 constexpr int kNoAllocMaxFrames = 256;
-constexpr size_t kNoAllocPartialBytes = (size_t)kNoAllocMaxFrames * kSlices * kSums * sizeof(double);
+constexpr size_t kNoAllocPartialBytes = (size_t)kNoAllocMaxFrames * kMaxSlices * kSums * 16;
 constexpr size_t kNoAllocBytes = kNoAllocPartialBytes + (size_t)kNoAllocMaxFrames * sizeof(unsigned int);
 static_assert(kNoAllocPartialBytes % 256 == 0, "counters start on a 256-byte boundary");
 
-// 114,688 B of partial sums (256 frames x 8 slices x 7 doubles), then 256 counters.
+// 917,504 B of slice totals (256 frames x 32 slices x 7 sums x 16 bytes), then 256 counters.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 constexpr int kMaxDevices = 64;
@@ -247,7 +299,7 @@ extern "C" vca_status vca_reduce_frames_noalloc(const float* block_values, int64
   g.nc = block_size / 2;
   int64_t launches = 0;
   e = launch_reduce(g, n_frames, block_values, prev_H_Y, prev_H_Y != nullptr, last_H_Y, features,
-                    static_cast<double*>(scratch),
+                    static_cast<unsigned long long*>(scratch),
                     reinterpret_cast<unsigned int*>(static_cast<unsigned char*>(scratch) + kNoAllocPartialBytes),
                     static_cast<cudaStream_t>(cuda_stream), &launches);
   if (e != cudaSuccess) {

@@ -65,7 +65,6 @@ struct TcMember {
   int tiles_x, tiles_per_frame;
   float inv_tiles_x, inv_tiles_per_frame;
   int W, H, cw, ch, nbx, nby;
-  int bps;                         // bytes per sample: 1 for 8-bit, 2 for 10-bit samples
   int64_t C, out_fstride;
   float* blockvals;
 };
@@ -91,10 +90,10 @@ struct TcTable {
 // 128-byte swizzle) and 64x64 chroma tiles with 128-byte rows and swizzle, 3 stages.
 template <int BPS>
 struct SmemLay {
-  static constexpr int kB = BPS == 1 ? 1 : 2;  // BPS 0 (8- and 10-bit members mixed) uses the 16-bit layout
-  static constexpr int kStages = kB == 1 ? 5 : 3;
-  static constexpr int kRawY = 128 * 128 * kB;
-  static constexpr int kRawC = 64 * 64 * kB;
+  static_assert(BPS == 1 || BPS == 2, "one sample size per launch");
+  static constexpr int kStages = BPS == 1 ? 5 : 3;
+  static constexpr int kRawY = 128 * 128 * BPS;
+  static constexpr int kRawC = 64 * 64 * BPS;
   static constexpr int kStageBytes = kRawY + 2 * kRawC;
   static constexpr int OFF_A2 = kStages * kStageBytes;   // luma: 2 slots x (hi, lo)
   static constexpr int OFF_A2C = OFF_A2 + 2 * 2 * kA2L;  // chroma: 2 slots x (hi, lo)
@@ -340,7 +339,7 @@ __device__ __forceinline__ uint32_t a2_addr(uint32_t sbase, int a2) {
 // (DC column) and c (the others), so that stage 1 leaves T' = c_k + sum in D1.
 template <int Nb, bool LP, int BPS>
 __device__ __forceinline__ void convert_job(const uint8_t* raw_plane, int jp, int h_rem, int w_rem, uint32_t ta1,
-                                            uint32_t td1, float c0, float c, int bps, int q, int lane) {
+                                            uint32_t td1, float c0, float c, int q, int lane) {
   using P = PC<Nb, LP>;
 #pragma unroll
   for (int g = 0; g < P::G; ++g) fill_cols<P::N1>(td1 + g * P::N1, c0, c);
@@ -354,12 +353,8 @@ __device__ __forceinline__ void convert_job(const uint8_t* raw_plane, int jp, in
     if (y >= h_rem) y = h_rem - 1;
     const int x = (idx & 3) * Nb;
 #pragma unroll
-    for (int c = 0; c < Nb / 16; ++c) {
-      if (BPS == 1 || (BPS == 0 && bps == 1))
-        convert_16<Nb, 1>(smem_u32(raw_plane), y, x + 16 * c, w_rem, ta1 + g * P::A1COLS + 8 * c);
-      else
-        convert_16<Nb, 2>(smem_u32(raw_plane), y, x + 16 * c, w_rem, ta1 + g * P::A1COLS + 8 * c);
-    }
+    for (int c = 0; c < Nb / 16; ++c)
+      convert_16<Nb, BPS>(smem_u32(raw_plane), y, x + 16 * c, w_rem, ta1 + g * P::A1COLS + 8 * c);
   }
 }
 
@@ -541,8 +536,9 @@ __device__ void convert_loop(const MS& ms, const Ctl& ctl, uint8_t* sm, uint32_t
   using SL = SmemLay<BPS>;
   constexpr int JPT = Jobs<LP>::PER_TILE;
   constexpr int T = 4 * Nb;  // tile edge of this plane in samples
-  float c0 = 0.0f, c = 0.0f;  // stage-1 presets of the tile's member
-  int bps = 1;
+  // Stage-1 presets 2^(s1-1) and, on the DC column, 2^(s1-1) - 1024 * 64 * N (the 1024 + x encoding).
+  constexpr float c = (float)(1 << (s1_of<Nb>(BPS) - 1));
+  constexpr float c0 = c - 1024.0f * 64.0f * (float)Nb;
   int r0, r1;
   plane_jobs<Nb, LP>(r0, r1);
   const int per_tile = r1 - r0;
@@ -555,10 +551,6 @@ __device__ void convert_loop(const MS& ms, const Ctl& ctl, uint8_t* sm, uint32_t
       const TcMember& M = ms[ti.m];
       h_rem = (Nb == 32 ? M.H : M.ch) - ti.ty * T;
       w_rem = (Nb == 32 ? M.W : M.cw) - ti.tx * T;
-      bps = BPS == 0 ? M.bps : BPS;
-      // Presets 2^(s1-1) and, on the DC column, 2^(s1-1) - 1024 * 64 * N (the 1024 + x encoding).
-      c = (float)(1 << (s1_of<Nb>(bps) - 1));
-      c0 = c - 1024.0f * 64.0f * (float)Nb;
       if (!wait_bar(ctl, b_raw_full(ti.stage), (t / SL::kStages) & 1, 4)) return;
     }
     const int jj = t * JPT + r;
@@ -569,9 +561,9 @@ __device__ void convert_loop(const MS& ms, const Ctl& ctl, uint8_t* sm, uint32_t
     tc_fence_after();
     // Plane offsets within the stage follow the member's sample size (the stage fits the largest).
     const uint8_t* raw =
-        sm + OFF_RAW + ti.stage * SL::kStageBytes + (plane == 0 ? 0 : 128 * 128 * bps + (plane - 1) * 64 * 64 * bps);
+        sm + OFF_RAW + ti.stage * SL::kStageBytes + (plane == 0 ? 0 : SL::kRawY + (plane - 1) * SL::kRawC);
     const uint32_t ta = tq + slot * kSlotCols;
-    convert_job<Nb, LP, BPS>(raw, jp, h_rem, w_rem, ta, ta + kD1Off, c0, c, bps, q, lane);
+    convert_job<Nb, LP, BPS>(raw, jp, h_rem, w_rem, ta, ta + kD1Off, c0, c, q, lane);
     tmem_wait_st();
     tc_fence_before();
     __syncwarp();
@@ -599,7 +591,7 @@ __device__ void epi1_loop(const MS& ms, const Ctl& ctl, uint32_t sbase, uint32_t
                           int step, int q, int lane) {
   using SL = SmemLay<BPS>;
   constexpr int JPT = Jobs<LP>::PER_TILE;
-  float s1inv = 0.0f;
+  const float s1inv = __int_as_float((127 - s1_of<Nb>(BPS)) << 23);  // 2^-s1
   const float hi0 = Nb == 32 ? kK1 - 2367488.0f : kK1 - 1183744.0f;
   const float lo = Nb == 32 ? 1024.0f : 512.0f;
   const uint32_t lo_off = Nb == 32 ? kA2L : kA2C;
@@ -609,10 +601,6 @@ __device__ void epi1_loop(const MS& ms, const Ctl& ctl, uint32_t sbase, uint32_t
   plane_jobs<Nb, LP>(r0, r1);
   const int n = n_items * (r1 - r0);
   for (int use = 0, t = 0, r = r0; use < n; ++use) {  // use: jobs of this plane type so far
-    if (r == r0) {  // 2^-s1 of the tile's member
-      const int bps = BPS == 0 ? ms[ms.member_of(item0 + t * step)].bps : BPS;
-      s1inv = __int_as_float((127 - s1_of<Nb>(bps)) << 23);
-    }
     const int jj = t * JPT + r;
     const int slot = jj % kSlots;
     const int a2 = use & 1;
@@ -780,18 +768,17 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
           for (int i = 0; i < 3; ++i) fence_tensormap_acquire(mm + i);
           fenced = ti.m;
         }
-        const int bps = BPS == 0 ? ms[ti.m].bps : BPS;
         uint8_t* dst = sm + OFF_RAW + stage * SL::kStageBytes;
         uint64_t* full = &bars[b_raw_full(stage)];
-        mbar_arrive_expect_tx(full, (uint32_t)(128 * 128 + 2 * 64 * 64) * bps);
-        if (bps == 1) {
+        mbar_arrive_expect_tx(full, SL::kStageBytes);
+        if (BPS == 1) {
           tma_load_3d(dst, mm, ti.tx * 128, ti.ty * 128, ti.f, full);
         } else {  // 16-bit luma: the tile is two 64-sample boxes side by side
           tma_load_3d(dst, mm, ti.tx * 128, ti.ty * 128, ti.f, full);
           tma_load_3d(dst + 128 * 64 * 2, mm, ti.tx * 128 + 64, ti.ty * 128, ti.f, full);
         }
-        tma_load_3d(dst + 128 * 128 * bps, mm + 1, ti.tx * 64, ti.ty * 64, ti.f, full);
-        tma_load_3d(dst + (128 * 128 + 64 * 64) * bps, mm + 2, ti.tx * 64, ti.ty * 64, ti.f, full);
+        tma_load_3d(dst + SL::kRawY, mm + 1, ti.tx * 64, ti.ty * 64, ti.f, full);
+        tma_load_3d(dst + SL::kRawY + SL::kRawC, mm + 2, ti.tx * 64, ti.ty * 64, ti.f, full);
         ++issued;
       }
       if (*abort_flag) {
@@ -961,13 +948,11 @@ cudaError_t launch_single(const TcParams& p, int grid, bool low_pass, bool dump,
   return dump ? launch_inst<false, true, 2, false>(p, grid, s) : launch_inst<false, false, 2, false>(p, grid, s);
 }
 
-// A batched launch: bps 1 or 2 for members of one sample size, 0 for a mix.
+// A batched launch of members of one sample size (bps 1 or 2).
 cudaError_t launch_batched(const TcParams& p, int grid, bool low_pass, int bps, cudaStream_t s) {
   if (bps == 1)
     return low_pass ? launch_inst<true, false, 1, true>(p, grid, s) : launch_inst<false, false, 1, true>(p, grid, s);
-  if (bps == 2)
-    return low_pass ? launch_inst<true, false, 2, true>(p, grid, s) : launch_inst<false, false, 2, true>(p, grid, s);
-  return low_pass ? launch_inst<true, false, 0, true>(p, grid, s) : launch_inst<false, false, 0, true>(p, grid, s);
+  return low_pass ? launch_inst<true, false, 2, true>(p, grid, s) : launch_inst<false, false, 2, true>(p, grid, s);
 }
 
 // One member's entry: geometry, outputs and stage-1 constants; returns its number of items.
@@ -984,7 +969,6 @@ int fill_member(TcMember& m, const Geometry& g, int item_base, int nframes, floa
   m.ch = g.ch;
   m.nbx = g.nbx;
   m.nby = g.nby;
-  m.bps = g.bps;
   m.C = g.C;
   m.out_fstride = (int64_t)N_ROWS * g.C;
   m.blockvals = blockvals;
@@ -1020,7 +1004,7 @@ cudaError_t tc_batch_fill(void* h, const TcBatchFrame* frames, int n) {
   for (int i = 0; i < n; ++i) {
     const Geometry& g = *frames[i].g;
     const FramePlanes& fp = frames[i].fp;
-    if (!tc_supported(g)) return cudaErrorInvalidValue;
+    if (!tc_supported(g) || g.bps != frames[0].g->bps) return cudaErrorInvalidValue;
     items += fill_member(tab->mem[i], g, items, 1, frames[i].blockvals);
     const CUtensorMapSwizzle swc = g.bps == 1 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
     cudaError_t e = make_map(&maps[3 * i], fp.y, g.W, g.H, fp.pitch_y, 0, 1, g.bps == 1 ? 128 : 64, 128, g.bps,
@@ -1035,13 +1019,13 @@ cudaError_t tc_batch_fill(void* h, const TcBatchFrame* frames, int n) {
 }
 
 cudaError_t tc_batch_prepare(int bps, bool low_pass) {
-  if (bps < 0 || bps > 2) return cudaErrorInvalidValue;
+  if (bps != 1 && bps != 2) return cudaErrorInvalidValue;
   return launch_batched(TcParams{}, 0, low_pass, bps, nullptr);
 }
 
 cudaError_t launch_tc_batch(const void* d_desc, int bps, bool low_pass, const DeviceTables& t, int* err,
                             cudaStream_t s) {
-  if (bps < 0 || bps > 2) return cudaErrorInvalidValue;
+  if (bps != 1 && bps != 2) return cudaErrorInvalidValue;
   TcParams p{};
   p.table = static_cast<const TcTable*>(d_desc);
   p.maps = reinterpret_cast<const CUtensorMap*>(static_cast<const uint8_t*>(d_desc) + kTcMapsOff);
