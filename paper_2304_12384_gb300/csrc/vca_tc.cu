@@ -18,15 +18,16 @@
 // A "job" is 128 stage-2 rows: 8 (low-pass) or 4 luma 32x32 blocks, or 16 / 8 chroma 16x16
 // blocks.  Per job:
 //   convert   raw u8 row -> fp16 (1024 + x, one PRMT per two samples) written to TMEM as the
-//             A operand; the stage-1 accumulators pre-set to c_k (the rounding offset 2^(s1-1),
-//             minus the 1024 * 64 * N encoding bias on the DC row);
-//   stage 1   D1 = c + X M^T (A from TMEM, M from shared memory), exact integers in FP32;
+//             A operand;
+//   stage 1   D1 = c + X M^T (A from TMEM, M from shared memory), exact integers in FP32; the
+//             presets c_k (the rounding offset 2^(s1-1), minus the 1024 * 64 * N encoding bias
+//             on the DC row) enter as one more MMA from constant shared-memory operands;
 //   epilogue1 T = floor(D1/2^s1) by one round-down FMA whose magic constant leaves
 //             U = T + 32768 in the low 16 bits and 0x64 in byte 2, so two PRMTs give the
 //             fp16 pairs (1024 + U_lo8, 1024 + U_hi8); stored MN-major (128-byte swizzle)
-//             as the stage-2 A operand -- the row/column transpose is the layout -- and the
-//             stage-2 accumulators pre-set to the magic constants of epilogue 2;
-//   stage 2   S_hi, S_lo = M T_hi, M T_lo (A MN-major from shared memory);
+//             as the stage-2 A operand -- the row/column transpose is the layout;
+//   stage 2   S_hi, S_lo = M T_hi, M T_lo (A MN-major from shared memory), the accumulators
+//             pre-set to the magic constants of epilogue 2 by one more MMA each;
 //   epilogue2 Z = floor((256 S_hi + S_lo + 2^(s2-1)) / 2^s2) by two round-down FMAs, then
 //             H_v = sum_u w(u,v) |Z| in increasing u and an xor tree over v.
 // Every partial sum is an integer below 2^24 in magnitude (or in [2^23, 2^24) for the
@@ -99,7 +100,10 @@ struct SmemLay {
   static constexpr int OFF_A2C = OFF_A2 + 2 * 2 * kA2L;  // chroma: 2 slots x (hi, lo)
   static constexpr int OFF_BL = OFF_A2C + 2 * 2 * kA2C;
   static constexpr int OFF_BC = OFF_BL + 2048;
-  static constexpr int OFF_BAR = OFF_BC + 512;
+  static constexpr int OFF_ONE = OFF_BC + 512;    // preset operand U (128 x 16)
+  static constexpr int OFF_KL = OFF_ONE + 4096;   // stage-1 preset operand K, luma (G N1 x 16)
+  static constexpr int OFF_KC = OFF_KL + 1024;    // and chroma
+  static constexpr int OFF_BAR = OFF_KC + 1024;
   static constexpr int OFF_MISC = OFF_BAR + kBars * 8;
   static constexpr int kSmemBytes = OFF_MISC + 64 + 1024;  // + slack to align the base to 1024
   // (the member table is a static shared array of kMemBytes beside this dynamic area)
@@ -126,7 +130,8 @@ __host__ __device__ constexpr int b_a2_free(int s) { return 2 * kMaxStages + 4 *
 __host__ __device__ constexpr int b_drain(int i) { return 2 * kMaxStages + 4 * kSlots + 2 * kA2Slots + i; }
 static_assert(b_drain(1) < kBars, "barrier area");
 
-constexpr int kThreads = 896;
+constexpr int kLumaConvertGroups = 1;  // warpgroups converting luma jobs (1 or 2)
+constexpr int kThreads = 896 + 128 * (kLumaConvertGroups - 1);
 constexpr uint32_t kTmemCols = 512;
 constexpr uint64_t kWaitNs = 2000000000ull;
 
@@ -221,13 +226,12 @@ __device__ __forceinline__ uint32_t raw_offset(int y, int xx) {
 }
 
 // Stage-1 operand conversion: 16 samples of this thread's row starting at column x (of the raw
-// tile, edge columns repeated past w_rem) -> 8 words of fp16 pairs (1024 + sample) at TMEM taddr.
+// tile, edge columns repeated past w_rem) -> 8 words of fp16 pairs (1024 + sample) in out.
 // 8-bit samples become fp16 0x6400 | x by one PRMT per two samples; 10-bit samples (below 1024)
 // by one AND-OR per two.
 template <int Nb, int BPS>
-__device__ __forceinline__ void convert_16(uint32_t base, int y, int x, int w_rem, uint32_t taddr) {
+__device__ __forceinline__ void convert_16(uint32_t base, int y, int x, int w_rem, uint32_t* out) {
   static_assert(BPS == 1 || BPS == 2, "one sample size");
-  uint32_t out[8];
   if (BPS == 1) {
     uint32_t words[4];
     if (x + 16 <= w_rem) {
@@ -275,7 +279,6 @@ __device__ __forceinline__ void convert_16(uint32_t base, int y, int x, int w_re
 #pragma unroll
     for (int i = 0; i < 8; ++i) out[i] = (words[i] & 0x03FF03FFu) | 0x64006400u;
   }
-  tmem_st<8>(taddr, out);
 }
 
 template <int N>
@@ -335,17 +338,18 @@ __device__ __forceinline__ uint32_t a2_addr(uint32_t sbase, int a2) {
 
 // ---- worker phases ----------------------------------------------------------
 
-// Writes the job's stage-1 A operand at ta1 and pre-sets its stage-1 accumulators at td1 to c0
-// (DC column) and c (the others), so that stage 1 leaves T' = c_k + sum in D1.
+// Writes the job's stage-1 A operand at ta1.
 template <int Nb, bool LP, int BPS>
 __device__ __forceinline__ void convert_job(const uint8_t* raw_plane, int jp, int h_rem, int w_rem, uint32_t ta1,
-                                            uint32_t td1, float c0, float c, int q, int lane) {
+                                            int q, int lane) {
   using P = PC<Nb, LP>;
-#pragma unroll
-  for (int g = 0; g < P::G; ++g) fill_cols<P::N1>(td1 + g * P::N1, c0, c);
+  // The job's groups occupy G * A1COLS consecutive columns, stored 16 at a time (8 if fewer).
+  constexpr int COLS = P::G * P::A1COLS;
+  constexpr int ST = COLS < 16 ? COLS : 16;
   const int l = 32 * q + lane;
   const int bg = l / Nb;
   const int r = l % Nb;
+  uint32_t out[ST];
 #pragma unroll
   for (int g = 0; g < P::G; ++g) {
     const int idx = jp * P::BPG2 + g * P::BPG1 + bg;
@@ -353,8 +357,11 @@ __device__ __forceinline__ void convert_job(const uint8_t* raw_plane, int jp, in
     if (y >= h_rem) y = h_rem - 1;
     const int x = (idx & 3) * Nb;
 #pragma unroll
-    for (int c = 0; c < Nb / 16; ++c)
-      convert_16<Nb, BPS>(smem_u32(raw_plane), y, x + 16 * c, w_rem, ta1 + g * P::A1COLS + 8 * c);
+    for (int c = 0; c < Nb / 16; ++c) {
+      const int col = g * P::A1COLS + 8 * c;  // first column of these 16 samples
+      convert_16<Nb, BPS>(smem_u32(raw_plane), y, x + 16 * c, w_rem, out + col % ST);
+      if ((col + 8) % ST == 0) tmem_st<ST>(ta1 + col + 8 - ST, out);
+    }
   }
 }
 
@@ -532,15 +539,19 @@ __device__ __forceinline__ void plane_jobs(int& r0, int& r1) {
 // Convert: raw samples of the tile -> stage-1 A operand in TMEM (and the D1 presets).
 template <int Nb, bool LP, int BPS, class MS>
 __device__ void convert_loop(const MS& ms, const Ctl& ctl, uint8_t* sm, uint32_t tq, int n_items, int item0,
-                             int step, int q, int lane) {
+                             int step, int q, int lane, int part) {
   using SL = SmemLay<BPS>;
   constexpr int JPT = Jobs<LP>::PER_TILE;
   constexpr int T = 4 * Nb;  // tile edge of this plane in samples
-  // Stage-1 presets 2^(s1-1) and, on the DC column, 2^(s1-1) - 1024 * 64 * N (the 1024 + x encoding).
-  constexpr float c = (float)(1 << (s1_of<Nb>(BPS) - 1));
-  constexpr float c0 = c - 1024.0f * 64.0f * (float)Nb;
   int r0, r1;
   plane_jobs<Nb, LP>(r0, r1);
+  if (Nb == 32 && kLumaConvertGroups == 2) {  // part 0 takes the first half of the tile's luma jobs
+    const int half = (r1 - r0) / 2;
+    if (part == 0)
+      r1 = r0 + half;
+    else
+      r0 += half;
+  }
   const int per_tile = r1 - r0;
   TileInfo ti{};
   int h_rem = 0, w_rem = 0;
@@ -563,7 +574,7 @@ __device__ void convert_loop(const MS& ms, const Ctl& ctl, uint8_t* sm, uint32_t
     const uint8_t* raw =
         sm + OFF_RAW + ti.stage * SL::kStageBytes + (plane == 0 ? 0 : SL::kRawY + (plane - 1) * SL::kRawC);
     const uint32_t ta = tq + slot * kSlotCols;
-    convert_job<Nb, LP, BPS>(raw, jp, h_rem, w_rem, ta, ta + kD1Off, c0, c, q, lane);
+    convert_job<Nb, LP, BPS>(raw, jp, h_rem, w_rem, ta, q, lane);
     tmem_wait_st();
     tc_fence_before();
     __syncwarp();
@@ -581,11 +592,12 @@ __device__ void convert_loop(const MS& ms, const Ctl& ctl, uint8_t* sm, uint32_t
   }
 }
 
-// Epilogue 1: T = floor(T'/2^s1) into the stage-2 operand (hi and lo bytes as fp16, MN-major), and
-// the stage-2 accumulators pre-set: hi starts at K1 - 1156 * 64 * N for u = 0 (the 1024 + byte
-// encoding of both halves) and K1 otherwise, lo at 2^(s2-1) (luma N = 32: s2 = 11; chroma
-// N = 16: s2 = 10; s1 = log2 N + B - 9 comes with the parameters).  Each plane type cycles through its own two stage-2 operand slots, so
-// every slot's full / free barriers see one in-order stream of jobs.
+// Epilogue 1: T = floor(T'/2^s1) into the stage-2 operand (hi and lo bytes as fp16, MN-major;
+// s1 = log2 N + B - 9), and the stage-2 accumulators pre-set: hi starts at K1 - 1156 * 64 * N for
+// u = 0 (the 1024 + byte encoding of both halves and the +128 offset of the hi byte) and K1
+// otherwise, lo at 2^(s2-1) (luma N = 32: s2 = 11; chroma N = 16: s2 = 10).  Each plane type
+// cycles through its own two stage-2 operand slots, so every slot's full / free barriers see one
+// in-order stream of jobs.
 template <int Nb, bool LP, int BPS, class MS>
 __device__ void epi1_loop(const MS& ms, const Ctl& ctl, uint32_t sbase, uint32_t tq, int n_items, int item0,
                           int step, int q, int lane) {
@@ -726,9 +738,32 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
     const __half h = __float2half_rn((float)p.M_c[n * 16 + kk]);
     *(__half*)(sm + SL::OFF_BC + (n >> 3) * 256 + (kk >> 3) * 128 + (n & 7) * 16 + (kk & 7) * 2) = h;
   }
+  // Stage-1 presets, applied by one more MMA per job ahead of the data: D1 = U x K^T with N = G N1
+  // (the job's groups side by side).  Every row of U is (1024, 1, 0, ...), so column n of D1
+  // starts at 1024 a_n + b_n for row n of K = (a_n, b_n, 0, ...): 2^(s1-1), the rounding offset
+  // of T, minus 1024 * 64 * N in each group's DC column (the bias of the 1024 + x sample
+  // encoding), split as a = -(multiple of 8 below 2^11) and b = P - 1024 a (|b| < 2^13, a multiple
+  // of 8), both exact in fp16.
+  for (int i = tid; i < 128 * 16; i += kThreads) {
+    const int m = i >> 4, kk = i & 15;
+    const float v = kk == 0 ? 1024.0f : kk == 1 ? 1.0f : 0.0f;
+    *(__half*)(sm + SL::OFF_ONE + (m >> 3) * 256 + (kk >> 3) * 128 + (m & 7) * 16 + (kk & 7) * 2) = __float2half_rn(v);
+  }
+  for (int i = tid; i < 2 * 32 * 16; i += kThreads) {
+    const int kk = i & 15, n = (i >> 4) & 31;
+    const bool luma = i < 32 * 16;
+    const int N = luma ? 32 : 16, N1 = luma ? L::N1 : Cc::N1, G = luma ? L::G : Cc::G;
+    if (n >= G * N1) continue;
+    const int P = (1 << (s1_of<32>(BPS) - (luma ? 1 : 2))) - (n % N1 == 0 ? 1024 * 64 * N : 0);
+    const int a = P >= 0 ? (P >> 10) & ~7 : -(((-P) >> 10) & ~7);
+    const float v = kk == 0 ? (float)a : kk == 1 ? (float)(P - a * 1024) : 0.0f;
+    *(__half*)(sm + (luma ? SL::OFF_KL : SL::OFF_KC) + (n >> 3) * 256 + (kk >> 3) * 128 + (n & 7) * 16 + (kk & 7) * 2) =
+        __float2half_rn(v);
+  }
   if (tid == 0) {
     for (int i = 0; i < kBars; ++i) mbar_init(&bars[i], 1);
-    for (int i = 0; i < SL::kStages; ++i) mbar_init(&bars[b_raw_empty(i)], 8);  // both convert warpgroups
+    for (int i = 0; i < SL::kStages; ++i)  // every convert warp arrives once per tile
+      mbar_init(&bars[b_raw_empty(i)], 4 * (kLumaConvertGroups + 1));
     for (int i = 0; i < kSlots; ++i) mbar_init(&bars[b_slot_free(i)], 4);
     for (int i = 0; i < kSlots; ++i) mbar_init(&bars[b_a1_full(i)], 4);
     for (int i = 0; i < kA2Slots; ++i) mbar_init(&bars[b_a2_full(i)], 4);
@@ -787,8 +822,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
           wait_bar(ctl, b_raw_full(t % SL::kStages), (t / SL::kStages) & 1, 1, true);
       }
     } else if (warp == 1 && lane == 0) {
-      // ---------------- stage-1 MMA issuer: D1 += A1 (TMEM) x M^T (D1 pre-set by convert) ----------------
+      // ---------------- stage-1 MMA issuer: D1 = U x K^T (presets), then D1 += A1 (TMEM) x M^T ----------------
       const uint32_t bl = sbase + SL::OFF_BL, bc = sbase + SL::OFF_BC;
+      const uint64_t du = smem_desc(sbase + SL::OFF_ONE, 128, 256, 0);
+      const uint64_t dkl = smem_desc(sbase + SL::OFF_KL, 128, 256, 0), dkc = smem_desc(sbase + SL::OFF_KC, 128, 256, 0);
+      constexpr uint32_t idPL = idesc_f16(128, L::G * L::N1, 0, 0), idPC = idesc_f16(128, Cc::G * Cc::N1, 0, 0);
       constexpr uint32_t idL = idesc_f16(128, L::N1, 0, 0), idC = idesc_f16(128, Cc::N1, 0, 0);
       bool ok = true;
       for (int j = 0; j < n_jobs; ++j) {
@@ -803,6 +841,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
         const uint32_t a = tmem + slot * kSlotCols;
         const uint32_t d = a + kD1Off;
         if (plane == 0) {
+          mma_ss(d, du, dkl, idPL, 0);  // presets of the job's groups
           // K-step outer: consecutive MMAs write different accumulators.
 #pragma unroll
           for (int ks = 0; ks < 2; ++ks)
@@ -810,6 +849,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
             for (int gg = 0; gg < L::G; ++gg)
               mma_ts(d + gg * L::N1, a + gg * L::A1COLS + ks * 8, smem_desc(bl + ks * 256, 128, 512, 0), idL, 1);
         } else {
+          mma_ss(d, du, dkc, idPC, 0);
 #pragma unroll
           for (int gg = 0; gg < Cc::G; ++gg)
             mma_ts(d + gg * Cc::N1, a + gg * Cc::A1COLS, smem_desc(bc, 128, 256, 0), idC, 1);
@@ -821,7 +861,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
         wait_bar(ctl, b_drain(0), 0, 2, true);
       }
     } else if (warp == 2 && lane == 0) {
-      // ---------------- stage-2 MMA issuer: D2 = A2 (smem, MN-major) x M^T, hi and lo ----------------
+      // ---------------- stage-2 MMA issuer: D2 += A2 (smem, MN-major) x M^T, hi and lo (D2 pre-set by epilogue 1) ----------------
       const uint32_t bl = sbase + SL::OFF_BL, bc = sbase + SL::OFF_BC;
       constexpr uint32_t id2L = idesc_f16(128, L::N1, 1, 0), id2C = idesc_f16(128, Cc::N1, 1, 0);
       bool ok = true;
@@ -857,10 +897,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
         wait_bar(ctl, b_drain(1), 0, 2, true);
       }
     }
-  } else if (role == 1) {
-    convert_loop<32, LP, BPS>(ms, ctl, sm, tmem + lanebase, n_items, item0, step, q, lane);
+  } else if (role == 1 || (kLumaConvertGroups == 2 && role == 7)) {
+    convert_loop<32, LP, BPS>(ms, ctl, sm, tmem + lanebase, n_items, item0, step, q, lane, role == 7);
   } else if (role == 6) {
-    convert_loop<16, LP, BPS>(ms, ctl, sm, tmem + lanebase, n_items, item0, step, q, lane);
+    convert_loop<16, LP, BPS>(ms, ctl, sm, tmem + lanebase, n_items, item0, step, q, lane, 0);
   } else if (role == 2) {
     epi1_loop<32, LP, BPS>(ms, ctl, sbase, tmem + lanebase, n_items, item0, step, q, lane);
   } else if (role == 3) {
