@@ -37,7 +37,8 @@ METRIC = "2160p 8-bit frames/sec (7 features), % of HBM roofline; p99 per-frame 
 PAPER_FPS = 292.68  # paper, Section 3: VCA v2.0 with all optimisations on 8 CPU threads, UHD 8-bit
 W, H = 3840, 2160
 FRAME_BYTES = W * H + 2 * (W // 2) * (H // 2)  # 12,441,600 B per 8-bit 4:2:0 frame
-KERNEL_SOURCES = ("paper_2304_12384_gb300/csrc/vca_tc.cu", "paper_2304_12384_gb300/csrc/vca_plain.cu")
+KERNEL_SOURCES = ("paper_2304_12384_gb300/csrc/vca_tc.cu", "paper_2304_12384_gb300/csrc/vca_plain.cu",
+                  "paper_2304_12384_gb300/csrc/vca_plain.cuh", "paper_2304_12384_gb300/csrc/vca_ptx.cuh")
 
 
 def parse_args():
@@ -52,6 +53,8 @@ def parse_args():
     p.add_argument("--block-size", type=int, default=32)
     p.add_argument("--full", action="store_true", help="all coefficients instead of the low-pass subset")
     p.add_argument("--no-extras", action="store_true", help="skip variants, latency, e2e and cpu baseline")
+    p.add_argument("--extras", default="all",
+                   help="comma-separated subset of latency,e2e,variants,siti,ladder,serving,cpu (default all)")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     return p.parse_args()
 
@@ -351,90 +354,105 @@ def run_extras(args, an, y, u, v, frames, stream, kern, lp, device):
     from paper_2304_12384_gb300 import vca
 
     out = {}
-    # Per-frame latency: one device-resident frame per push, features read back (blocking).
-    lat = []
-    for i in range(20 + 200):
+    chosen = set(args.extras.split(","))
+
+    def want(name):
+        return "all" in chosen or name in chosen
+
+    if want("latency"):
+        # Per-frame latency: one device-resident frame per push, features read back (blocking).
+        lat = []
+        for i in range(20 + 200):
+            t0 = time.perf_counter()
+            an.push(y[i % args.frames], u[i % args.frames], v[i % args.frames])
+            last = vca.vca_read_frame_features(an.handle, an.frames_pushed - 1, 1)
+            t1 = time.perf_counter()
+            if i >= 20:
+                lat.append((t1 - t0) * 1000.0)
+        assert last.frame >= 0
+        out["latency_ms"] = {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                             "frames": len(lat), "mode": "one 2160p frame per push, blocking feature read"}
+
+    if want("e2e"):
+        # End to end: pinned host frames through the same call, copies inside the timed region.
+        hy = y.cpu().pin_memory()
+        hu = u.cpu().pin_memory()
+        hv = v.cpu().pin_memory()
+        for _ in range(2):
+            an.push(hy, hu, hv)
+        an.sync()
+        steps = max(3, min(args.steps, 10))
         t0 = time.perf_counter()
-        an.push(y[i % args.frames], u[i % args.frames], v[i % args.frames])
-        last = vca.vca_read_frame_features(an.handle, an.frames_pushed - 1, 1)
-        t1 = time.perf_counter()
-        if i >= 20:
-            lat.append((t1 - t0) * 1000.0)
-    assert last.frame >= 0
-    out["latency_ms"] = {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                         "frames": len(lat), "mode": "one 2160p frame per push, blocking feature read"}
+        for _ in range(steps):
+            an.push(hy, hu, hv)
+            vca.vca_read_frame_features(an.handle, an.frames_pushed - 1, 1)
+        an.sync()
+        el = time.perf_counter() - t0
+        out["e2e"] = {"value": steps * args.frames / el, "unit": "frames/s",
+                      "h2d_bytes_per_step": args.frames * FRAME_BYTES, "d2h_bytes_per_step": args.frames * 8 * 8}
+        del hy, hu, hv
 
-    # End to end: pinned host frames through the same call, copies inside the timed region.
-    hy = y.cpu().pin_memory()
-    hu = u.cpu().pin_memory()
-    hv = v.cpu().pin_memory()
-    for _ in range(2):
-        an.push(hy, hu, hv)
-    an.sync()
-    steps = max(3, min(args.steps, 10))
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        an.push(hy, hu, hv)
-        vca.vca_read_frame_features(an.handle, an.frames_pushed - 1, 1)
-    an.sync()
-    el = time.perf_counter() - t0
-    out["e2e"] = {"value": steps * args.frames / el, "unit": "frames/s",
-                  "h2d_bytes_per_step": args.frames * FRAME_BYTES, "d2h_bytes_per_step": args.frames * 8 * 8}
-    del hy, hu, hv
+    if want("variants"):
+        # Other block-size / low-pass variants and the plain CUDA-core form, same frames.
+        variants = {}
+        lp_name = {False: "full", True: "lowpass", "downsample": "downsample"}
+        for (bs, vlp, vk) in ((32, True, vca.VCA_KERNEL_PLAIN), (32, False, kern), (16, True, kern), (16, False, kern),
+                              (32, False, vca.VCA_KERNEL_PLAIN), (32, "downsample", vca.VCA_KERNEL_AUTO)):
+            try:
+                a2 = vca.Analyzer(W, H, 8, bs, vlp, kernel=vk, max_batch=args.frames, stream=stream.cuda_stream)
+            except vca.VcaError as e:
+                variants[f"w{bs}_{lp_name[vlp]}_{vk}"] = f"unsupported: {e}"
+                continue
+            name = f"w{bs}_{lp_name[vlp]}_{ {1: 'plain', 2: 'tc'}[a2.kernel] }"
+            ms, kms, _ = time_pushes(a2, y, u, v, max(3, args.steps // 3), 2, stream, lambda: None)
+            n = max(3, args.steps // 3) * args.frames
+            gbs = args.frames * FRAME_BYTES / (kms / 1000.0) / 1e9
+            variants[name] = {"fps": n / (ms / 1000.0), "kernel_ms_per_launch": kms,
+                              "hbm_frac_of_measured": gbs / load_peaks()[0]}
+            a2.close()
+        # 10-bit 2160p (16-bit words): tensor-core and CUDA-core forms on the same frames.
+        _, (y10, u10, v10) = make_device_frames(args, device, bit_depth=10)
+        for vk in (vca.VCA_KERNEL_TC, vca.VCA_KERNEL_PLAIN):
+            a2 = vca.Analyzer(W, H, 10, 32, True, kernel=vk, max_batch=args.frames, stream=stream.cuda_stream)
+            name = f"w32_lowpass_10bit_{ {1: 'plain', 2: 'tc'}[a2.kernel] }"
+            ms, kms, _ = time_pushes(a2, y10, u10, v10, max(3, args.steps // 3), 2, stream, lambda: None)
+            n = max(3, args.steps // 3) * args.frames
+            gbs = args.frames * 2 * FRAME_BYTES / (kms / 1000.0) / 1e9
+            variants[name] = {"fps": n / (ms / 1000.0), "kernel_ms_per_launch": kms,
+                              "hbm_frac_of_measured": gbs / load_peaks()[0]}
+            a2.close()
+        del y10, u10, v10
+        out["variants"] = variants
 
-    # Other block-size / low-pass variants and the plain CUDA-core form, same frames.
-    variants = {}
-    lp_name = {False: "full", True: "lowpass", "downsample": "downsample"}
-    for (bs, vlp, vk) in ((32, True, vca.VCA_KERNEL_PLAIN), (32, False, kern), (16, True, kern), (16, False, kern),
-                          (32, False, vca.VCA_KERNEL_PLAIN), (32, "downsample", vca.VCA_KERNEL_AUTO)):
-        try:
-            a2 = vca.Analyzer(W, H, 8, bs, vlp, kernel=vk, max_batch=args.frames, stream=stream.cuda_stream)
-        except vca.VcaError as e:
-            variants[f"w{bs}_{lp_name[vlp]}_{vk}"] = f"unsupported: {e}"
-            continue
-        name = f"w{bs}_{lp_name[vlp]}_{ {1: 'plain', 2: 'tc'}[a2.kernel] }"
-        ms, kms, _ = time_pushes(a2, y, u, v, max(3, args.steps // 3), 2, stream, lambda: None)
-        n = max(3, args.steps // 3) * args.frames
-        variants[name] = {"fps": n / (ms / 1000.0), "kernel_ms_per_launch": kms,
-                          "hbm_frac_of_measured": args.frames * FRAME_BYTES / (kms / 1000.0) / 1e9 / load_peaks()[0]}
-        a2.close()
-    # 10-bit 2160p (16-bit words): tensor-core and CUDA-core forms on the same frames.
-    _, (y10, u10, v10) = make_device_frames(args, device, bit_depth=10)
-    for vk in (vca.VCA_KERNEL_TC, vca.VCA_KERNEL_PLAIN):
-        a2 = vca.Analyzer(W, H, 10, 32, True, kernel=vk, max_batch=args.frames, stream=stream.cuda_stream)
-        name = f"w32_lowpass_10bit_{ {1: 'plain', 2: 'tc'}[a2.kernel] }"
-        ms, kms, _ = time_pushes(a2, y10, u10, v10, max(3, args.steps // 3), 2, stream, lambda: None)
-        n = max(3, args.steps // 3) * args.frames
-        variants[name] = {"fps": n / (ms / 1000.0), "kernel_ms_per_launch": kms,
-                          "hbm_frac_of_measured": args.frames * 2 * FRAME_BYTES / (kms / 1000.0) / 1e9 / load_peaks()[0]}
-        a2.close()
-    del y10, u10, v10
-    out["variants"] = variants
-
-    # SI / TI of the same 2160p frames (the paper's comparison features; its CPU reference runs
-    # at 8.55 fps on an i7-11370H, Section 3 -- another machine, context only).
-    s = vca.Siti(W, H, 8, max_batch=args.frames, stream=stream.cuda_stream)
-    s.push(y)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    reps = 5
-    for _ in range(reps):
+    if want("siti"):
+        # SI / TI of the same 2160p frames (the paper's comparison features; its CPU reference runs
+        # at 8.55 fps on an i7-11370H, Section 3 -- another machine, context only).
+        s = vca.Siti(W, H, 8, max_batch=args.frames, stream=stream.cuda_stream)
         s.push(y)
-    el = time.perf_counter() - t0
-    out["siti"] = {"fps": reps * args.frames / el, "frames_per_push": args.frames, "launches_per_push": 2,
-                   "hbm_frac_of_measured": reps * args.frames * W * H / el / 1e9 / load_peaks()[0],
-                   "timing": "host wall clock per synchronous push (luma read once, 3x3 neighbourhood from cache)"}
-    s.close()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = 5
+        for _ in range(reps):
+            s.push(y)
+        el = time.perf_counter() - t0
+        out["siti"] = {"fps": reps * args.frames / el, "frames_per_push": args.frames, "launches_per_push": 2,
+                       "hbm_frac_of_measured": reps * args.frames * W * H / el / 1e9 / load_peaks()[0],
+                       "timing": "host wall clock per synchronous push (luma read once, 3x3 neighbourhood from cache)"}
+        s.close()
 
-    out["ladder"] = run_ladder(args, stream)
-    out["serving"] = run_serving(args)
+    if want("ladder"):
+        out["ladder"] = run_ladder(args, stream)
 
-    # CPU oracle on the host cores, bounded sample of the same workload.
-    cfg = Config(W, H, 8, args.block_size, lp)
-    fps, n = oracle_fps(frames[:2], cfg, args.cpu_seconds)
-    out["cpu_baseline"] = {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
-                           "sample": f"{n} frames of the same 3840x2160 workload through the FP64/int64 oracle "
-                                     f"(numpy, one process, single-threaded integer matmul)"}
+    if want("serving"):
+        out["serving"] = run_serving(args)
+
+    if want("cpu"):
+        # CPU oracle on the host cores, bounded sample of the same workload.
+        cfg = Config(W, H, 8, args.block_size, lp)
+        fps, n = oracle_fps(frames[:2], cfg, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                               "sample": f"{n} frames of the same 3840x2160 workload through the FP64/int64 oracle "
+                                         f"(numpy, one process, single-threaded integer matmul)"}
     return out
 
 
