@@ -169,6 +169,26 @@ vca_status vca_stream_join(vca_analyzer* a);
 vca_status vca_export_state(vca_analyzer* a, void* buf, size_t* len);
 vca_status vca_import_state(vca_analyzer* a, const void* buf, size_t len);
 
+/* Drop-in DCT matrix (an encoder's own integer table, for example a standard's hand-tuned one,
+ * in place of the round-cosine matrix M_N of the transform reading above; Section 2 item (2):
+ * the analyzer's DCT is an encoder's integer routine).  matrix: n x n int8, row-major, row k =
+ * basis function k, n one of the analyzer's transform sizes (w, and the chroma block size; a
+ * 4:4:4 analyzer's planes share one size).  Every later push, coefficient dump and batch tick
+ * uses it, on either kernel.  Requirements (vca_check_dct_matrix): n in {4, 8, 16, 32},
+ * matrix[0][0] = 64, and the even/odd symmetry of the DCT at every level (the level-L matrix is
+ * rows 0, n/L, 2n/L, ... on their first L columns; its row k is even about the middle for even k
+ * and odd for odd k), so that the butterfly and the matrix forms agree and every row but the
+ * first sums to 0; for bit depths up to 10, T = (X M^T + 2^(s1-1)) >> s1 must stay within 16
+ * bits.  The library copies the matrix.  VCA_E_STATE after the first push or inside a batch;
+ * VCA_E_ARG (with the reason in vca_last_error) for a wrong size or a matrix that fails a
+ * requirement.  Analyzers whose matrices differ can share a batch, which then runs the CUDA-core
+ * kernel. */
+vca_status vca_set_dct_matrix(vca_analyzer* a, int32_t n, const int8_t* matrix);
+
+/* Checks a matrix against the requirements of vca_set_dct_matrix for the given bit depth (8, 10
+ * or 12), on the host only. */
+vca_status vca_check_dct_matrix(int32_t n, int32_t bit_depth, const int8_t* matrix);
+
 /* Frames pushed since vca_open (or since the frame count an imported state carried). */
 vca_status vca_frames_pushed(vca_analyzer* a, int64_t* frames);
 

@@ -150,17 +150,19 @@ def round_shift(v, s: int) -> np.ndarray:
     return (v + (np.int64(1) << np.int64(s - 1))) >> np.int64(s)
 
 
-def int_dct2_stages(blocks, bit_depth: int, low_pass: bool = False):
+def int_dct2_stages(blocks, bit_depth: int, low_pass: bool = False, M=None):
     """Two-stage integer forward DCT of blocks shaped (..., N, N).
 
     Stage 1 (rows):    T[r][k] = (sum_c x[r][c] M[k][c] + 2^(s1-1)) >> s1
     Stage 2 (columns): Z[u][v] = (sum_r M[u][r] T[r][v] + 2^(s2-1)) >> s2
     Low-pass (Section 2 item (3)): k and u run over the first N/2 rows of M only.
+    M is the N x N integer matrix (default: the round-cosine matrix; a caller may supply another
+    table of the same structure, such as an encoder's hand-tuned one).
     Returns (T, Z) as int64 arrays; T is (..., N, Nk) and Z is (..., Nk, Nk).
     """
     x = np.asarray(blocks, dtype=np.int64)
     N = x.shape[-1]
-    M = int_dct_matrix(N)
+    M = int_dct_matrix(N) if M is None else np.asarray(M, dtype=np.int64)
     Nk = N // 2 if low_pass else N
     Mk = M[:Nk]
     s1, s2 = transform_shifts(N, bit_depth)
@@ -169,18 +171,24 @@ def int_dct2_stages(blocks, bit_depth: int, low_pass: bool = False):
     return T, Z
 
 
-def int_dct2(blocks, bit_depth: int, low_pass: bool = False) -> np.ndarray:
+def int_dct2(blocks, bit_depth: int, low_pass: bool = False, M=None) -> np.ndarray:
     """Quantised coefficients Z of the two-stage integer transform (see int_dct2_stages)."""
-    return int_dct2_stages(blocks, bit_depth, low_pass)[1]
+    return int_dct2_stages(blocks, bit_depth, low_pass, M)[1]
 
 
-def _butterfly_1d(x: np.ndarray, N: int) -> np.ndarray:
+def _butterfly_1d(x: np.ndarray, N: int, M=None) -> np.ndarray:
     """Raw 1-D integer transform y[k] = sum_n M_N[k][n] x[n] along the last axis.
 
     Even/odd decomposition: even outputs are the N/2-point transform of
-    e[n] = x[n] + x[N-1-n]; odd outputs apply the odd rows of M_N (first half of
-    the columns) to o[n] = x[n] - x[N-1-n].  Recurses down to M_1 = [[64]].
+    e[n] = x[n] + x[N-1-n] with the matrix of M's even rows on the first N/2 columns; odd outputs
+    apply the odd rows of M (first half of the columns) to o[n] = x[n] - x[N-1-n].  Recurses
+    down to the 1 x 1 matrix [[64]].  This equals the matrix form exactly when M has the DCT's
+    structure (row 0 all 64, row k even / odd about the middle for even / odd k, and the even
+    rows on the first half forming a matrix of the same structure).
     """
+    if M is None:
+        M = int_dct_matrix(N)
+    M = np.asarray(M, dtype=np.int64)
     if N == 1:
         return 64 * x
     h = N // 2
@@ -189,18 +197,18 @@ def _butterfly_1d(x: np.ndarray, N: int) -> np.ndarray:
     e = a + b
     o = a - b
     y = np.empty(x.shape[:-1] + (N,), dtype=np.int64)
-    y[..., 0::2] = _butterfly_1d(e, h)
-    y[..., 1::2] = np.matmul(o, int_dct_matrix(N)[1::2, :h].T)
+    y[..., 0::2] = _butterfly_1d(e, h, M[0::2, :h])
+    y[..., 1::2] = np.matmul(o, M[1::2, :h].T)
     return y
 
 
-def int_dct2_butterfly(blocks, bit_depth: int) -> np.ndarray:
+def int_dct2_butterfly(blocks, bit_depth: int, M=None) -> np.ndarray:
     """Same two-stage integer transform computed with the recursive butterfly (full Z only)."""
     x = np.asarray(blocks, dtype=np.int64)
     N = x.shape[-1]
     s1, s2 = transform_shifts(N, bit_depth)
-    T = round_shift(_butterfly_1d(x, N), s1)
-    Zt = round_shift(_butterfly_1d(np.swapaxes(T, -1, -2), N), s2)
+    T = round_shift(_butterfly_1d(x, N, M), s1)
+    Zt = round_shift(_butterfly_1d(np.swapaxes(T, -1, -2), N, M), s2)
     return np.swapaxes(Zt, -1, -2)
 
 
@@ -245,6 +253,16 @@ class Config:
     pad_mode: str = "replicate"  # or "skip"
     downsample: bool = False     # the downsample reading of the low-pass option (excludes low_pass)
     chroma_format: str = "420"   # or "444"
+    # Caller-supplied integer DCT matrices: ((N, rows), ...) with rows a tuple of N tuples of N
+    # ints; a transform size without an entry uses the round-cosine matrix int_dct_matrix(N).
+    dct_matrices: tuple = ()
+
+    def matrix(self, n: int) -> np.ndarray:
+        """The n x n integer DCT matrix of this configuration."""
+        for size, rows in self.dct_matrices:
+            if size == n:
+                return np.asarray(rows, dtype=np.int64)
+        return int_dct_matrix(n)
 
     def transform_sizes(self) -> tuple[int, int]:
         """(luma, chroma) block size of the transform: w and w/2 (4:2:0) or w (4:4:4), each
@@ -284,9 +302,9 @@ def plane_blocks(plane: np.ndarray, n: int, nbx: int, nby: int) -> np.ndarray:
     return padded.reshape(nby, n, nbx, n).transpose(0, 2, 1, 3).reshape(nby * nbx, n, n)
 
 
-def plane_block_values(plane, n: int, nbx: int, nby: int, bit_depth: int, low_pass: bool):
-    """Per-block (H, L, Z) of one plane with n x n blocks."""
-    Z = int_dct2(plane_blocks(plane, n, nbx, nby), bit_depth, low_pass)
+def plane_block_values(plane, n: int, nbx: int, nby: int, bit_depth: int, low_pass: bool, M=None):
+    """Per-block (H, L, Z) of one plane with n x n blocks (M: the n x n matrix, default round-cosine)."""
+    Z = int_dct2(plane_blocks(plane, n, nbx, nby), bit_depth, low_pass, M)
     return block_texture_energy(Z, n), block_brightness(Z), Z
 
 
@@ -310,7 +328,7 @@ def frame_block_values(y, u, v, cfg: Config) -> dict:
         y, u, v = downsample_plane(y), downsample_plane(u), downsample_plane(v)
     out = {}
     for name, plane, n in (("Y", y, ny), ("U", u, nc), ("V", v, nc)):
-        H, L, _ = plane_block_values(plane, n, nbx, nby, cfg.bit_depth, cfg.low_pass)
+        H, L, _ = plane_block_values(plane, n, nbx, nby, cfg.bit_depth, cfg.low_pass, cfg.matrix(n))
         out["H_" + name] = H
         out["L_" + name] = L
     return out

@@ -92,6 +92,7 @@ struct vca_analyzer {
 
   void* d_tables = nullptr;
   DeviceTables tables{};
+  int8_t M_host[2][32 * 32] = {};  // host copies of the luma and chroma matrices (N = g.w, g.nc)
   float* d_blockvals = nullptr;  // 2 x max_batch + 1 frames of [6][C]: two push buffers, then a dump slot
   float* last_bv = nullptr;      // block values of the most recent push
   int bv_slot = 0;               // push buffer of the next push
@@ -640,6 +641,8 @@ vca_status vca_open(const vca_config* cfg, void* cuda_stream, vca_analyzer** out
   a->tables.M_c = reinterpret_cast<const int8_t*>(tb + oMc);
   a->tables.W_y = reinterpret_cast<const float*>(tb + oWy);
   a->tables.W_c = reinterpret_cast<const float*>(tb + oWc);
+  memcpy(a->M_host[0], host.data(), (size_t)w * w);
+  memcpy(a->M_host[1], host.data() + oMc, (size_t)nc * nc);
 
   const size_t bv = (size_t)(2 * a->max_batch + 1) * vca::N_ROWS * g.C * sizeof(float);
   OPEN_CUDA(cudaMalloc(&a->d_blockvals, bv), "allocating block values");
@@ -857,6 +860,34 @@ vca_status vca_export_state(vca_analyzer* a, void* buf, size_t* len) {
   return VCA_OK;
 }
 
+vca_status vca_check_dct_matrix(int32_t n, int32_t bit_depth, const int8_t* matrix) {
+  if (!matrix) return fail(VCA_E_ARG, "matrix is NULL");
+  if (bit_depth != 8 && bit_depth != 10 && bit_depth != 12) return fail(VCA_E_ARG, "bit_depth must be 8, 10 or 12");
+  char why[160];
+  if (!vca::check_dct_matrix(n, bit_depth, matrix, why, sizeof why)) return fail(VCA_E_ARG, "DCT matrix rejected: %s", why);
+  return VCA_OK;
+}
+
+vca_status vca_set_dct_matrix(vca_analyzer* a, int32_t n, const int8_t* matrix) {
+  if (!a || !matrix) return fail(VCA_E_ARG, "NULL argument");
+  if (a->batch) return fail(VCA_E_STATE, "the analyzer belongs to a batch");
+  if (a->frames_pushed != 0 || !a->pending.empty())
+    return fail(VCA_E_STATE, "the DCT matrix can only be set before the first push");
+  if (n != a->g.w && n != a->g.nc)
+    return fail(VCA_E_ARG, "matrix size %d is not a transform size of this analyzer (%d, %d)", n, a->g.w, a->g.nc);
+  vca_status s = vca_check_dct_matrix(n, a->g.B, matrix);
+  if (s != VCA_OK) return s;
+  const size_t oMc = round_up((size_t)a->g.w * a->g.w, 256);  // the table layout of vca_open
+  uint8_t* tb = static_cast<uint8_t*>(a->d_tables);
+  for (int i = 0; i < 2; ++i) {
+    if (n != (i == 0 ? a->g.w : a->g.nc)) continue;
+    VCA_CUDA(cudaMemcpy(tb + (i == 0 ? 0 : oMc), matrix, (size_t)n * n, cudaMemcpyHostToDevice),
+             "uploading the DCT matrix");
+    memcpy(a->M_host[i], matrix, (size_t)n * n);
+  }
+  return VCA_OK;
+}
+
 vca_status vca_import_state(vca_analyzer* a, const void* buf, size_t len) {
   if (!a || !buf) return fail(VCA_E_ARG, "NULL argument");
   if (len < sizeof(StateHeader)) return fail(VCA_E_ARG, "state buffer too small");
@@ -947,7 +978,13 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
   b->nc = members[0]->g.nc;
   b->low_pass = members[0]->g.low_pass;
   b->tc = n <= vca::tc_batch_max_members();
-  for (int i = 0; i < n; ++i) b->tc = b->tc && members[i]->kernel == VCA_KERNEL_TC;
+  for (int i = 0; i < n; ++i) {
+    const vca_analyzer* a = members[i];
+    b->tc = b->tc && a->kernel == VCA_KERNEL_TC;
+    // one launch reads one pair of matrices: the members must share them
+    b->tc = b->tc && memcmp(a->M_host[0], members[0]->M_host[0], (size_t)a->g.w * a->g.w) == 0 &&
+            memcmp(a->M_host[1], members[0]->M_host[1], (size_t)a->g.nc * a->g.nc) == 0;
+  }
   bool has_bps[3] = {false, false, false};
   for (int i = 0; i < n; ++i) has_bps[members[i]->g.bps] = true;
   b->tc_groups = has_bps[1] && has_bps[2] ? 2 : 1;

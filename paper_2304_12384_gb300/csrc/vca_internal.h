@@ -80,6 +80,11 @@ void make_dct_matrix(int N, int8_t* out);
 void make_energy_weights(int N, float* out);
 // Stage shifts s1 = log2 N + B - 9, s2 = log2 N + 6.
 void transform_shifts(int N, int B, int* s1, int* s2);
+// True if m (N x N, row-major) can replace the round-cosine matrix for B-bit samples: N in
+// {4, 8, 16, 32}, m[0][0] = 64, the even/odd DCT symmetry at every level (what the butterfly
+// form and the tensor-core bias cancellation rely on), and T within 16 bits for B <= 10.  Else
+// false with a one-line reason in why.
+bool check_dct_matrix(int N, int B, const int8_t* m, char* why, size_t why_len);
 
 // CUDA-core analysis of n frames: writes block values (and, when the dump pointers are
 // non-null, the quantised coefficients of frame 0).  Returns the launch status and adds

@@ -116,6 +116,8 @@ _PROTOS = {
     "vca_batch_sync": (_P,),
     "vca_batch_launch_count": (_P, ctypes.POINTER(_I64)),
     "vca_batch_kernel": (_P, ctypes.POINTER(_I32)),
+    "vca_set_dct_matrix": (_P, _I32, _P),
+    "vca_check_dct_matrix": (_I32, _I32, _P),
     "vca_batch_destroy": (_P,),
     "vca_server_create": (ctypes.c_size_t, ctypes.POINTER(_P)),
     "vca_server_add_channel": (_P, ctypes.POINTER(VcaConfig), _I32, ctypes.POINTER(_I32)),
@@ -275,6 +277,27 @@ def vca_import_state(a, state: bytes):
     return _check(lib().vca_import_state(a, buf, len(state)))
 
 
+def _int8_matrix(n, matrix):
+    import numpy as np
+
+    m = np.ascontiguousarray(np.asarray(matrix), dtype=np.int8)
+    if m.shape != (n, n):
+        raise ValueError(f"matrix must be {n} x {n}")
+    return m
+
+
+def vca_set_dct_matrix(a, n: int, matrix) -> int:
+    """Drop-in n x n integer DCT matrix (int8 values, row k = basis function k)."""
+    m = _int8_matrix(n, matrix)
+    return _check(lib().vca_set_dct_matrix(_P(a), n, m.ctypes.data))
+
+
+def vca_check_dct_matrix(n: int, bit_depth: int, matrix) -> int:
+    """VCA_OK if the matrix meets the drop-in requirements, else raises VcaError with the reason."""
+    m = _int8_matrix(n, matrix)
+    return _check(lib().vca_check_dct_matrix(n, bit_depth, m.ctypes.data))
+
+
 def vca_frames_pushed(a) -> int:
     n = _I64()
     _check(lib().vca_frames_pushed(a, ctypes.byref(n)))
@@ -326,6 +349,14 @@ class Analyzer:
         self.handle = vca_open(self.cfg, stream)
         self.blocks_x, self.blocks_y = vca_block_count(self.cfg)
         self.C = self.blocks_x * self.blocks_y
+        self.dct_matrices = {}  # transform size -> drop-in matrix set through set_dct_matrix
+
+    def set_dct_matrix(self, n, matrix):
+        """Replace the n x n integer DCT matrix (before the first push)."""
+        import numpy as np
+
+        vca_set_dct_matrix(self.handle, n, matrix)
+        self.dct_matrices[n] = np.asarray(matrix, dtype=np.int64).copy()
 
     def close(self):
         if self.handle:

@@ -171,3 +171,37 @@ def test_batch_444_and_block_8(vca):
             assert [m.frame_features(t) for t in range(3)] == [s_.frame_features(t) for t in range(3)]
             m.close()
             s_.close()
+
+
+def test_batch_with_drop_in_matrices(vca):
+    # Members sharing a drop-in matrix stay on the tensor-core kernel; members whose matrices differ
+    # share a batch on the CUDA-core kernel.  Either way each channel matches its single analyzer.
+    from vca_testutil import structured_dct_matrix
+
+    m32 = structured_dct_matrix(32, (((32, 0, 0), -1), ((16, 3, 4), 1)))
+    chans = [(640, 352, 8), (320, 180, 10)]
+    frames = [frames_list(SequenceSpec(w, h, 3, 90 + i, bit_depth=bd, sigma=4.0)) for i, (w, h, bd) in enumerate(chans)]
+    dev = [to_device(f) for f in frames]
+    for same in (True, False):
+        members = [vca.Analyzer(w, h, bd, 32, True, max_batch=3) for (w, h, bd) in chans]
+        singles = [vca.Analyzer(w, h, bd, 32, True, max_batch=3) for (w, h, bd) in chans]
+        for i, (a, s_) in enumerate(zip(members, singles)):
+            if same or i == 0:
+                a.set_dct_matrix(32, m32)
+                s_.set_dct_matrix(32, m32)
+        batch = vca.Batch(members)
+        assert batch.kernel == (vca.VCA_KERNEL_TC if same else vca.VCA_KERNEL_PLAIN)
+        for t in range(3):
+            batch.tick([(y[t], u[t], v[t]) for (y, u, v) in dev])
+            for s_, (y, u, v) in zip(singles, dev):
+                s_.push(y[t], u[t], v[t])
+        batch.close()
+        for i, (m, s_) in enumerate(zip(members, singles)):
+            got = [m.frame_features(t) for t in range(3)]
+            if same:  # same kernel as the single analyzer: identical bits
+                assert got == [s_.frame_features(t) for t in range(3)]
+            per, _ = oracle_sequence(frames[i], oracle_config(m))
+            for t, e in enumerate(per):
+                assert_features_close(got[t], e, where=f"channel {i} frame {t} (same={same})")
+            m.close()
+            s_.close()

@@ -40,13 +40,15 @@ def open_analyzer(vca, kernel, **kw):
 
 
 def run_and_compare(vca, kernel, frames, *, width, height, bit_depth=8, block_size=32, low_pass=False, pad_mode=0,
-                    batch=None, dump_frames=(0,), block_frames=None, chroma_format=0):
+                    batch=None, dump_frames=(0,), block_frames=None, chroma_format=0, matrices=None):
     import torch
 
     an = open_analyzer(vca, kernel, width=width, height=height, bit_depth=bit_depth, block_size=block_size,
                        low_pass=low_pass, pad_mode=pad_mode, max_batch=max(len(frames), 1),
                        chroma_format=chroma_format)
     try:
+        for n, m in (matrices or {}).items():
+            an.set_dct_matrix(n, m)
         y, u, v = to_device(frames)
         assert an.kernel == KERNELS[kernel]
         an.push(y, u, v)
@@ -294,3 +296,48 @@ def test_variant_rules(vca):
     with pytest.raises(vca.VcaError) as ei:
         vca.Analyzer(640, 352, 8, 32, chroma_format=vca.VCA_CHROMA_422)
     assert ei.value.status == vca.VCA_E_UNSUPPORTED
+
+
+# ---- drop-in DCT matrices (an encoder's own integer table in place of the round-cosine one) ----
+
+def _drop_in_matrices():
+    from vca_testutil import structured_dct_matrix
+    return {32: structured_dct_matrix(32, (((32, 0, 0), -1), ((32, 7, 9), 2), ((16, 3, 4), 1), ((8, 1, 0), -1))),
+            16: structured_dct_matrix(16, (((16, 0, 0), -1), ((16, 5, 3), 1), ((8, 2, 1), -2), ((4, 0, 1), 1)))}
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+@pytest.mark.parametrize("low_pass", [True, False])
+@pytest.mark.parametrize("bit_depth", [8, 10])
+def test_drop_in_matrix(vca, kernel, low_pass, bit_depth):
+    mats = _drop_in_matrices()
+    for n, m in mats.items():
+        assert vca.vca_check_dct_matrix(n, bit_depth, m) == 0
+    frames = frames_list(SequenceSpec(200, 120, 4, 51, bit_depth=bit_depth, sigma=6.0, cuts=(2,)))
+    run_and_compare(vca, kernel, frames, width=200, height=120, bit_depth=bit_depth, low_pass=low_pass,
+                    dump_frames=(0, 3), matrices=mats)
+
+
+def test_drop_in_matrix_rules(vca):
+    import numpy as np
+
+    mats = _drop_in_matrices()
+    frames = to_device(frames_list(SequenceSpec(200, 120, 2, 52)))
+    an = vca.Analyzer(200, 120, 8, 32, True, max_batch=2)
+    try:
+        with pytest.raises(vca.VcaError) as ei:  # not a transform size of this analyzer
+            an.set_dct_matrix(8, np.full((8, 8), 64))
+        assert ei.value.status == vca.VCA_E_ARG
+        bad = mats[32].copy()
+        bad[5, 0] += 1
+        with pytest.raises(vca.VcaError) as ei:
+            an.set_dct_matrix(32, bad)
+        assert ei.value.status == vca.VCA_E_ARG and "symmetry" in str(ei.value)
+        an.set_dct_matrix(32, mats[32])
+        y, u, v = frames
+        an.push(y[0:1], u[0:1], v[0:1])
+        with pytest.raises(vca.VcaError) as ei:  # after the first push
+            an.set_dct_matrix(16, mats[16])
+        assert ei.value.status == vca.VCA_E_STATE
+    finally:
+        an.close()

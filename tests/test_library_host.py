@@ -90,3 +90,66 @@ def test_null_arguments_are_rejected(libvca):
     assert L.vca_push_frames(None, None, None, None, 0, 0, 0, 0, 1, 1) == -1
     assert L.vca_read_frame_features(None, 0, 1, None) == -1
     assert L.vca_close(None) == 0
+
+
+# ---- drop-in DCT matrices: the library's structural check, pinned by what the oracle computes ----
+
+def _matrix_cases():
+    import numpy as np
+
+    from oracle import int_dct_matrix
+    from vca_testutil import structured_dct_matrix
+
+    good = []
+    for n in (4, 8, 16, 32):
+        good.append(("round-cosine", n, int_dct_matrix(n)))
+        good.append(("structured", n, structured_dct_matrix(n, (((n, 0, 0), -1), ((n // 2, 0, 0), -1)))))
+    bad = []
+    m = int_dct_matrix(8)
+    m[3, 7] += 1
+    bad.append(("odd row not odd", 8, m, "symmetry"))
+    m = int_dct_matrix(16)
+    m[2, 0] += 1  # even row of the top level, and odd row of level 8: both mirrors broken
+    bad.append(("even row not even", 16, m, "symmetry"))
+    m = int_dct_matrix(32)
+    m[0, :] = 63
+    bad.append(("row 0 not 64", 32, m, "not 64"))
+    m = structured_dct_matrix(32)
+    m[1::2, :16] = np.sign(m[1::2, :16]) * 127  # legal structure, but T leaves 16 bits
+    m[1::2, 16:] = -m[1::2, 15::-1]
+    bad.append(("T beyond 16 bits", 32, m, "limit"))
+    return good, bad
+
+
+def test_check_dct_matrix_accepts_structured_matrices(libvca):
+    import numpy as np
+
+    from oracle import int_dct2, int_dct2_butterfly
+    good, _ = _matrix_cases()
+    rng = np.random.default_rng(11)
+    for name, n, m in good:
+        for bd in (8, 10, 12):
+            assert libvca.vca_check_dct_matrix(n, bd, m) == 0, (name, n, bd)
+        # what acceptance promises: the butterfly and matrix forms agree
+        x = rng.integers(0, 256, size=(8, n, n))
+        assert np.array_equal(int_dct2_butterfly(x, 8, m), int_dct2(x, 8, False, m)), (name, n)
+
+
+def test_check_dct_matrix_rejects_with_reasons(libvca):
+    import numpy as np
+
+    from oracle import int_dct2, int_dct2_butterfly
+    _, bad = _matrix_cases()
+    rng = np.random.default_rng(12)
+    for name, n, m, reason in bad:
+        with pytest.raises(libvca.VcaError) as ei:
+            libvca.vca_check_dct_matrix(n, 8, m)
+        assert ei.value.status == -1 and reason in str(ei.value), (name, str(ei.value))
+        if reason == "symmetry":  # and the forms do disagree on some block
+            x = rng.integers(0, 256, size=(16, n, n))
+            assert not np.array_equal(int_dct2_butterfly(x, 8, m), int_dct2(x, 8, False, m)), name
+    # the T bound binds only up to 10 bits (12-bit samples run on 32-bit integers)
+    assert libvca.vca_check_dct_matrix(32, 12, bad[-1][2]) == 0
+    m = np.full((6, 6), 64)
+    with pytest.raises(libvca.VcaError):
+        libvca.vca_check_dct_matrix(6, 8, m)

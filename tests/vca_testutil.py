@@ -15,7 +15,7 @@ Tolerance (per feature, FP32 block arithmetic against the FP64 oracle):
 import numpy as np
 
 from oracle import (Config, analyze_sequence, block_grid, downsample_plane, frame_block_values, int_dct2,
-                    plane_blocks, sequence_features)
+                    int_dct_matrix, plane_blocks, sequence_features)
 from synth import pack_planes
 
 FEATURES = ("E_Y", "h", "L_Y", "E_U", "E_V", "L_U", "L_V")
@@ -53,9 +53,42 @@ def to_host_pinned(frames, pitch_align=64):
 
 def oracle_config(an) -> Config:
     c = an.cfg
+    mats = tuple((n, tuple(tuple(int(v) for v in row) for row in m)) for n, m in sorted(an.dct_matrices.items()))
     return Config(c.width, c.height, c.bit_depth, c.block_size, c.low_pass == 1,
                   "skip" if c.pad_mode == 1 else "replicate", downsample=c.low_pass == 2,
-                  chroma_format="444" if c.chroma_format == 1 else "420")
+                  chroma_format="444" if c.chroma_format == 1 else "420", dct_matrices=mats)
+
+
+def structured_dct_matrix(N, changes=()):
+    """An N x N integer matrix with the structure of the DCT, built from its free entries.
+
+    At each level L = N, N/2, ..., 2 the free entries are the odd rows of the level's matrix on
+    its first L/2 columns; the other half of an odd row is its negated mirror image, the even rows
+    are the level L/2 matrix and its mirror image, and level 1 is [[64]].  The free entries start
+    from the round-cosine matrix's; `changes` adds ((L, j, n), delta) to odd row j (row 2j+1 of
+    level L) at column n."""
+    M0 = int_dct_matrix(N)
+    free = {}
+    L = N
+    while L >= 2:
+        free[L] = M0[::N // L, :L][1::2, :L // 2].copy()
+        L //= 2
+    for (L, j, n), d in changes:
+        free[L][j, n] += d
+
+    def build(L):
+        if L == 1:
+            return np.array([[64]], dtype=np.int64)
+        h = L // 2
+        E = build(h)
+        M = np.zeros((L, L), dtype=np.int64)
+        M[0::2, :h] = E
+        M[0::2, h:] = E[:, ::-1]
+        M[1::2, :h] = free[L]
+        M[1::2, h:] = -free[L][:, ::-1]
+        return M
+
+    return build(N)
 
 
 def oracle_coefficients(frame, cfg: Config):
@@ -65,9 +98,9 @@ def oracle_coefficients(frame, cfg: Config):
         y, u, v = downsample_plane(y), downsample_plane(u), downsample_plane(v)
     ny, nc = cfg.transform_sizes()
     return {
-        "Y": int_dct2(plane_blocks(y, ny, nbx, nby), cfg.bit_depth, cfg.low_pass),
-        "U": int_dct2(plane_blocks(u, nc, nbx, nby), cfg.bit_depth, cfg.low_pass),
-        "V": int_dct2(plane_blocks(v, nc, nbx, nby), cfg.bit_depth, cfg.low_pass),
+        "Y": int_dct2(plane_blocks(y, ny, nbx, nby), cfg.bit_depth, cfg.low_pass, cfg.matrix(ny)),
+        "U": int_dct2(plane_blocks(u, nc, nbx, nby), cfg.bit_depth, cfg.low_pass, cfg.matrix(nc)),
+        "V": int_dct2(plane_blocks(v, nc, nbx, nby), cfg.bit_depth, cfg.low_pass, cfg.matrix(nc)),
     }
 
 
