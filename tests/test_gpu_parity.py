@@ -158,12 +158,15 @@ def test_frame_by_frame_equals_batch_and_is_deterministic(vca, kernel):
 
 
 @pytest.mark.parametrize("kernel", list(KERNELS))
-def test_host_frames_equal_device_frames(vca, kernel):
-    frames = frames_list(tiny_spec(6))[:6]
+@pytest.mark.parametrize("size", [(640, 352), (200, 120)])  # rows and frames back to back; padded rows
+def test_host_frames_equal_device_frames(vca, kernel, size):
+    W, H = size
+    frames = frames_list(tiny_spec(6))[:6] if size == (640, 352) else frames_list(SequenceSpec(W, H, 6, 61))
     y, u, v = to_device(frames)
     hy, hu, hv = to_host_pinned(frames)
-    a = open_analyzer(vca, kernel, width=640, height=352, max_batch=6)
-    b = open_analyzer(vca, kernel, width=640, height=352, max_batch=6)
+    assert (hy.stride(-2) == W) == (size == (640, 352))
+    a = open_analyzer(vca, kernel, width=W, height=H, max_batch=6)
+    b = open_analyzer(vca, kernel, width=W, height=H, max_batch=6)
     try:
         a.push(y, u, v)
         b.push(hy, hu, hv)
@@ -172,6 +175,30 @@ def test_host_frames_equal_device_frames(vca, kernel):
         # pageable (non-pinned) host memory and a single-frame push
         b.push(hy[0].clone(), hu[0].clone(), hv[0].clone())
         assert b.frame_features(6)["h"] > 0
+    finally:
+        a.close()
+        b.close()
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+def test_large_host_pushes_equal_device_pushes(vca, kernel):
+    # 40 dense host frames (one copy per plane), then pushes of 6 and 37 frames on the same
+    # staging buffer.
+    frames = frames_list(SequenceSpec(640, 352, 40, 62, sigma=5.0, cuts=(17,), motion=3))
+    y, u, v = to_device(frames)
+    hy, hu, hv = to_host_pinned(frames)
+    a = open_analyzer(vca, kernel, width=640, height=352, max_batch=40)
+    b = open_analyzer(vca, kernel, width=640, height=352, max_batch=40)
+    try:
+        for sl in (slice(0, 40), slice(0, 6), slice(3, 40)):
+            a.push(y[sl], u[sl], v[sl])
+            b.push(hy[sl], hu[sl], hv[sl])
+        n = 40 + 6 + 37
+        assert [a.frame_features(t) for t in range(n)] == [b.frame_features(t) for t in range(n)]
+        cfg = oracle_config(a)
+        per, _ = oracle_sequence(frames, cfg)
+        for t in (0, 16, 17, 39):
+            assert_features_close(b.frame_features(t), per[t], where=f"frame {t}")
     finally:
         a.close()
         b.close()
