@@ -3,7 +3,8 @@
 //
 // Persistent kernel, one CTA of 28 warps per SM, specialised by warpgroup:
 //   warpgroup 0   warp 0: TMA producer (one 128x128 luma + two 64x64 chroma tiles per work item
-//                 into a 5-stage ring, 128-byte / 64-byte swizzled); warp 1: TMEM owner and
+//                 into a 5-stage ring, 128-byte / 64-byte swizzled; 10-bit samples as 16-bit
+//                 words: two 64-sample luma boxes, 3 stages); warp 1: TMEM owner and
 //                 stage-1 MMA issuer; warp 2: stage-2 MMA issuer (tcgen05.mma kind::f16, FP32
 //                 accumulate), so neither stage waits on the other's epilogue;
 //   warpgroups 1, 6  convert (luma jobs, chroma jobs): raw samples -> stage-1 A operand in TMEM;
@@ -17,8 +18,8 @@
 //
 // A "job" is 128 stage-2 rows: 8 (low-pass) or 4 luma 32x32 blocks, or 16 / 8 chroma 16x16
 // blocks.  Per job:
-//   convert   raw u8 row -> fp16 (1024 + x, one PRMT per two samples) written to TMEM as the
-//             A operand;
+//   convert   raw row -> fp16 (1024 + x: one PRMT per two 8-bit samples, one AND-OR per two
+//             10-bit samples) written to TMEM as the A operand;
 //   stage 1   D1 = c + X M^T (A from TMEM, M from shared memory), exact integers in FP32; the
 //             presets c_k (the rounding offset 2^(s1-1), minus the 1024 * 64 * N encoding bias
 //             on the DC row) enter as one more MMA from constant shared-memory operands;
@@ -27,12 +28,16 @@
 //             fp16 pairs (1024 + U_lo8, 1024 + U_hi8); stored MN-major (128-byte swizzle)
 //             as the stage-2 A operand -- the row/column transpose is the layout;
 //   stage 2   S_hi, S_lo = M T_hi, M T_lo (A MN-major from shared memory), the accumulators
-//             pre-set to the magic constants of epilogue 2 by one more MMA each;
+//             pre-set by epilogue 1 to the magic constants of epilogue 2;
 //   epilogue2 Z = floor((256 S_hi + S_lo + 2^(s2-1)) / 2^s2) by two round-down FMAs, then
 //             H_v = sum_u w(u,v) |Z| in increasing u and an xor tree over v.
 // Every partial sum is an integer below 2^24 in magnitude (or in [2^23, 2^24) for the
 // pre-offset accumulators), so the FP32 tensor-core accumulation is exact and Z is
 // bit-identical to the integer definition; H uses the same FP32 order as the CUDA-core form.
+//
+// A launch covers one analyzer's frames (its geometry in the kernel parameters) or, for a batched
+// tick, one frame of each of up to 64 analyzers of one sample size (a member table and tensor
+// maps in device memory, copied to shared memory / fenced by each CTA).
 //
 // Every wait is bounded (about two seconds); on timeout the kernel raises a flag in *err,
 // stops, waits for its own copies and MMAs, frees TMEM and returns.
@@ -130,8 +135,7 @@ __host__ __device__ constexpr int b_a2_free(int s) { return 2 * kMaxStages + 4 *
 __host__ __device__ constexpr int b_drain(int i) { return 2 * kMaxStages + 4 * kSlots + 2 * kA2Slots + i; }
 static_assert(b_drain(1) < kBars, "barrier area");
 
-constexpr int kLumaConvertGroups = 1;  // warpgroups converting luma jobs (1 or 2)
-constexpr int kThreads = 896 + 128 * (kLumaConvertGroups - 1);
+constexpr int kThreads = 896;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint64_t kWaitNs = 2000000000ull;
 
@@ -539,19 +543,12 @@ __device__ __forceinline__ void plane_jobs(int& r0, int& r1) {
 // Convert: raw samples of the tile -> stage-1 A operand in TMEM (and the D1 presets).
 template <int Nb, bool LP, int BPS, class MS>
 __device__ void convert_loop(const MS& ms, const Ctl& ctl, uint8_t* sm, uint32_t tq, int n_items, int item0,
-                             int step, int q, int lane, int part) {
+                             int step, int q, int lane) {
   using SL = SmemLay<BPS>;
   constexpr int JPT = Jobs<LP>::PER_TILE;
   constexpr int T = 4 * Nb;  // tile edge of this plane in samples
   int r0, r1;
   plane_jobs<Nb, LP>(r0, r1);
-  if (Nb == 32 && kLumaConvertGroups == 2) {  // part 0 takes the first half of the tile's luma jobs
-    const int half = (r1 - r0) / 2;
-    if (part == 0)
-      r1 = r0 + half;
-    else
-      r0 += half;
-  }
   const int per_tile = r1 - r0;
   TileInfo ti{};
   int h_rem = 0, w_rem = 0;
@@ -762,8 +759,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
   }
   if (tid == 0) {
     for (int i = 0; i < kBars; ++i) mbar_init(&bars[i], 1);
-    for (int i = 0; i < SL::kStages; ++i)  // every convert warp arrives once per tile
-      mbar_init(&bars[b_raw_empty(i)], 4 * (kLumaConvertGroups + 1));
+    for (int i = 0; i < SL::kStages; ++i) mbar_init(&bars[b_raw_empty(i)], 8);  // both convert warpgroups
     for (int i = 0; i < kSlots; ++i) mbar_init(&bars[b_slot_free(i)], 4);
     for (int i = 0; i < kSlots; ++i) mbar_init(&bars[b_a1_full(i)], 4);
     for (int i = 0; i < kA2Slots; ++i) mbar_init(&bars[b_a2_full(i)], 4);
@@ -897,10 +893,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
         wait_bar(ctl, b_drain(1), 0, 2, true);
       }
     }
-  } else if (role == 1 || (kLumaConvertGroups == 2 && role == 7)) {
-    convert_loop<32, LP, BPS>(ms, ctl, sm, tmem + lanebase, n_items, item0, step, q, lane, role == 7);
+  } else if (role == 1) {
+    convert_loop<32, LP, BPS>(ms, ctl, sm, tmem + lanebase, n_items, item0, step, q, lane);
   } else if (role == 6) {
-    convert_loop<16, LP, BPS>(ms, ctl, sm, tmem + lanebase, n_items, item0, step, q, lane, 0);
+    convert_loop<16, LP, BPS>(ms, ctl, sm, tmem + lanebase, n_items, item0, step, q, lane);
   } else if (role == 2) {
     epi1_loop<32, LP, BPS>(ms, ctl, sbase, tmem + lanebase, n_items, item0, step, q, lane);
   } else if (role == 3) {
