@@ -157,14 +157,15 @@ struct vca_batch {
   // 10-bit in 16-bit words); two groups run as two launches on forked streams of the graph.
   int tc_groups = 1;
   int tc_gbps[2] = {1, 2};
-  size_t tc_desc_bytes = 0;        // one group's descriptor block
+  std::vector<uint8_t> tc_params[2];  // per group: the launch's parameter block (member table, tensor maps)
+  cudaGraphNode_t tc_node[2][2] = {};  // per graph and group: the tensor-core launch's node
   cudaStream_t stream = nullptr;
   cudaStream_t stream2 = nullptr;  // the second group's branch while capturing
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   vca::BatchCta* d_map = nullptr;
   int n_cta = 0;
   size_t ma_bytes = 0, desc_bytes = 0;
-  uint8_t* d_desc = nullptr;       // analysis arguments (tensor-core descriptor block or BatchMemberArgs[n]) | ReduceArgs[n]
+  uint8_t* d_desc = nullptr;       // BatchMemberArgs[n] (CUDA-core batches) | ReduceArgs[n]
   uint8_t* h_desc[2] = {nullptr, nullptr};
   int* d_err = nullptr;            // the tensor-core kernel's wait-timeout flag
   int* h_err = nullptr;            // pinned, one per graph
@@ -539,13 +540,10 @@ cudaError_t build_tick_graph(vca_batch* b, int k) {
     if (e1 == cudaSuccess && b->tc_groups == 2) {  // fork: the second group on its own branch
       e1 = cudaEventRecord(b->fork_ev, b->stream);
       if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(b->stream2, b->fork_ev, 0);
-      if (e1 == cudaSuccess)
-        e1 = vca::launch_tc_batch(b->d_desc + b->tc_desc_bytes, b->tc_gbps[1], b->low_pass, b->m[0]->tables,
-                                  b->d_err, b->stream2);
+      if (e1 == cudaSuccess) e1 = vca::launch_tc_batch(b->tc_params[1].data(), b->tc_gbps[1], b->low_pass, b->stream2);
       if (e1 == cudaSuccess) e1 = cudaEventRecord(b->join_ev, b->stream2);
     }
-    if (e1 == cudaSuccess)
-      e1 = vca::launch_tc_batch(b->d_desc, b->tc_gbps[0], b->low_pass, b->m[0]->tables, b->d_err, b->stream);
+    if (e1 == cudaSuccess) e1 = vca::launch_tc_batch(b->tc_params[0].data(), b->tc_gbps[0], b->low_pass, b->stream);
     if (e1 == cudaSuccess && b->tc_groups == 2) e1 = cudaStreamWaitEvent(b->stream, b->join_ev, 0);
   } else if (e1 == cudaSuccess) {
     e1 = vca::launch_batch_plain(b->d_map, b->n_cta, reinterpret_cast<const vca::BatchMemberArgs*>(b->d_desc), b->w,
@@ -562,6 +560,24 @@ cudaError_t build_tick_graph(vca_batch* b, int k) {
   e = cudaStreamEndCapture(b->stream, &b->graph[k]);
   if (e1 != cudaSuccess) return e1;
   if (e != cudaSuccess) return e;
+  if (b->tc) {  // the tensor-core launches, whose parameters each tick replaces
+    size_t count = 0;
+    e = cudaGraphGetNodes(b->graph[k], nullptr, &count);
+    std::vector<cudaGraphNode_t> nodes(count);
+    if (e == cudaSuccess && count) e = cudaGraphGetNodes(b->graph[k], nodes.data(), &count);
+    for (size_t i = 0; e == cudaSuccess && i < count; ++i) {
+      cudaGraphNodeType type;
+      e = cudaGraphNodeGetType(nodes[i], &type);
+      if (e != cudaSuccess || type != cudaGraphNodeTypeKernel) continue;
+      cudaKernelNodeParams kp{};
+      e = cudaGraphKernelNodeGetParams(nodes[i], &kp);
+      for (int gi = 0; e == cudaSuccess && gi < b->tc_groups; ++gi)
+        if (kp.func == vca::tc_batch_kernel(b->tc_gbps[gi], b->low_pass)) b->tc_node[k][gi] = nodes[i];
+    }
+    if (e != cudaSuccess) return e;
+    for (int gi = 0; gi < b->tc_groups; ++gi)
+      if (!b->tc_node[k][gi]) return cudaErrorGraphExecUpdateFailure;
+  }
   return cudaGraphInstantiate(&b->exec[k], b->graph[k], 0);
 }
 
@@ -1058,8 +1074,8 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
     return fail(VCA_E_ARG, "batch too large");
   }
   b->n_cta = (int)map.size();
-  b->tc_desc_bytes = round_up(vca::tc_batch_desc_bytes(), 256);
-  b->ma_bytes = b->tc ? b->tc_groups * b->tc_desc_bytes : round_up((size_t)n * sizeof(vca::BatchMemberArgs), 256);
+  for (int gi = 0; b->tc && gi < b->tc_groups; ++gi) b->tc_params[gi].assign(vca::tc_batch_params_bytes(), 0);
+  b->ma_bytes = b->tc ? 0 : round_up((size_t)n * sizeof(vca::BatchMemberArgs), 256);
   b->desc_bytes = b->ma_bytes + (size_t)n * sizeof(vca::ReduceArgs);
   BATCH_CUDA(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking), "creating the batch stream");
   if (!b->tc) {
@@ -1146,9 +1162,17 @@ vca_status vca_batch_tick(vca_batch* b, const vca_frame_ref* frames) {
     tick.members.push_back({i, a->frames_pushed, a->has_prev != 0});
   }
   for (int gi = 0; b->tc && gi < b->tc_groups; ++gi) {
-    const cudaError_t e = vca::tc_batch_fill(b->h_desc[k] + gi * b->tc_desc_bytes, b->tc_frames[gi].data(),
-                                             (int)b->tc_frames[gi].size());
+    cudaError_t e = vca::tc_batch_fill(b->tc_params[gi].data(), b->tc_frames[gi].data(), (int)b->tc_frames[gi].size(),
+                                       b->m[0]->tables, b->d_err);
     if (e != cudaSuccess) return cuda_fail(e, "encoding the tensor maps of a batch tick");
+    // The graph's launch takes this tick's parameter block (copied by the call).
+    cudaKernelNodeParams kp{};
+    e = cudaGraphKernelNodeGetParams(b->tc_node[k][gi], &kp);
+    void* args[1] = {b->tc_params[gi].data()};
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(b->exec[k], b->tc_node[k][gi], &kp);
+    if (e != cudaSuccess) return cuda_fail(e, "setting the parameters of a batch tick");
   }
   int prev_dev = -1;
   cudaGetDevice(&prev_dev);

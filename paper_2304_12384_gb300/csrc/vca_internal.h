@@ -100,25 +100,26 @@ cudaError_t launch_tc(const Geometry& g, const FramePlanes& fp, int nframes, con
 bool tc_supported(const Geometry& g);
 
 // Batched tensor-core analysis: one frame of each of up to tc_batch_max_members() analyzers of
-// one sample size in one launch of the persistent kernel.  The launch reads a descriptor block (the member table and
-// each member's tensor maps, tc_batch_desc_bytes() bytes, 128-byte aligned) that the host writes
-// with tc_batch_fill and copies to the device unchanged before the launch.
+// one sample size in one launch of the persistent kernel.  The launch's member table and tensor
+// maps are its kernel parameters (tc_batch_params_bytes(), about 29 KB), which the host fills
+// with tc_batch_fill; a captured launch's parameters are replaced per tick in the graph.
 struct TcBatchFrame {
   const Geometry* g;   // the member's analysis geometry (tc_supported)
   FramePlanes fp;      // its frame (frame strides unused)
   float* blockvals;    // its [6][C] block values
 };
 int tc_batch_max_members();
-size_t tc_batch_desc_bytes();
-// Fills the descriptor block at h (host memory) for n frames; cudaErrorInvalidValue if n is out
-// of range, the frames' sample sizes differ or a tensor map cannot be encoded.
-cudaError_t tc_batch_fill(void* h, const TcBatchFrame* frames, int n);
+size_t tc_batch_params_bytes();
+// Fills the parameter block at params (host memory, tc_batch_params_bytes()) for n frames, the
+// DCT tables t and the device error flag err; cudaErrorInvalidValue if n is out of range, the
+// frames' sample sizes differ or a tensor map cannot be encoded.
+cudaError_t tc_batch_fill(void* params, const TcBatchFrame* frames, int n, const DeviceTables& t, int* err);
 // Sets up the kernel instance for this sample size and low_pass (outside any stream capture).
 cudaError_t tc_batch_prepare(int bps, bool low_pass);
-// Launches the analysis of the descriptor block at d_desc (device).  bps: the members' sample
-// size (1 or 2).
-cudaError_t launch_tc_batch(const void* d_desc, int bps, bool low_pass, const DeviceTables& t, int* err,
-                            cudaStream_t s);
+// Launches the analysis with the parameter block params (host memory; bps 1 or 2).
+cudaError_t launch_tc_batch(const void* params, int bps, bool low_pass, cudaStream_t s);
+// The kernel a batched launch of this sample size and low_pass runs (to find its graph node).
+const void* tc_batch_kernel(int bps, bool low_pass);
 
 // Exact frame reduction: features of n frames (the block sums exact in 128-bit fixed point, each
 // total rounded once to FP64) and the h state update.  `partials` holds reduce_partials_bytes(max

@@ -81,14 +81,8 @@ template <int Nb>
 __host__ __device__ constexpr int s1_of(int bps) {
   return (Nb == 32 ? 5 : 4) + (bps == 1 ? 8 : 10) - 9;
 }
-constexpr int kMemBytes = kMaxMembers * (int)sizeof(TcMember);
 static_assert(sizeof(TcMember) % 8 == 0, "member table entries are copied as words");
 
-// The member table of a batched launch, in device memory.
-struct TcTable {
-  int n_members, total_items, pad[2];
-  TcMember mem[kMaxMembers];
-};
 
 // Shared-memory layout for BPS bytes per sample.  8-bit: a 128x128 luma tile (128-byte rows,
 // 128-byte swizzle) and two 64x64 chroma tiles (64-byte rows and swizzle), 5 stages.  10-bit
@@ -111,8 +105,7 @@ struct SmemLay {
   static constexpr int OFF_BAR = OFF_KC + 1024;
   static constexpr int OFF_MISC = OFF_BAR + kBars * 8;
   static constexpr int kSmemBytes = OFF_MISC + 64 + 1024;  // + slack to align the base to 1024
-  // (the member table is a static shared array of kMemBytes beside this dynamic area)
-  static_assert(kStages <= kMaxStages && OFF_A2 % 1024 == 0 && kSmemBytes + kMemBytes <= 232448, "layout");
+  static_assert(kStages <= kMaxStages && OFF_A2 % 1024 == 0 && kSmemBytes <= 232448, "layout");
 };
 
 // TMEM layout: 8 job slots of 64 columns, each holding the stage-1 operand A1 at [0, 32), the
@@ -144,19 +137,25 @@ constexpr float kT1 = 14974976.0f;  // 2^23 + 0x640000 + 0x8000
 constexpr float kK1 = 12582912.0f;  // 1.5 * 2^23
 constexpr uint32_t kSel6464 = 0x64646464u;
 
-struct TcParams {
-  const TcTable* table;     // batched launch: members in device memory; null: mem0 below
-  const CUtensorMap* maps;  // batched launch: Y, U, V maps of each member
-  int total_items;          // single analyzer
-  TcMember mem0;            // single analyzer
+// Kernel parameters of a launch over up to MAXM members: one analyzer's frames (MAXM = 1) or one
+// frame of each channel of a batched tick (MAXM = kMaxMembers; about 29 KB, within the 32,764
+// bytes a kernel may take).  The member table and the tensor maps live in parameter space, read
+// through the constant cache; a batched tick graph rewrites them per tick.
+template <int MAXM>
+struct TcParamsT {
   int16_t* zdump[3];
   const int8_t* M_y;
   const int8_t* M_c;
   const float* W_y;
   const float* W_c;
   int* err;
-  CUtensorMap map0[3];              // single analyzer: Y, U, V
+  int n_members, total_items;
+  TcMember mem[MAXM];
+  CUtensorMap maps[3 * MAXM];  // Y, U, V of each member
 };
+using TcParams = TcParamsT<1>;
+using TcBatchParams = TcParamsT<kMaxMembers>;
+static_assert(sizeof(TcBatchParams) <= 32764, "kernel parameter space");
 
 template <int Nb, bool LP>
 struct PC {
@@ -417,7 +416,7 @@ __device__ __forceinline__ void epilogue1(uint32_t td1, uint32_t td2, uint32_t a
 }
 
 template <int Nb, bool LP, bool DUMP>
-__device__ __forceinline__ void epilogue2(const TcParams& p, const TcMember& M, uint32_t td2, const JobCtx& jc,
+__device__ __forceinline__ void epilogue2(int16_t* const* zdump, const TcMember& M, uint32_t td2, const JobCtx& jc,
                                           int q, int lane,
                                           const float (&wts)[PC<Nb, LP>::NK], float einv, float c2,
                                           uint64_t* slot_free) {
@@ -433,7 +432,7 @@ __device__ __forceinline__ void epilogue2(const TcParams& p, const TcMember& M, 
   const bool valid = bx < M.nbx && by < M.nby;
   const int64_t k = (int64_t)by * M.nbx + bx;
   int16_t* zd = nullptr;
-  if (DUMP) zd = (valid && jc.f == 0) ? p.zdump[jc.plane] + k * NK * NK : nullptr;
+  if (DUMP) zd = (valid && jc.f == 0) ? zdump[jc.plane] + k * NK * NK : nullptr;
   float H = 0.0f, z00 = 0.0f;
 #pragma unroll
   for (int h0 = 0; h0 < NK; h0 += HALF) {
@@ -632,8 +631,8 @@ __device__ void epi1_loop(const MS& ms, const Ctl& ctl, uint32_t sbase, uint32_t
 }
 
 // Epilogue 2: Z, the block energy H and brightness L, for every job of one plane type.
-template <int Nb, bool LP, bool DUMP, class MS>
-__device__ void epi2_loop(const TcParams& p, const MS& ms, const Ctl& ctl, uint32_t tq, int n_items, int item0,
+template <int Nb, bool LP, bool DUMP, class PP, class MS>
+__device__ void epi2_loop(const PP& p, const MS& ms, const Ctl& ctl, uint32_t tq, int n_items, int item0,
                           int step, int q, int lane) {
   using P = PC<Nb, LP>;
   constexpr int JPT = Jobs<LP>::PER_TILE;
@@ -661,7 +660,7 @@ __device__ void epi2_loop(const TcParams& p, const MS& ms, const Ctl& ctl, uint3
     plane_of<LP>(r, jc.plane, jc.jp);
     if (!wait_bar(ctl, b_d2(slot), (jj / kSlots) & 1, 4, false, true)) return;
     tc_fence_after();
-    epilogue2<Nb, LP, DUMP>(p, ms[m], tq + slot * kSlotCols, jc, q, lane, w, einv, c2,
+    epilogue2<Nb, LP, DUMP>(p.zdump, ms[m], tq + slot * kSlotCols, jc, q, lane, w, einv, c2,
                             &ctl.bars[b_slot_free(slot)]);
     if (++r == r1) {
       r = r0;
@@ -671,7 +670,8 @@ __device__ void epi2_loop(const TcParams& p, const MS& ms, const Ctl& ctl, uint3
 }
 
 template <bool LP, bool DUMP, int BPS, bool BATCH>
-__global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__ TcParams p) {
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_kernel(const __grid_constant__ TcParamsT<BATCH ? kMaxMembers : 1> p) {
   using L = PC<32, LP>;
   using Cc = PC<16, LP>;
   constexpr int JPT = Jobs<LP>::PER_TILE;
@@ -689,8 +689,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
   const int q = warp & 3;      // TMEM lane quarter of this warp
   const int cta = blockIdx.x;
   const int grid = gridDim.x;
-  const int n_mem = BATCH ? p.table->n_members : 1;
-  const int total_items = BATCH ? p.table->total_items : p.total_items;
+  const int total_items = p.total_items;
   // This CTA's items: item0, item0 + step, ...  A single analyzer's CTAs take every grid-th item
   // (neighbouring CTAs read neighbouring tiles); a batched launch gives each CTA one contiguous
   // run, so that a CTA meets few members (and few tensor maps).
@@ -707,20 +706,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
   const int n_jobs = n_items * JPT;
   Ctl ctl{bars, abort_flag, p.err};
 
-  // A batched launch's member table, copied into shared memory as 8-byte words.
-  __shared__ alignas(16) TcMember s_mem[BATCH ? kMaxMembers : 1];
-  if (BATCH) {
-    const uint64_t* src = (const uint64_t*)p.table->mem;
-    uint64_t* dst = (uint64_t*)s_mem;
-    const int words = n_mem * (int)(sizeof(TcMember) / 8);
-    for (int i = tid; i < words; i += kThreads) dst[i] = src[i];
-  }
   using MS = typename MemberView<BATCH>::T;
   MS ms = [&] {
     if constexpr (BATCH)
-      return MemberTable{s_mem, n_mem, 0};
+      return MemberTable{p.mem, p.n_members, 0};
     else
-      return OneMember{p.mem0};
+      return OneMember{p.mem[0]};
   }();
 
   // Constant B operands (the integer DCT matrices as fp16), K-major without swizzle:
@@ -767,9 +758,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
     fence_mbar_init();
   }
   if (warp == 0 && lane == 0 && !BATCH) {
-    prefetch_tensormap(&p.map0[0]);
-    prefetch_tensormap(&p.map0[1]);
-    prefetch_tensormap(&p.map0[2]);
+    prefetch_tensormap(&p.maps[0]);
+    prefetch_tensormap(&p.maps[1]);
+    prefetch_tensormap(&p.maps[2]);
   }
   if (warp == 1) {
     tmem_alloc(tmem_slot, kTmemCols);
@@ -786,19 +777,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_kernel(const __grid_constant__
   if (role == 0) {
     if (warp == 0 && lane == 0) {
       // ---------------- TMA producer: tiles in order into the ring ----------------
-      const CUtensorMap* maps = BATCH ? p.maps : p.map0;
       int issued = 0;
-      int fenced = -1;  // batched launch: the member whose maps were last fenced
       for (int t = 0; t < n_items; ++t) {
         const int stage = t % SL::kStages;
         if (t >= SL::kStages && !wait_bar(ctl, b_raw_empty(stage), ((t / SL::kStages) - 1) & 1, 1, false, true))
           break;
         const TileInfo ti = tile_info(ms, t, item0, step, SL::kStages);
-        const CUtensorMap* mm = maps + 3 * ti.m;
-        if (BATCH && ti.m != fenced) {
-          for (int i = 0; i < 3; ++i) fence_tensormap_acquire(mm + i);
-          fenced = ti.m;
-        }
+        const CUtensorMap* mm = &p.maps[3 * ti.m];
         uint8_t* dst = sm + OFF_RAW + stage * SL::kStageBytes;
         uint64_t* full = &bars[b_raw_full(stage)];
         mbar_arrive_expect_tx(full, SL::kStageBytes);
@@ -964,7 +949,7 @@ cudaError_t prepare_inst() {
 
 // grid 0: only prepare the instance.
 template <bool LP, bool DUMP, int BPS, bool BATCH>
-cudaError_t launch_inst(const TcParams& p, int grid, cudaStream_t s) {
+cudaError_t launch_inst(const TcParamsT<BATCH ? kMaxMembers : 1>& p, int grid, cudaStream_t s) {
   const cudaError_t attr = prepare_inst<LP, DUMP, BPS, BATCH>();
   if (attr != cudaSuccess) return attr;
   if (grid <= 0) return cudaSuccess;
@@ -985,7 +970,7 @@ cudaError_t launch_single(const TcParams& p, int grid, bool low_pass, bool dump,
 }
 
 // A batched launch of members of one sample size (bps 1 or 2).
-cudaError_t launch_batched(const TcParams& p, int grid, bool low_pass, int bps, cudaStream_t s) {
+cudaError_t launch_batched(const TcBatchParams& p, int grid, bool low_pass, int bps, cudaStream_t s) {
   if (bps == 1)
     return low_pass ? launch_inst<true, false, 1, true>(p, grid, s) : launch_inst<false, false, 1, true>(p, grid, s);
   return low_pass ? launch_inst<true, false, 2, true>(p, grid, s) : launch_inst<false, false, 2, true>(p, grid, s);
@@ -1025,53 +1010,53 @@ bool tc_supported(const Geometry& g) {
          g.s1c == s1_of<16>(g.bps) && encode_fn() != nullptr;
 }
 
-// Descriptor block of a batched launch: the member table, then three tensor maps per member.
-constexpr size_t kTcMapsOff = (sizeof(TcTable) + 127) / 128 * 128;
-
 int tc_batch_max_members() { return kMaxMembers; }
 
-size_t tc_batch_desc_bytes() { return kTcMapsOff + (size_t)3 * kMaxMembers * sizeof(CUtensorMap); }
+size_t tc_batch_params_bytes() { return sizeof(TcBatchParams); }
 
-cudaError_t tc_batch_fill(void* h, const TcBatchFrame* frames, int n) {
+cudaError_t tc_batch_fill(void* params, const TcBatchFrame* frames, int n, const DeviceTables& t, int* err) {
   if (n < 0 || n > kMaxMembers) return cudaErrorInvalidValue;
-  TcTable* tab = static_cast<TcTable*>(h);
-  CUtensorMap* maps = reinterpret_cast<CUtensorMap*>(static_cast<uint8_t*>(h) + kTcMapsOff);
-  int items = 0;
-  for (int i = 0; i < n; ++i) {
-    const Geometry& g = *frames[i].g;
-    const FramePlanes& fp = frames[i].fp;
-    if (!tc_supported(g) || g.bps != frames[0].g->bps) return cudaErrorInvalidValue;
-    items += fill_member(tab->mem[i], g, items, 1, frames[i].blockvals);
-    const CUtensorMapSwizzle swc = g.bps == 1 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
-    cudaError_t e = make_map(&maps[3 * i], fp.y, g.W, g.H, fp.pitch_y, 0, 1, g.bps == 1 ? 128 : 64, 128, g.bps,
-                             CU_TENSOR_MAP_SWIZZLE_128B);
-    if (e == cudaSuccess) e = make_map(&maps[3 * i + 1], fp.u, g.cw, g.ch, fp.pitch_uv, 0, 1, 64, 64, g.bps, swc);
-    if (e == cudaSuccess) e = make_map(&maps[3 * i + 2], fp.v, g.cw, g.ch, fp.pitch_uv, 0, 1, 64, 64, g.bps, swc);
-    if (e != cudaSuccess) return e;
-  }
-  tab->n_members = n;
-  tab->total_items = items;
-  return cudaSuccess;
-}
-
-cudaError_t tc_batch_prepare(int bps, bool low_pass) {
-  if (bps != 1 && bps != 2) return cudaErrorInvalidValue;
-  return launch_batched(TcParams{}, 0, low_pass, bps, nullptr);
-}
-
-cudaError_t launch_tc_batch(const void* d_desc, int bps, bool low_pass, const DeviceTables& t, int* err,
-                            cudaStream_t s) {
-  if (bps != 1 && bps != 2) return cudaErrorInvalidValue;
-  TcParams p{};
-  p.table = static_cast<const TcTable*>(d_desc);
-  p.maps = reinterpret_cast<const CUtensorMap*>(static_cast<const uint8_t*>(d_desc) + kTcMapsOff);
+  TcBatchParams& p = *static_cast<TcBatchParams*>(params);
+  p.zdump[0] = p.zdump[1] = p.zdump[2] = nullptr;
   p.M_y = t.M_y;
   p.M_c = t.M_c;
   p.W_y = t.W_y;
   p.W_c = t.W_c;
   p.err = err;
-  // The number of items is known only on the device; CTAs beyond it find no work.
-  return launch_batched(p, sm_count(), low_pass, bps, s);
+  int items = 0;
+  for (int i = 0; i < n; ++i) {
+    const Geometry& g = *frames[i].g;
+    const FramePlanes& fp = frames[i].fp;
+    if (!tc_supported(g) || g.bps != frames[0].g->bps) return cudaErrorInvalidValue;
+    items += fill_member(p.mem[i], g, items, 1, frames[i].blockvals);
+    const CUtensorMapSwizzle swc = g.bps == 1 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
+    cudaError_t e = make_map(&p.maps[3 * i], fp.y, g.W, g.H, fp.pitch_y, 0, 1, g.bps == 1 ? 128 : 64, 128, g.bps,
+                             CU_TENSOR_MAP_SWIZZLE_128B);
+    if (e == cudaSuccess) e = make_map(&p.maps[3 * i + 1], fp.u, g.cw, g.ch, fp.pitch_uv, 0, 1, 64, 64, g.bps, swc);
+    if (e == cudaSuccess) e = make_map(&p.maps[3 * i + 2], fp.v, g.cw, g.ch, fp.pitch_uv, 0, 1, 64, 64, g.bps, swc);
+    if (e != cudaSuccess) return e;
+  }
+  p.n_members = n;
+  p.total_items = items;
+  return cudaSuccess;
+}
+
+cudaError_t tc_batch_prepare(int bps, bool low_pass) {
+  if (bps != 1 && bps != 2) return cudaErrorInvalidValue;
+  static TcBatchParams unused{};
+  return launch_batched(unused, 0, low_pass, bps, nullptr);
+}
+
+cudaError_t launch_tc_batch(const void* params, int bps, bool low_pass, cudaStream_t s) {
+  if (bps != 1 && bps != 2) return cudaErrorInvalidValue;
+  // The number of items is known from the parameters; CTAs beyond it find no work.
+  return launch_batched(*static_cast<const TcBatchParams*>(params), sm_count(), low_pass, bps, s);
+}
+
+const void* tc_batch_kernel(int bps, bool low_pass) {
+  if (bps == 1)
+    return low_pass ? (const void*)tc_kernel<true, false, 1, true> : (const void*)tc_kernel<false, false, 1, true>;
+  return low_pass ? (const void*)tc_kernel<true, false, 2, true> : (const void*)tc_kernel<false, false, 2, true>;
 }
 
 cudaError_t launch_tc(const Geometry& g, const FramePlanes& fp, int nframes, const DeviceTables& t, float* blockvals,
@@ -1089,10 +1074,11 @@ cudaError_t launch_tc(const Geometry& g, const FramePlanes& fp, int nframes, con
   if (e == cudaSuccess) e = make_map(&mv, fp.v, g.cw, g.ch, fp.pitch_uv, fp.fstride_uv, nframes, 64, 64, bps, swc);
   if (e != cudaSuccess) return e;
   TcParams p{};
-  p.total_items = fill_member(p.mem0, g, 0, nframes, blockvals);
-  p.map0[0] = my;
-  p.map0[1] = mu;
-  p.map0[2] = mv;
+  p.n_members = 1;
+  p.total_items = fill_member(p.mem[0], g, 0, nframes, blockvals);
+  p.maps[0] = my;
+  p.maps[1] = mu;
+  p.maps[2] = mv;
   for (int i = 0; i < 3; ++i) p.zdump[i] = zdump ? zdump[i] : nullptr;
   p.M_y = t.M_y;
   p.M_c = t.M_c;
