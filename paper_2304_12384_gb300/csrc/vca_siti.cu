@@ -6,7 +6,8 @@
 //   TI_t = std over all pixels of F_t - F_{t-1}, and 0 without a previous frame;
 // the sequence values are the maxima (TI over t >= 1).  std is the population deviation.
 //
-// One kernel pass per push reads every frame once (the 3x3 neighbourhood comes from L1/L2) and
+// One kernel pass per push reads every frame once (each warp keeps the three rows around its
+// current row in registers and takes the horizontal neighbours from the adjacent lanes) and
 // accumulates four sums per frame: sum Gx^2 + Gy^2 and sum D, sum D^2 exactly in 64-bit
 // integers, and sum sqrt(Gx^2 + Gy^2) (FP32 square root) in fixed point (2^-16 steps) -- integer
 // sums, so the warp-level atomics give the same result in any order.  A finalize kernel turns the
@@ -18,6 +19,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "vca.h"
@@ -25,8 +27,10 @@
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kRows = 4;  // rows per CTA
+constexpr int kWarps = 4;       // warps per CTA
+constexpr int kPx = 4;          // consecutive samples per lane
+constexpr int kStrip = 32 * kPx;  // columns per warp
+constexpr int kRun = 32;        // rows per warp
 constexpr double kMagScale = 65536.0;
 
 struct SitiArgs {
@@ -38,54 +42,136 @@ struct SitiArgs {
   unsigned long long* acc;  // [frame][4]: sum m2, sum mag * 2^16, sum D (two's complement), sum D^2
 };
 
+// Samples x0 .. x0+3 of one row (one 4- or 8-byte load when they all lie inside the row, else one
+// load each, zero past the edge).
 template <typename Pix>
-__device__ __forceinline__ int px(const uint8_t* base, int64_t pitch, int y, int x) {
-  return (int)reinterpret_cast<const Pix*>(base + (int64_t)y * pitch)[x];
+__device__ __forceinline__ void load4(const uint8_t* rowp, int x0, int W, int (&v)[kPx]) {
+  const Pix* row = reinterpret_cast<const Pix*>(rowp);
+  if (x0 + kPx - 1 < W) {
+    if (sizeof(Pix) == 1) {
+      const uint32_t w = *reinterpret_cast<const uint32_t*>(row + x0);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) v[i] = (int)((w >> (8 * i)) & 0xffu);
+    } else {
+      const uint2 w = *reinterpret_cast<const uint2*>(row + x0);
+      v[0] = (int)(w.x & 0xffffu);
+      v[1] = (int)(w.x >> 16);
+      v[2] = (int)(w.y & 0xffffu);
+      v[3] = (int)(w.y >> 16);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < kPx; ++i) v[i] = x0 + i < W ? (int)row[x0 + i] : 0;
+  }
 }
 
+// One row of a lane's window: its 4 samples and the neighbours on either side (from the adjacent
+// lanes, or loaded at the warp's edges): p[0] = x0 - 1, p[1 + i] = x0 + i, p[5] = x0 + 4.
 template <typename Pix>
-__global__ void __launch_bounds__(kThreads) siti_kernel(const SitiArgs a) {
-  const int f = blockIdx.y;
+__device__ __forceinline__ void load_row(const uint8_t* rowp, int x0, int W, int lane, int (&p)[kPx + 2]) {
+  int v[kPx];
+  load4<Pix>(rowp, x0, W, v);
+  const Pix* row = reinterpret_cast<const Pix*>(rowp);
+  int left = __shfl_up_sync(0xffffffffu, v[kPx - 1], 1);
+  int right = __shfl_down_sync(0xffffffffu, v[0], 1);
+  if (lane == 0) left = x0 > 0 && x0 - 1 < W ? (int)row[x0 - 1] : 0;
+  if (lane == 31) right = x0 + kPx < W ? (int)row[x0 + kPx] : 0;
+  p[0] = left;
+#pragma unroll
+  for (int i = 0; i < kPx; ++i) p[i + 1] = v[i];
+  p[kPx + 1] = right;
+}
+
+// Each warp walks down kRun rows of a 128-column strip of one frame with the three rows around
+// the current one in registers: per row one load of its 4 samples per lane, the neighbours by
+// shuffle, and the same for the previous frame.
+template <typename Pix, bool kWide>
+__global__ void __launch_bounds__(kWarps * 32) siti_kernel(const SitiArgs a) {
+  // A lane covers at most kRun * 4 = 128 pixels.  Up to 10-bit samples gx^2 + gy^2 < 2^25, so the
+  // lane's sum fits 32 bits, and a row's 4 magnitudes (each < 2^29 in 2^-16 steps) too; 12-bit
+  // samples take 64 bits for both (gx^2 + gy^2 < 2^30, magnitudes < 2^31).  D^2 < 2^24 and
+  // |D| < 2^12 at every depth, so the lane's sums of those fit 32 bits.
+  using Acc = typename std::conditional<kWide, unsigned long long, unsigned int>::type;
+  const int lane = threadIdx.x & 31;
+  const int f = blockIdx.z;
+  const int y0 = (blockIdx.y * kWarps + (threadIdx.x >> 5)) * kRun;
+  if (y0 >= a.H) return;  // whole warps only
+  const int y1 = min(y0 + kRun, a.H);
+  const int x0 = blockIdx.x * kStrip + lane * kPx;
   const uint8_t* F = a.y + (int64_t)f * a.fstride;
   const uint8_t* P = f > 0 ? a.y + (int64_t)(f - 1) * a.fstride : a.prev;
   const int64_t pp = f > 0 ? a.pitch : a.prev_pitch;
-  unsigned long long m2 = 0, mag = 0, d1 = 0, d2 = 0;
-  const int y0 = blockIdx.x * kRows;
-  for (int yy = y0; yy < min(y0 + kRows, a.H); ++yy) {
-    for (int x = threadIdx.x; x < a.W; x += kThreads) {
-      const int c = px<Pix>(F, a.pitch, yy, x);
-      if (P) {
-        const long long d = (long long)c - px<Pix>(P, pp, yy, x);
-        d1 += (unsigned long long)d;
-        d2 += (unsigned long long)(d * d);
-      }
-      if (yy >= 1 && yy <= a.H - 2 && x >= 1 && x <= a.W - 2) {
-        const int tl = px<Pix>(F, a.pitch, yy - 1, x - 1), tc = px<Pix>(F, a.pitch, yy - 1, x),
-                  tr = px<Pix>(F, a.pitch, yy - 1, x + 1);
-        const int ml = px<Pix>(F, a.pitch, yy, x - 1), mr = px<Pix>(F, a.pitch, yy, x + 1);
-        const int bl = px<Pix>(F, a.pitch, yy + 1, x - 1), bc = px<Pix>(F, a.pitch, yy + 1, x),
-                  br = px<Pix>(F, a.pitch, yy + 1, x + 1);
-        const long long gx = (long long)(tr + 2 * mr + br) - (tl + 2 * ml + bl);
-        const long long gy = (long long)(bl + 2 * bc + br) - (tl + 2 * tc + tr);
-        const unsigned long long s = (unsigned long long)(gx * gx + gy * gy);
-        m2 += s;
-        mag += (unsigned long long)__float2ll_rn(__fsqrt_rn((float)s) * (float)kMagScale);
+  Acc m2 = 0;
+  unsigned long long mag = 0;
+  unsigned int d2 = 0;
+  int d1 = 0;
+  int up[kPx + 2], mid[kPx + 2], dn[kPx + 2];
+#pragma unroll
+  for (int i = 0; i < kPx + 2; ++i) up[i] = 0;
+  if (y0 > 0) load_row<Pix>(F + (int64_t)(y0 - 1) * a.pitch, x0, a.W, lane, up);
+  load_row<Pix>(F + (int64_t)y0 * a.pitch, x0, a.W, lane, mid);
+  for (int r = y0; r < y1; ++r) {
+    if (r + 1 < a.H) {
+      load_row<Pix>(F + (int64_t)(r + 1) * a.pitch, x0, a.W, lane, dn);
+    } else {
+#pragma unroll
+      for (int i = 0; i < kPx + 2; ++i) dn[i] = 0;
+    }
+    if (P) {
+      int pv[kPx];
+      load4<Pix>(P + (int64_t)r * pp, x0, a.W, pv);
+#pragma unroll
+      for (int i = 0; i < kPx; ++i) {
+        if (x0 + i < a.W) {
+          const int d = mid[i + 1] - pv[i];
+          d1 += d;
+          d2 += (unsigned int)(d * d);
+        }
       }
     }
+    if (r >= 1 && r <= a.H - 2) {
+      // Separable Sobel: per column the vertical smoothing up + 2 mid + dn and difference dn - up.
+      int sm[kPx + 2], df[kPx + 2];
+#pragma unroll
+      for (int i = 0; i < kPx + 2; ++i) {
+        sm[i] = up[i] + 2 * mid[i] + dn[i];
+        df[i] = dn[i] - up[i];
+      }
+      Acc row_mag = 0;
+#pragma unroll
+      for (int i = 0; i < kPx; ++i) {
+        const int x = x0 + i;
+        if (x >= 1 && x <= a.W - 2) {
+          const int gx = sm[i + 2] - sm[i];
+          const int gy = df[i] + 2 * df[i + 1] + df[i + 2];
+          const unsigned int sq = (unsigned int)(gx * gx + gy * gy);
+          m2 += sq;
+          // the magnitude in 2^-16 steps, below 2^31: a 32-bit conversion rounds it as a 64-bit one would
+          row_mag += (Acc)(unsigned int)__float2int_rn(__fsqrt_rn((float)sq) * (float)kMagScale);
+        }
+      }
+      mag += row_mag;
+    }
+#pragma unroll
+    for (int i = 0; i < kPx + 2; ++i) {
+      up[i] = mid[i];
+      mid[i] = dn[i];
+    }
   }
+  unsigned long long s0 = m2, s2 = (unsigned long long)(long long)d1, s3 = d2;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    m2 += __shfl_xor_sync(0xffffffffu, m2, o);
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
     mag += __shfl_xor_sync(0xffffffffu, mag, o);
-    d1 += __shfl_xor_sync(0xffffffffu, d1, o);
-    d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    s3 += __shfl_xor_sync(0xffffffffu, s3, o);
   }
-  if ((threadIdx.x & 31) == 0) {
+  if (lane == 0) {
     unsigned long long* acc = a.acc + (int64_t)f * 4;
-    atomicAdd(acc + 0, m2);
+    atomicAdd(acc + 0, s0);
     atomicAdd(acc + 1, mag);
-    atomicAdd(acc + 2, d1);
-    atomicAdd(acc + 3, d2);
+    atomicAdd(acc + 2, s2);
+    atomicAdd(acc + 3, s3);
   }
 }
 
@@ -207,11 +293,15 @@ vca_status vca_siti_push(vca_siti* s, const void* y, int64_t pitch, int64_t fram
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_acc, 0, (size_t)n_frames * 4 * sizeof(unsigned long long), s->stream);
   if (e == cudaSuccess) {
     SitiArgs a{src, p, fs, s->has_prev ? s->d_prev : nullptr, s->prev_pitch, s->W, s->H, s->d_acc};
-    const dim3 grid((unsigned)((s->H + kRows - 1) / kRows), (unsigned)n_frames);
+    const int runs = (s->H + kRun - 1) / kRun;
+    const dim3 grid((unsigned)((s->W + kStrip - 1) / kStrip), (unsigned)((runs + kWarps - 1) / kWarps),
+                    (unsigned)n_frames);
     if (s->bps == 1)
-      siti_kernel<uint8_t><<<grid, kThreads, 0, s->stream>>>(a);
+      siti_kernel<uint8_t, false><<<grid, kWarps * 32, 0, s->stream>>>(a);
+    else if (s->B <= 10)
+      siti_kernel<uint16_t, false><<<grid, kWarps * 32, 0, s->stream>>>(a);
     else
-      siti_kernel<uint16_t><<<grid, kThreads, 0, s->stream>>>(a);
+      siti_kernel<uint16_t, true><<<grid, kWarps * 32, 0, s->stream>>>(a);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {
