@@ -270,6 +270,36 @@ def time_pushes(an, y, u, v, steps, warmup, stream, barrier):
     return ms, kernel_ms, launches
 
 
+def rank_reducers(world, backend="nccl", device=None):
+    """(barrier, max_over_ranks) for world ranks: process-group collectives when world > 1 (the
+    group is created here if needed), no-ops for one rank."""
+    if world <= 1:
+        return (lambda: None), (lambda x: x)
+    import torch
+    import torch.distributed as dist
+
+    if not dist.is_initialized():
+        if backend == "nccl":
+            dist.init_process_group(backend, device_id=device)
+        else:
+            dist.init_process_group(backend)
+    where = device if backend == "nccl" else "cpu"
+
+    def max_over_ranks(x):
+        t = torch.tensor([x], dtype=torch.float64, device=where)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    return dist.barrier, max_over_ranks
+
+
+def whole_job_rate(ms_local, steps, frames_per_step, world, max_over_ranks):
+    """Frames/s of the whole job: every rank's frames over the slowest rank's time (ms), and the
+    milliseconds per step of that rank."""
+    ms_max = max_over_ranks(ms_local)
+    return steps * frames_per_step * world / (ms_max / 1000.0), ms_max / steps
+
+
 def run_vca(args):
     import torch
 
@@ -279,23 +309,7 @@ def run_vca(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=device)
-
-        def barrier():
-            dist.barrier()
-
-        def max_over_ranks(x):
-            t = torch.tensor([x], dtype=torch.float64, device=device)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            return float(t.item())
-    else:
-        def barrier():
-            pass
-
-        def max_over_ranks(x):
-            return x
+    barrier, max_over_ranks = rank_reducers(world, "nccl", device)
 
     vbuild.build()
     kern = {"auto": vca.VCA_KERNEL_AUTO, "plain": vca.VCA_KERNEL_PLAIN, "tc": vca.VCA_KERNEL_TC}[args.kernel]
@@ -310,10 +324,7 @@ def run_vca(args):
     sampler.start()
     ms, kernel_ms, launches = time_pushes(an, y, u, v, args.steps, args.warmup, stream, barrier)
     clocks = sampler.stop()
-    ms_max = max_over_ranks(ms)
-    frames_total = args.steps * args.frames * world
-    value = frames_total / (ms_max / 1000.0)
-    ms_per_step = ms_max / args.steps
+    value, ms_per_step = whole_job_rate(ms, args.steps, args.frames, world, max_over_ranks)
 
     peak, peak_kind = load_peaks()
     kernel_frames_per_launch = args.frames
