@@ -205,3 +205,25 @@ def test_batch_with_drop_in_matrices(vca):
                 assert_features_close(got[t], e, where=f"channel {i} frame {t} (same={same})")
             m.close()
             s_.close()
+
+
+def test_batch_beyond_the_member_table_runs_on_cuda_cores(vca):
+    # A tensor-core launch holds at most 64 members; a larger batch of tensor-core analyzers takes
+    # the CUDA-core kernel and still matches the oracle.
+    n = 65
+    frames = frames_list(SequenceSpec(64, 64, 2, 95, sigma=4.0))
+    y, u, v = to_device(frames)
+    members = [vca.Analyzer(64, 64, 8, 32, True, max_batch=1) for _ in range(n)]
+    try:
+        assert members[0].kernel == vca.VCA_KERNEL_TC
+        with vca.Batch(members) as batch:
+            assert batch.kernel == vca.VCA_KERNEL_PLAIN
+            for t in range(2):
+                batch.tick([(y[t], u[t], v[t])] * n)
+        per, _ = oracle_sequence(frames, oracle_config(members[0]))
+        for i in (0, 31, 64):
+            for t in range(2):
+                assert_features_close(members[i].frame_features(t), per[t], where=f"member {i} frame {t}")
+    finally:
+        for a in members:
+            a.close()
