@@ -234,9 +234,13 @@ typedef struct {
 /* Groups n analyzers (1 .. 65535, distinct, none already in a batch).  Waits for the analyzers'
  * earlier work and captures two tick graphs on a stream of its own.  If every analyzer runs the
  * tensor-core kernel and n <= 64, a tick analyses them with the persistent tensor-core kernel:
- * one launch for the 8-bit members and one for the 10-bit members, the two on forked branches
- * of the tick graph (the tensor maps of the tick's frames are encoded on the host at each tick);
- * otherwise with one launch of the batched CUDA-core kernel, whose CTA map is built here.  VCA_E_ARG for mismatched devices, block sizes or low_pass. */
+ * one launch for the 8-bit members and one for the 10-bit members, side by side on forked
+ * branches of the tick graph with the device's SMs split between them in proportion to their
+ * tiles.  The tensor maps of a tick's frames are encoded on the host; each analyzer keeps those
+ * of its last 8 distinct frames (by plane pointers and pitches), so frames ticked from a ring of
+ * up to 8 buffers per channel are encoded once.  Otherwise a tick is one launch of the batched
+ * CUDA-core kernel, whose CTA map is built here.  VCA_E_ARG for mismatched devices, block sizes
+ * or low_pass. */
 vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch** out);
 
 /* The kernel family a batch's ticks run: VCA_KERNEL_TC or VCA_KERNEL_PLAIN. */

@@ -7,6 +7,8 @@
 // moves the features into a pinned ring slot whose event tells readers when it landed.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -142,9 +144,14 @@ struct vca_analyzer {
 // A batch of analyzers ticked together: one frame each per tick, analysed by one launch of the
 // batched tensor-core kernel (every member on the tensor-core kernel, at most
 // tc_batch_max_members()) or of the batched plain kernel, and one launch of the batched
-// reduction, replayed from a CUDA graph.  The per-tick arguments live in pinned host memory that
-// a copy node of the graph uploads, so the graph never changes; two graphs alternate so that a
-// tick's arguments can be written while the previous tick runs.
+// reduction, replayed from a CUDA graph.  A tensor-core batch passes every per-tick argument as
+// kernel parameters, replaced in the graph's kernel nodes each tick (the analysis launches' member
+// tables and tensor maps, the reduction's arguments), and its reduction writes the features (and
+// the analysis timeout flag beside them) straight into mapped pinned host memory, so its graph
+// is the analysis launches and the reduction, nothing else.  A plain batch's per-tick arguments
+// live in pinned host memory that a copy node of the graph uploads, and a copy node reads the
+// features back.  Two graphs alternate so that a tick's arguments and results can be in use
+// while the previous tick runs.
 struct vca_batch {
   std::vector<vca_analyzer*> m;
   int n = 0;
@@ -157,6 +164,7 @@ struct vca_batch {
   // 10-bit in 16-bit words); two groups run as two launches on forked streams of the graph.
   int tc_groups = 1;
   int tc_gbps[2] = {1, 2};
+  int sms = 1;                     // SMs of the device: the CTAs of a tick's tensor-core launches
   std::vector<uint8_t> tc_params[2];  // per group: the launch's parameter block (member table, tensor maps)
   cudaGraphNode_t tc_node[2][2] = {};  // per graph and group: the tensor-core launch's node
   cudaStream_t stream = nullptr;
@@ -165,13 +173,17 @@ struct vca_batch {
   vca::BatchCta* d_map = nullptr;
   int n_cta = 0;
   size_t ma_bytes = 0, desc_bytes = 0;
-  uint8_t* d_desc = nullptr;       // BatchMemberArgs[n] (CUDA-core batches) | ReduceArgs[n]
+  uint8_t* d_desc = nullptr;       // CUDA-core batches: BatchMemberArgs[n] | ReduceArgs[n]
   uint8_t* h_desc[2] = {nullptr, nullptr};
   int* d_err = nullptr;            // the tensor-core kernel's wait-timeout flag
   int* h_err = nullptr;            // pinned, one per graph
+  vca::ReduceBatchParams* red_params = nullptr;  // tensor-core batches: the reduction's parameters
+  cudaGraphNode_t red_node[2] = {};              // and its node in each graph
   std::vector<vca::TcBatchFrame> tc_frames[2];
-  double* d_feats = nullptr;       // n x FEAT_STRIDE
-  double* h_feats[2] = {nullptr, nullptr};
+  std::vector<vca::TcMapCache*> tc_maps;  // per member: tensor maps of its recent frames
+  double* d_feats = nullptr;       // CUDA-core batches: n x FEAT_STRIDE
+  double* h_feats[2] = {nullptr, nullptr};  // pinned, per graph (tensor-core batches: mapped, + flag row)
+  double* h_feats_dev[2] = {nullptr, nullptr};  // the device's view of h_feats (tensor-core batches)
   unsigned long long* d_partials = nullptr;
   int red_slices = 1;              // slices per frame of the batched reduction
   unsigned int* d_counters = nullptr;
@@ -456,8 +468,8 @@ vca_status batch_harvest_front(vca_batch* b, bool blocking) {
     if (q == cudaErrorNotReady) return fail(VCA_E_AGAIN, "frame features not ready yet");
     if (q != cudaSuccess) return cuda_fail(q, "querying a batch tick");
   }
-  if (b->h_err[t.k] != 0) {
-    const int code = b->h_err[t.k];
+  const int code = b->tc ? (int)b->h_feats[t.k][(size_t)b->n * vca::FEAT_STRIDE] : b->h_err[t.k];
+  if (code != 0) {
     b->h_err[t.k] = 0;
     b->pending.pop_front();
     return fail(VCA_E_TIMEOUT, "batched analysis kernel gave up on a bounded wait (code %d); the tick's frames are lost",
@@ -515,10 +527,12 @@ void destroy_batch(vca_batch* b) {
     if (b->h_desc[k]) cudaFreeHost(b->h_desc[k]);
     if (b->h_feats[k]) cudaFreeHost(b->h_feats[k]);
   }
+  for (vca::TcMapCache* c : b->tc_maps) vca::tc_map_cache_free(c);
   cudaFree(b->d_map);
   cudaFree(b->d_desc);
   cudaFree(b->d_err);
   if (b->h_err) cudaFreeHost(b->h_err);
+  delete b->red_params;
   cudaFree(b->d_feats);
   cudaFree(b->d_partials);
   cudaFree(b->d_counters);
@@ -530,14 +544,20 @@ void destroy_batch(vca_batch* b) {
   delete b;
 }
 
-// Captures tick graph k: upload the arguments, analyse, reduce, read the features back.
+// Bytes of a tick's features on the host: n rows, then (tensor-core batches) the row holding the
+// analysis kernel's timeout flag.
+size_t feats_bytes(const vca_batch* b) {
+  return (size_t)(b->n + (b->tc ? 1 : 0)) * vca::FEAT_STRIDE * sizeof(double);
+}
+
+// Captures tick graph k: analyse and reduce (CUDA-core batches: upload the arguments first and
+// read the features back after).
 cudaError_t build_tick_graph(vca_batch* b, int k) {
   cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
-  cudaError_t e1 = cudaMemcpyAsync(b->d_desc, b->h_desc[k], b->desc_bytes, cudaMemcpyHostToDevice, b->stream);
-  if (e1 == cudaSuccess && b->tc) {
-    e1 = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
-    if (e1 == cudaSuccess && b->tc_groups == 2) {  // fork: the second group on its own branch
+  cudaError_t e1 = cudaSuccess;
+  if (b->tc) {
+    if (b->tc_groups == 2) {  // fork: the second group on its own branch
       e1 = cudaEventRecord(b->fork_ev, b->stream);
       if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(b->stream2, b->fork_ev, 0);
       if (e1 == cudaSuccess) e1 = vca::launch_tc_batch(b->tc_params[1].data(), b->tc_gbps[1], b->low_pass, b->stream2);
@@ -545,22 +565,22 @@ cudaError_t build_tick_graph(vca_batch* b, int k) {
     }
     if (e1 == cudaSuccess) e1 = vca::launch_tc_batch(b->tc_params[0].data(), b->tc_gbps[0], b->low_pass, b->stream);
     if (e1 == cudaSuccess && b->tc_groups == 2) e1 = cudaStreamWaitEvent(b->stream, b->join_ev, 0);
-  } else if (e1 == cudaSuccess) {
-    e1 = vca::launch_batch_plain(b->d_map, b->n_cta, reinterpret_cast<const vca::BatchMemberArgs*>(b->d_desc), b->w,
-                                 b->nc, b->low_pass, b->stream);
+    if (e1 == cudaSuccess) e1 = vca::launch_reduce_batch_params(*b->red_params, b->stream);
+  } else {
+    e1 = cudaMemcpyAsync(b->d_desc, b->h_desc[k], b->desc_bytes, cudaMemcpyHostToDevice, b->stream);
+    if (e1 == cudaSuccess)
+      e1 = vca::launch_batch_plain(b->d_map, b->n_cta, reinterpret_cast<const vca::BatchMemberArgs*>(b->d_desc),
+                                   b->w, b->nc, b->low_pass, b->stream);
+    if (e1 == cudaSuccess)
+      e1 = vca::launch_reduce_batch(reinterpret_cast<const vca::ReduceArgs*>(b->d_desc + b->ma_bytes), b->n,
+                                    b->red_slices, b->stream);
   }
-  if (e1 == cudaSuccess)
-    e1 = vca::launch_reduce_batch(reinterpret_cast<const vca::ReduceArgs*>(b->d_desc + b->ma_bytes), b->n,
-                                  b->red_slices, b->stream);
-  if (e1 == cudaSuccess)
-    e1 = cudaMemcpyAsync(b->h_feats[k], b->d_feats, (size_t)b->n * vca::FEAT_STRIDE * sizeof(double),
-                         cudaMemcpyDeviceToHost, b->stream);
-  if (e1 == cudaSuccess && b->tc)
-    e1 = cudaMemcpyAsync(b->h_err + k, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+  if (e1 == cudaSuccess && !b->tc)
+    e1 = cudaMemcpyAsync(b->h_feats[k], b->d_feats, feats_bytes(b), cudaMemcpyDeviceToHost, b->stream);
   e = cudaStreamEndCapture(b->stream, &b->graph[k]);
   if (e1 != cudaSuccess) return e1;
   if (e != cudaSuccess) return e;
-  if (b->tc) {  // the tensor-core launches, whose parameters each tick replaces
+  if (b->tc) {  // the tensor-core launches and the reduction, whose parameters each tick replaces
     size_t count = 0;
     e = cudaGraphGetNodes(b->graph[k], nullptr, &count);
     std::vector<cudaGraphNode_t> nodes(count);
@@ -573,10 +593,12 @@ cudaError_t build_tick_graph(vca_batch* b, int k) {
       e = cudaGraphKernelNodeGetParams(nodes[i], &kp);
       for (int gi = 0; e == cudaSuccess && gi < b->tc_groups; ++gi)
         if (kp.func == vca::tc_batch_kernel(b->tc_gbps[gi], b->low_pass)) b->tc_node[k][gi] = nodes[i];
+      if (e == cudaSuccess && kp.func == vca::reduce_batch_params_kernel()) b->red_node[k] = nodes[i];
     }
     if (e != cudaSuccess) return e;
     for (int gi = 0; gi < b->tc_groups; ++gi)
       if (!b->tc_node[k][gi]) return cudaErrorGraphExecUpdateFailure;
+    if (!b->red_node[k]) return cudaErrorGraphExecUpdateFailure;
   }
   return cudaGraphInstantiate(&b->exec[k], b->graph[k], 0);
 }
@@ -1055,6 +1077,7 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
     vca_status st = harvest_all(members[i]);
     if (st != VCA_OK) {
       destroy_batch(b);
+      if (prev_dev >= 0) cudaSetDevice(prev_dev);
       return st;
     }
     BATCH_CUDA(cudaStreamSynchronize(members[i]->stream), "waiting for an analyzer's earlier work");
@@ -1085,6 +1108,8 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
   }
   for (int gi = 0; b->tc && gi < b->tc_groups; ++gi)
     BATCH_CUDA(vca::tc_batch_prepare(b->tc_gbps[gi], b->low_pass), "preparing the tensor-core kernel");
+  BATCH_CUDA(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device), "querying the SM count");
+  if (b->sms < 1) b->sms = 1;
   if (b->tc && b->tc_groups == 2) {
     BATCH_CUDA(cudaStreamCreateWithFlags(&b->stream2, cudaStreamNonBlocking), "creating the batch's second stream");
     BATCH_CUDA(cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming), "creating batch events");
@@ -1096,16 +1121,46 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
   b->h_err[0] = b->h_err[1] = 0;
   b->tc_frames[0].reserve(n);
   b->tc_frames[1].reserve(n);
-  BATCH_CUDA(cudaMalloc(&b->d_desc, b->desc_bytes), "allocating tick arguments");
-  BATCH_CUDA(cudaMalloc(&b->d_feats, (size_t)n * vca::FEAT_STRIDE * sizeof(double)), "allocating features");
+  for (int i = 0; b->tc && i < n; ++i) {
+    b->tc_maps.push_back(vca::tc_map_cache_new());
+    if (!b->tc_maps.back()) {
+      destroy_batch(b);
+      if (prev_dev >= 0) cudaSetDevice(prev_dev);
+      return fail(VCA_E_NOMEM, "allocating tensor-map caches");
+    }
+  }
+  if (b->tc) {
+    b->red_params = new (std::nothrow) vca::ReduceBatchParams();
+    if (!b->red_params) {
+      destroy_batch(b);
+      if (prev_dev >= 0) cudaSetDevice(prev_dev);
+      return fail(VCA_E_NOMEM, "host allocation failed");
+    }
+  } else {
+    BATCH_CUDA(cudaMalloc(&b->d_desc, b->desc_bytes), "allocating tick arguments");
+  }
+  if (!b->tc) BATCH_CUDA(cudaMalloc(&b->d_feats, feats_bytes(b)), "allocating features");
+  if (b->tc) {
+    b->red_params->n = n;
+    b->red_params->S = b->red_slices;
+    b->red_params->err = b->d_err;
+  }
   BATCH_CUDA(cudaMalloc(&b->d_partials, vca::reduce_partials_bytes(n)), "allocating reduction scratch");
   BATCH_CUDA(cudaMalloc(&b->d_counters, (size_t)n * sizeof(unsigned int)), "allocating counters");
   BATCH_CUDA(cudaMemset(b->d_counters, 0, (size_t)n * sizeof(unsigned int)), "clearing counters");
   for (int k = 0; k < 2; ++k) {
-    BATCH_CUDA(cudaMallocHost(&b->h_desc[k], b->desc_bytes), "allocating pinned tick arguments");
-    memset(b->h_desc[k], 0, b->desc_bytes);
-    BATCH_CUDA(cudaMallocHost(&b->h_feats[k], (size_t)n * vca::FEAT_STRIDE * sizeof(double)),
+    if (!b->tc) {
+      BATCH_CUDA(cudaMallocHost(&b->h_desc[k], b->desc_bytes), "allocating pinned tick arguments");
+      memset(b->h_desc[k], 0, b->desc_bytes);
+    }
+    BATCH_CUDA(cudaHostAlloc(&b->h_feats[k], feats_bytes(b), b->tc ? cudaHostAllocMapped : cudaHostAllocDefault),
                "allocating pinned features");
+    memset(b->h_feats[k], 0, feats_bytes(b));
+    if (b->tc) {
+      BATCH_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&b->h_feats_dev[k]), b->h_feats[k], 0),
+                 "mapping the features");
+      b->red_params->err_out = b->h_feats_dev[k] + (size_t)n * vca::FEAT_STRIDE;
+    }
     BATCH_CUDA(cudaEventCreateWithFlags(&b->ev[k], cudaEventDisableTiming), "creating batch events");
     BATCH_CUDA(build_tick_graph(b, k), "capturing the tick graph");
   }
@@ -1129,8 +1184,8 @@ vca_status vca_batch_tick(vca_batch* b, const vca_frame_ref* frames) {
     vca_status s = check_planes(b->m[i], frames[i].y, frames[i].u, frames[i].v, frames[i].pitch_y, frames[i].pitch_uv);
     if (s != VCA_OK) return fail(s, "frame of analyzer %d: %s", i, vca_last_error());
   }
-  auto* ma = reinterpret_cast<vca::BatchMemberArgs*>(b->h_desc[k]);
-  auto* ra = reinterpret_cast<vca::ReduceArgs*>(b->h_desc[k] + b->ma_bytes);
+  auto* ma = b->tc ? nullptr : reinterpret_cast<vca::BatchMemberArgs*>(b->h_desc[k]);
+  auto* ra = b->tc ? b->red_params->a : reinterpret_cast<vca::ReduceArgs*>(b->h_desc[k] + b->ma_bytes);
   vca_batch::Tick tick;
   tick.k = k;
   b->tc_frames[0].clear();
@@ -1148,7 +1203,7 @@ vca_status vca_batch_tick(vca_batch* b, const vca_frame_ref* frames) {
       b->tc_frames[gi].push_back({&a->g,
                               {static_cast<const uint8_t*>(f.y), static_cast<const uint8_t*>(f.u),
                                static_cast<const uint8_t*>(f.v), f.pitch_y, f.pitch_uv, 0, 0},
-                              a->d_blockvals});
+                              a->d_blockvals, b->tc_maps[i]});
     } else {
       ma[i].pa[0] = member_plain_args(a, 0, frames[i]);
       ma[i].pa[1] = member_plain_args(a, 1, frames[i]);
@@ -1156,23 +1211,53 @@ vca_status vca_batch_tick(vca_batch* b, const vca_frame_ref* frames) {
       ma[i].active = 1;
     }
     ra[i] = vca::reduce_args(a->g, 1, a->d_blockvals, a->d_prevH[a->cur_prev], a->has_prev,
-                             a->d_prevH[a->cur_prev ^ 1], b->d_feats + (size_t)i * vca::FEAT_STRIDE,
+                             a->d_prevH[a->cur_prev ^ 1],
+                             (b->tc ? b->h_feats_dev[k] : b->d_feats) + (size_t)i * vca::FEAT_STRIDE,
                              b->d_partials + (size_t)i * vca::reduce_partials_bytes(1) / sizeof(unsigned long long),
                              b->d_counters + i);
     tick.members.push_back({i, a->frames_pushed, a->has_prev != 0});
   }
+  int grid[2] = {b->sms, b->sms};
   for (int gi = 0; b->tc && gi < b->tc_groups; ++gi) {
     cudaError_t e = vca::tc_batch_fill(b->tc_params[gi].data(), b->tc_frames[gi].data(), (int)b->tc_frames[gi].size(),
                                        b->m[0]->tables, b->d_err);
     if (e != cudaSuccess) return cuda_fail(e, "encoding the tensor maps of a batch tick");
-    // The graph's launch takes this tick's parameter block (copied by the call).
+  }
+  if (b->tc && b->tc_groups == 2 && b->sms >= 2) {
+    // The two sample sizes' launches run side by side on disjoint SMs (a CTA holds a whole SM),
+    // the SMs split in proportion to their work: a tile of 16-bit words costs about 1.15 x a tile
+    // of bytes.  So the tick pays one pipeline fill and drain instead of two in sequence.  Each
+    // share is even: with an odd split one SM pair held a CTA of each launch, and those two CTAs
+    // ran 1.6x slower than all the others (measured), which set the tick's time.
+    double w[2];
+    for (int gi = 0; gi < 2; ++gi)
+      w[gi] = vca::tc_batch_items(b->tc_params[gi].data()) * (b->tc_gbps[gi] == 2 ? 1.15 : 1.0);
+    int g0 = w[0] + w[1] > 0.0 ? (int)std::lround(b->sms * w[0] / (w[0] + w[1])) : b->sms / 2;
+    g0 = (g0 + 1) & ~1;
+    g0 = std::min(std::max(g0, 1), b->sms - 1);
+    grid[0] = g0;
+    grid[1] = b->sms - g0;
+  }
+  for (int gi = 0; b->tc && gi < b->tc_groups; ++gi) {
+    // The graph's launch takes this tick's parameter block (copied by the call) and grid.
     cudaKernelNodeParams kp{};
-    e = cudaGraphKernelNodeGetParams(b->tc_node[k][gi], &kp);
+    cudaError_t e = cudaGraphKernelNodeGetParams(b->tc_node[k][gi], &kp);
     void* args[1] = {b->tc_params[gi].data()};
     kp.kernelParams = args;
     kp.extra = nullptr;
+    kp.gridDim = dim3((unsigned)grid[gi]);
     if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(b->exec[k], b->tc_node[k][gi], &kp);
     if (e != cudaSuccess) return cuda_fail(e, "setting the parameters of a batch tick");
+  }
+  if (b->tc) {
+    b->red_params->err_out = b->h_feats_dev[k] + (size_t)b->n * vca::FEAT_STRIDE;
+    cudaKernelNodeParams kp{};
+    cudaError_t e = cudaGraphKernelNodeGetParams(b->red_node[k], &kp);
+    void* args[1] = {b->red_params};
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(b->exec[k], b->red_node[k], &kp);
+    if (e != cudaSuccess) return cuda_fail(e, "setting the reduction parameters of a batch tick");
   }
   int prev_dev = -1;
   cudaGetDevice(&prev_dev);

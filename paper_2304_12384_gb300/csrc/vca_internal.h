@@ -103,10 +103,18 @@ bool tc_supported(const Geometry& g);
 // one sample size in one launch of the persistent kernel.  The launch's member table and tensor
 // maps are its kernel parameters (tc_batch_params_bytes(), about 29 KB), which the host fills
 // with tc_batch_fill; a captured launch's parameters are replaced per tick in the graph.
+// A member's tensor maps for its most recent distinct frames: frames pushed from a ring of
+// device buffers repeat their plane addresses, and a tick whose frame matches an entry (plane
+// pointers and pitches) copies its three maps instead of encoding them again.  One cache per
+// member of a batch (the member's geometry is fixed), owned by the batch.
+struct TcMapCache;
+TcMapCache* tc_map_cache_new();
+void tc_map_cache_free(TcMapCache* c);
 struct TcBatchFrame {
   const Geometry* g;   // the member's analysis geometry (tc_supported)
   FramePlanes fp;      // its frame (frame strides unused)
   float* blockvals;    // its [6][C] block values
+  TcMapCache* maps;    // the member's map cache, or null to encode every tick
 };
 int tc_batch_max_members();
 size_t tc_batch_params_bytes();
@@ -116,7 +124,10 @@ size_t tc_batch_params_bytes();
 cudaError_t tc_batch_fill(void* params, const TcBatchFrame* frames, int n, const DeviceTables& t, int* err);
 // Sets up the kernel instance for this sample size and low_pass (outside any stream capture).
 cudaError_t tc_batch_prepare(int bps, bool low_pass);
-// Launches the analysis with the parameter block params (host memory; bps 1 or 2).
+// Work items (128x128 luma tiles) of a filled parameter block.
+int tc_batch_items(const void* params);
+// Launches the analysis with the parameter block params (host memory; bps 1 or 2) on one CTA per
+// SM of the device.
 cudaError_t launch_tc_batch(const void* params, int bps, bool low_pass, cudaStream_t s);
 // The kernel a batched launch of this sample size and low_pass runs (to find its graph node).
 const void* tc_batch_kernel(int bps, bool low_pass);
@@ -138,6 +149,22 @@ ReduceArgs reduce_args(const Geometry& g, int nframes, const float* blockvals, c
 cudaError_t launch_reduce_batch(const ReduceArgs* d_args, int n, int slices, cudaStream_t s);
 // Slices per frame of a batched reduction whose largest member has max_C blocks per plane.
 int reduce_batch_slices(int64_t max_C);
+
+// The same batched reduction with its arguments as kernel parameters (batches of at most
+// kMaxBatchMembers analyzers), so that a tick's graph needs no upload of them: a[m] as above for
+// m < n, S slices per frame.  The launch also hands the analysis kernel's wait-timeout flag to
+// the host: one thread copies *err into *err_out (as a double, next to the features the tick
+// reads back) and clears *err for the next tick.  err may be null.
+constexpr int kMaxBatchMembers = 64;
+struct ReduceBatchParams {
+  ReduceArgs a[kMaxBatchMembers];
+  int n, S;
+  int* err;
+  double* err_out;
+};
+cudaError_t launch_reduce_batch_params(const ReduceBatchParams& p, cudaStream_t s);
+// The kernel launch_reduce_batch_params runs (to find its graph node).
+const void* reduce_batch_params_kernel();
 
 // One CTA of the batched plain kernel: analyzer `member`, plane kind (0 luma, 1 chroma), plane
 // within the kind (chroma: 0 U, 1 V) and block chunk (BPC blocks).

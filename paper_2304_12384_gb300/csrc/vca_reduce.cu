@@ -166,7 +166,29 @@ __global__ void __launch_bounds__(kThreads) reduce_batch_kernel(const ReduceArgs
   reduce_slice(a, 0, blockIdx.x % S, S);
 }
 
+// The same with the members' arguments in the kernel parameters; also hands over the analysis
+// kernel's timeout flag (the analysis launches of the tick have finished before this one starts,
+// and the next tick's start after it ends).
+__global__ void __launch_bounds__(kThreads) reduce_batch_params_kernel_(const __grid_constant__ ReduceBatchParams p) {
+  if (blockIdx.x == 0 && threadIdx.x == 0 && p.err) {
+    *p.err_out = (double)*p.err;
+    *p.err = 0;
+  }
+  const ReduceArgs& a = p.a[blockIdx.x / p.S];
+  if (a.nframes == 0) return;
+  reduce_slice(a, 0, blockIdx.x % p.S, p.S);
+}
+
 }  // namespace
+
+cudaError_t launch_reduce_batch_params(const ReduceBatchParams& p, cudaStream_t s) {
+  if (p.n <= 0 || p.n > kMaxBatchMembers) return cudaErrorInvalidValue;
+  if (p.S < 1 || p.S > kMaxSlices) return cudaErrorInvalidValue;
+  reduce_batch_params_kernel_<<<p.n * p.S, kThreads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+const void* reduce_batch_params_kernel() { return (const void*)reduce_batch_params_kernel_; }
 
 size_t reduce_partials_bytes(int max_frames) { return (size_t)max_frames * kMaxSlices * kSums * 16; }
 

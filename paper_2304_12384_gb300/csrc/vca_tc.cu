@@ -46,6 +46,7 @@
 
 #include <cstring>
 #include <mutex>
+#include <new>
 
 #include "vca_internal.h"
 #include "vca_ptx.cuh"
@@ -61,7 +62,7 @@ constexpr int kA2C = 4096;      // of one chroma job: 128 rows x 16 K x fp16
 constexpr int OFF_RAW = 0;
 constexpr int kBars = 80;
 constexpr int kA2Slots = 4;     // 0-1 luma jobs, 2-3 chroma jobs
-constexpr int kMaxMembers = 64;
+constexpr int kMaxMembers = kMaxBatchMembers;
 
 // One analyzer ("member") of a launch: its work items, geometry, outputs and stage-1 constants.
 // A single analyzer's launch has one member with all its frames; a batched tick has one member
@@ -1010,6 +1011,21 @@ bool tc_supported(const Geometry& g) {
          g.s1c == s1_of<16>(g.bps) && encode_fn() != nullptr;
 }
 
+struct TcMapCache {
+  static constexpr int kEntries = 8;
+  struct Entry {
+    const void *y, *u, *v;
+    int64_t pitch_y, pitch_uv;
+    CUtensorMap m[3];
+  };
+  Entry e[kEntries];
+  int n = 0, next = 0;  // entries in use; the one replaced next (oldest first)
+};
+
+TcMapCache* tc_map_cache_new() { return new (std::nothrow) TcMapCache(); }
+
+void tc_map_cache_free(TcMapCache* c) { delete c; }
+
 int tc_batch_max_members() { return kMaxMembers; }
 
 size_t tc_batch_params_bytes() { return sizeof(TcBatchParams); }
@@ -1029,17 +1045,40 @@ cudaError_t tc_batch_fill(void* params, const TcBatchFrame* frames, int n, const
     const FramePlanes& fp = frames[i].fp;
     if (!tc_supported(g) || g.bps != frames[0].g->bps) return cudaErrorInvalidValue;
     items += fill_member(p.mem[i], g, items, 1, frames[i].blockvals);
+    TcMapCache* c = frames[i].maps;
+    const TcMapCache::Entry* hit = nullptr;
+    for (int j = 0; c && j < c->n && !hit; ++j) {
+      const TcMapCache::Entry& x = c->e[j];
+      if (x.y == fp.y && x.u == fp.u && x.v == fp.v && x.pitch_y == fp.pitch_y && x.pitch_uv == fp.pitch_uv) hit = &x;
+    }
+    if (hit) {
+      std::memcpy(&p.maps[3 * i], hit->m, sizeof hit->m);
+      continue;
+    }
     const CUtensorMapSwizzle swc = g.bps == 1 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
     cudaError_t e = make_map(&p.maps[3 * i], fp.y, g.W, g.H, fp.pitch_y, 0, 1, g.bps == 1 ? 128 : 64, 128, g.bps,
                              CU_TENSOR_MAP_SWIZZLE_128B);
     if (e == cudaSuccess) e = make_map(&p.maps[3 * i + 1], fp.u, g.cw, g.ch, fp.pitch_uv, 0, 1, 64, 64, g.bps, swc);
     if (e == cudaSuccess) e = make_map(&p.maps[3 * i + 2], fp.v, g.cw, g.ch, fp.pitch_uv, 0, 1, 64, 64, g.bps, swc);
     if (e != cudaSuccess) return e;
+    if (c) {
+      TcMapCache::Entry& x = c->e[c->next];
+      x.y = fp.y;
+      x.u = fp.u;
+      x.v = fp.v;
+      x.pitch_y = fp.pitch_y;
+      x.pitch_uv = fp.pitch_uv;
+      std::memcpy(x.m, &p.maps[3 * i], sizeof x.m);
+      c->next = (c->next + 1) % TcMapCache::kEntries;
+      if (c->n < TcMapCache::kEntries) ++c->n;
+    }
   }
   p.n_members = n;
   p.total_items = items;
   return cudaSuccess;
 }
+
+int tc_batch_items(const void* params) { return static_cast<const TcBatchParams*>(params)->total_items; }
 
 cudaError_t tc_batch_prepare(int bps, bool low_pass) {
   if (bps != 1 && bps != 2) return cudaErrorInvalidValue;

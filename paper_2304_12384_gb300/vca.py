@@ -197,7 +197,8 @@ def vca_batch_create(handles) -> int:
 
 
 def vca_batch_tick(batch: int, refs) -> None:
-    arr = (VcaFrameRef * len(refs))(*refs)
+    """refs: one VcaFrameRef per member of the batch (a sequence or a ctypes array of them)."""
+    arr = refs if isinstance(refs, ctypes.Array) else (VcaFrameRef * len(refs))(*refs)
     _check(lib().vca_batch_tick(_P(batch), arr))
 
 
@@ -454,19 +455,30 @@ class Batch:
         self.analyzers = list(analyzers)
         self.handle = vca_batch_create([a.handle for a in self.analyzers])
 
-    def tick(self, frames):
-        """frames: one (y, u, v) device-tensor triple per analyzer (one frame each), or None to skip."""
-        refs = []
-        for f in frames:
+    def frame_refs(self, frames):
+        """The tick argument for frames (as for tick), built once.  A caller that ticks from a ring
+        of resident frame buffers can keep one per ring slot and pass it to tick unchanged."""
+        if len(frames) != len(self.analyzers):
+            raise ValueError(f"one frame (or None) per analyzer: {len(self.analyzers)} expected, got {len(frames)}")
+        refs = (VcaFrameRef * len(frames))()
+        for i, f in enumerate(frames):
             if f is None:
-                refs.append(VcaFrameRef(None, None, None, 0, 0))
                 continue
             y, u, v = f
             es = y.element_size()
             if u.stride(-2) != v.stride(-2):
                 raise ValueError("U and V planes must share a pitch")
-            refs.append(VcaFrameRef(y.data_ptr(), u.data_ptr(), v.data_ptr(), y.stride(-2) * es, u.stride(-2) * es))
-        vca_batch_tick(self.handle, refs)
+            refs[i] = VcaFrameRef(y.data_ptr(), u.data_ptr(), v.data_ptr(), y.stride(-2) * es, u.stride(-2) * es)
+        return refs
+
+    def tick(self, frames):
+        """frames: one (y, u, v) device-tensor triple per analyzer (one frame each), or None to
+        skip it; or the result of frame_refs."""
+        if not isinstance(frames, ctypes.Array):
+            frames = self.frame_refs(frames)
+        elif len(frames) != len(self.analyzers) or frames._type_ is not VcaFrameRef:
+            raise ValueError("a prepared tick argument must come from this batch's frame_refs")
+        vca_batch_tick(self.handle, frames)
 
     def sync(self):
         vca_batch_sync(self.handle)

@@ -227,3 +227,44 @@ def test_batch_beyond_the_member_table_runs_on_cuda_cores(vca):
     finally:
         for a in members:
             a.close()
+
+
+@pytest.mark.parametrize("ring", [3, 10])
+def test_batch_ticks_from_a_ring_of_buffers(vca, ring):
+    # Frames ticked from a ring of resident buffers rewritten in place, through tick arguments built
+    # once per ring slot: the batch reuses each member's tensor maps by plane address (ring 3: every
+    # tick after the first three hits; ring 10: more slots than a member keeps, so entries are
+    # replaced).  Each channel matches its single analyzer fed the same frames, bit for bit.
+    import torch
+
+    ticks = 14
+    chans = CHANNELS
+    frames = [frames_list(SequenceSpec(w, h, ticks, 500 + i, bit_depth=bd, sigma=4.0, cuts=(7,), motion=3))
+              for i, (w, h, bd) in enumerate(chans)]
+    dev = [to_device(f) for f in frames]
+    rings = [tuple(torch.empty((ring,) + tuple(p.shape[1:]), dtype=p.dtype, device=p.device) for p in d)
+             for d in dev]
+    members = [vca.Analyzer(w, h, bd, 32, True, max_batch=2) for (w, h, bd) in chans]
+    singles = [vca.Analyzer(w, h, bd, 32, True, max_batch=2) for (w, h, bd) in chans]
+    try:
+        with vca.Batch(members) as batch:
+            assert batch.kernel == vca.VCA_KERNEL_TC
+            slots = [batch.frame_refs([(ry[s], ru[s], rv[s]) for (ry, ru, rv) in rings]) for s in range(ring)]
+            with pytest.raises(ValueError):
+                batch.frame_refs([(rings[0][0][0], rings[0][1][0], rings[0][2][0])])
+            for t in range(ticks):
+                s = t % ring
+                for d, r in zip(dev, rings):
+                    for p, rp in zip(d, r):
+                        rp[s].copy_(p[t])
+                torch.cuda.synchronize()
+                batch.tick(slots[s])
+                batch.sync()
+                for a, (y, u, v) in zip(singles, dev):
+                    a.push(y[t], u[t], v[t])
+        for i, (m, a) in enumerate(zip(members, singles)):
+            got = [m.frame_features(t) for t in range(ticks)]
+            assert got == [a.frame_features(t) for t in range(ticks)], f"channel {i}"
+    finally:
+        for a in members + singles:
+            a.close()
