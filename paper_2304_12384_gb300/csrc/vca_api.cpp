@@ -104,15 +104,16 @@ struct vca_analyzer {
   bool red_recorded[2] = {false, false};
   float* d_prevH[2] = {nullptr, nullptr};
   int cur_prev = 0;
-  double* d_feats = nullptr;     // max_batch * FEAT_STRIDE
   int* d_err = nullptr;          // kernel wait-timeout flags: one per push buffer, one for dumps
   unsigned long long* d_red_partials = nullptr;  // frame-reduction scratch
   unsigned int* d_red_counters = nullptr; // one arrival counter per frame, kept at zero between launches
   uint8_t* d_staging = nullptr;  // host frames are copied here
   size_t staging_bytes = 0;
 
-  double* h_ring = nullptr;      // pinned, kRing slots of max_batch * FEAT_STRIDE
-  int* h_err = nullptr;          // pinned, one timeout flag per ring slot
+  double* h_ring = nullptr;      // pinned and mapped, kRing slots of max_batch * FEAT_STRIDE
+  double* h_ring_dev = nullptr;  // the device's view of h_ring (the reduction writes there)
+  int* h_err = nullptr;          // pinned and mapped, one timeout flag per ring slot
+  int* h_err_dev = nullptr;      // the device's view of h_err
   cudaEvent_t ring_ev[kRing] = {};
   cudaEvent_t t0_ev[kRing] = {};   // analysis-kernel timing, per ring slot
   cudaEvent_t t1_ev[kRing] = {};
@@ -277,7 +278,6 @@ void destroy(vca_analyzer* a) {
   cudaFree(a->d_blockvals);
   cudaFree(a->d_prevH[0]);
   cudaFree(a->d_prevH[1]);
-  cudaFree(a->d_feats);
   cudaFree(a->d_err);
   cudaFree(a->d_red_partials);
   cudaFree(a->d_red_counters);
@@ -717,7 +717,6 @@ vca_status vca_open(const vca_config* cfg, void* cuda_stream, vca_analyzer** out
     OPEN_CUDA(cudaMalloc(&a->d_prevH[i], (size_t)g.C * sizeof(float)), "allocating h state");
     OPEN_CUDA(cudaMemset(a->d_prevH[i], 0, (size_t)g.C * sizeof(float)), "clearing h state");
   }
-  OPEN_CUDA(cudaMalloc(&a->d_feats, (size_t)a->max_batch * vca::FEAT_STRIDE * sizeof(double)), "allocating features");
   OPEN_CUDA(cudaMalloc(&a->d_red_partials, vca::reduce_partials_bytes(a->max_batch)), "allocating reduction scratch");
   OPEN_CUDA(cudaMalloc(&a->d_red_counters, (size_t)a->max_batch * sizeof(unsigned int)), "allocating counters");
   OPEN_CUDA(cudaMemset(a->d_red_counters, 0, (size_t)a->max_batch * sizeof(unsigned int)), "clearing counters");
@@ -737,10 +736,13 @@ vca_status vca_open(const vca_config* cfg, void* cuda_stream, vca_analyzer** out
     OPEN_CUDA(cudaEventCreateWithFlags(&a->an_done[b], cudaEventDisableTiming), "creating events");
     OPEN_CUDA(cudaEventCreateWithFlags(&a->red_done[b], cudaEventDisableTiming), "creating events");
   }
-  OPEN_CUDA(cudaMallocHost(&a->h_err, kRing * sizeof(int)), "allocating pinned error flags");
+  OPEN_CUDA(cudaHostAlloc(&a->h_err, kRing * sizeof(int), cudaHostAllocMapped), "allocating pinned error flags");
   memset(a->h_err, 0, kRing * sizeof(int));
-  OPEN_CUDA(cudaMallocHost(&a->h_ring, (size_t)kRing * a->max_batch * vca::FEAT_STRIDE * sizeof(double)),
+  OPEN_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&a->h_err_dev), a->h_err, 0), "mapping error flags");
+  OPEN_CUDA(cudaHostAlloc(&a->h_ring, (size_t)kRing * a->max_batch * vca::FEAT_STRIDE * sizeof(double),
+                          cudaHostAllocMapped),
             "allocating pinned feature ring");
+  OPEN_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&a->h_ring_dev), a->h_ring, 0), "mapping the feature ring");
   for (auto& ev : a->ring_ev) OPEN_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "creating events");
   for (auto& ev : a->t0_ev) OPEN_CUDA(cudaEventCreate(&ev), "creating timing events");
   for (auto& ev : a->t1_ev) OPEN_CUDA(cudaEventCreate(&ev), "creating timing events");
@@ -778,14 +780,15 @@ vca_status vca_push_frames(vca_analyzer* a, const void* y, const void* u, const 
   }
   const int slot = a->next_slot;
   const bool timed = a->timing;
-  // Analysis on the analyzer's stream into push buffer bs; the reduction and the read-back on the
-  // side stream, so they overlap the next push's analysis (which uses the other buffer).
+  // Analysis on the analyzer's stream into push buffer bs; the reduction on the side stream, so it
+  // overlaps the next push's analysis (which uses the other buffer).  The reduction writes the
+  // features and the analysis kernel's timeout flag (which it then clears) straight into the
+  // mapped pinned ring slot: no copies.
   const int bs = a->bv_slot;
   float* bv = a->d_blockvals + (size_t)bs * a->max_batch * vca::N_ROWS * a->g.C;
   int* derr = a->d_err + bs;
   if (a->red_recorded[bs])
     VCA_CUDA(cudaStreamWaitEvent(a->stream, a->red_done[bs], 0), "ordering after the previous reduction");
-  VCA_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), a->stream), "clearing the error flag");
   if (timed) VCA_CUDA(cudaEventRecord(a->t0_ev[slot], a->stream), "recording timing event");
   cudaError_t e = run_analysis(a, fp, n_frames, bv, nullptr, derr);
   if (e != cudaSuccess) return cuda_fail(e, "launching the analysis kernel");
@@ -793,13 +796,9 @@ vca_status vca_push_frames(vca_analyzer* a, const void* y, const void* u, const 
   VCA_CUDA(cudaEventRecord(a->an_done[bs], a->stream), "recording analysis event");
   VCA_CUDA(cudaStreamWaitEvent(a->side, a->an_done[bs], 0), "ordering the reduction");
   e = vca::launch_reduce(a->g, n_frames, bv, a->d_prevH[a->cur_prev], a->has_prev, a->d_prevH[a->cur_prev ^ 1],
-                         a->d_feats, a->d_red_partials, a->d_red_counters, a->side, &a->launches);
+                         a->h_ring_dev + (size_t)slot * a->max_batch * vca::FEAT_STRIDE, a->d_red_partials,
+                         a->d_red_counters, a->side, &a->launches, derr, a->h_err_dev + slot);
   if (e != cudaSuccess) return cuda_fail(e, "launching the frame reduction");
-  VCA_CUDA(cudaMemcpyAsync(a->h_ring + (size_t)slot * a->max_batch * vca::FEAT_STRIDE, a->d_feats,
-                           (size_t)n_frames * vca::FEAT_STRIDE * sizeof(double), cudaMemcpyDeviceToHost, a->side),
-           "copying features to the host");
-  VCA_CUDA(cudaMemcpyAsync(a->h_err + slot, derr, sizeof(int), cudaMemcpyDeviceToHost, a->side),
-           "copying the error flag");
   VCA_CUDA(cudaEventRecord(a->ring_ev[slot], a->side), "recording feature event");
   VCA_CUDA(cudaEventRecord(a->red_done[bs], a->side), "recording reduction event");
   a->red_recorded[bs] = true;

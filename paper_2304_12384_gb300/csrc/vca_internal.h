@@ -135,10 +135,13 @@ const void* tc_batch_kernel(int bps, bool low_pass);
 // Exact frame reduction: features of n frames (the block sums exact in 128-bit fixed point, each
 // total rounded once to FP64) and the h state update.  `partials` holds reduce_partials_bytes(max
 // frames) of scratch; `counters` (one per frame) must be zero on entry and is zero again on exit.
+// feats may be mapped pinned host memory.  If err is not null, the launch also copies the analysis
+// kernel's timeout flag *err into *err_out (which may be mapped host memory) and clears *err.
 size_t reduce_partials_bytes(int max_frames);
 cudaError_t launch_reduce(const Geometry& g, int nframes, const float* blockvals, const float* prevH_in,
                           int has_prev, float* prevH_out, double* feats, unsigned long long* partials,
-                          unsigned int* counters, cudaStream_t s, int64_t* launches);
+                          unsigned int* counters, cudaStream_t s, int64_t* launches, int* err = nullptr,
+                          int* err_out = nullptr);
 
 // Reduction arguments of one analyzer (reduce_partials_bytes(nframes) of `partials`; `counters`
 // zero on entry).

@@ -155,7 +155,13 @@ __device__ __forceinline__ void reduce_slice(const ReduceArgs& a, int f, int sli
   }
 }
 
-__global__ void __launch_bounds__(kThreads) reduce_kernel(const ReduceArgs a, int S) {
+// err, if not null: the analysis kernel's timeout flag, copied into *err_out and cleared (the
+// analysis launch has finished before this one starts).
+__global__ void __launch_bounds__(kThreads) reduce_kernel(const ReduceArgs a, int S, int* err, int* err_out) {
+  if (err && blockIdx.x == 0 && threadIdx.x == 0) {
+    *err_out = *err;
+    *err = 0;
+  }
   reduce_slice(a, blockIdx.x / S, blockIdx.x % S, S);
 }
 
@@ -194,11 +200,11 @@ size_t reduce_partials_bytes(int max_frames) { return (size_t)max_frames * kMaxS
 
 cudaError_t launch_reduce(const Geometry& g, int nframes, const float* blockvals, const float* prevH_in,
                           int has_prev, float* prevH_out, double* feats, unsigned long long* partials,
-                          unsigned int* counters, cudaStream_t s, int64_t* launches) {
+                          unsigned int* counters, cudaStream_t s, int64_t* launches, int* err, int* err_out) {
   if (nframes <= 0) return cudaSuccess;
   const ReduceArgs a = reduce_args(g, nframes, blockvals, prevH_in, has_prev, prevH_out, feats, partials, counters);
   const int S = slices_for(g.C);
-  reduce_kernel<<<nframes * S, kThreads, 0, s>>>(a, S);
+  reduce_kernel<<<nframes * S, kThreads, 0, s>>>(a, S, err, err_out);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) ++*launches;
   return e;
