@@ -1233,7 +1233,8 @@ vca_status vca_batch_tick(vca_batch* b, const vca_frame_ref* frames) {
       w[gi] = vca::tc_batch_items(b->tc_params[gi].data()) * (b->tc_gbps[gi] == 2 ? 1.15 : 1.0);
     int g0 = w[0] + w[1] > 0.0 ? (int)std::lround(b->sms * w[0] / (w[0] + w[1])) : b->sms / 2;
     g0 = (g0 + 1) & ~1;
-    g0 = std::min(std::max(g0, 1), b->sms - 1);
+    const int lo = b->sms >= 4 ? 2 : 1;  // a launch with no tiles this tick still gets a (full) SM pair
+    g0 = std::min(std::max(g0, lo), b->sms - lo);
     grid[0] = g0;
     grid[1] = b->sms - g0;
   }

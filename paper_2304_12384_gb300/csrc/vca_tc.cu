@@ -36,8 +36,8 @@
 // bit-identical to the integer definition; H uses the same FP32 order as the CUDA-core form.
 //
 // A launch covers one analyzer's frames (its geometry in the kernel parameters) or, for a batched
-// tick, one frame of each of up to 64 analyzers of one sample size (a member table and tensor
-// maps in device memory, copied to shared memory / fenced by each CTA).
+// tick, one frame of each of up to 64 analyzers of one sample size (a member table and their
+// tensor maps, also in the kernel parameters, read through the constant cache).
 //
 // Every wait is bounded (about two seconds); on timeout the kernel raises a flag in *err,
 // stops, waits for its own copies and MMAs, frees TMEM and returns.

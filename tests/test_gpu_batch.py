@@ -268,3 +268,33 @@ def test_batch_ticks_from_a_ring_of_buffers(vca, ring):
     finally:
         for a in members + singles:
             a.close()
+
+
+def test_batch_tick_without_one_sample_size(vca):
+    # Ticks in which every 8-bit or every 10-bit member of a mixed tensor-core batch sits out (that
+    # launch has no tiles) still match single analyzers fed the same frames, bit for bit.
+    chans = [(640, 352, 8), (320, 180, 10), (200, 120, 10)]
+    pattern = [(0, 1, 2), (0,), (1, 2), (), (2,), (0, 1, 2)]  # members taking part, per tick
+    frames = [frames_list(SequenceSpec(w, h, len(pattern), 80 + i, bit_depth=bd, sigma=4.0, motion=2))
+              for i, (w, h, bd) in enumerate(chans)]
+    dev = [to_device(f) for f in frames]
+    members = [vca.Analyzer(w, h, bd, 32, True, max_batch=2) for (w, h, bd) in chans]
+    singles = [vca.Analyzer(w, h, bd, 32, True, max_batch=2) for (w, h, bd) in chans]
+    try:
+        with vca.Batch(members) as batch:
+            assert batch.kernel == vca.VCA_KERNEL_TC
+            for t, on in enumerate(pattern):
+                refs = []
+                for i, (y, u, v) in enumerate(dev):
+                    if i in on:
+                        refs.append((y[t], u[t], v[t]))
+                        singles[i].push(y[t], u[t], v[t])
+                    else:
+                        refs.append(None)
+                batch.tick(refs)
+        for i, (m, a) in enumerate(zip(members, singles)):
+            n = sum(i in on for on in pattern)
+            assert [m.frame_features(k) for k in range(n)] == [a.frame_features(k) for k in range(n)], f"channel {i}"
+    finally:
+        for a in members + singles:
+            a.close()
