@@ -298,3 +298,32 @@ def test_batch_tick_without_one_sample_size(vca):
     finally:
         for a in members + singles:
             a.close()
+
+
+def test_ladder_size_batch_matches_single_analyzers(vca):
+    # The batched tick at full size, in the launch configuration the ladder benchmark times: 24
+    # channels from 640x360 to 3840x2160, half 10-bit (two tensor-core launches side by side, each
+    # CTA on a run of 25-28 tiles).  Three ticks against single analyzers fed the same frames, bit
+    # for bit; the 2160p 8-bit channel's first frame also against the oracle.
+    from synth import ladder_specs
+
+    specs = ladder_specs(4, n_frames=3)
+    frames = [frames_list(sp, 0, 3) for sp in specs]
+    dev = [to_device(f) for f in frames]
+    members = [vca.Analyzer(sp.width, sp.height, sp.bit_depth, 32, True, max_batch=1) for sp in specs]
+    singles = [vca.Analyzer(sp.width, sp.height, sp.bit_depth, 32, True, max_batch=1) for sp in specs]
+    try:
+        with vca.Batch(members) as batch:
+            assert batch.kernel == vca.VCA_KERNEL_TC
+            for t in range(3):
+                batch.tick([(y[t], u[t], v[t]) for (y, u, v) in dev])
+                for a, (y, u, v) in zip(singles, dev):
+                    a.push(y[t], u[t], v[t])
+        for i, (m, a) in enumerate(zip(members, singles)):
+            assert [m.frame_features(t) for t in range(3)] == [a.frame_features(t) for t in range(3)], f"channel {i}"
+        big = next(i for i, sp in enumerate(specs) if sp.width == 3840 and sp.bit_depth == 8)
+        per, _ = oracle_sequence(frames[big][:1], oracle_config(members[big]))
+        assert_features_close(members[big].frame_features(0), per[0], where="2160p 8-bit channel, frame 0")
+    finally:
+        for a in members + singles:
+            a.close()
