@@ -153,3 +153,32 @@ def test_check_dct_matrix_rejects_with_reasons(libvca):
     m = np.full((6, 6), 64)
     with pytest.raises(libvca.VcaError):
         libvca.vca_check_dct_matrix(6, 8, m)
+
+
+def test_batch_frame_refs_marshalling(libvca):
+    # Batch.frame_refs builds the C tick argument on the host (no GPU involved): one entry per
+    # analyzer, plane pointers and byte pitches from the tensors, zeros for a skipped channel, and
+    # a length check so that the library never reads past the array.
+    import torch
+
+    vca = libvca
+    batch = vca.Batch.__new__(vca.Batch)
+    batch.analyzers = [object(), object()]
+    batch.handle = None
+    y8 = torch.zeros(2, 36, 64, dtype=torch.uint8)
+    u8 = torch.zeros(2, 18, 48, dtype=torch.uint8)
+    y16 = torch.zeros(2, 20, 32, dtype=torch.int16)
+    u16 = torch.zeros(2, 10, 32, dtype=torch.int16)
+    refs = batch.frame_refs([(y8[1], u8[1], u8[0]), (y16[0], u16[0], u16[1])])
+    assert isinstance(refs, ctypes.Array) and len(refs) == 2
+    assert (refs[0].y, refs[0].u, refs[0].v) == (y8[1].data_ptr(), u8[1].data_ptr(), u8[0].data_ptr())
+    assert (refs[0].pitch_y, refs[0].pitch_uv) == (64, 48)
+    assert (refs[1].pitch_y, refs[1].pitch_uv) == (64, 64)  # 16-bit samples: pitches in bytes
+    skipped = batch.frame_refs([None, (y16[0], u16[0], u16[1])])
+    assert skipped[0].y is None and skipped[0].pitch_y == 0
+    with pytest.raises(ValueError):
+        batch.frame_refs([(y8[0], u8[0], u8[1])])  # one frame for two analyzers
+    with pytest.raises(ValueError):
+        batch.frame_refs([(y8[0], u8[0], y16[0]), None])  # U and V pitches differ
+    with pytest.raises(ValueError):
+        batch.tick((vca.VcaFrameRef * 3)())  # a prepared argument of the wrong length
