@@ -1,20 +1,30 @@
 // Tensor-core form of the analyzer's per-block work (Section 2 of the paper: integer DCT of
 // every Y, U, V block, texture energy H and brightness L; Section 2 item (3): low-pass).
 //
-// Persistent kernel, one CTA of 28 warps per SM, specialised by warpgroup:
-//   warpgroup 0   warp 0: TMA producer (one 128x128 luma + two 64x64 chroma tiles per work item
-//                 into a 5-stage ring, 128-byte / 64-byte swizzled; 10-bit samples as 16-bit
-//                 words: two 64-sample luma boxes, 3 stages); warp 1: TMEM owner and
-//                 stage-1 MMA issuer; warp 2: stage-2 MMA issuer (tcgen05.mma kind::f16, FP32
-//                 accumulate), so neither stage waits on the other's epilogue;
-//   warpgroups 1, 6  convert (luma jobs, chroma jobs): raw samples -> stage-1 A operand in TMEM;
-//   warpgroups 2, 3  epilogue 1 (luma jobs, chroma jobs): stage-1 accumulators -> stage-2 A
-//                 operand in shared memory;
-//   warpgroups 4, 5  epilogue 2 (luma jobs, chroma jobs): stage-2 accumulators -> block
-//                 energies and brightness.
-// Each warpgroup has one warp per TMEM lane quarter.  Jobs flow through 8 TMEM slots (64 columns
-// each) and, per plane type, 2 shared-memory operand slots; every slot has a full and a free
-// mbarrier, so the roles run concurrently on different jobs.
+// Persistent kernel, one CTA of 28 warps per SM.  A work item is one 128x128 luma tile and the
+// two co-located 64x64 chroma tiles; it is processed as one unit (low-pass) or two units of half
+// its block rows (all coefficients).  Roles:
+//   warp 0        TMA producer: tiles in order into a ring (8-bit samples: 4 stages of one
+//                 128x128 luma box, 128-byte swizzle, and two 64x64 chroma boxes, 64-byte
+//                 swizzle; 10-bit samples as 16-bit words: 2 stages, the luma tile as two
+//                 64-sample boxes, all 128-byte swizzled), and each tile's record (frame,
+//                 position, distance to the frame's edges) into a ring in shared memory;
+//   warps 1-7     MMA issuers (tcgen05.mma kind::f16, FP32 accumulate), one thread each with fixed
+//                 streams: stage 1 of luma job 0, of luma job 1, of chroma; stage 2 of luma job 0,
+//                 of luma job 1, of the chroma hi and of the chroma lo operands.  A thread is held
+//                 for over a hundred cycles by every MMA it issues, however small, while MMAs
+//                 from different warps overlap in the tensor pipe, so the issue is spread out;
+//   warpgroup 2   convert luma, warpgroup 3 convert chroma: raw samples -> stage-1 A operands
+//                 in TMEM;
+//   warpgroup 4   epilogue 1 luma: stage-1 accumulators -> stage-2 A operand in shared memory,
+//                 and the stage-2 accumulator presets;
+//   warpgroup 5   epilogue 2 luma: stage-2 accumulators -> block energies and brightness;
+//   warpgroup 6   both chroma epilogues (chroma has half the luma work per unit).
+// Each role waits once per unit.  TMEM holds 2 stage-1 operand slots and 3 (low-pass) or 2
+// accumulator slots, shared memory 2 sets of stage-2 operands, so up to 3 units are in flight.
+// Every SM sub-partition runs warps of every role (each role spans the four TMEM lane quarters),
+// so its instruction cache holds the whole kernel: per-unit loops stay rolled and rare paths
+// (tiles on a frame's right edge) out of line.
 //
 // A "job" is 128 stage-2 rows: 8 (low-pass) or 4 luma 32x32 blocks, or 16 / 8 chroma 16x16
 // blocks.  Per job:
@@ -31,6 +41,8 @@
 //             pre-set by epilogue 1 to the magic constants of epilogue 2;
 //   epilogue2 Z = floor((256 S_hi + S_lo + 2^(s2-1)) / 2^s2) by two round-down FMAs, then
 //             H_v = sum_u w(u,v) |Z| in increasing u and an xor tree over v.
+// U and V share their MMAs: a U row and a V row lie side by side along K and the B operand holds
+// the chroma matrix in the U half of N for the U K-step and in the V half for the V K-step.
 // Every partial sum is an integer below 2^24 in magnitude (or in [2^23, 2^24) for the
 // pre-offset accumulators), so the FP32 tensor-core accumulation is exact and Z is
 // bit-identical to the integer definition; H uses the same FP32 order as the CUDA-core form.
@@ -56,12 +68,14 @@ namespace {
 
 using namespace ptx;
 
-constexpr int kMaxStages = 5;  // raw tile ring (barrier indices are laid out for the longest)
+constexpr int kMaxStages = 4;   // raw tile ring (barrier indices are laid out for the longest)
 constexpr int kA2L = 8192;      // one stage-2 operand (hi or lo) of one luma job: 128 rows x 32 K x fp16
 constexpr int kA2C = 4096;      // of one chroma job: 128 rows x 16 K x fp16
+constexpr int kA2Unit = 2 * 2 * kA2L + 2 * 2 * kA2C;  // a unit's: luma jobs 0-1, then U and V; hi, lo each
 constexpr int OFF_RAW = 0;
-constexpr int kBars = 80;
-constexpr int kA2Slots = 4;     // 0-1 luma jobs, 2-3 chroma jobs
+constexpr int kASlots = 2;      // stage-1 operand (A1) slots in TMEM
+constexpr int kA2Sets = 2;      // stage-2 operand sets in shared memory
+constexpr int kIssuers = 7;     // MMA-issuing threads (warps 1-7, lane 0)
 constexpr int kMaxMembers = kMaxBatchMembers;
 
 // One analyzer ("member") of a launch: its work items, geometry, outputs and stage-1 constants.
@@ -86,48 +100,55 @@ static_assert(sizeof(TcMember) % 8 == 0, "member table entries are copied as wor
 
 
 // Shared-memory layout for BPS bytes per sample.  8-bit: a 128x128 luma tile (128-byte rows,
-// 128-byte swizzle) and two 64x64 chroma tiles (64-byte rows and swizzle), 5 stages.  10-bit
+// 128-byte swizzle) and two 64x64 chroma tiles (64-byte rows and swizzle), 4 stages.  10-bit
 // (16-bit words): the luma tile as two 64-sample-wide boxes side by side (128-byte rows each,
-// 128-byte swizzle) and 64x64 chroma tiles with 128-byte rows and swizzle, 3 stages.
+// 128-byte swizzle) and 64x64 chroma tiles with 128-byte rows and swizzle, 2 stages.  Then two
+// sets of stage-2 operands, the DCT matrices as B operands and the stage-1 preset operands.
 template <int BPS>
 struct SmemLay {
   static_assert(BPS == 1 || BPS == 2, "one sample size per launch");
-  static constexpr int kStages = BPS == 1 ? 5 : 3;
+  static constexpr int kStages = BPS == 1 ? 4 : 2;
   static constexpr int kRawY = 128 * 128 * BPS;
   static constexpr int kRawC = 64 * 64 * BPS;
   static constexpr int kStageBytes = kRawY + 2 * kRawC;
-  static constexpr int OFF_A2 = kStages * kStageBytes;   // luma: 2 slots x (hi, lo)
-  static constexpr int OFF_A2C = OFF_A2 + 2 * 2 * kA2L;  // chroma: 2 slots x (hi, lo)
-  static constexpr int OFF_BL = OFF_A2C + 2 * 2 * kA2C;
-  static constexpr int OFF_BC = OFF_BL + 2048;
-  static constexpr int OFF_ONE = OFF_BC + 512;    // preset operand U (128 x 16)
-  static constexpr int OFF_KL = OFF_ONE + 4096;   // stage-1 preset operand K, luma (G N1 x 16)
-  static constexpr int OFF_KC = OFF_KL + 1024;    // and chroma
-  static constexpr int OFF_BAR = OFF_KC + 1024;
-  static constexpr int OFF_MISC = OFF_BAR + kBars * 8;
+  static constexpr int OFF_A2 = kStages * kStageBytes;         // kA2Sets x kA2Unit
+  static constexpr int OFF_BL = OFF_A2 + kA2Sets * kA2Unit;    // luma DCT matrix (32 x 32 fp16)
+  static constexpr int OFF_BCU = OFF_BL + 2048;                // chroma matrix in the U half of N (32 x 16)
+  static constexpr int OFF_BCV = OFF_BCU + 1024;               // and in the V half
+  static constexpr int OFF_ONE = OFF_BCV + 1024;               // preset operand U (128 x 16)
+  static constexpr int OFF_KL = OFF_ONE + 4096;                // preset operand K, luma (32 x 16)
+  static constexpr int OFF_KC = OFF_KL + 1024;                 // and chroma (32 x 16)
+  static constexpr int OFF_REC = OFF_KC + 1024;                // tile records (16 x 32 B)
+  static constexpr int OFF_BAR = OFF_REC + 16 * 32;
+  static constexpr int OFF_MISC = OFF_BAR + 48 * 8;
   static constexpr int kSmemBytes = OFF_MISC + 64 + 1024;  // + slack to align the base to 1024
-  static_assert(kStages <= kMaxStages && OFF_A2 % 1024 == 0 && kSmemBytes <= 232448, "layout");
+  static_assert(kStages <= kMaxStages && OFF_A2 % 1024 == 0 && kA2Unit % 1024 == 0 && kSmemBytes <= 232448,
+                "layout");
 };
 
-// TMEM layout: 8 job slots of 64 columns, each holding the stage-1 operand A1 at [0, 32), the
-// stage-1 accumulators D1 at [32, 64), and then the stage-2 accumulators D2 over [0, 32)
-// (low-pass) or [0, 64) (all coefficients) once stage 1 has consumed A1 and epilogue 1 has read
-// D1 into registers.
-constexpr int kSlots = 8;
-constexpr int kSlotCols = 64;
-constexpr int kD1Off = 32;
+// Stage-2 operand (hi; lo follows at +kA2L / +kA2C) of luma job j or chroma plane p of an operand set.
+__device__ __forceinline__ uint32_t a2_luma(uint32_t a2set, int j) { return a2set + j * 2 * kA2L; }
+__device__ __forceinline__ uint32_t a2_chroma(uint32_t a2set, int p) { return a2set + 4 * kA2L + p * 2 * kA2C; }
 
-// barrier indices
+// barrier indices: the raw ring; per A1 slot; per accumulator slot; per stage-2 operand set
 __host__ __device__ constexpr int b_raw_full(int s) { return s; }
 __host__ __device__ constexpr int b_raw_empty(int s) { return kMaxStages + s; }
-__host__ __device__ constexpr int b_slot_free(int s) { return 2 * kMaxStages + s; }
-__host__ __device__ constexpr int b_d1(int s) { return 2 * kMaxStages + kSlots + s; }
-__host__ __device__ constexpr int b_d2(int s) { return 2 * kMaxStages + 2 * kSlots + s; }
-__host__ __device__ constexpr int b_a1_full(int s) { return 2 * kMaxStages + 3 * kSlots + s; }
-__host__ __device__ constexpr int b_a2_full(int s) { return 2 * kMaxStages + 4 * kSlots + s; }
-__host__ __device__ constexpr int b_a2_free(int s) { return 2 * kMaxStages + 4 * kSlots + kA2Slots + s; }
-__host__ __device__ constexpr int b_drain(int i) { return 2 * kMaxStages + 4 * kSlots + 2 * kA2Slots + i; }
-static_assert(b_drain(1) < kBars, "barrier area");
+__host__ __device__ constexpr int b_a1l_full(int a) { return 8 + a; }    // convert luma -> stage-1 luma issuers
+__host__ __device__ constexpr int b_a1c_full(int a) { return 10 + a; }   // convert chroma -> stage-1 chroma issuer
+__host__ __device__ constexpr int b_a1l_free(int a) { return 12 + a; }   // stage-1 luma MMAs read A1
+__host__ __device__ constexpr int b_a1c_free(int a) { return 14 + a; }   // stage-1 chroma MMAs read A1
+__host__ __device__ constexpr int b_d1l(int d) { return 16 + d; }        // stage-1 luma MMAs done
+__host__ __device__ constexpr int b_d1c(int d) { return 19 + d; }        // stage-1 chroma MMAs done
+__host__ __device__ constexpr int b_a2l_full(int e) { return 22 + e; }   // epilogue 1 luma -> stage-2 issuers
+__host__ __device__ constexpr int b_a2c_full(int e) { return 24 + e; }   // epilogue 1 chroma -> stage-2 issuers
+__host__ __device__ constexpr int b_a2l_free(int e) { return 26 + e; }   // stage-2 luma MMAs read A2
+__host__ __device__ constexpr int b_a2c_free(int e) { return 28 + e; }   // stage-2 chroma MMAs read A2
+__host__ __device__ constexpr int b_d2l(int d) { return 30 + d; }        // stage-2 luma MMAs done
+__host__ __device__ constexpr int b_d2c(int d) { return 33 + d; }        // stage-2 chroma MMAs done
+__host__ __device__ constexpr int b_dfree(int d) { return 36 + d; }      // both epilogues 2 read the slot
+__host__ __device__ constexpr int b_drain(int i) { return 39 + i; }
+constexpr int kBars = 48;
+static_assert(b_drain(kIssuers - 1) < kBars, "barrier area");
 
 constexpr int kThreads = 896;
 constexpr uint32_t kTmemCols = 512;
@@ -166,14 +187,40 @@ struct PC {
   static constexpr int BPG2 = 128 / NK;           // blocks per job (128 stage-2 rows)
   static constexpr int G = BPG2 / BPG1;           // stage-1 groups per job
   static constexpr int JOBS = 16 / BPG2;          // jobs of this plane per tile
-  static constexpr int A1COLS = Nb / 2;           // TMEM columns of one group's A operand
 };
 
+// A unit: the whole tile (low-pass) or half its block rows (all coefficients): two luma jobs and
+// one job per chroma plane.  U and V share their MMAs: the chroma A operands put a U row and a V
+// row side by side along K, and the B operand holds the chroma matrix in the U half of N for the
+// U K-step and in the V half for the V K-step, so one accumulator holds U's coefficients and then
+// V's (no padding of N for the 8 low-pass chroma coefficients).  TMEM holds kASlots stage-1
+// operand slots and DS accumulator slots:
+//   A1 slot   luma group g (one block row) at 16 g; chroma group g at A1C + 16 g (U 8 columns,
+//             then V 8 columns);
+//   D slot    luma D1 group g at g N1, then D2 of job j: hi at 2 j N1, lo at (2 j + 1) N1;
+//             chroma D1 group g at DC + g NCC, then D2: hi at DC, lo at DC + NCC.
+// A D2 that overlaps a D1 is written by the epilogue-1 warpgroup of the same plane type after it
+// has read the whole D1.
 template <bool LP>
-struct Jobs {
+struct Unit {
   using L = PC<32, LP>;
-  using Cc = PC<16, LP>;
-  static constexpr int PER_TILE = L::JOBS + 2 * Cc::JOBS;
+  using C = PC<16, LP>;
+  static constexpr int UPT = LP ? 1 : 2;        // units per tile
+  static constexpr int UR = LP ? 4 : 2;         // luma block rows (= luma stage-1 groups) per unit
+  static constexpr int GC = UR / 2;             // chroma stage-1 groups per unit (two block rows each)
+  static constexpr int NKC = C::NK;             // chroma coefficients kept per dimension
+  static constexpr int NCC = 2 * NKC;           // chroma MMA N: U then V
+  static constexpr int A1C = 16 * UR;
+  static constexpr int A1COLS = A1C + 16 * GC;  // low-pass 96, all coefficients 48
+  static constexpr int DC = LP ? 64 : 128;
+  static constexpr int DCOLS = LP ? 96 : 192;
+  static constexpr int DS = LP ? 3 : 2;         // accumulator slots (units in flight)
+  static constexpr int DBASE = kASlots * A1COLS;
+  static_assert(DBASE + DS * DCOLS <= (int)kTmemCols, "TMEM columns");
+  static_assert(UR * L::N1 <= DC && 4 * L::N1 <= DC && DC + 2 * NCC <= DCOLS && DC + GC * NCC <= DCOLS, "D slot");
+  static_assert(L::JOBS == 2 * UPT && C::JOBS == UPT && L::G * 2 == UR && C::G == GC, "jobs per unit");
+  static __device__ __forceinline__ uint32_t a1(int a) { return (uint32_t)(a * A1COLS); }
+  static __device__ __forceinline__ uint32_t d(int ds) { return (uint32_t)(DBASE + ds * DCOLS); }
 };
 
 __device__ __forceinline__ uint64_t now_ns() {
@@ -208,9 +255,9 @@ __device__ __noinline__ bool wait_bar_slow(uint64_t* bar, uint32_t parity, volat
 // Bounded wait on barrier idx.  Roles on the critical path spin; the producer (sleep = true) lets
 // its thread sleep in hardware between polls.
 __device__ __forceinline__ bool wait_bar(const Ctl& c, int idx, uint32_t parity, int code, bool ignore_abort = false,
-                                         bool sleep = false) {
+                                         bool sleep = true) {
   uint64_t* bar = c.bars + idx;
-  if (mbar_try_wait(bar, parity)) return true;
+  if (sleep ? mbar_try_wait_sleep(bar, parity) : mbar_try_wait(bar, parity)) return true;
   return wait_bar_slow(bar, parity, c.abort, c.err, code, ignore_abort, sleep);
 }
 
@@ -229,6 +276,21 @@ __device__ __forceinline__ uint32_t raw_offset(int y, int xx) {
   return (uint32_t)(box * (Nb == 32 ? 128 : 64) * 128 + y * 128 + ((chunk ^ (y & 7)) << 4) + (cx & 7) * 2);
 }
 
+// Sample words of 16 samples of row y from column x, columns from w_rem on repeating the last one
+// (a frame's right edge).  Out of line: only edge tiles take it.
+template <int Nb, int BPS>
+__device__ __noinline__ void load_16_edge(uint32_t base, int y, int x, int w_rem, uint32_t* words) {
+  constexpr int NW = BPS == 1 ? 4 : 8;
+  for (int i = 0; i < NW; ++i) words[i] = 0;
+  for (int c = 0; c < 16; ++c) {
+    const int xx = min(x + c, w_rem - 1);
+    if (BPS == 1)
+      words[c >> 2] |= (uint32_t)lds_u8(base + raw_offset<Nb, 1>(y, xx)) << (8 * (c & 3));
+    else
+      words[c >> 1] |= (uint32_t)lds_u16(base + raw_offset<Nb, 2>(y, xx)) << (16 * (c & 1));
+  }
+}
+
 // Stage-1 operand conversion: 16 samples of this thread's row starting at column x (of the raw
 // tile, edge columns repeated past w_rem) -> 8 words of fp16 pairs (1024 + sample) in out.
 // 8-bit samples become fp16 0x6400 | x by one PRMT per two samples; 10-bit samples (below 1024)
@@ -245,13 +307,7 @@ __device__ __forceinline__ void convert_16(uint32_t base, int y, int x, int w_re
       words[2] = q.z;
       words[3] = q.w;
     } else {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) words[i] = 0;
-#pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        const uint32_t b = lds_u8(base + raw_offset<Nb, 1>(y, min(x + c, w_rem - 1)));
-        words[c >> 2] |= b << (8 * (c & 3));
-      }
+      load_16_edge<Nb, 1>(base, y, x, w_rem, words);
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -272,13 +328,7 @@ __device__ __forceinline__ void convert_16(uint32_t base, int y, int x, int w_re
       words[6] = q1.z;
       words[7] = q1.w;
     } else {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) words[i] = 0;
-#pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        const uint32_t v = lds_u16(base + raw_offset<Nb, 2>(y, min(x + c, w_rem - 1)));
-        words[c >> 1] |= v << (16 * (c & 1));
-      }
+      load_16_edge<Nb, 2>(base, y, x, w_rem, words);
     }
 #pragma unroll
     for (int i = 0; i < 8; ++i) out[i] = (words[i] & 0x03FF03FFu) | 0x64006400u;
@@ -290,104 +340,17 @@ __device__ __forceinline__ void fill_cols(uint32_t taddr, float first, float res
   tmem_fill<N>(taddr, __float_as_uint(first), __float_as_uint(rest));
 }
 
-// Block coordinates of one job for the epilogue that writes its results.
-struct JobCtx {
-  int plane;  // 0 Y, 1 U, 2 V
-  int jp;     // job index within the plane's tile
-  int f;      // frame
-  int tx, ty; // tile position (units of 4 blocks)
-};
-
-template <bool LP>
-__device__ __forceinline__ void plane_of(int j, int& plane, int& jp) {
-  constexpr int JL = PC<32, LP>::JOBS;
-  constexpr int JC = PC<16, LP>::JOBS;
-  if (j < JL) {
-    plane = 0;
-    jp = j;
-  } else if (j < JL + JC) {
-    plane = 1;
-    jp = j - JL;
-  } else {
-    plane = 2;
-    jp = j - JL - JC;
-  }
-}
-
-// Stage-2 operand slot of job j and its use count: each plane type cycles through its own two
-// slots, so every slot's full / free barriers see one in-order stream of jobs (a barrier is never
-// waited on more than one phase ahead of its current phase).
-template <bool LP>
-__device__ __forceinline__ void a2_slot_of(int j, int& slot, int& use) {
-  constexpr int JPT = Jobs<LP>::PER_TILE;
-  constexpr int JL = PC<32, LP>::JOBS;
-  const int t = j / JPT, r = j - t * JPT;
-  if (r < JL) {
-    const int idx = t * JL + r;
-    slot = idx & 1;
-    use = idx >> 1;
-  } else {
-    const int idx = t * (JPT - JL) + (r - JL);
-    slot = 2 + (idx & 1);
-    use = idx >> 1;
-  }
-}
-
-// Shared-memory address of the stage-2 operand (hi; lo follows at +kA2L / +kA2C).
-template <int BPS>
-__device__ __forceinline__ uint32_t a2_addr(uint32_t sbase, int a2) {
-  using SL = SmemLay<BPS>;
-  return a2 < 2 ? sbase + SL::OFF_A2 + a2 * 2 * kA2L : sbase + SL::OFF_A2C + (a2 - 2) * 2 * kA2C;
-}
-
-// ---- worker phases ----------------------------------------------------------
-
-// Writes the job's stage-1 A operand at ta1.
-template <int Nb, bool LP, int BPS>
-__device__ __forceinline__ void convert_job(const uint8_t* raw_plane, int jp, int h_rem, int w_rem, uint32_t ta1,
-                                            int q, int lane) {
-  using P = PC<Nb, LP>;
-  // The job's groups occupy G * A1COLS consecutive columns, stored 16 at a time (8 if fewer).
-  constexpr int COLS = P::G * P::A1COLS;
-  constexpr int ST = COLS < 16 ? COLS : 16;
-  const int l = 32 * q + lane;
-  const int bg = l / Nb;
-  const int r = l % Nb;
-  uint32_t out[ST];
-#pragma unroll
-  for (int g = 0; g < P::G; ++g) {
-    const int idx = jp * P::BPG2 + g * P::BPG1 + bg;
-    int y = (idx >> 2) * Nb + r;
-    if (y >= h_rem) y = h_rem - 1;
-    const int x = (idx & 3) * Nb;
-#pragma unroll
-    for (int c = 0; c < Nb / 16; ++c) {
-      const int col = g * P::A1COLS + 8 * c;  // first column of these 16 samples
-      convert_16<Nb, BPS>(smem_u32(raw_plane), y, x + 16 * c, w_rem, out + col % ST);
-      if ((col + 8) % ST == 0) tmem_st<ST>(ta1 + col + 8 - ST, out);
-    }
-  }
-}
-
-// Reads D1 (stage-1 accumulators at td1 + g*N1), writes the stage-2 operand to shared memory, and
-// pre-sets the stage-2 accumulators at td2 (hi) and td2 + N1 (lo), which may overlap D1.
+// Reads D1 (stage-1 accumulators at td1 + g*N1) and writes the stage-2 operand to shared memory.
 template <int Nb, bool LP>
-__device__ __forceinline__ void epilogue1(uint32_t td1, uint32_t td2, uint32_t a2hi, uint32_t a2lo, int q, int lane,
-                                          float s1inv, float hi0, float lo) {
+__device__ __forceinline__ void epilogue1(uint32_t td1, uint32_t a2hi, uint32_t a2lo, int q, int lane, float s1inv) {
   using P = PC<Nb, LP>;
   constexpr int NK = P::NK;
   const int l = 32 * q + lane;
   const int bg = l / Nb;
   const int r = l % Nb;
-  // D1 is read 16 columns at a time (bounds register use).  The stage-2 hi presets at [0, N1)
-  // never overlap D1 (at column kD1Off = 32); the lo presets at [N1, 2 N1) do when N1 = 32 (all
-  // coefficients, luma), so they are written after every column of D1 has been read.
-  constexpr int CH = NK < 16 ? NK : 16;
-  constexpr bool kLoOverD1 = 2 * P::N1 > kD1Off;
-  fill_cols<P::N1>(td2, hi0, kK1);
-  if (!kLoOverD1) fill_cols<P::N1>(td2 + P::N1, lo, lo);
+  constexpr int CH = NK < 8 ? NK : 8;  // D1 columns read at a time (bounds register use)
   const uint32_t rowoff = (uint32_t)((r >> 3) * 2048 + (r & 7) * 128);
-#pragma unroll
+#pragma unroll 1
   for (int g = 0; g < P::G; ++g) {
 #pragma unroll
     for (int h0 = 0; h0 < NK; h0 += CH) {
@@ -413,39 +376,26 @@ __device__ __forceinline__ void epilogue1(uint32_t td1, uint32_t td2, uint32_t a
       }
     }
   }
-  if (kLoOverD1) fill_cols<P::N1>(td2 + P::N1, lo, lo);
 }
 
-template <int Nb, bool LP, bool DUMP>
-__device__ __forceinline__ void epilogue2(int16_t* const* zdump, const TcMember& M, uint32_t td2, const JobCtx& jc,
-                                          int q, int lane,
-                                          const float (&wts)[PC<Nb, LP>::NK], float einv, float c2,
-                                          uint64_t* slot_free) {
+// Reads this thread's stage-2 accumulators (hi at td2, lo at td2 + LO), forms Z, the row sums of
+// w(u, v) |Z| in increasing u and the block energy H by an xor tree over the NK rows of the block;
+// the block's v = 0 thread stores H at out[0] and L = sqrt(Z(0,0)) at out[C] (out null: block outside
+// the frame).  DUMP: the coefficients to zd (u-major) as well.
+template <int Nb, bool LP, bool DUMP, int LO>
+__device__ __forceinline__ void epilogue2(uint32_t td2, int lane, const float (&wts)[PC<Nb, LP>::NK], float einv,
+                                          float c2, float* out, int64_t C, int16_t* zd) {
   using P = PC<Nb, LP>;
   constexpr int NK = P::NK;
-  constexpr int HALF = NK > 16 ? 8 : NK;  // columns loaded at a time (bounds register use)
-  const int m = 32 * q + lane;
-  const int b2 = m / NK;
-  const int v = m % NK;
-  const int idx = jc.jp * P::BPG2 + b2;
-  const int bx = jc.tx * 4 + (idx & 3);
-  const int by = jc.ty * 4 + (idx >> 2);
-  const bool valid = bx < M.nbx && by < M.nby;
-  const int64_t k = (int64_t)by * M.nbx + bx;
-  int16_t* zd = nullptr;
-  if (DUMP) zd = (valid && jc.f == 0) ? zdump[jc.plane] + k * NK * NK : nullptr;
+  constexpr int HALF = NK > 8 ? 8 : NK;  // columns loaded at a time (bounds register use)
+  const int v = lane % NK;
   float H = 0.0f, z00 = 0.0f;
 #pragma unroll
   for (int h0 = 0; h0 < NK; h0 += HALF) {
     uint32_t hi[HALF], lo[HALF];
     tmem_ld<HALF>(td2 + h0, hi);
-    tmem_ld<HALF>(td2 + P::N1 + h0, lo);
+    tmem_ld<HALF>(td2 + LO + h0, lo);
     tmem_wait_ld();
-    if (h0 + HALF == NK) {  // every accumulator of the slot is in registers: hand the slot back
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(slot_free);
-    }
 #pragma unroll
     for (int uu = 0; uu < HALF; ++uu) {
       const int u = h0 + uu;
@@ -458,10 +408,9 @@ __device__ __forceinline__ void epilogue2(int16_t* const* zdump, const TcMember&
   }
 #pragma unroll
   for (int o = NK / 2; o > 0; o >>= 1) H += __shfl_xor_sync(0xffffffffu, H, o);
-  if (valid && v == 0) {
-    float* out = M.blockvals + (int64_t)jc.f * M.out_fstride + (2 * jc.plane) * M.C + k;
+  if (out && v == 0) {
     out[0] = H;
-    out[M.C] = __fsqrt_rn(z00);
+    out[C] = __fsqrt_rn(z00);
   }
 }
 
@@ -528,145 +477,428 @@ __device__ __forceinline__ TileInfo tile_info(const MS& ms, int t, int item0, in
   return ti;
 }
 
-// ---- role loops (one instantiation per plane type) -------------------------------
+// ---- role loops ---------------------------------------------------------------------
 //
-// Jobs are numbered jj = t * JPT + r (tile t of this CTA, r < JPT): luma jobs first, then U,
-// then V.  Job jj lives in TMEM slot jj % kSlots; each role visits only its plane type's jobs.
+// Unit u of this CTA (tile u / UPT, half u % UPT) uses A1 slot u % 2, accumulator slot u % DS
+// and stage-2 operand set u % 2.  A slot's barriers complete once per use, so a wait for unit u
+// is on the parity of the number of earlier uses of that slot.
 
-template <int Nb, bool LP>
-__device__ __forceinline__ void plane_jobs(int& r0, int& r1) {
-  constexpr int JL = PC<32, LP>::JOBS;
-  r0 = Nb == 32 ? 0 : JL;
-  r1 = Nb == 32 ? JL : Jobs<LP>::PER_TILE;
+// Slot cursor: the slot of the current unit and the parity of its use count.
+template <int N>
+struct Cursor {
+  int slot = 0;
+  uint32_t par = 0;
+  __device__ __forceinline__ void next() {
+    if (++slot == N) {
+      slot = 0;
+      par ^= 1u;
+    }
+  }
+};
+
+// A tile as the roles see it, written once by the producer into a ring of kTileRecs entries
+// (entry t % kTileRecs for the CTA's tile t) before it issues the tile's copies.  The ring is
+// deep enough: the producer runs at most kStages tiles ahead of the convert warps, which run at
+// most kASlots + DS units ahead of the last epilogue.
+struct TileRec {
+  int f, tx, ty, m;    // frame, tile position (units of 4 blocks), member
+  int hy, wy, hc, wc;  // luma / chroma rows and columns from the tile's origin to the frame's edge
+};
+constexpr int kTileRecs = 16;
+static_assert(sizeof(TileRec) == 32, "two 16-byte loads");
+
+__device__ __forceinline__ TileRec load_rec(const TileRec* ring, int t) {
+  const uint32_t a = smem_u32(ring + (t & (kTileRecs - 1)));
+  const uint4 x = lds128(a), y = lds128(a + 16);
+  return TileRec{(int)x.x, (int)x.y, (int)x.z, (int)x.w, (int)y.x, (int)y.y, (int)y.z, (int)y.w};
 }
 
-// Convert: raw samples of the tile -> stage-1 A operand in TMEM (and the D1 presets).
-template <int Nb, bool LP, int BPS, class MS>
-__device__ void convert_loop(const MS& ms, const Ctl& ctl, uint8_t* sm, uint32_t tq, int n_items, int item0,
-                             int step, int q, int lane) {
+// 32 samples (8-bit) from two 16-sample chunks -> 16 words of fp16 pairs (1024 + x).
+__device__ __forceinline__ void convert_32_u8(uint32_t addr0, uint32_t addr1, uint32_t (&out)[16]) {
+  const uint4 a = lds128(addr0), b = lds128(addr1);
+  const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    out[2 * i] = prmt(w[i], kSel6464, 0x5140);
+    out[2 * i + 1] = prmt(w[i], kSel6464, 0x5342);
+  }
+}
+
+// Convert, luma: the unit's block rows of the raw luma tile -> stage-1 A operands in TMEM (thread
+// 32 q + lane converts row `lane` of block q of each block row).
+template <bool LP, int BPS>
+__device__ void convert_luma_loop(const TileRec* recs, const Ctl& ctl, uint8_t* sm, uint32_t tq, int n_items, int q,
+                                  int lane) {
   using SL = SmemLay<BPS>;
-  constexpr int JPT = Jobs<LP>::PER_TILE;
-  constexpr int T = 4 * Nb;  // tile edge of this plane in samples
-  int r0, r1;
-  plane_jobs<Nb, LP>(r0, r1);
-  const int per_tile = r1 - r0;
-  TileInfo ti{};
-  int h_rem = 0, w_rem = 0;
-  const int n = n_items * per_tile;
-  for (int k = 0, t = 0, r = r0; k < n; ++k) {
-    if (r == r0) {
-      ti = tile_info(ms, t, item0, step, SL::kStages);
-      const TcMember& M = ms[ti.m];
-      h_rem = (Nb == 32 ? M.H : M.ch) - ti.ty * T;
-      w_rem = (Nb == 32 ? M.W : M.cw) - ti.tx * T;
-      if (!wait_bar(ctl, b_raw_full(ti.stage), (t / SL::kStages) & 1, 4)) return;
+  using U = Unit<LP>;
+  int hy = 0, wy = 0, stage = 0;
+  bool inside = false;
+  // Byte offsets of this thread's two 16-sample chunks within a block row (8-bit, 128-byte swizzle).
+  const uint32_t off0 = (uint32_t)(lane * 128 + (((2 * q) ^ (lane & 7)) << 4));
+  const uint32_t off1 = (uint32_t)(lane * 128 + (((2 * q + 1) ^ (lane & 7)) << 4));
+  Cursor<kASlots> ca;
+  const int n = n_items * U::UPT;
+  for (int u = 0, t = 0, h = 0; u < n; ++u, ca.next()) {
+    if (h == 0) {
+      stage = t % SL::kStages;
+      if (!wait_bar(ctl, b_raw_full(stage), (t / SL::kStages) & 1, 4)) return;
+      const TileRec r = load_rec(recs, t);
+      hy = r.hy;
+      wy = r.wy;
+      inside = hy >= 128 && wy >= 128;
     }
-    const int jj = t * JPT + r;
-    int plane, jp;
-    plane_of<LP>(r, plane, jp);
-    const int slot = jj % kSlots;
-    if (jj >= kSlots && !wait_bar(ctl, b_slot_free(slot), ((jj / kSlots) - 1) & 1, 4)) return;
+    if (u >= kASlots && !wait_bar(ctl, b_a1l_free(ca.slot), ca.par ^ 1u, 4)) return;
     tc_fence_after();
-    // Plane offsets within the stage follow the member's sample size (the stage fits the largest).
-    const uint8_t* raw =
-        sm + OFF_RAW + ti.stage * SL::kStageBytes + (plane == 0 ? 0 : SL::kRawY + (plane - 1) * SL::kRawC);
-    const uint32_t ta = tq + slot * kSlotCols;
-    convert_job<Nb, LP, BPS>(raw, jp, h_rem, w_rem, ta, q, lane);
+    const uint32_t rbase = smem_u32(sm + OFF_RAW + stage * SL::kStageBytes);
+    const uint32_t ta = tq + U::a1(ca.slot);
+#pragma unroll 1
+    for (int gl = 0; gl < U::UR; ++gl) {
+      const int brow = h * U::UR + gl;
+      uint32_t out[16];
+      if (BPS == 1 && inside) {
+        const uint32_t rb = rbase + (uint32_t)(brow * 4096);
+        convert_32_u8(rb + off0, rb + off1, out);
+      } else {
+        int y = brow * 32 + lane;
+        if (y >= hy) y = hy - 1;
+        convert_16<32, BPS>(rbase, y, 32 * q, wy, out);
+        convert_16<32, BPS>(rbase, y, 32 * q + 16, wy, out + 8);
+      }
+      tmem_st<16>(ta + 16 * gl, out);
+    }
     tmem_wait_st();
     tc_fence_before();
     __syncwarp();
-    const bool last = r == r1 - 1;
+    const bool last = h == U::UPT - 1;
     if (lane == 0) {
-      mbar_arrive(&ctl.bars[b_a1_full(slot)]);
-      if (last) mbar_arrive(&ctl.bars[b_raw_empty(ti.stage)]);
+      mbar_arrive(&ctl.bars[b_a1l_full(ca.slot)]);
+      if (last) mbar_arrive(&ctl.bars[b_raw_empty(stage)]);
     }
     if (last) {
-      r = r0;
+      h = 0;
       ++t;
     } else {
-      ++r;
+      ++h;
     }
   }
 }
 
-// Epilogue 1: T = floor(T'/2^s1) into the stage-2 operand (hi and lo bytes as fp16, MN-major;
-// s1 = log2 N + B - 9), and the stage-2 accumulators pre-set: hi starts at K1 - 1156 * 64 * N for
-// u = 0 (the 1024 + byte encoding of both halves and the +128 offset of the hi byte) and K1
-// otherwise, lo at 2^(s2-1) (luma N = 32: s2 = 11; chroma N = 16: s2 = 10).  Each plane type
-// cycles through its own two stage-2 operand slots, so every slot's full / free barriers see one
-// in-order stream of jobs.
-template <int Nb, bool LP, int BPS, class MS>
-__device__ void epi1_loop(const MS& ms, const Ctl& ctl, uint32_t sbase, uint32_t tq, int n_items, int item0,
-                          int step, int q, int lane) {
+// Convert, chroma: the unit's chroma groups (8 blocks x 16 rows each) of U and V -> stage-1 A
+// operands, a U row and a V row side by side (thread 32 q + lane converts row lane % 16 of
+// block (32 q + lane) / 16 of the group in both planes).
+template <bool LP, int BPS>
+__device__ void convert_chroma_loop(const TileRec* recs, const Ctl& ctl, uint8_t* sm, uint32_t tq, int n_items, int q,
+                                    int lane) {
   using SL = SmemLay<BPS>;
-  constexpr int JPT = Jobs<LP>::PER_TILE;
-  const float s1inv = __int_as_float((127 - s1_of<Nb>(BPS)) << 23);  // 2^-s1
-  const float hi0 = Nb == 32 ? kK1 - 2367488.0f : kK1 - 1183744.0f;
-  const float lo = Nb == 32 ? 1024.0f : 512.0f;
-  const uint32_t lo_off = Nb == 32 ? kA2L : kA2C;
-  const uint32_t a2base = Nb == 32 ? sbase + SL::OFF_A2 : sbase + SL::OFF_A2C;
-  const int a2first = Nb == 32 ? 0 : 2;
-  int r0, r1;
-  plane_jobs<Nb, LP>(r0, r1);
-  const int n = n_items * (r1 - r0);
-  for (int use = 0, t = 0, r = r0; use < n; ++use) {  // use: jobs of this plane type so far
-    const int jj = t * JPT + r;
-    const int slot = jj % kSlots;
-    const int a2 = use & 1;
-    if (!wait_bar(ctl, b_d1(slot), (jj / kSlots) & 1, 4, false, true)) return;
-    if (use >= 2 && !wait_bar(ctl, b_a2_free(a2first + a2), ((use >> 1) - 1) & 1, 4, false, true)) return;
+  using U = Unit<LP>;
+  int hc = 0, wc = 0, stage = 0;
+  bool inside = false;
+  const int l = 32 * q + lane;
+  const int bg = l >> 4, r = l & 15;
+  // 8-bit, 64-byte rows and swizzle: row y of this thread's block, chunk (block column) bg & 3
+  const uint32_t coff = (uint32_t)((((bg >> 2) * 16 + r) * 64) + (((bg & 3) ^ ((r >> 1) & 3)) << 4));
+  Cursor<kASlots> ca;
+  const int n = n_items * U::UPT;
+  for (int u = 0, t = 0, h = 0; u < n; ++u, ca.next()) {
+    if (h == 0) {
+      stage = t % SL::kStages;
+      if (!wait_bar(ctl, b_raw_full(stage), (t / SL::kStages) & 1, 4)) return;
+      const TileRec rr = load_rec(recs, t);
+      hc = rr.hc;
+      wc = rr.wc;
+      inside = hc >= 64 && wc >= 64;
+    }
+    if (u >= kASlots && !wait_bar(ctl, b_a1c_free(ca.slot), ca.par ^ 1u, 4)) return;
     tc_fence_after();
-    const uint32_t ahi = a2base + a2 * 2 * lo_off;
-    const uint32_t td = tq + slot * kSlotCols;
-    epilogue1<Nb, LP>(td + kD1Off, td, ahi, ahi + lo_off, q, lane, s1inv, hi0, lo);
+    const uint32_t raw = smem_u32(sm + OFF_RAW + stage * SL::kStageBytes + SL::kRawY);
+    const uint32_t ta = tq + U::a1(ca.slot) + U::A1C;
+#pragma unroll 1
+    for (int g = 0; g < U::GC; ++g) {
+      const int gt = h * U::GC + g;  // group within the chroma tile (two block rows)
+      uint32_t out[16];
+      if (BPS == 1 && inside) {
+        const uint32_t a = raw + (uint32_t)(gt * 2048) + coff;
+        convert_32_u8(a, a + SL::kRawC, out);
+      } else {
+        const int idx = 8 * gt + bg;
+        int y = (idx >> 2) * 16 + r;
+        if (y >= hc) y = hc - 1;
+        const int x = (idx & 3) * 16;
+        convert_16<16, BPS>(raw, y, x, wc, out);
+        convert_16<16, BPS>(raw + SL::kRawC, y, x, wc, out + 8);
+      }
+      tmem_st<16>(ta + 16 * g, out);
+    }
+    tmem_wait_st();
+    tc_fence_before();
+    __syncwarp();
+    const bool last = h == U::UPT - 1;
+    if (lane == 0) {
+      mbar_arrive(&ctl.bars[b_a1c_full(ca.slot)]);
+      if (last) mbar_arrive(&ctl.bars[b_raw_empty(stage)]);
+    }
+    if (last) {
+      h = 0;
+      ++t;
+    } else {
+      ++h;
+    }
+  }
+}
+
+// Epilogue 1 luma: T = floor(T'/2^s1) of both luma jobs into the stage-2 operands (hi and lo bytes
+// as fp16, MN-major; s1 = log2 N + B - 9), then the stage-2 accumulators pre-set: hi starts at
+// K1 - 1156 * 64 * N for u = 0 (the 1024 + byte encoding of both halves and the +128 offset of the
+// hi byte) and K1 otherwise, lo at 2^(s2-1) (N = 32: s2 = 11).
+template <bool LP, int BPS>
+__device__ void epi1_luma_loop(const Ctl& ctl, uint32_t sbase, uint32_t tq, int n_items, int q, int lane) {
+  using SL = SmemLay<BPS>;
+  using U = Unit<LP>;
+  using P = PC<32, LP>;
+  const float s1inv = __int_as_float((127 - s1_of<32>(BPS)) << 23);  // 2^-s1
+  Cursor<U::DS> cd;
+  Cursor<kA2Sets> ce;
+  const int n = n_items * U::UPT;
+  for (int u = 0; u < n; ++u, cd.next(), ce.next()) {
+    if (!wait_bar(ctl, b_d1l(cd.slot), cd.par, 4)) return;
+    if (u >= kA2Sets && !wait_bar(ctl, b_a2l_free(ce.slot), ce.par ^ 1u, 4)) return;
+    tc_fence_after();
+    const uint32_t td = tq + U::d(cd.slot);
+    const uint32_t a2 = sbase + SL::OFF_A2 + (uint32_t)(ce.slot * kA2Unit);
+#pragma unroll 1
+    for (int j = 0; j < 2; ++j) {
+      const uint32_t ahi = a2_luma(a2, j);
+      epilogue1<32, LP>(td + j * P::G * P::N1, ahi, ahi + kA2L, q, lane, s1inv);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {  // D2 overlaps D1: written after every D1 column was read
+      fill_cols<P::N1>(td + 2 * j * P::N1, kK1 - 2367488.0f, kK1);
+      fill_cols<P::N1>(td + (2 * j + 1) * P::N1, 1024.0f, 1024.0f);
+    }
     tmem_wait_st();
     fence_proxy_async_smem();
     tc_fence_before();
     __syncwarp();
-    if (lane == 0) mbar_arrive(&ctl.bars[b_a2_full(a2first + a2)]);
-    if (++r == r1) {
-      r = r0;
+    if (lane == 0) mbar_arrive(&ctl.bars[b_a2l_full(ce.slot)]);
+  }
+}
+
+// Output address of this thread's block values: block index k of the block that row m = 32 q + lane of
+// job jp of an N-point plane covers (NK stage-2 rows per block), or -1 outside the frame.
+template <int NK, int BPG2>
+__device__ __forceinline__ int64_t block_of(const TcMember& M, const TileRec& r, int jp, int q, int lane) {
+  const int idx = jp * BPG2 + (32 * q + lane) / NK;
+  const int bx = r.tx * 4 + (idx & 3), by = r.ty * 4 + (idx >> 2);
+  return (bx < M.nbx && by < M.nby) ? (int64_t)by * M.nbx + bx : -1;
+}
+
+// Epilogue 2 luma: Z, the block energy H and brightness L of both luma jobs, then the slot's luma
+// columns are handed back.
+template <bool LP, bool DUMP, class PP, class MS>
+__device__ void epi2_luma_loop(const PP& p, const MS& ms, const TileRec* recs, const Ctl& ctl, uint32_t tq,
+                               int n_items, int q, int lane) {
+  using P = PC<32, LP>;
+  using U = Unit<LP>;
+  float w[P::NK];
+#pragma unroll
+  for (int uu = 0; uu < P::NK; ++uu) w[uu] = p.W_y[uu * 32 + (lane % P::NK)];
+  Cursor<U::DS> cd;
+  const int n = n_items * U::UPT;
+  TileRec rec{};
+  for (int u = 0, t = 0, h = 0; u < n; ++u, cd.next()) {
+    if (!wait_bar(ctl, b_d2l(cd.slot), cd.par, 4)) return;
+    tc_fence_after();
+    if (h == 0) rec = load_rec(recs, t);  // written by the producer before this unit's copies
+    const TcMember& M = ms[rec.m];
+    const uint32_t td = tq + U::d(cd.slot);
+    float* const base = M.blockvals + (int64_t)rec.f * M.out_fstride;
+#pragma unroll 1
+    for (int j = 0; j < 2; ++j) {
+      const int64_t k = block_of<P::NK, P::BPG2>(M, rec, h * 2 + j, q, lane);
+      int16_t* zd = (DUMP && k >= 0 && rec.f == 0) ? p.zdump[0] + k * P::NK * P::NK : nullptr;
+      epilogue2<32, LP, DUMP, P::N1>(td + 2 * j * P::N1, lane, w, 0.125f, kK1 - kK1 / 8.0f,
+                                     k >= 0 ? base + k : nullptr, M.C, zd);
+    }
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&ctl.bars[b_dfree(cd.slot)]);
+    if (++h == U::UPT) {
+      h = 0;
       ++t;
     }
   }
 }
 
-// Epilogue 2: Z, the block energy H and brightness L, for every job of one plane type.
-template <int Nb, bool LP, bool DUMP, class PP, class MS>
-__device__ void epi2_loop(const PP& p, const MS& ms, const Ctl& ctl, uint32_t tq, int n_items, int item0,
-                          int step, int q, int lane) {
-  using P = PC<Nb, LP>;
-  constexpr int JPT = Jobs<LP>::PER_TILE;
-  const float* Wt = Nb == 32 ? p.W_y : p.W_c;
+// Chroma epilogues, one warpgroup: for unit u, epilogue 1 (as for luma, both planes: s2 = 10,
+// presets K1 - 1156 * 64 * 16 on each plane's u = 0 column, 512 for lo), then epilogue 2 of
+// unit u - 1.
+template <bool LP, bool DUMP, int BPS, class PP, class MS>
+__device__ void chroma_epi_loop(const PP& p, const MS& ms, const TileRec* recs, const Ctl& ctl, uint32_t sbase,
+                                uint32_t tq, int n_items, int q, int lane) {
+  using SL = SmemLay<BPS>;
+  using U = Unit<LP>;
+  using P = PC<16, LP>;
+  constexpr int NKC = U::NKC, NCC = U::NCC;
+  const float s1inv = __int_as_float((127 - s1_of<16>(BPS)) << 23);
   float w[P::NK];
 #pragma unroll
-  for (int u = 0; u < P::NK; ++u) w[u] = Wt[u * Nb + (lane % P::NK)];
-  const float einv = Nb == 32 ? 0.125f : 0.25f;
-  const float c2 = Nb == 32 ? kK1 - kK1 / 8.0f : kK1 - kK1 / 4.0f;
-  int r0, r1;
-  plane_jobs<Nb, LP>(r0, r1);
-  const int n = n_items * (r1 - r0);
-  JobCtx jc{};
-  int m = 0;
-  for (int k = 0, t = 0, r = r0; k < n; ++k) {
-    if (r == r0) {
-      const TileInfo ti = tile_info(ms, t, item0, step);
-      jc.f = ti.f;
-      jc.tx = ti.tx;
-      jc.ty = ti.ty;
-      m = ti.m;
+  for (int uu = 0; uu < P::NK; ++uu) w[uu] = p.W_c[uu * 16 + (lane % P::NK)];
+  // hi presets of both planes side by side: the u = 0 column of U and of V start lower
+  uint32_t hip[NCC];
+#pragma unroll
+  for (int c = 0; c < NCC; ++c) hip[c] = __float_as_uint(c % NKC == 0 ? kK1 - 1183744.0f : kK1);
+  Cursor<U::DS> cd, cd2;
+  Cursor<kA2Sets> ce;
+  const int n = n_items * U::UPT;
+  TileRec rec{};
+  for (int u = 0, t = 0, h = 0; u <= n; ++u) {
+    if (u < n) {  // epilogue 1 of unit u
+      if (!wait_bar(ctl, b_d1c(cd.slot), cd.par, 4)) return;
+      if (u >= kA2Sets && !wait_bar(ctl, b_a2c_free(ce.slot), ce.par ^ 1u, 4)) return;
+      tc_fence_after();
+      const uint32_t td = tq + U::d(cd.slot) + U::DC;
+      const uint32_t a2 = sbase + SL::OFF_A2 + (uint32_t)(ce.slot * kA2Unit);
+#pragma unroll 1
+      for (int pl = 0; pl < 2; ++pl) {
+        const uint32_t ahi = a2_chroma(a2, pl);
+        epilogue1<16, LP>(td + pl * NKC, ahi, ahi + kA2C, q, lane, s1inv);
+      }
+      tmem_st<NCC>(td, hip);
+      fill_cols<NCC>(td + NCC, 512.0f, 512.0f);
+      tmem_wait_st();
+      fence_proxy_async_smem();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ctl.bars[b_a2c_full(ce.slot)]);
+      cd.next();
+      ce.next();
     }
-    const int jj = t * JPT + r;
-    const int slot = jj % kSlots;
-    plane_of<LP>(r, jc.plane, jc.jp);
-    if (!wait_bar(ctl, b_d2(slot), (jj / kSlots) & 1, 4, false, true)) return;
-    tc_fence_after();
-    epilogue2<Nb, LP, DUMP>(p.zdump, ms[m], tq + slot * kSlotCols, jc, q, lane, w, einv, c2,
-                            &ctl.bars[b_slot_free(slot)]);
-    if (++r == r1) {
-      r = r0;
-      ++t;
+    if (u >= 1) {  // epilogue 2 of unit u - 1
+      if (!wait_bar(ctl, b_d2c(cd2.slot), cd2.par, 4)) return;
+      tc_fence_after();
+      if (h == 0) rec = load_rec(recs, t);
+      const TcMember& M = ms[rec.m];
+      const uint32_t td = tq + U::d(cd2.slot) + U::DC;
+      const int64_t k = block_of<P::NK, P::BPG2>(M, rec, h, q, lane);  // U and V share the block
+      float* const base = M.blockvals + (int64_t)rec.f * M.out_fstride;
+#pragma unroll 1
+      for (int pl = 0; pl < 2; ++pl) {
+        int16_t* zd = (DUMP && k >= 0 && rec.f == 0) ? p.zdump[1 + pl] + k * P::NK * P::NK : nullptr;
+        epilogue2<16, LP, DUMP, NCC>(td + pl * NKC, lane, w, 0.25f, kK1 - kK1 / 4.0f,
+                                     k >= 0 ? base + (2 + 2 * pl) * M.C + k : nullptr, M.C, zd);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ctl.bars[b_dfree(cd2.slot)]);
+      cd2.next();
+      if (++h == U::UPT) {
+        h = 0;
+        ++t;
+      }
     }
+  }
+}
+
+// MMA issue: issuer id owns stage 1 of luma job 0 (id 0) or 1 (id 1), stage 1 of chroma (id 2),
+// stage 2 of luma job 0 (3) or 1 (4), of the chroma hi (5) or lo (6) operands.  Stage-1 issuers
+// wait for the unit's A1 and, from the DS-th unit on, for its accumulator slot; they commit to the
+// slot's D1 barrier and to the A1 slot's free barrier.  Stage-2 issuers wait for the operand set
+// and commit to the slot's D2 barrier and the set's free barrier.  Barriers count one commit per
+// issuer of the plane type.  Descriptors are built once; per unit only the slot offsets change.
+template <bool LP, int BPS>
+__device__ void issuer_loop(const Ctl& ctl, uint32_t sbase, uint32_t tmem, int id, int n_items) {
+  using SL = SmemLay<BPS>;
+  using U = Unit<LP>;
+  using L = PC<32, LP>;
+  constexpr int NCC = U::NCC;
+  const uint64_t bl0 = smem_desc(sbase + SL::OFF_BL, 128, 512, 0), bl1 = smem_desc(sbase + SL::OFF_BL + 256, 128, 512, 0);
+  const uint64_t dbu = smem_desc(sbase + SL::OFF_BCU, 128, 256, 0), dbv = smem_desc(sbase + SL::OFF_BCV, 128, 256, 0);
+  const uint64_t du = smem_desc(sbase + SL::OFF_ONE, 128, 256, 0);
+  const int n = n_items * U::UPT;
+  Cursor<kASlots> ca;
+  Cursor<U::DS> cd;
+  Cursor<kA2Sets> ce;
+  bool ok = true;
+  if (id < 3) {
+    const uint64_t dk = smem_desc(sbase + (id < 2 ? SL::OFF_KL : SL::OFF_KC), 128, 256, 0);
+    const uint32_t aoff = id < 2 ? (uint32_t)(id * 16 * L::G) : (uint32_t)U::A1C;
+    const uint32_t doff = id < 2 ? (uint32_t)(id * L::G * L::N1) : (uint32_t)U::DC;
+    for (int u = 0; u < n; ++u, ca.next(), cd.next()) {
+      if (!wait_bar(ctl, id < 2 ? b_a1l_full(ca.slot) : b_a1c_full(ca.slot), ca.par, 2) ||
+          (u >= U::DS && !wait_bar(ctl, b_dfree(cd.slot), cd.par ^ 1u, 2))) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a = tmem + U::a1(ca.slot) + aoff, d = tmem + U::d(cd.slot) + doff;
+      // D1 = U x K^T (presets of the stream's columns), then D1 += A1 (TMEM) x M^T.
+      if (id < 2) {
+        mma_ss(d, du, dk, idesc_f16(128, L::G * L::N1, 0, 0), 0);
+        // K-step outer: consecutive MMAs write different accumulators.
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+          for (int gg = 0; gg < L::G; ++gg)
+            mma_ts(d + gg * L::N1, a + gg * 16 + ks * 8, ks ? bl1 : bl0, idesc_f16(128, L::N1, 0, 0), 1);
+        mma_commit(&ctl.bars[b_d1l(cd.slot)]);
+        mma_commit(&ctl.bars[b_a1l_free(ca.slot)]);
+      } else {
+        mma_ss(d, du, dk, idesc_f16(128, U::GC * NCC, 0, 0), 0);
+#pragma unroll
+        for (int g = 0; g < U::GC; ++g) {
+          mma_ts(d + g * NCC, a + 16 * g, dbu, idesc_f16(128, NCC, 0, 0), 1);      // U row against the U half
+          mma_ts(d + g * NCC, a + 16 * g + 8, dbv, idesc_f16(128, NCC, 0, 0), 1);  // V row against the V half
+        }
+        mma_commit(&ctl.bars[b_d1c(cd.slot)]);
+        mma_commit(&ctl.bars[b_a1c_free(ca.slot)]);
+      }
+    }
+  } else {
+    // D2 += A2 (smem, MN-major) x M^T (D2 pre-set by epilogue 1); descriptors of operand set 0,
+    // set 1 is kA2Unit bytes further.
+    const bool luma = id < 5;
+    const int j = id - 3;
+    const uint32_t lo = id == 6 ? 1u : 0u;
+    const uint32_t a2 = sbase + SL::OFF_A2;
+    uint64_t ad[4];
+    if (luma) {
+      const uint32_t ahi = a2_luma(a2, j);
+      ad[0] = smem_desc(ahi, 1024, 2048, 2);
+      ad[1] = smem_desc(ahi + kA2L, 1024, 2048, 2);
+      ad[2] = smem_desc(ahi + 4096, 1024, 2048, 2);
+      ad[3] = smem_desc(ahi + kA2L + 4096, 1024, 2048, 2);
+    } else {
+      ad[0] = smem_desc(a2_chroma(a2, 0) + lo * kA2C, 1024, 2048, 2);
+      ad[1] = smem_desc(a2_chroma(a2, 1) + lo * kA2C, 1024, 2048, 2);
+      ad[2] = ad[3] = 0;
+    }
+    const uint32_t doff = luma ? (uint32_t)(2 * j * L::N1) : (uint32_t)(U::DC + lo * NCC);
+    for (int u = 0; u < n; ++u, cd.next(), ce.next()) {
+      if (!wait_bar(ctl, luma ? b_a2l_full(ce.slot) : b_a2c_full(ce.slot), ce.par, 2)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint64_t so = (uint64_t)(ce.slot * (kA2Unit >> 4));  // descriptor address field of the set
+      const uint32_t d = tmem + U::d(cd.slot) + doff;
+      if (luma) {
+        mma_ss(d, ad[0] + so, bl0, idesc_f16(128, L::N1, 1, 0), 1);
+        mma_ss(d + L::N1, ad[1] + so, bl0, idesc_f16(128, L::N1, 1, 0), 1);
+        mma_ss(d, ad[2] + so, bl1, idesc_f16(128, L::N1, 1, 0), 1);
+        mma_ss(d + L::N1, ad[3] + so, bl1, idesc_f16(128, L::N1, 1, 0), 1);
+        mma_commit(&ctl.bars[b_d2l(cd.slot)]);
+        mma_commit(&ctl.bars[b_a2l_free(ce.slot)]);
+      } else {
+        mma_ss(d, ad[0] + so, dbu, idesc_f16(128, NCC, 1, 0), 1);
+        mma_ss(d, ad[1] + so, dbv, idesc_f16(128, NCC, 1, 0), 1);
+        mma_commit(&ctl.bars[b_d2c(cd.slot)]);
+        mma_commit(&ctl.bars[b_a2c_free(ce.slot)]);
+      }
+    }
+  }
+  if (!ok) {  // let this thread's MMAs finish before the CTA frees TMEM
+    mma_commit(&ctl.bars[b_drain(id)]);
+    wait_bar(ctl, b_drain(id), 0, 2, true);
   }
 }
 
@@ -674,14 +906,13 @@ template <bool LP, bool DUMP, int BPS, bool BATCH>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_kernel(const __grid_constant__ TcParamsT<BATCH ? kMaxMembers : 1> p) {
   using L = PC<32, LP>;
-  using Cc = PC<16, LP>;
-  constexpr int JPT = Jobs<LP>::PER_TILE;
-  static_assert(kSlots % JPT == 0, "a TMEM slot must always hold the same plane type");
+  using U = Unit<LP>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   using SL = SmemLay<BPS>;
   uint64_t* bars = (uint64_t*)(sm + SL::OFF_BAR);
   uint32_t* tmem_slot = (uint32_t*)(sm + SL::OFF_MISC);
+  TileRec* recs = (TileRec*)(sm + SL::OFF_REC);
   volatile int* abort_flag = (volatile int*)(sm + SL::OFF_MISC + 4);
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
@@ -704,7 +935,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     n_items = cta < total_items ? (total_items - cta + grid - 1) / grid : 0;
     step = grid;
   }
-  const int n_jobs = n_items * JPT;
   Ctl ctl{bars, abort_flag, p.err};
 
   using MS = typename MemberView<BATCH>::T;
@@ -716,34 +946,37 @@ __global__ void __launch_bounds__(kThreads, 1)
   }();
 
   // Constant B operands (the integer DCT matrices as fp16), K-major without swizzle:
-  // element (n, k) at (n/8)*SBO + (k/8)*128 + (n%8)*16 + (k%8)*2.
+  // element (n, k) at (n/8)*SBO + (k/8)*128 + (n%8)*16 + (k%8)*2.  Luma: M (N1 rows, K = 32).
+  // Chroma: M's first NKC rows in rows [0, NKC) of the U operand and rows [NKC, 2 NKC) of the V
+  // operand, zero elsewhere (K = 16).
   for (int i = tid; i < L::N1 * 32; i += kThreads) {
     const int n = i >> 5, kk = i & 31;
     const __half h = __float2half_rn((float)p.M_y[n * 32 + kk]);
     *(__half*)(sm + SL::OFF_BL + (n >> 3) * 512 + (kk >> 3) * 128 + (n & 7) * 16 + (kk & 7) * 2) = h;
   }
-  for (int i = tid; i < 16 * 16; i += kThreads) {
-    const int n = i >> 4, kk = i & 15;
-    const __half h = __float2half_rn((float)p.M_c[n * 16 + kk]);
-    *(__half*)(sm + SL::OFF_BC + (n >> 3) * 256 + (kk >> 3) * 128 + (n & 7) * 16 + (kk & 7) * 2) = h;
+  for (int i = tid; i < 2 * 32 * 16; i += kThreads) {
+    const int pl = i >> 9, n = (i >> 4) & 31, kk = i & 15;
+    const int row = n - pl * U::NKC;  // matrix row held at operand row n
+    const float v = (row >= 0 && row < U::NKC) ? (float)p.M_c[row * 16 + kk] : 0.0f;
+    *(__half*)(sm + (pl ? SL::OFF_BCV : SL::OFF_BCU) + (n >> 3) * 256 + (kk >> 3) * 128 + (n & 7) * 16 + (kk & 7) * 2) =
+        __float2half_rn(v);
   }
-  // Stage-1 presets, applied by one more MMA per job ahead of the data: D1 = U x K^T with N = G N1
-  // (the job's groups side by side).  Every row of U is (1024, 1, 0, ...), so column n of D1
+  // Stage-1 presets, applied by one more MMA per stream ahead of the data: D1 = U x K^T with N =
+  // the stream's D1 columns side by side.  Every row of U is (1024, 1, 0, ...), so column n of D1
   // starts at 1024 a_n + b_n for row n of K = (a_n, b_n, 0, ...): 2^(s1-1), the rounding offset
-  // of T, minus 1024 * 64 * N in each group's DC column (the bias of the 1024 + x sample
-  // encoding), split as a = -(multiple of 8 below 2^11) and b = P - 1024 a (|b| < 2^13, a multiple
-  // of 8), both exact in fp16.
+  // of T, minus 1024 * 64 * N in each DC column (the bias of the 1024 + x sample encoding), split
+  // as a = -(multiple of 8 below 2^11) and b = P - 1024 a (|b| < 2^13, a multiple of 8), both exact
+  // in fp16.  Luma DC columns: every N1-th; chroma: every NKC-th (U and V alternate).
   for (int i = tid; i < 128 * 16; i += kThreads) {
     const int m = i >> 4, kk = i & 15;
     const float v = kk == 0 ? 1024.0f : kk == 1 ? 1.0f : 0.0f;
     *(__half*)(sm + SL::OFF_ONE + (m >> 3) * 256 + (kk >> 3) * 128 + (m & 7) * 16 + (kk & 7) * 2) = __float2half_rn(v);
   }
   for (int i = tid; i < 2 * 32 * 16; i += kThreads) {
-    const int kk = i & 15, n = (i >> 4) & 31;
     const bool luma = i < 32 * 16;
-    const int N = luma ? 32 : 16, N1 = luma ? L::N1 : Cc::N1, G = luma ? L::G : Cc::G;
-    if (n >= G * N1) continue;
-    const int P = (1 << (s1_of<32>(BPS) - (luma ? 1 : 2))) - (n % N1 == 0 ? 1024 * 64 * N : 0);
+    const int kk = i & 15, n = (i >> 4) & 31;
+    const int N = luma ? 32 : 16, period = luma ? L::N1 : U::NKC;
+    const int P = (1 << (s1_of<32>(BPS) - (luma ? 1 : 2))) - (n % period == 0 ? 1024 * 64 * N : 0);
     const int a = P >= 0 ? (P >> 10) & ~7 : -(((-P) >> 10) & ~7);
     const float v = kk == 0 ? (float)a : kk == 1 ? (float)(P - a * 1024) : 0.0f;
     *(__half*)(sm + (luma ? SL::OFF_KL : SL::OFF_KC) + (n >> 3) * 256 + (kk >> 3) * 128 + (n & 7) * 16 + (kk & 7) * 2) =
@@ -752,9 +985,23 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (tid == 0) {
     for (int i = 0; i < kBars; ++i) mbar_init(&bars[i], 1);
     for (int i = 0; i < SL::kStages; ++i) mbar_init(&bars[b_raw_empty(i)], 8);  // both convert warpgroups
-    for (int i = 0; i < kSlots; ++i) mbar_init(&bars[b_slot_free(i)], 4);
-    for (int i = 0; i < kSlots; ++i) mbar_init(&bars[b_a1_full(i)], 4);
-    for (int i = 0; i < kA2Slots; ++i) mbar_init(&bars[b_a2_full(i)], 4);
+    for (int a = 0; a < kASlots; ++a) {
+      mbar_init(&bars[b_a1l_full(a)], 4);  // convert luma warps
+      mbar_init(&bars[b_a1c_full(a)], 4);  // convert chroma warps
+      mbar_init(&bars[b_a1l_free(a)], 2);  // issuers 0, 1
+    }
+    for (int d = 0; d < U::DS; ++d) {
+      mbar_init(&bars[b_d1l(d)], 2);   // issuers 0, 1
+      mbar_init(&bars[b_d2l(d)], 2);   // issuers 3, 4
+      mbar_init(&bars[b_d2c(d)], 2);   // issuers 5, 6
+      mbar_init(&bars[b_dfree(d)], 8); // epilogue-2 luma and chroma warps
+    }
+    for (int e = 0; e < kA2Sets; ++e) {
+      mbar_init(&bars[b_a2l_full(e)], 4);  // epilogue-1 luma warps
+      mbar_init(&bars[b_a2c_full(e)], 4);  // chroma epilogue warps
+      mbar_init(&bars[b_a2l_free(e)], 2);  // issuers 3, 4
+      mbar_init(&bars[b_a2c_free(e)], 2);  // issuers 5, 6
+    }
     *abort_flag = 0;
     fence_mbar_init();
   }
@@ -775,8 +1022,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t sbase = smem_u32(sm);
   const uint32_t lanebase = (uint32_t)(32 * q) << 16;
 
-  if (role == 0) {
-    if (warp == 0 && lane == 0) {
+  if (warp == 0) {
+    if (lane == 0) {
       // ---------------- TMA producer: tiles in order into the ring ----------------
       int issued = 0;
       for (int t = 0; t < n_items; ++t) {
@@ -784,6 +1031,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (t >= SL::kStages && !wait_bar(ctl, b_raw_empty(stage), ((t / SL::kStages) - 1) & 1, 1, false, true))
           break;
         const TileInfo ti = tile_info(ms, t, item0, step, SL::kStages);
+        {
+          const TcMember& M = ms[ti.m];
+          TileRec* rec = recs + (t & (kTileRecs - 1));
+          *rec = TileRec{ti.f, ti.tx, ti.ty, ti.m, M.H - ti.ty * 128, M.W - ti.tx * 128, M.ch - ti.ty * 64,
+                         M.cw - ti.tx * 64};
+        }
         const CUtensorMap* mm = &p.maps[3 * ti.m];
         uint8_t* dst = sm + OFF_RAW + stage * SL::kStageBytes;
         uint64_t* full = &bars[b_raw_full(stage)];
@@ -803,94 +1056,19 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int t = (issued > SL::kStages ? issued - SL::kStages : 0); t < issued; ++t)
           wait_bar(ctl, b_raw_full(t % SL::kStages), (t / SL::kStages) & 1, 1, true);
       }
-    } else if (warp == 1 && lane == 0) {
-      // ---------------- stage-1 MMA issuer: D1 = U x K^T (presets), then D1 += A1 (TMEM) x M^T ----------------
-      const uint32_t bl = sbase + SL::OFF_BL, bc = sbase + SL::OFF_BC;
-      const uint64_t du = smem_desc(sbase + SL::OFF_ONE, 128, 256, 0);
-      const uint64_t dkl = smem_desc(sbase + SL::OFF_KL, 128, 256, 0), dkc = smem_desc(sbase + SL::OFF_KC, 128, 256, 0);
-      constexpr uint32_t idPL = idesc_f16(128, L::G * L::N1, 0, 0), idPC = idesc_f16(128, Cc::G * Cc::N1, 0, 0);
-      constexpr uint32_t idL = idesc_f16(128, L::N1, 0, 0), idC = idesc_f16(128, Cc::N1, 0, 0);
-      bool ok = true;
-      for (int j = 0; j < n_jobs; ++j) {
-        int plane, jp;
-        plane_of<LP>(j % JPT, plane, jp);
-        const int slot = j % kSlots;
-        if (!wait_bar(ctl, b_a1_full(slot), (j / kSlots) & 1, 2)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t a = tmem + slot * kSlotCols;
-        const uint32_t d = a + kD1Off;
-        if (plane == 0) {
-          mma_ss(d, du, dkl, idPL, 0);  // presets of the job's groups
-          // K-step outer: consecutive MMAs write different accumulators.
-#pragma unroll
-          for (int ks = 0; ks < 2; ++ks)
-#pragma unroll
-            for (int gg = 0; gg < L::G; ++gg)
-              mma_ts(d + gg * L::N1, a + gg * L::A1COLS + ks * 8, smem_desc(bl + ks * 256, 128, 512, 0), idL, 1);
-        } else {
-          mma_ss(d, du, dkc, idPC, 0);
-#pragma unroll
-          for (int gg = 0; gg < Cc::G; ++gg)
-            mma_ts(d + gg * Cc::N1, a + gg * Cc::A1COLS, smem_desc(bc, 128, 256, 0), idC, 1);
-        }
-        mma_commit(&bars[b_d1(slot)]);
-      }
-      if (!ok) {
-        mma_commit(&bars[b_drain(0)]);
-        wait_bar(ctl, b_drain(0), 0, 2, true);
-      }
-    } else if (warp == 2 && lane == 0) {
-      // ---------------- stage-2 MMA issuer: D2 += A2 (smem, MN-major) x M^T, hi and lo (D2 pre-set by epilogue 1) ----------------
-      const uint32_t bl = sbase + SL::OFF_BL, bc = sbase + SL::OFF_BC;
-      constexpr uint32_t id2L = idesc_f16(128, L::N1, 1, 0), id2C = idesc_f16(128, Cc::N1, 1, 0);
-      bool ok = true;
-      for (int j = 0; j < n_jobs; ++j) {
-        int plane, jp;
-        plane_of<LP>(j % JPT, plane, jp);
-        int a2, use;
-        a2_slot_of<LP>(j, a2, use);
-        if (!wait_bar(ctl, b_a2_full(a2), use & 1, 2)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t d = tmem + (j % kSlots) * kSlotCols;
-        const uint32_t ahi = a2_addr<BPS>(sbase, a2);
-        if (plane == 0) {
-#pragma unroll
-          for (int ks = 0; ks < 2; ++ks) {
-            const uint64_t b = smem_desc(bl + ks * 256, 128, 512, 0);
-            mma_ss(d, smem_desc(ahi + ks * 4096, 1024, 2048, 2), b, id2L, 1);
-            mma_ss(d + L::N1, smem_desc(ahi + kA2L + ks * 4096, 1024, 2048, 2), b, id2L, 1);
-          }
-        } else {
-          const uint64_t b = smem_desc(bc, 128, 256, 0);
-          mma_ss(d, smem_desc(ahi, 1024, 2048, 2), b, id2C, 1);
-          mma_ss(d + Cc::N1, smem_desc(ahi + kA2C, 1024, 2048, 2), b, id2C, 1);
-        }
-        mma_commit(&bars[b_d2(j % kSlots)]);
-        mma_commit(&bars[b_a2_free(a2)]);
-      }
-      if (!ok) {
-        mma_commit(&bars[b_drain(1)]);
-        wait_bar(ctl, b_drain(1), 0, 2, true);
-      }
     }
-  } else if (role == 1) {
-    convert_loop<32, LP, BPS>(ms, ctl, sm, tmem + lanebase, n_items, item0, step, q, lane);
-  } else if (role == 6) {
-    convert_loop<16, LP, BPS>(ms, ctl, sm, tmem + lanebase, n_items, item0, step, q, lane);
+  } else if (warp <= kIssuers) {
+    if (lane == 0) issuer_loop<LP, BPS>(ctl, sbase, tmem, warp - 1, n_items);
   } else if (role == 2) {
-    epi1_loop<32, LP, BPS>(ms, ctl, sbase, tmem + lanebase, n_items, item0, step, q, lane);
+    convert_luma_loop<LP, BPS>(recs, ctl, sm, tmem + lanebase, n_items, q, lane);
   } else if (role == 3) {
-    epi1_loop<16, LP, BPS>(ms, ctl, sbase, tmem + lanebase, n_items, item0, step, q, lane);
+    convert_chroma_loop<LP, BPS>(recs, ctl, sm, tmem + lanebase, n_items, q, lane);
   } else if (role == 4) {
-    epi2_loop<32, LP, DUMP>(p, ms, ctl, tmem + lanebase, n_items, item0, step, q, lane);
+    epi1_luma_loop<LP, BPS>(ctl, sbase, tmem + lanebase, n_items, q, lane);
+  } else if (role == 5) {
+    epi2_luma_loop<LP, DUMP>(p, ms, recs, ctl, tmem + lanebase, n_items, q, lane);
   } else {
-    epi2_loop<16, LP, DUMP>(p, ms, ctl, tmem + lanebase, n_items, item0, step, q, lane);
+    chroma_epi_loop<LP, DUMP, BPS>(p, ms, recs, ctl, sbase, tmem + lanebase, n_items, q, lane);
   }
 
   tc_fence_before();
