@@ -16,8 +16,7 @@
 //                 from different warps overlap in the tensor pipe, so the issue is spread out;
 //   warpgroup 2   convert luma, warpgroup 3 convert chroma: raw samples -> stage-1 A operands
 //                 in TMEM;
-//   warpgroup 4   epilogue 1 luma: stage-1 accumulators -> stage-2 A operand in shared memory,
-//                 and the stage-2 accumulator presets;
+//   warpgroup 4   epilogue 1 luma: stage-1 accumulators -> stage-2 A operand in shared memory;
 //   warpgroup 5   epilogue 2 luma: stage-2 accumulators -> block energies and brightness;
 //   warpgroup 6   both chroma epilogues (chroma has half the luma work per unit).
 // Each role waits once per unit.  TMEM holds 2 stage-1 operand slots and 3 (low-pass) or 2
@@ -38,7 +37,7 @@
 //             fp16 pairs (1024 + U_lo8, 1024 + U_hi8); stored MN-major (128-byte swizzle)
 //             as the stage-2 A operand -- the row/column transpose is the layout;
 //   stage 2   S_hi, S_lo = M T_hi, M T_lo (A MN-major from shared memory), the accumulators
-//             pre-set by epilogue 1 to the magic constants of epilogue 2;
+//             pre-set to the magic constants of epilogue 2 by one more MMA per stream;
 //   epilogue2 Z = floor((256 S_hi + S_lo + 2^(s2-1)) / 2^s2) by two round-down FMAs, then
 //             H_v = sum_u w(u,v) |Z| in increasing u and an xor tree over v.
 // U and V share their MMAs: a U row and a V row lie side by side along K and the B operand holds
@@ -118,7 +117,10 @@ struct SmemLay {
   static constexpr int OFF_ONE = OFF_BCV + 1024;               // preset operand U (128 x 16)
   static constexpr int OFF_KL = OFF_ONE + 4096;                // preset operand K, luma (32 x 16)
   static constexpr int OFF_KC = OFF_KL + 1024;                 // and chroma (32 x 16)
-  static constexpr int OFF_REC = OFF_KC + 1024;                // tile records (16 x 32 B)
+  static constexpr int OFF_K2L = OFF_KC + 1024;                // stage-2 preset operand, luma hi and lo (64 x 16)
+  static constexpr int OFF_K2CH = OFF_K2L + 2048;              // chroma hi (32 x 16)
+  static constexpr int OFF_K2CL = OFF_K2CH + 1024;             // chroma lo (32 x 16)
+  static constexpr int OFF_REC = OFF_K2CL + 1024;              // tile records (16 x 32 B)
   static constexpr int OFF_BAR = OFF_REC + 16 * 32;
   static constexpr int OFF_MISC = OFF_BAR + 48 * 8;
   static constexpr int kSmemBytes = OFF_MISC + 64 + 1024;  // + slack to align the base to 1024
@@ -340,77 +342,89 @@ __device__ __forceinline__ void fill_cols(uint32_t taddr, float first, float res
   tmem_fill<N>(taddr, __float_as_uint(first), __float_as_uint(rest));
 }
 
-// Reads D1 (stage-1 accumulators at td1 + g*N1) and writes the stage-2 operand to shared memory.
+// Reads D1 (stage-1 accumulators at td1 + g*N1) and writes the stage-2 operand to shared memory,
+// 8 columns at a time; the TMEM load of the next 8 columns is in flight while this thread
+// converts the current ones.
 template <int Nb, bool LP>
 __device__ __forceinline__ void epilogue1(uint32_t td1, uint32_t a2hi, uint32_t a2lo, int q, int lane, float s1inv) {
   using P = PC<Nb, LP>;
   constexpr int NK = P::NK;
+  constexpr int CPG = NK / 8;    // 8-column chunks per group
+  constexpr int S = P::G * CPG;  // chunks of the job
   const int l = 32 * q + lane;
   const int bg = l / Nb;
   const int r = l % Nb;
-  constexpr int CH = NK < 8 ? NK : 8;  // D1 columns read at a time (bounds register use)
   const uint32_t rowoff = (uint32_t)((r >> 3) * 2048 + (r & 7) * 128);
-#pragma unroll 1
-  for (int g = 0; g < P::G; ++g) {
+  uint32_t buf[2][8];
+  tmem_ld<8>(td1, buf[0]);
 #pragma unroll
-    for (int h0 = 0; h0 < NK; h0 += CH) {
-      uint32_t acc[CH];
-      tmem_ld<CH>(td1 + g * P::N1 + h0, acc);
-      tmem_wait_ld();
-      uint32_t hi[CH / 2], lw[CH / 2];
+  for (int st = 0; st < S; ++st) {
+    const int g = st / CPG, h0 = (st % CPG) * 8;
+    tmem_wait_ld();
+    if (st + 1 < S) tmem_ld<8>(td1 + ((st + 1) / CPG) * P::N1 + ((st + 1) % CPG) * 8, buf[(st + 1) & 1]);
+    const uint32_t(&acc)[8] = buf[st & 1];
+    uint32_t hi[4], lw[4];
 #pragma unroll
-      for (int k = 0; k < CH; k += 2) {
-        // D1 already holds T' = c_k + sum (the accumulators were pre-set), an exact integer.
-        const uint32_t za = __float_as_uint(__fmaf_rd(__uint_as_float(acc[k]), s1inv, kT1));
-        const uint32_t zb = __float_as_uint(__fmaf_rd(__uint_as_float(acc[k + 1]), s1inv, kT1));
-        lw[k / 2] = prmt(za, zb, 0x6420);
-        hi[k / 2] = prmt(za, zb, 0x6521);
-      }
-      const int m0 = (g * P::BPG1 + bg) * NK + h0;
-#pragma unroll
-      for (int cc = 0; cc < CH / 8; ++cc) {
-        const int m = m0 + 8 * cc;
-        const uint32_t off = rowoff + (uint32_t)((m >> 6) * 1024) + (uint32_t)(((((m & 63) >> 3) ^ (r & 7))) << 4);
-        sts128(a2hi + off, hi[4 * cc], hi[4 * cc + 1], hi[4 * cc + 2], hi[4 * cc + 3]);
-        sts128(a2lo + off, lw[4 * cc], lw[4 * cc + 1], lw[4 * cc + 2], lw[4 * cc + 3]);
-      }
+    for (int k = 0; k < 8; k += 2) {
+      // D1 already holds T' = c_k + sum (the accumulators were pre-set), an exact integer.
+      const uint32_t za = __float_as_uint(__fmaf_rd(__uint_as_float(acc[k]), s1inv, kT1));
+      const uint32_t zb = __float_as_uint(__fmaf_rd(__uint_as_float(acc[k + 1]), s1inv, kT1));
+      lw[k / 2] = prmt(za, zb, 0x6420);
+      hi[k / 2] = prmt(za, zb, 0x6521);
     }
+    const int m = (g * P::BPG1 + bg) * NK + h0;
+    const uint32_t off = rowoff + (uint32_t)((m >> 6) * 1024) + (uint32_t)(((((m & 63) >> 3) ^ (r & 7))) << 4);
+    sts128(a2hi + off, hi[0], hi[1], hi[2], hi[3]);
+    sts128(a2lo + off, lw[0], lw[1], lw[2], lw[3]);
   }
 }
 
-// Reads this thread's stage-2 accumulators (hi at td2, lo at td2 + LO), forms Z, the row sums of
-// w(u, v) |Z| in increasing u and the block energy H by an xor tree over the NK rows of the block;
-// the block's v = 0 thread stores H at out[0] and L = sqrt(Z(0,0)) at out[C] (out null: block outside
-// the frame).  DUMP: the coefficients to zd (u-major) as well.
+// Epilogue 2 of two jobs of one plane type (luma: both luma jobs; chroma: U and V): for job j the
+// stage-2 accumulators hi at td2[j] and lo at td2[j] + LO form Z, the row sums of w(u, v) |Z| in
+// increasing u and the block energy H by an xor tree over the NK rows of the block; the block's
+// v = 0 thread stores H at out[j][0] and L = sqrt(Z(0,0)) at out[j][C] (null: block outside the
+// frame).  DUMP: the coefficients to zd[j] (u-major) as well.  The TMEM loads of the next 8
+// columns are in flight while the current ones are processed.
 template <int Nb, bool LP, bool DUMP, int LO>
-__device__ __forceinline__ void epilogue2(uint32_t td2, int lane, const float (&wts)[PC<Nb, LP>::NK], float einv,
-                                          float c2, float* out, int64_t C, int16_t* zd) {
+__device__ __forceinline__ void epilogue2(const uint32_t (&td2)[2], int lane, const float (&wts)[PC<Nb, LP>::NK],
+                                          float einv, float c2, float* const (&out)[2], int64_t C,
+                                          int16_t* const (&zd)[2]) {
   using P = PC<Nb, LP>;
   constexpr int NK = P::NK;
-  constexpr int HALF = NK > 8 ? 8 : NK;  // columns loaded at a time (bounds register use)
+  constexpr int CPJ = NK / 8;  // 8-column chunks per job
+  constexpr int S = 2 * CPJ;
   const int v = lane % NK;
+  uint32_t bh[2][8], bl[2][8];
+  tmem_ld<8>(td2[0], bh[0]);
+  tmem_ld<8>(td2[0] + LO, bl[0]);
   float H = 0.0f, z00 = 0.0f;
 #pragma unroll
-  for (int h0 = 0; h0 < NK; h0 += HALF) {
-    uint32_t hi[HALF], lo[HALF];
-    tmem_ld<HALF>(td2 + h0, hi);
-    tmem_ld<HALF>(td2 + LO + h0, lo);
+  for (int st = 0; st < S; ++st) {
+    const int j = st / CPJ, h0 = (st % CPJ) * 8;
     tmem_wait_ld();
+    if (st + 1 < S) {
+      const uint32_t t1 = td2[(st + 1) / CPJ] + ((st + 1) % CPJ) * 8;
+      tmem_ld<8>(t1, bh[(st + 1) & 1]);
+      tmem_ld<8>(t1 + LO, bl[(st + 1) & 1]);
+    }
 #pragma unroll
-    for (int uu = 0; uu < HALF; ++uu) {
+    for (int uu = 0; uu < 8; ++uu) {
       const int u = h0 + uu;
-      const float w = __fmaf_rd(__uint_as_float(lo[uu]), 0.00390625f, __uint_as_float(hi[uu]));
+      const float w = __fmaf_rd(__uint_as_float(bl[st & 1][uu]), 0.00390625f, __uint_as_float(bh[st & 1][uu]));
       const float z = __fmaf_rd(w, einv, c2) - kK1;
       if (u == 0) z00 = z;
-      if (DUMP && zd) zd[u * NK + v] = (int16_t)z;
+      if (DUMP && zd[j]) zd[j][u * NK + v] = (int16_t)z;
       H = fmaf(fabsf(z), wts[u], H);
     }
-  }
+    if (h0 + 8 == NK) {  // job j complete
 #pragma unroll
-  for (int o = NK / 2; o > 0; o >>= 1) H += __shfl_xor_sync(0xffffffffu, H, o);
-  if (out && v == 0) {
-    out[0] = H;
-    out[C] = __fsqrt_rn(z00);
+      for (int o = NK / 2; o > 0; o >>= 1) H += __shfl_xor_sync(0xffffffffu, H, o);
+      if (out[j] && v == 0) {
+        out[j][0] = H;
+        out[j][C] = __fsqrt_rn(z00);
+      }
+      H = 0.0f;
+    }
   }
 }
 
@@ -647,9 +661,7 @@ __device__ void convert_chroma_loop(const TileRec* recs, const Ctl& ctl, uint8_t
 }
 
 // Epilogue 1 luma: T = floor(T'/2^s1) of both luma jobs into the stage-2 operands (hi and lo bytes
-// as fp16, MN-major; s1 = log2 N + B - 9), then the stage-2 accumulators pre-set: hi starts at
-// K1 - 1156 * 64 * N for u = 0 (the 1024 + byte encoding of both halves and the +128 offset of the
-// hi byte) and K1 otherwise, lo at 2^(s2-1) (N = 32: s2 = 11).
+// as fp16, MN-major; s1 = log2 N + B - 9).
 template <bool LP, int BPS>
 __device__ void epi1_luma_loop(const Ctl& ctl, uint32_t sbase, uint32_t tq, int n_items, int q, int lane) {
   using SL = SmemLay<BPS>;
@@ -670,12 +682,6 @@ __device__ void epi1_luma_loop(const Ctl& ctl, uint32_t sbase, uint32_t tq, int 
       const uint32_t ahi = a2_luma(a2, j);
       epilogue1<32, LP>(td + j * P::G * P::N1, ahi, ahi + kA2L, q, lane, s1inv);
     }
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {  // D2 overlaps D1: written after every D1 column was read
-      fill_cols<P::N1>(td + 2 * j * P::N1, kK1 - 2367488.0f, kK1);
-      fill_cols<P::N1>(td + (2 * j + 1) * P::N1, 1024.0f, 1024.0f);
-    }
-    tmem_wait_st();
     fence_proxy_async_smem();
     tc_fence_before();
     __syncwarp();
@@ -712,13 +718,17 @@ __device__ void epi2_luma_loop(const PP& p, const MS& ms, const TileRec* recs, c
     const TcMember& M = ms[rec.m];
     const uint32_t td = tq + U::d(cd.slot);
     float* const base = M.blockvals + (int64_t)rec.f * M.out_fstride;
-#pragma unroll 1
+    uint32_t td2[2];
+    float* out[2];
+    int16_t* zd[2];
+#pragma unroll
     for (int j = 0; j < 2; ++j) {
       const int64_t k = block_of<P::NK, P::BPG2>(M, rec, h * 2 + j, q, lane);
-      int16_t* zd = (DUMP && k >= 0 && rec.f == 0) ? p.zdump[0] + k * P::NK * P::NK : nullptr;
-      epilogue2<32, LP, DUMP, P::N1>(td + 2 * j * P::N1, lane, w, 0.125f, kK1 - kK1 / 8.0f,
-                                     k >= 0 ? base + k : nullptr, M.C, zd);
+      td2[j] = td + 2 * j * P::N1;
+      out[j] = k >= 0 ? base + k : nullptr;
+      zd[j] = (DUMP && k >= 0 && rec.f == 0) ? p.zdump[0] + k * P::NK * P::NK : nullptr;
     }
+    epilogue2<32, LP, DUMP, P::N1>(td2, lane, w, 0.125f, kK1 - kK1 / 8.0f, out, M.C, zd);
     tc_fence_before();
     __syncwarp();
     if (lane == 0) mbar_arrive(&ctl.bars[b_dfree(cd.slot)]);
@@ -729,9 +739,8 @@ __device__ void epi2_luma_loop(const PP& p, const MS& ms, const TileRec* recs, c
   }
 }
 
-// Chroma epilogues, one warpgroup: for unit u, epilogue 1 (as for luma, both planes: s2 = 10,
-// presets K1 - 1156 * 64 * 16 on each plane's u = 0 column, 512 for lo), then epilogue 2 of
-// unit u - 1.
+// Chroma epilogues, one warpgroup: for unit u, epilogue 1 (as for luma, both planes), then
+// epilogue 2 of unit u - 1.
 template <bool LP, bool DUMP, int BPS, class PP, class MS>
 __device__ void chroma_epi_loop(const PP& p, const MS& ms, const TileRec* recs, const Ctl& ctl, uint32_t sbase,
                                 uint32_t tq, int n_items, int q, int lane) {
@@ -743,10 +752,6 @@ __device__ void chroma_epi_loop(const PP& p, const MS& ms, const TileRec* recs, 
   float w[P::NK];
 #pragma unroll
   for (int uu = 0; uu < P::NK; ++uu) w[uu] = p.W_c[uu * 16 + (lane % P::NK)];
-  // hi presets of both planes side by side: the u = 0 column of U and of V start lower
-  uint32_t hip[NCC];
-#pragma unroll
-  for (int c = 0; c < NCC; ++c) hip[c] = __float_as_uint(c % NKC == 0 ? kK1 - 1183744.0f : kK1);
   Cursor<U::DS> cd, cd2;
   Cursor<kA2Sets> ce;
   const int n = n_items * U::UPT;
@@ -763,9 +768,6 @@ __device__ void chroma_epi_loop(const PP& p, const MS& ms, const TileRec* recs, 
         const uint32_t ahi = a2_chroma(a2, pl);
         epilogue1<16, LP>(td + pl * NKC, ahi, ahi + kA2C, q, lane, s1inv);
       }
-      tmem_st<NCC>(td, hip);
-      fill_cols<NCC>(td + NCC, 512.0f, 512.0f);
-      tmem_wait_st();
       fence_proxy_async_smem();
       tc_fence_before();
       __syncwarp();
@@ -781,12 +783,16 @@ __device__ void chroma_epi_loop(const PP& p, const MS& ms, const TileRec* recs, 
       const uint32_t td = tq + U::d(cd2.slot) + U::DC;
       const int64_t k = block_of<P::NK, P::BPG2>(M, rec, h, q, lane);  // U and V share the block
       float* const base = M.blockvals + (int64_t)rec.f * M.out_fstride;
-#pragma unroll 1
+      uint32_t td2[2];
+      float* out[2];
+      int16_t* zd[2];
+#pragma unroll
       for (int pl = 0; pl < 2; ++pl) {
-        int16_t* zd = (DUMP && k >= 0 && rec.f == 0) ? p.zdump[1 + pl] + k * P::NK * P::NK : nullptr;
-        epilogue2<16, LP, DUMP, NCC>(td + pl * NKC, lane, w, 0.25f, kK1 - kK1 / 4.0f,
-                                     k >= 0 ? base + (2 + 2 * pl) * M.C + k : nullptr, M.C, zd);
+        td2[pl] = td + pl * NKC;
+        out[pl] = k >= 0 ? base + (2 + 2 * pl) * M.C + k : nullptr;
+        zd[pl] = (DUMP && k >= 0 && rec.f == 0) ? p.zdump[1 + pl] + k * P::NK * P::NK : nullptr;
       }
+      epilogue2<16, LP, DUMP, NCC>(td2, lane, w, 0.25f, kK1 - kK1 / 4.0f, out, M.C, zd);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&ctl.bars[b_dfree(cd2.slot)]);
@@ -854,8 +860,8 @@ __device__ void issuer_loop(const Ctl& ctl, uint32_t sbase, uint32_t tmem, int i
       }
     }
   } else {
-    // D2 += A2 (smem, MN-major) x M^T (D2 pre-set by epilogue 1); descriptors of operand set 0,
-    // set 1 is kA2Unit bytes further.
+    // D2 = presets, then D2 += A2 (smem, MN-major) x M^T; descriptors of operand set 0, set 1 is
+    // kA2Unit bytes further.
     const bool luma = id < 5;
     const int j = id - 3;
     const uint32_t lo = id == 6 ? 1u : 0u;
@@ -873,6 +879,10 @@ __device__ void issuer_loop(const Ctl& ctl, uint32_t sbase, uint32_t tmem, int i
       ad[2] = ad[3] = 0;
     }
     const uint32_t doff = luma ? (uint32_t)(2 * j * L::N1) : (uint32_t)(U::DC + lo * NCC);
+    // stage-2 presets (D2 = U x K2^T, overwriting): the stream's hi and lo columns (luma) or its
+    // hi or lo columns (chroma)
+    const uint64_t dk2 = smem_desc(sbase + (luma ? SL::OFF_K2L : lo ? SL::OFF_K2CL : SL::OFF_K2CH), 128, 256, 0);
+    const uint32_t idP2 = luma ? idesc_f16(128, 2 * L::N1, 0, 0) : idesc_f16(128, NCC, 0, 0);
     for (int u = 0; u < n; ++u, cd.next(), ce.next()) {
       if (!wait_bar(ctl, luma ? b_a2l_full(ce.slot) : b_a2c_full(ce.slot), ce.par, 2)) {
         ok = false;
@@ -881,6 +891,7 @@ __device__ void issuer_loop(const Ctl& ctl, uint32_t sbase, uint32_t tmem, int i
       tc_fence_after();
       const uint64_t so = (uint64_t)(ce.slot * (kA2Unit >> 4));  // descriptor address field of the set
       const uint32_t d = tmem + U::d(cd.slot) + doff;
+      mma_ss(d, du, dk2, idP2, 0);
       if (luma) {
         mma_ss(d, ad[0] + so, bl0, idesc_f16(128, L::N1, 1, 0), 1);
         mma_ss(d + L::N1, ad[1] + so, bl0, idesc_f16(128, L::N1, 1, 0), 1);
@@ -981,6 +992,31 @@ __global__ void __launch_bounds__(kThreads, 1)
     const float v = kk == 0 ? (float)a : kk == 1 ? (float)(P - a * 1024) : 0.0f;
     *(__half*)(sm + (luma ? SL::OFF_KL : SL::OFF_KC) + (n >> 3) * 256 + (kk >> 3) * 128 + (n & 7) * 16 + (kk & 7) * 2) =
         __float2half_rn(v);
+  }
+  // Stage-2 presets, by one more MMA per stage-2 stream: hi accumulators start at K1, minus
+  // 1156 * 64 * N on each u = 0 column (the 1024 + byte encoding of both halves and the +128
+  // offset of the hi byte), lo accumulators at 2^(s2-1) (luma N = 32: s2 = 11; chroma: 10), the
+  // magic constants of epilogue 2; split as for the stage-1 presets.  Luma: N1 hi rows then N1 lo
+  // rows; chroma: NCC rows each for hi (u = 0 every NKC-th) and lo.
+  for (int i = tid; i < (64 + 32 + 32) * 16; i += kThreads) {
+    const int kk = i & 15, row = i >> 4;
+    int P, off, n;
+    if (row < 64) {
+      n = row;
+      off = SL::OFF_K2L;
+      P = n < L::N1 ? (n == 0 ? 12582912 - 1156 * 64 * 32 : 12582912) : 1024;
+    } else if (row < 96) {
+      n = row - 64;
+      off = SL::OFF_K2CH;
+      P = n % U::NKC == 0 ? 12582912 - 1156 * 64 * 16 : 12582912;
+    } else {
+      n = row - 96;
+      off = SL::OFF_K2CL;
+      P = 512;
+    }
+    const int a = (P >> 10) & ~7;
+    const float v = kk == 0 ? (float)a : kk == 1 ? (float)(P - a * 1024) : 0.0f;
+    *(__half*)(sm + off + (n >> 3) * 256 + (kk >> 3) * 128 + (n & 7) * 16 + (kk & 7) * 2) = __float2half_rn(v);
   }
   if (tid == 0) {
     for (int i = 0; i < kBars; ++i) mbar_init(&bars[i], 1);
