@@ -152,7 +152,7 @@ __host__ __device__ constexpr int b_drain(int i) { return 39 + i; }
 constexpr int kBars = 48;
 static_assert(b_drain(kIssuers - 1) < kBars, "barrier area");
 
-constexpr int kThreads = 896;
+constexpr int kThreads = 1024;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint64_t kWaitNs = 2000000000ull;
 
@@ -257,7 +257,7 @@ __device__ __noinline__ bool wait_bar_slow(uint64_t* bar, uint32_t parity, volat
 // Bounded wait on barrier idx.  Roles on the critical path spin; the producer (sleep = true) lets
 // its thread sleep in hardware between polls.
 __device__ __forceinline__ bool wait_bar(const Ctl& c, int idx, uint32_t parity, int code, bool ignore_abort = false,
-                                         bool sleep = true) {
+                                         bool sleep = false) {
   uint64_t* bar = c.bars + idx;
   if (sleep ? mbar_try_wait_sleep(bar, parity) : mbar_try_wait(bar, parity)) return true;
   return wait_bar_slow(bar, parity, c.abort, c.err, code, ignore_abort, sleep);
@@ -342,24 +342,41 @@ __device__ __forceinline__ void fill_cols(uint32_t taddr, float first, float res
   tmem_fill<N>(taddr, __float_as_uint(first), __float_as_uint(rest));
 }
 
+// Byte offsets within a stage-2 operand of this thread's 8-column chunks of a job (chunk st: group
+// st / (NK / 8), columns 8 (st % (NK / 8)) ..): thread 32 q + lane holds row r = l % Nb of block
+// l / Nb of each group, and writes stage-2 rows m = (g BPG1 + l / Nb) NK + h0 .. + 7 at K = r
+// (MN-major, 128-byte swizzle: 8-row K groups of 2048 bytes, 64-row M atoms of 1024 bytes).
+template <int Nb, bool LP>
+struct E1Offs {
+  static constexpr int S = PC<Nb, LP>::G * (PC<Nb, LP>::NK / 8);
+  uint32_t off[S];
+  __device__ __forceinline__ E1Offs(int q, int lane) {
+    using P = PC<Nb, LP>;
+    const int l = 32 * q + lane;
+    const int bg = l / Nb, r = l % Nb;
+    const uint32_t rowoff = (uint32_t)((r >> 3) * 2048 + (r & 7) * 128);
+#pragma unroll
+    for (int st = 0; st < S; ++st) {
+      const int g = st / (P::NK / 8), h0 = (st % (P::NK / 8)) * 8;
+      const int m = (g * P::BPG1 + bg) * P::NK + h0;
+      off[st] = rowoff + (uint32_t)((m >> 6) * 1024) + (uint32_t)(((((m & 63) >> 3) ^ (r & 7))) << 4);
+    }
+  }
+};
+
 // Reads D1 (stage-1 accumulators at td1 + g*N1) and writes the stage-2 operand to shared memory,
 // 8 columns at a time; the TMEM load of the next 8 columns is in flight while this thread
 // converts the current ones.
 template <int Nb, bool LP>
-__device__ __forceinline__ void epilogue1(uint32_t td1, uint32_t a2hi, uint32_t a2lo, int q, int lane, float s1inv) {
+__device__ __forceinline__ void epilogue1(uint32_t td1, uint32_t a2hi, uint32_t a2lo, const E1Offs<Nb, LP>& eo,
+                                          float s1inv) {
   using P = PC<Nb, LP>;
-  constexpr int NK = P::NK;
-  constexpr int CPG = NK / 8;    // 8-column chunks per group
-  constexpr int S = P::G * CPG;  // chunks of the job
-  const int l = 32 * q + lane;
-  const int bg = l / Nb;
-  const int r = l % Nb;
-  const uint32_t rowoff = (uint32_t)((r >> 3) * 2048 + (r & 7) * 128);
+  constexpr int CPG = P::NK / 8;  // 8-column chunks per group
+  constexpr int S = E1Offs<Nb, LP>::S;
   uint32_t buf[2][8];
   tmem_ld<8>(td1, buf[0]);
 #pragma unroll
   for (int st = 0; st < S; ++st) {
-    const int g = st / CPG, h0 = (st % CPG) * 8;
     tmem_wait_ld();
     if (st + 1 < S) tmem_ld<8>(td1 + ((st + 1) / CPG) * P::N1 + ((st + 1) % CPG) * 8, buf[(st + 1) & 1]);
     const uint32_t(&acc)[8] = buf[st & 1];
@@ -372,19 +389,18 @@ __device__ __forceinline__ void epilogue1(uint32_t td1, uint32_t a2hi, uint32_t 
       lw[k / 2] = prmt(za, zb, 0x6420);
       hi[k / 2] = prmt(za, zb, 0x6521);
     }
-    const int m = (g * P::BPG1 + bg) * NK + h0;
-    const uint32_t off = rowoff + (uint32_t)((m >> 6) * 1024) + (uint32_t)(((((m & 63) >> 3) ^ (r & 7))) << 4);
-    sts128(a2hi + off, hi[0], hi[1], hi[2], hi[3]);
-    sts128(a2lo + off, lw[0], lw[1], lw[2], lw[3]);
+    sts128(a2hi + eo.off[st], hi[0], hi[1], hi[2], hi[3]);
+    sts128(a2lo + eo.off[st], lw[0], lw[1], lw[2], lw[3]);
   }
 }
 
 // Epilogue 2 of two jobs of one plane type (luma: both luma jobs; chroma: U and V): for job j the
 // stage-2 accumulators hi at td2[j] and lo at td2[j] + LO form Z, the row sums of w(u, v) |Z| in
 // increasing u and the block energy H by an xor tree over the NK rows of the block; the block's
-// v = 0 thread stores H at out[j][0] and L = sqrt(Z(0,0)) at out[j][C] (null: block outside the
-// frame).  DUMP: the coefficients to zd[j] (u-major) as well.  The TMEM loads of the next 8
-// columns are in flight while the current ones are processed.
+// v = 0 thread stores job 0's H at out[0][0] and L = sqrt(Z(0,0)) at out[0][C], its v = NK/2
+// thread job 1's at out[1] (null: block outside the frame).  DUMP: the coefficients to zd[j]
+// (u-major) as well.  The TMEM loads of the next 8 columns are in flight while the current ones
+// are processed.
 template <int Nb, bool LP, bool DUMP, int LO>
 __device__ __forceinline__ void epilogue2(const uint32_t (&td2)[2], int lane, const float (&wts)[PC<Nb, LP>::NK],
                                           float einv, float c2, float* const (&out)[2], int64_t C,
@@ -397,7 +413,7 @@ __device__ __forceinline__ void epilogue2(const uint32_t (&td2)[2], int lane, co
   uint32_t bh[2][8], bl[2][8];
   tmem_ld<8>(td2[0], bh[0]);
   tmem_ld<8>(td2[0] + LO, bl[0]);
-  float H = 0.0f, z00 = 0.0f;
+  float H = 0.0f, H0 = 0.0f, z00 = 0.0f, z0 = 0.0f;
 #pragma unroll
   for (int st = 0; st < S; ++st) {
     const int j = st / CPJ, h0 = (st % CPJ) * 8;
@@ -416,15 +432,26 @@ __device__ __forceinline__ void epilogue2(const uint32_t (&td2)[2], int lane, co
       if (DUMP && zd[j]) zd[j][u * NK + v] = (int16_t)z;
       H = fmaf(fabsf(z), wts[u], H);
     }
-    if (h0 + 8 == NK) {  // job j complete
-#pragma unroll
-      for (int o = NK / 2; o > 0; o >>= 1) H += __shfl_xor_sync(0xffffffffu, H, o);
-      if (out[j] && v == 0) {
-        out[j][0] = H;
-        out[j][C] = __fsqrt_rn(z00);
-      }
+    if (j == 0 && h0 + 8 == NK) {  // job 0 complete
+      H0 = H;
+      z0 = z00;
       H = 0.0f;
     }
+  }
+  // Both xor trees in one: the first stage sends job 1's row sum from the lower half of the block's
+  // lanes and job 0's from the upper half, so that the lower half goes on with job 0 and the upper
+  // half with job 1 -- every addition is the one of the separate trees (operands swapped at most).
+  const bool upper = (v & (NK / 2)) != 0;
+  float X = (upper ? H : H0) + __shfl_xor_sync(0xffffffffu, upper ? H0 : H, NK / 2);
+#pragma unroll
+  for (int o = NK / 4; o > 0; o >>= 1) X += __shfl_xor_sync(0xffffffffu, X, o);
+  // job 1's Z(0,0) (held by its v = 0 lane) to the block's v = NK/2 lane; one square root for both
+  const float z1 = __shfl_xor_sync(0xffffffffu, z00, NK / 2);
+  const float L = __fsqrt_rn(upper ? z1 : z0);
+  float* const o = upper ? out[1] : out[0];
+  if (o && (v & (NK / 2 - 1)) == 0) {
+    o[0] = X;
+    o[C] = L;
   }
 }
 
@@ -668,6 +695,7 @@ __device__ void epi1_luma_loop(const Ctl& ctl, uint32_t sbase, uint32_t tq, int 
   using U = Unit<LP>;
   using P = PC<32, LP>;
   const float s1inv = __int_as_float((127 - s1_of<32>(BPS)) << 23);  // 2^-s1
+  const E1Offs<32, LP> eo(q, lane);
   Cursor<U::DS> cd;
   Cursor<kA2Sets> ce;
   const int n = n_items * U::UPT;
@@ -680,7 +708,7 @@ __device__ void epi1_luma_loop(const Ctl& ctl, uint32_t sbase, uint32_t tq, int 
 #pragma unroll 1
     for (int j = 0; j < 2; ++j) {
       const uint32_t ahi = a2_luma(a2, j);
-      epilogue1<32, LP>(td + j * P::G * P::N1, ahi, ahi + kA2L, q, lane, s1inv);
+      epilogue1<32, LP>(td + j * P::G * P::N1, ahi, ahi + kA2L, eo, s1inv);
     }
     fence_proxy_async_smem();
     tc_fence_before();
@@ -743,12 +771,13 @@ __device__ void epi2_luma_loop(const PP& p, const MS& ms, const TileRec* recs, c
 // epilogue 2 of unit u - 1.
 template <bool LP, bool DUMP, int BPS, class PP, class MS>
 __device__ void chroma_epi_loop(const PP& p, const MS& ms, const TileRec* recs, const Ctl& ctl, uint32_t sbase,
-                                uint32_t tq, int n_items, int q, int lane) {
+                                uint32_t tq, int n_items, int q, int lane, int mode) {
   using SL = SmemLay<BPS>;
   using U = Unit<LP>;
   using P = PC<16, LP>;
   constexpr int NKC = U::NKC, NCC = U::NCC;
   const float s1inv = __int_as_float((127 - s1_of<16>(BPS)) << 23);
+  const E1Offs<16, LP> eo(q, lane);
   float w[P::NK];
 #pragma unroll
   for (int uu = 0; uu < P::NK; ++uu) w[uu] = p.W_c[uu * 16 + (lane % P::NK)];
@@ -757,7 +786,7 @@ __device__ void chroma_epi_loop(const PP& p, const MS& ms, const TileRec* recs, 
   const int n = n_items * U::UPT;
   TileRec rec{};
   for (int u = 0, t = 0, h = 0; u <= n; ++u) {
-    if (u < n) {  // epilogue 1 of unit u
+    if (u < n && (mode & 1)) {  // epilogue 1 of unit u
       if (!wait_bar(ctl, b_d1c(cd.slot), cd.par, 4)) return;
       if (u >= kA2Sets && !wait_bar(ctl, b_a2c_free(ce.slot), ce.par ^ 1u, 4)) return;
       tc_fence_after();
@@ -766,7 +795,7 @@ __device__ void chroma_epi_loop(const PP& p, const MS& ms, const TileRec* recs, 
 #pragma unroll 1
       for (int pl = 0; pl < 2; ++pl) {
         const uint32_t ahi = a2_chroma(a2, pl);
-        epilogue1<16, LP>(td + pl * NKC, ahi, ahi + kA2C, q, lane, s1inv);
+        epilogue1<16, LP>(td + pl * NKC, ahi, ahi + kA2C, eo, s1inv);
       }
       fence_proxy_async_smem();
       tc_fence_before();
@@ -775,7 +804,7 @@ __device__ void chroma_epi_loop(const PP& p, const MS& ms, const TileRec* recs, 
       cd.next();
       ce.next();
     }
-    if (u >= 1) {  // epilogue 2 of unit u - 1
+    if (u >= 1 && (mode & 2)) {  // epilogue 2 of unit u - 1
       if (!wait_bar(ctl, b_d2c(cd2.slot), cd2.par, 4)) return;
       tc_fence_after();
       if (h == 0) rec = load_rec(recs, t);
@@ -1103,8 +1132,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     epi1_luma_loop<LP, BPS>(ctl, sbase, tmem + lanebase, n_items, q, lane);
   } else if (role == 5) {
     epi2_luma_loop<LP, DUMP>(p, ms, recs, ctl, tmem + lanebase, n_items, q, lane);
+  } else if (role == 6) {
+    chroma_epi_loop<LP, DUMP, BPS>(p, ms, recs, ctl, sbase, tmem + lanebase, n_items, q, lane, 1);
   } else {
-    chroma_epi_loop<LP, DUMP, BPS>(p, ms, recs, ctl, sbase, tmem + lanebase, n_items, q, lane);
+    chroma_epi_loop<LP, DUMP, BPS>(p, ms, recs, ctl, sbase, tmem + lanebase, n_items, q, lane, 2);
   }
 
   tc_fence_before();
