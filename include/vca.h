@@ -362,26 +362,30 @@ vca_status vca_siti_close(vca_siti* s);
  * up front to decide admission; a host thread with other streams in flight, for which an
  * allocation may block and a free waits for the whole device).
  *
- * Computes, like the analyzer (Section 2 of the paper), per frame f: E_P = sum_k H_{P,k} /
- * (C N_P^2), L_P = sum_k L_{P,k} / C, h = sum_k |H_{Y,k,f} - H_{Y,k,f-1}| / (C w^2).
+ * It runs the analyzer's own frame reduction: per frame f, E_P = sum_k H_{P,k} / (C N_P^2),
+ * L_P = sum_k L_{P,k} / C, h = sum_k |H_{Y,k,f} - H_{Y,k,f-1}| / (C w^2), each sum exact in
+ * 2^-23 fixed point and rounded once to FP64.
  *   block_values  device, [n_frames][6][C] FP32, rows H_Y, L_Y, H_U, L_U, H_V, L_V (C =
- *                 blocks_per_plane, raster block order); read only.  Values must lie in
- *                 [0, 2^30); each is summed exactly when it is a multiple of 2^-23 (every value
- *                 the analyzer writes is: 0 or at least 1), else rounded to the nearest one.
- *   block_size    luma block size w: 32 or 16 (chroma blocks are w/2).
+ *                 blocks_per_plane, raster block order) of a 4:2:0 analyzer; read only.  Each
+ *                 value in [0, 2^30) is summed exactly after truncation toward zero to a
+ *                 multiple of 2^-23 (every value the analyzer writes is a multiple already: 0
+ *                 or at least 1).  Values outside [0, 2^30) -- negative (also -0.0), NaN,
+ *                 infinite or too large -- count as 0.
+ *   block_size    luma block size w: 32 or 16.  Chroma blocks are taken as w/2 x w/2 (4:2:0):
+ *                 block values of a 4:4:4 analyzer would give E_U and E_V 4 times too large.
  *   n_frames      1 .. 256: the frames the fixed scratch holds; more gives VCA_E_ARG.
  *   prev_H_Y      device, C FP32 luma energies of the frame before frame 0, or NULL for h = 0
  *                 on frame 0.
  *   last_H_Y      device, C FP32, receives H_Y of frame n_frames - 1 (the next call's
- *                 prev_H_Y); must not be prev_H_Y.
+ *                 prev_H_Y); its bytes must overlap neither prev_H_Y nor block_values.
  *   features      device, n_frames x 8 doubles: E_Y, h, L_Y, E_U, E_V, L_U, L_V, 0.
  *   cuda_stream   the stream the work is queued on (NULL: legacy default stream); the call
  *                 returns without waiting.
  * The caller owns every buffer.  The scratch is one fixed array per device: calls that may
  * overlap on the device (unordered streams, several host threads) race on it; order them.
  * The first call on a device looks the array up and may load the module, so make it before
- * any stream capture.  VCA_E_ARG for NULL outputs, a bad block size or a size outside the
- * limits; VCA_E_CUDA if the lookup or the launch fails. */
+ * any stream capture.  VCA_E_ARG for NULL outputs, a bad block size, a size outside the
+ * limits or overlapping buffers; VCA_E_CUDA if the lookup or the launch fails. */
 vca_status vca_reduce_frames_noalloc(const float* block_values, int64_t blocks_per_plane, int32_t block_size,
                                      int32_t n_frames, const float* prev_H_Y, float* last_H_Y,
                                      double* features, void* cuda_stream);

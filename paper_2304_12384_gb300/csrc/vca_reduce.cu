@@ -37,12 +37,14 @@ int slices_for(int64_t C) {
   return (int)(s < 1 ? 1 : s > kMaxSlices ? kMaxSlices : s);
 }
 
-// v * 2^23 for a block value v that is 0 or a float in [1, 2^40): the significand shifted by the
-// unbiased exponent.  (The analyzer writes no value in (0, 1); such a value would be truncated.)
+// v * 2^23 truncated to an integer, for a block value v in [0, 2^30): the significand shifted by
+// the unbiased exponent.  Every value the analyzer writes is 0 or at least 1 (a multiple of
+// 2^-23), so nothing is truncated for them.  Values outside [0, 2^30) -- negative (also -0.0),
+// NaN, infinite or 2^30 and above -- and values below 2^-24 count as 0.
 __device__ __forceinline__ unsigned long long fixed23(float v) {
   const uint32_t b = __float_as_uint(v);
-  if (b == 0u) return 0ull;
-  const int e = (int)(b >> 23) - 127;
+  const int e = (int)(b >> 23) - 127;  // 128 for NaN and infinities
+  if ((b >> 31) != 0u || e >= 30 || e < -24) return 0ull;
   const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
   return e >= 0 ? m << e : m >> -e;
 }
@@ -296,8 +298,20 @@ extern "C" vca_status vca_reduce_frames_noalloc(const float* block_values, int64
              (int)n_frames, kNoAllocMaxFrames);
     return noalloc_fail(VCA_E_ARG, msg);
   }
-  if (prev_H_Y == last_H_Y)
-    return noalloc_fail(VCA_E_ARG, "vca_reduce_frames_noalloc: prev_H_Y and last_H_Y must be different buffers");
+  // last_H_Y is written by the CTAs of the last frame while others still read prev_H_Y and the
+  // block values: its bytes may overlap neither.
+  {
+    const uintptr_t l0 = (uintptr_t)last_H_Y, l1 = l0 + (uintptr_t)blocks_per_plane * sizeof(float);
+    const uintptr_t b0 = (uintptr_t)block_values,
+                    b1 = b0 + (uintptr_t)n_frames * N_ROWS * (uintptr_t)blocks_per_plane * sizeof(float);
+    if (l0 < b1 && b0 < l1)
+      return noalloc_fail(VCA_E_ARG, "vca_reduce_frames_noalloc: last_H_Y overlaps block_values");
+    if (prev_H_Y) {
+      const uintptr_t p0 = (uintptr_t)prev_H_Y, p1 = p0 + (uintptr_t)blocks_per_plane * sizeof(float);
+      if (l0 < p1 && p0 < l1)
+        return noalloc_fail(VCA_E_ARG, "vca_reduce_frames_noalloc: last_H_Y overlaps prev_H_Y");
+    }
+  }
 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

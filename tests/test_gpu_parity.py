@@ -368,3 +368,50 @@ def test_drop_in_matrix_rules(vca):
         assert ei.value.status == vca.VCA_E_STATE
     finally:
         an.close()
+
+
+# ---- per-feature error of the tensor-core path against the FP64 oracle ----
+
+def _feature_error_table(vca, frames, width, height, bit_depth):
+    """Max relative error per feature over the frames (h also relative to max(h, E_Y))."""
+    from vca_testutil import FEATURES
+
+    an = open_analyzer(vca, "tc", width=width, height=height, bit_depth=bit_depth, block_size=32, low_pass=True,
+                       max_batch=len(frames))
+    try:
+        an.push(*to_device(frames))
+        per, _ = oracle_sequence(frames, oracle_config(an))
+        err = {k: 0.0 for k in FEATURES}
+        err["h_vs_max(h,E_Y)"] = 0.0
+        for t, exp in enumerate(per):
+            got = an.frame_features(t)
+            for k in FEATURES:
+                if exp[k] != 0.0:
+                    err[k] = max(err[k], abs(got[k] - exp[k]) / abs(exp[k]))
+                else:
+                    assert got[k] == 0.0, (t, k, got[k])
+            err["h_vs_max(h,E_Y)"] = max(err["h_vs_max(h,E_Y)"],
+                                         abs(got["h"] - exp["h"]) / max(abs(exp["h"]), abs(exp["E_Y"])))
+        return err
+    finally:
+        an.close()
+
+
+@pytest.mark.parametrize("case", ["2160p_8bit", "ladder_1080p_10bit"])
+def test_feature_error_statement(vca, case):
+    # The error of every feature against the FP64 oracle, measured and printed (pytest -s shows the
+    # table), and bounded: E and L within 1e-6 relative; h within 1e-6 relative to max(h, E_Y) (h is a
+    # sum of differences of FP32 block energies and cancels), and here also within 1e-5 of itself.
+    if case == "2160p_8bit":
+        frames = frames_list(uhd_spec(3), 0, 4)
+        err = _feature_error_table(vca, frames, 3840, 2160, 8)
+    else:
+        from synth import ladder_specs
+        spec = [s for s in ladder_specs(4, n_frames=6) if s.width == 1920 and s.bit_depth == 10][0]
+        frames = frames_list(spec)
+        err = _feature_error_table(vca, frames, 1920, 1080, 10)
+    print(f"\nmax relative error per feature ({case}): " + ", ".join(f"{k} {v:.2e}" for k, v in err.items()))
+    for k in ("E_Y", "L_Y", "E_U", "E_V", "L_U", "L_V"):
+        assert err[k] <= 1e-6, (k, err[k])
+    assert err["h_vs_max(h,E_Y)"] <= 1e-6
+    assert err["h"] <= 1e-5
