@@ -54,7 +54,7 @@ def parse_args():
     p.add_argument("--full", action="store_true", help="all coefficients instead of the low-pass subset")
     p.add_argument("--no-extras", action="store_true", help="skip variants, latency, e2e and cpu baseline")
     p.add_argument("--extras", default="all",
-                   help="comma-separated subset of latency,e2e,variants,siti,ladder,serving,cpu (default all)")
+                   help="comma-separated subset of latency,e2e,variants,tune,siti,ladder,serving,cpu (default all)")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     return p.parse_args()
 
@@ -477,6 +477,19 @@ def run_extras(args, an, y, u, v, frames, stream, kern, lp, device):
         del y10, u10, v10
         out["variants"] = variants
 
+    if want("tune"):
+        # Launch-shape tuning of the benchmark's configuration on its own frames (16 of them): every
+        # candidate's analysis time per frame, the chosen shape and its gain over the default one.
+        vca.vca_tune_clear()
+        cfg = vca._config(W, H, 8, args.block_size, lp)
+        chosen, cands = vca.vca_autotune(cfg, y[:16], u[:16], v[:16], reps=5, stream=stream.cuda_stream)
+        default = [c for c in cands if c["kernel"] == 2 and c["tc_ctas"] == 0] or \
+                  [c for c in cands if c["kernel"] == 1 and c["plain_warps"] == 4]
+        out["tune"] = {"chosen": chosen, "candidates": cands,
+                       "gain_over_default": default[0]["ms_per_frame"] / chosen["ms_per_frame"],
+                       "note": "vca_autotune on 16 of the step's frames; the bench step itself runs the default shape"}
+        vca.vca_tune_clear()
+
     if want("siti"):
         # SI / TI of the same 2160p frames (the paper's comparison features; its CPU reference runs
         # at 8.55 fps on an i7-11370H, Section 3 -- another machine, context only).
@@ -570,15 +583,22 @@ def run_ladder(args, stream, distinct=2, ticks=200):
     batch = vca.Batch(ans)
     batch_refs = [batch.frame_refs(r) for r in tick_refs]
     warm = 10
-    for t in range(warm):
-        batch.tick(batch_refs[t % distinct])
-    batch.sync()
-    t0 = time.perf_counter()
-    for t in range(ticks):
-        batch.tick(batch_refs[t % distinct])
-    batch.sync()
-    el_b = time.perf_counter() - t0
-    launches = batch.launches()
+
+    def timed_ticks():
+        for t in range(warm):
+            batch.tick(batch_refs[t % distinct])
+        batch.sync()
+        t0 = time.perf_counter()
+        for t in range(ticks):
+            batch.tick(batch_refs[t % distinct])
+        batch.sync()
+        return time.perf_counter() - t0
+
+    el_default = timed_ticks()  # SM split weight at creation (1.15)
+    weight, _ = batch.autotune(batch_refs[0], reps=40)
+    l0 = batch.launches()
+    el_b = timed_ticks()
+    launches = batch.launches() - l0
     batch.close()
 
     for t in range(3):
@@ -601,6 +621,7 @@ def run_ladder(args, stream, distinct=2, ticks=200):
             "batched_ticks_per_s": tb, "batched_gbs": tb * tick_bytes / 1e9,
             "batched_hbm_frac_of_measured": tb * tick_bytes / 1e9 / peak,
             "batched_launches_per_tick": launches / (ticks + warm),
+            "split_weight_tuned": weight, "batched_ticks_per_s_untuned": ticks / el_default,
             "per_channel_push_ticks_per_s": ticks / el_s,
             "hbm_roofline_ticks_per_s": peak * 1e9 / tick_bytes,
             "timing": "host wall clock around queued ticks, synchronized at both ends; frames device-resident"}

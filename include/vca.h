@@ -264,6 +264,61 @@ vca_status vca_batch_launch_count(vca_batch* b, int64_t* launches);
 /* Waits for the batch's ticks and dissolves it; the analyzers stay open.  NULL is accepted. */
 vca_status vca_batch_destroy(vca_batch* b);
 
+/* ---- Launch-shape tuning ------------------------------------------------------------------
+ * Run-time tuning of how the kernels are launched (the paper, whose speed comes from a CPU
+ * design, has no counterpart).  The library keeps one table of launch shapes per process, one
+ * entry per analyzer configuration (width, height, bit depth, block size, low-pass, chroma
+ * format).  vca_open follows the entry of its configuration: the kernel family when cfg->kernel
+ * is VCA_KERNEL_AUTO (an entry naming the tensor-core form where it cannot run is ignored), and
+ * the CTA sizes whatever the kernel.  Every shape computes the same features, bit for bit.  The
+ * table starts empty, or with the file named by the environment variable VCA_TUNE_FILE (read at
+ * the first vca_open or tuning call; a missing or bad file is ignored). */
+typedef struct {
+  int32_t width, height, bit_depth, block_size, low_pass, chroma_format;  /* the configuration */
+  int32_t kernel;       /* VCA_KERNEL_PLAIN or VCA_KERNEL_TC */
+  int32_t plain_warps;  /* CTA size of the CUDA-core form: 2, 4 or 8 warps (blocks per CTA =
+                           warps * 32 / w for luma, warps * 32 / (w/2) for 4:2:0 chroma) */
+  int32_t tc_ctas;      /* CTAs of a tensor-core launch: 0 = one per SM (never more than the SMs) */
+  float ms_per_frame;   /* analysis time per frame measured for this shape, 0 if not measured */
+} vca_tune_entry;
+
+/* Measures every candidate shape of configuration cfg on the current device -- the CUDA-core form
+ * with 2, 4 and 8 warps per CTA; the tensor-core form, where it covers cfg, on all, three
+ * quarters and half of the SMs (even counts) -- by pushing the caller's n_frames device frames
+ * (planes as for vca_push_frames, 16-byte aligned) reps times through a temporary analyzer per
+ * candidate (after two untimed pushes), timing the analysis kernels with CUDA events on
+ * cuda_stream.  The fastest becomes cfg's table entry and is returned in *chosen; the first
+ * max_candidates measured candidates go to candidates[] and their count to *n_candidates (either
+ * may be NULL).  Allocates device memory for the temporary analyzers: not for a hot path.
+ * VCA_E_ARG for a bad configuration or arguments; errors of vca_open / vca_push_frames pass on. */
+vca_status vca_autotune(const vca_config* cfg, const void* y, const void* u, const void* v, int64_t pitch_y,
+                        int64_t pitch_uv, int64_t frame_stride_y, int64_t frame_stride_uv, int32_t n_frames,
+                        int32_t reps, void* cuda_stream, vca_tune_entry* candidates, int32_t max_candidates,
+                        int32_t* n_candidates, vca_tune_entry* chosen);
+/* Adds or replaces the entry of e's configuration (VCA_E_ARG for a bad configuration or shape). */
+vca_status vca_tune_set(const vca_tune_entry* e);
+/* The entry of cfg's configuration (cfg->kernel and max_batch are not part of the key);
+ * VCA_E_AGAIN if the table has none. */
+vca_status vca_tune_lookup(const vca_config* cfg, vca_tune_entry* out);
+vca_status vca_tune_clear(void);
+/* The table as text, one entry per line: width height bit_depth block_size low_pass
+ * chroma_format kernel plain_warps tc_ctas ms_per_frame ('#' starts a comment line).  Load
+ * replaces the table; a file with a malformed line gives VCA_E_ARG and leaves it unchanged. */
+vca_status vca_tune_save(const char* path);
+vca_status vca_tune_load(const char* path);
+
+/* A batch whose tensor-core members come in two sample sizes runs a tick as two launches side by
+ * side, with the SMs split in proportion to their tiles, a tile of 16-bit words weighted against a
+ * byte tile.  vca_batch_split_weight sets that weight (0.25 .. 4; 1.15 at creation);
+ * vca_batch_autotune ticks the batch reps times with frames (after two untimed ticks) for each
+ * weight in {1.0, 1.15, 1.3, 1.5, 1.75}, timed with CUDA events on the batch's stream, keeps the
+ * fastest for the batch and returns it with its milliseconds per tick (a batch of one sample size
+ * is timed once and keeps its weight).  The ticks are real: their features reach the members.
+ * Call with the batch's device current. */
+vca_status vca_batch_split_weight(vca_batch* b, float weight);
+vca_status vca_batch_autotune(vca_batch* b, const vca_frame_ref* frames, int32_t reps, float* weight,
+                              float* ms_per_tick);
+
 /* ---- Serving runtime ----------------------------------------------------------------------
  *
  * A server holds live channels (one analyzer each, h state kept on the device between segments)

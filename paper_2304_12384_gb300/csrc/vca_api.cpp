@@ -88,6 +88,8 @@ struct vca_analyzer {
   int64_t down_pitch_y = 0, down_pitch_uv = 0;
   size_t down_off_u = 0, down_off_v = 0;
   int kernel = VCA_KERNEL_PLAIN;
+  int plain_warps = 4;   // CTA size of the CUDA-core form (launch-shape table or 4)
+  int tc_ctas = 0;       // CTAs of a tensor-core launch (0: one per SM)
   int device = 0;
   cudaStream_t stream = nullptr;
   int max_batch = kDefaultBatch;
@@ -165,6 +167,7 @@ struct vca_batch {
   // 10-bit in 16-bit words); two groups run as two launches on forked streams of the graph.
   int tc_groups = 1;
   int tc_gbps[2] = {1, 2};
+  float w16 = 1.15f;  // a tile of 16-bit words against a byte tile, when the SMs are split
   int sms = 1;                     // SMs of the device: the CTAs of a tick's tensor-core launches
   std::vector<uint8_t> tc_params[2];  // per group: the launch's parameter block (member table, tensor maps)
   cudaGraphNode_t tc_node[2][2] = {};  // per graph and group: the tensor-core launch's node
@@ -451,8 +454,8 @@ cudaError_t run_analysis(vca_analyzer* a, const FramePlanes& fp_in, int n, float
                      a->down_pitch_uv, (int64_t)a->down_fbytes, (int64_t)a->down_fbytes};
   }
   if (a->kernel == VCA_KERNEL_TC)
-    return vca::launch_tc(a->g, fp, n, a->tables, blockvals, zdump, err, a->stream, &a->launches);
-  return vca::launch_plain(a->g, fp, n, a->tables, blockvals, zdump, a->stream, &a->launches);
+    return vca::launch_tc(a->g, fp, n, a->tables, blockvals, zdump, err, a->stream, &a->launches, a->tc_ctas);
+  return vca::launch_plain(a->g, fp, n, a->tables, blockvals, zdump, a->stream, &a->launches, a->plain_warps);
 }
 
 
@@ -643,6 +646,16 @@ vca::PlainArgs member_plain_args(const vca_analyzer* a, int kind, const vca_fram
 
 }  // namespace
 
+namespace vca {
+vca_status set_launch_shape(vca_analyzer* a, int plain_warps, int tc_ctas) {
+  if (!a || (plain_warps != 2 && plain_warps != 4 && plain_warps != 8) || tc_ctas < 0)
+    return fail(VCA_E_ARG, "launch shape: plain_warps 2, 4 or 8 and tc_ctas >= 0");
+  a->plain_warps = plain_warps;
+  a->tc_ctas = tc_ctas;
+  return VCA_OK;
+}
+}  // namespace vca
+
 extern "C" {
 
 vca_status vca_block_count(const vca_config* cfg, int64_t* blocks_x, int64_t* blocks_y) {
@@ -661,7 +674,14 @@ vca_status vca_open(const vca_config* cfg, void* cuda_stream, vca_analyzer** out
   vca_status s = check_config(cfg, &g, &gin);
   if (s != VCA_OK) return s;
   int kernel = cfg->kernel;
-  if (kernel == VCA_KERNEL_AUTO) kernel = vca::tc_supported(g) ? VCA_KERNEL_TC : VCA_KERNEL_PLAIN;
+  // The launch-shape table (vca_autotune / vca_tune_*) gives this configuration's CTA sizes and,
+  // for VCA_KERNEL_AUTO, the kernel family.
+  vca_tune_entry shape{};
+  const bool tuned = vca::tune_lookup(*cfg, &shape);
+  if (kernel == VCA_KERNEL_AUTO)
+    kernel = tuned && (shape.kernel == VCA_KERNEL_PLAIN || vca::tc_supported(g))
+                 ? shape.kernel
+                 : (vca::tc_supported(g) ? VCA_KERNEL_TC : VCA_KERNEL_PLAIN);
   if (kernel == VCA_KERNEL_TC && !vca::tc_supported(g))
     return fail(VCA_E_UNSUPPORTED, "the tensor-core kernel does not support this configuration");
 
@@ -671,6 +691,10 @@ vca_status vca_open(const vca_config* cfg, void* cuda_stream, vca_analyzer** out
   a->g = g;
   a->gin = gin;
   a->kernel = kernel;
+  if (tuned) {
+    a->plain_warps = shape.plain_warps;
+    a->tc_ctas = shape.tc_ctas;
+  }
   a->stream = (cudaStream_t)cuda_stream;
   a->max_batch = cfg->max_batch > 0 ? cfg->max_batch : kDefaultBatch;
   cudaError_t e = cudaGetDevice(&a->device);
@@ -1230,7 +1254,7 @@ vca_status vca_batch_tick(vca_batch* b, const vca_frame_ref* frames) {
     // ran 1.6x slower than all the others (measured), which set the tick's time.
     double w[2];
     for (int gi = 0; gi < 2; ++gi)
-      w[gi] = vca::tc_batch_items(b->tc_params[gi].data()) * (b->tc_gbps[gi] == 2 ? 1.15 : 1.0);
+      w[gi] = vca::tc_batch_items(b->tc_params[gi].data()) * (b->tc_gbps[gi] == 2 ? (double)b->w16 : 1.0);
     int g0 = w[0] + w[1] > 0.0 ? (int)std::lround(b->sms * w[0] / (w[0] + w[1])) : b->sms / 2;
     g0 = (g0 + 1) & ~1;
     const int lo = b->sms >= 4 ? 2 : 1;  // a launch with no tiles this tick still gets a (full) SM pair
@@ -1289,6 +1313,51 @@ vca_status vca_batch_sync(vca_batch* b) {
 vca_status vca_batch_kernel(vca_batch* b, int32_t* kernel) {
   if (!b || !kernel) return fail(VCA_E_ARG, "NULL argument");
   *kernel = b->tc ? VCA_KERNEL_TC : VCA_KERNEL_PLAIN;
+  return VCA_OK;
+}
+
+vca_status vca_batch_split_weight(vca_batch* b, float weight) {
+  if (!b || !(weight >= 0.25f && weight <= 4.0f)) return fail(VCA_E_ARG, "split weight must be in [0.25, 4]");
+  b->w16 = weight;
+  return VCA_OK;
+}
+
+vca_status vca_batch_autotune(vca_batch* b, const vca_frame_ref* frames, int32_t reps, float* weight,
+                              float* ms_per_tick) {
+  if (!b || !frames || reps < 1) return fail(VCA_E_ARG, "vca_batch_autotune: needs a batch, frames and reps >= 1");
+  const float cands[] = {1.0f, 1.15f, 1.3f, 1.5f, 1.75f};
+  const bool split = b->tc && b->tc_groups == 2;
+  float best_w = b->w16, best_ms = -1.0f;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  VCA_CUDA(cudaEventCreate(&e0), "creating tuning events");
+  VCA_CUDA(cudaEventCreate(&e1), "creating tuning events");
+  vca_status st = VCA_OK;
+  for (float w : cands) {
+    if (!split && w != cands[0]) break;  // one sample size: nothing to split, one timing
+    if (split) b->w16 = w;
+    for (int r = 0; st == VCA_OK && r < 2; ++r) st = vca_batch_tick(b, frames);  // warm-up
+    if (st == VCA_OK) st = vca_batch_sync(b);
+    if (st != VCA_OK) break;
+    cudaEventRecord(e0, b->stream);
+    for (int r = 0; st == VCA_OK && r < reps; ++r) st = vca_batch_tick(b, frames);
+    cudaEventRecord(e1, b->stream);
+    if (st == VCA_OK) st = vca_batch_sync(b);
+    if (st != VCA_OK) break;
+    float ms = 0.0f;
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= (float)reps;
+    if (best_ms < 0.0f || ms < best_ms) {
+      best_ms = ms;
+      best_w = w;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != VCA_OK) return st;
+  b->w16 = best_w;
+  if (weight) *weight = best_w;
+  if (ms_per_tick) *ms_per_tick = best_ms;
   return VCA_OK;
 }
 

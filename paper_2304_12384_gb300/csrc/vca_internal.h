@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "vca.h"
+
 namespace vca {
 
 // Per-frame block values are stored as [frame][6][C] FP32: the order of the six rows.
@@ -89,14 +91,18 @@ bool check_dct_matrix(int N, int B, const int8_t* m, char* why, size_t why_len);
 // CUDA-core analysis of n frames: writes block values (and, when the dump pointers are
 // non-null, the quantised coefficients of frame 0).  Returns the launch status and adds
 // the number of kernels launched to *launches.
+// warps: CTA size of the block routine, 2, 4 or 8 warps (blocks per CTA = warps * 32 / N).
 cudaError_t launch_plain(const Geometry& g, const FramePlanes& fp, int nframes, const DeviceTables& t,
-                         float* blockvals, int16_t* const zdump[3], cudaStream_t s, int64_t* launches);
+                         float* blockvals, int16_t* const zdump[3], cudaStream_t s, int64_t* launches,
+                         int warps = 4);
 
 // Tensor-core analysis (same outputs).  Returns cudaErrorNotSupported if the geometry is
 // outside what the tensor-core kernel handles.  *err (device) receives a nonzero code if a
 // bounded wait inside the kernel gave up.
+// ctas: CTAs of the launch (0: one per SM; never more than the SMs or the tiles).
 cudaError_t launch_tc(const Geometry& g, const FramePlanes& fp, int nframes, const DeviceTables& t,
-                      float* blockvals, int16_t* const zdump[3], int* err, cudaStream_t s, int64_t* launches);
+                      float* blockvals, int16_t* const zdump[3], int* err, cudaStream_t s, int64_t* launches,
+                      int ctas = 0);
 bool tc_supported(const Geometry& g);
 
 // Batched tensor-core analysis: one frame of each of up to tc_batch_max_members() analyzers of
@@ -210,5 +216,10 @@ cudaError_t launch_downsample(const DownArgs& a, int nframes, int bps, cudaStrea
 
 // Sets the calling thread's vca_last_error message.
 void record_error(const char* msg);
+
+// Launch shapes (vca_tune.cpp): the table entry of a configuration, if any; an analyzer's CTA
+// size of the CUDA-core form (2, 4 or 8 warps) and CTA count of a tensor-core launch (0: one per SM).
+bool tune_lookup(const vca_config& c, vca_tune_entry* out);
+vca_status set_launch_shape(vca_analyzer* a, int plain_warps, int tc_ctas);
 
 }  // namespace vca

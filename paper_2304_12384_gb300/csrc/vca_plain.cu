@@ -8,33 +8,45 @@
 namespace vca {
 namespace {
 
-template <int N, bool LP, typename Pix>
-__global__ void __launch_bounds__(kWarps * 32) plain_kernel(const PlainArgs p) {
-  __shared__ PlainSmem<N, LP> sh;
-  plain_blocks<N, LP, Pix>(p, blockIdx.y, blockIdx.z, blockIdx.x, sh);
+template <int N, bool LP, typename Pix, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) plain_kernel(const PlainArgs p) {
+  __shared__ PlainSmem<N, LP, WARPS> sh;
+  plain_blocks<N, LP, Pix, WARPS>(p, blockIdx.y, blockIdx.z, blockIdx.x, sh);
 }
 
-template <int N>
+template <int N, int WARPS>
 cudaError_t launch_planes(const PlainArgs& a, int nplanes, int nframes, bool lp, int bps, cudaStream_t s) {
-  constexpr int BPC = kWarps * (32 / N);
+  constexpr int BPC = WARPS * (32 / N);
   dim3 grid((unsigned)((a.C + BPC - 1) / BPC), nplanes, nframes);
-  dim3 block(kWarps * 32);
+  dim3 block(WARPS * 32);
   if (lp) {
-    if (bps == 1) plain_kernel<N, true, uint8_t><<<grid, block, 0, s>>>(a);
-    else plain_kernel<N, true, uint16_t><<<grid, block, 0, s>>>(a);
+    if (bps == 1) plain_kernel<N, true, uint8_t, WARPS><<<grid, block, 0, s>>>(a);
+    else plain_kernel<N, true, uint16_t, WARPS><<<grid, block, 0, s>>>(a);
   } else {
-    if (bps == 1) plain_kernel<N, false, uint8_t><<<grid, block, 0, s>>>(a);
-    else plain_kernel<N, false, uint16_t><<<grid, block, 0, s>>>(a);
+    if (bps == 1) plain_kernel<N, false, uint8_t, WARPS><<<grid, block, 0, s>>>(a);
+    else plain_kernel<N, false, uint16_t, WARPS><<<grid, block, 0, s>>>(a);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_n(int N, const PlainArgs& a, int nplanes, int nframes, bool lp, int bps, cudaStream_t s) {
+template <int WARPS>
+cudaError_t launch_nw(int N, const PlainArgs& a, int nplanes, int nframes, bool lp, int bps, cudaStream_t s) {
   switch (N) {
-    case 32: return launch_planes<32>(a, nplanes, nframes, lp, bps, s);
-    case 16: return launch_planes<16>(a, nplanes, nframes, lp, bps, s);
-    case 8: return launch_planes<8>(a, nplanes, nframes, lp, bps, s);
-    case 4: return launch_planes<4>(a, nplanes, nframes, lp, bps, s);
+    case 32: return launch_planes<32, WARPS>(a, nplanes, nframes, lp, bps, s);
+    case 16: return launch_planes<16, WARPS>(a, nplanes, nframes, lp, bps, s);
+    case 8: return launch_planes<8, WARPS>(a, nplanes, nframes, lp, bps, s);
+    case 4: return launch_planes<4, WARPS>(a, nplanes, nframes, lp, bps, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// warps per CTA: 2, 4 (the default) or 8
+cudaError_t launch_n(int N, const PlainArgs& a, int nplanes, int nframes, bool lp, int bps, cudaStream_t s,
+                     int warps) {
+  switch (warps) {
+    case 2: return launch_nw<2>(N, a, nplanes, nframes, lp, bps, s);
+    case 4: return launch_nw<4>(N, a, nplanes, nframes, lp, bps, s);
+    case 8: return launch_nw<8>(N, a, nplanes, nframes, lp, bps, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -42,7 +54,7 @@ cudaError_t launch_n(int N, const PlainArgs& a, int nplanes, int nframes, bool l
 }  // namespace
 
 cudaError_t launch_plain(const Geometry& g, const FramePlanes& fp, int nframes, const DeviceTables& t,
-                         float* blockvals, int16_t* const zdump[3], cudaStream_t s, int64_t* launches) {
+                         float* blockvals, int16_t* const zdump[3], cudaStream_t s, int64_t* launches, int warps) {
   if (nframes <= 0) return cudaSuccess;
   PlainArgs a{};
   a.nbx = g.nbx;
@@ -65,7 +77,7 @@ cudaError_t launch_plain(const Geometry& g, const FramePlanes& fp, int nframes, 
   a.outH[1] = a.outL[1] = nullptr;
   a.zdump[0] = zdump ? zdump[0] : nullptr;
   a.zdump[1] = nullptr;
-  cudaError_t e = launch_n(g.w, a, 1, nframes, g.low_pass, g.bps, s);
+  cudaError_t e = launch_n(g.w, a, 1, nframes, g.low_pass, g.bps, s, warps);
   if (e != cudaSuccess) return e;
   ++*launches;
 
@@ -86,7 +98,7 @@ cudaError_t launch_plain(const Geometry& g, const FramePlanes& fp, int nframes, 
   a.outL[1] = blockvals + ROW_L_V * g.C;
   a.zdump[0] = zdump ? zdump[1] : nullptr;
   a.zdump[1] = zdump ? zdump[2] : nullptr;
-  e = launch_n(g.nc, a, 2, nframes, g.low_pass, g.bps, s);
+  e = launch_n(g.nc, a, 2, nframes, g.low_pass, g.bps, s, warps);
   if (e != cudaSuccess) return e;
   ++*launches;
   return cudaSuccess;

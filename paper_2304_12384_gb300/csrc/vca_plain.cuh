@@ -94,25 +94,25 @@ struct Butterfly<1, NK, S, LD> {
   static __device__ __forceinline__ void run(const int (&x)[1], int (&y)[NK], const int*) { y[0] = 64 * x[0]; }
 };
 
-// Shared memory of one CTA of the block routine.
-template <int N, bool LP>
+// Shared memory of one CTA of the block routine (WARPS warps).
+template <int N, bool LP, int WARPS = kWarps>
 struct PlainSmem {
   static constexpr int NK = LP ? N / 2 : N;
   static constexpr int BPW = 32 / N;
   __align__(16) int M[N][N];
   float W[NK][NK];
-  int T[kWarps][BPW][N][NK + 1];
+  int T[WARPS][BPW][N][NK + 1];
 };
 
-// Blocks chunk * BPC .. chunk * BPC + BPC - 1 of plane `plane` of frame f (one CTA of 4 warps; the
-// warp owns 32/N blocks).  Stage 1: lane (j, r) keeps row r of block j in registers and produces
+// Blocks chunk * BPC .. chunk * BPC + BPC - 1 of plane `plane` of frame f (one CTA of WARPS warps,
+// BPC = WARPS * 32/N; the warp owns 32/N blocks).  Stage 1: lane (j, r) keeps row r of block j in registers and produces
 // T[r][k]; stage 2: lane (j, v) keeps column v of T and produces Z[u][v], accumulating H_v.
-template <int N, bool LP, typename Pix>
+template <int N, bool LP, typename Pix, int WARPS = kWarps>
 __device__ __forceinline__ void plain_blocks(const PlainArgs& p, int plane, int f, int64_t chunk,
-                                             PlainSmem<N, LP>& sh) {
+                                             PlainSmem<N, LP, WARPS>& sh) {
   constexpr int NK = LP ? N / 2 : N;
   constexpr int BPW = 32 / N;
-  constexpr int BPC = kWarps * BPW;
+  constexpr int BPC = WARPS * BPW;
   auto& sM = sh.M;
   auto& sW = sh.W;
   auto& sT = sh.T;
@@ -120,8 +120,8 @@ __device__ __forceinline__ void plain_blocks(const PlainArgs& p, int plane, int 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const int lane = tid & 31;
-  for (int i = tid; i < N * N; i += kWarps * 32) sM[i / N][i % N] = p.M[i];
-  for (int i = tid; i < NK * NK; i += kWarps * 32) sW[i / NK][i % NK] = p.W[(i / NK) * N + (i % NK)];
+  for (int i = tid; i < N * N; i += WARPS * 32) sM[i / N][i % N] = p.M[i];
+  for (int i = tid; i < NK * NK; i += WARPS * 32) sW[i / NK][i % NK] = p.W[(i / NK) * N + (i % NK)];
   __syncthreads();
 
   const int j = lane / N;

@@ -1344,7 +1344,7 @@ const void* tc_batch_kernel(int bps, bool low_pass) {
 }
 
 cudaError_t launch_tc(const Geometry& g, const FramePlanes& fp, int nframes, const DeviceTables& t, float* blockvals,
-                      int16_t* const zdump[3], int* err, cudaStream_t s, int64_t* launches) {
+                      int16_t* const zdump[3], int* err, cudaStream_t s, int64_t* launches, int ctas) {
   if (!tc_supported(g)) return cudaErrorNotSupported;
   if (nframes <= 0) return cudaSuccess;
   // 8-bit: 128x128 luma boxes (128-byte swizzle), 64x64 chroma boxes (64-byte swizzle); 16-bit:
@@ -1369,7 +1369,8 @@ cudaError_t launch_tc(const Geometry& g, const FramePlanes& fp, int nframes, con
   p.W_y = t.W_y;
   p.W_c = t.W_c;
   p.err = err;
-  const int grid = p.total_items < sm_count() ? p.total_items : sm_count();
+  int grid = ctas > 0 && ctas < sm_count() ? ctas : sm_count();
+  if (p.total_items < grid) grid = p.total_items;
   e = launch_single(p, grid, g.low_pass, zdump != nullptr, bps, s);
   if (e == cudaSuccess) ++*launches;
   return e;

@@ -64,6 +64,16 @@ class VcaFrameRef(ctypes.Structure):
                 ("pitch_y", ctypes.c_int64), ("pitch_uv", ctypes.c_int64)]
 
 
+class VcaTuneEntry(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("bit_depth", ctypes.c_int32),
+                ("block_size", ctypes.c_int32), ("low_pass", ctypes.c_int32), ("chroma_format", ctypes.c_int32),
+                ("kernel", ctypes.c_int32), ("plain_warps", ctypes.c_int32), ("tc_ctas", ctypes.c_int32),
+                ("ms_per_frame", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class VcaSegmentDone(ctypes.Structure):
     _fields_ = [("channel", ctypes.c_int32), ("status", ctypes.c_int32), ("tag", ctypes.c_uint64),
                 ("first_frame", ctypes.c_int64), ("n_frames", ctypes.c_int32), ("pad", ctypes.c_int32),
@@ -111,6 +121,16 @@ _PROTOS = {
     "vca_read_kernel_timing": (_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)),
     "vca_close": (_P,),
     "vca_reduce_frames_noalloc": (_P, _I64, _I32, _I32, _P, _P, _P, _P),
+    "vca_autotune": (ctypes.POINTER(VcaConfig), _P, _P, _P, _I64, _I64, _I64, _I64, _I32, _I32, _P,
+                     ctypes.POINTER(VcaTuneEntry), _I32, ctypes.POINTER(_I32), ctypes.POINTER(VcaTuneEntry)),
+    "vca_tune_set": (ctypes.POINTER(VcaTuneEntry),),
+    "vca_tune_lookup": (ctypes.POINTER(VcaConfig), ctypes.POINTER(VcaTuneEntry)),
+    "vca_tune_clear": (),
+    "vca_tune_save": (ctypes.c_char_p,),
+    "vca_tune_load": (ctypes.c_char_p,),
+    "vca_batch_split_weight": (_P, ctypes.c_float),
+    "vca_batch_autotune": (_P, ctypes.POINTER(VcaFrameRef), _I32, ctypes.POINTER(ctypes.c_float),
+                           ctypes.POINTER(ctypes.c_float)),
     "vca_batch_create": (ctypes.POINTER(_P), _I32, ctypes.POINTER(_P)),
     "vca_batch_tick": (_P, ctypes.POINTER(VcaFrameRef)),
     "vca_batch_sync": (_P,),
@@ -187,6 +207,58 @@ def vca_reduce_frames_noalloc(block_values: int, blocks_per_plane: int, block_si
     """Frame features from device block values with no device allocation (device pointers)."""
     return _check(lib().vca_reduce_frames_noalloc(_P(block_values), blocks_per_plane, block_size, n_frames,
                                                   _P(prev_H_Y or 0), _P(last_H_Y), _P(features), _P(stream)))
+
+
+def _config(width, height, bit_depth=8, block_size=32, low_pass=False, chroma_format=0, kernel=0,
+            max_batch=0) -> "VcaConfig":
+    c = VcaConfig()
+    c.width, c.height, c.bit_depth, c.block_size = width, height, bit_depth, block_size
+    c.low_pass = {False: 0, True: 1, "downsample": 2}.get(low_pass, low_pass)
+    c.chroma_format, c.kernel, c.max_batch = chroma_format, kernel, max_batch
+    return c
+
+
+def vca_autotune(cfg: "VcaConfig", y, u, v, reps: int = 3, stream: int = 0):
+    """Tunes the launch shape of cfg on (F, H, pitch) device frame tensors; returns (chosen entry,
+    list of measured candidates) as dicts.  The chosen shape becomes cfg's table entry."""
+    es = y.element_size()
+    n = y.shape[0]
+    cands = (VcaTuneEntry * 16)()
+    ncand = _I32()
+    chosen = VcaTuneEntry()
+    _check(lib().vca_autotune(ctypes.byref(cfg), _P(y.data_ptr()), _P(u.data_ptr()), _P(v.data_ptr()),
+                              y.stride(-2) * es, u.stride(-2) * es, y.stride(0) * es, u.stride(0) * es, n, reps,
+                              _P(stream), cands, 16, ctypes.byref(ncand), ctypes.byref(chosen)))
+    return chosen.as_dict(), [cands[i].as_dict() for i in range(min(ncand.value, 16))]
+
+
+def vca_tune_set(**entry) -> None:
+    e = VcaTuneEntry()
+    for k, val in entry.items():
+        setattr(e, k, val)
+    _check(lib().vca_tune_set(ctypes.byref(e)))
+
+
+def vca_tune_lookup(cfg: "VcaConfig"):
+    """The table entry of cfg's configuration as a dict, or None."""
+    e = VcaTuneEntry()
+    st = lib().vca_tune_lookup(ctypes.byref(cfg), ctypes.byref(e))
+    if st == VCA_E_AGAIN:
+        return None
+    _check(st)
+    return e.as_dict()
+
+
+def vca_tune_clear() -> None:
+    _check(lib().vca_tune_clear())
+
+
+def vca_tune_save(path: str) -> None:
+    _check(lib().vca_tune_save(os.fsencode(path)))
+
+
+def vca_tune_load(path: str) -> None:
+    _check(lib().vca_tune_load(os.fsencode(path)))
 
 
 def vca_batch_create(handles) -> int:
@@ -482,6 +554,17 @@ class Batch:
 
     def sync(self):
         vca_batch_sync(self.handle)
+
+    def set_split_weight(self, weight: float) -> None:
+        _check(lib().vca_batch_split_weight(_P(self.handle), ctypes.c_float(weight)))
+
+    def autotune(self, frames, reps: int = 20):
+        """Tunes the SM split of this batch's ticks on frames (as for tick); returns (weight, ms per tick)."""
+        if not isinstance(frames, ctypes.Array):
+            frames = self.frame_refs(frames)
+        w, ms = ctypes.c_float(), ctypes.c_float()
+        _check(lib().vca_batch_autotune(_P(self.handle), frames, reps, ctypes.byref(w), ctypes.byref(ms)))
+        return w.value, ms.value
 
     def launches(self) -> int:
         return vca_batch_launch_count(self.handle)
