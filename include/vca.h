@@ -319,6 +319,21 @@ vca_status vca_batch_split_weight(vca_batch* b, float weight);
 vca_status vca_batch_autotune(vca_batch* b, const vca_frame_ref* frames, int32_t reps, float* weight,
                               float* ms_per_tick);
 
+/* ---- Failure-path test hook ----------------------------------------------------------------
+ * Every wait of the tensor-core kernel (on a barrier that a copy, an MMA or another role
+ * completes) gives up after a time limit: the CTA raises a flag, stops its roles, waits for its
+ * own copies and MMAs, frees its tensor memory and returns, and the push's (or tick's) features
+ * are reported lost with VCA_E_TIMEOUT (by the read or sync that meets them, and by every later
+ * read of one of those frames).  After such a report the analyzer (or each member of the batch)
+ * restarts its h chain: the lost frames' energies are no previous-frame state, so the next frame
+ * pushed after the report has h = 0 (a push queued before the report still compares with them).  These calls exercise that path without any fault: wait_limit_ns sets
+ * the limit for the analyzer's (batch's) launches from now on (0: the default, about 2 s), and
+ * withhold_tile >= 0 makes the next push's (tick's first launch's) work item of that number -- its
+ * index among the launch's 128x128 tiles -- get no copies, so the wait for it runs out; -1 none.
+ * No counterpart in the paper.  VCA_E_UNSUPPORTED for the CUDA-core form (it has no waits). */
+vca_status vca_debug_wait(vca_analyzer* a, int64_t wait_limit_ns, int32_t withhold_tile);
+vca_status vca_batch_debug_wait(vca_batch* b, int64_t wait_limit_ns, int32_t withhold_tile);
+
 /* ---- Serving runtime ----------------------------------------------------------------------
  *
  * A server holds live channels (one analyzer each, h state kept on the device between segments)

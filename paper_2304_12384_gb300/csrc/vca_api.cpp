@@ -90,6 +90,8 @@ struct vca_analyzer {
   int kernel = VCA_KERNEL_PLAIN;
   int plain_warps = 4;   // CTA size of the CUDA-core form (launch-shape table or 4)
   int tc_ctas = 0;       // CTAs of a tensor-core launch (0: one per SM)
+  long long dbg_wait_ns = 0;  // failure-path test hook (vca_debug_wait): wait limit of the kernel
+  int dbg_withhold = -1;      // and the tile of the next push whose copies are withheld
   int device = 0;
   cudaStream_t stream = nullptr;
   int max_batch = kDefaultBatch;
@@ -168,6 +170,8 @@ struct vca_batch {
   int tc_groups = 1;
   int tc_gbps[2] = {1, 2};
   float w16 = 1.15f;  // a tile of 16-bit words against a byte tile, when the SMs are split
+  long long dbg_wait_ns = 0;  // failure-path test hook (vca_batch_debug_wait)
+  int dbg_withhold = -1;
   int sms = 1;                     // SMs of the device: the CTAs of a tick's tensor-core launches
   std::vector<uint8_t> tc_params[2];  // per group: the launch's parameter block (member table, tensor maps)
   cudaGraphNode_t tc_node[2][2] = {};  // per graph and group: the tensor-core launch's node
@@ -304,6 +308,15 @@ void destroy(vca_analyzer* a) {
   delete a;
 }
 
+// The result list keeps one entry per pushed frame: a frame lost to a kernel wait timeout has frame
+// number -1 (reading it gives VCA_E_TIMEOUT).
+vca_frame_features lost_frame() {
+  vca_frame_features ff{};
+  ff.frame = -1;
+  ff.E_Y = ff.h = ff.L_Y = ff.E_U = ff.E_V = ff.L_U = ff.L_V = std::nan("");
+  return ff;
+}
+
 vca_status harvest_front(vca_analyzer* a, bool blocking) {
   const auto p = a->pending.front();
   if (blocking) {
@@ -321,6 +334,8 @@ vca_status harvest_front(vca_analyzer* a, bool blocking) {
   }
   if (a->h_err[p.slot] != 0) {
     a->pending.pop_front();
+    a->has_prev = 0;  // the lost frames' energies are no previous-frame state: h restarts
+    for (int i = 0; i < p.n; ++i) a->done.push_back(lost_frame());
     return fail(VCA_E_TIMEOUT, "analysis kernel gave up on a bounded wait (code %d); frames %lld..%lld are lost",
                 a->h_err[p.slot], (long long)p.first, (long long)(p.first + p.n - 1));
   }
@@ -454,7 +469,12 @@ cudaError_t run_analysis(vca_analyzer* a, const FramePlanes& fp_in, int n, float
                      a->down_pitch_uv, (int64_t)a->down_fbytes, (int64_t)a->down_fbytes};
   }
   if (a->kernel == VCA_KERNEL_TC)
-    return vca::launch_tc(a->g, fp, n, a->tables, blockvals, zdump, err, a->stream, &a->launches, a->tc_ctas);
+  {
+    const int withhold = a->dbg_withhold;
+    a->dbg_withhold = -1;  // one push only
+    return vca::launch_tc(a->g, fp, n, a->tables, blockvals, zdump, err, a->stream, &a->launches, a->tc_ctas,
+                          a->dbg_wait_ns, withhold);
+  }
   return vca::launch_plain(a->g, fp, n, a->tables, blockvals, zdump, a->stream, &a->launches, a->plain_warps);
 }
 
@@ -475,6 +495,10 @@ vca_status batch_harvest_front(vca_batch* b, bool blocking) {
   if (code != 0) {
     b->h_err[t.k] = 0;
     b->pending.pop_front();
+    for (const auto& mm : t.members) {  // as for a single analyzer
+      b->m[mm.index]->has_prev = 0;
+      b->m[mm.index]->done.push_back(lost_frame());
+    }
     return fail(VCA_E_TIMEOUT, "batched analysis kernel gave up on a bounded wait (code %d); the tick's frames are lost",
                 code);
   }
@@ -854,6 +878,7 @@ vca_status vca_read_frame_features(vca_analyzer* a, int64_t frame, int32_t block
     if (s != VCA_OK) return s;
   }
   *out = a->done[(size_t)(frame - a->done_base)];
+  if (out->frame < 0) return fail(VCA_E_TIMEOUT, "frame %lld was lost to a kernel wait timeout", (long long)frame);
   return VCA_OK;
 }
 
@@ -1243,9 +1268,10 @@ vca_status vca_batch_tick(vca_batch* b, const vca_frame_ref* frames) {
   int grid[2] = {b->sms, b->sms};
   for (int gi = 0; b->tc && gi < b->tc_groups; ++gi) {
     cudaError_t e = vca::tc_batch_fill(b->tc_params[gi].data(), b->tc_frames[gi].data(), (int)b->tc_frames[gi].size(),
-                                       b->m[0]->tables, b->d_err);
+                                       b->m[0]->tables, b->d_err, b->dbg_wait_ns, gi == 0 ? b->dbg_withhold : -1);
     if (e != cudaSuccess) return cuda_fail(e, "encoding the tensor maps of a batch tick");
   }
+  b->dbg_withhold = -1;  // one tick only
   if (b->tc && b->tc_groups == 2 && b->sms >= 2) {
     // The two sample sizes' launches run side by side on disjoint SMs (a CTA holds a whole SM),
     // the SMs split in proportion to their work: a tile of 16-bit words costs about 1.15 x a tile
@@ -1313,6 +1339,22 @@ vca_status vca_batch_sync(vca_batch* b) {
 vca_status vca_batch_kernel(vca_batch* b, int32_t* kernel) {
   if (!b || !kernel) return fail(VCA_E_ARG, "NULL argument");
   *kernel = b->tc ? VCA_KERNEL_TC : VCA_KERNEL_PLAIN;
+  return VCA_OK;
+}
+
+vca_status vca_debug_wait(vca_analyzer* a, int64_t wait_limit_ns, int32_t withhold_tile) {
+  if (!a || wait_limit_ns < 0 || withhold_tile < -1) return fail(VCA_E_ARG, "vca_debug_wait: bad argument");
+  if (a->kernel != VCA_KERNEL_TC) return fail(VCA_E_UNSUPPORTED, "vca_debug_wait: the CUDA-core form has no waits");
+  a->dbg_wait_ns = wait_limit_ns;
+  a->dbg_withhold = withhold_tile;
+  return VCA_OK;
+}
+
+vca_status vca_batch_debug_wait(vca_batch* b, int64_t wait_limit_ns, int32_t withhold_tile) {
+  if (!b || wait_limit_ns < 0 || withhold_tile < -1) return fail(VCA_E_ARG, "vca_batch_debug_wait: bad argument");
+  if (!b->tc) return fail(VCA_E_UNSUPPORTED, "vca_batch_debug_wait: the batch runs the CUDA-core form");
+  b->dbg_wait_ns = wait_limit_ns;
+  b->dbg_withhold = withhold_tile;
   return VCA_OK;
 }
 

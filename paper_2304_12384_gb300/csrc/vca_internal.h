@@ -99,10 +99,13 @@ cudaError_t launch_plain(const Geometry& g, const FramePlanes& fp, int nframes, 
 // Tensor-core analysis (same outputs).  Returns cudaErrorNotSupported if the geometry is
 // outside what the tensor-core kernel handles.  *err (device) receives a nonzero code if a
 // bounded wait inside the kernel gave up.
-// ctas: CTAs of the launch (0: one per SM; never more than the SMs or the tiles).
+// ctas: CTAs of the launch (0: one per SM; never more than the SMs or the tiles).  wait_ns: limit
+// of the kernel's bounded waits (0: about 2 s); withhold >= 0: a work item (128x128 tile, counted
+// over the launch) whose copies are not issued, so that the wait for it runs out (failure-path
+// tests).
 cudaError_t launch_tc(const Geometry& g, const FramePlanes& fp, int nframes, const DeviceTables& t,
                       float* blockvals, int16_t* const zdump[3], int* err, cudaStream_t s, int64_t* launches,
-                      int ctas = 0);
+                      int ctas = 0, long long wait_ns = 0, int withhold = -1);
 bool tc_supported(const Geometry& g);
 
 // Batched tensor-core analysis: one frame of each of up to tc_batch_max_members() analyzers of
@@ -127,7 +130,8 @@ size_t tc_batch_params_bytes();
 // Fills the parameter block at params (host memory, tc_batch_params_bytes()) for n frames, the
 // DCT tables t and the device error flag err; cudaErrorInvalidValue if n is out of range, the
 // frames' sample sizes differ or a tensor map cannot be encoded.
-cudaError_t tc_batch_fill(void* params, const TcBatchFrame* frames, int n, const DeviceTables& t, int* err);
+cudaError_t tc_batch_fill(void* params, const TcBatchFrame* frames, int n, const DeviceTables& t, int* err,
+                          long long wait_ns = 0, int withhold = -1);
 // Sets up the kernel instance for this sample size and low_pass (outside any stream capture).
 cudaError_t tc_batch_prepare(int bps, bool low_pass);
 // Work items (128x128 luma tiles) of a filled parameter block.

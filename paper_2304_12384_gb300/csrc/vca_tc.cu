@@ -1,7 +1,7 @@
 // Tensor-core form of the analyzer's per-block work (Section 2 of the paper: integer DCT of
 // every Y, U, V block, texture energy H and brightness L; Section 2 item (3): low-pass).
 //
-// Persistent kernel, one CTA of 28 warps per SM.  A work item is one 128x128 luma tile and the
+// Persistent kernel, one CTA of 32 warps per SM.  A work item is one 128x128 luma tile and the
 // two co-located 64x64 chroma tiles; it is processed as one unit (low-pass) or two units of half
 // its block rows (all coefficients).  Roles:
 //   warp 0        TMA producer: tiles in order into a ring (8-bit samples: 4 stages of one
@@ -18,7 +18,7 @@
 //                 in TMEM;
 //   warpgroup 4   epilogue 1 luma: stage-1 accumulators -> stage-2 A operand in shared memory;
 //   warpgroup 5   epilogue 2 luma: stage-2 accumulators -> block energies and brightness;
-//   warpgroup 6   both chroma epilogues (chroma has half the luma work per unit).
+//   warpgroups 6, 7  epilogue 1 and epilogue 2 chroma (U and V together).
 // Each role waits once per unit.  TMEM holds 2 stage-1 operand slots and 3 (low-pass) or 2
 // accumulator slots, shared memory 2 sets of stage-2 operands, so up to 3 units are in flight.
 // Every SM sub-partition runs warps of every role (each role spans the four TMEM lane quarters),
@@ -50,8 +50,10 @@
 // tick, one frame of each of up to 64 analyzers of one sample size (a member table and their
 // tensor maps, also in the kernel parameters, read through the constant cache).
 //
-// Every wait is bounded (about two seconds); on timeout the kernel raises a flag in *err,
-// stops, waits for its own copies and MMAs, frees TMEM and returns.
+// Every wait is bounded (about two seconds, or the launch's wait limit); on timeout the kernel
+// raises a flag in *err, stops, waits for its own copies and MMAs, frees TMEM and returns.  A
+// launch may name one work item whose copies the producer withholds, so that the wait for it
+// runs out (the failure path's test).
 #include <cuda.h>
 #include <cuda_fp16.h>
 
@@ -173,6 +175,8 @@ struct TcParamsT {
   const float* W_y;
   const float* W_c;
   int* err;
+  long long wait_ns;  // limit of every bounded wait
+  int withhold;       // work item whose copies the producer does not issue (-1: none; failure-path tests)
   int n_members, total_items;
   TcMember mem[MAXM];
   CUtensorMap maps[3 * MAXM];  // Y, U, V of each member
@@ -235,18 +239,19 @@ struct Ctl {
   uint64_t* bars;
   volatile int* abort;
   int* err;
+  uint64_t wait_ns;
 };
 
 // Bounded wait: false on timeout (flag raised) or when another role aborted.
 __device__ __noinline__ bool wait_bar_slow(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
-                                          int code, bool ignore_abort, bool sleep) {
+                                          int code, bool ignore_abort, bool sleep, uint64_t wait_ns) {
   const uint64_t t0 = now_ns();
   for (;;) {
 #pragma unroll 1
     for (int i = 0; i < 32; ++i)
       if (sleep ? mbar_try_wait_sleep(bar, parity) : mbar_try_wait(bar, parity)) return true;
     if (!ignore_abort && *abort_flag) return false;
-    if (now_ns() - t0 > kWaitNs) {
+    if (now_ns() - t0 > wait_ns) {
       *abort_flag = 1;
       atomicOr(err, code);
       return false;
@@ -260,7 +265,7 @@ __device__ __forceinline__ bool wait_bar(const Ctl& c, int idx, uint32_t parity,
                                          bool sleep = false) {
   uint64_t* bar = c.bars + idx;
   if (sleep ? mbar_try_wait_sleep(bar, parity) : mbar_try_wait(bar, parity)) return true;
-  return wait_bar_slow(bar, parity, c.abort, c.err, code, ignore_abort, sleep);
+  return wait_bar_slow(bar, parity, c.abort, c.err, code, ignore_abort, sleep, c.wait_ns);
 }
 
 // Byte offset of sample xx of row y of the raw tile of this plane type.
@@ -975,7 +980,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     n_items = cta < total_items ? (total_items - cta + grid - 1) / grid : 0;
     step = grid;
   }
-  Ctl ctl{bars, abort_flag, p.err};
+  Ctl ctl{bars, abort_flag, p.err, p.wait_ns > 0 ? (uint64_t)p.wait_ns : kWaitNs};
 
   using MS = typename MemberView<BATCH>::T;
   MS ms = [&] {
@@ -1105,6 +1110,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         const CUtensorMap* mm = &p.maps[3 * ti.m];
         uint8_t* dst = sm + OFF_RAW + stage * SL::kStageBytes;
         uint64_t* full = &bars[b_raw_full(stage)];
+        if (item0 + t * step == p.withhold) {  // failure-path test: the stage never fills
+          ++issued;
+          continue;
+        }
         mbar_arrive_expect_tx(full, SL::kStageBytes);
         if (BPS == 1) {
           tma_load_3d(dst, mm, ti.tx * 128, ti.ty * 128, ti.f, full);
@@ -1116,11 +1125,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         tma_load_3d(dst + SL::kRawY + SL::kRawC, mm + 2, ti.tx * 64, ti.ty * 64, ti.f, full);
         ++issued;
       }
-      if (*abort_flag) {
-        // Let every copy this CTA issued land before the CTA's shared memory goes away.
-        for (int t = (issued > SL::kStages ? issued - SL::kStages : 0); t < issued; ++t)
+      // Every copy this CTA issued lands before its shared memory goes away: in a normal run the
+      // convert warps waited for each tile, but a role that gave up on a wait no longer does.
+      for (int t = (issued > SL::kStages ? issued - SL::kStages : 0); t < issued; ++t)
+        if (item0 + t * step != p.withhold)
           wait_bar(ctl, b_raw_full(t % SL::kStages), (t / SL::kStages) & 1, 1, true);
-      }
     }
   } else if (warp <= kIssuers) {
     if (lane == 0) issuer_loop<LP, BPS>(ctl, sbase, tmem, warp - 1, n_items);
@@ -1275,7 +1284,8 @@ int tc_batch_max_members() { return kMaxMembers; }
 
 size_t tc_batch_params_bytes() { return sizeof(TcBatchParams); }
 
-cudaError_t tc_batch_fill(void* params, const TcBatchFrame* frames, int n, const DeviceTables& t, int* err) {
+cudaError_t tc_batch_fill(void* params, const TcBatchFrame* frames, int n, const DeviceTables& t, int* err,
+                          long long wait_ns, int withhold) {
   if (n < 0 || n > kMaxMembers) return cudaErrorInvalidValue;
   TcBatchParams& p = *static_cast<TcBatchParams*>(params);
   p.zdump[0] = p.zdump[1] = p.zdump[2] = nullptr;
@@ -1284,6 +1294,8 @@ cudaError_t tc_batch_fill(void* params, const TcBatchFrame* frames, int n, const
   p.W_y = t.W_y;
   p.W_c = t.W_c;
   p.err = err;
+  p.wait_ns = wait_ns;
+  p.withhold = withhold;
   int items = 0;
   for (int i = 0; i < n; ++i) {
     const Geometry& g = *frames[i].g;
@@ -1344,7 +1356,8 @@ const void* tc_batch_kernel(int bps, bool low_pass) {
 }
 
 cudaError_t launch_tc(const Geometry& g, const FramePlanes& fp, int nframes, const DeviceTables& t, float* blockvals,
-                      int16_t* const zdump[3], int* err, cudaStream_t s, int64_t* launches, int ctas) {
+                      int16_t* const zdump[3], int* err, cudaStream_t s, int64_t* launches, int ctas,
+                      long long wait_ns, int withhold) {
   if (!tc_supported(g)) return cudaErrorNotSupported;
   if (nframes <= 0) return cudaSuccess;
   // 8-bit: 128x128 luma boxes (128-byte swizzle), 64x64 chroma boxes (64-byte swizzle); 16-bit:
@@ -1369,6 +1382,8 @@ cudaError_t launch_tc(const Geometry& g, const FramePlanes& fp, int nframes, con
   p.W_y = t.W_y;
   p.W_c = t.W_c;
   p.err = err;
+  p.wait_ns = wait_ns;
+  p.withhold = withhold;
   int grid = ctas > 0 && ctas < sm_count() ? ctas : sm_count();
   if (p.total_items < grid) grid = p.total_items;
   e = launch_single(p, grid, g.low_pass, zdump != nullptr, bps, s);

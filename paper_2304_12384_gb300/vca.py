@@ -129,6 +129,8 @@ _PROTOS = {
     "vca_tune_save": (ctypes.c_char_p,),
     "vca_tune_load": (ctypes.c_char_p,),
     "vca_batch_split_weight": (_P, ctypes.c_float),
+    "vca_debug_wait": (_P, _I64, _I32),
+    "vca_batch_debug_wait": (_P, _I64, _I32),
     "vca_batch_autotune": (_P, ctypes.POINTER(VcaFrameRef), _I32, ctypes.POINTER(ctypes.c_float),
                            ctypes.POINTER(ctypes.c_float)),
     "vca_batch_create": (ctypes.POINTER(_P), _I32, ctypes.POINTER(_P)),
@@ -247,6 +249,14 @@ def vca_tune_lookup(cfg: "VcaConfig"):
         return None
     _check(st)
     return e.as_dict()
+
+
+def vca_debug_wait(handle: int, wait_limit_ns: int, withhold_tile: int = -1) -> None:
+    _check(lib().vca_debug_wait(_P(handle), wait_limit_ns, withhold_tile))
+
+
+def vca_batch_debug_wait(handle: int, wait_limit_ns: int, withhold_tile: int = -1) -> None:
+    _check(lib().vca_batch_debug_wait(_P(handle), wait_limit_ns, withhold_tile))
 
 
 def vca_tune_clear() -> None:
