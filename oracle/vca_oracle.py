@@ -20,17 +20,25 @@ not reproduce.  Every definition below is therefore a *reading*, stated where it
 is used:
 
 * input: planar Y, U, V, integer samples of bit depth B in {8, 10, 12}; chroma
-  4:2:0 (planes of half width and height) or 4:4:4 (full-size planes);
+  4:2:0 (planes of half width and height), 4:2:2 (half width, full height) or
+  4:4:4 (full-size planes);
 * block grid: luma w x w blocks, chroma blocks covering the same picture area
-  ((w/2) x (w/2) samples in 4:2:0, w x w in 4:4:4) on the same (co-located)
-  grid; partial blocks at the right/bottom edge are completed by repeating the
-  last row/column ("replicate"), or dropped ("skip");
+  ((w/2) x (w/2) samples in 4:2:0, (w/2) wide by w tall in 4:2:2, w x w in
+  4:4:4) on the same (co-located) grid; partial blocks at the right/bottom edge
+  are completed by repeating the last row/column ("replicate"), or dropped
+  ("skip");
 * integer DCT matrix M_N[k][n] = round_half_away(64 sqrt(N) alpha_k
   cos(pi (2n+1) k / 2N)) and the two-stage forward transform of HEVC encoders:
   rows first with shift s1 = log2 N + B - 9, then columns with s2 = log2 N + 6,
   each stage adding 2^(s-1) before an arithmetic right shift;
 * low-pass: only coefficients with u, v < N/2 are computed (stage 1 keeps the
   first N/2 row outputs, stage 2 the first N/2 column outputs);
+* rectangular (4:2:2 chroma) blocks of Nv rows and Nh columns: rows first with
+  the Nh-point matrix and s1 = log2 Nh + B - 9, then columns with the Nv-point
+  matrix and s2 = log2 Nv + 6 (each stage's shift from its own length, as the
+  encoders' rectangular transforms do); low-pass keeps the first half of each
+  dimension; weights w(u,v) = exp(|((u+1)(v+1)/(Nv Nh))^2 - 1|); E divides by
+  C Nv Nh;
 * low-pass, downsample reading: every plane is first downsampled by two in each
   direction (the rounded mean of each 2x2 group, (a + b + c + d + 2) >> 2, edges
   repeated for odd sizes); the downsampled frame is then analysed with half-size
@@ -216,6 +224,50 @@ def int_dct2_butterfly(blocks, bit_depth: int, M=None) -> np.ndarray:
 # Block features (Section 2: E, L per block)
 # ---------------------------------------------------------------------------
 
+def int_dct2_rect_stages(blocks, bit_depth: int, low_pass: bool = False, Mh=None, Mv=None):
+    """Two-stage integer forward transform of rectangular blocks shaped (..., Nv, Nh).
+
+    Stage 1 (rows, Nh-point):    T[r][k] = (sum_c x[r][c] Mh[k][c] + 2^(s1-1)) >> s1, s1 = log2 Nh + B - 9
+    Stage 2 (columns, Nv-point): Z[u][v] = (sum_r Mv[u][r] T[r][v] + 2^(s2-1)) >> s2, s2 = log2 Nv + 6
+    Low-pass: k < Nh/2 and u < Nv/2.  Mh, Mv default to the round-cosine matrices.
+    Returns (T, Z): T is (..., Nv, Nkh), Z is (..., Nkv, Nkh).
+    """
+    x = np.asarray(blocks, dtype=np.int64)
+    Nv, Nh = x.shape[-2], x.shape[-1]
+    Mh = int_dct_matrix(Nh) if Mh is None else np.asarray(Mh, dtype=np.int64)
+    Mv = int_dct_matrix(Nv) if Mv is None else np.asarray(Mv, dtype=np.int64)
+    Nkh = Nh // 2 if low_pass else Nh
+    Nkv = Nv // 2 if low_pass else Nv
+    s1 = transform_shifts(Nh, bit_depth)[0]
+    s2 = transform_shifts(Nv, bit_depth)[1]
+    T = round_shift(np.matmul(x, Mh[:Nkh].T), s1)
+    Z = round_shift(np.matmul(Mv[:Nkv], T), s2)
+    return T, Z
+
+
+def int_dct2_rect(blocks, bit_depth: int, low_pass: bool = False, Mh=None, Mv=None) -> np.ndarray:
+    """Quantised coefficients Z of the rectangular two-stage transform (see int_dct2_rect_stages)."""
+    return int_dct2_rect_stages(blocks, bit_depth, low_pass, Mh, Mv)[1]
+
+
+def energy_weights_rect(Nv: int, Nh: int) -> np.ndarray:
+    """w(u,v) = exp(|((u+1)(v+1)/(Nv Nh))^2 - 1|) for 0 <= u < Nv, 0 <= v < Nh."""
+    w = np.empty((Nv, Nh), dtype=np.float64)
+    for u in range(Nv):
+        for v in range(Nh):
+            w[u, v] = math.exp(abs(((u + 1) * (v + 1) / (Nv * Nh)) ** 2 - 1.0))
+    return w
+
+
+def block_texture_energy_rect(Z: np.ndarray, Nv: int, Nh: int) -> np.ndarray:
+    """H = sum_{(u,v) != (0,0)} w(u,v) |Z(u,v)| of rectangular blocks (FP64)."""
+    Z = np.asarray(Z, dtype=np.int64)
+    Nkv, Nkh = Z.shape[-2], Z.shape[-1]
+    w = energy_weights_rect(Nv, Nh)[:Nkv, :Nkh].copy()
+    w[0, 0] = 0.0
+    return np.sum(np.abs(Z).astype(np.float64) * w, axis=(-2, -1))
+
+
 def energy_weights(N: int) -> np.ndarray:
     """w_N(u,v) = exp(|((u+1)(v+1)/N^2)^2 - 1|) for 0 <= u, v < N."""
     w = np.empty((N, N), dtype=np.float64)
@@ -252,7 +304,7 @@ class Config:
     low_pass: bool = False
     pad_mode: str = "replicate"  # or "skip"
     downsample: bool = False     # the downsample reading of the low-pass option (excludes low_pass)
-    chroma_format: str = "420"   # or "444"
+    chroma_format: str = "420"   # or "422", "444"
     # Caller-supplied integer DCT matrices: ((N, rows), ...) with rows a tuple of N tuples of N
     # ints; a transform size without an entry uses the round-cosine matrix int_dct_matrix(N).
     dct_matrices: tuple = ()
@@ -266,10 +318,16 @@ class Config:
 
     def transform_sizes(self) -> tuple[int, int]:
         """(luma, chroma) block size of the transform: w and w/2 (4:2:0) or w (4:4:4), each
-        halved when downsampling."""
+        halved when downsampling; for 4:2:2 the chroma block's width (w/2)."""
         w = self.block_size
         c = w if self.chroma_format == "444" else w // 2
         return (w // 2, c // 2) if self.downsample else (w, c)
+
+    def chroma_block(self) -> tuple[int, int]:
+        """(rows, columns) of a chroma block: (w/2, w/2) in 4:2:0, (w, w/2) in 4:2:2, (w, w) in
+        4:4:4 (halved when downsampling, 4:2:0 only)."""
+        w, c = self.transform_sizes()
+        return (w, c) if self.chroma_format == "422" else (c, c)
 
 
 def block_grid(cfg: Config) -> tuple[int, int]:
@@ -283,23 +341,25 @@ def block_grid(cfg: Config) -> tuple[int, int]:
 
 
 def chroma_shape(cfg: Config) -> tuple[int, int]:
-    """(height, width) of a chroma plane: half size in 4:2:0, full size in 4:4:4."""
+    """(height, width) of a chroma plane: half size in 4:2:0, half width in 4:2:2, full size in
+    4:4:4."""
     if cfg.chroma_format == "444":
         return cfg.height, cfg.width
+    if cfg.chroma_format == "422":
+        return cfg.height, (cfg.width + 1) // 2
     return (cfg.height + 1) // 2, (cfg.width + 1) // 2
 
 
-def plane_blocks(plane: np.ndarray, n: int, nbx: int, nby: int) -> np.ndarray:
-    """Blocks of one plane in raster order, shaped (nby*nbx, n, n).
-
-    Rows/columns past the plane's edge repeat its last row/column.
-    """
+def plane_blocks(plane: np.ndarray, n: int, nbx: int, nby: int, nh: int | None = None) -> np.ndarray:
+    """Blocks of one plane in raster order, shaped (nby*nbx, n, nh): n rows and nh (default n)
+    columns each.  Rows/columns past the plane's edge repeat its last row/column."""
+    nh = n if nh is None else nh
     plane = np.asarray(plane)
     ph, pw = plane.shape
     ys = np.minimum(np.arange(nby * n), ph - 1)
-    xs = np.minimum(np.arange(nbx * n), pw - 1)
+    xs = np.minimum(np.arange(nbx * nh), pw - 1)
     padded = plane[ys][:, xs].astype(np.int64)
-    return padded.reshape(nby, n, nbx, n).transpose(0, 2, 1, 3).reshape(nby * nbx, n, n)
+    return padded.reshape(nby, n, nbx, nh).transpose(0, 2, 1, 3).reshape(nby * nbx, n, nh)
 
 
 def plane_block_values(plane, n: int, nbx: int, nby: int, bit_depth: int, low_pass: bool, M=None):
@@ -328,7 +388,13 @@ def frame_block_values(y, u, v, cfg: Config) -> dict:
         y, u, v = downsample_plane(y), downsample_plane(u), downsample_plane(v)
     out = {}
     for name, plane, n in (("Y", y, ny), ("U", u, nc), ("V", v, nc)):
-        H, L, _ = plane_block_values(plane, n, nbx, nby, cfg.bit_depth, cfg.low_pass, cfg.matrix(n))
+        if name != "Y" and cfg.chroma_format == "422":
+            nv, nh = cfg.chroma_block()
+            Z = int_dct2_rect(plane_blocks(plane, nv, nbx, nby, nh), cfg.bit_depth, cfg.low_pass, cfg.matrix(nh),
+                              cfg.matrix(nv))
+            H, L = block_texture_energy_rect(Z, nv, nh), block_brightness(Z)
+        else:
+            H, L, _ = plane_block_values(plane, n, nbx, nby, cfg.bit_depth, cfg.low_pass, cfg.matrix(n))
         out["H_" + name] = H
         out["L_" + name] = L
     return out
@@ -346,12 +412,13 @@ def frame_features(values: dict, prev_HY, cfg: Config) -> dict:
     """
     nbx, nby = block_grid(cfg)
     C = nbx * nby
-    w, c = cfg.transform_sizes()
+    w, _ = cfg.transform_sizes()
+    cv, ch = cfg.chroma_block()
     f = {
         "E_Y": float(np.sum(values["H_Y"])) / (C * w * w),
         "L_Y": float(np.sum(values["L_Y"])) / C,
-        "E_U": float(np.sum(values["H_U"])) / (C * c * c),
-        "E_V": float(np.sum(values["H_V"])) / (C * c * c),
+        "E_U": float(np.sum(values["H_U"])) / (C * cv * ch),
+        "E_V": float(np.sum(values["H_V"])) / (C * cv * ch),
         "L_U": float(np.sum(values["L_U"])) / C,
         "L_V": float(np.sum(values["L_V"])) / C,
     }

@@ -73,7 +73,7 @@ class SequenceSpec:
     n_patches: tuple = (3, 6)
     flat_fraction: float = 0.0           # share of the area made of flat, noise-free blocks
     flat_align: int = 32                 # luma alignment of the flat rectangles
-    chroma_format: str = "420"           # "420" or "444"
+    chroma_format: str = "420"           # "420", "422" or "444"
     extra: dict = field(default_factory=dict)
 
 
@@ -157,8 +157,12 @@ def generate(spec: SequenceSpec, start: int = 0, stop: int | None = None):
     """
     stop = spec.n_frames if stop is None else min(stop, spec.n_frames)
     W, H = spec.width, spec.height
-    full_chroma = spec.chroma_format == "444"
-    cw, ch = (W, H) if full_chroma else ((W + 1) // 2, (H + 1) // 2)
+    if spec.chroma_format == "444":
+        cw, ch = W, H
+    elif spec.chroma_format == "422":
+        cw, ch = (W + 1) // 2, H
+    else:
+        cw, ch = (W + 1) // 2, (H + 1) // 2
     scale = 1 << (spec.bit_depth - 8)
     dtype = np.uint16 if spec.bit_depth > 8 else np.uint8
     cuts = set(spec.cuts)
@@ -201,11 +205,12 @@ def generate(spec: SequenceSpec, start: int = 0, stop: int | None = None):
         nrng = np.random.Generator(np.random.PCG64(noise_seed))
         planes = []
         for i, (scene, w, h) in enumerate(((scenes[0], W, H), (scenes[1], cw, ch), (scenes[2], cw, ch))):
-            div = 1 if i == 0 or full_chroma else 2
-            img = _render(scene, w, h, ox / div, oy / div)
+            dx = 1 if i == 0 or cw == W else 2
+            dy = 1 if i == 0 or ch == H else 2
+            img = _render(scene, w, h, ox / dx, oy / dy)
             img += (sigma * nrng.standard_normal((h, w), dtype=np.float32))
             for (x0, y0, x1, y1, level) in rects:
-                img[y0 // div:y1 // div, x0 // div:x1 // div] = level + (0 if i == 0 else 0)
+                img[y0 // dy:y1 // dy, x0 // dx:x1 // dx] = level
             lo, hi = LUMA_RANGE_8 if i == 0 else CHROMA_RANGE_8
             planes.append(_quantize(img, lo, hi, scale, dtype))
         yield tuple(planes)
