@@ -86,9 +86,13 @@ typedef struct vca_config {
   int32_t pad_mode;    /* VCA_PAD_REPLICATE (default) or VCA_PAD_SKIP */
   int32_t kernel;      /* VCA_KERNEL_AUTO, VCA_KERNEL_PLAIN (CUDA cores) or VCA_KERNEL_TC (tensor cores) */
   int32_t max_batch;   /* most frames one vca_push_frames call may carry; 0 selects 64 */
-  int32_t chroma_format; /* VCA_CHROMA_420 (default: half-size chroma planes, w/2 blocks) or
-                            VCA_CHROMA_444 (full-size chroma planes, w blocks); VCA_CHROMA_422
-                            (non-square chroma blocks) gives VCA_E_UNSUPPORTED */
+  int32_t chroma_format; /* VCA_CHROMA_420 (default: half-size chroma planes, w/2 blocks),
+                            VCA_CHROMA_444 (full-size chroma planes, w blocks) or VCA_CHROMA_422
+                            (half-width, full-height chroma planes; blocks of w rows by w/2
+                            columns: rows take the (w/2)-point transform, columns the w-point
+                            one, each stage the shift of its own length; E_U and E_V divide by
+                            C w^2/2).  The paper names no 4:2:2 block shape: this is the
+                            co-located reading.  4:2:2 runs on the CUDA cores. */
 } vca_config;
 
 /* The seven features of one frame (Section 2), frame = 0-based index since vca_open. */
@@ -147,7 +151,8 @@ vca_status vca_read_block_values(vca_analyzer* a, int32_t index, float* H_Y, flo
 /* Quantised coefficients Z of one frame, computed by the analyzer's kernel with
  * the coefficient dump enabled (bit-exact integers; parity checks).  zy, zu, zv
  * are device buffers of C*Nk*Nk int16 each (Nk = N, or N/2 with VCA_LOWPASS_QUARTER;
- * N = w for Y, w/2 for U, V, halved again with VCA_LOWPASS_DOWNSAMPLE), block-major,
+ * N = w for Y, w/2 for U, V, halved again with VCA_LOWPASS_DOWNSAMPLE; in 4:2:2, U and V
+ * hold C*Nkv*Nkh with Nkv, Nkh those of the w-row, w/2-column blocks), block-major,
  * then row u, then column v.  Planes are on the device.  Does not change the
  * analyzer's frame count or h state. */
 vca_status vca_dump_coefficients(vca_analyzer* a, const void* y, const void* u, const void* v,
@@ -214,7 +219,7 @@ vca_status vca_close(vca_analyzer* a);
  * with one launch of the batched CUDA-core block kernel (Section 2 of the paper: integer DCT,
  * texture energy and brightness of every block of every channel) and one launch of the batched
  * frame reduction, replayed from a CUDA graph.  The analyzers may differ in frame size and bit
- * depth; they must share device, block size and low_pass.  Features arrive in each analyzer as
+ * depth; they must share device, block size, chroma format and low_pass.  Features arrive in each analyzer as
  * if its frames had been pushed one at a time: read them with vca_read_frame_features /
  * vca_read_sequence_features, and the h state carries across ticks and across the batch's
  * destruction.  While in a batch an analyzer accepts no vca_push_frame(s),

@@ -163,6 +163,7 @@ struct vca_batch {
   int device = 0;
   int w = 32;
   int nc = 16;
+  int ncv = 16;
   bool low_pass = false;
   bool tc = false;                 // analysis on the tensor-core kernel
   // Tensor-core members are launched in one group per sample size (8-bit samples in bytes,
@@ -224,10 +225,9 @@ vca_status check_config(const vca_config* c, Geometry* g, Geometry* gin = nullpt
     return fail(VCA_E_ARG, "bit_depth must be 8, 10 or 12");
   if (c->block_size != 8 && c->block_size != 16 && c->block_size != 32)
     return fail(VCA_E_ARG, "block_size must be 8, 16 or 32");
-  if (c->chroma_format == VCA_CHROMA_422)
-    return fail(VCA_E_UNSUPPORTED, "4:2:2 would need non-square chroma blocks; not supported");
-  if (c->chroma_format != VCA_CHROMA_420 && c->chroma_format != VCA_CHROMA_444)
-    return fail(VCA_E_ARG, "chroma_format must be VCA_CHROMA_420 or VCA_CHROMA_444");
+  if (c->chroma_format != VCA_CHROMA_420 && c->chroma_format != VCA_CHROMA_444 &&
+      c->chroma_format != VCA_CHROMA_422)
+    return fail(VCA_E_ARG, "chroma_format must be VCA_CHROMA_420, VCA_CHROMA_444 or VCA_CHROMA_422");
   if (c->low_pass < VCA_LOWPASS_OFF || c->low_pass > VCA_LOWPASS_DOWNSAMPLE)
     return fail(VCA_E_ARG, "low_pass must be 0, 1 or 2");
   if (c->low_pass == VCA_LOWPASS_DOWNSAMPLE && (c->block_size != 32 || c->chroma_format != VCA_CHROMA_420))
@@ -240,12 +240,14 @@ vca_status check_config(const vca_config* c, Geometry* g, Geometry* gin = nullpt
   q.W = c->width;
   q.H = c->height;
   const bool full_chroma = c->chroma_format == VCA_CHROMA_444;
+  const bool chroma_422 = c->chroma_format == VCA_CHROMA_422;
   q.cw = full_chroma ? c->width : c->width / 2;
-  q.ch = full_chroma ? c->height : c->height / 2;
+  q.ch = full_chroma || chroma_422 ? c->height : c->height / 2;
   q.B = c->bit_depth;
   q.bps = c->bit_depth > 8 ? 2 : 1;
   q.w = c->block_size;
   q.nc = full_chroma ? c->block_size : c->block_size / 2;
+  q.ncv = chroma_422 ? c->block_size : q.nc;  // 4:2:2: w rows of w/2 samples
   if (c->pad_mode == VCA_PAD_REPLICATE) {
     q.nbx = (q.W + q.w - 1) / q.w;
     q.nby = (q.H + q.w - 1) / q.w;
@@ -257,7 +259,9 @@ vca_status check_config(const vca_config* c, Geometry* g, Geometry* gin = nullpt
   if (q.C <= 0) return fail(VCA_E_ARG, "frame smaller than one block with pad_mode skip");
   q.low_pass = c->low_pass == VCA_LOWPASS_QUARTER;
   vca::transform_shifts(q.w, q.B, &q.s1y, &q.s2y);
-  vca::transform_shifts(q.nc, q.B, &q.s1c, &q.s2c);
+  int unused;
+  vca::transform_shifts(q.nc, q.B, &q.s1c, &unused);
+  vca::transform_shifts(q.ncv, q.B, &unused, &q.s2c);
   if (gin) *gin = q;
   if (c->low_pass == VCA_LOWPASS_DOWNSAMPLE) {
     // Halved planes, half-size blocks, same block grid (ceil(ceil(W/2) / (w/2)) = ceil(W/w)).
@@ -267,6 +271,7 @@ vca_status check_config(const vca_config* c, Geometry* g, Geometry* gin = nullpt
     q.ch = (q.ch + 1) / 2;
     q.w /= 2;
     q.nc /= 2;
+    q.ncv /= 2;
     vca::transform_shifts(q.w, q.B, &q.s1y, &q.s2y);
     vca::transform_shifts(q.nc, q.B, &q.s1c, &q.s2c);
   }
@@ -597,7 +602,7 @@ cudaError_t build_tick_graph(vca_batch* b, int k) {
     e1 = cudaMemcpyAsync(b->d_desc, b->h_desc[k], b->desc_bytes, cudaMemcpyHostToDevice, b->stream);
     if (e1 == cudaSuccess)
       e1 = vca::launch_batch_plain(b->d_map, b->n_cta, reinterpret_cast<const vca::BatchMemberArgs*>(b->d_desc),
-                                   b->w, b->nc, b->low_pass, b->stream);
+                                   b->w, b->nc, b->ncv, b->low_pass, b->stream);
     if (e1 == cudaSuccess)
       e1 = vca::launch_reduce_batch(reinterpret_cast<const vca::ReduceArgs*>(b->d_desc + b->ma_bytes), b->n,
                                     b->red_slices, b->stream);
@@ -647,6 +652,7 @@ vca::PlainArgs member_plain_args(const vca_analyzer* a, int kind, const vca_fram
     pa.s1 = g.s1y;
     pa.s2 = g.s2y;
     pa.M = a->tables.M_y;
+    pa.M2 = a->tables.M_y;
     pa.W = a->tables.W_y;
     pa.outH[0] = bv + vca::ROW_H_Y * g.C;
     pa.outL[0] = bv + vca::ROW_L_Y * g.C;
@@ -659,6 +665,7 @@ vca::PlainArgs member_plain_args(const vca_analyzer* a, int kind, const vca_fram
     pa.s1 = g.s1c;
     pa.s2 = g.s2c;
     pa.M = a->tables.M_c;
+    pa.M2 = a->tables.M_cv;
     pa.W = a->tables.W_c;
     pa.outH[0] = bv + vca::ROW_H_U * g.C;
     pa.outL[0] = bv + vca::ROW_L_U * g.C;
@@ -737,22 +744,24 @@ vca_status vca_open(const vca_config* cfg, void* cuda_stream, vca_analyzer** out
     }                          \
   } while (0)
 
-  // Tables: M_y | M_c | W_y | W_c, each 256-byte aligned.
-  const int w = g.w, nc = g.nc;
+  // Tables: M_y | M_c | W_y | W_c, each 256-byte aligned.  The chroma column matrix is M_c, or
+  // M_y when the chroma blocks are w rows tall (4:2:2).
+  const int w = g.w, nc = g.nc, ncv = g.ncv;
   const size_t oMc = round_up((size_t)w * w, 256);
   const size_t oWy = oMc + round_up((size_t)nc * nc, 256);
   const size_t oWc = oWy + round_up((size_t)w * w * 4, 256);
-  const size_t tbytes = oWc + round_up((size_t)nc * nc * 4, 256);
+  const size_t tbytes = oWc + round_up((size_t)ncv * nc * 4, 256);
   std::vector<uint8_t> host(tbytes, 0);
   vca::make_dct_matrix(w, reinterpret_cast<int8_t*>(host.data()));
   vca::make_dct_matrix(nc, reinterpret_cast<int8_t*>(host.data() + oMc));
   vca::make_energy_weights(w, reinterpret_cast<float*>(host.data() + oWy));
-  vca::make_energy_weights(nc, reinterpret_cast<float*>(host.data() + oWc));
+  vca::make_energy_weights_rect(ncv, nc, reinterpret_cast<float*>(host.data() + oWc));
   OPEN_CUDA(cudaMalloc(&a->d_tables, tbytes), "allocating tables");
   OPEN_CUDA(cudaMemcpy(a->d_tables, host.data(), tbytes, cudaMemcpyHostToDevice), "uploading tables");
   uint8_t* tb = static_cast<uint8_t*>(a->d_tables);
   a->tables.M_y = reinterpret_cast<const int8_t*>(tb);
   a->tables.M_c = reinterpret_cast<const int8_t*>(tb + oMc);
+  a->tables.M_cv = ncv == nc ? a->tables.M_c : a->tables.M_y;
   a->tables.W_y = reinterpret_cast<const float*>(tb + oWy);
   a->tables.W_c = reinterpret_cast<const float*>(tb + oWc);
   memcpy(a->M_host[0], host.data(), (size_t)w * w);
@@ -1078,7 +1087,8 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
     for (int j = 0; j < i; ++j)
       if (members[j] == a) return fail(VCA_E_ARG, "analyzer %d appears twice", i);
     if (a->device != members[0]->device) return fail(VCA_E_ARG, "analyzers of a batch must share one device");
-    if (a->g.w != members[0]->g.w || a->g.nc != members[0]->g.nc || a->g.low_pass != members[0]->g.low_pass)
+    if (a->g.w != members[0]->g.w || a->g.nc != members[0]->g.nc || a->g.ncv != members[0]->g.ncv ||
+        a->g.low_pass != members[0]->g.low_pass)
       return fail(VCA_E_ARG, "analyzers of a batch must share block size, chroma format and low_pass");
     if (a->cfg.low_pass == VCA_LOWPASS_DOWNSAMPLE)
       return fail(VCA_E_UNSUPPORTED, "the downsample reading is not available in batches");
@@ -1090,6 +1100,7 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
   b->device = members[0]->device;
   b->w = members[0]->g.w;
   b->nc = members[0]->g.nc;
+  b->ncv = members[0]->g.ncv;
   b->low_pass = members[0]->g.low_pass;
   b->tc = n <= vca::tc_batch_max_members();
   for (int i = 0; i < n; ++i) {
@@ -1135,7 +1146,7 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
   for (int i = 0; i < n && !b->tc; ++i) {
     const Geometry& g = members[i]->g;
     const int64_t cl = (g.C + vca::plain_blocks_per_cta(g.w) - 1) / vca::plain_blocks_per_cta(g.w);
-    const int64_t cc = (g.C + vca::plain_blocks_per_cta(g.nc) - 1) / vca::plain_blocks_per_cta(g.nc);
+    const int64_t cc = (g.C + vca::plain_blocks_per_cta(g.ncv) - 1) / vca::plain_blocks_per_cta(g.ncv);
     for (int64_t c = 0; c < cl; ++c) map.push_back({(uint16_t)i, 0, 0, (uint32_t)c});
     for (int pl = 0; pl < 2; ++pl)
       for (int64_t c = 0; c < cc; ++c) map.push_back({(uint16_t)i, 1, (uint8_t)pl, (uint32_t)c});

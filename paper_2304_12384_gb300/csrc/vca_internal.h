@@ -20,12 +20,13 @@ struct Geometry {
   int B;             // bit depth (8 or 10)
   int bps;           // bytes per sample (1 or 2)
   int w;             // luma block size
-  int nc;            // chroma block size (w / 2)
+  int nc;            // chroma block columns (w / 2; w in 4:4:4)
+  int ncv;           // chroma block rows (nc, except w in 4:2:2)
   int nbx, nby;      // block grid (shared by all planes)
   int64_t C;         // blocks per plane
   bool low_pass;
   int s1y, s2y;      // transform shifts, luma
-  int s1c, s2c;      // transform shifts, chroma
+  int s1c, s2c;      // transform shifts, chroma (s1 of the row length nc, s2 of the column length ncv)
 };
 
 // Planes of frame 0 of a batch and the byte strides to the next row / frame.
@@ -40,9 +41,10 @@ struct FramePlanes {
 // Device copies of the integer DCT matrices and FP32 energy weights (weight (0,0) = 0).
 struct DeviceTables {
   const int8_t* M_y;   // w x w
-  const int8_t* M_c;   // (w/2) x (w/2)
+  const int8_t* M_c;   // nc x nc: the chroma row transform
+  const int8_t* M_cv;  // ncv x ncv: the chroma column transform (M_c, or M_y in 4:2:2)
   const float* W_y;    // w x w
-  const float* W_c;    // (w/2) x (w/2)
+  const float* W_c;    // ncv x nc (row stride nc)
 };
 
 // Arguments of one launch of the plain block routine (one plane kind of a batch of frames).
@@ -54,8 +56,9 @@ struct PlainArgs {
   int nbx;
   int64_t C;
   int s1, s2;
-  const int8_t* M;         // N x N
-  const float* W;          // N x N, W[0] = 0
+  const int8_t* M;         // NH x NH: the row transform
+  const int8_t* M2;        // NV x NV: the column transform (M when the blocks are square)
+  const float* W;          // NV x NH, W[0] = 0
   float* outH[2];
   float* outL[2];
   int64_t out_fstride;     // floats between frames of block values
@@ -80,6 +83,9 @@ struct ReduceArgs {
 void make_dct_matrix(int N, int8_t* out);
 // Energy weights w_N(u,v) = exp(|((u+1)(v+1)/N^2)^2 - 1|) rounded to FP32, with (0,0) set to 0.
 void make_energy_weights(int N, float* out);
+// Rectangular form for blocks of Nv rows and Nh columns: w(u,v) = exp(|((u+1)(v+1)/(Nv Nh))^2 - 1|)
+// at out[u * Nh + v], (0,0) set to 0.
+void make_energy_weights_rect(int Nv, int Nh, float* out);
 // Stage shifts s1 = log2 N + B - 9, s2 = log2 N + 6.
 void transform_shifts(int N, int B, int* s1, int* s2);
 // True if m (N x N, row-major) can replace the round-cosine matrix for B-bit samples: N in
@@ -195,13 +201,13 @@ struct BatchMemberArgs {
   int32_t active;
   int32_t pad[2];
 };
-// Blocks per CTA of the plain routine for block size N.
-constexpr int plain_blocks_per_cta(int N) { return 4 * (32 / N); }
+// Blocks per CTA of the (4-warp) plain routine for blocks of NV rows.
+constexpr int plain_blocks_per_cta(int NV) { return 4 * (32 / NV); }
 // The batched plain analysis of one frame per analyzer: n_cta CTAs described by d_map (device),
-// arguments d_args (device, one per analyzer).  All analyzers share block sizes w (luma) and nc
-// (chroma) and low_pass.
+// arguments d_args (device, one per analyzer).  All analyzers share block sizes w (luma) and
+// ncv x nc (chroma rows x columns) and low_pass.
 cudaError_t launch_batch_plain(const BatchCta* d_map, int n_cta, const BatchMemberArgs* d_args, int w, int nc,
-                               bool low_pass, cudaStream_t s);
+                               int ncv, bool low_pass, cudaStream_t s);
 
 // One plane of the 2x2 downsample: n frames of w x h samples at src (pitch, frame stride in
 // bytes) -> wd x hd = ceil(w/2) x ceil(h/2) samples at dst.

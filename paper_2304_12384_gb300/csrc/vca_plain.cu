@@ -8,45 +8,59 @@
 namespace vca {
 namespace {
 
-template <int N, bool LP, typename Pix, int WARPS>
+template <int NV, int NH, bool LP, typename Pix, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) plain_kernel(const PlainArgs p) {
-  __shared__ PlainSmem<N, LP, WARPS> sh;
-  plain_blocks<N, LP, Pix, WARPS>(p, blockIdx.y, blockIdx.z, blockIdx.x, sh);
+  __shared__ PlainSmem<NV, NH, LP, WARPS> sh;
+  plain_blocks<NV, NH, LP, Pix, WARPS>(p, blockIdx.y, blockIdx.z, blockIdx.x, sh);
 }
 
-template <int N, int WARPS>
+template <int NV, int NH, int WARPS>
 cudaError_t launch_planes(const PlainArgs& a, int nplanes, int nframes, bool lp, int bps, cudaStream_t s) {
-  constexpr int BPC = WARPS * (32 / N);
+  constexpr int BPC = WARPS * (32 / NV);
   dim3 grid((unsigned)((a.C + BPC - 1) / BPC), nplanes, nframes);
   dim3 block(WARPS * 32);
   if (lp) {
-    if (bps == 1) plain_kernel<N, true, uint8_t, WARPS><<<grid, block, 0, s>>>(a);
-    else plain_kernel<N, true, uint16_t, WARPS><<<grid, block, 0, s>>>(a);
+    if (bps == 1) plain_kernel<NV, NH, true, uint8_t, WARPS><<<grid, block, 0, s>>>(a);
+    else plain_kernel<NV, NH, true, uint16_t, WARPS><<<grid, block, 0, s>>>(a);
   } else {
-    if (bps == 1) plain_kernel<N, false, uint8_t, WARPS><<<grid, block, 0, s>>>(a);
-    else plain_kernel<N, false, uint16_t, WARPS><<<grid, block, 0, s>>>(a);
+    if (bps == 1) plain_kernel<NV, NH, false, uint8_t, WARPS><<<grid, block, 0, s>>>(a);
+    else plain_kernel<NV, NH, false, uint16_t, WARPS><<<grid, block, 0, s>>>(a);
   }
   return cudaGetLastError();
 }
 
+// Blocks of NV rows and NH columns: square (NV = NH in {32, 16, 8, 4}) or the 4:2:2 chroma
+// shapes (NV = 2 NH, NV in {32, 16, 8}).
 template <int WARPS>
-cudaError_t launch_nw(int N, const PlainArgs& a, int nplanes, int nframes, bool lp, int bps, cudaStream_t s) {
-  switch (N) {
-    case 32: return launch_planes<32, WARPS>(a, nplanes, nframes, lp, bps, s);
-    case 16: return launch_planes<16, WARPS>(a, nplanes, nframes, lp, bps, s);
-    case 8: return launch_planes<8, WARPS>(a, nplanes, nframes, lp, bps, s);
-    case 4: return launch_planes<4, WARPS>(a, nplanes, nframes, lp, bps, s);
-    default: return cudaErrorInvalidValue;
+cudaError_t launch_nw(int NV, int NH, const PlainArgs& a, int nplanes, int nframes, bool lp, int bps,
+                      cudaStream_t s) {
+  if (NV == NH) {
+    switch (NV) {
+      case 32: return launch_planes<32, 32, WARPS>(a, nplanes, nframes, lp, bps, s);
+      case 16: return launch_planes<16, 16, WARPS>(a, nplanes, nframes, lp, bps, s);
+      case 8: return launch_planes<8, 8, WARPS>(a, nplanes, nframes, lp, bps, s);
+      case 4: return launch_planes<4, 4, WARPS>(a, nplanes, nframes, lp, bps, s);
+      default: return cudaErrorInvalidValue;
+    }
   }
+  if (NV == 2 * NH) {
+    switch (NV) {
+      case 32: return launch_planes<32, 16, WARPS>(a, nplanes, nframes, lp, bps, s);
+      case 16: return launch_planes<16, 8, WARPS>(a, nplanes, nframes, lp, bps, s);
+      case 8: return launch_planes<8, 4, WARPS>(a, nplanes, nframes, lp, bps, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  return cudaErrorInvalidValue;
 }
 
 // warps per CTA: 2, 4 (the default) or 8
-cudaError_t launch_n(int N, const PlainArgs& a, int nplanes, int nframes, bool lp, int bps, cudaStream_t s,
-                     int warps) {
+cudaError_t launch_n(int NV, int NH, const PlainArgs& a, int nplanes, int nframes, bool lp, int bps,
+                     cudaStream_t s, int warps) {
   switch (warps) {
-    case 2: return launch_nw<2>(N, a, nplanes, nframes, lp, bps, s);
-    case 4: return launch_nw<4>(N, a, nplanes, nframes, lp, bps, s);
-    case 8: return launch_nw<8>(N, a, nplanes, nframes, lp, bps, s);
+    case 2: return launch_nw<2>(NV, NH, a, nplanes, nframes, lp, bps, s);
+    case 4: return launch_nw<4>(NV, NH, a, nplanes, nframes, lp, bps, s);
+    case 8: return launch_nw<8>(NV, NH, a, nplanes, nframes, lp, bps, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -71,13 +85,14 @@ cudaError_t launch_plain(const Geometry& g, const FramePlanes& fp, int nframes, 
   a.s1 = g.s1y;
   a.s2 = g.s2y;
   a.M = t.M_y;
+  a.M2 = t.M_y;
   a.W = t.W_y;
   a.outH[0] = blockvals + ROW_H_Y * g.C;
   a.outL[0] = blockvals + ROW_L_Y * g.C;
   a.outH[1] = a.outL[1] = nullptr;
   a.zdump[0] = zdump ? zdump[0] : nullptr;
   a.zdump[1] = nullptr;
-  cudaError_t e = launch_n(g.w, a, 1, nframes, g.low_pass, g.bps, s, warps);
+  cudaError_t e = launch_n(g.w, g.w, a, 1, nframes, g.low_pass, g.bps, s, warps);
   if (e != cudaSuccess) return e;
   ++*launches;
 
@@ -91,6 +106,7 @@ cudaError_t launch_plain(const Geometry& g, const FramePlanes& fp, int nframes, 
   a.s1 = g.s1c;
   a.s2 = g.s2c;
   a.M = t.M_c;
+  a.M2 = t.M_cv;
   a.W = t.W_c;
   a.outH[0] = blockvals + ROW_H_U * g.C;
   a.outL[0] = blockvals + ROW_L_U * g.C;
@@ -98,7 +114,7 @@ cudaError_t launch_plain(const Geometry& g, const FramePlanes& fp, int nframes, 
   a.outL[1] = blockvals + ROW_L_V * g.C;
   a.zdump[0] = zdump ? zdump[1] : nullptr;
   a.zdump[1] = zdump ? zdump[2] : nullptr;
-  e = launch_n(g.nc, a, 2, nframes, g.low_pass, g.bps, s, warps);
+  e = launch_n(g.ncv, g.nc, a, 2, nframes, g.low_pass, g.bps, s, warps);
   if (e != cudaSuccess) return e;
   ++*launches;
   return cudaSuccess;

@@ -6,6 +6,8 @@
 // and produces T[r][k] = (sum_c x[r][c] M[k][c] + 2^(s1-1)) >> s1; stage 2: lane (j, v)
 // keeps column v of T in registers and produces Z[u][v] = (sum_r M[u][r] T[r][v] +
 // 2^(s2-1)) >> s2, accumulating H_v = sum_u w(u,v) |Z[u][v]| in increasing u with FMA.
+// 4:2:2 chroma blocks are rectangular (w rows of w/2 samples): the rows take the (w/2)-point
+// matrix and the columns the w-point one, each stage with the shift of its own length.
 // Both sums use the even/odd butterfly (Butterfly below), which equals the matrix form exactly.
 // The block energy is then the xor-butterfly sum of H_v over the NK lanes of the block
 // (offsets NK/2 .. 1), the same order the tensor-core form uses, so both forms give
@@ -94,38 +96,50 @@ struct Butterfly<1, NK, S, LD> {
   static __device__ __forceinline__ void run(const int (&x)[1], int (&y)[NK], const int*) { y[0] = 64 * x[0]; }
 };
 
-// Shared memory of one CTA of the block routine (WARPS warps).
-template <int N, bool LP, int WARPS = kWarps>
+// Shared memory of one CTA of the block routine (WARPS warps) for blocks of NV rows and NH columns:
+// the row matrix (NH x NH), the column matrix when the blocks are not square (NV x NV), the weights
+// of the kept coefficients and each warp's stage-1 output.
+template <int NV, int NH, bool LP, int WARPS = kWarps>
 struct PlainSmem {
-  static constexpr int NK = LP ? N / 2 : N;
-  static constexpr int BPW = 32 / N;
-  __align__(16) int M[N][N];
-  float W[NK][NK];
-  int T[WARPS][BPW][N][NK + 1];
+  static constexpr int NKV = LP ? NV / 2 : NV;
+  static constexpr int NKH = LP ? NH / 2 : NH;
+  static constexpr int BPW = 32 / NV;
+  static constexpr int NM2 = NV != NH ? NV : 1;
+  __align__(16) int M[NH][NH];
+  __align__(16) int M2[NM2][NM2];
+  float W[NKV][NKH];
+  int T[WARPS][BPW][NV][NKH + 1];
 };
 
-// Blocks chunk * BPC .. chunk * BPC + BPC - 1 of plane `plane` of frame f (one CTA of WARPS warps,
-// BPC = WARPS * 32/N; the warp owns 32/N blocks).  Stage 1: lane (j, r) keeps row r of block j in registers and produces
-// T[r][k]; stage 2: lane (j, v) keeps column v of T and produces Z[u][v], accumulating H_v.
-template <int N, bool LP, typename Pix, int WARPS = kWarps>
+// Blocks chunk * BPC .. chunk * BPC + BPC - 1 of plane `plane` of frame f (one CTA of WARPS
+// warps, BPC = WARPS * 32/NV; the warp owns 32/NV blocks).  Stage 1: lane (j, r) keeps row r of
+// block j (NH samples) in registers and produces T[r][k] with the NH-point matrix; stage 2: lane
+// (j, v) keeps column v of T (NV values) and produces Z[u][v] with the NV-point matrix,
+// accumulating H_v.  Square blocks (NV = NH) use one matrix for both stages.
+template <int NV, int NH, bool LP, typename Pix, int WARPS = kWarps>
 __device__ __forceinline__ void plain_blocks(const PlainArgs& p, int plane, int f, int64_t chunk,
-                                             PlainSmem<N, LP, WARPS>& sh) {
-  constexpr int NK = LP ? N / 2 : N;
-  constexpr int BPW = 32 / N;
+                                             PlainSmem<NV, NH, LP, WARPS>& sh) {
+  constexpr int NKV = LP ? NV / 2 : NV;
+  constexpr int NKH = LP ? NH / 2 : NH;
+  constexpr int BPW = 32 / NV;
   constexpr int BPC = WARPS * BPW;
-  auto& sM = sh.M;
-  auto& sW = sh.W;
   auto& sT = sh.T;
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const int lane = tid & 31;
-  for (int i = tid; i < N * N; i += WARPS * 32) sM[i / N][i % N] = p.M[i];
-  for (int i = tid; i < NK * NK; i += WARPS * 32) sW[i / NK][i % NK] = p.W[(i / NK) * N + (i % NK)];
+  for (int i = tid; i < NH * NH; i += WARPS * 32) sh.M[i / NH][i % NH] = p.M[i];
+  if constexpr (NV != NH)
+    for (int i = tid; i < NV * NV; i += WARPS * 32) sh.M2[i / NV][i % NV] = p.M2[i];
+  for (int i = tid; i < NKV * NKH; i += WARPS * 32) sh.W[i / NKH][i % NKH] = p.W[(i / NKH) * NH + (i % NKH)];
   __syncthreads();
+  const int* m1 = &sh.M[0][0];
+  const int* m2;
+  if constexpr (NV != NH) m2 = &sh.M2[0][0];
+  else m2 = m1;
 
-  const int j = lane / N;
-  const int r = lane % N;
+  const int j = lane / NV;
+  const int r = lane % NV;
   const int64_t k = chunk * BPC + warp * BPW + j;
   const bool valid = k < p.C;
   const int bx = valid ? (int)(k % p.nbx) : 0;
@@ -135,36 +149,36 @@ __device__ __forceinline__ void plain_blocks(const PlainArgs& p, int plane, int 
   const int off2 = 1 << (p.s2 - 1);
 
   if (valid) {
-    int x[N];
-    const int yy = min(by * N + r, p.height - 1);
-    load_row<N, Pix>(reinterpret_cast<const Pix*>(base + (int64_t)yy * p.pitch), bx * N, p.width, x);
-    int y[NK];
-    Butterfly<N, NK, 1, N>::run(x, y, &sM[0][0]);
+    int x[NH];
+    const int yy = min(by * NV + r, p.height - 1);
+    load_row<NH, Pix>(reinterpret_cast<const Pix*>(base + (int64_t)yy * p.pitch), bx * NH, p.width, x);
+    int y[NKH];
+    Butterfly<NH, NKH, 1, NH>::run(x, y, m1);
 #pragma unroll
-    for (int kk = 0; kk < NK; ++kk) sT[warp][j][r][kk] = (y[kk] + off1) >> p.s1;
+    for (int kk = 0; kk < NKH; ++kk) sT[warp][j][r][kk] = (y[kk] + off1) >> p.s1;
   }
   __syncwarp();
 
   float H = 0.0f;
   int z00 = 0;
   const int v = r;
-  if (valid && v < NK) {
-    int t[N];
+  if (valid && v < NKH) {
+    int t[NV];
 #pragma unroll
-    for (int rr = 0; rr < N; ++rr) t[rr] = sT[warp][j][rr][v];
-    int16_t* zd = p.zdump[plane] && f == 0 ? p.zdump[plane] + k * NK * NK : nullptr;
-    int zr[NK];
-    Butterfly<N, NK, 1, N>::run(t, zr, &sM[0][0]);
+    for (int rr = 0; rr < NV; ++rr) t[rr] = sT[warp][j][rr][v];
+    int16_t* zd = p.zdump[plane] && f == 0 ? p.zdump[plane] + k * NKV * NKH : nullptr;
+    int zr[NKV];
+    Butterfly<NV, NKV, 1, NV>::run(t, zr, m2);
 #pragma unroll
-    for (int u = 0; u < NK; ++u) {
+    for (int u = 0; u < NKV; ++u) {
       const int z = (zr[u] + off2) >> p.s2;
       if (u == 0) z00 = z;
-      if (zd) zd[u * NK + v] = (int16_t)z;
-      H = fmaf(fabsf((float)z), sW[u][v], H);
+      if (zd) zd[u * NKH + v] = (int16_t)z;
+      H = fmaf(fabsf((float)z), sh.W[u][v], H);
     }
   }
 #pragma unroll
-  for (int o = NK / 2; o > 0; o >>= 1) H += __shfl_xor_sync(0xffffffffu, H, o);
+  for (int o = NKH / 2; o > 0; o >>= 1) H += __shfl_xor_sync(0xffffffffu, H, o);
   if (valid && v == 0) {
     p.outH[plane][f * p.out_fstride + k] = H;
     p.outL[plane][f * p.out_fstride + k] = __fsqrt_rn((float)z00);

@@ -225,7 +225,7 @@ ReduceArgs reduce_args(const Geometry& g, int nframes, const float* blockvals, c
   a.nframes = nframes;
   a.has_prev = has_prev;
   a.normY = (double)g.C * g.w * g.w;
-  a.normC = (double)g.C * g.nc * g.nc;
+  a.normC = (double)g.C * g.ncv * g.nc;
   return a;
 }
 
@@ -339,6 +339,7 @@ extern "C" vca_status vca_reduce_frames_noalloc(const float* block_values, int64
   g.C = blocks_per_plane;
   g.w = block_size;
   g.nc = block_size / 2;
+  g.ncv = g.nc;
   int64_t launches = 0;
   e = launch_reduce(g, n_frames, block_values, prev_H_Y, prev_H_Y != nullptr, last_H_Y, features,
                     static_cast<unsigned long long*>(scratch),

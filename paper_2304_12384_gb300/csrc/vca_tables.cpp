@@ -22,15 +22,17 @@ void make_dct_matrix(int N, int8_t* out) {
   }
 }
 
-void make_energy_weights(int N, float* out) {
-  for (int u = 0; u < N; ++u) {
-    for (int v = 0; v < N; ++v) {
-      const double r = (double)(u + 1) * (v + 1) / ((double)N * N);
-      out[u * N + v] = (float)std::exp(std::fabs(r * r - 1.0));
+void make_energy_weights_rect(int Nv, int Nh, float* out) {
+  for (int u = 0; u < Nv; ++u) {
+    for (int v = 0; v < Nh; ++v) {
+      const double r = (double)(u + 1) * (v + 1) / ((double)Nv * Nh);
+      out[u * Nh + v] = (float)std::exp(std::fabs(r * r - 1.0));
     }
   }
   out[0] = 0.0f;  // the DC coefficient carries no texture
 }
+
+void make_energy_weights(int N, float* out) { make_energy_weights_rect(N, N, out); }
 
 void transform_shifts(int N, int B, int* s1, int* s2) {
   int l = 0;

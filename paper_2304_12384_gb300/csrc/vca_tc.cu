@@ -1261,7 +1261,7 @@ int sm_count() {
 }  // namespace
 
 bool tc_supported(const Geometry& g) {
-  return (g.B == 8 || g.B == 10) && g.w == 32 && g.nc == 16 && g.s1y == s1_of<32>(g.bps) &&
+  return (g.B == 8 || g.B == 10) && g.w == 32 && g.nc == 16 && g.ncv == 16 && g.s1y == s1_of<32>(g.bps) &&
          g.s1c == s1_of<16>(g.bps) && encode_fn() != nullptr;
 }
 

@@ -498,8 +498,9 @@ class Analyzer:
         w = self.cfg.block_size
         nk_y = w // 2 if self.cfg.low_pass else w  # quarter: N/2 coefficients; downsample: w/2 blocks
         nk_c = nk_y if self.cfg.chroma_format == VCA_CHROMA_444 else nk_y // 2
+        nkv_c = nk_y if self.cfg.chroma_format == VCA_CHROMA_422 else nk_c  # 4:2:2: w rows, w/2 columns
         zy = torch.empty((self.C, nk_y, nk_y), dtype=torch.int16, device=y.device)
-        zu = torch.empty((self.C, nk_c, nk_c), dtype=torch.int16, device=y.device)
+        zu = torch.empty((self.C, nkv_c, nk_c), dtype=torch.int16, device=y.device)
         zv = torch.empty_like(zu)
         py, pitch_y, _ = self._plane_args(y)
         pu, pitch_uv, _ = self._plane_args(u)

@@ -149,10 +149,12 @@ def test_batch_state_rules(vca):
             x.close()
 
 
-def test_batch_444_and_block_8(vca):
-    # Batches of 4:4:4 channels and of 8 x 8-block channels match single analyzers bit for bit.
-    for kw in ({"chroma_format": vca.VCA_CHROMA_444, "block_size": 16}, {"chroma_format": 0, "block_size": 8}):
-        cf = "444" if kw["chroma_format"] == 1 else "420"
+def test_batch_444_422_and_block_8(vca):
+    # Batches of 4:4:4 channels, of 4:2:2 channels and of 8 x 8-block channels match single
+    # analyzers bit for bit.
+    for kw in ({"chroma_format": vca.VCA_CHROMA_444, "block_size": 16}, {"chroma_format": 0, "block_size": 8},
+               {"chroma_format": vca.VCA_CHROMA_422, "block_size": 32}, {"chroma_format": vca.VCA_CHROMA_422, "block_size": 8}):
+        cf = {1: "444", 2: "422"}.get(kw["chroma_format"], "420")
         chans = [(200, 120, 8), (136, 72, 12)]
         frames = [frames_list(SequenceSpec(w, h, 3, 60 + i, bit_depth=bd, sigma=4.0, chroma_format=cf))
                   for i, (w, h, bd) in enumerate(chans)]
@@ -171,6 +173,16 @@ def test_batch_444_and_block_8(vca):
             assert [m.frame_features(t) for t in range(3)] == [s_.frame_features(t) for t in range(3)]
             m.close()
             s_.close()
+    # 4:2:0 and 4:2:2 channels with the same block size do not share a batch
+    a = vca.Analyzer(200, 120, 8, 32, False, kernel=vca.VCA_KERNEL_PLAIN)
+    b = vca.Analyzer(200, 120, 8, 32, False, kernel=vca.VCA_KERNEL_PLAIN, chroma_format=vca.VCA_CHROMA_422)
+    try:
+        with pytest.raises(vca.VcaError) as ei:
+            vca.Batch([a, b])
+        assert ei.value.status == vca.VCA_E_ARG
+    finally:
+        a.close()
+        b.close()
 
 
 def test_batch_with_drop_in_matrices(vca):

@@ -312,17 +312,44 @@ def test_chroma_444(vca, block_size, bit_depth):
                     low_pass=block_size == 16, dump_frames=(0, 3), chroma_format=1)
 
 
+@pytest.mark.parametrize("block_size", [32, 16, 8])
+@pytest.mark.parametrize("bit_depth", [8, 10, 12])
+def test_chroma_422(vca, block_size, bit_depth):
+    # 4:2:2: half-width, full-height chroma planes and chroma blocks of w rows by w/2 columns; 200 x 120
+    # leaves partial blocks at the right and bottom edges of every plane, and the chroma planes'
+    # 100-sample rows leave a ragged last block column at every block size.
+    frames = frames_list(SequenceSpec(200, 120, 4, 54 + bit_depth, bit_depth=bit_depth, sigma=5.0, cuts=(2,),
+                                      chroma_format="422", periods=(2.0, 24.0)))
+    for low_pass in (False, True):
+        run_and_compare(vca, "plain", frames, width=200, height=120, bit_depth=bit_depth, block_size=block_size,
+                        low_pass=low_pass, dump_frames=(0, 3), chroma_format=vca.VCA_CHROMA_422)
+
+
+@pytest.mark.parametrize("pad_mode", [0, 1])
+def test_chroma_422_hd_sampled(vca, pad_mode):
+    # 1080p 10-bit 4:2:2 (1080 = 33 * 32 + 24: a ragged block row) in one push of several frames.
+    frames = frames_list(SequenceSpec(1920, 1080, 3, 57, bit_depth=10, sigma=4.0, chroma_format="422"))
+    run_and_compare(vca, "plain", frames, width=1920, height=1080, bit_depth=10, block_size=32, pad_mode=pad_mode,
+                    dump_frames=(2,), block_frames=(0, 2), chroma_format=vca.VCA_CHROMA_422)
+
+
 def test_variant_rules(vca):
-    # The tensor-core form covers 8-bit 4:2:0 with 32 x 32 blocks; the others run on CUDA cores.
-    for kw in ({"bit_depth": 12}, {"block_size": 8}, {"chroma_format": 1}):
+    # The tensor-core form covers 8- and 10-bit 4:2:0 with 32 x 32 blocks; the others run on CUDA cores.
+    for kw in ({"bit_depth": 12}, {"block_size": 8}, {"chroma_format": 1}, {"chroma_format": 2}):
         args = dict(width=640, height=352, bit_depth=8, block_size=32)
         args.update(kw)
         an = vca.Analyzer(**args)
         assert an.kernel == vca.VCA_KERNEL_PLAIN
         an.close()
     with pytest.raises(vca.VcaError) as ei:
-        vca.Analyzer(640, 352, 8, 32, chroma_format=vca.VCA_CHROMA_422)
+        vca.Analyzer(640, 352, 8, 32, chroma_format=vca.VCA_CHROMA_422, kernel=vca.VCA_KERNEL_TC)
     assert ei.value.status == vca.VCA_E_UNSUPPORTED
+    with pytest.raises(vca.VcaError) as ei:
+        vca.Analyzer(640, 352, 8, 32, chroma_format=vca.VCA_CHROMA_422, low_pass=2)
+    assert ei.value.status == vca.VCA_E_UNSUPPORTED
+    with pytest.raises(vca.VcaError) as ei:
+        vca.Analyzer(640, 352, 8, 32, chroma_format=3)
+    assert ei.value.status == vca.VCA_E_ARG
 
 
 # ---- drop-in DCT matrices (an encoder's own integer table in place of the round-cosine one) ----

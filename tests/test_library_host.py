@@ -54,7 +54,7 @@ def test_status_strings(libvca):
     ((3840, 2160, 9, 32, 0, 0, 0, 64), -1),   # bit depth
     ((3840, 2160, 8, 24, 0, 0, 0, 64), -1),   # block size
     ((3840, 2160, 14, 32, 0, 0, 0, 64), -1),  # bit depth 14
-    ((3840, 2160, 8, 32, 0, 0, 0, 64, 2), -2),  # 4:2:2 unsupported
+    ((3840, 2160, 8, 32, 2, 0, 0, 64, 2), -2),  # 4:2:2 with the downsample reading
     ((3840, 2160, 8, 32, 0, 0, 0, 64, 5), -1),  # chroma format
     ((3840, 2160, 8, 32, 3, 0, 0, 64), -1),   # low_pass flag
     ((3840, 2160, 8, 16, 2, 0, 0, 64), -2),   # downsample reading needs block 32

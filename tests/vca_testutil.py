@@ -15,7 +15,7 @@ Tolerance (per feature, FP32 block arithmetic against the FP64 oracle):
 import numpy as np
 
 from oracle import (Config, analyze_sequence, block_grid, downsample_plane, frame_block_values, int_dct2,
-                    int_dct_matrix, plane_blocks, sequence_features)
+                    int_dct2_rect, int_dct_matrix, plane_blocks, sequence_features)
 from synth import pack_planes
 
 FEATURES = ("E_Y", "h", "L_Y", "E_U", "E_V", "L_U", "L_V")
@@ -56,7 +56,7 @@ def oracle_config(an) -> Config:
     mats = tuple((n, tuple(tuple(int(v) for v in row) for row in m)) for n, m in sorted(an.dct_matrices.items()))
     return Config(c.width, c.height, c.bit_depth, c.block_size, c.low_pass == 1,
                   "skip" if c.pad_mode == 1 else "replicate", downsample=c.low_pass == 2,
-                  chroma_format="444" if c.chroma_format == 1 else "420", dct_matrices=mats)
+                  chroma_format={1: "444", 2: "422"}.get(c.chroma_format, "420"), dct_matrices=mats)
 
 
 def structured_dct_matrix(N, changes=()):
@@ -96,11 +96,14 @@ def oracle_coefficients(frame, cfg: Config):
     y, u, v = frame
     if cfg.downsample:
         y, u, v = downsample_plane(y), downsample_plane(u), downsample_plane(v)
-    ny, nc = cfg.transform_sizes()
+    ny, _ = cfg.transform_sizes()
+    nv, nh = cfg.chroma_block()
     return {
         "Y": int_dct2(plane_blocks(y, ny, nbx, nby), cfg.bit_depth, cfg.low_pass, cfg.matrix(ny)),
-        "U": int_dct2(plane_blocks(u, nc, nbx, nby), cfg.bit_depth, cfg.low_pass, cfg.matrix(nc)),
-        "V": int_dct2(plane_blocks(v, nc, nbx, nby), cfg.bit_depth, cfg.low_pass, cfg.matrix(nc)),
+        "U": int_dct2_rect(plane_blocks(u, nv, nbx, nby, nh), cfg.bit_depth, cfg.low_pass, cfg.matrix(nh),
+                           cfg.matrix(nv)),
+        "V": int_dct2_rect(plane_blocks(v, nv, nbx, nby, nh), cfg.bit_depth, cfg.low_pass, cfg.matrix(nh),
+                           cfg.matrix(nv)),
     }
 
 
