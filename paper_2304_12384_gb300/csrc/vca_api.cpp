@@ -592,10 +592,10 @@ cudaError_t build_tick_graph(vca_batch* b, int k) {
     if (b->tc_groups == 2) {  // fork: the second group on its own branch
       e1 = cudaEventRecord(b->fork_ev, b->stream);
       if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(b->stream2, b->fork_ev, 0);
-      if (e1 == cudaSuccess) e1 = vca::launch_tc_batch(b->tc_params[1].data(), b->tc_gbps[1], b->low_pass, b->stream2);
+      if (e1 == cudaSuccess) e1 = vca::launch_tc_batch(b->tc_params[1].data(), b->w, b->tc_gbps[1], b->low_pass, b->stream2);
       if (e1 == cudaSuccess) e1 = cudaEventRecord(b->join_ev, b->stream2);
     }
-    if (e1 == cudaSuccess) e1 = vca::launch_tc_batch(b->tc_params[0].data(), b->tc_gbps[0], b->low_pass, b->stream);
+    if (e1 == cudaSuccess) e1 = vca::launch_tc_batch(b->tc_params[0].data(), b->w, b->tc_gbps[0], b->low_pass, b->stream);
     if (e1 == cudaSuccess && b->tc_groups == 2) e1 = cudaStreamWaitEvent(b->stream, b->join_ev, 0);
     if (e1 == cudaSuccess) e1 = vca::launch_reduce_batch_params(*b->red_params, b->stream);
   } else {
@@ -624,7 +624,7 @@ cudaError_t build_tick_graph(vca_batch* b, int k) {
       cudaKernelNodeParams kp{};
       e = cudaGraphKernelNodeGetParams(nodes[i], &kp);
       for (int gi = 0; e == cudaSuccess && gi < b->tc_groups; ++gi)
-        if (kp.func == vca::tc_batch_kernel(b->tc_gbps[gi], b->low_pass)) b->tc_node[k][gi] = nodes[i];
+        if (kp.func == vca::tc_batch_kernel(b->w, b->tc_gbps[gi], b->low_pass)) b->tc_node[k][gi] = nodes[i];
       if (e == cudaSuccess && kp.func == vca::reduce_batch_params_kernel()) b->red_node[k] = nodes[i];
     }
     if (e != cudaSuccess) return e;
@@ -1166,7 +1166,7 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
                "uploading the CTA map");
   }
   for (int gi = 0; b->tc && gi < b->tc_groups; ++gi)
-    BATCH_CUDA(vca::tc_batch_prepare(b->tc_gbps[gi], b->low_pass), "preparing the tensor-core kernel");
+    BATCH_CUDA(vca::tc_batch_prepare(b->w, b->tc_gbps[gi], b->low_pass), "preparing the tensor-core kernel");
   BATCH_CUDA(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device), "querying the SM count");
   if (b->sms < 1) b->sms = 1;
   if (b->tc && b->tc_groups == 2) {

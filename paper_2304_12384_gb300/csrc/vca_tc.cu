@@ -46,6 +46,12 @@
 // pre-offset accumulators), so the FP32 tensor-core accumulation is exact and Z is
 // bit-identical to the integer definition; H uses the same FP32 order as the CUDA-core form.
 //
+// 16x16 luma / 8x8 chroma blocks run the same data flow on 32x32 / 16x16 super-blocks of four
+// blocks each: the DCT matrix appears twice along the diagonal of every B operand (rows first:
+// the left and right halves of a super-block row get separate transforms; columns: the top and
+// bottom halves), the presets and shifts are those of the smaller transform, and epilogue 2 sums
+// each quadrant of a super-block's coefficients into its own block energy.
+//
 // A launch covers one analyzer's frames (its geometry in the kernel parameters) or, for a batched
 // tick, one frame of each of up to 64 analyzers of one sample size (a member table and their
 // tensor maps, also in the kernel parameters, read through the constant cache).
@@ -91,12 +97,22 @@ struct TcMember {
   float* blockvals;
 };
 
-// Stage-1 shift s1 = log2 N + B - 9 of a plane type; the bit depth follows from the sample size
-// (8-bit samples in bytes, 10-bit in 16-bit words).
-template <int Nb>
-__host__ __device__ constexpr int s1_of(int bps) {
-  return (Nb == 32 ? 5 : 4) + (bps == 1 ? 8 : 10) - 9;
+// Stage-1 shift s1 = log2 N + B - 9 of an N-point transform; the bit depth follows from the sample
+// size (8-bit samples in bytes, 10-bit in 16-bit words).
+__host__ __device__ constexpr int s1_of(int N, int bps) {
+  return (N == 32 ? 5 : N == 16 ? 4 : 3) + (bps == 1 ? 8 : 10) - 9;
 }
+
+// Block sizes of a launch: 32x32 luma and 16x16 chroma blocks, or (SUB) 16x16 luma and 8x8
+// chroma blocks processed as the four quadrants of each 32x32 / 16x16 area ("super-block").
+// Every operand, MMA and layout is the one of the 32x32 form; the B operands hold the smaller
+// matrix twice along the diagonal, so that the two halves of a super-block row (stage 1) or
+// column (stage 2) take separate transforms, and epilogue 2 sums each quadrant on its own.
+template <bool SUB>
+struct Blk {
+  static constexpr int NL = SUB ? 16 : 32;  // luma block size
+  static constexpr int NC = SUB ? 8 : 16;   // chroma block size
+};
 static_assert(sizeof(TcMember) % 8 == 0, "member table entries are copied as words");
 
 
@@ -460,6 +476,84 @@ __device__ __forceinline__ void epilogue2(const uint32_t (&td2)[2], int lane, co
   }
 }
 
+// Epilogue 2 of super-blocks of four blocks (16x16 luma / 8x8 chroma blocks), two jobs as in
+// epilogue2: thread (super-block, v') holds column v' of the super-block's coefficients, the left
+// blocks' columns in v' < G and the right blocks' in v' >= G (G = NK / 2 coefficients per block
+// and dimension), and rows u' < G of the top blocks, u' >= G of the bottom ones.  Each thread sums
+// w(u, v) |Z| in increasing u separately for the top and bottom block of each job; four xor trees
+// over the G lanes of a block, merged into one shuffle sequence, give the energies of the top and
+// bottom blocks of both jobs, which lanes 0, G/4, G/2, 3G/4 of the G-lane group store (with L =
+// sqrt(Z(0,0)) of the block).  sb[j]: super-block of job j (x, y in super-blocks); orow[j]: the
+// output row of H (L follows at + C); zd[j]: the coefficient dump of the plane (DUMP, frame 0).
+template <int Nb, bool LP, bool DUMP, int LO>
+__device__ __forceinline__ void epilogue2_sub(const uint32_t (&td2)[2], int lane, const float (&wts)[PC<Nb, LP>::NK / 2],
+                                              float einv, float c2, const int2 (&sb)[2], float* const (&orow)[2],
+                                              int nbx, int nby, int64_t C, int16_t* const (&zd)[2]) {
+  using P = PC<Nb, LP>;
+  constexpr int NK = P::NK;
+  constexpr int G = NK / 2;
+  constexpr int CPJ = NK / 8;
+  constexpr int S = 2 * CPJ;
+  const int vp = lane % NK;
+  const int v = vp % G;
+  uint32_t bh[2][8], bl[2][8];
+  tmem_ld<8>(td2[0], bh[0]);
+  tmem_ld<8>(td2[0] + LO, bl[0]);
+  float Ht[2] = {0.0f, 0.0f}, Hb[2] = {0.0f, 0.0f}, zt[2] = {0.0f, 0.0f}, zb[2] = {0.0f, 0.0f};
+#pragma unroll
+  for (int st = 0; st < S; ++st) {
+    const int j = st / CPJ, h0 = (st % CPJ) * 8;
+    tmem_wait_ld();
+    if (st + 1 < S) {
+      const uint32_t t1 = td2[(st + 1) / CPJ] + ((st + 1) % CPJ) * 8;
+      tmem_ld<8>(t1, bh[(st + 1) & 1]);
+      tmem_ld<8>(t1 + LO, bl[(st + 1) & 1]);
+    }
+#pragma unroll
+    for (int uu = 0; uu < 8; ++uu) {
+      const int up = h0 + uu;
+      const float w = __fmaf_rd(__uint_as_float(bl[st & 1][uu]), 0.00390625f, __uint_as_float(bh[st & 1][uu]));
+      const float z = __fmaf_rd(w, einv, c2) - kK1;
+      if (up == 0) zt[j] = z;
+      if (up == G) zb[j] = z;
+      if (DUMP && zd[j] && sb[j].x >= 0) {
+        const int bx = 2 * sb[j].x + vp / G, by = 2 * sb[j].y + up / G;
+        if (bx < nbx && by < nby) zd[j][((int64_t)by * nbx + bx) * G * G + (up % G) * G + v] = (int16_t)z;
+      }
+      if (up < G)
+        Ht[j] = fmaf(fabsf(z), wts[up], Ht[j]);
+      else
+        Hb[j] = fmaf(fabsf(z), wts[up - G], Hb[j]);
+    }
+  }
+  // Four trees in one: at offset G/2 the lower half of the group goes on with job 0 (top and
+  // bottom), the upper half with job 1; at G/4 each quarter keeps one block; then plain xor steps.
+  // Every addition is one of the separate trees' (operands swapped at most).
+  const bool upper = v >= G / 2;
+  const float X = (upper ? Ht[1] : Ht[0]) + __shfl_xor_sync(0xffffffffu, upper ? Ht[0] : Ht[1], G / 2);
+  const float Y = (upper ? Hb[1] : Hb[0]) + __shfl_xor_sync(0xffffffffu, upper ? Hb[0] : Hb[1], G / 2);
+  const bool uq = (v % (G / 2)) >= G / 4;
+  float R = (uq ? Y : X) + __shfl_xor_sync(0xffffffffu, uq ? X : Y, G / 4);
+#pragma unroll
+  for (int o = G / 8; o > 0; o >>= 1) R += __shfl_xor_sync(0xffffffffu, R, o);
+  // Z(0,0) of each block sits in the group's lane 0: lane G/4 takes the bottom block's of job 0,
+  // lane G/2 the top block's of job 1, lane 3G/4 the bottom block's of job 1.
+  const float zb0 = __shfl_xor_sync(0xffffffffu, zb[0], G / 4);
+  const float zt1 = __shfl_xor_sync(0xffffffffu, zt[1], G / 2);
+  const float zb1 = __shfl_xor_sync(0xffffffffu, zb[1], 3 * G / 4);
+  const int quarter = v / (G / 4);
+  if ((v % (G / 4)) == 0) {
+    const int j = quarter >> 1, dy = quarter & 1;
+    const float z = quarter == 0 ? zt[0] : quarter == 1 ? zb0 : quarter == 2 ? zt1 : zb1;
+    const int bx = 2 * sb[j].x + vp / G, by = 2 * sb[j].y + dy;
+    if (orow[j] && sb[j].x >= 0 && bx < nbx && by < nby) {
+      const int64_t k = (int64_t)by * nbx + bx;
+      orow[j][k] = R;
+      orow[j][C + k] = __fsqrt_rn(z);
+    }
+  }
+}
+
 // Tile bookkeeping of a role's current tile.
 struct TileInfo {
   int f, tx, ty, stage, t, m;  // frame, tile position, ring stage, CTA-local tile number, member
@@ -694,12 +788,12 @@ __device__ void convert_chroma_loop(const TileRec* recs, const Ctl& ctl, uint8_t
 
 // Epilogue 1 luma: T = floor(T'/2^s1) of both luma jobs into the stage-2 operands (hi and lo bytes
 // as fp16, MN-major; s1 = log2 N + B - 9).
-template <bool LP, int BPS>
+template <bool LP, bool SUB, int BPS>
 __device__ void epi1_luma_loop(const Ctl& ctl, uint32_t sbase, uint32_t tq, int n_items, int q, int lane) {
   using SL = SmemLay<BPS>;
   using U = Unit<LP>;
   using P = PC<32, LP>;
-  const float s1inv = __int_as_float((127 - s1_of<32>(BPS)) << 23);  // 2^-s1
+  const float s1inv = __int_as_float((127 - s1_of(Blk<SUB>::NL, BPS)) << 23);  // 2^-s1
   const E1Offs<32, LP> eo(q, lane);
   Cursor<U::DS> cd;
   Cursor<kA2Sets> ce;
@@ -731,16 +825,26 @@ __device__ __forceinline__ int64_t block_of(const TcMember& M, const TileRec& r,
   return (bx < M.nbx && by < M.nby) ? (int64_t)by * M.nbx + bx : -1;
 }
 
+// Super-block (x, y in super-blocks of the frame) of the stage-2 row m = 32 q + lane of job jp.
+template <int NK, int BPG2>
+__device__ __forceinline__ int2 superblock_of(const TileRec& r, int jp, int q, int lane) {
+  const int idx = jp * BPG2 + (32 * q + lane) / NK;
+  return make_int2(r.tx * 4 + (idx & 3), r.ty * 4 + (idx >> 2));
+}
+
 // Epilogue 2 luma: Z, the block energy H and brightness L of both luma jobs, then the slot's luma
 // columns are handed back.
-template <bool LP, bool DUMP, class PP, class MS>
+template <bool LP, bool SUB, bool DUMP, class PP, class MS>
 __device__ void epi2_luma_loop(const PP& p, const MS& ms, const TileRec* recs, const Ctl& ctl, uint32_t tq,
                                int n_items, int q, int lane) {
   using P = PC<32, LP>;
   using U = Unit<LP>;
-  float w[P::NK];
+  constexpr int NW = SUB ? P::NK / 2 : P::NK;  // weights per thread: one block column
+  constexpr int NL = Blk<SUB>::NL;
+  constexpr float einv = SUB ? 0.25f : 0.125f;  // 2^8 / 2^s2, s2 = log2 N + 6
+  float w[NW];
 #pragma unroll
-  for (int uu = 0; uu < P::NK; ++uu) w[uu] = p.W_y[uu * 32 + (lane % P::NK)];
+  for (int uu = 0; uu < NW; ++uu) w[uu] = p.W_y[uu * NL + (lane % P::NK) % NW];
   Cursor<U::DS> cd;
   const int n = n_items * U::UPT;
   TileRec rec{};
@@ -754,14 +858,26 @@ __device__ void epi2_luma_loop(const PP& p, const MS& ms, const TileRec* recs, c
     uint32_t td2[2];
     float* out[2];
     int16_t* zd[2];
+    if constexpr (SUB) {
+      int2 sb[2];
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int64_t k = block_of<P::NK, P::BPG2>(M, rec, h * 2 + j, q, lane);
-      td2[j] = td + 2 * j * P::N1;
-      out[j] = k >= 0 ? base + k : nullptr;
-      zd[j] = (DUMP && k >= 0 && rec.f == 0) ? p.zdump[0] + k * P::NK * P::NK : nullptr;
+      for (int j = 0; j < 2; ++j) {
+        sb[j] = superblock_of<P::NK, P::BPG2>(rec, h * 2 + j, q, lane);
+        td2[j] = td + 2 * j * P::N1;
+        out[j] = base;
+        zd[j] = (DUMP && rec.f == 0) ? p.zdump[0] : nullptr;
+      }
+      epilogue2_sub<32, LP, DUMP, P::N1>(td2, lane, w, einv, kK1 - kK1 * einv, sb, out, M.nbx, M.nby, M.C, zd);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int64_t k = block_of<P::NK, P::BPG2>(M, rec, h * 2 + j, q, lane);
+        td2[j] = td + 2 * j * P::N1;
+        out[j] = k >= 0 ? base + k : nullptr;
+        zd[j] = (DUMP && k >= 0 && rec.f == 0) ? p.zdump[0] + k * P::NK * P::NK : nullptr;
+      }
+      epilogue2<32, LP, DUMP, P::N1>(td2, lane, w, einv, kK1 - kK1 * einv, out, M.C, zd);
     }
-    epilogue2<32, LP, DUMP, P::N1>(td2, lane, w, 0.125f, kK1 - kK1 / 8.0f, out, M.C, zd);
     tc_fence_before();
     __syncwarp();
     if (lane == 0) mbar_arrive(&ctl.bars[b_dfree(cd.slot)]);
@@ -774,18 +890,21 @@ __device__ void epi2_luma_loop(const PP& p, const MS& ms, const TileRec* recs, c
 
 // Chroma epilogues, one warpgroup: for unit u, epilogue 1 (as for luma, both planes), then
 // epilogue 2 of unit u - 1.
-template <bool LP, bool DUMP, int BPS, class PP, class MS>
+template <bool LP, bool SUB, bool DUMP, int BPS, class PP, class MS>
 __device__ void chroma_epi_loop(const PP& p, const MS& ms, const TileRec* recs, const Ctl& ctl, uint32_t sbase,
                                 uint32_t tq, int n_items, int q, int lane, int mode) {
   using SL = SmemLay<BPS>;
   using U = Unit<LP>;
   using P = PC<16, LP>;
   constexpr int NKC = U::NKC, NCC = U::NCC;
-  const float s1inv = __int_as_float((127 - s1_of<16>(BPS)) << 23);
+  constexpr int NW = SUB ? P::NK / 2 : P::NK;
+  constexpr int NC = Blk<SUB>::NC;
+  constexpr float einv = SUB ? 0.5f : 0.25f;  // 2^8 / 2^s2
+  const float s1inv = __int_as_float((127 - s1_of(NC, BPS)) << 23);
   const E1Offs<16, LP> eo(q, lane);
-  float w[P::NK];
+  float w[NW];
 #pragma unroll
-  for (int uu = 0; uu < P::NK; ++uu) w[uu] = p.W_c[uu * 16 + (lane % P::NK)];
+  for (int uu = 0; uu < NW; ++uu) w[uu] = p.W_c[uu * NC + (lane % P::NK) % NW];
   Cursor<U::DS> cd, cd2;
   Cursor<kA2Sets> ce;
   const int n = n_items * U::UPT;
@@ -815,18 +934,30 @@ __device__ void chroma_epi_loop(const PP& p, const MS& ms, const TileRec* recs, 
       if (h == 0) rec = load_rec(recs, t);
       const TcMember& M = ms[rec.m];
       const uint32_t td = tq + U::d(cd2.slot) + U::DC;
-      const int64_t k = block_of<P::NK, P::BPG2>(M, rec, h, q, lane);  // U and V share the block
       float* const base = M.blockvals + (int64_t)rec.f * M.out_fstride;
       uint32_t td2[2];
       float* out[2];
       int16_t* zd[2];
+      if constexpr (SUB) {
+        const int2 sb0 = superblock_of<P::NK, P::BPG2>(rec, h, q, lane);  // U and V share the super-block
+        const int2 sb[2] = {sb0, sb0};
 #pragma unroll
-      for (int pl = 0; pl < 2; ++pl) {
-        td2[pl] = td + pl * NKC;
-        out[pl] = k >= 0 ? base + (2 + 2 * pl) * M.C + k : nullptr;
-        zd[pl] = (DUMP && k >= 0 && rec.f == 0) ? p.zdump[1 + pl] + k * P::NK * P::NK : nullptr;
+        for (int pl = 0; pl < 2; ++pl) {
+          td2[pl] = td + pl * NKC;
+          out[pl] = base + (2 + 2 * pl) * M.C;
+          zd[pl] = (DUMP && rec.f == 0) ? p.zdump[1 + pl] : nullptr;
+        }
+        epilogue2_sub<16, LP, DUMP, NCC>(td2, lane, w, einv, kK1 - kK1 * einv, sb, out, M.nbx, M.nby, M.C, zd);
+      } else {
+        const int64_t k = block_of<P::NK, P::BPG2>(M, rec, h, q, lane);  // U and V share the block
+#pragma unroll
+        for (int pl = 0; pl < 2; ++pl) {
+          td2[pl] = td + pl * NKC;
+          out[pl] = k >= 0 ? base + (2 + 2 * pl) * M.C + k : nullptr;
+          zd[pl] = (DUMP && k >= 0 && rec.f == 0) ? p.zdump[1 + pl] + k * P::NK * P::NK : nullptr;
+        }
+        epilogue2<16, LP, DUMP, NCC>(td2, lane, w, einv, kK1 - kK1 * einv, out, M.C, zd);
       }
-      epilogue2<16, LP, DUMP, NCC>(td2, lane, w, 0.25f, kK1 - kK1 / 4.0f, out, M.C, zd);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&ctl.bars[b_dfree(cd2.slot)]);
@@ -947,11 +1078,12 @@ __device__ void issuer_loop(const Ctl& ctl, uint32_t sbase, uint32_t tmem, int i
   }
 }
 
-template <bool LP, bool DUMP, int BPS, bool BATCH>
+template <bool LP, bool SUB, bool DUMP, int BPS, bool BATCH>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_kernel(const __grid_constant__ TcParamsT<BATCH ? kMaxMembers : 1> p) {
   using L = PC<32, LP>;
   using U = Unit<LP>;
+  constexpr int NL = Blk<SUB>::NL, NC = Blk<SUB>::NC;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   using SL = SmemLay<BPS>;
@@ -993,16 +1125,31 @@ __global__ void __launch_bounds__(kThreads, 1)
   // Constant B operands (the integer DCT matrices as fp16), K-major without swizzle:
   // element (n, k) at (n/8)*SBO + (k/8)*128 + (n%8)*16 + (k%8)*2.  Luma: M (N1 rows, K = 32).
   // Chroma: M's first NKC rows in rows [0, NKC) of the U operand and rows [NKC, 2 NKC) of the V
-  // operand, zero elsewhere (K = 16).
+  // operand, zero elsewhere (K = 16).  SUB: the smaller matrix's first N1/2 (luma) or NKC/2
+  // (chroma) rows twice along the diagonal -- operand row n = (half, row), column k = (half, col).
   for (int i = tid; i < L::N1 * 32; i += kThreads) {
     const int n = i >> 5, kk = i & 31;
-    const __half h = __float2half_rn((float)p.M_y[n * 32 + kk]);
-    *(__half*)(sm + SL::OFF_BL + (n >> 3) * 512 + (kk >> 3) * 128 + (n & 7) * 16 + (kk & 7) * 2) = h;
+    float v;
+    if (SUB) {
+      const int hn = L::N1 / 2;
+      v = (n / hn == kk / 16) ? (float)p.M_y[(n % hn) * 16 + (kk % 16)] : 0.0f;
+    } else {
+      v = (float)p.M_y[n * 32 + kk];
+    }
+    *(__half*)(sm + SL::OFF_BL + (n >> 3) * 512 + (kk >> 3) * 128 + (n & 7) * 16 + (kk & 7) * 2) = __float2half_rn(v);
   }
   for (int i = tid; i < 2 * 32 * 16; i += kThreads) {
     const int pl = i >> 9, n = (i >> 4) & 31, kk = i & 15;
     const int row = n - pl * U::NKC;  // matrix row held at operand row n
-    const float v = (row >= 0 && row < U::NKC) ? (float)p.M_c[row * 16 + kk] : 0.0f;
+    float v = 0.0f;
+    if (row >= 0 && row < U::NKC) {
+      if (SUB) {
+        const int hn = U::NKC / 2;
+        v = (row / hn == kk / 8) ? (float)p.M_c[(row % hn) * 8 + (kk % 8)] : 0.0f;
+      } else {
+        v = (float)p.M_c[row * 16 + kk];
+      }
+    }
     *(__half*)(sm + (pl ? SL::OFF_BCV : SL::OFF_BCU) + (n >> 3) * 256 + (kk >> 3) * 128 + (n & 7) * 16 + (kk & 7) * 2) =
         __float2half_rn(v);
   }
@@ -1011,7 +1158,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   // starts at 1024 a_n + b_n for row n of K = (a_n, b_n, 0, ...): 2^(s1-1), the rounding offset
   // of T, minus 1024 * 64 * N in each DC column (the bias of the 1024 + x sample encoding), split
   // as a = -(multiple of 8 below 2^11) and b = P - 1024 a (|b| < 2^13, a multiple of 8), both exact
-  // in fp16.  Luma DC columns: every N1-th; chroma: every NKC-th (U and V alternate).
+  // in fp16.  Luma DC columns: every N1-th; chroma: every NKC-th (U and V alternate); SUB: every
+  // N1/2-th and NKC/2-th (the left and right blocks of a super-block).
   for (int i = tid; i < 128 * 16; i += kThreads) {
     const int m = i >> 4, kk = i & 15;
     const float v = kk == 0 ? 1024.0f : kk == 1 ? 1.0f : 0.0f;
@@ -1020,8 +1168,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   for (int i = tid; i < 2 * 32 * 16; i += kThreads) {
     const bool luma = i < 32 * 16;
     const int kk = i & 15, n = (i >> 4) & 31;
-    const int N = luma ? 32 : 16, period = luma ? L::N1 : U::NKC;
-    const int P = (1 << (s1_of<32>(BPS) - (luma ? 1 : 2))) - (n % period == 0 ? 1024 * 64 * N : 0);
+    const int N = luma ? NL : NC, period = (luma ? L::N1 : U::NKC) / (SUB ? 2 : 1);
+    const int P = (1 << (s1_of(N, BPS) - 1)) - (n % period == 0 ? 1024 * 64 * N : 0);
     const int a = P >= 0 ? (P >> 10) & ~7 : -(((-P) >> 10) & ~7);
     const float v = kk == 0 ? (float)a : kk == 1 ? (float)(P - a * 1024) : 0.0f;
     *(__half*)(sm + (luma ? SL::OFF_KL : SL::OFF_KC) + (n >> 3) * 256 + (kk >> 3) * 128 + (n & 7) * 16 + (kk & 7) * 2) =
@@ -1029,24 +1177,25 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   // Stage-2 presets, by one more MMA per stage-2 stream: hi accumulators start at K1, minus
   // 1156 * 64 * N on each u = 0 column (the 1024 + byte encoding of both halves and the +128
-  // offset of the hi byte), lo accumulators at 2^(s2-1) (luma N = 32: s2 = 11; chroma: 10), the
-  // magic constants of epilogue 2; split as for the stage-1 presets.  Luma: N1 hi rows then N1 lo
-  // rows; chroma: NCC rows each for hi (u = 0 every NKC-th) and lo.
+  // offset of the hi byte), lo accumulators at 2^(s2-1) (s2 = log2 N + 6: 11 for N = 32, 10 for
+  // 16, 9 for 8), the magic constants of epilogue 2; split as for the stage-1 presets.  Luma: N1
+  // hi rows then N1 lo rows; chroma: NCC rows each for hi (u = 0 every NKC-th; SUB: every
+  // N1/2-th and NKC/2-th, the top and bottom blocks) and lo.
   for (int i = tid; i < (64 + 32 + 32) * 16; i += kThreads) {
     const int kk = i & 15, row = i >> 4;
     int P, off, n;
     if (row < 64) {
       n = row;
       off = SL::OFF_K2L;
-      P = n < L::N1 ? (n == 0 ? 12582912 - 1156 * 64 * 32 : 12582912) : 1024;
+      P = n < L::N1 ? (n % (SUB ? L::N1 / 2 : L::N1) == 0 ? 12582912 - 1156 * 64 * NL : 12582912) : NL * 32;
     } else if (row < 96) {
       n = row - 64;
       off = SL::OFF_K2CH;
-      P = n % U::NKC == 0 ? 12582912 - 1156 * 64 * 16 : 12582912;
+      P = n % (SUB ? U::NKC / 2 : U::NKC) == 0 ? 12582912 - 1156 * 64 * NC : 12582912;
     } else {
       n = row - 96;
       off = SL::OFF_K2CL;
-      P = 512;
+      P = NC * 32;
     }
     const int a = (P >> 10) & ~7;
     const float v = kk == 0 ? (float)a : kk == 1 ? (float)(P - a * 1024) : 0.0f;
@@ -1138,13 +1287,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (role == 3) {
     convert_chroma_loop<LP, BPS>(recs, ctl, sm, tmem + lanebase, n_items, q, lane);
   } else if (role == 4) {
-    epi1_luma_loop<LP, BPS>(ctl, sbase, tmem + lanebase, n_items, q, lane);
+    epi1_luma_loop<LP, SUB, BPS>(ctl, sbase, tmem + lanebase, n_items, q, lane);
   } else if (role == 5) {
-    epi2_luma_loop<LP, DUMP>(p, ms, recs, ctl, tmem + lanebase, n_items, q, lane);
+    epi2_luma_loop<LP, SUB, DUMP>(p, ms, recs, ctl, tmem + lanebase, n_items, q, lane);
   } else if (role == 6) {
-    chroma_epi_loop<LP, DUMP, BPS>(p, ms, recs, ctl, sbase, tmem + lanebase, n_items, q, lane, 1);
+    chroma_epi_loop<LP, SUB, DUMP, BPS>(p, ms, recs, ctl, sbase, tmem + lanebase, n_items, q, lane, 1);
   } else {
-    chroma_epi_loop<LP, DUMP, BPS>(p, ms, recs, ctl, sbase, tmem + lanebase, n_items, q, lane, 2);
+    chroma_epi_loop<LP, SUB, DUMP, BPS>(p, ms, recs, ctl, sbase, tmem + lanebase, n_items, q, lane, 2);
   }
 
   tc_fence_before();
@@ -1191,52 +1340,67 @@ cudaError_t make_map(CUtensorMap* m, const void* base, int w, int h, int64_t pit
 }
 
 // Raises the instance's dynamic shared-memory limit (once per process).
-template <bool LP, bool DUMP, int BPS, bool BATCH>
+template <bool LP, bool SUB, bool DUMP, int BPS, bool BATCH>
 cudaError_t prepare_inst() {
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(tc_kernel<LP, DUMP, BPS, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    attr = cudaFuncSetAttribute(tc_kernel<LP, SUB, DUMP, BPS, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 SmemLay<BPS>::kSmemBytes);
   });
   return attr;
 }
 
 // grid 0: only prepare the instance.
-template <bool LP, bool DUMP, int BPS, bool BATCH>
+template <bool LP, bool SUB, bool DUMP, int BPS, bool BATCH>
 cudaError_t launch_inst(const TcParamsT<BATCH ? kMaxMembers : 1>& p, int grid, cudaStream_t s) {
-  const cudaError_t attr = prepare_inst<LP, DUMP, BPS, BATCH>();
+  const cudaError_t attr = prepare_inst<LP, SUB, DUMP, BPS, BATCH>();
   if (attr != cudaSuccess) return attr;
   if (grid <= 0) return cudaSuccess;
-  tc_kernel<LP, DUMP, BPS, BATCH><<<grid, kThreads, SmemLay<BPS>::kSmemBytes, s>>>(p);
+  tc_kernel<LP, SUB, DUMP, BPS, BATCH><<<grid, kThreads, SmemLay<BPS>::kSmemBytes, s>>>(p);
   return cudaGetLastError();
 }
 
-// A single analyzer's launch (bps 1 or 2).
-cudaError_t launch_single(const TcParams& p, int grid, bool low_pass, bool dump, int bps, cudaStream_t s) {
-  if (bps == 1) {
-    if (low_pass)
-      return dump ? launch_inst<true, true, 1, false>(p, grid, s) : launch_inst<true, false, 1, false>(p, grid, s);
-    return dump ? launch_inst<false, true, 1, false>(p, grid, s) : launch_inst<false, false, 1, false>(p, grid, s);
-  }
-  if (low_pass)
-    return dump ? launch_inst<true, true, 2, false>(p, grid, s) : launch_inst<true, false, 2, false>(p, grid, s);
-  return dump ? launch_inst<false, true, 2, false>(p, grid, s) : launch_inst<false, false, 2, false>(p, grid, s);
-}
-
-// A batched launch of members of one sample size (bps 1 or 2).
-cudaError_t launch_batched(const TcBatchParams& p, int grid, bool low_pass, int bps, cudaStream_t s) {
+template <bool SUB, bool DUMP>
+cudaError_t launch_single_sd(const TcParams& p, int grid, bool low_pass, int bps, cudaStream_t s) {
   if (bps == 1)
-    return low_pass ? launch_inst<true, false, 1, true>(p, grid, s) : launch_inst<false, false, 1, true>(p, grid, s);
-  return low_pass ? launch_inst<true, false, 2, true>(p, grid, s) : launch_inst<false, false, 2, true>(p, grid, s);
+    return low_pass ? launch_inst<true, SUB, DUMP, 1, false>(p, grid, s)
+                    : launch_inst<false, SUB, DUMP, 1, false>(p, grid, s);
+  return low_pass ? launch_inst<true, SUB, DUMP, 2, false>(p, grid, s)
+                  : launch_inst<false, SUB, DUMP, 2, false>(p, grid, s);
 }
 
-// One member's entry: geometry, outputs and stage-1 constants; returns its number of items.
+// A single analyzer's launch (bps 1 or 2; w 32, or 16 for the super-block form).
+cudaError_t launch_single(const TcParams& p, int grid, int w, bool low_pass, bool dump, int bps, cudaStream_t s) {
+  if (w == 16)
+    return dump ? launch_single_sd<true, true>(p, grid, low_pass, bps, s)
+                : launch_single_sd<true, false>(p, grid, low_pass, bps, s);
+  return dump ? launch_single_sd<false, true>(p, grid, low_pass, bps, s)
+              : launch_single_sd<false, false>(p, grid, low_pass, bps, s);
+}
+
+template <bool SUB>
+cudaError_t launch_batched_s(const TcBatchParams& p, int grid, bool low_pass, int bps, cudaStream_t s) {
+  if (bps == 1)
+    return low_pass ? launch_inst<true, SUB, false, 1, true>(p, grid, s)
+                    : launch_inst<false, SUB, false, 1, true>(p, grid, s);
+  return low_pass ? launch_inst<true, SUB, false, 2, true>(p, grid, s)
+                  : launch_inst<false, SUB, false, 2, true>(p, grid, s);
+}
+
+// A batched launch of members of one sample size (bps 1 or 2) and block size w.
+cudaError_t launch_batched(const TcBatchParams& p, int grid, int w, bool low_pass, int bps, cudaStream_t s) {
+  return w == 16 ? launch_batched_s<true>(p, grid, low_pass, bps, s) : launch_batched_s<false>(p, grid, low_pass, bps, s);
+}
+
+// One member's entry: geometry, outputs and stage-1 constants; returns its number of items.  A
+// tile is 128 x 128 luma samples: 4 x 4 blocks of 32 x 32, or 8 x 8 of 16 x 16.
 int fill_member(TcMember& m, const Geometry& g, int item_base, int nframes, float* blockvals) {
   m = TcMember{};
   m.item_base = item_base;
-  m.tiles_x = (g.nbx + 3) / 4;
-  m.tiles_per_frame = m.tiles_x * ((g.nby + 3) / 4);
+  const int bpt = 128 / g.w;
+  m.tiles_x = (g.nbx + bpt - 1) / bpt;
+  m.tiles_per_frame = m.tiles_x * ((g.nby + bpt - 1) / bpt);
   m.inv_tiles_x = 1.0f / (float)m.tiles_x;
   m.inv_tiles_per_frame = 1.0f / (float)m.tiles_per_frame;
   m.W = g.W;
@@ -1261,8 +1425,9 @@ int sm_count() {
 }  // namespace
 
 bool tc_supported(const Geometry& g) {
-  return (g.B == 8 || g.B == 10) && g.w == 32 && g.nc == 16 && g.ncv == 16 && g.s1y == s1_of<32>(g.bps) &&
-         g.s1c == s1_of<16>(g.bps) && encode_fn() != nullptr;
+  const bool sizes = (g.w == 32 && g.nc == 16) || (g.w == 16 && g.nc == 8);
+  return (g.B == 8 || g.B == 10) && sizes && g.ncv == g.nc && g.s1y == s1_of(g.w, g.bps) &&
+         g.s1c == s1_of(g.nc, g.bps) && encode_fn() != nullptr;
 }
 
 struct TcMapCache {
@@ -1300,7 +1465,7 @@ cudaError_t tc_batch_fill(void* params, const TcBatchFrame* frames, int n, const
   for (int i = 0; i < n; ++i) {
     const Geometry& g = *frames[i].g;
     const FramePlanes& fp = frames[i].fp;
-    if (!tc_supported(g) || g.bps != frames[0].g->bps) return cudaErrorInvalidValue;
+    if (!tc_supported(g) || g.bps != frames[0].g->bps || g.w != frames[0].g->w) return cudaErrorInvalidValue;
     items += fill_member(p.mem[i], g, items, 1, frames[i].blockvals);
     TcMapCache* c = frames[i].maps;
     const TcMapCache::Entry* hit = nullptr;
@@ -1337,22 +1502,27 @@ cudaError_t tc_batch_fill(void* params, const TcBatchFrame* frames, int n, const
 
 int tc_batch_items(const void* params) { return static_cast<const TcBatchParams*>(params)->total_items; }
 
-cudaError_t tc_batch_prepare(int bps, bool low_pass) {
-  if (bps != 1 && bps != 2) return cudaErrorInvalidValue;
+cudaError_t tc_batch_prepare(int w, int bps, bool low_pass) {
+  if ((bps != 1 && bps != 2) || (w != 32 && w != 16)) return cudaErrorInvalidValue;
   static TcBatchParams unused{};
-  return launch_batched(unused, 0, low_pass, bps, nullptr);
+  return launch_batched(unused, 0, w, low_pass, bps, nullptr);
 }
 
-cudaError_t launch_tc_batch(const void* params, int bps, bool low_pass, cudaStream_t s) {
-  if (bps != 1 && bps != 2) return cudaErrorInvalidValue;
+cudaError_t launch_tc_batch(const void* params, int w, int bps, bool low_pass, cudaStream_t s) {
+  if ((bps != 1 && bps != 2) || (w != 32 && w != 16)) return cudaErrorInvalidValue;
   // The number of items is known from the parameters; CTAs beyond it find no work.
-  return launch_batched(*static_cast<const TcBatchParams*>(params), sm_count(), low_pass, bps, s);
+  return launch_batched(*static_cast<const TcBatchParams*>(params), sm_count(), w, low_pass, bps, s);
 }
 
-const void* tc_batch_kernel(int bps, bool low_pass) {
+template <bool SUB>
+const void* tc_batch_kernel_s(int bps, bool low_pass) {
   if (bps == 1)
-    return low_pass ? (const void*)tc_kernel<true, false, 1, true> : (const void*)tc_kernel<false, false, 1, true>;
-  return low_pass ? (const void*)tc_kernel<true, false, 2, true> : (const void*)tc_kernel<false, false, 2, true>;
+    return low_pass ? (const void*)tc_kernel<true, SUB, false, 1, true> : (const void*)tc_kernel<false, SUB, false, 1, true>;
+  return low_pass ? (const void*)tc_kernel<true, SUB, false, 2, true> : (const void*)tc_kernel<false, SUB, false, 2, true>;
+}
+
+const void* tc_batch_kernel(int w, int bps, bool low_pass) {
+  return w == 16 ? tc_batch_kernel_s<true>(bps, low_pass) : tc_batch_kernel_s<false>(bps, low_pass);
 }
 
 cudaError_t launch_tc(const Geometry& g, const FramePlanes& fp, int nframes, const DeviceTables& t, float* blockvals,
@@ -1386,7 +1556,7 @@ cudaError_t launch_tc(const Geometry& g, const FramePlanes& fp, int nframes, con
   p.withhold = withhold;
   int grid = ctas > 0 && ctas < sm_count() ? ctas : sm_count();
   if (p.total_items < grid) grid = p.total_items;
-  e = launch_single(p, grid, g.low_pass, zdump != nullptr, bps, s);
+  e = launch_single(p, grid, g.w, g.low_pass, zdump != nullptr, bps, s);
   if (e == cudaSuccess) ++*launches;
   return e;
 }

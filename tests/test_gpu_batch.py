@@ -51,16 +51,17 @@ CASES = [  # (kernel, channels): the tensor-core batch with one sample size (byt
 ]
 
 
+@pytest.mark.parametrize("block_size", [32, 16])
 @pytest.mark.parametrize("low_pass", [True, False])
 @pytest.mark.parametrize("kind,channels", CASES, ids=["plain", "tc-mixed", "tc-8bit", "tc-10bit"])
-def test_batch_matches_single_analyzers_and_oracle(vca, low_pass, kind, channels):
+def test_batch_matches_single_analyzers_and_oracle(vca, block_size, low_pass, kind, channels):
     import torch
 
     kernel = vca.VCA_KERNEL_TC if kind == "tc" else vca.VCA_KERNEL_PLAIN
     frames = [_channel_frames(i, *c) for i, c in enumerate(channels)]
     dev = [to_device(f) for f in frames]
-    members = [vca.Analyzer(w, h, bd, 32, low_pass, kernel=kernel, max_batch=4) for (w, h, bd) in channels]
-    singles = [vca.Analyzer(w, h, bd, 32, low_pass, kernel=kernel, max_batch=4) for (w, h, bd) in channels]
+    members = [vca.Analyzer(w, h, bd, block_size, low_pass, kernel=kernel, max_batch=4) for (w, h, bd) in channels]
+    singles = [vca.Analyzer(w, h, bd, block_size, low_pass, kernel=kernel, max_batch=4) for (w, h, bd) in channels]
     fed = [[] for _ in channels]
     try:
         batch = vca.Batch(members)

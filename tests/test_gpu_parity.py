@@ -260,31 +260,34 @@ def test_argument_errors_on_device(vca, kernel):
 
 # Downsample reading of the low-pass option: halved planes (rounded 2x2 mean, odd edges
 # repeated) analysed with 16 x 16 / 8 x 8 blocks on the 32-block grid.
+@pytest.mark.parametrize("kernel", list(KERNELS))
 @pytest.mark.parametrize("bit_depth", [8, 10])
 @pytest.mark.parametrize("size", [(640, 352), (200, 120), (202, 118)])
-def test_downsample_reading(vca, bit_depth, size):
+def test_downsample_reading(vca, kernel, bit_depth, size):
     w, h = size
     frames = frames_list(SequenceSpec(w, h, 5, 41, bit_depth=bit_depth, sigma=4.0, cuts=(3,)))
-    run_and_compare(vca, "plain", frames, width=w, height=h, bit_depth=bit_depth, low_pass="downsample",
+    run_and_compare(vca, kernel, frames, width=w, height=h, bit_depth=bit_depth, low_pass="downsample",
                     dump_frames=(0, 3))
 
 
-def test_downsample_reading_hd(vca):
+@pytest.mark.parametrize("kernel", list(KERNELS))
+def test_downsample_reading_hd(vca, kernel):
     frames = frames_list(hd_spec(2, 3))
-    run_and_compare(vca, "plain", frames, width=1920, height=1080, low_pass="downsample", dump_frames=(2,),
+    run_and_compare(vca, kernel, frames, width=1920, height=1080, low_pass="downsample", dump_frames=(2,),
                     block_frames=(0,))
 
 
 def test_downsample_reading_rules(vca):
+    # The halved planes take 16 x 16 / 8 x 8 blocks, which the tensor-core form covers at 8 and 10 bits.
     an = vca.Analyzer(640, 352, 8, 32, "downsample")
+    assert an.kernel == vca.VCA_KERNEL_TC
+    an.close()
+    an = vca.Analyzer(640, 352, 12, 32, "downsample")
     assert an.kernel == vca.VCA_KERNEL_PLAIN
     an.close()
-    for kw in ({"block_size": 16}, {"kernel": vca.VCA_KERNEL_TC}):
-        args = dict(block_size=32, kernel=vca.VCA_KERNEL_AUTO)
-        args.update(kw)
-        with pytest.raises(vca.VcaError) as ei:
-            vca.Analyzer(640, 352, 8, args["block_size"], "downsample", kernel=args["kernel"])
-        assert ei.value.status == vca.VCA_E_UNSUPPORTED
+    with pytest.raises(vca.VcaError) as ei:
+        vca.Analyzer(640, 352, 8, 16, "downsample")
+    assert ei.value.status == vca.VCA_E_UNSUPPORTED
 
 
 # Input variants: 8 x 8 blocks (4 x 4 chroma), 12-bit samples, 4:4:4 chroma (CUDA-core form).
