@@ -450,6 +450,7 @@ def run_extras(args, an, y, u, v, frames, stream, kern, lp, device):
         variants = {}
         lp_name = {False: "full", True: "lowpass", "downsample": "downsample"}
         for (bs, vlp, vk) in ((32, True, vca.VCA_KERNEL_PLAIN), (32, False, kern), (16, True, kern), (16, False, kern),
+                              (16, True, vca.VCA_KERNEL_PLAIN), (16, False, vca.VCA_KERNEL_PLAIN),
                               (32, False, vca.VCA_KERNEL_PLAIN), (32, "downsample", vca.VCA_KERNEL_AUTO)):
             try:
                 a2 = vca.Analyzer(W, H, 8, bs, vlp, kernel=vk, max_batch=args.frames, stream=stream.cuda_stream)
@@ -475,6 +476,17 @@ def run_extras(args, an, y, u, v, frames, stream, kern, lp, device):
                               "hbm_frac_of_measured": gbs / load_peaks()[0]}
             a2.close()
         del y10, u10, v10
+        # 4:2:2 (CUDA cores): half-width, full-height chroma planes -- the two halves of the luma
+        # planes serve as U and V, so a frame reads 2 W H bytes.
+        a2 = vca.Analyzer(W, H, 8, 32, True, kernel=vca.VCA_KERNEL_AUTO, max_batch=args.frames,
+                          stream=stream.cuda_stream, chroma_format=vca.VCA_CHROMA_422)
+        ms, kms, _ = time_pushes(a2, y, y[:, :, : W // 2], y[:, :, W // 2:], max(3, args.steps // 3), 2, stream,
+                                 lambda: None)
+        n = max(3, args.steps // 3) * args.frames
+        gbs = args.frames * 2 * W * H / (kms / 1000.0) / 1e9
+        variants[f"w32_lowpass_422_{ {1: 'plain', 2: 'tc'}[a2.kernel] }"] = {
+            "fps": n / (ms / 1000.0), "kernel_ms_per_launch": kms, "hbm_frac_of_measured": gbs / load_peaks()[0]}
+        a2.close()
         out["variants"] = variants
 
     if want("tune"):
