@@ -522,7 +522,8 @@ def run_extras(args, an, y, u, v, frames, stream, kern, lp, device):
         out["ladder"] = run_ladder(args, stream)
 
     if want("serving"):
-        out["serving"] = run_serving(args)
+        out["serving"] = run_serving(args, policy=0)
+        out["serving_ticks"] = run_serving(args, policy=1)
 
     if want("cpu"):
         # CPU oracle on the host cores (all of them, and one), bounded samples of the same workload;
@@ -639,12 +640,13 @@ def run_ladder(args, stream, distinct=2, ticks=200):
             "timing": "host wall clock around queued ticks, synchronized at both ends; frames device-resident"}
 
 
-def run_serving(args, n_channels=64, distinct=4, capacity_s=3.0, poisson_s=6.0, seed=5):
+def run_serving(args, n_channels=64, distinct=4, capacity_s=3.0, poisson_s=6.0, seed=5, policy=0):
     """Serving loop: 64 live channels (frame size uniform over the six ladder resolutions, 8/10-bit
     mix, 2-second segments at 30 or 60 fps = 60 or 120 frames), segments copied from device
-    buffers into the server's rings (standing in for a decoder) and analysed by continuous
-    batching.  First the capacity (segments/s with every channel submitting back to back), then
-    Poisson arrivals per channel at 0.8 x capacity in total; latency = features ready - arrival."""
+    buffers into the server's rings (standing in for a decoder) and analysed under the server's
+    policy (0: each landed segment one multi-frame work item; 1: frame-interleaved batched ticks).
+    First the capacity (segments/s with every channel submitting back to back), then Poisson
+    arrivals per channel at 0.8 x capacity in total; latency = features ready - arrival."""
     import numpy as np
     import torch
 
@@ -671,7 +673,7 @@ def run_serving(args, n_channels=64, distinct=4, capacity_s=3.0, poisson_s=6.0, 
             planes.append(t[torch.arange(120, device="cuda") % distinct].contiguous())
         src[(w, h, bd)] = planes
     torch.cuda.synchronize()
-    srv = vca.Server()
+    srv = vca.Server(policy=policy)
     ids = [srv.add_channel(w, h, bd, 32, True, max_segment_frames=seg) for (w, h, bd, seg) in chans]
     stats0 = srv.stats()
 
@@ -743,6 +745,8 @@ def run_serving(args, n_channels=64, distinct=4, capacity_s=3.0, poisson_s=6.0, 
                            "max": float(lat.max()), "mean": float(lat.mean())},
             "device_budget_bytes": st["budget_bytes"], "device_used_bytes": st["used_bytes"],
             "launches": st["launches"] - stats0["launches"], "ticks": st["ticks"],
+            "policy": "segments (one multi-frame push per landed segment)" if policy == 0
+            else "ticks (one frame of every channel per batched tick)",
             "mix": "frame size uniform over 640x360..3840x2160, 8/10-bit, 60/120-frame segments; "
                    "segments copied device-to-device into the server's rings inside the measured latency"}
 

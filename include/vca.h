@@ -347,14 +347,21 @@ vca_status vca_batch_debug_wait(vca_batch* b, int64_t wait_limit_ns, int32_t wit
  * A server holds live channels (one analyzer each, h state kept on the device between segments)
  * and runs a scheduler thread of its own.  A channel's producer (a decoder writing into device
  * memory, say) fills one of the channel's two segment slots -- device buffers owned by the
- * server -- and submits it; the scheduler ticks continuously, each tick analysing the next
- * frame of every channel that has a submitted segment (one batched tick, vca_batch_tick), so
- * channels join and leave ticks as segments arrive and finish.  A finished segment appears in
- * vca_server_poll with its submit and feature-ready times (steady clock, ns).
- * Admission is by device memory: a channel costs its analyzer's state plus its two segment slots
+ * server -- and submits it.  The scheduler follows one of two policies (vca_server_set_policy):
+ *   VCA_SERVE_SEGMENTS (default): a segment whose frames have landed is one work item, pushed to
+ *     the channel's own analyzer in vca_push_frames calls of up to 128 frames on the channel's
+ *     own stream, so channels run side by side and a segment waits only for its own frames;
+ *   VCA_SERVE_TICKS: frame-interleaved continuous batching, each tick analysing the next frame
+ *     of every channel that has a submitted segment (one batched tick, vca_batch_tick), so
+ *     channels join and leave ticks as segments arrive and finish; all channels then share
+ *     block size, chroma format and low_pass (the batch rule).
+ * A finished segment appears in vca_server_poll with its submit and feature-ready times (steady
+ * clock, ns).  Admission is by device memory: a channel costs its analyzer's state (which under
+ * the segments policy holds the block values of up to 2 x 128 frames) plus its two segment slots
  * (2 x max_segment_frames frames); vca_server_add_channel gives VCA_E_NOMEM when the budget
- * cannot hold it.  All channels of a server share block size and low_pass (the batch rule). */
+ * cannot hold it.  No counterpart in the paper (its analyzer runs one video at a time). */
 typedef struct vca_server vca_server;
+enum { VCA_SERVE_SEGMENTS = 0, VCA_SERVE_TICKS = 1 };
 
 typedef struct {
   int32_t channel;
@@ -368,7 +375,7 @@ typedef struct {
 } vca_segment_done;
 
 typedef struct {
-  int64_t ticks, frames, launches;
+  int64_t ticks, frames, launches;  /* ticks: batched ticks (VCA_SERVE_TICKS) or pushes (segments) */
   int64_t budget_bytes, used_bytes;
   int32_t channels;
   int32_t pad;
@@ -377,6 +384,9 @@ typedef struct {
 /* device_budget_bytes = 0: 90 % of the device memory free now.  Starts the scheduler thread
  * on the current device. */
 vca_status vca_server_create(size_t device_budget_bytes, vca_server** out);
+/* VCA_SERVE_SEGMENTS or VCA_SERVE_TICKS; before the first vca_server_add_channel (VCA_E_STATE
+ * after it), VCA_E_ARG for any other value. */
+vca_status vca_server_set_policy(vca_server* s, int32_t policy);
 /* Admits a channel (cfg as for vca_open; max_batch is ignored) whose segments hold up to
  * max_segment_frames frames; *id receives its number. */
 vca_status vca_server_add_channel(vca_server* s, const vca_config* cfg, int32_t max_segment_frames, int32_t* id);

@@ -1,9 +1,14 @@
 // Serving runtime on top of the analyzer and batch API (include/vca.h): live channels submit
-// segments of frames that already sit in the server's device memory; a scheduler thread runs
-// continuous batching -- every tick takes the next frame of every channel that has a segment in
-// progress and analyses them together (one batched tick: Section 2 of the paper for each
-// channel's frame), so channels join and leave ticks as their segments arrive and finish.  The h
-// state of every channel stays on the device between segments.
+// segments of frames that already sit in the server's device memory, and a scheduler thread
+// analyses them (Section 2 of the paper for every frame) under one of two policies:
+//   segments (default): a segment whose frames have landed is one work item -- its frames go to
+//     the channel's own analyzer in multi-frame pushes (one launch of the block kernel and one of
+//     the reduction per push, the h chain inside the push), on the channel's own stream, so
+//     channels run side by side and a segment waits for nobody's frames but its own;
+//   ticks: frame-interleaved continuous batching -- every tick takes the next frame of every
+//     channel that has a segment in progress and analyses them together (one batched tick), so
+//     channels join and leave ticks as their segments arrive and finish.
+// The h state of every channel stays on the device between segments.
 //
 // Admission is by device memory: a channel costs its analyzer's state plus a two-slot ring of
 // segment buffers in HBM (a producer, e.g. a decoder, fills one slot while the other is being
@@ -33,6 +38,9 @@ int64_t now_ns() {
 }
 
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Most frames of one push under the segments policy (longer segments take several pushes).
+constexpr int kPushFrames = 128;
 
 vca_status sfail(vca_status s, const char* fmt, ...) {
   char buf[512];
@@ -75,6 +83,7 @@ struct Channel {
 
 struct vca_server {
   int device = 0;
+  int policy = VCA_SERVE_SEGMENTS;
   size_t budget = 0;
   size_t used = 0;
   std::deque<Channel> ch;    // references stay valid as channels are added
@@ -98,14 +107,24 @@ struct vca_server {
 namespace {
 
 // Device bytes of an analyzer of this configuration (the allocations vca_open makes for
-// max_batch = 1), rounded up generously for allocator granularity.
+// c.max_batch frames per push), rounded up generously for allocator granularity.
 size_t analyzer_cost(const vca_config& c, int64_t C) {
   const size_t w = c.block_size, nc = c.chroma_format == VCA_CHROMA_444 ? w : w / 2;
-  size_t b = round_up(w * w + nc * nc + 4 * (w * w + nc * nc), 4096);
-  b += round_up(2 * 6 * (size_t)C * 4, 4096);   // block values, 1 + 1 frames
-  b += 2 * round_up((size_t)C * 4, 4096);        // previous-frame luma energies
-  b += 4 * 4096;                                  // features, reduction scratch, counters, flag
+  const size_t ncv = c.chroma_format == VCA_CHROMA_422 ? w : nc;
+  const size_t mb = (size_t)c.max_batch;
+  size_t b = round_up(w * w + nc * nc + 4 * (w * w + ncv * nc), 4096);
+  b += round_up((2 * mb + 1) * 6 * (size_t)C * 4, 4096);  // block values: two push buffers + a dump slot
+  b += 2 * round_up((size_t)C * 4, 4096);                  // previous-frame luma energies
+  b += round_up(vca::reduce_partials_bytes((int)mb), 4096) + round_up(mb * 4, 4096);  // reduction scratch
+  b += 4 * 4096;                                            // features, flag
   return b;
+}
+
+// Chroma plane rows and columns of a configuration.
+void chroma_size(const vca_config& c, int* cw, int* ch) {
+  const bool full = c.chroma_format == VCA_CHROMA_444, c422 = c.chroma_format == VCA_CHROMA_422;
+  *cw = full ? c.width : c.width / 2;
+  *ch = full || c422 ? c.height : c.height / 2;
 }
 
 // Moves segments whose last frame's features have arrived to the completion queue.
@@ -152,11 +171,80 @@ void finish_segments(vca_server* s, bool blocking) {
   }
 }
 
+// Segments policy: every channel whose oldest segment has landed gets it pushed as one work item
+// (pushes of up to kPushFrames frames).  Returns false when the scheduler must stop.
+bool push_landed_segments(vca_server* s, bool* pushed) {
+  size_t n;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    n = s->ch.size();
+  }
+  for (size_t i = 0; i < n; ++i) {
+    Channel* cp;
+    Segment g;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      cp = &s->ch[i];
+      if (!cp->live || cp->queue.empty()) continue;
+      g = cp->queue.front();
+      if (g.ready) {
+        cudaError_t q = cudaEventQuery(g.ready);
+        if (q == cudaErrorNotReady) continue;
+        cudaGetLastError();
+      }
+    }
+    Channel& c = *cp;
+    const uint8_t* base = c.ring + (size_t)g.slot * c.slot_bytes;
+    vca_status st = VCA_OK;
+    int pushes = 0;
+    for (int f = 0; f < g.n && st == VCA_OK; f += kPushFrames, ++pushes) {
+      const int k = g.n - f < kPushFrames ? g.n - f : kPushFrames;
+      std::lock_guard<std::mutex> le(s->eng);
+      st = vca_push_frames(c.an, base + (size_t)f * c.ystride, base + c.off_u + (size_t)f * c.cstride,
+                           base + c.off_v + (size_t)f * c.cstride, c.pitch_y, c.pitch_uv, (int64_t)c.ystride,
+                           (int64_t)c.cstride, k, 1);
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (st != VCA_OK) {
+      s->worker_status = st;
+      snprintf(s->worker_error, sizeof s->worker_error, "%s", vca_last_error());
+      return false;
+    }
+    g.first_frame = c.frames_queued;
+    g.next = g.n;
+    c.frames_queued += g.n;
+    c.finishing.push_back(g);
+    c.queue.pop_front();
+    s->ticks += pushes;
+    s->frames += g.n;
+    *pushed = true;
+  }
+  return true;
+}
+
 void worker_main(vca_server* s) {
   cudaSetDevice(s->device);
   std::vector<vca_frame_ref> refs;
   std::vector<Channel*> active;
   for (;;) {
+    if (s->policy == VCA_SERVE_SEGMENTS) {
+      {
+        std::unique_lock<std::mutex> lk(s->mu);
+        auto has_work = [&] {
+          if (s->stop) return true;
+          for (auto& c : s->ch)
+            if (c.live && (!c.queue.empty() || !c.finishing.empty())) return true;
+          return false;
+        };
+        s->cv.wait_for(lk, std::chrono::milliseconds(50), has_work);
+        if (s->stop) break;
+      }
+      bool pushed = false;
+      if (!push_landed_segments(s, &pushed)) break;
+      finish_segments(s, false);
+      if (!pushed) std::this_thread::sleep_for(std::chrono::microseconds(20));
+      continue;
+    }
     bool rebuild = false;
     {
       std::unique_lock<std::mutex> lk(s->mu);
@@ -309,10 +397,16 @@ vca_status vca_server_add_channel(vca_server* s, const vca_config* cfg, int32_t 
   vca_status st = vca_block_count(cfg, &bx, &by);
   if (st != VCA_OK) return st;
   vca_config c = *cfg;
-  c.max_batch = 1;
+  int policy;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    policy = s->policy;
+  }
+  // Ticks analyse one frame per channel; segments push up to kPushFrames frames at a time.
+  c.max_batch = policy == VCA_SERVE_TICKS ? 1 : (max_segment_frames < kPushFrames ? max_segment_frames : kPushFrames);
   const int bps = c.bit_depth > 8 ? 2 : 1;
-  const bool full_chroma = c.chroma_format == VCA_CHROMA_444;
-  const int cw = full_chroma ? c.width : c.width / 2, chh = full_chroma ? c.height : c.height / 2;
+  int cw, chh;
+  chroma_size(c, &cw, &chh);
   const int64_t py = (int64_t)round_up((size_t)c.width * bps, 256), pc = (int64_t)round_up((size_t)cw * bps, 256);
   const size_t ystride = (size_t)py * c.height, cstride = (size_t)pc * chh;
   const size_t off_u = round_up(ystride * max_segment_frames, 256);
@@ -355,7 +449,7 @@ vca_status vca_server_add_channel(vca_server* s, const vca_config* cfg, int32_t 
     ch.live = true;
     s->ch.push_back(std::move(ch));
     *id = s->ch.back().id;
-    s->rebuild = true;
+    s->rebuild = s->policy == VCA_SERVE_TICKS;
   }
   s->cv.notify_all();
   return VCA_OK;
@@ -444,11 +538,12 @@ vca_status vca_server_submit_frames(vca_server* s, int32_t id, const vca_frame_r
   }
   const Channel& c = *cp;
   const int bps = c.cfg.bit_depth > 8 ? 2 : 1;
-  const bool full_chroma = c.cfg.chroma_format == VCA_CHROMA_444;
-  const size_t wy = (size_t)c.cfg.width * bps, wc = (size_t)(full_chroma ? c.cfg.width : c.cfg.width / 2) * bps;
+  int cw, hc;
+  chroma_size(c.cfg, &cw, &hc);
+  const size_t wy = (size_t)c.cfg.width * bps, wc = (size_t)cw * bps;
   if (frame0->pitch_y < (int64_t)wy || frame0->pitch_uv < (int64_t)wc) return sfail(VCA_E_ARG, "pitch smaller than a row");
   uint8_t* dst = c.ring + (size_t)slot * c.slot_bytes;
-  const int h = c.cfg.height, hc = full_chroma ? c.cfg.height : c.cfg.height / 2;
+  const int h = c.cfg.height;
   cudaError_t e = cudaSuccess;
   if (ready_event) e = cudaStreamWaitEvent(s->copy_stream, (cudaEvent_t)ready_event, 0);
   // Frames stacked without gaps (frame stride = pitch x rows) copy as one 2-D copy per plane.
@@ -530,8 +625,21 @@ vca_status vca_server_stats(vca_server* s, vca_server_stats_t* st) {
   {
     std::lock_guard<std::mutex> le(s->eng);
     if (s->batch) vca_batch_launch_count(s->batch, &l);
+    for (auto& c : s->ch) {  // the channels' own pushes (segments policy)
+      int64_t x = 0;
+      if (c.live && c.an && vca_launch_count(c.an, &x) == VCA_OK) l += x;
+    }
   }
   st->launches = s->launches_retired + l;
+  return VCA_OK;
+}
+
+vca_status vca_server_set_policy(vca_server* s, int32_t policy) {
+  if (!s) return sfail(VCA_E_ARG, "server is NULL");
+  if (policy != VCA_SERVE_SEGMENTS && policy != VCA_SERVE_TICKS) return sfail(VCA_E_ARG, "unknown policy %d", policy);
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (!s->ch.empty()) return sfail(VCA_E_STATE, "the policy is set before the first channel is added");
+  s->policy = policy;
   return VCA_OK;
 }
 

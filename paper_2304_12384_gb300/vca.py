@@ -30,6 +30,7 @@ VCA_LOWPASS_DOWNSAMPLE = 2
 VCA_CHROMA_420 = 0
 VCA_CHROMA_444 = 1
 VCA_CHROMA_422 = 2
+VCA_SERVE_SEGMENTS, VCA_SERVE_TICKS = 0, 1
 VCA_KERNEL_AUTO = 0
 VCA_KERNEL_PLAIN = 1
 VCA_KERNEL_TC = 2
@@ -142,6 +143,7 @@ _PROTOS = {
     "vca_check_dct_matrix": (_I32, _I32, _P),
     "vca_batch_destroy": (_P,),
     "vca_server_create": (ctypes.c_size_t, ctypes.POINTER(_P)),
+    "vca_server_set_policy": (_P, ctypes.c_int32),
     "vca_server_add_channel": (_P, ctypes.POINTER(VcaConfig), _I32, ctypes.POINTER(_I32)),
     "vca_server_segment_buffer": (_P, _I32, _I32, ctypes.POINTER(VcaFrameRef), ctypes.POINTER(_I64),
                                   ctypes.POINTER(_I64)),
@@ -269,6 +271,10 @@ def vca_tune_save(path: str) -> None:
 
 def vca_tune_load(path: str) -> None:
     _check(lib().vca_tune_load(os.fsencode(path)))
+
+
+def vca_server_set_policy(server: int, policy: int) -> None:
+    _check(lib().vca_server_set_policy(_P(server), policy))
 
 
 def vca_batch_create(handles) -> int:
@@ -606,10 +612,12 @@ class Server:
     """Serving runtime: live channels, segment submission, continuous batching on a native
     scheduler thread, admission by a device-memory budget."""
 
-    def __init__(self, device_budget_bytes=0):
+    def __init__(self, device_budget_bytes=0, policy=None):
         h = _P()
         _check(lib().vca_server_create(device_budget_bytes, ctypes.byref(h)))
         self.handle = h.value
+        if policy is not None:
+            _check(lib().vca_server_set_policy(_P(self.handle), policy))
 
     def add_channel(self, width, height, bit_depth=8, block_size=32, low_pass=True, max_segment_frames=120,
                     pad_mode=VCA_PAD_REPLICATE, chroma_format=VCA_CHROMA_420) -> int:
