@@ -394,6 +394,8 @@ __device__ __forceinline__ void epilogue1(uint32_t td1, uint32_t a2hi, uint32_t 
   using P = PC<Nb, LP>;
   constexpr int CPG = P::NK / 8;  // 8-column chunks per group
   constexpr int S = E1Offs<Nb, LP>::S;
+  const uint64_t s1inv2 = f2pack(__float_as_uint(s1inv), __float_as_uint(s1inv));
+  const uint64_t kT1x2 = f2pack(__float_as_uint(kT1), __float_as_uint(kT1));
   uint32_t buf[2][8];
   tmem_ld<8>(td1, buf[0]);
 #pragma unroll
@@ -404,9 +406,11 @@ __device__ __forceinline__ void epilogue1(uint32_t td1, uint32_t a2hi, uint32_t 
     uint32_t hi[4], lw[4];
 #pragma unroll
     for (int k = 0; k < 8; k += 2) {
-      // D1 already holds T' = c_k + sum (the accumulators were pre-set), an exact integer.
-      const uint32_t za = __float_as_uint(__fmaf_rd(__uint_as_float(acc[k]), s1inv, kT1));
-      const uint32_t zb = __float_as_uint(__fmaf_rd(__uint_as_float(acc[k + 1]), s1inv, kT1));
+      // D1 already holds T' = c_k + sum (the accumulators were pre-set), an exact integer; two
+      // columns per packed round-down FMA.
+      float fa, fb;
+      f2unpack(f2fma_rm(f2pack(acc[k], acc[k + 1]), s1inv2, kT1x2), fa, fb);
+      const uint32_t za = __float_as_uint(fa), zb = __float_as_uint(fb);
       lw[k / 2] = prmt(za, zb, 0x6420);
       hi[k / 2] = prmt(za, zb, 0x6521);
     }
@@ -431,6 +435,10 @@ __device__ __forceinline__ void epilogue2(const uint32_t (&td2)[2], int lane, co
   constexpr int CPJ = NK / 8;  // 8-column chunks per job
   constexpr int S = 2 * CPJ;
   const int v = lane % NK;
+  const uint64_t k256 = f2pack(__float_as_uint(0.00390625f), __float_as_uint(0.00390625f));
+  const uint64_t einv2 = f2pack(__float_as_uint(einv), __float_as_uint(einv));
+  const uint64_t c22 = f2pack(__float_as_uint(c2), __float_as_uint(c2));
+  const uint64_t mK1 = f2pack(__float_as_uint(-kK1), __float_as_uint(-kK1));
   uint32_t bh[2][8], bl[2][8];
   tmem_ld<8>(td2[0], bh[0]);
   tmem_ld<8>(td2[0] + LO, bl[0]);
@@ -445,13 +453,20 @@ __device__ __forceinline__ void epilogue2(const uint32_t (&td2)[2], int lane, co
       tmem_ld<8>(t1 + LO, bl[(st + 1) & 1]);
     }
 #pragma unroll
-    for (int uu = 0; uu < 8; ++uu) {
-      const int u = h0 + uu;
-      const float w = __fmaf_rd(__uint_as_float(bl[st & 1][uu]), 0.00390625f, __uint_as_float(bh[st & 1][uu]));
-      const float z = __fmaf_rd(w, einv, c2) - kK1;
-      if (u == 0) z00 = z;
-      if (DUMP && zd[j]) zd[j][u * NK + v] = (int16_t)z;
-      H = fmaf(fabsf(z), wts[u], H);
+    for (int uu = 0; uu < 8; uu += 2) {
+      // Two rows u per packed instruction: w = lo/256 + hi and Z = floor(w 2^-(s2-8)) (round-down
+      // FMAs), then the FMA chain of H in increasing u.
+      const uint64_t w2 = f2fma_rm(f2pack(bl[st & 1][uu], bl[st & 1][uu + 1]), k256,
+                                   f2pack(bh[st & 1][uu], bh[st & 1][uu + 1]));
+      float z[2];
+      f2unpack(f2add(f2fma_rm(w2, einv2, c22), mK1), z[0], z[1]);
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int u = h0 + uu + e;
+        if (u == 0) z00 = z[e];
+        if (DUMP && zd[j]) zd[j][u * NK + v] = (int16_t)z[e];
+        H = fmaf(fabsf(z[e]), wts[u], H);
+      }
     }
     if (j == 0 && h0 + 8 == NK) {  // job 0 complete
       H0 = H;
@@ -496,6 +511,10 @@ __device__ __forceinline__ void epilogue2_sub(const uint32_t (&td2)[2], int lane
   constexpr int S = 2 * CPJ;
   const int vp = lane % NK;
   const int v = vp % G;
+  const uint64_t k256 = f2pack(__float_as_uint(0.00390625f), __float_as_uint(0.00390625f));
+  const uint64_t einv2 = f2pack(__float_as_uint(einv), __float_as_uint(einv));
+  const uint64_t c22 = f2pack(__float_as_uint(c2), __float_as_uint(c2));
+  const uint64_t mK1 = f2pack(__float_as_uint(-kK1), __float_as_uint(-kK1));
   uint32_t bh[2][8], bl[2][8];
   tmem_ld<8>(td2[0], bh[0]);
   tmem_ld<8>(td2[0] + LO, bl[0]);
@@ -510,20 +529,26 @@ __device__ __forceinline__ void epilogue2_sub(const uint32_t (&td2)[2], int lane
       tmem_ld<8>(t1 + LO, bl[(st + 1) & 1]);
     }
 #pragma unroll
-    for (int uu = 0; uu < 8; ++uu) {
-      const int up = h0 + uu;
-      const float w = __fmaf_rd(__uint_as_float(bl[st & 1][uu]), 0.00390625f, __uint_as_float(bh[st & 1][uu]));
-      const float z = __fmaf_rd(w, einv, c2) - kK1;
-      if (up == 0) zt[j] = z;
-      if (up == G) zb[j] = z;
-      if (DUMP && zd[j] && sb[j].x >= 0) {
-        const int bx = 2 * sb[j].x + vp / G, by = 2 * sb[j].y + up / G;
-        if (bx < nbx && by < nby) zd[j][((int64_t)by * nbx + bx) * G * G + (up % G) * G + v] = (int16_t)z;
+    for (int uu = 0; uu < 8; uu += 2) {
+      const uint64_t w2 = f2fma_rm(f2pack(bl[st & 1][uu], bl[st & 1][uu + 1]), k256,
+                                   f2pack(bh[st & 1][uu], bh[st & 1][uu + 1]));
+      float zz[2];
+      f2unpack(f2add(f2fma_rm(w2, einv2, c22), mK1), zz[0], zz[1]);
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int up = h0 + uu + e;
+        const float z = zz[e];
+        if (up == 0) zt[j] = z;
+        if (up == G) zb[j] = z;
+        if (DUMP && zd[j] && sb[j].x >= 0) {
+          const int bx = 2 * sb[j].x + vp / G, by = 2 * sb[j].y + up / G;
+          if (bx < nbx && by < nby) zd[j][((int64_t)by * nbx + bx) * G * G + (up % G) * G + v] = (int16_t)z;
+        }
+        if (up < G)
+          Ht[j] = fmaf(fabsf(z), wts[up], Ht[j]);
+        else
+          Hb[j] = fmaf(fabsf(z), wts[up - G], Hb[j]);
       }
-      if (up < G)
-        Ht[j] = fmaf(fabsf(z), wts[up], Ht[j]);
-      else
-        Hb[j] = fmaf(fabsf(z), wts[up - G], Hb[j]);
     }
   }
   // Four trees in one: at offset G/2 the lower half of the group goes on with job 0 (top and
