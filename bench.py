@@ -407,10 +407,10 @@ def run_extras(args, an, y, u, v, frames, stream, kern, lp, device):
     from paper_2304_12384_gb300 import vca
 
     out = {}
-    chosen = set(args.extras.split(","))
+    wanted = frozenset(args.extras.split(","))
 
     def want(name):
-        return "all" in chosen or name in chosen
+        return "all" in wanted or name in wanted
 
     if want("latency"):
         # Per-frame latency: one device-resident frame per push, features read back (blocking).
@@ -494,11 +494,11 @@ def run_extras(args, an, y, u, v, frames, stream, kern, lp, device):
         # candidate's analysis time per frame, the chosen shape and its gain over the default one.
         vca.vca_tune_clear()
         cfg = vca._config(W, H, 8, args.block_size, lp)
-        chosen, cands = vca.vca_autotune(cfg, y[:16], u[:16], v[:16], reps=5, stream=stream.cuda_stream)
+        best, cands = vca.vca_autotune(cfg, y[:16], u[:16], v[:16], reps=5, stream=stream.cuda_stream)
         default = [c for c in cands if c["kernel"] == 2 and c["tc_ctas"] == 0] or \
                   [c for c in cands if c["kernel"] == 1 and c["plain_warps"] == 4]
-        out["tune"] = {"chosen": chosen, "candidates": cands,
-                       "gain_over_default": default[0]["ms_per_frame"] / chosen["ms_per_frame"],
+        out["tune"] = {"chosen": best, "candidates": cands,
+                       "gain_over_default": default[0]["ms_per_frame"] / best["ms_per_frame"],
                        "note": "vca_autotune on 16 of the step's frames; the bench step itself runs the default shape"}
         vca.vca_tune_clear()
 
