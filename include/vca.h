@@ -240,11 +240,12 @@ typedef struct {
 } vca_frame_ref;
 
 /* Groups n analyzers (1 .. 65535, distinct, none already in a batch).  Waits for the analyzers'
- * earlier work and captures two tick graphs on a stream of its own.  If every analyzer runs the
- * tensor-core kernel and n <= 64, a tick analyses them with the persistent tensor-core kernel:
- * one launch for the 8-bit members and one for the 10-bit members, side by side on forked
- * branches of the tick graph with the device's SMs split between them in proportion to their
- * tiles.  The tensor maps of a tick's frames are encoded on the host; each analyzer keeps those
+ * earlier work and builds two tick graphs on a stream of its own.  If every analyzer runs the
+ * tensor-core kernel (with the same DCT matrices), a tick analyses them with the persistent
+ * tensor-core kernel: the 8-bit members and the 10-bit members on two branches of the tick
+ * graph, side by side with the device's SMs split between them in proportion to their tiles,
+ * each branch one launch per 64 members (one after another), then one reduction launch per 64
+ * members.  The tensor maps of a tick's frames are encoded on the host; each analyzer keeps those
  * of its last 8 distinct frames (by plane pointers and pitches), so frames ticked from a ring of
  * up to 8 buffers per channel are encoded once.  Otherwise a tick is one launch of the batched
  * CUDA-core kernel, whose CTA map is built here.  VCA_E_ARG for mismatched devices, block sizes

@@ -146,14 +146,15 @@ struct vca_analyzer {
   int64_t seq_nh = 0;
 };
 
-// A batch of analyzers ticked together: one frame each per tick, analysed by one launch of the
-// batched tensor-core kernel (every member on the tensor-core kernel, at most
-// tc_batch_max_members()) or of the batched plain kernel, and one launch of the batched
-// reduction, replayed from a CUDA graph.  A tensor-core batch passes every per-tick argument as
-// kernel parameters, replaced in the graph's kernel nodes each tick (the analysis launches' member
-// tables and tensor maps, the reduction's arguments), and its reduction writes the features (and
-// the analysis timeout flag beside them) straight into mapped pinned host memory, so its graph
-// is the analysis launches and the reduction, nothing else.  A plain batch's per-tick arguments
+// A batch of analyzers ticked together: one frame each per tick, analysed by the batched
+// tensor-core kernel (every member on the tensor-core kernel: one launch per sample size and
+// chunk of up to tc_batch_max_members() members) or by one launch of the batched plain kernel,
+// then the batched reduction, replayed from a CUDA graph.  A tensor-core batch passes every
+// per-tick argument as kernel parameters, replaced in the graph's kernel nodes each tick (the
+// analysis launches' member tables and tensor maps, the reduction's arguments), and its reduction
+// writes the features (and the analysis timeout flag beside them) straight into mapped pinned
+// host memory, so its graph is the analysis launches and the reductions, nothing else; it is
+// built node by node.  A plain batch's per-tick arguments
 // live in pinned host memory that a copy node of the graph uploads, and a copy node reads the
 // features back.  Two graphs alternate so that a tick's arguments and results can be in use
 // while the previous tick runs.
@@ -166,19 +167,25 @@ struct vca_batch {
   int ncv = 16;
   bool low_pass = false;
   bool tc = false;                 // analysis on the tensor-core kernel
-  // Tensor-core members are launched in one group per sample size (8-bit samples in bytes,
-  // 10-bit in 16-bit words); two groups run as two launches on forked streams of the graph.
-  int tc_groups = 1;
-  int tc_gbps[2] = {1, 2};
+  // Tensor-core launches: one per sample size (8-bit samples in bytes, 10-bit in 16-bit words)
+  // and chunk of up to tc_batch_max_members() members.  The sample sizes are two branches of the
+  // graph that run side by side on a split of the SMs, each branch's chunks one after another.
+  struct TcLaunch {
+    int bps = 1;
+    int branch = 0;
+    std::vector<uint8_t> params;            // the launch's parameter block (member table, tensor maps)
+    std::vector<vca::TcBatchFrame> frames;  // this tick's frames of its members
+    cudaGraphNode_t node[2] = {};           // its node in each graph
+  };
+  std::vector<TcLaunch> tcl;
+  std::vector<int> tcl_of;  // per member: its launch
+  int branches = 1;
+  int branch_bps[2] = {1, 2};
   float w16 = 1.15f;  // a tile of 16-bit words against a byte tile, when the SMs are split
   long long dbg_wait_ns = 0;  // failure-path test hook (vca_batch_debug_wait)
   int dbg_withhold = -1;
   int sms = 1;                     // SMs of the device: the CTAs of a tick's tensor-core launches
-  std::vector<uint8_t> tc_params[2];  // per group: the launch's parameter block (member table, tensor maps)
-  cudaGraphNode_t tc_node[2][2] = {};  // per graph and group: the tensor-core launch's node
   cudaStream_t stream = nullptr;
-  cudaStream_t stream2 = nullptr;  // the second group's branch while capturing
-  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   vca::BatchCta* d_map = nullptr;
   int n_cta = 0;
   size_t ma_bytes = 0, desc_bytes = 0;
@@ -186,9 +193,10 @@ struct vca_batch {
   uint8_t* h_desc[2] = {nullptr, nullptr};
   int* d_err = nullptr;            // the tensor-core kernel's wait-timeout flag
   int* h_err = nullptr;            // pinned, one per graph
-  vca::ReduceBatchParams* red_params = nullptr;  // tensor-core batches: the reduction's parameters
-  cudaGraphNode_t red_node[2] = {};              // and its node in each graph
-  std::vector<vca::TcBatchFrame> tc_frames[2];
+  // Tensor-core batches: the reduction's parameters, one launch per chunk of up to
+  // kMaxBatchMembers members, and their nodes in each graph.
+  std::vector<vca::ReduceBatchParams*> red;
+  std::vector<cudaGraphNode_t> red_node[2];
   std::vector<vca::TcMapCache*> tc_maps;  // per member: tensor maps of its recent frames
   double* d_feats = nullptr;       // CUDA-core batches: n x FEAT_STRIDE
   double* h_feats[2] = {nullptr, nullptr};  // pinned, per graph (tensor-core batches: mapped, + flag row)
@@ -564,14 +572,11 @@ void destroy_batch(vca_batch* b) {
   cudaFree(b->d_desc);
   cudaFree(b->d_err);
   if (b->h_err) cudaFreeHost(b->h_err);
-  delete b->red_params;
+  for (vca::ReduceBatchParams* r : b->red) delete r;
   cudaFree(b->d_feats);
   cudaFree(b->d_partials);
   cudaFree(b->d_counters);
   if (b->stream) cudaStreamDestroy(b->stream);
-  if (b->stream2) cudaStreamDestroy(b->stream2);
-  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
-  if (b->join_ev) cudaEventDestroy(b->join_ev);
   if (prev_dev >= 0) cudaSetDevice(prev_dev);
   delete b;
 }
@@ -582,56 +587,51 @@ size_t feats_bytes(const vca_batch* b) {
   return (size_t)(b->n + (b->tc ? 1 : 0)) * vca::FEAT_STRIDE * sizeof(double);
 }
 
-// Captures tick graph k: analyse and reduce (CUDA-core batches: upload the arguments first and
-// read the features back after).
+// Builds tick graph k.  Tensor-core batches: node by node -- each branch's analysis launches one
+// after another, then the reductions, which depend on both branches.  CUDA-core batches: captured
+// -- upload the arguments, analyse, reduce, read the features back.
 cudaError_t build_tick_graph(vca_batch* b, int k) {
+  if (b->tc) {
+    cudaError_t e = cudaGraphCreate(&b->graph[k], 0);
+    cudaGraphNode_t tail[2] = {nullptr, nullptr};
+    for (auto& L : b->tcl) {
+      if (e != cudaSuccess) return e;
+      void* args[1] = {L.params.data()};
+      cudaKernelNodeParams kp;
+      e = vca::tc_batch_node_params(b->w, L.bps, b->low_pass, b->sms, args, &kp);
+      if (e != cudaSuccess) return e;
+      const cudaGraphNode_t dep = tail[L.branch];
+      e = cudaGraphAddKernelNode(&L.node[k], b->graph[k], dep ? &dep : nullptr, dep ? 1 : 0, &kp);
+      tail[L.branch] = L.node[k];
+    }
+    std::vector<cudaGraphNode_t> deps;
+    for (cudaGraphNode_t t : tail)
+      if (t) deps.push_back(t);
+    b->red_node[k].assign(b->red.size(), nullptr);
+    for (size_t j = 0; e == cudaSuccess && j < b->red.size(); ++j) {
+      void* args[1] = {b->red[j]};
+      cudaKernelNodeParams kp;
+      e = vca::reduce_batch_params_node(b->red[j], args, &kp);
+      if (e == cudaSuccess)
+        e = cudaGraphAddKernelNode(&b->red_node[k][j], b->graph[k], deps.data(), deps.size(), &kp);
+    }
+    if (e != cudaSuccess) return e;
+    return cudaGraphInstantiate(&b->exec[k], b->graph[k], 0);
+  }
   cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
-  cudaError_t e1 = cudaSuccess;
-  if (b->tc) {
-    if (b->tc_groups == 2) {  // fork: the second group on its own branch
-      e1 = cudaEventRecord(b->fork_ev, b->stream);
-      if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(b->stream2, b->fork_ev, 0);
-      if (e1 == cudaSuccess) e1 = vca::launch_tc_batch(b->tc_params[1].data(), b->w, b->tc_gbps[1], b->low_pass, b->stream2);
-      if (e1 == cudaSuccess) e1 = cudaEventRecord(b->join_ev, b->stream2);
-    }
-    if (e1 == cudaSuccess) e1 = vca::launch_tc_batch(b->tc_params[0].data(), b->w, b->tc_gbps[0], b->low_pass, b->stream);
-    if (e1 == cudaSuccess && b->tc_groups == 2) e1 = cudaStreamWaitEvent(b->stream, b->join_ev, 0);
-    if (e1 == cudaSuccess) e1 = vca::launch_reduce_batch_params(*b->red_params, b->stream);
-  } else {
-    e1 = cudaMemcpyAsync(b->d_desc, b->h_desc[k], b->desc_bytes, cudaMemcpyHostToDevice, b->stream);
-    if (e1 == cudaSuccess)
-      e1 = vca::launch_batch_plain(b->d_map, b->n_cta, reinterpret_cast<const vca::BatchMemberArgs*>(b->d_desc),
-                                   b->w, b->nc, b->ncv, b->low_pass, b->stream);
-    if (e1 == cudaSuccess)
-      e1 = vca::launch_reduce_batch(reinterpret_cast<const vca::ReduceArgs*>(b->d_desc + b->ma_bytes), b->n,
-                                    b->red_slices, b->stream);
-  }
-  if (e1 == cudaSuccess && !b->tc)
+  cudaError_t e1 = cudaMemcpyAsync(b->d_desc, b->h_desc[k], b->desc_bytes, cudaMemcpyHostToDevice, b->stream);
+  if (e1 == cudaSuccess)
+    e1 = vca::launch_batch_plain(b->d_map, b->n_cta, reinterpret_cast<const vca::BatchMemberArgs*>(b->d_desc), b->w,
+                                 b->nc, b->ncv, b->low_pass, b->stream);
+  if (e1 == cudaSuccess)
+    e1 = vca::launch_reduce_batch(reinterpret_cast<const vca::ReduceArgs*>(b->d_desc + b->ma_bytes), b->n,
+                                  b->red_slices, b->stream);
+  if (e1 == cudaSuccess)
     e1 = cudaMemcpyAsync(b->h_feats[k], b->d_feats, feats_bytes(b), cudaMemcpyDeviceToHost, b->stream);
   e = cudaStreamEndCapture(b->stream, &b->graph[k]);
   if (e1 != cudaSuccess) return e1;
   if (e != cudaSuccess) return e;
-  if (b->tc) {  // the tensor-core launches and the reduction, whose parameters each tick replaces
-    size_t count = 0;
-    e = cudaGraphGetNodes(b->graph[k], nullptr, &count);
-    std::vector<cudaGraphNode_t> nodes(count);
-    if (e == cudaSuccess && count) e = cudaGraphGetNodes(b->graph[k], nodes.data(), &count);
-    for (size_t i = 0; e == cudaSuccess && i < count; ++i) {
-      cudaGraphNodeType type;
-      e = cudaGraphNodeGetType(nodes[i], &type);
-      if (e != cudaSuccess || type != cudaGraphNodeTypeKernel) continue;
-      cudaKernelNodeParams kp{};
-      e = cudaGraphKernelNodeGetParams(nodes[i], &kp);
-      for (int gi = 0; e == cudaSuccess && gi < b->tc_groups; ++gi)
-        if (kp.func == vca::tc_batch_kernel(b->w, b->tc_gbps[gi], b->low_pass)) b->tc_node[k][gi] = nodes[i];
-      if (e == cudaSuccess && kp.func == vca::reduce_batch_params_kernel()) b->red_node[k] = nodes[i];
-    }
-    if (e != cudaSuccess) return e;
-    for (int gi = 0; gi < b->tc_groups; ++gi)
-      if (!b->tc_node[k][gi]) return cudaErrorGraphExecUpdateFailure;
-    if (!b->red_node[k]) return cudaErrorGraphExecUpdateFailure;
-  }
   return cudaGraphInstantiate(&b->exec[k], b->graph[k], 0);
 }
 
@@ -1102,7 +1102,7 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
   b->nc = members[0]->g.nc;
   b->ncv = members[0]->g.ncv;
   b->low_pass = members[0]->g.low_pass;
-  b->tc = n <= vca::tc_batch_max_members();
+  b->tc = true;
   for (int i = 0; i < n; ++i) {
     const vca_analyzer* a = members[i];
     b->tc = b->tc && a->kernel == VCA_KERNEL_TC;
@@ -1112,8 +1112,27 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
   }
   bool has_bps[3] = {false, false, false};
   for (int i = 0; i < n; ++i) has_bps[members[i]->g.bps] = true;
-  b->tc_groups = has_bps[1] && has_bps[2] ? 2 : 1;
-  if (b->tc_groups == 1) b->tc_gbps[0] = members[0]->g.bps;
+  b->branches = has_bps[1] && has_bps[2] ? 2 : 1;
+  if (b->branches == 1) b->branch_bps[0] = members[0]->g.bps;
+  if (b->tc) {  // each branch's members in chunks of up to tc_batch_max_members(), in member order
+    b->tcl_of.assign(n, -1);
+    const int cap = vca::tc_batch_max_members();
+    for (int br = 0; br < b->branches; ++br) {
+      int cur = -1, count = 0;
+      for (int i = 0; i < n; ++i) {
+        if (members[i]->g.bps != b->branch_bps[br]) continue;
+        if (cur < 0 || count == cap) {
+          b->tcl.emplace_back();
+          cur = (int)b->tcl.size() - 1;
+          b->tcl[cur].bps = b->branch_bps[br];
+          b->tcl[cur].branch = br;
+          count = 0;
+        }
+        b->tcl_of[i] = cur;
+        ++count;
+      }
+    }
+  }
   int64_t max_C = 0;
   for (int i = 0; i < n; ++i) max_C = members[i]->g.C > max_C ? members[i]->g.C : max_C;
   b->red_slices = vca::reduce_batch_slices(max_C);
@@ -1156,7 +1175,10 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
     return fail(VCA_E_ARG, "batch too large");
   }
   b->n_cta = (int)map.size();
-  for (int gi = 0; b->tc && gi < b->tc_groups; ++gi) b->tc_params[gi].assign(vca::tc_batch_params_bytes(), 0);
+  for (auto& L : b->tcl) {
+    L.params.assign(vca::tc_batch_params_bytes(), 0);
+    L.frames.reserve((size_t)vca::tc_batch_max_members());
+  }
   b->ma_bytes = b->tc ? 0 : round_up((size_t)n * sizeof(vca::BatchMemberArgs), 256);
   b->desc_bytes = b->ma_bytes + (size_t)n * sizeof(vca::ReduceArgs);
   BATCH_CUDA(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking), "creating the batch stream");
@@ -1165,21 +1187,14 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
     BATCH_CUDA(cudaMemcpy(b->d_map, map.data(), map.size() * sizeof(vca::BatchCta), cudaMemcpyHostToDevice),
                "uploading the CTA map");
   }
-  for (int gi = 0; b->tc && gi < b->tc_groups; ++gi)
-    BATCH_CUDA(vca::tc_batch_prepare(b->w, b->tc_gbps[gi], b->low_pass), "preparing the tensor-core kernel");
+  for (int br = 0; b->tc && br < b->branches; ++br)
+    BATCH_CUDA(vca::tc_batch_prepare(b->w, b->branch_bps[br], b->low_pass), "preparing the tensor-core kernel");
   BATCH_CUDA(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device), "querying the SM count");
   if (b->sms < 1) b->sms = 1;
-  if (b->tc && b->tc_groups == 2) {
-    BATCH_CUDA(cudaStreamCreateWithFlags(&b->stream2, cudaStreamNonBlocking), "creating the batch's second stream");
-    BATCH_CUDA(cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming), "creating batch events");
-    BATCH_CUDA(cudaEventCreateWithFlags(&b->join_ev, cudaEventDisableTiming), "creating batch events");
-  }
   BATCH_CUDA(cudaMalloc(&b->d_err, sizeof(int)), "allocating the error flag");
   BATCH_CUDA(cudaMemset(b->d_err, 0, sizeof(int)), "clearing the error flag");
   BATCH_CUDA(cudaMallocHost(&b->h_err, 2 * sizeof(int)), "allocating pinned error flags");
   b->h_err[0] = b->h_err[1] = 0;
-  b->tc_frames[0].reserve(n);
-  b->tc_frames[1].reserve(n);
   for (int i = 0; b->tc && i < n; ++i) {
     b->tc_maps.push_back(vca::tc_map_cache_new());
     if (!b->tc_maps.back()) {
@@ -1188,22 +1203,23 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
       return fail(VCA_E_NOMEM, "allocating tensor-map caches");
     }
   }
-  if (b->tc) {
-    b->red_params = new (std::nothrow) vca::ReduceBatchParams();
-    if (!b->red_params) {
+  for (int c0 = 0; b->tc && c0 < n; c0 += vca::kMaxBatchMembers) {
+    vca::ReduceBatchParams* r = new (std::nothrow) vca::ReduceBatchParams();
+    if (!r) {
       destroy_batch(b);
       if (prev_dev >= 0) cudaSetDevice(prev_dev);
       return fail(VCA_E_NOMEM, "host allocation failed");
     }
-  } else {
+    b->red.push_back(r);
+    r->n = std::min(n - c0, vca::kMaxBatchMembers);
+    r->S = b->red_slices;
+    r->err = c0 == 0 ? b->d_err : nullptr;  // the first chunk hands the timeout flag over
+    r->err_out = nullptr;
+  }
+  if (!b->tc) {
     BATCH_CUDA(cudaMalloc(&b->d_desc, b->desc_bytes), "allocating tick arguments");
   }
   if (!b->tc) BATCH_CUDA(cudaMalloc(&b->d_feats, feats_bytes(b)), "allocating features");
-  if (b->tc) {
-    b->red_params->n = n;
-    b->red_params->S = b->red_slices;
-    b->red_params->err = b->d_err;
-  }
   BATCH_CUDA(cudaMalloc(&b->d_partials, vca::reduce_partials_bytes(n)), "allocating reduction scratch");
   BATCH_CUDA(cudaMalloc(&b->d_counters, (size_t)n * sizeof(unsigned int)), "allocating counters");
   BATCH_CUDA(cudaMemset(b->d_counters, 0, (size_t)n * sizeof(unsigned int)), "clearing counters");
@@ -1218,7 +1234,7 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
     if (b->tc) {
       BATCH_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&b->h_feats_dev[k]), b->h_feats[k], 0),
                  "mapping the features");
-      b->red_params->err_out = b->h_feats_dev[k] + (size_t)n * vca::FEAT_STRIDE;
+      b->red[0]->err_out = b->h_feats_dev[k] + (size_t)n * vca::FEAT_STRIDE;
     }
     BATCH_CUDA(cudaEventCreateWithFlags(&b->ev[k], cudaEventDisableTiming), "creating batch events");
     BATCH_CUDA(build_tick_graph(b, k), "capturing the tick graph");
@@ -1244,22 +1260,24 @@ vca_status vca_batch_tick(vca_batch* b, const vca_frame_ref* frames) {
     if (s != VCA_OK) return fail(s, "frame of analyzer %d: %s", i, vca_last_error());
   }
   auto* ma = b->tc ? nullptr : reinterpret_cast<vca::BatchMemberArgs*>(b->h_desc[k]);
-  auto* ra = b->tc ? b->red_params->a : reinterpret_cast<vca::ReduceArgs*>(b->h_desc[k] + b->ma_bytes);
+  auto* ra_plain = b->tc ? nullptr : reinterpret_cast<vca::ReduceArgs*>(b->h_desc[k] + b->ma_bytes);
+  // A member's reduction arguments: its chunk's parameters (tensor-core) or the uploaded array.
+  auto ra = [&](int i) -> vca::ReduceArgs& {
+    return b->tc ? b->red[i / vca::kMaxBatchMembers]->a[i % vca::kMaxBatchMembers] : ra_plain[i];
+  };
   vca_batch::Tick tick;
   tick.k = k;
-  b->tc_frames[0].clear();
-  b->tc_frames[1].clear();
+  for (auto& L : b->tcl) L.frames.clear();
   for (int i = 0; i < b->n; ++i) {
     vca_analyzer* a = b->m[i];
     if (!frames[i].y) {
       if (!b->tc) ma[i].active = 0;
-      ra[i].nframes = 0;
+      ra(i).nframes = 0;
       continue;
     }
     if (b->tc) {
       const vca_frame_ref& f = frames[i];
-      const int gi = b->tc_groups == 2 && a->g.bps == b->tc_gbps[1] ? 1 : 0;
-      b->tc_frames[gi].push_back({&a->g,
+      b->tcl[b->tcl_of[i]].frames.push_back({&a->g,
                               {static_cast<const uint8_t*>(f.y), static_cast<const uint8_t*>(f.u),
                                static_cast<const uint8_t*>(f.v), f.pitch_y, f.pitch_uv, 0, 0},
                               a->d_blockvals, b->tc_maps[i]});
@@ -1269,7 +1287,7 @@ vca_status vca_batch_tick(vca_batch* b, const vca_frame_ref* frames) {
       ma[i].bps = a->g.bps;
       ma[i].active = 1;
     }
-    ra[i] = vca::reduce_args(a->g, 1, a->d_blockvals, a->d_prevH[a->cur_prev], a->has_prev,
+    ra(i) = vca::reduce_args(a->g, 1, a->d_blockvals, a->d_prevH[a->cur_prev], a->has_prev,
                              a->d_prevH[a->cur_prev ^ 1],
                              (b->tc ? b->h_feats_dev[k] : b->d_feats) + (size_t)i * vca::FEAT_STRIDE,
                              b->d_partials + (size_t)i * vca::reduce_partials_bytes(1) / sizeof(unsigned long long),
@@ -1277,21 +1295,22 @@ vca_status vca_batch_tick(vca_batch* b, const vca_frame_ref* frames) {
     tick.members.push_back({i, a->frames_pushed, a->has_prev != 0});
   }
   int grid[2] = {b->sms, b->sms};
-  for (int gi = 0; b->tc && gi < b->tc_groups; ++gi) {
-    cudaError_t e = vca::tc_batch_fill(b->tc_params[gi].data(), b->tc_frames[gi].data(), (int)b->tc_frames[gi].size(),
-                                       b->m[0]->tables, b->d_err, b->dbg_wait_ns, gi == 0 ? b->dbg_withhold : -1);
+  for (size_t li = 0; li < b->tcl.size(); ++li) {
+    auto& L = b->tcl[li];
+    cudaError_t e = vca::tc_batch_fill(L.params.data(), L.frames.data(), (int)L.frames.size(), b->m[0]->tables,
+                                       b->d_err, b->dbg_wait_ns, li == 0 ? b->dbg_withhold : -1);
     if (e != cudaSuccess) return cuda_fail(e, "encoding the tensor maps of a batch tick");
   }
   b->dbg_withhold = -1;  // one tick only
-  if (b->tc && b->tc_groups == 2 && b->sms >= 2) {
+  if (b->tc && b->branches == 2 && b->sms >= 2) {
     // The two sample sizes' launches run side by side on disjoint SMs (a CTA holds a whole SM),
     // the SMs split in proportion to their work: a tile of 16-bit words costs about 1.15 x a tile
     // of bytes.  So the tick pays one pipeline fill and drain instead of two in sequence.  Each
     // share is even: with an odd split one SM pair held a CTA of each launch, and those two CTAs
     // ran 1.6x slower than all the others (measured), which set the tick's time.
-    double w[2];
-    for (int gi = 0; gi < 2; ++gi)
-      w[gi] = vca::tc_batch_items(b->tc_params[gi].data()) * (b->tc_gbps[gi] == 2 ? (double)b->w16 : 1.0);
+    double w[2] = {0.0, 0.0};
+    for (const auto& L : b->tcl)
+      w[L.branch] += vca::tc_batch_items(L.params.data()) * (L.bps == 2 ? (double)b->w16 : 1.0);
     int g0 = w[0] + w[1] > 0.0 ? (int)std::lround(b->sms * w[0] / (w[0] + w[1])) : b->sms / 2;
     g0 = (g0 + 1) & ~1;
     const int lo = b->sms >= 4 ? 2 : 1;  // a launch with no tiles this tick still gets a (full) SM pair
@@ -1299,26 +1318,23 @@ vca_status vca_batch_tick(vca_batch* b, const vca_frame_ref* frames) {
     grid[0] = g0;
     grid[1] = b->sms - g0;
   }
-  for (int gi = 0; b->tc && gi < b->tc_groups; ++gi) {
-    // The graph's launch takes this tick's parameter block (copied by the call) and grid.
-    cudaKernelNodeParams kp{};
-    cudaError_t e = cudaGraphKernelNodeGetParams(b->tc_node[k][gi], &kp);
-    void* args[1] = {b->tc_params[gi].data()};
-    kp.kernelParams = args;
-    kp.extra = nullptr;
-    kp.gridDim = dim3((unsigned)grid[gi]);
-    if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(b->exec[k], b->tc_node[k][gi], &kp);
+  for (auto& L : b->tcl) {
+    // The graph's launch takes this tick's parameter block (copied by the call) and its branch's grid.
+    void* args[1] = {L.params.data()};
+    cudaKernelNodeParams kp;
+    cudaError_t e = vca::tc_batch_node_params(b->w, L.bps, b->low_pass, grid[L.branch], args, &kp);
+    if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(b->exec[k], L.node[k], &kp);
     if (e != cudaSuccess) return cuda_fail(e, "setting the parameters of a batch tick");
   }
   if (b->tc) {
-    b->red_params->err_out = b->h_feats_dev[k] + (size_t)b->n * vca::FEAT_STRIDE;
-    cudaKernelNodeParams kp{};
-    cudaError_t e = cudaGraphKernelNodeGetParams(b->red_node[k], &kp);
-    void* args[1] = {b->red_params};
-    kp.kernelParams = args;
-    kp.extra = nullptr;
-    if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(b->exec[k], b->red_node[k], &kp);
-    if (e != cudaSuccess) return cuda_fail(e, "setting the reduction parameters of a batch tick");
+    b->red[0]->err_out = b->h_feats_dev[k] + (size_t)b->n * vca::FEAT_STRIDE;
+    for (size_t j = 0; j < b->red.size(); ++j) {
+      void* args[1] = {b->red[j]};
+      cudaKernelNodeParams kp;
+      cudaError_t e = vca::reduce_batch_params_node(b->red[j], args, &kp);
+      if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(b->exec[k], b->red_node[k][j], &kp);
+      if (e != cudaSuccess) return cuda_fail(e, "setting the reduction parameters of a batch tick");
+    }
   }
   int prev_dev = -1;
   cudaGetDevice(&prev_dev);
@@ -1338,7 +1354,8 @@ vca_status vca_batch_tick(vca_batch* b, const vca_frame_ref* frames) {
   b->pending.push_back(std::move(tick));
   b->next_k ^= 1;
   b->ticks += 1;
-  b->launches += (b->tc ? b->tc_groups : 1) + 1;  // analysis (one per sample-size group), reduction
+  // analysis (tensor-core: one launch per sample size and chunk), reduction (one per chunk)
+  b->launches += b->tc ? (int64_t)(b->tcl.size() + b->red.size()) : 2;
   return VCA_OK;
 }
 
@@ -1379,7 +1396,7 @@ vca_status vca_batch_autotune(vca_batch* b, const vca_frame_ref* frames, int32_t
                               float* ms_per_tick) {
   if (!b || !frames || reps < 1) return fail(VCA_E_ARG, "vca_batch_autotune: needs a batch, frames and reps >= 1");
   const float cands[] = {1.0f, 1.15f, 1.3f, 1.5f, 1.75f};
-  const bool split = b->tc && b->tc_groups == 2;
+  const bool split = b->tc && b->branches == 2;
   float best_w = b->w16, best_ms = -1.0f;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   VCA_CUDA(cudaEventCreate(&e0), "creating tuning events");

@@ -142,11 +142,11 @@ cudaError_t tc_batch_fill(void* params, const TcBatchFrame* frames, int n, const
 cudaError_t tc_batch_prepare(int w, int bps, bool low_pass);
 // Work items (128x128 luma tiles) of a filled parameter block.
 int tc_batch_items(const void* params);
-// Launches the analysis with the parameter block params (host memory; bps 1 or 2) on one CTA per
-// SM of the device.
-cudaError_t launch_tc_batch(const void* params, int w, int bps, bool low_pass, cudaStream_t s);
 // The kernel a batched launch of this sample size and low_pass runs (to find its graph node).
 const void* tc_batch_kernel(int w, int bps, bool low_pass);
+// Kernel-node parameters of one batched tensor-core launch (its function, grid, block and dynamic
+// shared memory; args[0] points at its parameter block), for a graph built node by node.
+cudaError_t tc_batch_node_params(int w, int bps, bool low_pass, int grid, void** args, cudaKernelNodeParams* kp);
 
 // Exact frame reduction: features of n frames (the block sums exact in 128-bit fixed point, each
 // total rounded once to FP64) and the h state update.  `partials` holds reduce_partials_bytes(max
@@ -169,8 +169,8 @@ cudaError_t launch_reduce_batch(const ReduceArgs* d_args, int n, int slices, cud
 // Slices per frame of a batched reduction whose largest member has max_C blocks per plane.
 int reduce_batch_slices(int64_t max_C);
 
-// The same batched reduction with its arguments as kernel parameters (batches of at most
-// kMaxBatchMembers analyzers), so that a tick's graph needs no upload of them: a[m] as above for
+// The same batched reduction with its arguments as kernel parameters (a chunk of at most
+// kMaxBatchMembers analyzers of a batch), so that a tick's graph needs no upload of them: a[m] as above for
 // m < n, S slices per frame.  The launch also hands the analysis kernel's wait-timeout flag to
 // the host: one thread copies *err into *err_out (as a double, next to the features the tick
 // reads back) and clears *err for the next tick.  err may be null.
@@ -181,9 +181,9 @@ struct ReduceBatchParams {
   int* err;
   double* err_out;
 };
-cudaError_t launch_reduce_batch_params(const ReduceBatchParams& p, cudaStream_t s);
-// The kernel launch_reduce_batch_params runs (to find its graph node).
-const void* reduce_batch_params_kernel();
+// Kernel-node parameters of the batched reduction of p (p.n members x p.S slices; args[0] points
+// at p), for a graph built node by node.
+cudaError_t reduce_batch_params_node(const ReduceBatchParams* p, void** args, cudaKernelNodeParams* kp);
 
 // One CTA of the batched plain kernel: analyzer `member`, plane kind (0 luma, 1 chroma), plane
 // within the kind (chroma: 0 U, 1 V) and block chunk (BPC blocks).

@@ -189,14 +189,17 @@ __global__ void __launch_bounds__(kThreads) reduce_batch_params_kernel_(const __
 
 }  // namespace
 
-cudaError_t launch_reduce_batch_params(const ReduceBatchParams& p, cudaStream_t s) {
-  if (p.n <= 0 || p.n > kMaxBatchMembers) return cudaErrorInvalidValue;
-  if (p.S < 1 || p.S > kMaxSlices) return cudaErrorInvalidValue;
-  reduce_batch_params_kernel_<<<p.n * p.S, kThreads, 0, s>>>(p);
-  return cudaGetLastError();
+cudaError_t reduce_batch_params_node(const ReduceBatchParams* p, void** args, cudaKernelNodeParams* kp) {
+  if (p->n <= 0 || p->n > kMaxBatchMembers || p->S < 1 || p->S > kMaxSlices) return cudaErrorInvalidValue;
+  *kp = cudaKernelNodeParams{};
+  kp->func = (void*)reduce_batch_params_kernel_;
+  kp->gridDim = dim3((unsigned)(p->n * p->S));
+  kp->blockDim = dim3(kThreads);
+  kp->sharedMemBytes = 0;
+  kp->kernelParams = args;
+  kp->extra = nullptr;
+  return cudaSuccess;
 }
-
-const void* reduce_batch_params_kernel() { return (const void*)reduce_batch_params_kernel_; }
 
 size_t reduce_partials_bytes(int max_frames) { return (size_t)max_frames * kMaxSlices * kSums * 16; }
 

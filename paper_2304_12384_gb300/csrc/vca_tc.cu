@@ -1533,12 +1533,6 @@ cudaError_t tc_batch_prepare(int w, int bps, bool low_pass) {
   return launch_batched(unused, 0, w, low_pass, bps, nullptr);
 }
 
-cudaError_t launch_tc_batch(const void* params, int w, int bps, bool low_pass, cudaStream_t s) {
-  if ((bps != 1 && bps != 2) || (w != 32 && w != 16)) return cudaErrorInvalidValue;
-  // The number of items is known from the parameters; CTAs beyond it find no work.
-  return launch_batched(*static_cast<const TcBatchParams*>(params), sm_count(), w, low_pass, bps, s);
-}
-
 template <bool SUB>
 const void* tc_batch_kernel_s(int bps, bool low_pass) {
   if (bps == 1)
@@ -1548,6 +1542,19 @@ const void* tc_batch_kernel_s(int bps, bool low_pass) {
 
 const void* tc_batch_kernel(int w, int bps, bool low_pass) {
   return w == 16 ? tc_batch_kernel_s<true>(bps, low_pass) : tc_batch_kernel_s<false>(bps, low_pass);
+}
+
+cudaError_t tc_batch_node_params(int w, int bps, bool low_pass, int grid, void** args, cudaKernelNodeParams* kp) {
+  const cudaError_t e = tc_batch_prepare(w, bps, low_pass);
+  if (e != cudaSuccess) return e;
+  *kp = cudaKernelNodeParams{};
+  kp->func = const_cast<void*>(tc_batch_kernel(w, bps, low_pass));
+  kp->gridDim = dim3((unsigned)(grid > 0 ? grid : 1));
+  kp->blockDim = dim3(kThreads);
+  kp->sharedMemBytes = bps == 1 ? SmemLay<1>::kSmemBytes : SmemLay<2>::kSmemBytes;
+  kp->kernelParams = args;
+  kp->extra = nullptr;
+  return cudaSuccess;
 }
 
 cudaError_t launch_tc(const Geometry& g, const FramePlanes& fp, int nframes, const DeviceTables& t, float* blockvals,

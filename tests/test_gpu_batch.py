@@ -220,25 +220,47 @@ def test_batch_with_drop_in_matrices(vca):
             s_.close()
 
 
-def test_batch_beyond_the_member_table_runs_on_cuda_cores(vca):
-    # A tensor-core launch holds at most 64 members; a larger batch of tensor-core analyzers takes
-    # the CUDA-core kernel and still matches the oracle.
-    n = 65
-    frames = frames_list(SequenceSpec(64, 64, 2, 95, sigma=4.0))
-    y, u, v = to_device(frames)
-    members = [vca.Analyzer(64, 64, 8, 32, True, max_batch=1) for _ in range(n)]
+def test_batch_beyond_one_member_table_stays_on_tensor_cores(vca):
+    # A tensor-core launch holds at most 64 members: 66 8-bit and 5 10-bit analyzers tick as three
+    # analysis launches (8-bit: 64 + 2 members, one after another; 10-bit: 5, beside them) and two
+    # reduction launches (64 + 7 members), every member matching its single analyzer bit for bit
+    # and the oracle; one member skips a tick.
+    n8, n10 = 66, 5
+    f8 = frames_list(SequenceSpec(64, 64, 3, 95, sigma=4.0))
+    f10 = frames_list(SequenceSpec(64, 64, 3, 96, bit_depth=10, sigma=4.0))
+    d8, d10 = to_device(f8), to_device(f10)
+    members = [vca.Analyzer(64, 64, 8, 32, True, max_batch=1) for _ in range(n8)] + \
+              [vca.Analyzer(64, 64, 10, 32, True, max_batch=1) for _ in range(n10)]
+    single8 = vca.Analyzer(64, 64, 8, 32, True, max_batch=1)
+    single10 = vca.Analyzer(64, 64, 10, 32, True, max_batch=1)
     try:
         assert members[0].kernel == vca.VCA_KERNEL_TC
         with vca.Batch(members) as batch:
-            assert batch.kernel == vca.VCA_KERNEL_PLAIN
-            for t in range(2):
-                batch.tick([(y[t], u[t], v[t])] * n)
-        per, _ = oracle_sequence(frames, oracle_config(members[0]))
-        for i in (0, 31, 64):
-            for t in range(2):
-                assert_features_close(members[i].frame_features(t), per[t], where=f"member {i} frame {t}")
+            assert batch.kernel == vca.VCA_KERNEL_TC
+            for t in range(3):
+                refs = [(d8[0][t], d8[1][t], d8[2][t])] * n8 + [(d10[0][t], d10[1][t], d10[2][t])] * n10
+                if t == 1:
+                    refs[65] = None
+                batch.tick(refs)
+                single8.push(d8[0][t], d8[1][t], d8[2][t])
+                single10.push(d10[0][t], d10[1][t], d10[2][t])
+            batch.sync()
+            assert batch.launches() == 3 * (3 + 2)
+        exp8 = [single8.frame_features(t) for t in range(3)]
+        exp10 = [single10.frame_features(t) for t in range(3)]
+        for i in (0, 1, 63, 64):
+            assert [members[i].frame_features(t) for t in range(3)] == exp8, f"member {i}"
+        for i in range(n8, n8 + n10):
+            assert [members[i].frame_features(t) for t in range(3)] == exp10, f"member {i}"
+        # member 65 skipped tick 1: its second frame is tick 2's frame, with h against tick 0's
+        got = [members[65].frame_features(t) for t in range(2)]
+        assert got[0] == exp8[0] and got[1]["E_Y"] == exp8[2]["E_Y"]
+        for fr, single, lst in ((f8, single8, exp8), (f10, single10, exp10)):
+            per, _ = oracle_sequence(fr, oracle_config(single))
+            for t in range(3):
+                assert_features_close(lst[t], per[t], where=f"frame {t}")
     finally:
-        for a in members:
+        for a in members + [single8, single10]:
             a.close()
 
 
