@@ -135,27 +135,6 @@ __device__ __forceinline__ void tmem_st<32>(uint32_t t, const uint32_t (&v)[32])
       "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31]));
 }
 
-// Stores `first` into the first column and `rest` into the other N-1 columns of this warp's 32 lanes
-// (the same register is repeated in the operand list, so no copies are made).
-template <int N>
-__device__ __forceinline__ void tmem_fill(uint32_t t, uint32_t first, uint32_t rest);
-template <>
-__device__ __forceinline__ void tmem_fill<8>(uint32_t t, uint32_t a, uint32_t b) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%2,%2,%2,%2,%2,%2};" ::"r"(t), "r"(a), "r"(b));
-}
-template <>
-__device__ __forceinline__ void tmem_fill<16>(uint32_t t, uint32_t a, uint32_t b) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2};" ::"r"(t),
-               "r"(a), "r"(b));
-}
-template <>
-__device__ __forceinline__ void tmem_fill<32>(uint32_t t, uint32_t a, uint32_t b) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,%2,"
-      "%2,%2,%2,%2,%2,%2,%2,%2};" ::"r"(t),
-      "r"(a), "r"(b));
-}
-
 // ---- UMMA descriptors and issue ---------------------------------------------
 
 // Shared-memory matrix descriptor (sm_100 family): start >> 4 at [0,14), leading byte offset >> 4 at

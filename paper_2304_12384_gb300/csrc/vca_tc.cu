@@ -358,11 +358,6 @@ __device__ __forceinline__ void convert_16(uint32_t base, int y, int x, int w_re
   }
 }
 
-template <int N>
-__device__ __forceinline__ void fill_cols(uint32_t taddr, float first, float rest) {
-  tmem_fill<N>(taddr, __float_as_uint(first), __float_as_uint(rest));
-}
-
 // Byte offsets within a stage-2 operand of this thread's 8-column chunks of a job (chunk st: group
 // st / (NK / 8), columns 8 (st % (NK / 8)) ..): thread 32 q + lane holds row r = l % Nb of block
 // l / Nb of each group, and writes stage-2 rows m = (g BPG1 + l / Nb) NK + h0 .. + 7 at K = r
