@@ -399,6 +399,20 @@ def run_vca(args):
         dist.destroy_process_group()
 
 
+EXTRAS = ("latency", "e2e", "variants", "tune", "siti", "ladder", "serving", "cpu")
+
+
+def extras_selector(spec):
+    """The predicate `name -> wanted?` of a comma-separated --extras value ("all" selects every
+    extra).  The set lives in this function's scope, so no name bound later in the caller can
+    change what is selected."""
+    wanted = frozenset(x.strip() for x in spec.split(",") if x.strip())
+    unknown = wanted - set(EXTRAS) - {"all"}
+    if unknown:
+        raise ValueError(f"unknown extras: {sorted(unknown)} (choose from {', '.join(EXTRAS)}, all)")
+    return lambda name: "all" in wanted or name in wanted
+
+
 def run_extras(args, an, y, u, v, frames, stream, kern, lp, device):
     import numpy as np
     import torch
@@ -407,10 +421,7 @@ def run_extras(args, an, y, u, v, frames, stream, kern, lp, device):
     from paper_2304_12384_gb300 import vca
 
     out = {}
-    wanted = frozenset(args.extras.split(","))
-
-    def want(name):
-        return "all" in wanted or name in wanted
+    want = extras_selector(args.extras)
 
     if want("latency"):
         # Per-frame latency: one device-resident frame per push, features read back (blocking).
