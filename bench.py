@@ -498,6 +498,17 @@ def run_extras(args, an, y, u, v, frames, stream, kern, lp, device):
         variants[f"w32_lowpass_422_{ {1: 'plain', 2: 'tc'}[a2.kernel] }"] = {
             "fps": n / (ms / 1000.0), "kernel_ms_per_launch": kms, "hbm_frac_of_measured": gbs / load_peaks()[0]}
         a2.close()
+        # 4:4:4: full-size chroma planes (the luma planes serve as U and V), 3 W H bytes per frame, on
+        # both kernels.
+        for vk in (vca.VCA_KERNEL_AUTO, vca.VCA_KERNEL_PLAIN):
+            a2 = vca.Analyzer(W, H, 8, 32, True, kernel=vk, max_batch=args.frames, stream=stream.cuda_stream,
+                              chroma_format=vca.VCA_CHROMA_444)
+            ms, kms, _ = time_pushes(a2, y, y, y, max(3, args.steps // 3), 2, stream, lambda: None)
+            n = max(3, args.steps // 3) * args.frames
+            gbs = args.frames * 3 * W * H / (kms / 1000.0) / 1e9
+            variants[f"w32_lowpass_444_{ {1: 'plain', 2: 'tc'}[a2.kernel] }"] = {
+                "fps": n / (ms / 1000.0), "kernel_ms_per_launch": kms, "hbm_frac_of_measured": gbs / load_peaks()[0]}
+            a2.close()
         out["variants"] = variants
 
     if want("tune"):

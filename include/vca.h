@@ -85,8 +85,8 @@ typedef struct vca_config {
                           only; not in batches) -- Section 2 item (3) */
   int32_t pad_mode;    /* VCA_PAD_REPLICATE (default) or VCA_PAD_SKIP */
   int32_t kernel;      /* VCA_KERNEL_AUTO, VCA_KERNEL_PLAIN (CUDA cores) or VCA_KERNEL_TC (tensor cores:
-                          8- and 10-bit 4:2:0 with 32x32 or 16x16 luma blocks, the downsample
-                          reading included; other configurations give VCA_E_UNSUPPORTED).  AUTO
+                          8- and 10-bit 4:2:0 and 4:4:4 with 32x32 or 16x16 luma blocks, the
+                          downsample reading included; other configurations give VCA_E_UNSUPPORTED).  AUTO
                           takes the tensor cores where they cover the configuration. */
   int32_t max_batch;   /* most frames one vca_push_frames call may carry; 0 selects 64 */
   int32_t chroma_format; /* VCA_CHROMA_420 (default: half-size chroma planes, w/2 blocks),

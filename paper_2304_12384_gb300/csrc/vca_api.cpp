@@ -598,7 +598,7 @@ cudaError_t build_tick_graph(vca_batch* b, int k) {
       if (e != cudaSuccess) return e;
       void* args[1] = {L.params.data()};
       cudaKernelNodeParams kp;
-      e = vca::tc_batch_node_params(b->w, L.bps, b->low_pass, b->sms, args, &kp);
+      e = vca::tc_batch_node_params(b->w, b->nc == b->w, L.bps, b->low_pass, b->sms, args, &kp);
       if (e != cudaSuccess) return e;
       const cudaGraphNode_t dep = tail[L.branch];
       e = cudaGraphAddKernelNode(&L.node[k], b->graph[k], dep ? &dep : nullptr, dep ? 1 : 0, &kp);
@@ -1188,7 +1188,7 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
                "uploading the CTA map");
   }
   for (int br = 0; b->tc && br < b->branches; ++br)
-    BATCH_CUDA(vca::tc_batch_prepare(b->w, b->branch_bps[br], b->low_pass), "preparing the tensor-core kernel");
+    BATCH_CUDA(vca::tc_batch_prepare(b->w, b->nc == b->w, b->branch_bps[br], b->low_pass), "preparing the tensor-core kernel");
   BATCH_CUDA(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device), "querying the SM count");
   if (b->sms < 1) b->sms = 1;
   BATCH_CUDA(cudaMalloc(&b->d_err, sizeof(int)), "allocating the error flag");
@@ -1322,7 +1322,7 @@ vca_status vca_batch_tick(vca_batch* b, const vca_frame_ref* frames) {
     // The graph's launch takes this tick's parameter block (copied by the call) and its branch's grid.
     void* args[1] = {L.params.data()};
     cudaKernelNodeParams kp;
-    cudaError_t e = vca::tc_batch_node_params(b->w, L.bps, b->low_pass, grid[L.branch], args, &kp);
+    cudaError_t e = vca::tc_batch_node_params(b->w, b->nc == b->w, L.bps, b->low_pass, grid[L.branch], args, &kp);
     if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(b->exec[k], L.node[k], &kp);
     if (e != cudaSuccess) return cuda_fail(e, "setting the parameters of a batch tick");
   }

@@ -139,14 +139,15 @@ size_t tc_batch_params_bytes();
 cudaError_t tc_batch_fill(void* params, const TcBatchFrame* frames, int n, const DeviceTables& t, int* err,
                           long long wait_ns = 0, int withhold = -1);
 // Sets up the kernel instance for this sample size and low_pass (outside any stream capture).
-cudaError_t tc_batch_prepare(int w, int bps, bool low_pass);
+cudaError_t tc_batch_prepare(int w, bool c444, int bps, bool low_pass);
 // Work items (128x128 luma tiles) of a filled parameter block.
 int tc_batch_items(const void* params);
 // The kernel a batched launch of this sample size and low_pass runs (to find its graph node).
-const void* tc_batch_kernel(int w, int bps, bool low_pass);
+const void* tc_batch_kernel(int w, bool c444, int bps, bool low_pass);
 // Kernel-node parameters of one batched tensor-core launch (its function, grid, block and dynamic
 // shared memory; args[0] points at its parameter block), for a graph built node by node.
-cudaError_t tc_batch_node_params(int w, int bps, bool low_pass, int grid, void** args, cudaKernelNodeParams* kp);
+cudaError_t tc_batch_node_params(int w, bool c444, int bps, bool low_pass, int grid, void** args,
+                                 cudaKernelNodeParams* kp);
 
 // Exact frame reduction: features of n frames (the block sums exact in 128-bit fixed point, each
 // total rounded once to FP64) and the h state update.  `partials` holds reduce_partials_bytes(max

@@ -46,6 +46,10 @@
 // pre-offset accumulators), so the FP32 tensor-core accumulation is exact and Z is
 // bit-identical to the integer definition; H uses the same FP32 order as the CUDA-core form.
 //
+// 4:4:4 (C444): the chroma planes have the luma plane's size, blocks and matrix, so each 128x128
+// tile of each plane is a work item of its own through the luma roles (the chroma roles and
+// issuers stay idle); epilogue 2 writes the item's plane's rows.
+//
 // 16x16 luma / 8x8 chroma blocks run the same data flow on 32x32 / 16x16 super-blocks of four
 // blocks each: the DCT matrix appears twice along the diagonal of every B operand (rows first:
 // the left and right halves of a super-block row get separate transforms; columns: the top and
@@ -90,8 +94,10 @@ constexpr int kMaxMembers = kMaxBatchMembers;
 // per channel with one frame each.  Items are numbered member by member, frame-major tiles.
 struct TcMember {
   int item_base;                   // first item of this member
-  int tiles_x, tiles_per_frame;
+  int tiles_x, tiles_per_frame;    // tiles_per_frame counts a 4:4:4 frame's three planes
   float inv_tiles_x, inv_tiles_per_frame;
+  int tiles_per_plane;             // 4:4:4: the tiles of one plane (plane p: items p T .. (p+1) T - 1)
+  float inv_tiles_per_plane;
   int W, H, cw, ch, nbx, nby;
   int64_t C, out_fstride;
   float* blockvals;
@@ -576,7 +582,7 @@ __device__ __forceinline__ void epilogue2_sub(const uint32_t (&td2)[2], int lane
 
 // Tile bookkeeping of a role's current tile.
 struct TileInfo {
-  int f, tx, ty, stage, t, m;  // frame, tile position, ring stage, CTA-local tile number, member
+  int f, tx, ty, stage, t, m, p;  // frame, tile position, ring stage, CTA-local tile number, member, plane
 };
 
 // a / b for 0 <= a < 2^24, b >= 1, from a float estimate that is off by at most one.
@@ -620,7 +626,7 @@ struct MemberView<true> {
   using T = MemberTable;
 };
 
-template <class MS>
+template <bool C444, class MS>
 __device__ __forceinline__ TileInfo tile_info(const MS& ms, int t, int item0, int step, int stages = kMaxStages) {
   TileInfo ti;
   const int item = item0 + t * step;
@@ -630,7 +636,12 @@ __device__ __forceinline__ TileInfo tile_info(const MS& ms, int t, int item0, in
   ti.m = m;
   ti.t = t;
   ti.f = div_small(local, M.tiles_per_frame, M.inv_tiles_per_frame);
-  const int r = local - ti.f * M.tiles_per_frame;
+  int r = local - ti.f * M.tiles_per_frame;
+  ti.p = 0;
+  if constexpr (C444) {
+    ti.p = div_small(r, M.tiles_per_plane, M.inv_tiles_per_plane);
+    r -= ti.p * M.tiles_per_plane;
+  }
   ti.ty = div_small(r, M.tiles_x, M.inv_tiles_x);
   ti.tx = r - ti.ty * M.tiles_x;
   ti.stage = t % stages;
@@ -663,6 +674,7 @@ struct Cursor {
 struct TileRec {
   int f, tx, ty, m;    // frame, tile position (units of 4 blocks), member
   int hy, wy, hc, wc;  // luma / chroma rows and columns from the tile's origin to the frame's edge
+                       // (4:4:4: hy, wy those of the item's plane, hc the plane, wc unused)
 };
 constexpr int kTileRecs = 16;
 static_assert(sizeof(TileRec) == 32, "two 16-byte loads");
@@ -854,7 +866,7 @@ __device__ __forceinline__ int2 superblock_of(const TileRec& r, int jp, int q, i
 
 // Epilogue 2 luma: Z, the block energy H and brightness L of both luma jobs, then the slot's luma
 // columns are handed back.
-template <bool LP, bool SUB, bool DUMP, class PP, class MS>
+template <bool LP, bool SUB, bool DUMP, bool C444, class PP, class MS>
 __device__ void epi2_luma_loop(const PP& p, const MS& ms, const TileRec* recs, const Ctl& ctl, uint32_t tq,
                                int n_items, int q, int lane) {
   using P = PC<32, LP>;
@@ -874,7 +886,8 @@ __device__ void epi2_luma_loop(const PP& p, const MS& ms, const TileRec* recs, c
     if (h == 0) rec = load_rec(recs, t);  // written by the producer before this unit's copies
     const TcMember& M = ms[rec.m];
     const uint32_t td = tq + U::d(cd.slot);
-    float* const base = M.blockvals + (int64_t)rec.f * M.out_fstride;
+    const int plane = C444 ? rec.hc : 0;  // the rows H, L of Y (0), U (1) or V (2)
+    float* const base = M.blockvals + (int64_t)rec.f * M.out_fstride + (int64_t)(2 * plane) * M.C;
     uint32_t td2[2];
     float* out[2];
     int16_t* zd[2];
@@ -885,7 +898,7 @@ __device__ void epi2_luma_loop(const PP& p, const MS& ms, const TileRec* recs, c
         sb[j] = superblock_of<P::NK, P::BPG2>(rec, h * 2 + j, q, lane);
         td2[j] = td + 2 * j * P::N1;
         out[j] = base;
-        zd[j] = (DUMP && rec.f == 0) ? p.zdump[0] : nullptr;
+        zd[j] = (DUMP && rec.f == 0) ? p.zdump[plane] : nullptr;
       }
       epilogue2_sub<32, LP, DUMP, P::N1>(td2, lane, w, einv, kK1 - kK1 * einv, sb, out, M.nbx, M.nby, M.C, zd);
     } else {
@@ -894,7 +907,7 @@ __device__ void epi2_luma_loop(const PP& p, const MS& ms, const TileRec* recs, c
         const int64_t k = block_of<P::NK, P::BPG2>(M, rec, h * 2 + j, q, lane);
         td2[j] = td + 2 * j * P::N1;
         out[j] = k >= 0 ? base + k : nullptr;
-        zd[j] = (DUMP && k >= 0 && rec.f == 0) ? p.zdump[0] + k * P::NK * P::NK : nullptr;
+        zd[j] = (DUMP && k >= 0 && rec.f == 0) ? p.zdump[plane] + k * P::NK * P::NK : nullptr;
       }
       epilogue2<32, LP, DUMP, P::N1>(td2, lane, w, einv, kK1 - kK1 * einv, out, M.C, zd);
     }
@@ -1098,7 +1111,7 @@ __device__ void issuer_loop(const Ctl& ctl, uint32_t sbase, uint32_t tmem, int i
   }
 }
 
-template <bool LP, bool SUB, bool DUMP, int BPS, bool BATCH>
+template <bool LP, bool SUB, bool DUMP, int BPS, bool BATCH, bool C444>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_kernel(const __grid_constant__ TcParamsT<BATCH ? kMaxMembers : 1> p) {
   using L = PC<32, LP>;
@@ -1223,7 +1236,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   if (tid == 0) {
     for (int i = 0; i < kBars; ++i) mbar_init(&bars[i], 1);
-    for (int i = 0; i < SL::kStages; ++i) mbar_init(&bars[b_raw_empty(i)], 8);  // both convert warpgroups
+    for (int i = 0; i < SL::kStages; ++i)
+      mbar_init(&bars[b_raw_empty(i)], C444 ? 4 : 8);  // the convert warpgroups (4:4:4: luma only)
     for (int a = 0; a < kASlots; ++a) {
       mbar_init(&bars[b_a1l_full(a)], 4);  // convert luma warps
       mbar_init(&bars[b_a1c_full(a)], 4);  // convert chroma warps
@@ -1233,7 +1247,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&bars[b_d1l(d)], 2);   // issuers 0, 1
       mbar_init(&bars[b_d2l(d)], 2);   // issuers 3, 4
       mbar_init(&bars[b_d2c(d)], 2);   // issuers 5, 6
-      mbar_init(&bars[b_dfree(d)], 8); // epilogue-2 luma and chroma warps
+      mbar_init(&bars[b_dfree(d)], C444 ? 4 : 8);  // epilogue-2 luma and chroma warps (4:4:4: luma)
     }
     for (int e = 0; e < kA2Sets; ++e) {
       mbar_init(&bars[b_a2l_full(e)], 4);  // epilogue-1 luma warps
@@ -1269,29 +1283,34 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int stage = t % SL::kStages;
         if (t >= SL::kStages && !wait_bar(ctl, b_raw_empty(stage), ((t / SL::kStages) - 1) & 1, 1, false, true))
           break;
-        const TileInfo ti = tile_info(ms, t, item0, step, SL::kStages);
+        const TileInfo ti = tile_info<C444>(ms, t, item0, step, SL::kStages);
         {
           const TcMember& M = ms[ti.m];
           TileRec* rec = recs + (t & (kTileRecs - 1));
-          *rec = TileRec{ti.f, ti.tx, ti.ty, ti.m, M.H - ti.ty * 128, M.W - ti.tx * 128, M.ch - ti.ty * 64,
-                         M.cw - ti.tx * 64};
+          if (C444)
+            *rec = TileRec{ti.f, ti.tx, ti.ty, ti.m, M.H - ti.ty * 128, M.W - ti.tx * 128, ti.p, 0};
+          else
+            *rec = TileRec{ti.f, ti.tx, ti.ty, ti.m, M.H - ti.ty * 128, M.W - ti.tx * 128, M.ch - ti.ty * 64,
+                           M.cw - ti.tx * 64};
         }
-        const CUtensorMap* mm = &p.maps[3 * ti.m];
+        const CUtensorMap* mm = &p.maps[3 * ti.m + ti.p];
         uint8_t* dst = sm + OFF_RAW + stage * SL::kStageBytes;
         uint64_t* full = &bars[b_raw_full(stage)];
         if (item0 + t * step == p.withhold) {  // failure-path test: the stage never fills
           ++issued;
           continue;
         }
-        mbar_arrive_expect_tx(full, SL::kStageBytes);
+        mbar_arrive_expect_tx(full, C444 ? SL::kRawY : SL::kStageBytes);
         if (BPS == 1) {
           tma_load_3d(dst, mm, ti.tx * 128, ti.ty * 128, ti.f, full);
         } else {  // 16-bit luma: the tile is two 64-sample boxes side by side
           tma_load_3d(dst, mm, ti.tx * 128, ti.ty * 128, ti.f, full);
           tma_load_3d(dst + 128 * 64 * 2, mm, ti.tx * 128 + 64, ti.ty * 128, ti.f, full);
         }
-        tma_load_3d(dst + SL::kRawY, mm + 1, ti.tx * 64, ti.ty * 64, ti.f, full);
-        tma_load_3d(dst + SL::kRawY + SL::kRawC, mm + 2, ti.tx * 64, ti.ty * 64, ti.f, full);
+        if (!C444) {
+          tma_load_3d(dst + SL::kRawY, mm + 1, ti.tx * 64, ti.ty * 64, ti.f, full);
+          tma_load_3d(dst + SL::kRawY + SL::kRawC, mm + 2, ti.tx * 64, ti.ty * 64, ti.f, full);
+        }
         ++issued;
       }
       // Every copy this CTA issued lands before its shared memory goes away: in a normal run the
@@ -1301,19 +1320,22 @@ __global__ void __launch_bounds__(kThreads, 1)
           wait_bar(ctl, b_raw_full(t % SL::kStages), (t / SL::kStages) & 1, 1, true);
     }
   } else if (warp <= kIssuers) {
-    if (lane == 0) issuer_loop<LP, BPS>(ctl, sbase, tmem, warp - 1, n_items);
+    // 4:4:4: the chroma issuers (stage 1 chroma: 2; stage 2 chroma hi, lo: 5, 6) have no work
+    const int id = warp - 1;
+    const bool chroma_issuer = id == 2 || id >= 5;
+    if (lane == 0 && !(C444 && chroma_issuer)) issuer_loop<LP, BPS>(ctl, sbase, tmem, id, n_items);
   } else if (role == 2) {
     convert_luma_loop<LP, BPS>(recs, ctl, sm, tmem + lanebase, n_items, q, lane);
   } else if (role == 3) {
-    convert_chroma_loop<LP, BPS>(recs, ctl, sm, tmem + lanebase, n_items, q, lane);
+    if (!C444) convert_chroma_loop<LP, BPS>(recs, ctl, sm, tmem + lanebase, n_items, q, lane);
   } else if (role == 4) {
     epi1_luma_loop<LP, SUB, BPS>(ctl, sbase, tmem + lanebase, n_items, q, lane);
   } else if (role == 5) {
-    epi2_luma_loop<LP, SUB, DUMP>(p, ms, recs, ctl, tmem + lanebase, n_items, q, lane);
+    epi2_luma_loop<LP, SUB, DUMP, C444>(p, ms, recs, ctl, tmem + lanebase, n_items, q, lane);
   } else if (role == 6) {
-    chroma_epi_loop<LP, SUB, DUMP, BPS>(p, ms, recs, ctl, sbase, tmem + lanebase, n_items, q, lane, 1);
+    if (!C444) chroma_epi_loop<LP, SUB, DUMP, BPS>(p, ms, recs, ctl, sbase, tmem + lanebase, n_items, q, lane, 1);
   } else {
-    chroma_epi_loop<LP, SUB, DUMP, BPS>(p, ms, recs, ctl, sbase, tmem + lanebase, n_items, q, lane, 2);
+    if (!C444) chroma_epi_loop<LP, SUB, DUMP, BPS>(p, ms, recs, ctl, sbase, tmem + lanebase, n_items, q, lane, 2);
   }
 
   tc_fence_before();
@@ -1360,67 +1382,104 @@ cudaError_t make_map(CUtensorMap* m, const void* base, int w, int h, int64_t pit
 }
 
 // Raises the instance's dynamic shared-memory limit (once per process).
-template <bool LP, bool SUB, bool DUMP, int BPS, bool BATCH>
+template <bool LP, bool SUB, bool DUMP, int BPS, bool BATCH, bool C444>
 cudaError_t prepare_inst() {
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(tc_kernel<LP, SUB, DUMP, BPS, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    attr = cudaFuncSetAttribute(tc_kernel<LP, SUB, DUMP, BPS, BATCH, C444>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 SmemLay<BPS>::kSmemBytes);
   });
   return attr;
 }
 
+template <bool BATCH>
+using ParamsOf = TcParamsT<BATCH ? kMaxMembers : 1>;
+
 // grid 0: only prepare the instance.
-template <bool LP, bool SUB, bool DUMP, int BPS, bool BATCH>
-cudaError_t launch_inst(const TcParamsT<BATCH ? kMaxMembers : 1>& p, int grid, cudaStream_t s) {
-  const cudaError_t attr = prepare_inst<LP, SUB, DUMP, BPS, BATCH>();
+template <bool LP, bool SUB, bool DUMP, int BPS, bool BATCH, bool C444>
+cudaError_t launch_inst(const ParamsOf<BATCH>& p, int grid, cudaStream_t s) {
+  const cudaError_t attr = prepare_inst<LP, SUB, DUMP, BPS, BATCH, C444>();
   if (attr != cudaSuccess) return attr;
   if (grid <= 0) return cudaSuccess;
-  tc_kernel<LP, SUB, DUMP, BPS, BATCH><<<grid, kThreads, SmemLay<BPS>::kSmemBytes, s>>>(p);
+  tc_kernel<LP, SUB, DUMP, BPS, BATCH, C444><<<grid, kThreads, SmemLay<BPS>::kSmemBytes, s>>>(p);
   return cudaGetLastError();
 }
 
-template <bool SUB, bool DUMP>
-cudaError_t launch_single_sd(const TcParams& p, int grid, bool low_pass, int bps, cudaStream_t s) {
+template <bool SUB, bool DUMP, bool BATCH, bool C444>
+cudaError_t launch_lb(const ParamsOf<BATCH>& p, int grid, bool low_pass, int bps, cudaStream_t s) {
   if (bps == 1)
-    return low_pass ? launch_inst<true, SUB, DUMP, 1, false>(p, grid, s)
-                    : launch_inst<false, SUB, DUMP, 1, false>(p, grid, s);
-  return low_pass ? launch_inst<true, SUB, DUMP, 2, false>(p, grid, s)
-                  : launch_inst<false, SUB, DUMP, 2, false>(p, grid, s);
+    return low_pass ? launch_inst<true, SUB, DUMP, 1, BATCH, C444>(p, grid, s)
+                    : launch_inst<false, SUB, DUMP, 1, BATCH, C444>(p, grid, s);
+  return low_pass ? launch_inst<true, SUB, DUMP, 2, BATCH, C444>(p, grid, s)
+                  : launch_inst<false, SUB, DUMP, 2, BATCH, C444>(p, grid, s);
 }
 
-// A single analyzer's launch (bps 1 or 2; w 32, or 16 for the super-block form).
-cudaError_t launch_single(const TcParams& p, int grid, int w, bool low_pass, bool dump, int bps, cudaStream_t s) {
+// A launch of the instance for block size w (32, or 16 for the super-block form), 4:4:4 or not,
+// low-pass or not, bps 1 or 2.
+template <bool DUMP, bool BATCH>
+cudaError_t launch_any(const ParamsOf<BATCH>& p, int grid, int w, bool c444, bool low_pass, int bps, cudaStream_t s) {
   if (w == 16)
-    return dump ? launch_single_sd<true, true>(p, grid, low_pass, bps, s)
-                : launch_single_sd<true, false>(p, grid, low_pass, bps, s);
-  return dump ? launch_single_sd<false, true>(p, grid, low_pass, bps, s)
-              : launch_single_sd<false, false>(p, grid, low_pass, bps, s);
+    return c444 ? launch_lb<true, DUMP, BATCH, true>(p, grid, low_pass, bps, s)
+                : launch_lb<true, DUMP, BATCH, false>(p, grid, low_pass, bps, s);
+  return c444 ? launch_lb<false, DUMP, BATCH, true>(p, grid, low_pass, bps, s)
+              : launch_lb<false, DUMP, BATCH, false>(p, grid, low_pass, bps, s);
 }
 
-template <bool SUB>
-cudaError_t launch_batched_s(const TcBatchParams& p, int grid, bool low_pass, int bps, cudaStream_t s) {
+// A single analyzer's launch.
+cudaError_t launch_single(const TcParams& p, int grid, int w, bool c444, bool low_pass, bool dump, int bps,
+                          cudaStream_t s) {
+  return dump ? launch_any<true, false>(p, grid, w, c444, low_pass, bps, s)
+              : launch_any<false, false>(p, grid, w, c444, low_pass, bps, s);
+}
+
+// A batched launch of members of one sample size.
+cudaError_t launch_batched(const TcBatchParams& p, int grid, int w, bool c444, bool low_pass, int bps, cudaStream_t s) {
+  return launch_any<false, true>(p, grid, w, c444, low_pass, bps, s);
+}
+
+// The batched kernel instance.
+template <bool SUB, bool C444>
+const void* batch_kernel_of(int bps, bool low_pass) {
   if (bps == 1)
-    return low_pass ? launch_inst<true, SUB, false, 1, true>(p, grid, s)
-                    : launch_inst<false, SUB, false, 1, true>(p, grid, s);
-  return low_pass ? launch_inst<true, SUB, false, 2, true>(p, grid, s)
-                  : launch_inst<false, SUB, false, 2, true>(p, grid, s);
+    return low_pass ? (const void*)tc_kernel<true, SUB, false, 1, true, C444>
+                    : (const void*)tc_kernel<false, SUB, false, 1, true, C444>;
+  return low_pass ? (const void*)tc_kernel<true, SUB, false, 2, true, C444>
+                  : (const void*)tc_kernel<false, SUB, false, 2, true, C444>;
 }
 
-// A batched launch of members of one sample size (bps 1 or 2) and block size w.
-cudaError_t launch_batched(const TcBatchParams& p, int grid, int w, bool low_pass, int bps, cudaStream_t s) {
-  return w == 16 ? launch_batched_s<true>(p, grid, low_pass, bps, s) : launch_batched_s<false>(p, grid, low_pass, bps, s);
+// Tensor maps of one frame's planes: the luma plane as 128x128 boxes (8-bit samples, 128-byte
+// swizzle) or as pairs of 64x128 boxes (16-bit words), and the chroma planes the same way in
+// 4:4:4, else as 64x64 boxes (64-byte swizzle for bytes, 128-byte for words).
+cudaError_t make_frame_maps(CUtensorMap* m, const Geometry& g, const FramePlanes& fp, int nframes) {
+  const bool c444 = g.nc == g.w;
+  const int bps = g.bps;
+  const int by = bps == 1 ? 128 : 64;
+  cudaError_t e = make_map(&m[0], fp.y, g.W, g.H, fp.pitch_y, fp.fstride_y, nframes, by, 128, bps,
+                           CU_TENSOR_MAP_SWIZZLE_128B);
+  for (int pl = 1; pl < 3 && e == cudaSuccess; ++pl) {
+    const uint8_t* base = pl == 1 ? fp.u : fp.v;
+    if (c444)
+      e = make_map(&m[pl], base, g.cw, g.ch, fp.pitch_uv, fp.fstride_uv, nframes, by, 128, bps,
+                   CU_TENSOR_MAP_SWIZZLE_128B);
+    else
+      e = make_map(&m[pl], base, g.cw, g.ch, fp.pitch_uv, fp.fstride_uv, nframes, 64, 64, bps,
+                   bps == 1 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B);
+  }
+  return e;
 }
 
 // One member's entry: geometry, outputs and stage-1 constants; returns its number of items.  A
-// tile is 128 x 128 luma samples: 4 x 4 blocks of 32 x 32, or 8 x 8 of 16 x 16.
+// tile is 128 x 128 luma samples: 4 x 4 blocks of 32 x 32, or 8 x 8 of 16 x 16; a 4:4:4 frame has
+// three planes of tiles.
 int fill_member(TcMember& m, const Geometry& g, int item_base, int nframes, float* blockvals) {
   m = TcMember{};
   m.item_base = item_base;
   const int bpt = 128 / g.w;
   m.tiles_x = (g.nbx + bpt - 1) / bpt;
-  m.tiles_per_frame = m.tiles_x * ((g.nby + bpt - 1) / bpt);
+  m.tiles_per_plane = m.tiles_x * ((g.nby + bpt - 1) / bpt);
+  m.inv_tiles_per_plane = 1.0f / (float)m.tiles_per_plane;
+  m.tiles_per_frame = m.tiles_per_plane * (g.nc == g.w ? 3 : 1);
   m.inv_tiles_x = 1.0f / (float)m.tiles_x;
   m.inv_tiles_per_frame = 1.0f / (float)m.tiles_per_frame;
   m.W = g.W;
@@ -1445,7 +1504,8 @@ int sm_count() {
 }  // namespace
 
 bool tc_supported(const Geometry& g) {
-  const bool sizes = (g.w == 32 && g.nc == 16) || (g.w == 16 && g.nc == 8);
+  // 4:2:0 (chroma blocks w/2) and 4:4:4 (chroma blocks w, through the luma roles)
+  const bool sizes = (g.w == 32 || g.w == 16) && (g.nc == g.w / 2 || g.nc == g.w);
   return (g.B == 8 || g.B == 10) && sizes && g.ncv == g.nc && g.s1y == s1_of(g.w, g.bps) &&
          g.s1c == s1_of(g.nc, g.bps) && encode_fn() != nullptr;
 }
@@ -1485,7 +1545,8 @@ cudaError_t tc_batch_fill(void* params, const TcBatchFrame* frames, int n, const
   for (int i = 0; i < n; ++i) {
     const Geometry& g = *frames[i].g;
     const FramePlanes& fp = frames[i].fp;
-    if (!tc_supported(g) || g.bps != frames[0].g->bps || g.w != frames[0].g->w) return cudaErrorInvalidValue;
+    if (!tc_supported(g) || g.bps != frames[0].g->bps || g.w != frames[0].g->w || g.nc != frames[0].g->nc)
+      return cudaErrorInvalidValue;
     items += fill_member(p.mem[i], g, items, 1, frames[i].blockvals);
     TcMapCache* c = frames[i].maps;
     const TcMapCache::Entry* hit = nullptr;
@@ -1497,11 +1558,9 @@ cudaError_t tc_batch_fill(void* params, const TcBatchFrame* frames, int n, const
       std::memcpy(&p.maps[3 * i], hit->m, sizeof hit->m);
       continue;
     }
-    const CUtensorMapSwizzle swc = g.bps == 1 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
-    cudaError_t e = make_map(&p.maps[3 * i], fp.y, g.W, g.H, fp.pitch_y, 0, 1, g.bps == 1 ? 128 : 64, 128, g.bps,
-                             CU_TENSOR_MAP_SWIZZLE_128B);
-    if (e == cudaSuccess) e = make_map(&p.maps[3 * i + 1], fp.u, g.cw, g.ch, fp.pitch_uv, 0, 1, 64, 64, g.bps, swc);
-    if (e == cudaSuccess) e = make_map(&p.maps[3 * i + 2], fp.v, g.cw, g.ch, fp.pitch_uv, 0, 1, 64, 64, g.bps, swc);
+    FramePlanes one = fp;
+    one.fstride_y = one.fstride_uv = 0;
+    cudaError_t e = make_frame_maps(&p.maps[3 * i], g, one, 1);
     if (e != cudaSuccess) return e;
     if (c) {
       TcMapCache::Entry& x = c->e[c->next];
@@ -1522,28 +1581,24 @@ cudaError_t tc_batch_fill(void* params, const TcBatchFrame* frames, int n, const
 
 int tc_batch_items(const void* params) { return static_cast<const TcBatchParams*>(params)->total_items; }
 
-cudaError_t tc_batch_prepare(int w, int bps, bool low_pass) {
+cudaError_t tc_batch_prepare(int w, bool c444, int bps, bool low_pass) {
   if ((bps != 1 && bps != 2) || (w != 32 && w != 16)) return cudaErrorInvalidValue;
   static TcBatchParams unused{};
-  return launch_batched(unused, 0, w, low_pass, bps, nullptr);
+  return launch_batched(unused, 0, w, c444, low_pass, bps, nullptr);
 }
 
-template <bool SUB>
-const void* tc_batch_kernel_s(int bps, bool low_pass) {
-  if (bps == 1)
-    return low_pass ? (const void*)tc_kernel<true, SUB, false, 1, true> : (const void*)tc_kernel<false, SUB, false, 1, true>;
-  return low_pass ? (const void*)tc_kernel<true, SUB, false, 2, true> : (const void*)tc_kernel<false, SUB, false, 2, true>;
+const void* tc_batch_kernel(int w, bool c444, int bps, bool low_pass) {
+  if (w == 16)
+    return c444 ? batch_kernel_of<true, true>(bps, low_pass) : batch_kernel_of<true, false>(bps, low_pass);
+  return c444 ? batch_kernel_of<false, true>(bps, low_pass) : batch_kernel_of<false, false>(bps, low_pass);
 }
 
-const void* tc_batch_kernel(int w, int bps, bool low_pass) {
-  return w == 16 ? tc_batch_kernel_s<true>(bps, low_pass) : tc_batch_kernel_s<false>(bps, low_pass);
-}
-
-cudaError_t tc_batch_node_params(int w, int bps, bool low_pass, int grid, void** args, cudaKernelNodeParams* kp) {
-  const cudaError_t e = tc_batch_prepare(w, bps, low_pass);
+cudaError_t tc_batch_node_params(int w, bool c444, int bps, bool low_pass, int grid, void** args,
+                                 cudaKernelNodeParams* kp) {
+  const cudaError_t e = tc_batch_prepare(w, c444, bps, low_pass);
   if (e != cudaSuccess) return e;
   *kp = cudaKernelNodeParams{};
-  kp->func = const_cast<void*>(tc_batch_kernel(w, bps, low_pass));
+  kp->func = const_cast<void*>(tc_batch_kernel(w, c444, bps, low_pass));
   kp->gridDim = dim3((unsigned)(grid > 0 ? grid : 1));
   kp->blockDim = dim3(kThreads);
   kp->sharedMemBytes = bps == 1 ? SmemLay<1>::kSmemBytes : SmemLay<2>::kSmemBytes;
@@ -1557,22 +1612,12 @@ cudaError_t launch_tc(const Geometry& g, const FramePlanes& fp, int nframes, con
                       long long wait_ns, int withhold) {
   if (!tc_supported(g)) return cudaErrorNotSupported;
   if (nframes <= 0) return cudaSuccess;
-  // 8-bit: 128x128 luma boxes (128-byte swizzle), 64x64 chroma boxes (64-byte swizzle); 16-bit:
-  // 64x128 luma boxes (two per tile) and 64x64 chroma boxes, all 128-byte rows and swizzle.
   const int bps = g.bps;
-  const CUtensorMapSwizzle swc = bps == 1 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
-  CUtensorMap my, mu, mv;
-  cudaError_t e = make_map(&my, fp.y, g.W, g.H, fp.pitch_y, fp.fstride_y, nframes, bps == 1 ? 128 : 64, 128, bps,
-                           CU_TENSOR_MAP_SWIZZLE_128B);
-  if (e == cudaSuccess) e = make_map(&mu, fp.u, g.cw, g.ch, fp.pitch_uv, fp.fstride_uv, nframes, 64, 64, bps, swc);
-  if (e == cudaSuccess) e = make_map(&mv, fp.v, g.cw, g.ch, fp.pitch_uv, fp.fstride_uv, nframes, 64, 64, bps, swc);
-  if (e != cudaSuccess) return e;
   TcParams p{};
+  cudaError_t e = make_frame_maps(p.maps, g, fp, nframes);
+  if (e != cudaSuccess) return e;
   p.n_members = 1;
   p.total_items = fill_member(p.mem[0], g, 0, nframes, blockvals);
-  p.maps[0] = my;
-  p.maps[1] = mu;
-  p.maps[2] = mv;
   for (int i = 0; i < 3; ++i) p.zdump[i] = zdump ? zdump[i] : nullptr;
   p.M_y = t.M_y;
   p.M_c = t.M_c;
@@ -1583,7 +1628,7 @@ cudaError_t launch_tc(const Geometry& g, const FramePlanes& fp, int nframes, con
   p.withhold = withhold;
   int grid = ctas > 0 && ctas < sm_count() ? ctas : sm_count();
   if (p.total_items < grid) grid = p.total_items;
-  e = launch_single(p, grid, g.w, g.low_pass, zdump != nullptr, bps, s);
+  e = launch_single(p, grid, g.w, g.nc == g.w, g.low_pass, zdump != nullptr, bps, s);
   if (e == cudaSuccess) ++*launches;
   return e;
 }

@@ -150,6 +150,36 @@ def test_batch_state_rules(vca):
             x.close()
 
 
+@pytest.mark.parametrize("block_size", [32, 16])
+def test_tc_batch_444(vca, block_size):
+    # 4:4:4 channels (8- and 10-bit) tick on the tensor-core kernel, each plane of a tile a work item;
+    # features equal the single analyzers' bit for bit and the oracle.
+    chans = [(200, 120, 8), (136, 72, 10), (256, 144, 8)]
+    frames = [frames_list(SequenceSpec(w, h, 3, 70 + i, bit_depth=bd, sigma=4.0, chroma_format="444"))
+              for i, (w, h, bd) in enumerate(chans)]
+    dev = [to_device(f) for f in frames]
+    members = [vca.Analyzer(w, h, bd, block_size, True, max_batch=3, chroma_format=vca.VCA_CHROMA_444)
+               for (w, h, bd) in chans]
+    singles = [vca.Analyzer(w, h, bd, block_size, True, max_batch=3, chroma_format=vca.VCA_CHROMA_444)
+               for (w, h, bd) in chans]
+    try:
+        with vca.Batch(members) as batch:
+            assert batch.kernel == vca.VCA_KERNEL_TC
+            for t in range(3):
+                batch.tick([(y[t], u[t], v[t]) for (y, u, v) in dev])
+                for s_, (y, u, v) in zip(singles, dev):
+                    s_.push(y[t], u[t], v[t])
+        for i, (m, s_) in enumerate(zip(members, singles)):
+            got = [m.frame_features(t) for t in range(3)]
+            assert got == [s_.frame_features(t) for t in range(3)], f"channel {i}"
+            per, _ = oracle_sequence(frames[i], oracle_config(m))
+            for t in range(3):
+                assert_features_close(got[t], per[t], where=f"channel {i} frame {t}")
+    finally:
+        for a in members + singles:
+            a.close()
+
+
 def test_batch_444_422_and_block_8(vca):
     # Batches of 4:4:4 channels, of 4:2:2 channels and of 8 x 8-block channels match single
     # analyzers bit for bit.

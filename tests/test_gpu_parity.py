@@ -307,12 +307,25 @@ def test_12_bit(vca, block_size, low_pass):
                     low_pass=low_pass, dump_frames=(1,))
 
 
-@pytest.mark.parametrize("block_size", [32, 16, 8])
-@pytest.mark.parametrize("bit_depth", [8, 12])
-def test_chroma_444(vca, block_size, bit_depth):
+CASES_444 = [("plain", bs, bd) for bs in (32, 16, 8) for bd in (8, 10, 12)] + \
+            [("tc", bs, bd) for bs in (32, 16) for bd in (8, 10)]  # what the tensor-core form covers
+
+
+@pytest.mark.parametrize("kernel,block_size,bit_depth", CASES_444)
+def test_chroma_444(vca, kernel, block_size, bit_depth):
+    # 4:4:4: full-size chroma planes with w x w blocks; the tensor-core form runs each plane of a tile
+    # through its luma roles (8 and 10 bits, w 32 and 16).
     frames = frames_list(SequenceSpec(200, 120, 4, 53, bit_depth=bit_depth, sigma=4.0, cuts=(2,), chroma_format="444"))
-    run_and_compare(vca, "plain", frames, width=200, height=120, bit_depth=bit_depth, block_size=block_size,
-                    low_pass=block_size == 16, dump_frames=(0, 3), chroma_format=1)
+    for low_pass in (False, True):
+        run_and_compare(vca, kernel, frames, width=200, height=120, bit_depth=bit_depth, block_size=block_size,
+                        low_pass=low_pass, dump_frames=(0, 3), chroma_format=1)
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+def test_chroma_444_hd_sampled(vca, kernel):
+    frames = frames_list(SequenceSpec(1920, 1080, 3, 58, bit_depth=8, sigma=4.0, chroma_format="444"))
+    run_and_compare(vca, kernel, frames, width=1920, height=1080, block_size=32, low_pass=True, dump_frames=(2,),
+                    block_frames=(0, 2), chroma_format=1)
 
 
 @pytest.mark.parametrize("block_size", [32, 16, 8])
@@ -337,12 +350,19 @@ def test_chroma_422_hd_sampled(vca, pad_mode):
 
 
 def test_variant_rules(vca):
-    # The tensor-core form covers 8- and 10-bit 4:2:0 with 32 x 32 blocks; the others run on CUDA cores.
-    for kw in ({"bit_depth": 12}, {"block_size": 8}, {"chroma_format": 1}, {"chroma_format": 2}):
+    # The tensor-core form covers 8- and 10-bit 4:2:0 and 4:4:4 with 32 x 32 or 16 x 16 blocks; the
+    # others run on CUDA cores.
+    for kw in ({"bit_depth": 12}, {"block_size": 8}, {"chroma_format": 2}):
         args = dict(width=640, height=352, bit_depth=8, block_size=32)
         args.update(kw)
         an = vca.Analyzer(**args)
         assert an.kernel == vca.VCA_KERNEL_PLAIN
+        an.close()
+    for kw in ({"chroma_format": 1}, {"chroma_format": 1, "block_size": 16, "bit_depth": 10}):
+        args = dict(width=640, height=352, bit_depth=8, block_size=32)
+        args.update(kw)
+        an = vca.Analyzer(**args)
+        assert an.kernel == vca.VCA_KERNEL_TC
         an.close()
     with pytest.raises(vca.VcaError) as ei:
         vca.Analyzer(640, 352, 8, 32, chroma_format=vca.VCA_CHROMA_422, kernel=vca.VCA_KERNEL_TC)
