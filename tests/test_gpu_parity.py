@@ -11,8 +11,9 @@ import numpy as np
 import pytest
 
 from synth import SequenceSpec, frames_list, hd_spec, tiny_spec, uhd_spec
-from vca_testutil import (assert_block_values_close, assert_features_close, frame_block_values, oracle_coefficients,
-                          oracle_config, oracle_sequence, to_device, to_host_pinned)
+from vca_testutil import (BLOCK_H_RTOL, BLOCK_L_RTOL, assert_block_values_close, assert_features_close,
+                          frame_block_values, oracle_coefficients, oracle_config, oracle_sequence, to_device,
+                          to_host_pinned)
 
 pytestmark = pytest.mark.gpu
 
@@ -465,3 +466,56 @@ def test_feature_error_statement(vca, case):
         assert err[k] <= 1e-6, (k, err[k])
     assert err["h_vs_max(h,E_Y)"] <= 1e-6
     assert err["h"] <= 1e-5
+
+
+# ---- the largest frame vca_open accepts ----
+
+@pytest.mark.parametrize("kernel,block_size,low_pass", [("tc", 32, True), ("tc", 16, False), ("plain", 32, True)])
+def test_maximum_frame_size_sampled(vca, kernel, block_size, low_pass):
+    # 16384 x 16384 8-bit 4:2:0, the largest frame vca_open accepts: 262,144 blocks of 32 x 32 per
+    # plane (1,048,576 of 16 x 16) and 16,384 tiles of 128 x 128, the widest indices of every kernel.
+    # Uniform noise drives the coefficients over their full range.  Block values are compared with
+    # the oracle on sampled blocks (the four corners, the edges, random interior ones), cut by hand
+    # from the planes; the frame features with exact sums of the kernel's own block values divided by
+    # the oracle's norms (the reduction sums exactly and rounds once).
+    import math
+
+    from oracle import block_brightness, block_texture_energy, int_dct2
+
+    W = H = 16384
+    rng = np.random.default_rng(16384 + block_size)
+    y = rng.integers(0, 256, size=(H, W), dtype=np.uint8)
+    u = rng.integers(0, 256, size=(H // 2, W // 2), dtype=np.uint8)
+    v = rng.integers(0, 256, size=(H // 2, W // 2), dtype=np.uint8)
+    an = open_analyzer(vca, kernel, width=W, height=H, bit_depth=8, block_size=block_size, low_pass=low_pass,
+                       max_batch=1)
+    try:
+        dy, du, dv = to_device([(y, u, v)])
+        an.push(dy, du, dv)
+        f = an.frame_features(0)
+        bv = an.block_values(0)
+    finally:
+        an.close()
+    w, nc = block_size, block_size // 2
+    nbx = nby = W // w
+    C = nbx * nby
+    assert bv["H_Y"].shape == (C,)
+    last = nbx - 1
+    picks = {0, last, last * nbx, C - 1, nbx // 2, (nby // 2) * nbx + last}
+    picks |= set(int(k) for k in rng.integers(0, C, size=40))
+    ks = np.array(sorted(picks))
+    bx, by = ks % nbx, ks // nbx
+    for name, plane, n in (("Y", y, w), ("U", u, nc), ("V", v, nc)):
+        blocks = np.stack([plane[j * n:(j + 1) * n, i * n:(i + 1) * n] for i, j in zip(bx, by)]).astype(np.int64)
+        Z = int_dct2(blocks, 8, low_pass)
+        eH, eL = block_texture_energy(Z, n), block_brightness(Z)
+        gH, gL = bv["H_" + name][ks].astype(np.float64), bv["L_" + name][ks].astype(np.float64)
+        bad = np.nonzero(np.abs(gH - eH) > BLOCK_H_RTOL * np.abs(eH))[0]
+        assert bad.size == 0, f"H_{name} off at blocks {ks[bad[:5]]}: {gH[bad[:5]]} vs {eH[bad[:5]]}"
+        bad = np.nonzero(np.abs(gL - eL) > BLOCK_L_RTOL * np.abs(eL))[0]
+        assert bad.size == 0, f"L_{name} off at blocks {ks[bad[:5]]}: {gL[bad[:5]]} vs {eL[bad[:5]]}"
+    exact = {k: math.fsum(bv[k].astype(np.float64)) for k in bv}
+    assert f["E_Y"] == exact["H_Y"] / (C * w * w) and f["L_Y"] == exact["L_Y"] / C
+    assert f["E_U"] == exact["H_U"] / (C * nc * nc) and f["E_V"] == exact["H_V"] / (C * nc * nc)
+    assert f["L_U"] == exact["L_U"] / C and f["L_V"] == exact["L_V"] / C
+    assert f["h"] == 0.0
