@@ -265,8 +265,8 @@ struct Ctl {
 };
 
 // Bounded wait: false on timeout (flag raised) or when another role aborted.
-__device__ __noinline__ bool wait_bar_slow(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
-                                          int code, bool ignore_abort, bool sleep, uint64_t wait_ns) {
+__device__ __forceinline__ bool wait_bar_poll(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                              int code, bool ignore_abort, bool sleep, uint64_t wait_ns) {
   const uint64_t t0 = now_ns();
   for (;;) {
 #pragma unroll 1
@@ -281,13 +281,25 @@ __device__ __noinline__ bool wait_bar_slow(uint64_t* bar, uint32_t parity, volat
   }
 }
 
+__device__ __noinline__ bool wait_bar_slow(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                          int code, bool ignore_abort, bool sleep, uint64_t wait_ns) {
+  return wait_bar_poll(bar, parity, abort_flag, err, code, ignore_abort, sleep, wait_ns);
+}
+
 // Bounded wait on barrier idx.  Roles on the critical path spin; the producer (sleep = true) lets
-// its thread sleep in hardware between polls.
+// its thread sleep in hardware between polls.  INL: the polling loop inline at every wait, which
+// saves the call (and the registers it saves and restores) where first polls often fail -- the
+// low-pass instances, 2 % faster; the all-coefficient instances, whose code is twice as large,
+// run 4 % slower with it (instruction-cache misses), so they call one out-of-line copy.
+template <bool INL>
 __device__ __forceinline__ bool wait_bar(const Ctl& c, int idx, uint32_t parity, int code, bool ignore_abort = false,
                                          bool sleep = false) {
   uint64_t* bar = c.bars + idx;
   if (sleep ? mbar_try_wait_sleep(bar, parity) : mbar_try_wait(bar, parity)) return true;
-  return wait_bar_slow(bar, parity, c.abort, c.err, code, ignore_abort, sleep, c.wait_ns);
+  if constexpr (INL)
+    return wait_bar_poll(bar, parity, c.abort, c.err, code, ignore_abort, sleep, c.wait_ns);
+  else
+    return wait_bar_slow(bar, parity, c.abort, c.err, code, ignore_abort, sleep, c.wait_ns);
 }
 
 // Byte offset of sample xx of row y of the raw tile of this plane type.
@@ -386,24 +398,31 @@ struct E1Offs {
   }
 };
 
-// Reads D1 (stage-1 accumulators at td1 + g*N1) and writes the stage-2 operand to shared memory,
-// 8 columns at a time; the TMEM load of the next 8 columns is in flight while this thread
-// converts the current ones.
-template <int Nb, bool LP>
-__device__ __forceinline__ void epilogue1(uint32_t td1, uint32_t a2hi, uint32_t a2lo, const E1Offs<Nb, LP>& eo,
-                                          float s1inv) {
+// Reads D1 of J jobs (job i: stage-1 accumulators at td1[i] + g*N1) and writes their stage-2
+// operands to shared memory (hi at a2hi[i], lo lo_off bytes further), 8 columns at a time; the
+// TMEM load of the next 8 columns (of the same job or the next) is in flight while this thread
+// converts the current ones.  The low-pass roles take both jobs in one pipeline (J = 2); the
+// all-coefficient ones, whose code is larger, one job per call (J = 1).
+template <int Nb, bool LP, int J>
+__device__ __forceinline__ void epilogue1(const uint32_t (&td1)[J], const uint32_t (&a2hi)[J], uint32_t lo_off,
+                                          const E1Offs<Nb, LP>& eo, float s1inv) {
   using P = PC<Nb, LP>;
   constexpr int CPG = P::NK / 8;  // 8-column chunks per group
-  constexpr int S = E1Offs<Nb, LP>::S;
+  constexpr int S1 = E1Offs<Nb, LP>::S;  // chunks per job
+  constexpr int S = J * S1;
   const uint64_t s1inv2 = f2pack(__float_as_uint(s1inv), __float_as_uint(s1inv));
   const uint64_t kT1x2 = f2pack(__float_as_uint(kT1), __float_as_uint(kT1));
   uint32_t buf[2][8];
-  tmem_ld<8>(td1, buf[0]);
+  tmem_ld<8>(td1[0], buf[0]);
 #pragma unroll
   for (int st = 0; st < S; ++st) {
     tmem_wait_ld();
-    if (st + 1 < S) tmem_ld<8>(td1 + ((st + 1) / CPG) * P::N1 + ((st + 1) % CPG) * 8, buf[(st + 1) & 1]);
+    if (st + 1 < S) {
+      const int sn = (st + 1) % S1;
+      tmem_ld<8>(td1[(st + 1) / S1] + (sn / CPG) * P::N1 + (sn % CPG) * 8, buf[(st + 1) & 1]);
+    }
     const uint32_t(&acc)[8] = buf[st & 1];
+    const uint32_t hiaddr = a2hi[st / S1] + eo.off[st % S1];
     uint32_t hi[4], lw[4];
 #pragma unroll
     for (int k = 0; k < 8; k += 2) {
@@ -415,8 +434,8 @@ __device__ __forceinline__ void epilogue1(uint32_t td1, uint32_t a2hi, uint32_t 
       lw[k / 2] = prmt(za, zb, 0x6420);
       hi[k / 2] = prmt(za, zb, 0x6521);
     }
-    sts128(a2hi + eo.off[st], hi[0], hi[1], hi[2], hi[3]);
-    sts128(a2lo + eo.off[st], lw[0], lw[1], lw[2], lw[3]);
+    sts128(hiaddr, hi[0], hi[1], hi[2], hi[3]);
+    sts128(hiaddr + lo_off, lw[0], lw[1], lw[2], lw[3]);
   }
 }
 
@@ -713,13 +732,13 @@ __device__ void convert_luma_loop(const TileRec* recs, const Ctl& ctl, uint8_t* 
   for (int u = 0, t = 0, h = 0; u < n; ++u, ca.next()) {
     if (h == 0) {
       stage = t % SL::kStages;
-      if (!wait_bar(ctl, b_raw_full(stage), (t / SL::kStages) & 1, 4)) return;
+      if (!wait_bar<LP>(ctl, b_raw_full(stage), (t / SL::kStages) & 1, 4)) return;
       const TileRec r = load_rec(recs, t);
       hy = r.hy;
       wy = r.wy;
       inside = hy >= 128 && wy >= 128;
     }
-    if (u >= kASlots && !wait_bar(ctl, b_a1l_free(ca.slot), ca.par ^ 1u, 4)) return;
+    if (u >= kASlots && !wait_bar<LP>(ctl, b_a1l_free(ca.slot), ca.par ^ 1u, 4)) return;
     tc_fence_after();
     const uint32_t rbase = smem_u32(sm + OFF_RAW + stage * SL::kStageBytes);
     const uint32_t ta = tq + U::a1(ca.slot);
@@ -774,13 +793,13 @@ __device__ void convert_chroma_loop(const TileRec* recs, const Ctl& ctl, uint8_t
   for (int u = 0, t = 0, h = 0; u < n; ++u, ca.next()) {
     if (h == 0) {
       stage = t % SL::kStages;
-      if (!wait_bar(ctl, b_raw_full(stage), (t / SL::kStages) & 1, 4)) return;
+      if (!wait_bar<LP>(ctl, b_raw_full(stage), (t / SL::kStages) & 1, 4)) return;
       const TileRec rr = load_rec(recs, t);
       hc = rr.hc;
       wc = rr.wc;
       inside = hc >= 64 && wc >= 64;
     }
-    if (u >= kASlots && !wait_bar(ctl, b_a1c_free(ca.slot), ca.par ^ 1u, 4)) return;
+    if (u >= kASlots && !wait_bar<LP>(ctl, b_a1c_free(ca.slot), ca.par ^ 1u, 4)) return;
     tc_fence_after();
     const uint32_t raw = smem_u32(sm + OFF_RAW + stage * SL::kStageBytes + SL::kRawY);
     const uint32_t ta = tq + U::a1(ca.slot) + U::A1C;
@@ -831,15 +850,20 @@ __device__ void epi1_luma_loop(const Ctl& ctl, uint32_t sbase, uint32_t tq, int 
   Cursor<kA2Sets> ce;
   const int n = n_items * U::UPT;
   for (int u = 0; u < n; ++u, cd.next(), ce.next()) {
-    if (!wait_bar(ctl, b_d1l(cd.slot), cd.par, 4)) return;
-    if (u >= kA2Sets && !wait_bar(ctl, b_a2l_free(ce.slot), ce.par ^ 1u, 4)) return;
+    if (!wait_bar<LP>(ctl, b_d1l(cd.slot), cd.par, 4)) return;
+    if (u >= kA2Sets && !wait_bar<LP>(ctl, b_a2l_free(ce.slot), ce.par ^ 1u, 4)) return;
     tc_fence_after();
     const uint32_t td = tq + U::d(cd.slot);
     const uint32_t a2 = sbase + SL::OFF_A2 + (uint32_t)(ce.slot * kA2Unit);
+    if constexpr (LP) {
+      const uint32_t tdj[2] = {td, td + P::G * P::N1}, ahj[2] = {a2_luma(a2, 0), a2_luma(a2, 1)};
+      epilogue1<32, LP, 2>(tdj, ahj, kA2L, eo, s1inv);
+    } else {
 #pragma unroll 1
-    for (int j = 0; j < 2; ++j) {
-      const uint32_t ahi = a2_luma(a2, j);
-      epilogue1<32, LP>(td + j * P::G * P::N1, ahi, ahi + kA2L, eo, s1inv);
+      for (int j = 0; j < 2; ++j) {
+        const uint32_t tdj[1] = {td + j * P::G * P::N1}, ahj[1] = {a2_luma(a2, j)};
+        epilogue1<32, LP, 1>(tdj, ahj, kA2L, eo, s1inv);
+      }
     }
     fence_proxy_async_smem();
     tc_fence_before();
@@ -881,7 +905,7 @@ __device__ void epi2_luma_loop(const PP& p, const MS& ms, const TileRec* recs, c
   const int n = n_items * U::UPT;
   TileRec rec{};
   for (int u = 0, t = 0, h = 0; u < n; ++u, cd.next()) {
-    if (!wait_bar(ctl, b_d2l(cd.slot), cd.par, 4)) return;
+    if (!wait_bar<LP>(ctl, b_d2l(cd.slot), cd.par, 4)) return;
     tc_fence_after();
     if (h == 0) rec = load_rec(recs, t);  // written by the producer before this unit's copies
     const TcMember& M = ms[rec.m];
@@ -944,15 +968,20 @@ __device__ void chroma_epi_loop(const PP& p, const MS& ms, const TileRec* recs, 
   TileRec rec{};
   for (int u = 0, t = 0, h = 0; u <= n; ++u) {
     if (u < n && (mode & 1)) {  // epilogue 1 of unit u
-      if (!wait_bar(ctl, b_d1c(cd.slot), cd.par, 4)) return;
-      if (u >= kA2Sets && !wait_bar(ctl, b_a2c_free(ce.slot), ce.par ^ 1u, 4)) return;
+      if (!wait_bar<LP>(ctl, b_d1c(cd.slot), cd.par, 4)) return;
+      if (u >= kA2Sets && !wait_bar<LP>(ctl, b_a2c_free(ce.slot), ce.par ^ 1u, 4)) return;
       tc_fence_after();
       const uint32_t td = tq + U::d(cd.slot) + U::DC;
       const uint32_t a2 = sbase + SL::OFF_A2 + (uint32_t)(ce.slot * kA2Unit);
+      if constexpr (LP) {
+        const uint32_t tdj[2] = {td, td + NKC}, ahj[2] = {a2_chroma(a2, 0), a2_chroma(a2, 1)};
+        epilogue1<16, LP, 2>(tdj, ahj, kA2C, eo, s1inv);
+      } else {
 #pragma unroll 1
-      for (int pl = 0; pl < 2; ++pl) {
-        const uint32_t ahi = a2_chroma(a2, pl);
-        epilogue1<16, LP>(td + pl * NKC, ahi, ahi + kA2C, eo, s1inv);
+        for (int pl = 0; pl < 2; ++pl) {
+          const uint32_t tdj[1] = {td + pl * NKC}, ahj[1] = {a2_chroma(a2, pl)};
+          epilogue1<16, LP, 1>(tdj, ahj, kA2C, eo, s1inv);
+        }
       }
       fence_proxy_async_smem();
       tc_fence_before();
@@ -962,7 +991,7 @@ __device__ void chroma_epi_loop(const PP& p, const MS& ms, const TileRec* recs, 
       ce.next();
     }
     if (u >= 1 && (mode & 2)) {  // epilogue 2 of unit u - 1
-      if (!wait_bar(ctl, b_d2c(cd2.slot), cd2.par, 4)) return;
+      if (!wait_bar<LP>(ctl, b_d2c(cd2.slot), cd2.par, 4)) return;
       tc_fence_after();
       if (h == 0) rec = load_rec(recs, t);
       const TcMember& M = ms[rec.m];
@@ -1028,8 +1057,8 @@ __device__ void issuer_loop(const Ctl& ctl, uint32_t sbase, uint32_t tmem, int i
     const uint32_t aoff = id < 2 ? (uint32_t)(id * 16 * L::G) : (uint32_t)U::A1C;
     const uint32_t doff = id < 2 ? (uint32_t)(id * L::G * L::N1) : (uint32_t)U::DC;
     for (int u = 0; u < n; ++u, ca.next(), cd.next()) {
-      if (!wait_bar(ctl, id < 2 ? b_a1l_full(ca.slot) : b_a1c_full(ca.slot), ca.par, 2) ||
-          (u >= U::DS && !wait_bar(ctl, b_dfree(cd.slot), cd.par ^ 1u, 2))) {
+      if (!wait_bar<LP>(ctl, id < 2 ? b_a1l_full(ca.slot) : b_a1c_full(ca.slot), ca.par, 2) ||
+          (u >= U::DS && !wait_bar<LP>(ctl, b_dfree(cd.slot), cd.par ^ 1u, 2))) {
         ok = false;
         break;
       }
@@ -1082,7 +1111,7 @@ __device__ void issuer_loop(const Ctl& ctl, uint32_t sbase, uint32_t tmem, int i
     const uint64_t dk2 = smem_desc(sbase + (luma ? SL::OFF_K2L : lo ? SL::OFF_K2CL : SL::OFF_K2CH), 128, 256, 0);
     const uint32_t idP2 = luma ? idesc_f16(128, 2 * L::N1, 0, 0) : idesc_f16(128, NCC, 0, 0);
     for (int u = 0; u < n; ++u, cd.next(), ce.next()) {
-      if (!wait_bar(ctl, luma ? b_a2l_full(ce.slot) : b_a2c_full(ce.slot), ce.par, 2)) {
+      if (!wait_bar<LP>(ctl, luma ? b_a2l_full(ce.slot) : b_a2c_full(ce.slot), ce.par, 2)) {
         ok = false;
         break;
       }
@@ -1107,7 +1136,7 @@ __device__ void issuer_loop(const Ctl& ctl, uint32_t sbase, uint32_t tmem, int i
   }
   if (!ok) {  // let this thread's MMAs finish before the CTA frees TMEM
     mma_commit(&ctl.bars[b_drain(id)]);
-    wait_bar(ctl, b_drain(id), 0, 2, true);
+    wait_bar<LP>(ctl, b_drain(id), 0, 2, true);
   }
 }
 
@@ -1281,7 +1310,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       int issued = 0;
       for (int t = 0; t < n_items; ++t) {
         const int stage = t % SL::kStages;
-        if (t >= SL::kStages && !wait_bar(ctl, b_raw_empty(stage), ((t / SL::kStages) - 1) & 1, 1, false, true))
+        if (t >= SL::kStages && !wait_bar<LP>(ctl, b_raw_empty(stage), ((t / SL::kStages) - 1) & 1, 1, false, true))
           break;
         const TileInfo ti = tile_info<C444>(ms, t, item0, step, SL::kStages);
         {
@@ -1317,7 +1346,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // convert warps waited for each tile, but a role that gave up on a wait no longer does.
       for (int t = (issued > SL::kStages ? issued - SL::kStages : 0); t < issued; ++t)
         if (item0 + t * step != p.withhold)
-          wait_bar(ctl, b_raw_full(t % SL::kStages), (t / SL::kStages) & 1, 1, true);
+          wait_bar<LP>(ctl, b_raw_full(t % SL::kStages), (t / SL::kStages) & 1, 1, true);
     }
   } else if (warp <= kIssuers) {
     // 4:4:4: the chroma issuers (stage 1 chroma: 2; stage 2 chroma hi, lo: 5, 6) have no work
