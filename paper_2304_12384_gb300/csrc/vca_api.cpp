@@ -193,15 +193,16 @@ struct vca_batch {
   uint8_t* h_desc[2] = {nullptr, nullptr};
   int* d_err = nullptr;            // the tensor-core kernel's wait-timeout flag
   int* h_err = nullptr;            // pinned, one per graph
-  // Tensor-core batches: the reduction's parameters, one launch per chunk of up to
-  // kMaxBatchMembers members, and their nodes in each graph.
-  std::vector<vca::ReduceBatchParams*> red;
-  std::vector<cudaGraphNode_t> red_node[2];
+  // Tensor-core batches: the frame reduction runs inside the analysis launches; per member its
+  // table entry (device), and per tick graph its accumulators and tile count (zero between ticks).
+  vca::TcRedMember* d_red = nullptr;
+  unsigned long long* d_red_acc = nullptr;  // [2][n][kRedSums][2]
+  unsigned int* d_red_done = nullptr;       // [2][n]
   std::vector<vca::TcMapCache*> tc_maps;  // per member: tensor maps of its recent frames
   double* d_feats = nullptr;       // CUDA-core batches: n x FEAT_STRIDE
   double* h_feats[2] = {nullptr, nullptr};  // pinned, per graph (tensor-core batches: mapped, + flag row)
   double* h_feats_dev[2] = {nullptr, nullptr};  // the device's view of h_feats (tensor-core batches)
-  unsigned long long* d_partials = nullptr;
+  unsigned long long* d_partials = nullptr;  // CUDA-core batches: the reduction's scratch
   int red_slices = 1;              // slices per frame of the batched reduction
   unsigned int* d_counters = nullptr;
   cudaGraph_t graph[2] = {nullptr, nullptr};
@@ -495,6 +496,10 @@ cudaError_t run_analysis(vca_analyzer* a, const FramePlanes& fp_in, int n, float
 // ---- batches ----------------------------------------------------------------------------
 
 // Delivers the features of the oldest tick in flight to its analyzers.
+// Bytes of a tensor-core batch's reduction accumulators: per tick graph and member, kRedSums sums
+// of two 64-bit parts.
+size_t red_acc_bytes(int n) { return 2 * (size_t)n * vca::kRedSums * 2 * sizeof(unsigned long long); }
+
 vca_status batch_harvest_front(vca_batch* b, bool blocking) {
   const vca_batch::Tick t = b->pending.front();
   if (blocking) {
@@ -507,6 +512,15 @@ vca_status batch_harvest_front(vca_batch* b, bool blocking) {
   const int code = b->tc ? (int)b->h_feats[t.k][(size_t)b->n * vca::FEAT_STRIDE] : b->h_err[t.k];
   if (code != 0) {
     b->h_err[t.k] = 0;
+    if (b->tc) {
+      // A tick that gave up leaves some members' sums and counts behind: clear graph t.k's set
+      // before that graph runs again (stream order; the other graph's set is its own).
+      cudaError_t e = cudaMemsetAsync(b->d_red_acc + (size_t)t.k * b->n * vca::kRedSums * 2, 0,
+                                      red_acc_bytes(b->n) / 2, b->stream);
+      if (e == cudaSuccess)
+        e = cudaMemsetAsync(b->d_red_done + (size_t)t.k * b->n, 0, (size_t)b->n * sizeof(unsigned int), b->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "clearing the reduction state of a failed tick");
+    }
     b->pending.pop_front();
     for (const auto& mm : t.members) {  // as for a single analyzer
       b->m[mm.index]->has_prev = 0;
@@ -572,7 +586,9 @@ void destroy_batch(vca_batch* b) {
   cudaFree(b->d_desc);
   cudaFree(b->d_err);
   if (b->h_err) cudaFreeHost(b->h_err);
-  for (vca::ReduceBatchParams* r : b->red) delete r;
+  cudaFree(b->d_red);
+  cudaFree(b->d_red_acc);
+  cudaFree(b->d_red_done);
   cudaFree(b->d_feats);
   cudaFree(b->d_partials);
   cudaFree(b->d_counters);
@@ -587,9 +603,9 @@ size_t feats_bytes(const vca_batch* b) {
   return (size_t)(b->n + (b->tc ? 1 : 0)) * vca::FEAT_STRIDE * sizeof(double);
 }
 
-// Builds tick graph k.  Tensor-core batches: node by node -- each branch's analysis launches one
-// after another, then the reductions, which depend on both branches.  CUDA-core batches: captured
-// -- upload the arguments, analyse, reduce, read the features back.
+// Builds tick graph k.  Tensor-core batches: node by node -- each branch's launches one after
+// another (each launch also reduces its members' frames to features).  CUDA-core batches:
+// captured -- upload the arguments, analyse, reduce, read the features back.
 cudaError_t build_tick_graph(vca_batch* b, int k) {
   if (b->tc) {
     cudaError_t e = cudaGraphCreate(&b->graph[k], 0);
@@ -603,17 +619,6 @@ cudaError_t build_tick_graph(vca_batch* b, int k) {
       const cudaGraphNode_t dep = tail[L.branch];
       e = cudaGraphAddKernelNode(&L.node[k], b->graph[k], dep ? &dep : nullptr, dep ? 1 : 0, &kp);
       tail[L.branch] = L.node[k];
-    }
-    std::vector<cudaGraphNode_t> deps;
-    for (cudaGraphNode_t t : tail)
-      if (t) deps.push_back(t);
-    b->red_node[k].assign(b->red.size(), nullptr);
-    for (size_t j = 0; e == cudaSuccess && j < b->red.size(); ++j) {
-      void* args[1] = {b->red[j]};
-      cudaKernelNodeParams kp;
-      e = vca::reduce_batch_params_node(b->red[j], args, &kp);
-      if (e == cudaSuccess)
-        e = cudaGraphAddKernelNode(&b->red_node[k][j], b->graph[k], deps.data(), deps.size(), &kp);
     }
     if (e != cudaSuccess) return e;
     return cudaGraphInstantiate(&b->exec[k], b->graph[k], 0);
@@ -1203,26 +1208,19 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
       return fail(VCA_E_NOMEM, "allocating tensor-map caches");
     }
   }
-  for (int c0 = 0; b->tc && c0 < n; c0 += vca::kMaxBatchMembers) {
-    vca::ReduceBatchParams* r = new (std::nothrow) vca::ReduceBatchParams();
-    if (!r) {
-      destroy_batch(b);
-      if (prev_dev >= 0) cudaSetDevice(prev_dev);
-      return fail(VCA_E_NOMEM, "host allocation failed");
-    }
-    b->red.push_back(r);
-    r->n = std::min(n - c0, vca::kMaxBatchMembers);
-    r->S = b->red_slices;
-    r->err = c0 == 0 ? b->d_err : nullptr;  // the first chunk hands the timeout flag over
-    r->err_out = nullptr;
-  }
-  if (!b->tc) {
+  if (b->tc) {
+    BATCH_CUDA(cudaMalloc(&b->d_red, (size_t)n * sizeof(vca::TcRedMember)), "allocating the reduction table");
+    BATCH_CUDA(cudaMalloc(&b->d_red_acc, red_acc_bytes(n)), "allocating reduction accumulators");
+    BATCH_CUDA(cudaMemset(b->d_red_acc, 0, red_acc_bytes(n)), "clearing reduction accumulators");
+    BATCH_CUDA(cudaMalloc(&b->d_red_done, 2 * (size_t)n * sizeof(unsigned int)), "allocating reduction counters");
+    BATCH_CUDA(cudaMemset(b->d_red_done, 0, 2 * (size_t)n * sizeof(unsigned int)), "clearing reduction counters");
+  } else {
     BATCH_CUDA(cudaMalloc(&b->d_desc, b->desc_bytes), "allocating tick arguments");
+    BATCH_CUDA(cudaMalloc(&b->d_feats, feats_bytes(b)), "allocating features");
+    BATCH_CUDA(cudaMalloc(&b->d_partials, vca::reduce_partials_bytes(n)), "allocating reduction scratch");
+    BATCH_CUDA(cudaMalloc(&b->d_counters, (size_t)n * sizeof(unsigned int)), "allocating counters");
+    BATCH_CUDA(cudaMemset(b->d_counters, 0, (size_t)n * sizeof(unsigned int)), "clearing counters");
   }
-  if (!b->tc) BATCH_CUDA(cudaMalloc(&b->d_feats, feats_bytes(b)), "allocating features");
-  BATCH_CUDA(cudaMalloc(&b->d_partials, vca::reduce_partials_bytes(n)), "allocating reduction scratch");
-  BATCH_CUDA(cudaMalloc(&b->d_counters, (size_t)n * sizeof(unsigned int)), "allocating counters");
-  BATCH_CUDA(cudaMemset(b->d_counters, 0, (size_t)n * sizeof(unsigned int)), "clearing counters");
   for (int k = 0; k < 2; ++k) {
     if (!b->tc) {
       BATCH_CUDA(cudaMallocHost(&b->h_desc[k], b->desc_bytes), "allocating pinned tick arguments");
@@ -1234,10 +1232,26 @@ vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch**
     if (b->tc) {
       BATCH_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&b->h_feats_dev[k]), b->h_feats[k], 0),
                  "mapping the features");
-      b->red[0]->err_out = b->h_feats_dev[k] + (size_t)n * vca::FEAT_STRIDE;
     }
     BATCH_CUDA(cudaEventCreateWithFlags(&b->ev[k], cudaEventDisableTiming), "creating batch events");
     BATCH_CUDA(build_tick_graph(b, k), "capturing the tick graph");
+  }
+  if (b->tc) {
+    std::vector<vca::TcRedMember> red((size_t)n);
+    for (int i = 0; i < n; ++i) {
+      const Geometry& g = members[i]->g;
+      vca::TcRedMember& r = red[(size_t)i];
+      for (int k = 0; k < 2; ++k) {
+        r.acc[k] = b->d_red_acc + ((size_t)k * n + i) * vca::kRedSums * 2;
+        r.done[k] = b->d_red_done + (size_t)k * n + i;
+        r.prevH[k] = members[i]->d_prevH[k];
+        r.feats[k] = b->h_feats_dev[k] + (size_t)i * vca::FEAT_STRIDE;
+      }
+      r.normY = (double)g.C * g.w * g.w;
+      r.normC = (double)g.C * g.ncv * g.nc;
+    }
+    BATCH_CUDA(cudaMemcpy(b->d_red, red.data(), red.size() * sizeof(vca::TcRedMember), cudaMemcpyHostToDevice),
+               "uploading the reduction table");
   }
 #undef BATCH_CUDA
   for (int i = 0; i < n; ++i) members[i]->batch = b;
@@ -1260,45 +1274,50 @@ vca_status vca_batch_tick(vca_batch* b, const vca_frame_ref* frames) {
     if (s != VCA_OK) return fail(s, "frame of analyzer %d: %s", i, vca_last_error());
   }
   auto* ma = b->tc ? nullptr : reinterpret_cast<vca::BatchMemberArgs*>(b->h_desc[k]);
-  auto* ra_plain = b->tc ? nullptr : reinterpret_cast<vca::ReduceArgs*>(b->h_desc[k] + b->ma_bytes);
-  // A member's reduction arguments: its chunk's parameters (tensor-core) or the uploaded array.
-  auto ra = [&](int i) -> vca::ReduceArgs& {
-    return b->tc ? b->red[i / vca::kMaxBatchMembers]->a[i % vca::kMaxBatchMembers] : ra_plain[i];
-  };
+  auto* ra = b->tc ? nullptr : reinterpret_cast<vca::ReduceArgs*>(b->h_desc[k] + b->ma_bytes);
   vca_batch::Tick tick;
   tick.k = k;
   for (auto& L : b->tcl) L.frames.clear();
   for (int i = 0; i < b->n; ++i) {
     vca_analyzer* a = b->m[i];
     if (!frames[i].y) {
-      if (!b->tc) ma[i].active = 0;
-      ra(i).nframes = 0;
+      if (!b->tc) {
+        ma[i].active = 0;
+        ra[i].nframes = 0;
+      }
       continue;
     }
     if (b->tc) {
+      // The launch reduces the frame too: the member's table entry, whether it has a previous
+      // frame and which of its buffers holds that frame's energies, and the graph's state set.
       const vca_frame_ref& f = frames[i];
+      const int flags = (a->has_prev ? vca::kRedHasPrev : 0) | (a->cur_prev ? vca::kRedPrevBuf : 0) |
+                        (k ? vca::kRedGraph : 0);
       b->tcl[b->tcl_of[i]].frames.push_back({&a->g,
                               {static_cast<const uint8_t*>(f.y), static_cast<const uint8_t*>(f.u),
                                static_cast<const uint8_t*>(f.v), f.pitch_y, f.pitch_uv, 0, 0},
-                              a->d_blockvals, b->tc_maps[i]});
+                              a->d_blockvals, b->tc_maps[i], i, flags});
     } else {
       ma[i].pa[0] = member_plain_args(a, 0, frames[i]);
       ma[i].pa[1] = member_plain_args(a, 1, frames[i]);
       ma[i].bps = a->g.bps;
       ma[i].active = 1;
+      ra[i] = vca::reduce_args(a->g, 1, a->d_blockvals, a->d_prevH[a->cur_prev], a->has_prev,
+                               a->d_prevH[a->cur_prev ^ 1], b->d_feats + (size_t)i * vca::FEAT_STRIDE,
+                               b->d_partials + (size_t)i * vca::reduce_partials_bytes(1) / sizeof(unsigned long long),
+                               b->d_counters + i);
     }
-    ra(i) = vca::reduce_args(a->g, 1, a->d_blockvals, a->d_prevH[a->cur_prev], a->has_prev,
-                             a->d_prevH[a->cur_prev ^ 1],
-                             (b->tc ? b->h_feats_dev[k] : b->d_feats) + (size_t)i * vca::FEAT_STRIDE,
-                             b->d_partials + (size_t)i * vca::reduce_partials_bytes(1) / sizeof(unsigned long long),
-                             b->d_counters + i);
     tick.members.push_back({i, a->frames_pushed, a->has_prev != 0});
   }
   int grid[2] = {b->sms, b->sms};
+  // The tick's timeout flag, beside the features in mapped memory: the launches set it only when a
+  // wait runs out (graph k's previous tick has been read).
+  if (b->tc) b->h_feats[k][(size_t)b->n * vca::FEAT_STRIDE] = 0.0;
   for (size_t li = 0; li < b->tcl.size(); ++li) {
     auto& L = b->tcl[li];
     cudaError_t e = vca::tc_batch_fill(L.params.data(), L.frames.data(), (int)L.frames.size(), b->m[0]->tables,
-                                       b->d_err, b->dbg_wait_ns, li == 0 ? b->dbg_withhold : -1);
+                                       b->d_err, b->d_red, b->h_feats_dev[k] + (size_t)b->n * vca::FEAT_STRIDE,
+                                       b->dbg_wait_ns, li == 0 ? b->dbg_withhold : -1);
     if (e != cudaSuccess) return cuda_fail(e, "encoding the tensor maps of a batch tick");
   }
   b->dbg_withhold = -1;  // one tick only
@@ -1326,16 +1345,6 @@ vca_status vca_batch_tick(vca_batch* b, const vca_frame_ref* frames) {
     if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(b->exec[k], L.node[k], &kp);
     if (e != cudaSuccess) return cuda_fail(e, "setting the parameters of a batch tick");
   }
-  if (b->tc) {
-    b->red[0]->err_out = b->h_feats_dev[k] + (size_t)b->n * vca::FEAT_STRIDE;
-    for (size_t j = 0; j < b->red.size(); ++j) {
-      void* args[1] = {b->red[j]};
-      cudaKernelNodeParams kp;
-      cudaError_t e = vca::reduce_batch_params_node(b->red[j], args, &kp);
-      if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(b->exec[k], b->red_node[k][j], &kp);
-      if (e != cudaSuccess) return cuda_fail(e, "setting the reduction parameters of a batch tick");
-    }
-  }
   int prev_dev = -1;
   cudaGetDevice(&prev_dev);
   if (prev_dev != b->device) VCA_CUDA(cudaSetDevice(b->device), "selecting the batch device");
@@ -1354,8 +1363,9 @@ vca_status vca_batch_tick(vca_batch* b, const vca_frame_ref* frames) {
   b->pending.push_back(std::move(tick));
   b->next_k ^= 1;
   b->ticks += 1;
-  // analysis (tensor-core: one launch per sample size and chunk), reduction (one per chunk)
-  b->launches += b->tc ? (int64_t)(b->tcl.size() + b->red.size()) : 2;
+  // tensor-core: one launch (analysis and reduction) per sample size and chunk; CUDA-core: analysis
+  // and reduction
+  b->launches += b->tc ? (int64_t)b->tcl.size() : 2;
   return VCA_OK;
 }
 

@@ -125,19 +125,41 @@ bool tc_supported(const Geometry& g);
 struct TcMapCache;
 TcMapCache* tc_map_cache_new();
 void tc_map_cache_free(TcMapCache* c);
+// Members of one batched tensor-core launch (a tick with more members of one sample size takes
+// several launches).
+constexpr int kMaxBatchMembers = 64;
 struct TcBatchFrame {
   const Geometry* g;   // the member's analysis geometry (tc_supported)
   FramePlanes fp;      // its frame (frame strides unused)
   float* blockvals;    // its [6][C] block values
   TcMapCache* maps;    // the member's map cache, or null to encode every tick
+  int red;             // its entry in the batch's TcRedMember table
+  int red_flags;       // kRedHasPrev | kRedPrevBuf * (previous energies in prevH[1]) | kRedGraph * k
 };
+// Frame reduction fused into a batched tensor-core tick, per member (device memory, written when
+// the batch is made).  At the end of the launch each CTA adds the exact fixed-point sums of its
+// own tiles' block values (and of |dH_Y|, reading the previous energies and writing this tick's)
+// to the member's accumulators and counts its tiles; the CTA that completes the count writes the
+// features and leaves the accumulators and the count at zero.  Tick graph k uses acc[k], done[k],
+// feats[k], so that a tick that failed leaves the other graph's state clean.
+struct TcRedMember {
+  unsigned long long* acc[2];  // kRedSums x (low 32-bit part, rest) totals
+  unsigned int* done[2];       // tiles counted
+  float* prevH[2];             // the analyzer's two previous-energy buffers
+  double* feats[2];            // the member's feature row (FEAT_STRIDE doubles; mapped host memory)
+  double normY, normC;         // C w^2 and C Nv Nh
+};
+constexpr int kRedSums = 7;  // H_Y, L_Y, H_U, L_U, H_V, L_V, |dH_Y|
+constexpr int kRedHasPrev = 1, kRedPrevBuf = 2, kRedGraph = 4;
 int tc_batch_max_members();
 size_t tc_batch_params_bytes();
 // Fills the parameter block at params (host memory, tc_batch_params_bytes()) for n frames, the
-// DCT tables t and the device error flag err; cudaErrorInvalidValue if n is out of range, the
-// frames' sample sizes differ or a tensor map cannot be encoded.
+// DCT tables t, the device error flag err, the fused reduction's member table red (device) and
+// err_host (the tick's flag in mapped host memory, set to the code of a wait that ran out);
+// cudaErrorInvalidValue if n is out of range, the frames' sample sizes differ or a tensor map
+// cannot be encoded.
 cudaError_t tc_batch_fill(void* params, const TcBatchFrame* frames, int n, const DeviceTables& t, int* err,
-                          long long wait_ns = 0, int withhold = -1);
+                          const TcRedMember* red, double* err_host, long long wait_ns = 0, int withhold = -1);
 // Sets up the kernel instance for this sample size and low_pass (outside any stream capture).
 cudaError_t tc_batch_prepare(int w, bool c444, int bps, bool low_pass);
 // Work items (128x128 luma tiles) of a filled parameter block.
@@ -169,22 +191,6 @@ ReduceArgs reduce_args(const Geometry& g, int nframes, const float* blockvals, c
 cudaError_t launch_reduce_batch(const ReduceArgs* d_args, int n, int slices, cudaStream_t s);
 // Slices per frame of a batched reduction whose largest member has max_C blocks per plane.
 int reduce_batch_slices(int64_t max_C);
-
-// The same batched reduction with its arguments as kernel parameters (a chunk of at most
-// kMaxBatchMembers analyzers of a batch), so that a tick's graph needs no upload of them: a[m] as above for
-// m < n, S slices per frame.  The launch also hands the analysis kernel's wait-timeout flag to
-// the host: one thread copies *err into *err_out (as a double, next to the features the tick
-// reads back) and clears *err for the next tick.  err may be null.
-constexpr int kMaxBatchMembers = 64;
-struct ReduceBatchParams {
-  ReduceArgs a[kMaxBatchMembers];
-  int n, S;
-  int* err;
-  double* err_out;
-};
-// Kernel-node parameters of the batched reduction of p (p.n members x p.S slices; args[0] points
-// at p), for a graph built node by node.
-cudaError_t reduce_batch_params_node(const ReduceBatchParams* p, void** args, cudaKernelNodeParams* kp);
 
 // One CTA of the batched plain kernel: analyzer `member`, plane kind (0 luma, 1 chroma), plane
 // within the kind (chroma: 0 U, 1 V) and block chunk (BPC blocks).

@@ -20,6 +20,7 @@
 #include <mutex>
 
 #include "vca.h"
+#include "vca_fixed.cuh"
 #include "vca_internal.h"
 
 namespace vca {
@@ -29,47 +30,11 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxSlices = 32;
 constexpr int64_t kSliceBlocks = 512;
-constexpr int kSums = 7;  // H_Y, L_Y, H_U, L_U, H_V, L_V, |dH_Y|
 
 // Slices of a frame of C blocks.
 int slices_for(int64_t C) {
   const int64_t s = (C + kSliceBlocks - 1) / kSliceBlocks;
   return (int)(s < 1 ? 1 : s > kMaxSlices ? kMaxSlices : s);
-}
-
-// v * 2^23 truncated to an integer, for a block value v in [0, 2^30): the significand shifted by
-// the unbiased exponent.  Every value the analyzer writes is 0 or at least 1 (a multiple of
-// 2^-23), so nothing is truncated for them.  Values outside [0, 2^30) -- negative (also -0.0),
-// NaN, infinite or 2^30 and above -- and values below 2^-24 count as 0.
-__device__ __forceinline__ unsigned long long fixed23(float v) {
-  const uint32_t b = __float_as_uint(v);
-  const int e = (int)(b >> 23) - 127;  // 128 for NaN and infinities
-  if ((b >> 31) != 0u || e >= 30 || e < -24) return 0ull;
-  const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
-  return e >= 0 ? m << e : m >> -e;
-}
-
-struct U128 {
-  unsigned long long lo, hi;
-};
-
-__device__ __forceinline__ void add_to(U128& a, unsigned long long v) {
-  asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, 0;" : "+l"(a.lo), "+l"(a.hi) : "l"(v));
-}
-
-__device__ __forceinline__ void add_to(U128& a, const U128& b) {
-  asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(a.lo), "+l"(a.hi) : "l"(b.lo), "l"(b.hi));
-}
-
-// The 128-bit integer as the nearest double (ties to even): its leading 64 bits, with a sticky
-// bit for anything below them, rounded once by the 64-bit conversion and scaled.
-__device__ __forceinline__ double to_double(const U128& a) {
-  if (a.hi == 0ull) return __ull2double_rn(a.lo);
-  const int lz = __clzll((long long)a.hi);
-  const unsigned long long top = lz ? (a.hi << lz) | (a.lo >> (64 - lz)) : a.hi;
-  const unsigned long long rest = lz ? a.lo << lz : a.lo;
-  const double scale = __hiloint2double((1023 + 64 - lz) << 20, 0);  // 2^(64 - lz)
-  return __ull2double_rn(top | (rest != 0ull ? 1ull : 0ull)) * scale;
 }
 
 // Slice `slice` of S of frame f (one CTA of kThreads threads).  partials: [frame][kMaxSlices][kSums]
@@ -136,20 +101,10 @@ __device__ __forceinline__ void reduce_slice(const ReduceArgs& a, int f, int sli
   if (tid < kSums) {  // thread r: sum r -> its feature (E_Y, h, L_Y, E_U, E_V, L_U, L_V)
     U128 t{0ull, 0ull};
     for (int sl = 0; sl < S; ++sl) add_to(t, slice_tot[sl][tid]);
-    const double total = to_double(t) * 1.1920928955078125e-07;  // x 2^-23 (exact)
     int slot;
-    double norm;
-    switch (tid) {
-      case ROW_H_Y: slot = 0; norm = a.normY; break;
-      case ROW_L_Y: slot = 2; norm = (double)C; break;
-      case ROW_H_U: slot = 3; norm = a.normC; break;
-      case ROW_L_U: slot = 5; norm = (double)C; break;
-      case ROW_H_V: slot = 4; norm = a.normC; break;
-      case ROW_L_V: slot = 6; norm = (double)C; break;
-      default: slot = 1; norm = a.normY; break;  // the |dH_Y| sum: h
-    }
+    const double value = feature_of_sum(tid, t, (double)C, a.normY, a.normC, slot);
     double* out = a.feats + (int64_t)f * FEAT_STRIDE;
-    out[slot] = total / norm;
+    out[slot] = value;
     if (tid == 0) {
       out[7] = 0.0;
       a.counters[f] = 0;  // ready for the next launch (stream order separates launches)
@@ -174,32 +129,7 @@ __global__ void __launch_bounds__(kThreads) reduce_batch_kernel(const ReduceArgs
   reduce_slice(a, 0, blockIdx.x % S, S);
 }
 
-// The same with the members' arguments in the kernel parameters; also hands over the analysis
-// kernel's timeout flag (the analysis launches of the tick have finished before this one starts,
-// and the next tick's start after it ends).
-__global__ void __launch_bounds__(kThreads) reduce_batch_params_kernel_(const __grid_constant__ ReduceBatchParams p) {
-  if (blockIdx.x == 0 && threadIdx.x == 0 && p.err) {
-    *p.err_out = (double)*p.err;
-    *p.err = 0;
-  }
-  const ReduceArgs& a = p.a[blockIdx.x / p.S];
-  if (a.nframes == 0) return;
-  reduce_slice(a, 0, blockIdx.x % p.S, p.S);
-}
-
 }  // namespace
-
-cudaError_t reduce_batch_params_node(const ReduceBatchParams* p, void** args, cudaKernelNodeParams* kp) {
-  if (p->n <= 0 || p->n > kMaxBatchMembers || p->S < 1 || p->S > kMaxSlices) return cudaErrorInvalidValue;
-  *kp = cudaKernelNodeParams{};
-  kp->func = (void*)reduce_batch_params_kernel_;
-  kp->gridDim = dim3((unsigned)(p->n * p->S));
-  kp->blockDim = dim3(kThreads);
-  kp->sharedMemBytes = 0;
-  kp->kernelParams = args;
-  kp->extra = nullptr;
-  return cudaSuccess;
-}
 
 size_t reduce_partials_bytes(int max_frames) { return (size_t)max_frames * kMaxSlices * kSums * 16; }
 

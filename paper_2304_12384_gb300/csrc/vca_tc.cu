@@ -71,6 +71,7 @@
 #include <mutex>
 #include <new>
 
+#include "vca_fixed.cuh"
 #include "vca_internal.h"
 #include "vca_ptx.cuh"
 
@@ -101,6 +102,8 @@ struct TcMember {
   int W, H, cw, ch, nbx, nby;
   int64_t C, out_fstride;
   float* blockvals;
+  int red, red_flags;              // batched ticks: entry in the fused reduction's table, flags
+  int pad_[2];
 };
 
 // Stage-1 shift s1 = log2 N + B - 9 of an N-point transform; the bit depth follows from the sample
@@ -197,6 +200,8 @@ struct TcParamsT {
   const float* W_y;
   const float* W_c;
   int* err;
+  const TcRedMember* red;  // batched ticks: the fused reduction's member table (device)
+  double* err_host;        // batched ticks: the tick's timeout flag (mapped host memory), or null
   long long wait_ns;  // limit of every bounded wait
   int withhold;       // work item whose copies the producer does not issue (-1: none; failure-path tests)
   int n_members, total_items;
@@ -261,12 +266,14 @@ struct Ctl {
   uint64_t* bars;
   volatile int* abort;
   int* err;
+  double* err_host;  // also set on timeout, if not null (batched ticks)
   uint64_t wait_ns;
 };
 
 // Bounded wait: false on timeout (flag raised) or when another role aborted.
 __device__ __forceinline__ bool wait_bar_poll(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
-                                              int code, bool ignore_abort, bool sleep, uint64_t wait_ns) {
+                                              double* err_host, int code, bool ignore_abort, bool sleep,
+                                              uint64_t wait_ns) {
   const uint64_t t0 = now_ns();
   for (;;) {
 #pragma unroll 1
@@ -276,14 +283,16 @@ __device__ __forceinline__ bool wait_bar_poll(uint64_t* bar, uint32_t parity, vo
     if (now_ns() - t0 > wait_ns) {
       *abort_flag = 1;
       atomicOr(err, code);
+      if (err_host) *err_host = (double)code;
       return false;
     }
   }
 }
 
 __device__ __noinline__ bool wait_bar_slow(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
-                                          int code, bool ignore_abort, bool sleep, uint64_t wait_ns) {
-  return wait_bar_poll(bar, parity, abort_flag, err, code, ignore_abort, sleep, wait_ns);
+                                          double* err_host, int code, bool ignore_abort, bool sleep,
+                                          uint64_t wait_ns) {
+  return wait_bar_poll(bar, parity, abort_flag, err, err_host, code, ignore_abort, sleep, wait_ns);
 }
 
 // Bounded wait on barrier idx.  Roles on the critical path spin; the producer (sleep = true) lets
@@ -297,9 +306,9 @@ __device__ __forceinline__ bool wait_bar(const Ctl& c, int idx, uint32_t parity,
   uint64_t* bar = c.bars + idx;
   if (sleep ? mbar_try_wait_sleep(bar, parity) : mbar_try_wait(bar, parity)) return true;
   if constexpr (INL)
-    return wait_bar_poll(bar, parity, c.abort, c.err, code, ignore_abort, sleep, c.wait_ns);
+    return wait_bar_poll(bar, parity, c.abort, c.err, c.err_host, code, ignore_abort, sleep, c.wait_ns);
   else
-    return wait_bar_slow(bar, parity, c.abort, c.err, code, ignore_abort, sleep, c.wait_ns);
+    return wait_bar_slow(bar, parity, c.abort, c.err, c.err_host, code, ignore_abort, sleep, c.wait_ns);
 }
 
 // Byte offset of sample xx of row y of the raw tile of this plane type.
@@ -439,17 +448,52 @@ __device__ __forceinline__ void epilogue1(const uint32_t (&td1)[J], const uint32
   }
 }
 
+// The block value a thread of epilogue 2 stores, at most one (e2_store_job: of which job): without
+// super-blocks the v = 0 thread of a block's NK lanes stores job 0's block and its v = NK/2 thread
+// job 1's; with super-blocks (G = NK/2 lanes per block column group) lanes v = 0, G/4, G/2, 3G/4
+// of the group store the top and bottom blocks of job 0, then of job 1.
+template <bool SUB, int NK>
+__device__ __forceinline__ int e2_store_job(int lane) {
+  if constexpr (SUB) {
+    constexpr int G = NK / 2;
+    return ((lane % NK) % G) / (G / 4) >> 1;
+  } else {
+    return ((lane % NK) & (NK / 2)) ? 1 : 0;
+  }
+}
+
+// This thread's store address for epilogue 2 (H at o[0], L at o[C]) without super-blocks: out[j]
+// is job j's block of this thread's rows (null outside the frame).
+template <int NK>
+__device__ __forceinline__ float* e2_store(int lane, float* const (&out)[2]) {
+  return ((lane % NK) & (NK / 2 - 1)) == 0 ? out[e2_store_job<false, NK>(lane)] : nullptr;
+}
+
+// The same for super-blocks: sb[j] is job j's super-block (x, y in super-blocks, x < 0: none),
+// orow[j] the output row of its plane; null for threads that store nothing or blocks outside the
+// frame.
+template <int NK>
+__device__ __forceinline__ float* e2_store_sub(int lane, const int2 (&sb)[2], float* const (&orow)[2], int nbx,
+                                               int nby) {
+  constexpr int G = NK / 2;
+  const int vp = lane % NK, v = vp % G;
+  if ((v % (G / 4)) != 0) return nullptr;
+  const int quarter = v / (G / 4);
+  const int j = quarter >> 1, dy = quarter & 1;
+  const int bx = 2 * sb[j].x + vp / G, by = 2 * sb[j].y + dy;
+  if (!orow[j] || sb[j].x < 0 || bx >= nbx || by >= nby) return nullptr;
+  return orow[j] + (int64_t)by * nbx + bx;
+}
+
 // Epilogue 2 of two jobs of one plane type (luma: both luma jobs; chroma: U and V): for job j the
 // stage-2 accumulators hi at td2[j] and lo at td2[j] + LO form Z, the row sums of w(u, v) |Z| in
-// increasing u and the block energy H by an xor tree over the NK rows of the block; the block's
-// v = 0 thread stores job 0's H at out[0][0] and L = sqrt(Z(0,0)) at out[0][C], its v = NK/2
-// thread job 1's at out[1] (null: block outside the frame).  DUMP: the coefficients to zd[j]
-// (u-major) as well.  The TMEM loads of the next 8 columns are in flight while the current ones
-// are processed.
+// increasing u and the block energy H by an xor tree over the NK rows of the block; a thread with
+// a store address o (e2_store) writes its block's H at o[0] and L = sqrt(Z(0,0)) at o[C].  DUMP:
+// the coefficients to zd[j] (u-major) as well.  The TMEM loads of the next 8 columns are in flight
+// while the current ones are processed.
 template <int Nb, bool LP, bool DUMP, int LO>
 __device__ __forceinline__ void epilogue2(const uint32_t (&td2)[2], int lane, const float (&wts)[PC<Nb, LP>::NK],
-                                          float einv, float c2, float* const (&out)[2], int64_t C,
-                                          int16_t* const (&zd)[2]) {
+                                          float einv, float c2, float* o, int64_t C, int16_t* const (&zd)[2]) {
   using P = PC<Nb, LP>;
   constexpr int NK = P::NK;
   constexpr int CPJ = NK / 8;  // 8-column chunks per job
@@ -504,8 +548,7 @@ __device__ __forceinline__ void epilogue2(const uint32_t (&td2)[2], int lane, co
   // job 1's Z(0,0) (held by its v = 0 lane) to the block's v = NK/2 lane; one square root for both
   const float z1 = __shfl_xor_sync(0xffffffffu, z00, NK / 2);
   const float L = __fsqrt_rn(upper ? z1 : z0);
-  float* const o = upper ? out[1] : out[0];
-  if (o && (v & (NK / 2 - 1)) == 0) {
+  if (o) {
     o[0] = X;
     o[C] = L;
   }
@@ -517,13 +560,13 @@ __device__ __forceinline__ void epilogue2(const uint32_t (&td2)[2], int lane, co
 // and dimension), and rows u' < G of the top blocks, u' >= G of the bottom ones.  Each thread sums
 // w(u, v) |Z| in increasing u separately for the top and bottom block of each job; four xor trees
 // over the G lanes of a block, merged into one shuffle sequence, give the energies of the top and
-// bottom blocks of both jobs, which lanes 0, G/4, G/2, 3G/4 of the G-lane group store (with L =
-// sqrt(Z(0,0)) of the block).  sb[j]: super-block of job j (x, y in super-blocks); orow[j]: the
-// output row of H (L follows at + C); zd[j]: the coefficient dump of the plane (DUMP, frame 0).
+// bottom blocks of both jobs, which lanes 0, G/4, G/2, 3G/4 of the G-lane group store at their
+// address o (e2_store_sub; H at o[0], L = sqrt(Z(0,0)) of the block at o[C]).  sb[j]: super-block
+// of job j (x, y in super-blocks); zd[j]: the coefficient dump of the plane (DUMP, frame 0).
 template <int Nb, bool LP, bool DUMP, int LO>
 __device__ __forceinline__ void epilogue2_sub(const uint32_t (&td2)[2], int lane, const float (&wts)[PC<Nb, LP>::NK / 2],
-                                              float einv, float c2, const int2 (&sb)[2], float* const (&orow)[2],
-                                              int nbx, int nby, int64_t C, int16_t* const (&zd)[2]) {
+                                              float einv, float c2, const int2 (&sb)[2], float* o, int nbx, int nby,
+                                              int64_t C, int16_t* const (&zd)[2]) {
   using P = PC<Nb, LP>;
   constexpr int NK = P::NK;
   constexpr int G = NK / 2;
@@ -587,15 +630,10 @@ __device__ __forceinline__ void epilogue2_sub(const uint32_t (&td2)[2], int lane
   const float zt1 = __shfl_xor_sync(0xffffffffu, zt[1], G / 2);
   const float zb1 = __shfl_xor_sync(0xffffffffu, zb[1], 3 * G / 4);
   const int quarter = v / (G / 4);
-  if ((v % (G / 4)) == 0) {
-    const int j = quarter >> 1, dy = quarter & 1;
-    const float z = quarter == 0 ? zt[0] : quarter == 1 ? zb0 : quarter == 2 ? zt1 : zb1;
-    const int bx = 2 * sb[j].x + vp / G, by = 2 * sb[j].y + dy;
-    if (orow[j] && sb[j].x >= 0 && bx < nbx && by < nby) {
-      const int64_t k = (int64_t)by * nbx + bx;
-      orow[j][k] = R;
-      orow[j][C + k] = __fsqrt_rn(z);
-    }
+  const float z = quarter == 0 ? zt[0] : quarter == 1 ? zb0 : quarter == 2 ? zt1 : zb1;
+  if (o) {
+    o[0] = R;
+    o[C] = __fsqrt_rn(z);
   }
 }
 
@@ -613,8 +651,8 @@ __device__ __forceinline__ int div_small(int a, int b, float binv) {
 }
 
 // The members of a launch as the roles see them.  A single analyzer's launch reads its one member
-// from the kernel parameters (fields become constant-bank operands); a batched launch reads the
-// member table that the CTA copied into shared memory.
+// from the kernel parameters (fields become constant-bank operands); a batched launch indexes the
+// member table in the kernel parameters.
 struct OneMember {
   const TcMember& m0;
   __device__ __forceinline__ int member_of(int) const { return 0; }
@@ -913,19 +951,20 @@ __device__ void epi2_luma_loop(const PP& p, const MS& ms, const TileRec* recs, c
     const int plane = C444 ? rec.hc : 0;  // the rows H, L of Y (0), U (1) or V (2)
     float* const base = M.blockvals + (int64_t)rec.f * M.out_fstride + (int64_t)(2 * plane) * M.C;
     uint32_t td2[2];
-    float* out[2];
     int16_t* zd[2];
     if constexpr (SUB) {
       int2 sb[2];
+      float* const orow[2] = {base, base};
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         sb[j] = superblock_of<P::NK, P::BPG2>(rec, h * 2 + j, q, lane);
         td2[j] = td + 2 * j * P::N1;
-        out[j] = base;
         zd[j] = (DUMP && rec.f == 0) ? p.zdump[plane] : nullptr;
       }
-      epilogue2_sub<32, LP, DUMP, P::N1>(td2, lane, w, einv, kK1 - kK1 * einv, sb, out, M.nbx, M.nby, M.C, zd);
+      float* const o = e2_store_sub<P::NK>(lane, sb, orow, M.nbx, M.nby);
+      epilogue2_sub<32, LP, DUMP, P::N1>(td2, lane, w, einv, kK1 - kK1 * einv, sb, o, M.nbx, M.nby, M.C, zd);
     } else {
+      float* out[2];
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const int64_t k = block_of<P::NK, P::BPG2>(M, rec, h * 2 + j, q, lane);
@@ -933,7 +972,7 @@ __device__ void epi2_luma_loop(const PP& p, const MS& ms, const TileRec* recs, c
         out[j] = k >= 0 ? base + k : nullptr;
         zd[j] = (DUMP && k >= 0 && rec.f == 0) ? p.zdump[plane] + k * P::NK * P::NK : nullptr;
       }
-      epilogue2<32, LP, DUMP, P::N1>(td2, lane, w, einv, kK1 - kK1 * einv, out, M.C, zd);
+      epilogue2<32, LP, DUMP, P::N1>(td2, lane, w, einv, kK1 - kK1 * einv, e2_store<P::NK>(lane, out), M.C, zd);
     }
     tc_fence_before();
     __syncwarp();
@@ -998,27 +1037,28 @@ __device__ void chroma_epi_loop(const PP& p, const MS& ms, const TileRec* recs, 
       const uint32_t td = tq + U::d(cd2.slot) + U::DC;
       float* const base = M.blockvals + (int64_t)rec.f * M.out_fstride;
       uint32_t td2[2];
-      float* out[2];
       int16_t* zd[2];
       if constexpr (SUB) {
         const int2 sb0 = superblock_of<P::NK, P::BPG2>(rec, h, q, lane);  // U and V share the super-block
         const int2 sb[2] = {sb0, sb0};
+        float* const orow[2] = {base + 2 * M.C, base + 4 * M.C};
 #pragma unroll
         for (int pl = 0; pl < 2; ++pl) {
           td2[pl] = td + pl * NKC;
-          out[pl] = base + (2 + 2 * pl) * M.C;
           zd[pl] = (DUMP && rec.f == 0) ? p.zdump[1 + pl] : nullptr;
         }
-        epilogue2_sub<16, LP, DUMP, NCC>(td2, lane, w, einv, kK1 - kK1 * einv, sb, out, M.nbx, M.nby, M.C, zd);
+        float* const o = e2_store_sub<P::NK>(lane, sb, orow, M.nbx, M.nby);
+        epilogue2_sub<16, LP, DUMP, NCC>(td2, lane, w, einv, kK1 - kK1 * einv, sb, o, M.nbx, M.nby, M.C, zd);
       } else {
         const int64_t k = block_of<P::NK, P::BPG2>(M, rec, h, q, lane);  // U and V share the block
+        float* out[2];
 #pragma unroll
         for (int pl = 0; pl < 2; ++pl) {
           td2[pl] = td + pl * NKC;
           out[pl] = k >= 0 ? base + (2 + 2 * pl) * M.C + k : nullptr;
           zd[pl] = (DUMP && k >= 0 && rec.f == 0) ? p.zdump[1 + pl] + k * P::NK * P::NK : nullptr;
         }
-        epilogue2<16, LP, DUMP, NCC>(td2, lane, w, einv, kK1 - kK1 * einv, out, M.C, zd);
+        epilogue2<16, LP, DUMP, NCC>(td2, lane, w, einv, kK1 - kK1 * einv, e2_store<P::NK>(lane, out), M.C, zd);
       }
       tc_fence_before();
       __syncwarp();
@@ -1140,6 +1180,149 @@ __device__ void issuer_loop(const Ctl& ctl, uint32_t sbase, uint32_t tmem, int i
   }
 }
 
+// ---- frame reduction of a batched tick, in each CTA's tail (see TcRedMember) ----------------
+//
+// After its role loops a CTA reduces the block values of its own tiles, still in L2.  Its run of
+// tiles covers one or more members ("segments"); all segments go through each step together, so
+// the tail costs a few memory round trips however many members the run touches:
+//   1. every thread takes one block at a time: fixed23 of the six rows (4:4:4: of its plane's two)
+//      and, for luma rows, |H - H_prev|, writing H as the next tick's previous energy; a warp
+//      whose 32 blocks are of one segment adds its warp sums to the segment's totals in shared
+//      memory, other warps add per thread (the totals kept as low-32-bit and high parts, exact);
+//   2. the totals of every segment go to the members' accumulators in global memory;
+//   3. one count per segment (its tiles); the CTA whose count completes a member
+//   4. writes the features -- the same exact totals, rounded once, as the separate frame
+//      reduction -- and leaves the accumulators and the count at zero.
+// The epilogues carry none of this: on the tensor-core pipeline's critical path every added
+// instruction or load costs far more than here (sums kept per unit in the epilogue-2 warps made
+// the batched launches a third slower).
+
+// Exact sum over the warp of per-thread values below 2^59 (the total is below 2^64): three 21-bit
+// limbs, each summed by one warp reduction (limb totals below 2^26).
+__device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
+  const unsigned a = __reduce_add_sync(0xffffffffu, (unsigned)(v & 0x1FFFFFull));
+  const unsigned b = __reduce_add_sync(0xffffffffu, (unsigned)((v >> 21) & 0x1FFFFFull));
+  const unsigned c = __reduce_add_sync(0xffffffffu, (unsigned)(v >> 42));
+  return (unsigned long long)a + ((unsigned long long)b << 21) + ((unsigned long long)c << 42);
+}
+
+// Adds v to a total kept as (sum of low 32-bit parts, sum of the rest) at t[0], t[1].
+__device__ __forceinline__ void add_split(unsigned long long* t, unsigned long long v) {
+  atomicAdd(t, v & 0xFFFFFFFFull);
+  atomicAdd(t + 1, v >> 32);
+}
+
+// scratch: shared memory (the raw ring, no longer in use) for kMaxMembers segments x kRedSums
+// split totals and a flag per segment.  Blocks are taken kThreads at a time, one per thread.
+template <bool SUB, bool C444, class PP>
+__device__ __noinline__ void red_tail(const PP& p, int item0, int n_items, unsigned long long* scratch) {
+  constexpr int BPT = SUB ? 8 : 4;  // blocks per tile side
+  constexpr int BPT2 = BPT * BPT;
+  const int tid = threadIdx.x, lane = tid & 31;
+  int* flags = reinterpret_cast<int*>(scratch + kMaxMembers * kRedSums * 2);
+  if (n_items <= 0) return;
+  MemberTable ms{p.mem, p.n_members, 0};
+  const int m0 = ms.member_of(item0);
+  const int nseg = ms.member_of(item0 + n_items - 1) - m0 + 1;
+  for (int i = tid; i < nseg * kRedSums * 2; i += kThreads) scratch[i] = 0ull;
+  __syncthreads();
+  // 1. blocks -> per-segment totals in shared memory
+  MemberTable mt{p.mem, p.n_members, m0};
+  const int nblocks = n_items * BPT2;
+  for (int base = 0; base < nblocks; base += kThreads) {
+    const int i = base + tid;
+    unsigned long long v[kRedSums];
+#pragma unroll
+    for (int r = 0; r < kRedSums; ++r) v[r] = 0ull;
+    int seg = -1;
+    if (i < nblocks) {
+      const int item = item0 + i / BPT2, b = i % BPT2;
+      const int m = mt.member_of(item);
+      const TcMember& M = mt[m];
+      seg = m - m0;
+      int r = item - M.item_base, pl = 0;
+      if constexpr (C444) {
+        pl = div_small(r, M.tiles_per_plane, M.inv_tiles_per_plane);
+        r -= pl * M.tiles_per_plane;
+      }
+      const int ty = div_small(r, M.tiles_x, M.inv_tiles_x), tx = r - ty * M.tiles_x;
+      const int bx = tx * BPT + b % BPT, by = ty * BPT + b / BPT;
+      if (bx < M.nbx && by < M.nby) {
+        const int64_t k = (int64_t)by * M.nbx + bx;
+        const float* bv = M.blockvals + k;
+#pragma unroll
+        for (int row = 0; row < N_ROWS; ++row)
+          if (!C444 || row / 2 == pl) v[row] = fixed23(bv[row * M.C]);
+        if (!C444 || pl == 0) {
+          const TcRedMember& R = p.red[M.red];
+          const int pb = (M.red_flags & kRedPrevBuf) ? 1 : 0;
+          const float hy = bv[0];
+          const unsigned long long fh = fixed23(hy);
+          const unsigned long long fp = (M.red_flags & kRedHasPrev) ? fixed23(R.prevH[pb][k]) : fh;
+          v[kRedSums - 1] = fh > fp ? fh - fp : fp - fh;
+          R.prevH[pb ^ 1][k] = hy;
+        }
+      }
+    }
+    const int seg0 = __shfl_sync(0xffffffffu, seg, 0);
+    if (__all_sync(0xffffffffu, seg == seg0 || seg < 0) && seg0 >= 0) {
+#pragma unroll
+      for (int r = 0; r < kRedSums; ++r) {
+        const unsigned long long w = warp_sum64(v[r]);
+        if (lane == 0) add_split(scratch + (seg0 * kRedSums + r) * 2, w);
+      }
+    } else if (seg >= 0) {
+#pragma unroll
+      for (int r = 0; r < kRedSums; ++r) add_split(scratch + (seg * kRedSums + r) * 2, v[r]);
+    }
+  }
+  __syncthreads();
+  // 2. each segment's totals to its member's accumulators
+  for (int i = tid; i < nseg * kRedSums; i += kThreads) {
+    const int sg = i / kRedSums, r = i % kRedSums;
+    const TcMember& M = ms[m0 + sg];
+    unsigned long long* acc = p.red[M.red].acc[(M.red_flags & kRedGraph) ? 1 : 0] + 2 * r;
+    // the segment's total lo + hi * 2^32, as a low-32-bit part and the rest
+    U128 t{scratch[i * 2], 0ull};
+    const unsigned long long hi = scratch[i * 2 + 1];
+    add_to(t, U128{hi << 32, hi >> 32});
+    atomicAdd(acc, t.lo & 0xFFFFFFFFull);
+    atomicAdd(acc + 1, (t.lo >> 32) | (t.hi << 32));
+    __threadfence();  // the totals before the count
+  }
+  __syncthreads();
+  // 3. one count per segment: this CTA's tiles of the member
+  for (int sg = tid; sg < nseg; sg += kThreads) {
+    const TcMember& M = ms[m0 + sg];
+    const int lo = max(item0, M.item_base), hi = min(item0 + n_items, M.item_base + M.tiles_per_frame);
+    const unsigned n = (unsigned)(hi - lo);
+    flags[sg] = atomicAdd(p.red[M.red].done[(M.red_flags & kRedGraph) ? 1 : 0], n) + n == (unsigned)M.tiles_per_frame;
+  }
+  __syncthreads();
+  // 4. the members this CTA completed: features, and the state left at zero
+  for (int i = tid; i < nseg * kRedSums; i += kThreads) {
+    const int sg = i / kRedSums, r = i % kRedSums;
+    if (!flags[sg]) continue;
+    __threadfence();  // every other CTA fenced its totals before its count
+    const TcMember& M = ms[m0 + sg];
+    const TcRedMember& R = p.red[M.red];
+    const int g = (M.red_flags & kRedGraph) ? 1 : 0;
+    volatile unsigned long long* acc = R.acc[g];
+    const unsigned long long lo = acc[2 * r], hi = acc[2 * r + 1];
+    U128 t{lo, 0ull};
+    add_to(t, U128{hi << 32, hi >> 32});
+    int slot;
+    const double f = feature_of_sum(r, t, (double)M.C, R.normY, R.normC, slot);
+    R.feats[g][slot] = f;
+    acc[2 * r] = 0ull;
+    acc[2 * r + 1] = 0ull;
+    if (r == 0) {
+      R.feats[g][7] = 0.0;
+      *R.done[g] = 0u;
+    }
+  }
+}
+
 template <bool LP, bool SUB, bool DUMP, int BPS, bool BATCH, bool C444>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_kernel(const __grid_constant__ TcParamsT<BATCH ? kMaxMembers : 1> p) {
@@ -1174,7 +1357,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     n_items = cta < total_items ? (total_items - cta + grid - 1) / grid : 0;
     step = grid;
   }
-  Ctl ctl{bars, abort_flag, p.err, p.wait_ns > 0 ? (uint64_t)p.wait_ns : kWaitNs};
+  Ctl ctl{bars, abort_flag, p.err, BATCH ? p.err_host : nullptr, p.wait_ns > 0 ? (uint64_t)p.wait_ns : kWaitNs};
 
   using MS = typename MemberView<BATCH>::T;
   MS ms = [&] {
@@ -1373,6 +1556,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     tmem_dealloc(tmem, kTmemCols);
   }
+  // Batched ticks: this CTA's share of its members' frame reductions (not after a wait ran out:
+  // the tick is lost, and the host clears its graph's reduction state).
+  if constexpr (BATCH) {
+    if (!*abort_flag) red_tail<SUB, C444>(p, item0, n_items, reinterpret_cast<unsigned long long*>(sm + OFF_RAW));
+  }
 }
 
 // ---- host side -------------------------------------------------------------------
@@ -1559,7 +1747,7 @@ int tc_batch_max_members() { return kMaxMembers; }
 size_t tc_batch_params_bytes() { return sizeof(TcBatchParams); }
 
 cudaError_t tc_batch_fill(void* params, const TcBatchFrame* frames, int n, const DeviceTables& t, int* err,
-                          long long wait_ns, int withhold) {
+                          const TcRedMember* red, double* err_host, long long wait_ns, int withhold) {
   if (n < 0 || n > kMaxMembers) return cudaErrorInvalidValue;
   TcBatchParams& p = *static_cast<TcBatchParams*>(params);
   p.zdump[0] = p.zdump[1] = p.zdump[2] = nullptr;
@@ -1568,6 +1756,8 @@ cudaError_t tc_batch_fill(void* params, const TcBatchFrame* frames, int n, const
   p.W_y = t.W_y;
   p.W_c = t.W_c;
   p.err = err;
+  p.red = red;
+  p.err_host = err_host;
   p.wait_ns = wait_ns;
   p.withhold = withhold;
   int items = 0;
@@ -1577,6 +1767,8 @@ cudaError_t tc_batch_fill(void* params, const TcBatchFrame* frames, int n, const
     if (!tc_supported(g) || g.bps != frames[0].g->bps || g.w != frames[0].g->w || g.nc != frames[0].g->nc)
       return cudaErrorInvalidValue;
     items += fill_member(p.mem[i], g, items, 1, frames[i].blockvals);
+    p.mem[i].red = frames[i].red;
+    p.mem[i].red_flags = frames[i].red_flags;
     TcMapCache* c = frames[i].maps;
     const TcMapCache::Entry* hit = nullptr;
     for (int j = 0; c && j < c->n && !hit; ++j) {

@@ -1,5 +1,7 @@
-"""Batched multi-stream ticks (one launch of the block kernel and one of the reduction for one
-frame of every channel, replayed from a CUDA graph) against single analyzers and the oracle.
+"""Batched multi-stream ticks (one frame of every channel per tick, replayed from a CUDA graph:
+on tensor cores one launch per sample size that also reduces each frame to its features, on CUDA
+cores one launch of the block kernel and one of the reduction) against single analyzers and the
+oracle.
 
 Channels of one batch differ in frame size (ragged block grids included) and bit depth; some
 ticks skip a channel.  Each channel's features must equal, bit for bit, those of its own
@@ -78,8 +80,10 @@ def test_batch_matches_single_analyzers_and_oracle(vca, block_size, low_pass, ki
                 fed[i].append(t)
             batch.tick(refs)
         batch.sync()
-        groups = len({bd > 8 for (_, _, bd) in channels}) if kind == "tc" else 1
-        assert batch.launches() == (groups + 1) * TICKS  # analysis launches per tick, then the reduction
+        # tensor cores: one launch per sample size, the reduction inside; CUDA cores: the block
+        # kernel, then the reduction
+        per_tick = len({bd > 8 for (_, _, bd) in channels}) if kind == "tc" else 2
+        assert batch.launches() == per_tick * TICKS
         for i, (w, h, bd) in enumerate(channels):
             got = [members[i].frame_features(k) for k in range(len(fed[i]))]
             exp = [singles[i].frame_features(k) for k in range(len(fed[i]))]
@@ -252,9 +256,9 @@ def test_batch_with_drop_in_matrices(vca):
 
 def test_batch_beyond_one_member_table_stays_on_tensor_cores(vca):
     # A tensor-core launch holds at most 64 members: 66 8-bit and 5 10-bit analyzers tick as three
-    # analysis launches (8-bit: 64 + 2 members, one after another; 10-bit: 5, beside them) and two
-    # reduction launches (64 + 7 members), every member matching its single analyzer bit for bit
-    # and the oracle; one member skips a tick.
+    # launches (8-bit: 64 + 2 members, one after another; 10-bit: 5, beside them), each reducing
+    # its members' frames, every member matching its single analyzer bit for bit and the oracle;
+    # one member skips a tick.
     n8, n10 = 66, 5
     f8 = frames_list(SequenceSpec(64, 64, 3, 95, sigma=4.0))
     f10 = frames_list(SequenceSpec(64, 64, 3, 96, bit_depth=10, sigma=4.0))
@@ -275,7 +279,7 @@ def test_batch_beyond_one_member_table_stays_on_tensor_cores(vca):
                 single8.push(d8[0][t], d8[1][t], d8[2][t])
                 single10.push(d10[0][t], d10[1][t], d10[2][t])
             batch.sync()
-            assert batch.launches() == 3 * (3 + 2)
+            assert batch.launches() == 3 * 3
         exp8 = [single8.frame_features(t) for t in range(3)]
         exp10 = [single10.frame_features(t) for t in range(3)]
         for i in (0, 1, 63, 64):
