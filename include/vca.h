@@ -219,9 +219,10 @@ vca_status vca_close(vca_analyzer* a);
 /* ---- Batched multi-stream ticks --------------------------------------------------------
  *
  * A batch ticks many analyzers (channels) together: each tick analyses one frame per analyzer
- * with one launch of the batched CUDA-core block kernel (Section 2 of the paper: integer DCT,
- * texture energy and brightness of every block of every channel) and one launch of the batched
- * frame reduction, replayed from a CUDA graph.  The analyzers may differ in frame size and bit
+ * (Section 2 of the paper: integer DCT, texture energy and brightness of every block of every
+ * channel, then the frame's seven features), replayed from a CUDA graph: with the persistent
+ * tensor-core kernel, which also reduces the frames to their features, or with one launch of the
+ * batched CUDA-core block kernel and one of the batched frame reduction.  The analyzers may differ in frame size and bit
  * depth; they must share device, block size, chroma format and low_pass.  Features arrive in each analyzer as
  * if its frames had been pushed one at a time: read them with vca_read_frame_features /
  * vca_read_sequence_features, and the h state carries across ticks and across the batch's
@@ -244,12 +245,13 @@ typedef struct {
  * tensor-core kernel (with the same DCT matrices), a tick analyses them with the persistent
  * tensor-core kernel: the 8-bit members and the 10-bit members on two branches of the tick
  * graph, side by side with the device's SMs split between them in proportion to their tiles,
- * each branch one launch per 64 members (one after another), then one reduction launch per 64
- * members.  The tensor maps of a tick's frames are encoded on the host; each analyzer keeps those
- * of its last 8 distinct frames (by plane pointers and pitches), so frames ticked from a ring of
- * up to 8 buffers per channel are encoded once.  Otherwise a tick is one launch of the batched
- * CUDA-core kernel, whose CTA map is built here.  VCA_E_ARG for mismatched devices, block sizes
- * or low_pass. */
+ * each branch one launch per 64 members (one after another); each launch ends by reducing its
+ * members' frames to their features (exact sums, identical to a single analyzer's).  The tensor
+ * maps of a tick's frames are encoded on the host; each analyzer keeps those of its last 8
+ * distinct frames (by plane pointers and pitches), so frames ticked from a ring of up to 8
+ * buffers per channel are encoded once.  Otherwise a tick is one launch of the batched CUDA-core
+ * kernel, whose CTA map is built here, and one of the batched reduction.  VCA_E_ARG for
+ * mismatched devices, block sizes or low_pass. */
 vca_status vca_batch_create(vca_analyzer* const* members, int32_t n, vca_batch** out);
 
 /* The kernel family a batch's ticks run: VCA_KERNEL_TC or VCA_KERNEL_PLAIN. */
@@ -266,8 +268,8 @@ vca_status vca_batch_tick(vca_batch* b, const vca_frame_ref* frames);
  * analyzers' frame counters and h state have moved on). */
 vca_status vca_batch_sync(vca_batch* b);
 
-/* Kernel launches issued by the batch's ticks: per tick, the analysis (two launches for a
- * tensor-core batch with 8- and 10-bit members, else one) and the reduction. */
+/* Kernel launches issued by the batch's ticks: per tick, for a tensor-core batch one launch per
+ * sample size and 64 members (analysis and reduction), else the analysis and the reduction. */
 vca_status vca_batch_launch_count(vca_batch* b, int64_t* launches);
 
 /* Waits for the batch's ticks and dissolves it; the analyzers stay open.  NULL is accepted. */
