@@ -38,7 +38,8 @@ PAPER_FPS = 292.68  # paper, Section 3: VCA v2.0 with all optimisations on 8 CPU
 W, H = 3840, 2160
 FRAME_BYTES = W * H + 2 * (W // 2) * (H // 2)  # 12,441,600 B per 8-bit 4:2:0 frame
 KERNEL_SOURCES = ("paper_2304_12384_gb300/csrc/vca_tc.cu", "paper_2304_12384_gb300/csrc/vca_plain.cu",
-                  "paper_2304_12384_gb300/csrc/vca_plain.cuh", "paper_2304_12384_gb300/csrc/vca_ptx.cuh")
+                  "paper_2304_12384_gb300/csrc/vca_plain.cuh", "paper_2304_12384_gb300/csrc/vca_ptx.cuh",
+                  "paper_2304_12384_gb300/csrc/vca_fixed.cuh")
 
 
 def parse_args():
