@@ -67,6 +67,7 @@
 #include <cuda.h>
 #include <cuda_fp16.h>
 
+#include <climits>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -123,6 +124,7 @@ struct Blk {
   static constexpr int NC = SUB ? 8 : 16;   // chroma block size
 };
 static_assert(sizeof(TcMember) % 8 == 0, "member table entries are copied as words");
+static_assert(sizeof(TcRedMember) % 8 == 0, "reduction entries are copied as words");
 
 
 // Shared-memory layout for BPS bytes per sample.  8-bit: a 128x128 luma tile (128-byte rows,
@@ -150,7 +152,8 @@ struct SmemLay {
   static constexpr int OFF_REC = OFF_K2CL + 1024;              // tile records (16 x 32 B)
   static constexpr int OFF_BAR = OFF_REC + 16 * 32;
   static constexpr int OFF_MISC = OFF_BAR + 48 * 8;
-  static constexpr int kSmemBytes = OFF_MISC + 64 + 1024;  // + slack to align the base to 1024
+  static constexpr int OFF_REDTAB = OFF_MISC + 64;            // batched ticks: the CTA's members' reduction entries
+  static constexpr int kSmemBytes = OFF_REDTAB + kMaxMembers * (int)sizeof(TcRedMember) + 1024;  // + alignment slack
   static_assert(kStages <= kMaxStages && OFF_A2 % 1024 == 0 && kA2Unit % 1024 == 0 && kSmemBytes <= 232448,
                 "layout");
 };
@@ -1185,10 +1188,12 @@ __device__ void issuer_loop(const Ctl& ctl, uint32_t sbase, uint32_t tmem, int i
 // After its role loops a CTA reduces the block values of its own tiles, still in L2.  Its run of
 // tiles covers one or more members ("segments"); all segments go through each step together, so
 // the tail costs a few memory round trips however many members the run touches:
-//   1. every thread takes one block at a time: fixed23 of the six rows (4:4:4: of its plane's two)
-//      and, for luma rows, |H - H_prev|, writing H as the next tick's previous energy; a warp
-//      whose 32 blocks are of one segment adds its warp sums to the segment's totals in shared
-//      memory, other warps add per thread (the totals kept as low-32-bit and high parts, exact);
+//   1. every thread takes one block at a time (kThreads blocks per pass): fixed23 of the six rows
+//      (4:4:4: of its plane's two) and, for luma rows, |H - H_prev|, writing H as the next tick's
+//      previous energy; a warp whose blocks are of one segment stores its warp sums in a slot of
+//      its own, then warp r adds sum r of every slot into the segments' totals in shared memory
+//      (warps whose blocks straddle two segments add per thread, atomically); the totals are kept
+//      as low-32-bit and high parts, exact;
 //   2. the totals of every segment go to the members' accumulators in global memory;
 //   3. one count per segment (its tiles); the CTA whose count completes a member
 //   4. writes the features -- the same exact totals, rounded once, as the separate frame
@@ -1213,13 +1218,21 @@ __device__ __forceinline__ void add_split(unsigned long long* t, unsigned long l
 }
 
 // scratch: shared memory (the raw ring, no longer in use) for kMaxMembers segments x kRedSums
-// split totals and a flag per segment.  Blocks are taken kThreads at a time, one per thread.
+// split totals, a flag per segment and the warps' slots.  Blocks are taken kThreads at a time,
+// one per thread.
+// tab: the reduction entries of the CTA's members (tab[m - m0] for member m, m0 the CTA's first),
+// copied into shared memory when the launch started.
 template <bool SUB, bool C444, class PP>
-__device__ __noinline__ void red_tail(const PP& p, int item0, int n_items, unsigned long long* scratch) {
+__device__ __noinline__ void red_tail(const PP& p, int item0, int n_items, unsigned long long* scratch,
+                                      const TcRedMember* tab) {
   constexpr int BPT = SUB ? 8 : 4;  // blocks per tile side
   constexpr int BPT2 = BPT * BPT;
   const int tid = threadIdx.x, lane = tid & 31;
+  constexpr int kWarps = kThreads / 32;
   int* flags = reinterpret_cast<int*>(scratch + kMaxMembers * kRedSums * 2);
+  unsigned long long* wslot = scratch + kMaxMembers * kRedSums * 2 + kMaxMembers / 2;  // [kWarps][kRedSums]
+  int* wseg = reinterpret_cast<int*>(wslot + kWarps * kRedSums);                     // segment of each slot
+  const int warp = tid >> 5;
   if (n_items <= 0) return;
   MemberTable ms{p.mem, p.n_members, 0};
   const int m0 = ms.member_of(item0);
@@ -1254,7 +1267,7 @@ __device__ __noinline__ void red_tail(const PP& p, int item0, int n_items, unsig
         for (int row = 0; row < N_ROWS; ++row)
           if (!C444 || row / 2 == pl) v[row] = fixed23(bv[row * M.C]);
         if (!C444 || pl == 0) {
-          const TcRedMember& R = p.red[M.red];
+          const TcRedMember& R = tab[seg];
           const int pb = (M.red_flags & kRedPrevBuf) ? 1 : 0;
           const float hy = bv[0];
           const unsigned long long fh = fixed23(hy);
@@ -1265,23 +1278,43 @@ __device__ __noinline__ void red_tail(const PP& p, int item0, int n_items, unsig
       }
     }
     const int seg0 = __shfl_sync(0xffffffffu, seg, 0);
-    if (__all_sync(0xffffffffu, seg == seg0 || seg < 0) && seg0 >= 0) {
+    if (__all_sync(0xffffffffu, seg == seg0 || seg < 0)) {
 #pragma unroll
       for (int r = 0; r < kRedSums; ++r) {
         const unsigned long long w = warp_sum64(v[r]);
-        if (lane == 0) add_split(scratch + (seg0 * kRedSums + r) * 2, w);
+        if (lane == 0) wslot[warp * kRedSums + r] = w;
       }
-    } else if (seg >= 0) {
+      if (lane == 0) wseg[warp] = seg0;  // -1: no blocks
+    } else {
+      if (seg >= 0) {
 #pragma unroll
-      for (int r = 0; r < kRedSums; ++r) add_split(scratch + (seg * kRedSums + r) * 2, v[r]);
+        for (int r = 0; r < kRedSums; ++r) add_split(scratch + (seg * kRedSums + r) * 2, v[r]);
+      }
+      if (lane == 0) wseg[warp] = -1;
     }
+    __syncthreads();
+    // Warp r folds sum r of the slots (each below 2^58) into the segments' totals; the segments of
+    // a pass are consecutive, in the order of the warps.
+    if (warp < kRedSums) {
+      const int sl = wseg[lane];
+      const unsigned long long x = sl >= 0 ? wslot[lane * kRedSums + warp] : 0ull;
+      const int first = __reduce_min_sync(0xffffffffu, sl >= 0 ? sl : INT_MAX);
+      const int last = __reduce_max_sync(0xffffffffu, sl);
+      for (int sg = first; sg <= last; ++sg) {
+        const unsigned long long t = warp_sum64(sl == sg ? x : 0ull);
+        if (lane == 0) {
+          scratch[(sg * kRedSums + warp) * 2] += t & 0xFFFFFFFFull;
+          scratch[(sg * kRedSums + warp) * 2 + 1] += t >> 32;
+        }
+      }
+    }
+    __syncthreads();  // the slots are reused by the next pass
   }
-  __syncthreads();
   // 2. each segment's totals to its member's accumulators
   for (int i = tid; i < nseg * kRedSums; i += kThreads) {
     const int sg = i / kRedSums, r = i % kRedSums;
     const TcMember& M = ms[m0 + sg];
-    unsigned long long* acc = p.red[M.red].acc[(M.red_flags & kRedGraph) ? 1 : 0] + 2 * r;
+    unsigned long long* acc = tab[sg].acc[(M.red_flags & kRedGraph) ? 1 : 0] + 2 * r;
     // the segment's total lo + hi * 2^32, as a low-32-bit part and the rest
     U128 t{scratch[i * 2], 0ull};
     const unsigned long long hi = scratch[i * 2 + 1];
@@ -1296,7 +1329,7 @@ __device__ __noinline__ void red_tail(const PP& p, int item0, int n_items, unsig
     const TcMember& M = ms[m0 + sg];
     const int lo = max(item0, M.item_base), hi = min(item0 + n_items, M.item_base + M.tiles_per_frame);
     const unsigned n = (unsigned)(hi - lo);
-    flags[sg] = atomicAdd(p.red[M.red].done[(M.red_flags & kRedGraph) ? 1 : 0], n) + n == (unsigned)M.tiles_per_frame;
+    flags[sg] = atomicAdd(tab[sg].done[(M.red_flags & kRedGraph) ? 1 : 0], n) + n == (unsigned)M.tiles_per_frame;
   }
   __syncthreads();
   // 4. the members this CTA completed: features, and the state left at zero
@@ -1305,7 +1338,7 @@ __device__ __noinline__ void red_tail(const PP& p, int item0, int n_items, unsig
     if (!flags[sg]) continue;
     __threadfence();  // every other CTA fenced its totals before its count
     const TcMember& M = ms[m0 + sg];
-    const TcRedMember& R = p.red[M.red];
+    const TcRedMember& R = tab[sg];
     const int g = (M.red_flags & kRedGraph) ? 1 : 0;
     volatile unsigned long long* acc = R.acc[g];
     const unsigned long long lo = acc[2 * r], hi = acc[2 * r + 1];
@@ -1446,6 +1479,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     const float v = kk == 0 ? (float)a : kk == 1 ? (float)(P - a * 1024) : 0.0f;
     *(__half*)(sm + off + (n >> 3) * 256 + (kk >> 3) * 128 + (n & 7) * 16 + (kk & 7) * 2) = __float2half_rn(v);
   }
+  if constexpr (BATCH) {
+    // The reduction entries of this CTA's members, for the launch's tail: read there from shared
+    // memory, each phase of the tail saves a dependent global load.
+    if (n_items > 0) {
+      MemberTable mt{p.mem, p.n_members, 0};
+      const int m0 = mt.member_of(item0);
+      const int nm = mt.member_of(item0 + n_items - 1) - m0 + 1;
+      constexpr int W = (int)(sizeof(TcRedMember) / 8);
+      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(p.red);
+      unsigned long long* dst = reinterpret_cast<unsigned long long*>(sm + SL::OFF_REDTAB);
+      for (int i = tid; i < nm * W; i += kThreads) dst[i] = src[(int64_t)mt[m0 + i / W].red * W + i % W];
+    }
+  }
   if (tid == 0) {
     for (int i = 0; i < kBars; ++i) mbar_init(&bars[i], 1);
     for (int i = 0; i < SL::kStages; ++i)
@@ -1559,7 +1605,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   // Batched ticks: this CTA's share of its members' frame reductions (not after a wait ran out:
   // the tick is lost, and the host clears its graph's reduction state).
   if constexpr (BATCH) {
-    if (!*abort_flag) red_tail<SUB, C444>(p, item0, n_items, reinterpret_cast<unsigned long long*>(sm + OFF_RAW));
+    if (!*abort_flag)
+      red_tail<SUB, C444>(p, item0, n_items, reinterpret_cast<unsigned long long*>(sm + OFF_RAW),
+                          reinterpret_cast<const TcRedMember*>(sm + SL::OFF_REDTAB));
   }
 }
 
