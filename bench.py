@@ -581,9 +581,9 @@ def run_extras(args, an, y, u, v, frames, stream, kern, lp, device):
 
 def run_ladder(args, stream, distinct=2, ticks=200):
     """24-channel ladder tick (4 channels at each of 640x360 .. 3840x2160, half 10-bit, block 32,
-    low-pass): the batched path (one graph per tick: a tensor-core launch per sample size and the
-    reduction for all channels) against one push per channel per tick through the
-    single-analyzer path."""
+    low-pass): the batched path (one graph per tick: a tensor-core launch per sample size, each
+    ending with the reduction of its channels' frames) against one push per channel per tick
+    through the single-analyzer path."""
     import numpy as np
     import torch
 

@@ -538,7 +538,8 @@ class Analyzer:
 
 
 class Batch:
-    """Analyzers ticked together: one frame per analyzer per tick in one batched launch."""
+    """Analyzers ticked together: one frame per analyzer per tick, replayed from a CUDA graph (on
+    tensor cores one launch per sample size, the frame reduction inside)."""
 
     def __init__(self, analyzers):
         self.analyzers = list(analyzers)
