@@ -1537,6 +1537,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       // ---------------- TMA producer: tiles in order into the ring ----------------
       int issued = 0;
+      const uint64_t pol = BATCH ? l2_evict_first_policy() : 0ull;
       for (int t = 0; t < n_items; ++t) {
         const int stage = t % SL::kStages;
         if (t >= SL::kStages && !wait_bar<LP>(ctl, b_raw_empty(stage), ((t / SL::kStages) - 1) & 1, 1, false, true))
@@ -1559,15 +1560,24 @@ __global__ void __launch_bounds__(kThreads, 1)
           continue;
         }
         mbar_arrive_expect_tx(full, C444 ? SL::kRawY : SL::kStageBytes);
+        // Batched ticks load the frames, which are read once, to be evicted from L2 first, so that
+        // the block values and previous energies the launch's reduction tail reads back stay there
+        // (2 % more ticks per second on the 24-channel ladder).
+        auto load = [&](void* d, const CUtensorMap* map, int x, int y) {
+          if constexpr (BATCH)
+            tma_load_3d_hint(d, map, x, y, ti.f, full, pol);
+          else
+            tma_load_3d(d, map, x, y, ti.f, full);
+        };
         if (BPS == 1) {
-          tma_load_3d(dst, mm, ti.tx * 128, ti.ty * 128, ti.f, full);
+          load(dst, mm, ti.tx * 128, ti.ty * 128);
         } else {  // 16-bit luma: the tile is two 64-sample boxes side by side
-          tma_load_3d(dst, mm, ti.tx * 128, ti.ty * 128, ti.f, full);
-          tma_load_3d(dst + 128 * 64 * 2, mm, ti.tx * 128 + 64, ti.ty * 128, ti.f, full);
+          load(dst, mm, ti.tx * 128, ti.ty * 128);
+          load(dst + 128 * 64 * 2, mm, ti.tx * 128 + 64, ti.ty * 128);
         }
         if (!C444) {
-          tma_load_3d(dst + SL::kRawY, mm + 1, ti.tx * 64, ti.ty * 64, ti.f, full);
-          tma_load_3d(dst + SL::kRawY + SL::kRawC, mm + 2, ti.tx * 64, ti.ty * 64, ti.f, full);
+          load(dst + SL::kRawY, mm + 1, ti.tx * 64, ti.ty * 64);
+          load(dst + SL::kRawY + SL::kRawC, mm + 2, ti.tx * 64, ti.ty * 64);
         }
         ++issued;
       }
