@@ -396,3 +396,41 @@ def test_ladder_size_batch_matches_single_analyzers(vca):
     finally:
         for a in members + singles:
             a.close()
+
+
+def test_batch_tail_over_several_passes_matches_single_analyzers(vca):
+    # 24 channels at 1920x1080 with 16x16 blocks: 3,240 tiles on the device's CTAs, about 21 tiles
+    # of 64 blocks per CTA, so each CTA's reduction tail takes its blocks in two passes of 1,024
+    # and its run spans several members (some of whose blocks share a warp with the next
+    # member's).  Half the channels 10-bit, one skips a tick; three ticks against single analyzers
+    # fed the same frames, bit for bit, and one channel against the oracle.
+    n = 24
+    specs = [SequenceSpec(1920, 1080, 3, 900 + i, bit_depth=8 if i % 2 == 0 else 10, sigma=4.0, motion=3)
+             for i in range(n)]
+    frames = [frames_list(sp) for sp in specs]
+    dev = [to_device(f) for f in frames]
+    members = [vca.Analyzer(1920, 1080, sp.bit_depth, 16, True, max_batch=1) for sp in specs]
+    singles = [vca.Analyzer(1920, 1080, sp.bit_depth, 16, True, max_batch=1) for sp in specs]
+    fed = [[] for _ in range(n)]
+    try:
+        with vca.Batch(members) as batch:
+            assert batch.kernel == vca.VCA_KERNEL_TC
+            for t in range(3):
+                refs = []
+                for i, (y, u, v) in enumerate(dev):
+                    if (t, i) == (1, 5):
+                        refs.append(None)
+                        continue
+                    refs.append((y[t], u[t], v[t]))
+                    singles[i].push(y[t], u[t], v[t])
+                    fed[i].append(t)
+                batch.tick(refs)
+        for i, (m, a) in enumerate(zip(members, singles)):
+            k = len(fed[i])
+            assert [m.frame_features(j) for j in range(k)] == [a.frame_features(j) for j in range(k)], f"channel {i}"
+        per, _ = oracle_sequence(frames[3][:3], oracle_config(members[3]))
+        for t in range(3):
+            assert_features_close(members[3].frame_features(t), per[t], where=f"channel 3 frame {t}")
+    finally:
+        for a in members + singles:
+            a.close()
