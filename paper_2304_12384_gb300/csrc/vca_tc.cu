@@ -1537,7 +1537,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       // ---------------- TMA producer: tiles in order into the ring ----------------
       int issued = 0;
-      const uint64_t pol = BATCH ? l2_evict_first_policy() : 0ull;
+      const uint64_t pol = l2_evict_first_policy();
       for (int t = 0; t < n_items; ++t) {
         const int stage = t % SL::kStages;
         if (t >= SL::kStages && !wait_bar<LP>(ctl, b_raw_empty(stage), ((t / SL::kStages) - 1) & 1, 1, false, true))
@@ -1560,14 +1560,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           continue;
         }
         mbar_arrive_expect_tx(full, C444 ? SL::kRawY : SL::kStageBytes);
-        // Batched ticks load the frames, which are read once, to be evicted from L2 first, so that
-        // the block values and previous energies the launch's reduction tail reads back stay there
-        // (2 % more ticks per second on the 24-channel ladder).
+        // The frames are read once: loaded to be evicted from L2 first, so that what is read again
+        // stays there -- in a batched tick the block values and previous energies that the
+        // launch's reduction tail reads back (2 % more ticks per second on the 24-channel ladder;
+        // single analyzers' low-pass launches measured 0.8 % faster).
         auto load = [&](void* d, const CUtensorMap* map, int x, int y) {
-          if constexpr (BATCH)
-            tma_load_3d_hint(d, map, x, y, ti.f, full, pol);
-          else
-            tma_load_3d(d, map, x, y, ti.f, full);
+          tma_load_3d_hint(d, map, x, y, ti.f, full, pol);
         };
         if (BPS == 1) {
           load(dst, mm, ti.tx * 128, ti.ty * 128);
